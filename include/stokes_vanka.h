@@ -1,0 +1,180 @@
+/*
+ * stokes_vanka.h -- C ABI of the GB300 (sm_103a) Q2-Q1 Stokes solver:
+ * FGMRES right-preconditioned by a monolithic geometric-multigrid V-cycle
+ * with additive Vanka relaxation.
+ *
+ * Paper: Spies, Olson, MacLachlan, "Exploiting mesh structure to improve
+ * multigrid performance for saddle point problems".
+ *   Section 2.1  -nu Lap u + grad p = f, div u = 0 on the unit square,
+ *                Dirichlet velocity on every edge, pressure in L2/R.
+ *   Section 2.2  Q2-Q1 Taylor-Hood on a uniform n x n grid,
+ *                A = [[L, B^T], [B, 0]], L_ij = a(psi_j, psi_i),
+ *                B_kj = b(psi_j, phi_k).
+ *   Section 2.3  lexicographic numbering on the structured grid.
+ *   Section 3    Algorithm 1 (MG): V-cycle, FE interpolation P, restriction P^T,
+ *                exact solve on the coarsest level (level 0).
+ *   Section 3.2  Algorithm 3 (additive Vanka): x += sum_i V_i^T W_i A_i^-1 V_i r.
+ *   Section 6.3  25 distinct patch matrices on a uniform grid (shared inverses).
+ *   Section 6.8  FGMRES preconditioned by the V-cycle.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Vectors are contiguous float64 DEVICE arrays owned by the caller, laid out
+ *    as [u_x | u_y | p]: u_x and u_y on the (2n+1)^2 Q2 nodes, p on the (n+1)^2
+ *    vertices, each row-major with the x index fastest; node (I, J) sits at
+ *    (I/(2n), J/(2n)), vertex (i, j) at (i/n, j/n).  Length
+ *    N(n) = 2 (2n+1)^2 + (n+1)^2.  Vectors of a level l use that level's n.
+ *  - The operator A is the Dirichlet-eliminated one: rows and columns of
+ *    boundary velocity nodes are identity rows/columns; it is symmetric and
+ *    singular with kernel (0, 1_p).  b(v, p) = -int p div v.
+ *  - Levels are numbered as in Algorithm 1: level 0 is the coarsest
+ *    (coarse_n x coarse_n), level L-1 the finest (n x n).
+ *  - Every call is stream-ordered on the stream given at creation and returns
+ *    without a host synchronisation, except stokes_fgmres_solve, the adjoint
+ *    and batched solves, which synchronise to read the convergence test.
+ *  - Input and output arrays must not overlap unless a call says otherwise.
+ *  - No C++ exception crosses this boundary.  Every call returns a
+ *    stokes_status; on failure stokes_last_error() returns a message
+ *    (thread-local, valid until the next call on the same thread).
+ *  - The hierarchy owns its workspace (level vectors, patch inverses, the
+ *    Krylov basis) and frees it in stokes_hierarchy_destroy.
+ */
+#ifndef STOKES_VANKA_H
+#define STOKES_VANKA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  STOKES_OK = 0,
+  STOKES_ERR_ARG = 1,        /* bad argument: size, null pointer, level index   */
+  STOKES_ERR_OOM = 2,        /* device allocation failed                         */
+  STOKES_ERR_CUDA = 3,       /* a CUDA runtime call or a kernel launch failed    */
+  STOKES_ERR_NONFINITE = 4,  /* NaN/Inf met in the right-hand side or residual   */
+  STOKES_NOT_CONVERGED = 5,  /* maxit reached; x holds the last iterate          */
+  STOKES_ERR_TIMEOUT = 6     /* a bounded device wait expired                    */
+} stokes_status;
+
+/* Arithmetic of the preconditioner.  FGMRES (residuals, Arnoldi, Givens, the
+ * update) and the coarse solve are FP64 in every mode. */
+typedef enum {
+  STOKES_FP64 = 0,        /* V-cycle entirely in FP64                              */
+  STOKES_MIXED_FP32 = 1,  /* V-cycle vectors, residuals and patch solves in FP32   */
+  STOKES_MIXED_BF16 = 2   /* as FP32, interior patch solves as BF16 tcgen05 GEMMs
+                             with FP32 accumulation                                */
+} stokes_precision;
+
+typedef struct {
+  int nu1;          /* pre-smoothing Vanka sweeps per level            (2)    */
+  int nu2;          /* post-smoothing Vanka sweeps per level           (2)    */
+  double omega;     /* Vanka damping: W_i = omega diag(1/m_j)          (0.7)  */
+  int coarse_n;     /* coarsest grid, >= 4; n = coarse_n * 2^k         (4)    */
+  int restart;      /* FGMRES restart length m, 1..64                  (30)   */
+  int maxit;        /* FGMRES iteration cap                            (1000) */
+  double rtol;      /* stop when ||b - A x|| <= rtol ||b - A x0||      (1e-8) */
+  stokes_precision prec;  /*                                          (FP64) */
+} stokes_params;
+
+typedef struct stokes_hierarchy stokes_hierarchy;
+
+/* Fill *p with the defaults shown above. */
+void stokes_default_params(stokes_params* p);
+
+/* Build the multigrid hierarchy for an n x n grid (Section 3: rediscretised
+ * levels n, n/2, ..., coarse_n), the 25 Vanka patch-class inverses per level
+ * (Section 6.3) and the coarse-grid inverse.  n must be coarse_n * 2^k with
+ * coarse_n >= 4.  viscosity > 0.  params may be NULL (defaults).  stream is a
+ * cudaStream_t (NULL = legacy default stream).  The Krylov workspace
+ * (2 restart + 1 vectors of N(n) doubles) is allocated here. */
+stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_params* params,
+                                      void* stream, stokes_hierarchy** out);
+stokes_status stokes_hierarchy_destroy(stokes_hierarchy* h);
+
+/* Number of levels L and the grid size n_l of level l (0 = coarsest). */
+stokes_status stokes_level_info(const stokes_hierarchy* h, int* num_levels, int* n_finest);
+stokes_status stokes_level_n(const stokes_hierarchy* h, int level, int* n_level);
+
+/* Right-hand side of the eliminated system (Section 2.2 with the boundary data
+ * moved to the right): b = [M f - L_{.,D} u_D on free velocity rows ;
+ * u_D on Dirichlet rows ; -B_{.,D} u_D on pressure rows].  f_nodal and
+ * u_dirichlet are [2, 2n+1, 2n+1] (nodal values; only the boundary entries of
+ * u_dirichlet are read), b has length N(n).  Finest level. */
+stokes_status stokes_assemble_rhs(stokes_hierarchy* h, const double* f_nodal,
+                                  const double* u_dirichlet, double* b);
+
+/* y = A x on level `level` (Section 2.2, the block matrix A). */
+stokes_status stokes_apply_operator(stokes_hierarchy* h, int level, const double* x, double* y);
+
+/* r = b - A x on level `level` (the residual step of Algorithm 1). */
+stokes_status stokes_residual(stokes_hierarchy* h, int level, const double* b, const double* x,
+                              double* r);
+
+/* One additive Vanka sweep on level `level` (Algorithm 3):
+ * x_out = x + sum_i V_i^T W_i A_i^-1 V_i (b - A x), W_i = omega diag(1/m_j),
+ * every patch using the same residual.  x == NULL means x = 0.  x_out must not
+ * alias x or b.  Runs in the hierarchy's precision for levels of the
+ * preconditioner; this entry point always uses FP64. */
+stokes_status stokes_vanka_sweep(stokes_hierarchy* h, int level, const double* x,
+                                 const double* b, double* x_out);
+
+/* r_coarse = P^T r_fine, from level `level` (>= 1) to level-1 (Algorithm 1,
+ * restriction).  P is the FE interpolation with Dirichlet rows/columns zero. */
+stokes_status stokes_restrict(stokes_hierarchy* h, int level, const double* r_fine,
+                              double* r_coarse);
+
+/* x_fine += P e_coarse, from level-1 to level `level` (>= 1) (Algorithm 1,
+ * correction). */
+stokes_status stokes_prolong_add(stokes_hierarchy* h, int level, const double* e_coarse,
+                                 double* x_fine);
+
+/* e = A_0^-1 r on level 0 (Algorithm 1, exact coarse solve): the solution of
+ * the bordered system [[A_0, e_p], [e_p^T, 0]] with e_p = (0, M_p 1), i.e. the
+ * pressure has zero mean.  FP64. */
+stokes_status stokes_coarse_solve(stokes_hierarchy* h, const double* r, double* e);
+
+/* x0 for FGMRES: x0 = b on Dirichlet velocity rows and 0 elsewhere (finest
+ * level; b and x0 of length N(n), may not alias). */
+stokes_status stokes_initial_guess(stokes_hierarchy* h, const double* b, double* x0);
+
+/* z = MG(r): one V(nu1, nu2) cycle on the finest level with zero initial
+ * guess (Algorithm 1).  r and z have length N(n); they must not alias. */
+stokes_status stokes_vcycle_apply(stokes_hierarchy* h, const double* r, double* z);
+
+/* Solve A x = b by FGMRES(restart) right-preconditioned with the V-cycle
+ * (Section 6.8).  x holds x0 on entry (its Dirichlet rows should equal b's)
+ * and the solution on exit.  iters (may be NULL) receives the number of
+ * preconditioned iterations, relres (may be NULL) the true relative residual
+ * ||b - A x|| / ||b - A x0|| recomputed in FP64 at exit.  Returns
+ * STOKES_NOT_CONVERGED after maxit iterations and STOKES_ERR_NONFINITE if b
+ * or a residual is not finite.  Synchronises the stream. */
+stokes_status stokes_fgmres_solve(stokes_hierarchy* h, const double* b, double* x, int* iters,
+                                  double* relres);
+
+/* Adjoint solve A^T lambda = g (A is symmetric, so the same FGMRES + MG solve
+ * with zero initial guess), then grad_f = R^T lambda where R maps nodal body
+ * forces to right-hand sides (b = R f + lifting): grad_f[c, J, I] =
+ * sum over free velocity rows k of M_(k),(I,J) lambda_k.  g has length N(n),
+ * lambda length N(n), grad_f length 2 (2n+1)^2.  grad_f may be NULL. */
+stokes_status stokes_solve_adjoint(stokes_hierarchy* h, const double* g, double* lambda,
+                                   double* grad_f, int* iters, double* relres);
+
+/* grad_f = R^T lambda (see stokes_solve_adjoint), without a solve. */
+stokes_status stokes_rhs_transpose(stokes_hierarchy* h, const double* lambda, double* grad_f);
+
+/* Solve nprob independent systems hs[k] x_k = b_k (each an FGMRES solve as
+ * above on its own hierarchy).  iters / relres are arrays of nprob entries
+ * (may be NULL).  Returns the first non-OK status. */
+stokes_status stokes_batched_solve(stokes_hierarchy* const* hs, int nprob, const double* const* b,
+                                   double* const* x, int* iters, double* relres);
+
+/* Message of the last failure on this thread ("" if none). */
+const char* stokes_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STOKES_VANKA_H */

@@ -1,0 +1,467 @@
+// sv_api.cu -- the C ABI (include/stokes_vanka.h): hierarchy set-up, the
+// V-cycle of Algorithm 1 driven from the host as a sequence of stream-ordered
+// kernel launches, and right-preconditioned FGMRES (Section 6.8) with every
+// vector operation on the device.  Only scalars of the convergence test cross
+// to the host (one 8-byte copy per iteration).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sv_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+stokes_status fail(stokes_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+stokes_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(e == cudaErrorMemoryAllocation ? STOKES_ERR_OOM : STOKES_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define SV_TRY(call, where)                       \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+stokes_status check_launch(const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, where);
+  return STOKES_OK;
+}
+
+sv::LevelDev make_level(int n, double nu) {
+  sv::LevelDev d;
+  d.n = n;
+  d.nq = 2 * n + 1;
+  d.np = n + 1;
+  d.nv = static_cast<long long>(d.nq) * d.nq;
+  d.N = 2 * d.nv + static_cast<long long>(d.np) * d.np;
+  d.h = 1.0 / n;
+  d.nu = nu;
+  return d;
+}
+
+void free_all(stokes_hierarchy* h) {
+  for (auto& L : h->lv) {
+    cudaFree(L.x0);
+    cudaFree(L.x1);
+    cudaFree(L.b);
+    cudaFree(L.r);
+    cudaFree(L.e);
+    cudaFree(L.cd);
+  }
+  h->lv.clear();
+  cudaFree(h->coarse_G);
+  cudaFree(h->V);
+  cudaFree(h->Z);
+  cudaFree(h->small);
+  cudaFree(h->partials);
+  if (h->host_scalars) cudaFreeHost(h->host_scalars);
+  h->coarse_G = h->V = h->Z = h->small = h->partials = h->host_scalars = nullptr;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+stokes_status check_level(const stokes_hierarchy* h, int level, int min_level = 0) {
+  if (h == nullptr) return fail(STOKES_ERR_ARG, "null hierarchy");
+  if (level < min_level || level >= static_cast<int>(h->lv.size()))
+    return fail(STOKES_ERR_ARG, "level index out of range");
+  return STOKES_OK;
+}
+
+// ---- V-cycle (Algorithm 1), FP64 ----
+void vcycle_f64(stokes_hierarchy* h, int l, const double* b, double* out) {
+  cudaStream_t s = h->stream;
+  sv::Level& L = h->lv[l];
+  if (l == 0) {
+    sv::launch_coarse(h->coarse_G, h->N0, b, out, s);
+    return;
+  }
+  const double w = h->prm.omega;
+  double* cur = nullptr;  // nullptr = zero initial guess
+  for (int it = 0; it < h->prm.nu1; ++it) {
+    double* dst = (cur == L.x0) ? L.x1 : L.x0;
+    sv::launch_vanka_f64(L.d, L.cd, cur, b, dst, w, s);
+    cur = dst;
+  }
+  if (cur == nullptr) {
+    sv::launch_fill(L.x0, 0.0, L.d.N, s);
+    cur = L.x0;
+  }
+  sv::Level& C = h->lv[l - 1];
+  sv::launch_apply(L.d, cur, b, L.r, 1, s);
+  sv::launch_restrict(L.d, C.d, L.r, C.b, s);
+  vcycle_f64(h, l - 1, C.b, C.e);
+  sv::launch_prolong_add(L.d, C.d, C.e, cur, s);
+  for (int it = 0; it < h->prm.nu2; ++it) {
+    double* dst = (it == h->prm.nu2 - 1) ? out : ((cur == L.x0) ? L.x1 : L.x0);
+    sv::launch_vanka_f64(L.d, L.cd, cur, b, dst, w, s);
+    cur = dst;
+  }
+  if (h->prm.nu2 == 0) cudaMemcpyAsync(out, cur, L.d.N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+
+stokes_status read_scalar(stokes_hierarchy* h, const double* dev, double* out) {
+  SV_TRY(cudaMemcpyAsync(h->host_scalars, dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+         "copy scalar");
+  SV_TRY(cudaStreamSynchronize(h->stream), "stream sync");
+  *out = h->host_scalars[0];
+  return STOKES_OK;
+}
+
+struct SmallBuf {
+  double *H, *g, *cs, *sn, *hcol, *h2, *y, *sc;
+};
+
+SmallBuf small_layout(stokes_hierarchy* h) {
+  const int m = h->m;
+  SmallBuf s;
+  s.H = h->small;
+  s.g = s.H + (m + 1) * m;
+  s.cs = s.g + (m + 1);
+  s.sn = s.cs + m;
+  s.hcol = s.sn + m;
+  s.h2 = s.hcol + (m + 1);
+  s.y = s.h2 + (m + 1);
+  s.sc = s.y + m;
+  return s;
+}
+
+// H ((m+1) m), g (m+1), cs (m), sn (m), hcol (m+1), h2 (m+1), y (m), 8 scalars
+size_t small_size(int m) { return static_cast<size_t>((m + 1) * m + 6 * m + 3 + 8); }
+
+// ||v||^2 into dev scalar, then the host value of ||v||
+stokes_status norm_host(stokes_hierarchy* h, const double* v, long long N, double* dev2, double* out) {
+  sv::launch_multidot(v, N, 1, v, N, h->partials, h->npart, dev2, 0, h->stream);
+  stokes_status st = check_launch("norm");
+  if (st != STOKES_OK) return st;
+  double v2;
+  st = read_scalar(h, dev2, &v2);
+  if (st != STOKES_OK) return st;
+  *out = std::sqrt(v2);
+  return STOKES_OK;
+}
+
+stokes_status fgmres(stokes_hierarchy* h, const double* b, double* x, int* iters_out,
+                     double* relres_out) {
+  cudaStream_t s = h->stream;
+  sv::Level& F = h->lv.back();
+  const long long N = F.d.N;
+  const int m = h->m;
+  SmallBuf sb = small_layout(h);
+  double* V = h->V;
+  double* Z = h->Z;
+  const long long ld = N;
+  int it = 0;
+  double beta0 = 0.0, beta = 0.0;
+  stokes_status st;
+
+  sv::launch_apply(F.d, x, b, V, 1, s);
+  if ((st = norm_host(h, V, N, sb.sc, &beta0)) != STOKES_OK) return st;
+  if (!std::isfinite(beta0)) return fail(STOKES_ERR_NONFINITE, "initial residual is not finite");
+  if (iters_out) *iters_out = 0;
+  if (relres_out) *relres_out = 0.0;
+  if (beta0 == 0.0) return STOKES_OK;
+  beta = beta0;
+  const double tol = h->prm.rtol * beta0;
+  stokes_status result = STOKES_NOT_CONVERGED;
+  while (true) {
+    sv::launch_scale(V, V, nullptr, 1.0 / beta, N, s);
+    sv::launch_fill(sb.g, 0.0, m + 1, s);
+    sv::launch_fill(sb.g, beta, 1, s);
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      double* vj = V + j * ld;
+      double* zj = Z + j * ld;
+      double* w = V + (j + 1) * ld;
+      vcycle_f64(h, static_cast<int>(h->lv.size()) - 1, vj, zj);
+      sv::launch_apply(F.d, zj, nullptr, w, 0, s);
+      // classical Gram-Schmidt, twice
+      sv::launch_multidot(V, ld, j + 1, w, N, h->partials, h->npart, sb.hcol, 0, s);
+      sv::launch_multiaxpy(w, V, ld, j + 1, sb.hcol, -1.0, N, s);
+      sv::launch_multidot(V, ld, j + 1, w, N, h->partials, h->npart, sb.h2, 0, s);
+      sv::launch_multiaxpy(w, V, ld, j + 1, sb.h2, -1.0, N, s);
+      sv::launch_add_small(sb.hcol, sb.h2, j + 1, s);
+      sv::launch_multidot(w, ld, 1, w, N, h->partials, h->npart, sb.sc, 0, s);
+      sv::launch_set_scalar(sb.sc + 1, sb.sc, s);
+      sv::launch_scale(w, w, sb.sc + 1, 0.0, N, s);
+      sv::launch_givens(sb.H, m + 1, sb.cs, sb.sn, sb.g, sb.hcol, sb.sc + 1, j, sb.sc + 2, s);
+      if ((st = check_launch("fgmres iteration")) != STOKES_OK) return st;
+      double est;
+      if ((st = read_scalar(h, sb.sc + 2, &est)) != STOKES_OK) return st;
+      ++it;
+      k = j + 1;
+      if (!std::isfinite(est)) return fail(STOKES_ERR_NONFINITE, "residual estimate is not finite");
+      if (est <= tol || it >= h->prm.maxit) break;
+    }
+    sv::launch_backsolve(sb.H, m + 1, sb.g, k, sb.y, s);
+    sv::launch_multiaxpy(x, Z, ld, k, sb.y, 1.0, N, s);
+    sv::launch_apply(F.d, x, b, V, 1, s);
+    if ((st = norm_host(h, V, N, sb.sc, &beta)) != STOKES_OK) return st;
+    if (!std::isfinite(beta)) return fail(STOKES_ERR_NONFINITE, "residual is not finite");
+    if (beta <= tol) {
+      result = STOKES_OK;
+      break;
+    }
+    if (it >= h->prm.maxit) break;
+  }
+  if (iters_out) *iters_out = it;
+  if (relres_out) *relres_out = beta / beta0;
+  if (result == STOKES_NOT_CONVERGED) return fail(result, "FGMRES reached maxit");
+  return STOKES_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void stokes_default_params(stokes_params* p) {
+  if (!p) return;
+  p->nu1 = 2;
+  p->nu2 = 2;
+  p->omega = 0.7;
+  p->coarse_n = 4;
+  p->restart = 30;
+  p->maxit = 1000;
+  p->rtol = 1e-8;
+  p->prec = STOKES_FP64;
+}
+
+const char* stokes_last_error(void) { return g_err.c_str(); }
+
+stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_params* params,
+                                      void* stream, stokes_hierarchy** out) {
+  g_err.clear();
+  if (out == nullptr) return fail(STOKES_ERR_ARG, "out is null");
+  *out = nullptr;
+  stokes_params prm;
+  stokes_default_params(&prm);
+  if (params) prm = *params;
+  if (!(viscosity > 0.0) || !std::isfinite(viscosity)) return fail(STOKES_ERR_ARG, "viscosity must be > 0");
+  if (prm.coarse_n < 4) return fail(STOKES_ERR_ARG, "coarse_n must be >= 4");
+  if (prm.restart < 1 || prm.restart > 64) return fail(STOKES_ERR_ARG, "restart must be in 1..64");
+  if (prm.nu1 < 0 || prm.nu2 < 0 || prm.maxit < 1 || !(prm.rtol >= 0.0) || !(prm.omega > 0.0))
+    return fail(STOKES_ERR_ARG, "bad smoothing / iteration parameters");
+  if (prm.prec != STOKES_FP64) return fail(STOKES_ERR_ARG, "precision mode not available in this build");
+  std::vector<int> sizes;
+  {
+    int m = n;
+    while (m > prm.coarse_n) {
+      if (m % 2) return fail(STOKES_ERR_ARG, "n must be coarse_n * 2^k");
+      sizes.push_back(m);
+      m /= 2;
+    }
+    if (m != prm.coarse_n) return fail(STOKES_ERR_ARG, "n must be coarse_n * 2^k");
+    sizes.push_back(m);
+  }
+  auto* h = new (std::nothrow) stokes_hierarchy();
+  if (!h) return fail(STOKES_ERR_OOM, "host allocation failed");
+  h->prm = prm;
+  h->nu = viscosity;
+  h->n = n;
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->m = prm.restart;
+  cudaError_t e = sv::vanka_f64_prepare();
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_fail(e, "kernel attributes");
+  }
+  h->lv.resize(sizes.size());
+  for (size_t k = 0; k < sizes.size(); ++k) {
+    sv::Level& L = h->lv[k];
+    const int nl = sizes[sizes.size() - 1 - k];
+    L.d = make_level(nl, viscosity);
+    const size_t N = static_cast<size_t>(L.d.N);
+    if ((e = dalloc(&L.x0, N)) != cudaSuccess || (e = dalloc(&L.x1, N)) != cudaSuccess ||
+        (e = dalloc(&L.b, N)) != cudaSuccess || (e = dalloc(&L.r, N)) != cudaSuccess ||
+        (e = dalloc(&L.e, N)) != cudaSuccess ||
+        (e = dalloc(&L.cd, static_cast<size_t>(sv::NCLASS) * sv::CD_STRIDE)) != cudaSuccess) {
+      free_all(h);
+      delete h;
+      return cuda_fail(e, "level allocation");
+    }
+    sv::build_class_data(nl, viscosity, L.cd_host, &L.full_inv_host);
+    e = cudaMemcpy(L.cd, L.cd_host.data(), L.cd_host.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      free_all(h);
+      delete h;
+      return cuda_fail(e, "class data upload");
+    }
+  }
+  {
+    std::vector<double> G;
+    if (!sv::coarse_inverse(prm.coarse_n, viscosity, G)) {
+      free_all(h);
+      delete h;
+      return fail(STOKES_ERR_ARG, "coarse bordered system is singular");
+    }
+    h->N0 = static_cast<int>(h->lv[0].d.N);
+    if ((e = dalloc(&h->coarse_G, G.size())) != cudaSuccess ||
+        (e = cudaMemcpy(h->coarse_G, G.data(), G.size() * sizeof(double), cudaMemcpyHostToDevice)) !=
+            cudaSuccess) {
+      free_all(h);
+      delete h;
+      return cuda_fail(e, "coarse inverse upload");
+    }
+  }
+  const size_t Nf = static_cast<size_t>(h->lv.back().d.N);
+  h->npart = sv::dot_blocks();
+  if ((e = dalloc(&h->V, Nf * (h->m + 1))) != cudaSuccess || (e = dalloc(&h->Z, Nf * h->m)) != cudaSuccess ||
+      (e = dalloc(&h->small, small_size(h->m))) != cudaSuccess ||
+      (e = dalloc(&h->partials, static_cast<size_t>(h->npart) * 64)) != cudaSuccess ||
+      (e = cudaMallocHost(reinterpret_cast<void**>(&h->host_scalars), 8 * sizeof(double))) != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return cuda_fail(e, "Krylov workspace allocation");
+  }
+  *out = h;
+  return STOKES_OK;
+}
+
+stokes_status stokes_hierarchy_destroy(stokes_hierarchy* h) {
+  if (!h) return STOKES_OK;
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+  return STOKES_OK;
+}
+
+stokes_status stokes_level_info(const stokes_hierarchy* h, int* num_levels, int* n_finest) {
+  if (!h) return fail(STOKES_ERR_ARG, "null hierarchy");
+  if (num_levels) *num_levels = static_cast<int>(h->lv.size());
+  if (n_finest) *n_finest = h->n;
+  return STOKES_OK;
+}
+
+stokes_status stokes_level_n(const stokes_hierarchy* h, int level, int* n_level) {
+  stokes_status st = check_level(h, level);
+  if (st != STOKES_OK) return st;
+  if (n_level) *n_level = h->lv[level].d.n;
+  return STOKES_OK;
+}
+
+stokes_status stokes_assemble_rhs(stokes_hierarchy* h, const double* f_nodal, const double* u_dirichlet,
+                                  double* b) {
+  if (!h || !f_nodal || !u_dirichlet || !b) return fail(STOKES_ERR_ARG, "null argument");
+  sv::launch_rhs(h->lv.back().d, f_nodal, u_dirichlet, b, h->stream);
+  return check_launch("assemble_rhs");
+}
+
+stokes_status stokes_rhs_transpose(stokes_hierarchy* h, const double* lambda, double* grad_f) {
+  if (!h || !lambda || !grad_f) return fail(STOKES_ERR_ARG, "null argument");
+  sv::launch_rhs_transpose(h->lv.back().d, lambda, grad_f, h->stream);
+  return check_launch("rhs_transpose");
+}
+
+stokes_status stokes_apply_operator(stokes_hierarchy* h, int level, const double* x, double* y) {
+  stokes_status st = check_level(h, level);
+  if (st != STOKES_OK) return st;
+  if (!x || !y) return fail(STOKES_ERR_ARG, "null vector");
+  sv::launch_apply(h->lv[level].d, x, nullptr, y, 0, h->stream);
+  return check_launch("apply_operator");
+}
+
+stokes_status stokes_residual(stokes_hierarchy* h, int level, const double* b, const double* x, double* r) {
+  stokes_status st = check_level(h, level);
+  if (st != STOKES_OK) return st;
+  if (!x || !b || !r) return fail(STOKES_ERR_ARG, "null vector");
+  sv::launch_apply(h->lv[level].d, x, b, r, 1, h->stream);
+  return check_launch("residual");
+}
+
+stokes_status stokes_vanka_sweep(stokes_hierarchy* h, int level, const double* x, const double* b,
+                                 double* x_out) {
+  stokes_status st = check_level(h, level);
+  if (st != STOKES_OK) return st;
+  if (!b || !x_out) return fail(STOKES_ERR_ARG, "null vector");
+  if (x_out == x || x_out == b) return fail(STOKES_ERR_ARG, "x_out must not alias x or b");
+  sv::Level& L = h->lv[level];
+  sv::launch_vanka_f64(L.d, L.cd, x, b, x_out, h->prm.omega, h->stream);
+  return check_launch("vanka_sweep");
+}
+
+stokes_status stokes_restrict(stokes_hierarchy* h, int level, const double* r_fine, double* r_coarse) {
+  stokes_status st = check_level(h, level, 1);
+  if (st != STOKES_OK) return st;
+  if (!r_fine || !r_coarse) return fail(STOKES_ERR_ARG, "null vector");
+  sv::launch_restrict(h->lv[level].d, h->lv[level - 1].d, r_fine, r_coarse, h->stream);
+  return check_launch("restrict");
+}
+
+stokes_status stokes_prolong_add(stokes_hierarchy* h, int level, const double* e_coarse, double* x_fine) {
+  stokes_status st = check_level(h, level, 1);
+  if (st != STOKES_OK) return st;
+  if (!e_coarse || !x_fine) return fail(STOKES_ERR_ARG, "null vector");
+  sv::launch_prolong_add(h->lv[level].d, h->lv[level - 1].d, e_coarse, x_fine, h->stream);
+  return check_launch("prolong_add");
+}
+
+stokes_status stokes_coarse_solve(stokes_hierarchy* h, const double* r, double* e) {
+  if (!h || !r || !e) return fail(STOKES_ERR_ARG, "null argument");
+  if (r == e) return fail(STOKES_ERR_ARG, "r and e must not alias");
+  sv::launch_coarse(h->coarse_G, h->N0, r, e, h->stream);
+  return check_launch("coarse_solve");
+}
+
+stokes_status stokes_initial_guess(stokes_hierarchy* h, const double* b, double* x0) {
+  if (!h || !b || !x0) return fail(STOKES_ERR_ARG, "null argument");
+  if (b == x0) return fail(STOKES_ERR_ARG, "b and x0 must not alias");
+  sv::launch_dirichlet_copy(h->lv.back().d, b, x0, h->stream);
+  return check_launch("initial_guess");
+}
+
+stokes_status stokes_vcycle_apply(stokes_hierarchy* h, const double* r, double* z) {
+  if (!h || !r || !z) return fail(STOKES_ERR_ARG, "null argument");
+  if (r == z) return fail(STOKES_ERR_ARG, "r and z must not alias");
+  vcycle_f64(h, static_cast<int>(h->lv.size()) - 1, r, z);
+  return check_launch("vcycle");
+}
+
+stokes_status stokes_fgmres_solve(stokes_hierarchy* h, const double* b, double* x, int* iters,
+                                  double* relres) {
+  if (!h || !b || !x) return fail(STOKES_ERR_ARG, "null argument");
+  g_err.clear();
+  return fgmres(h, b, x, iters, relres);
+}
+
+stokes_status stokes_solve_adjoint(stokes_hierarchy* h, const double* g, double* lambda, double* grad_f,
+                                   int* iters, double* relres) {
+  if (!h || !g || !lambda) return fail(STOKES_ERR_ARG, "null argument");
+  // initial guess: zero on free rows, g on Dirichlet rows (A has identity rows there)
+  sv::launch_dirichlet_copy(h->lv.back().d, g, lambda, h->stream);
+  stokes_status st = fgmres(h, g, lambda, iters, relres);
+  if (st != STOKES_OK) return st;
+  if (grad_f) {
+    sv::launch_rhs_transpose(h->lv.back().d, lambda, grad_f, h->stream);
+    return check_launch("rhs_transpose");
+  }
+  return STOKES_OK;
+}
+
+stokes_status stokes_batched_solve(stokes_hierarchy* const* hs, int nprob, const double* const* b,
+                                   double* const* x, int* iters, double* relres) {
+  if (!hs || nprob < 0 || (nprob > 0 && (!b || !x))) return fail(STOKES_ERR_ARG, "null argument");
+  stokes_status first = STOKES_OK;
+  for (int k = 0; k < nprob; ++k) {
+    stokes_status st = stokes_fgmres_solve(hs[k], b[k], x[k], iters ? iters + k : nullptr,
+                                           relres ? relres + k : nullptr);
+    if (st != STOKES_OK && first == STOKES_OK) first = st;
+  }
+  return first;
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// sv_internal.h -- internal types of the Stokes/Vanka library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "stokes_vanka.h"
+
+namespace sv {
+
+// Per-class patch data for the Schur-factored exact patch solve.  A patch
+// matrix is A_i = [[K, 0, bx^T], [0, K, by^T], [bx, by, 0]] in slot order
+// (u_x 5x5 window, u_y window, p); slots outside the domain or on Dirichlet
+// nodes carry identity rows of K and zero b entries.  With z = K^-1 [bx by]^T
+// and s = [bx by] z:  dp = (z . r_u - r_p) / s,  du = K^-1 r_u - z dp,
+// which equals A_i^-1 r exactly (block elimination).
+constexpr int CD_KINV = 0;      // 25 x 25, row-major
+constexpr int CD_Z = 625;       // 50: z for u_x slots, then u_y slots
+constexpr int CD_SINV = 675;    // 1 / s
+constexpr int CD_STRIDE = 680;  // doubles per class
+constexpr int NCLASS = 25;
+constexpr int INTERIOR_CLASS = 12;  // 5 * 2 + 2
+
+// Device-side description of one level (passed by value to kernels).
+struct LevelDev {
+  int n;       // elements per axis
+  int nq;      // Q2 nodes per axis, 2n + 1
+  int np;      // Q1 vertices per axis, n + 1
+  long long nv;  // nq * nq
+  long long N;   // 2 nv + np^2
+  double h;    // 1 / n
+  double nu;   // viscosity
+};
+
+struct Level {
+  LevelDev d;
+  double* x0 = nullptr;   // iterate (ping)
+  double* x1 = nullptr;   // iterate (pong)
+  double* b = nullptr;    // right-hand side of this level
+  double* r = nullptr;    // residual scratch
+  double* e = nullptr;    // V-cycle result of this level (coarse correction)
+  double* cd = nullptr;   // NCLASS * CD_STRIDE class data (device)
+  std::vector<double> cd_host;
+  std::vector<double> full_inv_host;  // NCLASS * 51 * 51 dense inverses (host)
+};
+
+}  // namespace sv
+
+struct stokes_hierarchy {
+  stokes_params prm;
+  double nu = 1.0;
+  int n = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<sv::Level> lv;     // lv[0] = coarsest
+  double* coarse_G = nullptr;    // N0 x N0 dense inverse of the bordered coarse system
+  int N0 = 0;
+  // FGMRES workspace
+  int m = 0;
+  double* V = nullptr;           // (m + 1) x N
+  double* Z = nullptr;           // m x N
+  double* small = nullptr;       // H, g, cs, sn, hcol, h2, y, scalars
+  double* partials = nullptr;    // dot-product partial sums
+  int npart = 0;                 // blocks of the dot kernels
+  double* host_scalars = nullptr;  // pinned host mirror of a few scalars
+};
+
+namespace sv {
+
+// ---- host setup (sv_setup.cu) ----
+// Class data (Schur factors) for a level, and the 51 x 51 dense inverses.
+void build_class_data(int n, double nu, std::vector<double>& cd, std::vector<double>* full_inv);
+// Dense N0 x N0 operator of a level (Dirichlet-eliminated), row-major.
+void dense_operator(int n, double nu, std::vector<double>& A);
+// G = leading N0 x N0 block of [[A, e], [e^T, 0]]^-1, e = (0, M_p 1).
+bool coarse_inverse(int n, double nu, std::vector<double>& G);
+// In-place Gauss-Jordan inverse with partial pivoting; false if singular.
+bool invert_dense(std::vector<double>& a, int m);
+
+// ---- kernels (sv_kernels_f64.cu) ----
+void launch_apply(const LevelDev& L, const double* x, const double* b, double* y, int residual,
+                  cudaStream_t s);
+void launch_rhs(const LevelDev& L, const double* f, const double* ud, double* b, cudaStream_t s);
+void launch_rhs_transpose(const LevelDev& L, const double* lam, double* g, cudaStream_t s);
+void launch_vanka_f64(const LevelDev& L, const double* cd, const double* x, const double* b,
+                      double* xo, double omega, cudaStream_t s);
+void launch_restrict(const LevelDev& F, const LevelDev& C, const double* rf, double* rc,
+                     cudaStream_t s);
+void launch_prolong_add(const LevelDev& F, const LevelDev& C, const double* ec, double* xf,
+                        cudaStream_t s);
+void launch_coarse(const double* G, int N0, const double* r, double* e, cudaStream_t s);
+cudaError_t vanka_f64_prepare();
+
+// ---- Krylov kernels (sv_krylov.cu) ----
+int dot_blocks();
+// partial sums of <V_k, w> for k < nk, V_k = V + k * ld; out[k] = sum (deterministic)
+void launch_multidot(const double* V, long long ld, int nk, const double* w, long long N,
+                     double* partials, int npart, double* out, int accumulate, cudaStream_t s);
+// w += sign * sum_k coef[k] V_k
+void launch_multiaxpy(double* w, const double* V, long long ld, int nk, const double* coef,
+                      double sign, long long N, cudaStream_t s);
+// y = x * (1 / *den) (den on device; y = 0 if *den == 0) ; or y = x * scal if den == nullptr
+void launch_scale(double* y, const double* x, const double* den, double scal, long long N,
+                  cudaStream_t s);
+// Givens step for column j of H (ld = m + 1); writes |g[j+1]| to *est
+void launch_givens(double* H, int ldh, double* cs, double* sn, double* g, const double* hcol,
+                   const double* hnorm, int j, double* est, cudaStream_t s);
+void launch_backsolve(const double* H, int ldh, const double* g, int k, double* y, cudaStream_t s);
+void launch_fill(double* p, double v, long long N, cudaStream_t s);
+void launch_set_scalar(double* p, const double* src_sqrt, cudaStream_t s);
+// a[k] += b[k], k < n (small device arrays)
+void launch_add_small(double* a, const double* b, int n, cudaStream_t s);
+// dst = src on Dirichlet velocity rows, 0 elsewhere
+void launch_dirichlet_copy(const LevelDev& L, const double* src, double* dst, cudaStream_t s);
+
+}  // namespace sv

@@ -1,0 +1,574 @@
+// sv_kernels_f64.cu -- FP64 kernels of the hot path on sm_103a:
+//   matrix-free Stokes operator / residual   (Section 2.2, Algorithm 1 residual)
+//   right-hand side assembly and its transpose (Section 2.2)
+//   fused additive Vanka sweep               (Section 3.2, Algorithm 3; Section 6.3)
+//   FE restriction P^T and prolongation P    (Section 3, Algorithm 1)
+//   dense coarse solve                       (Algorithm 1, level 0)
+#include <cuda_runtime.h>
+
+#include "sv_internal.h"
+#include "sv_stencil.cuh"
+
+namespace sv {
+namespace {
+
+__device__ __forceinline__ bool is_free(int I, int J, int nq) {
+  return I > 0 && J > 0 && I < nq - 1 && J < nq - 1;
+}
+
+// ---------------------------------------------------------------------------
+// Operator: y = A x (residual = 0) or y = b - A x (residual = 1).
+// One thread per Q2 node (both velocity components) and one per vertex.
+// ---------------------------------------------------------------------------
+__global__ void k_apply_vel(LevelDev L, const double* __restrict__ x, const double* __restrict__ b,
+                            double* __restrict__ y, int residual) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nq = L.nq, np = L.np, n = L.n;
+  if (I >= nq || J >= nq) return;
+  const long long nv = L.nv;
+  const long long k = static_cast<long long>(J) * nq + I;
+  double ax, ay;
+  if (!is_free(I, J, nq)) {
+    ax = x[k];
+    ay = x[nv + k];
+  } else {
+    double sx = 0.0, sy = 0.0;
+#pragma unroll
+    for (int dJ = -2; dJ <= 2; ++dJ) {
+      const int J2 = J + dJ;
+      const double mJ = m1(J, dJ), kJ = k1(J, dJ);
+      if (J2 <= 0 || J2 >= nq - 1 || (mJ == 0.0 && kJ == 0.0)) continue;
+#pragma unroll
+      for (int dI = -2; dI <= 2; ++dI) {
+        const int I2 = I + dI;
+        if (I2 <= 0 || I2 >= nq - 1) continue;
+        const double c = k1(I, dI) * mJ + m1(I, dI) * kJ;
+        if (c == 0.0) continue;
+        const long long kk = static_cast<long long>(J2) * nq + I2;
+        sx = fma(c, x[kk], sx);
+        sy = fma(c, x[nv + kk], sy);
+      }
+    }
+    const double* p = x + 2 * nv;
+    double gx = 0.0, gy = 0.0;
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int j = J / 2 + dj;
+      if (j < 0 || j > n) continue;
+#pragma unroll
+      for (int di = -1; di <= 1; ++di) {
+        const int i = I / 2 + di;
+        if (i < 0 || i > n) continue;
+        const double pv = p[static_cast<long long>(j) * np + i];
+        gx = fma(ccol(I, i) * ncol(J, j), pv, gx);
+        gy = fma(ncol(I, i) * ccol(J, j), pv, gy);
+      }
+    }
+    const double cl = L.nu / 90.0, cb = -L.h / 18.0;
+    ax = cl * sx + cb * gx;
+    ay = cl * sy + cb * gy;
+  }
+  if (residual) {
+    y[k] = b[k] - ax;
+    y[nv + k] = b[nv + k] - ay;
+  } else {
+    y[k] = ax;
+    y[nv + k] = ay;
+  }
+}
+
+__global__ void k_apply_p(LevelDev L, const double* __restrict__ x, const double* __restrict__ b,
+                          double* __restrict__ y, int residual) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nq = L.nq, np = L.np;
+  if (i >= np || j >= np) return;
+  const long long nv = L.nv;
+  double s = 0.0;
+#pragma unroll
+  for (int dJ = -2; dJ <= 2; ++dJ) {
+    const int J = 2 * j + dJ;
+    if (J <= 0 || J >= nq - 1) continue;
+#pragma unroll
+    for (int dI = -2; dI <= 2; ++dI) {
+      const int I = 2 * i + dI;
+      if (I <= 0 || I >= nq - 1) continue;
+      const long long kk = static_cast<long long>(J) * nq + I;
+      const double cx = crow(dI) * nrow(dJ), cy = nrow(dI) * crow(dJ);
+      if (cx != 0.0) s = fma(cx, x[kk], s);
+      if (cy != 0.0) s = fma(cy, x[nv + kk], s);
+    }
+  }
+  const double a = -L.h / 18.0 * s;
+  const long long k = 2 * nv + static_cast<long long>(j) * np + i;
+  y[k] = residual ? b[k] - a : a;
+}
+
+// ---------------------------------------------------------------------------
+// Right-hand side b = [M f - L_{.,D} u_D ; u_D on D ; -B_{.,D} u_D].
+// ---------------------------------------------------------------------------
+__global__ void k_rhs_vel(LevelDev L, const double* __restrict__ f, const double* __restrict__ ud,
+                          double* __restrict__ b) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nq = L.nq;
+  if (I >= nq || J >= nq) return;
+  const long long nv = L.nv;
+  const long long k = static_cast<long long>(J) * nq + I;
+  if (!is_free(I, J, nq)) {
+    b[k] = ud[k];
+    b[nv + k] = ud[nv + k];
+    return;
+  }
+  double mx = 0.0, my = 0.0, lx = 0.0, ly = 0.0;
+  for (int dJ = -2; dJ <= 2; ++dJ) {
+    const int J2 = J + dJ;
+    if (J2 < 0 || J2 >= nq) continue;
+    for (int dI = -2; dI <= 2; ++dI) {
+      const int I2 = I + dI;
+      if (I2 < 0 || I2 >= nq) continue;
+      const long long kk = static_cast<long long>(J2) * nq + I2;
+      const double mm = m1(I, dI) * m1(J, dJ);
+      mx = fma(mm, f[kk], mx);
+      my = fma(mm, f[nv + kk], my);
+      if (!is_free(I2, J2, nq)) {
+        const double c = k1(I, dI) * m1(J, dJ) + m1(I, dI) * k1(J, dJ);
+        lx = fma(c, ud[kk], lx);
+        ly = fma(c, ud[nv + kk], ly);
+      }
+    }
+  }
+  const double cm = (L.h / 30.0) * (L.h / 30.0), cl = L.nu / 90.0;
+  b[k] = cm * mx - cl * lx;
+  b[nv + k] = cm * my - cl * ly;
+}
+
+__global__ void k_rhs_p(LevelDev L, const double* __restrict__ ud, double* __restrict__ b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nq = L.nq, np = L.np, n = L.n;
+  if (i >= np || j >= np) return;
+  const long long nv = L.nv;
+  // -B_{.,D} u_D with B = -(C (x) N) h for u_x, -(N (x) C) h for u_y
+  double s = 0.0;
+  for (int J = 2 * j - 2; J <= 2 * j + 2; ++J) {
+    if (J < 0 || J >= nq) continue;
+    for (int I = 2 * i - 2; I <= 2 * i + 2; ++I) {
+      if (I < 0 || I >= nq || is_free(I, J, nq)) continue;
+      const long long kk = static_cast<long long>(J) * nq + I;
+      s += c1_full(i, I, n) * n1_full(j, J, n) * ud[kk];
+      s += n1_full(i, I, n) * c1_full(j, J, n) * ud[nv + kk];
+    }
+  }
+  b[2 * nv + static_cast<long long>(j) * np + i] = L.h * s;
+}
+
+// grad_f = R^T lambda: sum over free velocity rows k of (M)_{k,(I,J)} lambda_k.
+__global__ void k_rhs_transpose(LevelDev L, const double* __restrict__ lam, double* __restrict__ g) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nq = L.nq;
+  if (I >= nq || J >= nq) return;
+  const long long nv = L.nv;
+  double sx = 0.0, sy = 0.0;
+  for (int dJ = -2; dJ <= 2; ++dJ) {
+    const int J2 = J + dJ;
+    for (int dI = -2; dI <= 2; ++dI) {
+      const int I2 = I + dI;
+      if (!is_free(I2, J2, nq)) continue;
+      // M is symmetric: M_{(I2,J2),(I,J)} = row of (I2,J2) at offset (-dI, -dJ)
+      const double mm = m1(I2, -dI) * m1(J2, -dJ);
+      const long long kk = static_cast<long long>(J2) * nq + I2;
+      sx = fma(mm, lam[kk], sx);
+      sy = fma(mm, lam[nv + kk], sy);
+    }
+  }
+  const double cm = (L.h / 30.0) * (L.h / 30.0);
+  const long long k = static_cast<long long>(J) * nq + I;
+  g[k] = cm * sx;
+  g[nv + k] = cm * sy;
+}
+
+// ---------------------------------------------------------------------------
+// Fused additive Vanka sweep (FP64).  A CTA owns TX x TY vertices; it computes
+// the residual on the patch windows of those vertices plus a one-vertex halo,
+// solves every patch of the (TX+2) x (TY+2) region exactly (Schur-factored
+// class inverse), and writes x + omega * (sum of patch corrections) / m_j for
+// the dofs it owns.  Owned dofs of vertex (i, j): Q2 nodes (2i-1..2i) x
+// (2j-1..2j), both components, and p(i, j).  No atomics: deterministic.
+// ---------------------------------------------------------------------------
+template <int TX, int TY>
+struct VTile {
+  static constexpr int XW = 2 * TX + 11, XH = 2 * TY + 11;  // x window, Q2 nodes
+  static constexpr int PW = TX + 6, PH = TY + 6;            // x window, vertices
+  static constexpr int RW = 2 * TX + 7, RH = 2 * TY + 7;    // residual window, Q2 nodes
+  static constexpr int QW = TX + 2, QH = TY + 2;            // patches (and residual vertices)
+  static constexpr int NPATCH = QW * QH;
+  static constexpr int SX = 2 * XW * XH, SP = PW * PH, SR = 2 * RW * RH, SRP = NPATCH;
+  static constexpr int SD = NPATCH * 51;
+  static constexpr int TOTAL = SX + SP + SR + SRP + SD;
+};
+
+constexpr int VK_TX = 8, VK_TY = 8, VK_NT = 128;
+
+template <int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) k_vanka_f64(LevelDev L, const double* __restrict__ cd,
+                                                  const double* __restrict__ x,
+                                                  const double* __restrict__ b,
+                                                  double* __restrict__ xo, double omega) {
+  using T = VTile<TX, TY>;
+  extern __shared__ double smem[];
+  double* sx = smem;
+  double* sp = sx + T::SX;
+  double* sr = sp + T::SP;
+  double* srp = sr + T::SR;
+  double* sd = srp + T::SRP;
+  const int n = L.n, nq = L.nq, np = L.np;
+  const long long nv = L.nv;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int tid = threadIdx.x;
+
+  // 1. x window (Dirichlet and outside entries read as 0: their columns are dropped)
+  {
+    const int XI0 = 2 * i0 - 6, XJ0 = 2 * j0 - 6;
+    for (int t = tid; t < T::SX; t += NT) {
+      const int c = t / (T::XW * T::XH);
+      const int rem = t - c * T::XW * T::XH;
+      const int jj = rem / T::XW, ii = rem - jj * T::XW;
+      const int I = XI0 + ii, J = XJ0 + jj;
+      double v = 0.0;
+      if (x != nullptr && is_free(I, J, nq)) v = x[c * nv + static_cast<long long>(J) * nq + I];
+      sx[t] = v;
+    }
+    for (int t = tid; t < T::SP; t += NT) {
+      const int jj = t / T::PW, ii = t - jj * T::PW;
+      const int i = i0 - 3 + ii, j = j0 - 3 + jj;
+      double v = 0.0;
+      if (x != nullptr && i >= 0 && j >= 0 && i <= n && j <= n)
+        v = x[2 * nv + static_cast<long long>(j) * np + i];
+      sp[t] = v;
+    }
+  }
+  __syncthreads();
+
+  // 2. residual r = b - A x on the windows of the (TX+2) x (TY+2) patches
+  const double cl = L.nu / 90.0, cb = -L.h / 18.0;
+  {
+    const int RI0 = 2 * i0 - 4, RJ0 = 2 * j0 - 4;
+    for (int t = tid; t < T::SR; t += NT) {
+      const int c = t / (T::RW * T::RH);
+      const int rem = t - c * T::RW * T::RH;
+      const int jj = rem / T::RW, ii = rem - jj * T::RW;
+      const int I = RI0 + ii, J = RJ0 + jj;
+      double r = 0.0;
+      if (I >= 0 && J >= 0 && I < nq && J < nq) {
+        const long long k = c * nv + static_cast<long long>(J) * nq + I;
+        if (!is_free(I, J, nq)) {
+          r = b[k] - (x != nullptr ? x[k] : 0.0);
+        } else {
+          const double* xs = sx + c * T::XW * T::XH + (jj + 2) * T::XW + (ii + 2);
+          double s = 0.0;
+#pragma unroll
+          for (int dJ = -2; dJ <= 2; ++dJ) {
+            const double mJ = m1(J, dJ), kJ = k1(J, dJ);
+#pragma unroll
+            for (int dI = -2; dI <= 2; ++dI) {
+              const double cc = k1(I, dI) * mJ + m1(I, dI) * kJ;
+              if (cc != 0.0) s = fma(cc, xs[dJ * T::XW + dI], s);
+            }
+          }
+          double g = 0.0;
+#pragma unroll
+          for (int dj = -1; dj <= 1; ++dj) {
+            const int j = J / 2 + dj;
+#pragma unroll
+            for (int di = -1; di <= 1; ++di) {
+              const int i = I / 2 + di;
+              const double w = (c == 0) ? ccol(I, i) * ncol(J, j) : ncol(I, i) * ccol(J, j);
+              if (w != 0.0) g = fma(w, sp[(j - (j0 - 3)) * T::PW + (i - (i0 - 3))], g);
+            }
+          }
+          r = b[k] - (cl * s + cb * g);
+        }
+      }
+      sr[t] = r;
+    }
+    for (int t = tid; t < T::SRP; t += NT) {
+      const int jj = t / T::QW, ii = t - jj * T::QW;
+      const int i = i0 - 1 + ii, j = j0 - 1 + jj;
+      double r = 0.0;
+      if (i >= 0 && j >= 0 && i <= n && j <= n) {
+        double s = 0.0;
+        // window of vertex (i, j) in sx: Q2 (2i + dI) - (2 i0 - 6) = 2 ii + 4 + dI
+        const double* xs0 = sx + (2 * jj + 4) * T::XW + (2 * ii + 4);
+        const double* xs1 = xs0 + T::XW * T::XH;
+#pragma unroll
+        for (int dJ = -2; dJ <= 2; ++dJ) {
+#pragma unroll
+          for (int dI = -2; dI <= 2; ++dI) {
+            const double wx = crow(dI) * nrow(dJ), wy = nrow(dI) * crow(dJ);
+            if (wx != 0.0) s = fma(wx, xs0[dJ * T::XW + dI], s);
+            if (wy != 0.0) s = fma(wy, xs1[dJ * T::XW + dI], s);
+          }
+        }
+        r = b[2 * nv + static_cast<long long>(j) * np + i] - cb * s;
+      }
+      srp[t] = r;
+    }
+  }
+  __syncthreads();
+
+  // 3. exact patch solves, one thread per patch
+  for (int t = tid; t < T::NPATCH; t += NT) {
+    const int qj = t / T::QW, qi = t - qj * T::QW;
+    const int pi = i0 - 1 + qi, pj = j0 - 1 + qj;
+    if (pi < 0 || pj < 0 || pi > n || pj > n) continue;
+    const int cls = 5 * axis_class(pj, n) + axis_class(pi, n);
+    const double* C = cd + cls * CD_STRIDE;
+    double ru[50];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int wj = 0; wj < 5; ++wj)
+#pragma unroll
+        for (int wi = 0; wi < 5; ++wi)
+          ru[c * 25 + wj * 5 + wi] = sr[c * T::RW * T::RH + (2 * qj + wj) * T::RW + 2 * qi + wi];
+    double zr = 0.0;
+#pragma unroll
+    for (int k = 0; k < 50; ++k) zr = fma(__ldg(C + CD_Z + k), ru[k], zr);
+    const double dp = (zr - srp[t]) * __ldg(C + CD_SINV);
+    double* D = sd + t * 51;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+#pragma unroll 1
+      for (int o = 0; o < 25; ++o) {
+        const double* Kr = C + CD_KINV + o * 25;
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < 25; ++k) acc = fma(__ldg(Kr + k), ru[c * 25 + k], acc);
+        D[c * 25 + o] = acc - __ldg(C + CD_Z + c * 25 + o) * dp;
+      }
+    }
+    D[50] = dp;
+  }
+  __syncthreads();
+
+  // 4. weighted additive update of the owned dofs
+  constexpr int OW = 2 * TX, OH = 2 * TY;
+  for (int t = tid; t < 2 * OW * OH + TX * TY; t += NT) {
+    if (t < 2 * OW * OH) {
+      const int c = t / (OW * OH);
+      const int rem = t - c * OW * OH;
+      const int oj = rem / OW, oi = rem - oj * OW;
+      const int I = 2 * i0 - 1 + oi, J = 2 * j0 - 1 + oj;
+      if (I < 0 || J < 0 || I >= nq || J >= nq) continue;
+      const int pil = I < 2 ? 0 : (I - 1) / 2, pih = min(n, (I + 2) / 2);
+      const int pjl = J < 2 ? 0 : (J - 1) / 2, pjh = min(n, (J + 2) / 2);
+      double acc = 0.0;
+      for (int pj = pjl; pj <= pjh; ++pj) {
+        for (int pi = pil; pi <= pih; ++pi) {
+          const int q = (pj - (j0 - 1)) * T::QW + (pi - (i0 - 1));
+          acc += sd[q * 51 + c * 25 + (J - 2 * pj + 2) * 5 + (I - 2 * pi + 2)];
+        }
+      }
+      const double m = static_cast<double>((pih - pil + 1) * (pjh - pjl + 1));
+      const long long k = c * nv + static_cast<long long>(J) * nq + I;
+      const double xold = x != nullptr ? x[k] : 0.0;
+      xo[k] = xold + omega * acc / m;
+    } else {
+      const int u = t - 2 * OW * OH;
+      const int vj = u / TX, vi = u - vj * TX;
+      const int i = i0 + vi, j = j0 + vj;
+      if (i > n || j > n) continue;
+      const int q = (vj + 1) * T::QW + (vi + 1);
+      const long long k = 2 * nv + static_cast<long long>(j) * np + i;
+      const double xold = x != nullptr ? x[k] : 0.0;
+      xo[k] = xold + omega * sd[q * 51 + 50];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Restriction r_c = P^T r_f and prolongation x_f += P e_c (FE interpolation,
+// Dirichlet rows of P (fine) and columns (coarse) zero).
+// 1D Q2 weights: coarse node C even: fine 2C + {-3:-1/8, -1:3/8, 0:1, 1:3/8, 3:-1/8};
+// C odd: fine 2C + {-1:3/4, 0:1, 1:3/4}.  Q1: fine 2c + {-1:1/2, 0:1, 1:1/2}.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double rq2(int C, int off) {
+  if (C & 1) return off == 0 ? 1.0 : ((off == 1 || off == -1) ? 0.75 : 0.0);
+  switch (off) {
+    case 0: return 1.0;
+    case 1: case -1: return 0.375;
+    case 3: case -3: return -0.125;
+    default: return 0.0;
+  }
+}
+__device__ __forceinline__ double rq1(int off) {
+  return off == 0 ? 1.0 : ((off == 1 || off == -1) ? 0.5 : 0.0);
+}
+
+__global__ void k_restrict(LevelDev F, LevelDev C, const double* __restrict__ rf,
+                           double* __restrict__ rc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  // velocity part over the coarse Q2 grid, pressure over the coarse vertices
+  if (I < C.nq && J < C.nq) {
+    const long long k = static_cast<long long>(J) * C.nq + I;
+    double sx = 0.0, sy = 0.0;
+    if (is_free(I, J, C.nq)) {
+      for (int dJ = -3; dJ <= 3; ++dJ) {
+        const double wJ = rq2(J, dJ);
+        const int FJ = 2 * J + dJ;
+        if (wJ == 0.0 || !(FJ > 0 && FJ < F.nq - 1)) continue;
+        for (int dI = -3; dI <= 3; ++dI) {
+          const double wI = rq2(I, dI);
+          const int FI = 2 * I + dI;
+          if (wI == 0.0 || !(FI > 0 && FI < F.nq - 1)) continue;
+          const long long kf = static_cast<long long>(FJ) * F.nq + FI;
+          sx = fma(wI * wJ, rf[kf], sx);
+          sy = fma(wI * wJ, rf[F.nv + kf], sy);
+        }
+      }
+    }
+    rc[k] = sx;
+    rc[C.nv + k] = sy;
+  }
+  if (I < C.np && J < C.np) {
+    double s = 0.0;
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int fj = 2 * J + dj;
+      if (fj < 0 || fj >= F.np) continue;
+      for (int di = -1; di <= 1; ++di) {
+        const int fi = 2 * I + di;
+        if (fi < 0 || fi >= F.np) continue;
+        s = fma(rq1(di) * rq1(dj), rf[2 * F.nv + static_cast<long long>(fj) * F.np + fi], s);
+      }
+    }
+    rc[2 * C.nv + static_cast<long long>(J) * C.np + I] = s;
+  }
+}
+
+// weights of the coarse element's local nodes at fine local position k/4 (Q2) or k/2 (Q1)
+__device__ __forceinline__ double pq2(int k, int a) {
+  // rows k = 0..4 (t = k/4), columns a = 0..2
+  const double W[5][3] = {{1.0, 0.0, 0.0},
+                          {0.375, 0.75, -0.125},
+                          {0.0, 1.0, 0.0},
+                          {-0.125, 0.75, 0.375},
+                          {0.0, 0.0, 1.0}};
+  return W[k][a];
+}
+
+__global__ void k_prolong_add(LevelDev F, LevelDev C, const double* __restrict__ ec,
+                              double* __restrict__ xf) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I < F.nq && J < F.nq && is_free(I, J, F.nq)) {
+    const int ex = min(I / 4, C.n - 1), ey = min(J / 4, C.n - 1);
+    const int kx = I - 4 * ex, ky = J - 4 * ey;
+    double sx = 0.0, sy = 0.0;
+    for (int b = 0; b < 3; ++b) {
+      const double wy = pq2(ky, b);
+      const int CJ = 2 * ey + b;
+      if (wy == 0.0 || CJ <= 0 || CJ >= C.nq - 1) continue;  // coarse Dirichlet row
+      for (int a = 0; a < 3; ++a) {
+        const double wx = pq2(kx, a);
+        const int CI = 2 * ex + a;
+        if (wx == 0.0 || !is_free(CI, CJ, C.nq)) continue;
+        const long long kc = static_cast<long long>(CJ) * C.nq + CI;
+        sx = fma(wx * wy, ec[kc], sx);
+        sy = fma(wx * wy, ec[C.nv + kc], sy);
+      }
+    }
+    const long long k = static_cast<long long>(J) * F.nq + I;
+    xf[k] += sx;
+    xf[F.nv + k] += sy;
+  }
+  if (I < F.np && J < F.np) {
+    const int ex = min(I / 2, C.n - 1), ey = min(J / 2, C.n - 1);
+    const int kx = I - 2 * ex, ky = J - 2 * ey;
+    double s = 0.0;
+    for (int b = 0; b < 2; ++b) {
+      const double wy = (b == 0) ? (1.0 - 0.5 * ky) : 0.5 * ky;
+      if (wy == 0.0) continue;
+      for (int a = 0; a < 2; ++a) {
+        const double wx = (a == 0) ? (1.0 - 0.5 * kx) : 0.5 * kx;
+        if (wx == 0.0) continue;
+        s = fma(wx * wy, ec[2 * C.nv + static_cast<long long>(ey + b) * C.np + (ex + a)], s);
+      }
+    }
+    xf[2 * F.nv + static_cast<long long>(J) * F.np + I] += s;
+  }
+}
+
+// e = G r, G dense N0 x N0 (one CTA)
+__global__ void k_coarse(const double* __restrict__ G, int N0, const double* __restrict__ r,
+                         double* __restrict__ e) {
+  extern __shared__ double sr_[];
+  for (int k = threadIdx.x; k < N0; k += blockDim.x) sr_[k] = r[k];
+  __syncthreads();
+  for (int row = threadIdx.x; row < N0; row += blockDim.x) {
+    double s = 0.0;
+    const double* g = G + static_cast<long long>(row) * N0;
+    for (int k = 0; k < N0; ++k) s = fma(g[k], sr_[k], s);
+    e[row] = s;
+  }
+}
+
+dim3 grid2(int nx, int ny, dim3 blk) {
+  return dim3((nx + blk.x - 1) / blk.x, (ny + blk.y - 1) / blk.y);
+}
+
+}  // namespace
+
+void launch_apply(const LevelDev& L, const double* x, const double* b, double* y, int residual,
+                  cudaStream_t s) {
+  dim3 blk(32, 8);
+  k_apply_vel<<<grid2(L.nq, L.nq, blk), blk, 0, s>>>(L, x, b, y, residual);
+  k_apply_p<<<grid2(L.np, L.np, blk), blk, 0, s>>>(L, x, b, y, residual);
+}
+
+void launch_rhs(const LevelDev& L, const double* f, const double* ud, double* b, cudaStream_t s) {
+  dim3 blk(32, 8);
+  k_rhs_vel<<<grid2(L.nq, L.nq, blk), blk, 0, s>>>(L, f, ud, b);
+  k_rhs_p<<<grid2(L.np, L.np, blk), blk, 0, s>>>(L, ud, b);
+}
+
+void launch_rhs_transpose(const LevelDev& L, const double* lam, double* g, cudaStream_t s) {
+  dim3 blk(32, 8);
+  k_rhs_transpose<<<grid2(L.nq, L.nq, blk), blk, 0, s>>>(L, lam, g);
+}
+
+cudaError_t vanka_f64_prepare() {
+  using T = VTile<VK_TX, VK_TY>;
+  return cudaFuncSetAttribute(k_vanka_f64<VK_TX, VK_TY, VK_NT>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(T::TOTAL * sizeof(double)));
+}
+
+void launch_vanka_f64(const LevelDev& L, const double* cd, const double* x, const double* b,
+                      double* xo, double omega, cudaStream_t s) {
+  using T = VTile<VK_TX, VK_TY>;
+  dim3 grid((L.np + VK_TX - 1) / VK_TX, (L.np + VK_TY - 1) / VK_TY);
+  k_vanka_f64<VK_TX, VK_TY, VK_NT><<<grid, VK_NT, T::TOTAL * sizeof(double), s>>>(L, cd, x, b, xo,
+                                                                                  omega);
+}
+
+void launch_restrict(const LevelDev& F, const LevelDev& C, const double* rf, double* rc,
+                     cudaStream_t s) {
+  dim3 blk(32, 8);
+  k_restrict<<<grid2(C.nq, C.nq, blk), blk, 0, s>>>(F, C, rf, rc);
+}
+
+void launch_prolong_add(const LevelDev& F, const LevelDev& C, const double* ec, double* xf,
+                        cudaStream_t s) {
+  dim3 blk(32, 8);
+  k_prolong_add<<<grid2(F.nq, F.nq, blk), blk, 0, s>>>(F, C, ec, xf);
+}
+
+void launch_coarse(const double* G, int N0, const double* r, double* e, cudaStream_t s) {
+  k_coarse<<<1, 256, N0 * sizeof(double), s>>>(G, N0, r, e);
+}
+
+}  // namespace sv

@@ -1,0 +1,269 @@
+"""GPU parity: every step of the hot path through the C ABI against the FP64 CPU oracle.
+
+Sizes span several 8 x 8 vertex tiles with ragged tails (n + 1 vertices per
+axis is never a multiple of 8).  Tolerances are relative to the largest
+magnitude of the reference: operator 1e-13, Vanka sweep and V-cycle 1e-12,
+FGMRES solutions 1e-10 (pressure normalised to zero mean on both sides).
+"""
+import numpy as np
+import pytest
+import torch
+
+import stokes_inputs as si
+from oracle import stokes_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+_ORACLE = {}
+
+
+def oracle_h(n):
+    if n not in _ORACLE:
+        _ORACLE[n] = O.build_hierarchy(n)
+    return _ORACLE[n]
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2401_06277_gb300 as p
+    from paper_2401_06277_gb300 import build
+    build.build()
+    return p
+
+
+_GPU = {}
+
+
+def gpu_h(pkg, n, **kw):
+    key = (n, tuple(sorted(kw.items())))
+    if key not in _GPU:
+        _GPU[key] = pkg.Hierarchy(n, **kw)
+    return _GPU[key]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def rvec(n, seed, dirichlet_zero=False, lv=None):
+    v = si.random_vector(n, seed)
+    if dirichlet_zero:
+        v[lv.dmask] = 0.0
+    return v
+
+
+@pytest.mark.parametrize("n", [4, 8, 16, 32, 64])
+def test_operator_and_residual(pkg, n):
+    H = gpu_h(pkg, n)
+    Ho = oracle_h(n)
+    lv = Ho.levels[-1]
+    x, b = rvec(n, 1), rvec(n, 2)
+    y = host(H.apply(dev(x)))
+    assert rel(y, lv.A @ x) <= 1e-13
+    r = host(H.residual(dev(b), dev(x)))
+    assert rel(r, b - lv.A @ x) <= 1e-13
+    # every level of the hierarchy
+    for l in range(H.levels - 1):
+        nl = H.level_n(l)
+        xl = rvec(nl, 10 + l)
+        assert rel(host(H.apply(dev(xl), level=l)), Ho.levels[l].A @ xl) <= 1e-13
+
+
+@pytest.mark.parametrize("n", [4, 8, 32])
+@pytest.mark.parametrize("force", ["manufactured", "random"])
+def test_rhs_assembly(pkg, n, force):
+    H = gpu_h(pkg, n)
+    lv = oracle_h(n).levels[-1]
+    f = si.manufactured_force(n) if force == "manufactured" else si.random_force(n, 5)
+    ud = si.manufactured_velocity(n)
+    b = host(H.assemble_rhs(dev(f), dev(ud)))
+    bo = O.assemble_rhs(lv, f, ud)
+    assert rel(b, bo) <= 1e-13
+    assert abs(b[2 * lv.mesh.nvel:].sum()) <= 1e-14 * max(1.0, np.abs(b).max())
+
+
+@pytest.mark.parametrize("n", [4, 8, 16, 32, 64])
+def test_vanka_sweep(pkg, n):
+    from paper_2401_06277_gb300 import stokes
+    H = gpu_h(pkg, n)
+    Ho = oracle_h(n)
+    for l in range(H.levels):
+        lv = Ho.levels[l]
+        nl = lv.mesh.n
+        x, b = rvec(nl, 3 + l), rvec(nl, 4 + l)
+        got = host(H.sweep(dev(x), dev(b), level=l))
+        ref = O.vanka_sweep(lv, x, b, 0.7)
+        assert rel(got, ref) <= 1e-12, (n, l, rel(got, ref))
+        # zero initial guess (x = NULL in the ABI)
+        out = torch.empty(lv.mesh.ndof, dtype=torch.float64, device="cuda")
+        stokes.stokes_vanka_sweep(H.handle, l, None, dev(b), out)
+        ref0 = O.vanka_sweep(lv, np.zeros_like(b), b, 0.7)
+        assert rel(host(out), ref0) <= 1e-12
+
+
+def test_vanka_sweep_rejects_aliasing(pkg):
+    from paper_2401_06277_gb300 import stokes
+    H = gpu_h(pkg, 8)
+    x = dev(rvec(8, 1))
+    with pytest.raises(stokes.StokesError):
+        stokes.stokes_vanka_sweep(H.handle, H.levels - 1, x, x, x)
+
+
+@pytest.mark.parametrize("n", [8, 16, 64])
+def test_restrict_and_prolong(pkg, n):
+    from paper_2401_06277_gb300 import stokes
+    H = gpu_h(pkg, n)
+    Ho = oracle_h(n)
+    for l in range(1, H.levels):
+        P = Ho.levels[l].P
+        nf, nc = Ho.levels[l].mesh.n, Ho.levels[l - 1].mesh.n
+        rf = rvec(nf, 20 + l)
+        rc = torch.empty(si.sizes(nc)[2], dtype=torch.float64, device="cuda")
+        stokes.stokes_restrict(H.handle, l, dev(rf), rc)
+        assert rel(host(rc), P.T @ rf) <= 1e-13
+        ec = rvec(nc, 30 + l)
+        xf = rvec(nf, 40 + l)
+        xt = dev(xf)
+        stokes.stokes_prolong_add(H.handle, l, dev(ec), xt)
+        assert rel(host(xt), xf + P @ ec) <= 1e-13
+
+
+def test_coarse_solve(pkg):
+    from paper_2401_06277_gb300 import stokes
+    H = gpu_h(pkg, 16)
+    Ho = oracle_h(16)
+    lv = Ho.levels[0]
+    x = rvec(4, 9, dirichlet_zero=True, lv=lv)
+    r = lv.A @ x
+    e = torch.empty_like(dev(r))
+    stokes.stokes_coarse_solve(H.handle, dev(r), e)
+    assert rel(host(e), O.coarse_solve(Ho, r)) <= 1e-12
+    # a consistent right-hand side is solved exactly, with int p = 0
+    assert rel(lv.A @ host(e), r) <= 1e-11
+
+
+@pytest.mark.parametrize("n", [4, 8, 16, 32, 64])
+def test_vcycle(pkg, n):
+    H = gpu_h(pkg, n)
+    Ho = oracle_h(n)
+    lv = Ho.levels[-1]
+    b = O.assemble_rhs(lv, si.random_force(n, 11), si.manufactured_velocity(n))
+    z = host(H.vcycle(dev(b)))
+    zo = O.vcycle(Ho, b)
+    assert rel(z, zo) <= 1e-12, rel(z, zo)
+    r = rvec(n, 12)
+    assert rel(host(H.vcycle(dev(r))), O.vcycle(Ho, r)) <= 1e-12
+
+
+@pytest.mark.parametrize("nu1,nu2", [(1, 1), (0, 2), (3, 0)])
+def test_vcycle_sweep_counts(pkg, nu1, nu2):
+    n = 16
+    H = gpu_h(pkg, n, nu1=nu1, nu2=nu2)
+    Ho = O.build_hierarchy(n, nu1=nu1, nu2=nu2)
+    r = rvec(n, 13)
+    assert rel(host(H.vcycle(dev(r))), O.vcycle(Ho, r)) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 64])
+def test_fgmres_solution(pkg, n):
+    H = gpu_h(pkg, n)
+    Ho = oracle_h(n)
+    lv = Ho.levels[-1]
+    f = si.manufactured_force(n) if n == 32 else si.random_force(n, 100 + n)
+    ud = si.manufactured_velocity(n)
+    b = O.assemble_rhs(lv, f, ud)
+    x, it, rr = H.solve(dev(b))
+    xg = O.normalize_pressure(lv, host(x))
+    res = O.solve(Ho, b)
+    xo = O.normalize_pressure(lv, res.x)
+    assert rr <= 1e-8 and res.converged
+    assert it == res.iters
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-10
+    # the true residual recomputed on the CPU
+    r0 = np.linalg.norm(b - lv.A @ O.initial_guess(lv, b))
+    assert np.linalg.norm(b - lv.A @ host(x)) / r0 <= 1.01e-8
+
+
+def test_fgmres_against_direct_solve(pkg):
+    n = 16
+    H = gpu_h(pkg, n, rtol=1e-13)
+    lv = oracle_h(n).levels[-1]
+    b = O.assemble_rhs(lv, si.random_force(n, 7), si.manufactured_velocity(n))
+    x, it, rr = H.solve(dev(b))
+    xd = O.normalize_pressure(lv, O.direct_solve(lv, b))
+    xg = O.normalize_pressure(lv, host(x))
+    assert np.linalg.norm(xg - xd) / np.linalg.norm(xd) <= 1e-10
+
+
+def test_fgmres_small_restart_and_maxit(pkg):
+    from paper_2401_06277_gb300 import stokes
+    n = 16
+    lv = oracle_h(n).levels[-1]
+    b = O.assemble_rhs(lv, si.manufactured_force(n), si.manufactured_velocity(n))
+    H3 = gpu_h(pkg, n, restart=3)
+    x, it, rr = H3.solve(dev(b))
+    ref = O.solve(O.build_hierarchy(n), b, restart=3)
+    assert it == ref.iters and rr <= 1e-8
+    H1 = gpu_h(pkg, n, maxit=2)
+    x, it, rr = H1.solve(dev(b), allow_not_converged=True)
+    assert it == 2 and rr > 1e-8
+    with pytest.raises(stokes.StokesError) as e:
+        H1.solve(dev(b))
+    assert e.value.status == stokes.STOKES_NOT_CONVERGED
+
+
+def test_fgmres_rejects_nonfinite_rhs(pkg):
+    from paper_2401_06277_gb300 import stokes
+    n = 8
+    H = gpu_h(pkg, n)
+    lv = oracle_h(n).levels[-1]
+    b = O.assemble_rhs(lv, si.manufactured_force(n), si.manufactured_velocity(n))
+    b[lv.mesh.nvel + 40] = np.nan
+    with pytest.raises(stokes.StokesError) as e:
+        H.solve(dev(b))
+    assert e.value.status == stokes.STOKES_ERR_NONFINITE
+
+
+def test_zero_rhs_returns_zero(pkg):
+    n = 8
+    H = gpu_h(pkg, n)
+    b = torch.zeros(si.sizes(n)[2], dtype=torch.float64, device="cuda")
+    x, it, rr = H.solve(b)
+    assert it == 0 and float(x.abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("nu", [0.01, 3.0])
+def test_viscosity(pkg, nu):
+    n = 16
+    H = gpu_h(pkg, n, viscosity=nu)
+    Ho = O.build_hierarchy(n, nu=nu)
+    r = rvec(n, 17)
+    assert rel(host(H.apply(dev(r))), Ho.levels[-1].A @ r) <= 1e-13
+    assert rel(host(H.vcycle(dev(r))), O.vcycle(Ho, r)) <= 1e-12
+
+
+def test_adjoint_gradient(pkg):
+    n = 16
+    H = gpu_h(pkg, n, rtol=1e-12)
+    lv = oracle_h(n).levels[-1]
+    f = si.random_force(n, 7)
+    ud = si.manufactured_velocity(n)
+    J, grad_o, x_o, lam_o = O.adjoint_gradient_dense(lv, f, ud, ud)
+    b = H.assemble_rhs(dev(f), dev(ud))
+    x, _, _ = H.solve(b)
+    g = x.clone()
+    nv2 = 2 * lv.mesh.nvel
+    g[:nv2] -= dev(ud.ravel())
+    g[nv2:] = 0.0
+    lam, grad, it, rr = H.adjoint(g)
+    grad = host(grad).reshape(grad_o.shape)
+    assert rel(grad, grad_o) <= 1e-9
