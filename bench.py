@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark of the Stokes / additive-Vanka multigrid / FGMRES hot path on GB300.
+
+Metric: Stokes DoF/s per Vanka V-cycle, together with the FGMRES time to a
+1e-8 relative residual.  One step = one FGMRES(30) solve to 1e-8,
+right-preconditioned by the V(2,2) additive-Vanka cycle (every hot-path step:
+residual, patch gather/solve/scatter, restriction, coarse solve, prolongation,
+Arnoldi).  value = dofs x V-cycles applied / timed seconds (all ranks).
+
+Default workload: 2048 x 2048 elements (37,769,219 dofs incl. Dirichlet rows),
+10 levels, FP64, body force i.i.d. N(0,1) nodal values (seed 0), Dirichlet
+velocity from the manufactured field.  Every vector (302 MB) is larger than
+L2, so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 2048] [--impl ours|reference]
+
+With N > 1 (torchrun) each rank solves its own independent replica of the
+problem (the method has no data-path exchange between problems): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Stokes DoF/s per Vanka V-cycle (FGMRES to 1e-8 residual)"
+UNIT = "DoF/s"
+SM_COUNT = 152
+ORACLE_N = 256
+
+
+def dofs(n: int) -> int:
+    return 2 * (2 * n + 1) ** 2 + (n + 1) ** 2
+
+
+def sweep_flops(n: int) -> float:
+    """Algorithmic FP64 flops of one additive Vanka sweep on an n x n grid.
+
+    Per vertex (one patch, and one cell of owned dofs: 4 Q2 nodes x 2
+    components + 1 pressure): residual 2 (2 (64 + 12) + 24) + 9 = 361,
+    Schur-factored patch solve 2 (2 * 625 + 50 + 50) + 2 = 2702, weighted
+    update 2 (9 + 6 + 6 + 4) + 16 + 2 = 68: 3131 flops per vertex."""
+    return 3131.0 * (n + 1) ** 2
+
+
+def sweep_bytes(n: int) -> float:
+    """Algorithmic bytes of one FP64 sweep: read x and b, write x."""
+    return 3.0 * 8.0 * dofs(n)
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            if self.bus_id and self.bus_id not in parts[1].lower() and parts[1].lower() not in self.bus_id:
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        mx = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle leg (subprocess, single-threaded BLAS)
+# --------------------------------------------------------------------------
+def oracle_worker(n: int, reps: int) -> None:
+    """Time the CPU oracle's FGMRES + V(2,2) solve at n x n (prints one JSON object)."""
+    import numpy as np
+
+    import stokes_inputs as si
+    from oracle import stokes_oracle as O
+
+    t0 = time.perf_counter()
+    H = O.build_hierarchy(n)
+    lv = H.levels[-1]
+    b = O.assemble_rhs(lv, si.random_force(n, 0), si.manufactured_velocity(n))
+    setup = time.perf_counter() - t0
+    times, its = [], []
+    for _ in range(reps):
+        t = time.perf_counter()
+        res = O.solve(H, b)
+        times.append(time.perf_counter() - t)
+        its.append(res.iters)
+    per = float(np.median(times))
+    it = int(np.median(its))
+    print(json.dumps({"n": n, "dofs": dofs(n), "solve_s": per, "iters": it, "setup_s": setup,
+                      "value": dofs(n) * it / per}))
+
+
+def run_oracle(n: int, reps: int) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", "--n", str(n),
+                        "--steps", str(reps)], capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle worker failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# --------------------------------------------------------------------------
+# distributed helpers
+# --------------------------------------------------------------------------
+def dist_setup(ngpus: int):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allsum(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def run_ours(args) -> None:
+    import torch
+
+    import stokes_inputs as si
+    import paper_2401_06277_gb300 as pkg
+    from paper_2401_06277_gb300 import build, stokes
+
+    ws, rank, local = dist_setup(args.gpus)
+    build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = args.n
+    N = dofs(n)
+    H = pkg.Hierarchy(n, rtol=1e-8, restart=30)
+    f_host = torch.from_numpy(si.random_force(n, args.seed + rank)).pin_memory()
+    ud_host = torch.from_numpy(si.manufactured_velocity(n)).pin_memory()
+    f = f_host.to(dev)
+    ud = ud_host.to(dev)
+    b = H.assemble_rhs(f, ud)
+    x = torch.empty_like(b)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        stokes.stokes_initial_guess(H.handle, b, x)
+        it, rel, st = stokes.stokes_fgmres_solve(H.handle, b, x)
+        return it, rel
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region ----
+    stokes.stokes_stats_reset(H.handle)
+    stokes.stokes_stats_enable_timing(H.handle, True)
+    l0 = stokes.stokes_stats_read(H.handle)["kernel_launches"]
+    props = torch.cuda.get_device_properties(dev)
+    bus = getattr(props, "pci_bus_id", None)
+    clocks = ClockSampler(f"{bus:02x}:00" if isinstance(bus, int) else None)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters, rels = [], []
+    for _ in range(args.steps):
+        it, rel = step()
+        iters.append(it)
+        rels.append(rel)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st = stokes.stokes_stats_read(H.handle)
+    stokes.stokes_stats_enable_timing(H.handle, False)
+    launches = st["kernel_launches"] - l0
+    ms_max = allmax(ws, ms)
+    vcycles_all = allsum(ws, st["vcycles"])
+    value = N * vcycles_all / (ms_max * 1e-3)
+
+    sweep_ms = st["sweep_ms"] / max(st["sweeps_timed"], 1)
+    fl = sweep_flops(n)
+    sm_max = args.sm_max_mhz or measured_peaks().get("sm_max_mhz", 2070.0)
+    peak_gflops = SM_COUNT * 4 * sm_max * 1e6 / 1e9   # 2 DFMA / clk / SM
+    achieved = fl / (sweep_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "kernel": "k_vanka_f64 (finest level)", "achieved": round(achieved, 2),
+                "peak": round(peak_gflops, 1), "unit": "GFLOP/s",
+                "frac": round(achieved / peak_gflops, 4), "traffic": args.traffic,
+                "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock",
+                "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": sweep_bytes(n),
+                "hbm_gbs_achieved": round(sweep_bytes(n) / (sweep_ms * 1e-3) / 1e9, 1),
+                "launch_ms": round(sweep_ms, 4), "launches_timed": st["sweeps_timed"]}
+
+    # ---- end-to-end through the public API with host buffers ----
+    x_host = torch.empty(N, dtype=torch.float64).pin_memory()
+    bi = f_host.numel() * 8 + ud_host.numel() * 8
+    bo = N * 8
+
+    def e2e_step():
+        f.copy_(f_host, non_blocking=True)
+        ud.copy_(ud_host, non_blocking=True)
+        stokes.stokes_assemble_rhs(H.handle, f, ud, b, n)
+        stokes.stokes_initial_guess(H.handle, b, x)
+        stokes.stokes_fgmres_solve(H.handle, b, x)
+        x_host.copy_(x, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    stokes.stokes_stats_reset(H.handle)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    e2e_ms = allmax(ws, e0.elapsed_time(e1))
+    e2e_vc = allsum(ws, stokes.stokes_stats_read(H.handle)["vcycles"])
+    e2e = {"value": N * e2e_vc / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
+           "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms / args.steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        o = run_oracle(ORACLE_N, 1)
+        cpu = {"value": o["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one FGMRES(30)+V(2,2) solve to 1e-8 at {o['n']}x{o['n']} ({o['dofs']} dofs, "
+                         f"{o['iters']} V-cycles, {o['solve_s']:.2f} s; setup {o['setup_s']:.1f} s excluded), "
+                         f"numpy/scipy, BLAS threads = 1"}
+    H.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"2D Stokes Q2-Q1, {n}x{n} elements, FP64, FGMRES(30) + V(2,2) "
+                                       f"additive Vanka (omega 0.7) to 1e-8, coarse 4x4",
+                           "n": n, "dofs": N, "levels": H.levels, "rhs": f"N(0,1) nodal force, seed {args.seed}",
+                           "l2": "inputs larger than L2 (each vector 8*dofs bytes)",
+                           "parallelism": f"replicas x{ws}"},
+                "time_to_solution_s": ms_max / args.steps / 1e3,
+                "iters": iters, "relres": rels, "vcycles": int(vcycles_all),
+                "ms_per_vcycle": ms_max / max(st["vcycles"], 1),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk}
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# reference arm: the CPU oracle, as it stands
+# --------------------------------------------------------------------------
+def run_reference(args) -> None:
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    n = ORACLE_N
+    # warm-up and timed steps: each step one oracle solve at n x n
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", "--n", str(n),
+                        "--steps", str(max(args.steps, 1))], capture_output=True, text=True, env=env,
+                       cwd=ROOT)
+    if r.returncode != 0:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle worker failed: " + r.stderr[-300:]}))
+        return
+    o = json.loads(r.stdout.strip().splitlines()[-1])
+    line = {"impl": "reference", "metric": METRIC, "value": o["value"], "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": o["solve_s"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"2D Stokes Q2-Q1, FP64, FGMRES(30) + V(2,2) additive Vanka to 1e-8; "
+                                   f"CPU oracle sample at {n}x{n}", "n": n, "dofs": o["dofs"]},
+            "cpu_baseline": {"value": o["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"median of {args.steps} solves at {n}x{n} ({o['iters']} V-cycles each)"},
+            "e2e": {"value": o["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_kernel(args) -> None:
+    """Time one kernel of the path alone on the finest level (for profiling): W + K launches."""
+    import torch
+
+    import stokes_inputs as si
+    import paper_2401_06277_gb300 as pkg
+    from paper_2401_06277_gb300 import build, stokes
+
+    build.build()
+    n = args.n
+    H = pkg.Hierarchy(n, restart=1)
+    lvl = H.levels - 1
+    x = torch.from_numpy(si.random_vector(n, 1)).cuda()
+    b = torch.from_numpy(si.random_vector(n, 2)).cuda()
+    out = torch.empty_like(b)
+    if args.kernel == "sweep":
+        fn = lambda: stokes.stokes_vanka_sweep(H.handle, lvl, x, b, out)
+        fl, by = sweep_flops(n), sweep_bytes(n)
+    elif args.kernel == "residual":
+        fn = lambda: stokes.stokes_residual(H.handle, lvl, b, x, out)
+        fl, by = 361.0 * (n + 1) ** 2, sweep_bytes(n)
+    else:
+        fn = lambda: stokes.stokes_vcycle_apply(H.handle, b, out)
+        fl, by = None, None
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    rec = {"kernel": args.kernel, "n": n, "ms": ms}
+    if fl:
+        rec["gflops"] = fl / (ms * 1e-3) / 1e9
+        rec["gbs"] = by / (ms * 1e-3) / 1e9
+    print(json.dumps(rec))
+    H.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--sm-max-mhz", type=float, default=None)
+    ap.add_argument("--traffic", type=float, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-worker", action="store_true")
+    ap.add_argument("--kernel", choices=["sweep", "residual", "vcycle"], default=None,
+                    help="time one kernel alone on the finest level (profiling mode)")
+    args = ap.parse_args()
+    if args.kernel:
+        run_kernel(args)
+        return
+    if args.oracle_worker:
+        oracle_worker(args.n, args.steps)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

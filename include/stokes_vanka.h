@@ -170,6 +170,23 @@ stokes_status stokes_rhs_transpose(stokes_hierarchy* h, const double* lambda, do
 stokes_status stokes_batched_solve(stokes_hierarchy* const* hs, int nprob, const double* const* b,
                                    double* const* x, int* iters, double* relres);
 
+/* Counters for measurement (the paper reports per-kernel runtimes, Section 6.2,
+ * and roofline positions, Section 6.7).  When timing is enabled the library
+ * records a CUDA-event pair on its stream around every finest-level Vanka
+ * sweep it launches; stokes_stats_read synchronises the stream and returns the
+ * summed event durations.  kernel_launches counts the CUDA kernels this
+ * library launched (all hierarchies, since load). */
+typedef struct {
+  long long kernel_launches;
+  long long vcycles;        /* V-cycles applied by this hierarchy since the last reset */
+  long long sweeps_timed;   /* finest-level sweeps timed since the last reset          */
+  double sweep_ms;          /* their summed durations (CUDA events)                    */
+} stokes_stats;
+
+stokes_status stokes_stats_enable_timing(stokes_hierarchy* h, int enable);
+stokes_status stokes_stats_reset(stokes_hierarchy* h);
+stokes_status stokes_stats_read(stokes_hierarchy* h, stokes_stats* out);
+
 /* Message of the last failure on this thread ("" if none). */
 const char* stokes_last_error(void);
 

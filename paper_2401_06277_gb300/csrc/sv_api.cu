@@ -83,6 +83,30 @@ stokes_status check_level(const stokes_hierarchy* h, int level, int min_level = 
   return STOKES_OK;
 }
 
+// Launch one FP64 sweep; on the finest level, bracket it with a CUDA-event
+// pair when timing is on (events are pooled and summed in stokes_stats_read).
+void timed_sweep(stokes_hierarchy* h, bool finest, sv::Level& L, const double* x, const double* b,
+                 double* xo) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h->timing && finest) {
+    if (h->ev_used + 2 > h->ev_pool.size()) {
+      for (int k = 0; k < 64; ++k) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) break;
+        h->ev_pool.push_back(e);
+      }
+    }
+    if (h->ev_used + 2 <= h->ev_pool.size()) {
+      e0 = h->ev_pool[h->ev_used];
+      e1 = h->ev_pool[h->ev_used + 1];
+      h->ev_used += 2;
+      cudaEventRecord(e0, h->stream);
+    }
+  }
+  sv::launch_vanka_f64(L.d, L.cd, x, b, xo, h->prm.omega, h->stream);
+  if (e1) cudaEventRecord(e1, h->stream);
+}
+
 // ---- V-cycle (Algorithm 1), FP64 ----
 void vcycle_f64(stokes_hierarchy* h, int l, const double* b, double* out) {
   cudaStream_t s = h->stream;
@@ -92,10 +116,11 @@ void vcycle_f64(stokes_hierarchy* h, int l, const double* b, double* out) {
     return;
   }
   const double w = h->prm.omega;
+  const bool finest = (l == static_cast<int>(h->lv.size()) - 1);
   double* cur = nullptr;  // nullptr = zero initial guess
   for (int it = 0; it < h->prm.nu1; ++it) {
     double* dst = (cur == L.x0) ? L.x1 : L.x0;
-    sv::launch_vanka_f64(L.d, L.cd, cur, b, dst, w, s);
+    timed_sweep(h, finest, L, cur, b, dst);
     cur = dst;
   }
   if (cur == nullptr) {
@@ -109,7 +134,7 @@ void vcycle_f64(stokes_hierarchy* h, int l, const double* b, double* out) {
   sv::launch_prolong_add(L.d, C.d, C.e, cur, s);
   for (int it = 0; it < h->prm.nu2; ++it) {
     double* dst = (it == h->prm.nu2 - 1) ? out : ((cur == L.x0) ? L.x1 : L.x0);
-    sv::launch_vanka_f64(L.d, L.cd, cur, b, dst, w, s);
+    timed_sweep(h, finest, L, cur, b, dst);
     cur = dst;
   }
   if (h->prm.nu2 == 0) cudaMemcpyAsync(out, cur, L.d.N * sizeof(double), cudaMemcpyDeviceToDevice, s);
@@ -188,6 +213,7 @@ stokes_status fgmres(stokes_hierarchy* h, const double* b, double* x, int* iters
       double* vj = V + j * ld;
       double* zj = Z + j * ld;
       double* w = V + (j + 1) * ld;
+      ++h->vcycles;
       vcycle_f64(h, static_cast<int>(h->lv.size()) - 1, vj, zj);
       sv::launch_apply(F.d, zj, nullptr, w, 0, s);
       // classical Gram-Schmidt, twice
@@ -332,9 +358,44 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   return STOKES_OK;
 }
 
+stokes_status stokes_stats_enable_timing(stokes_hierarchy* h, int enable) {
+  if (!h) return fail(STOKES_ERR_ARG, "null hierarchy");
+  h->timing = enable != 0;
+  return STOKES_OK;
+}
+
+stokes_status stokes_stats_reset(stokes_hierarchy* h) {
+  if (!h) return fail(STOKES_ERR_ARG, "null hierarchy");
+  SV_TRY(cudaStreamSynchronize(h->stream), "stats reset");
+  h->ev_used = 0;
+  h->sweeps_timed = 0;
+  h->sweep_ms = 0.0;
+  h->vcycles = 0;
+  return STOKES_OK;
+}
+
+stokes_status stokes_stats_read(stokes_hierarchy* h, stokes_stats* out) {
+  if (!h || !out) return fail(STOKES_ERR_ARG, "null argument");
+  SV_TRY(cudaStreamSynchronize(h->stream), "stats read");
+  for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
+    float ms = 0.0f;
+    SV_TRY(cudaEventElapsedTime(&ms, h->ev_pool[k], h->ev_pool[k + 1]), "event elapsed");
+    h->sweep_ms += ms;
+    ++h->sweeps_timed;
+  }
+  h->ev_used = 0;
+  out->kernel_launches = sv::g_launches.load();
+  out->vcycles = h->vcycles;
+  out->sweeps_timed = h->sweeps_timed;
+  out->sweep_ms = h->sweep_ms;
+  return STOKES_OK;
+}
+
 stokes_status stokes_hierarchy_destroy(stokes_hierarchy* h) {
   if (!h) return STOKES_OK;
   cudaStreamSynchronize(h->stream);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  h->ev_pool.clear();
   free_all(h);
   delete h;
   return STOKES_OK;
@@ -427,6 +488,7 @@ stokes_status stokes_initial_guess(stokes_hierarchy* h, const double* b, double*
 stokes_status stokes_vcycle_apply(stokes_hierarchy* h, const double* r, double* z) {
   if (!h || !r || !z) return fail(STOKES_ERR_ARG, "null argument");
   if (r == z) return fail(STOKES_ERR_ARG, "r and z must not alias");
+  ++h->vcycles;
   vcycle_f64(h, static_cast<int>(h->lv.size()) - 1, r, z);
   return check_launch("vcycle");
 }

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <string>
 #include <vector>
@@ -65,9 +66,20 @@ struct stokes_hierarchy {
   double* partials = nullptr;    // dot-product partial sums
   int npart = 0;                 // blocks of the dot kernels
   double* host_scalars = nullptr;  // pinned host mirror of a few scalars
+  // measurement
+  bool timing = false;
+  long long vcycles = 0;
+  std::vector<cudaEvent_t> ev_pool;   // pairs (start, stop) of finest-level sweeps
+  size_t ev_used = 0;
+  long long sweeps_timed = 0;
+  double sweep_ms = 0.0;
 };
 
 namespace sv {
+
+// kernels launched by this library (every launch_* adds its own count)
+extern std::atomic<long long> g_launches;
+inline void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // ---- host setup (sv_setup.cu) ----
 // Class data (Schur factors) for a level, and the 51 x 51 dense inverses.

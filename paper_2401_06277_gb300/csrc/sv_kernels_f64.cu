@@ -524,18 +524,21 @@ dim3 grid2(int nx, int ny, dim3 blk) {
 
 void launch_apply(const LevelDev& L, const double* x, const double* b, double* y, int residual,
                   cudaStream_t s) {
+  count_launches(2);
   dim3 blk(32, 8);
   k_apply_vel<<<grid2(L.nq, L.nq, blk), blk, 0, s>>>(L, x, b, y, residual);
   k_apply_p<<<grid2(L.np, L.np, blk), blk, 0, s>>>(L, x, b, y, residual);
 }
 
 void launch_rhs(const LevelDev& L, const double* f, const double* ud, double* b, cudaStream_t s) {
+  count_launches(2);
   dim3 blk(32, 8);
   k_rhs_vel<<<grid2(L.nq, L.nq, blk), blk, 0, s>>>(L, f, ud, b);
   k_rhs_p<<<grid2(L.np, L.np, blk), blk, 0, s>>>(L, ud, b);
 }
 
 void launch_rhs_transpose(const LevelDev& L, const double* lam, double* g, cudaStream_t s) {
+  count_launches(1);
   dim3 blk(32, 8);
   k_rhs_transpose<<<grid2(L.nq, L.nq, blk), blk, 0, s>>>(L, lam, g);
 }
@@ -549,6 +552,7 @@ cudaError_t vanka_f64_prepare() {
 
 void launch_vanka_f64(const LevelDev& L, const double* cd, const double* x, const double* b,
                       double* xo, double omega, cudaStream_t s) {
+  count_launches(1);
   using T = VTile<VK_TX, VK_TY>;
   dim3 grid((L.np + VK_TX - 1) / VK_TX, (L.np + VK_TY - 1) / VK_TY);
   k_vanka_f64<VK_TX, VK_TY, VK_NT><<<grid, VK_NT, T::TOTAL * sizeof(double), s>>>(L, cd, x, b, xo,
@@ -557,17 +561,20 @@ void launch_vanka_f64(const LevelDev& L, const double* cd, const double* x, cons
 
 void launch_restrict(const LevelDev& F, const LevelDev& C, const double* rf, double* rc,
                      cudaStream_t s) {
+  count_launches(1);
   dim3 blk(32, 8);
   k_restrict<<<grid2(C.nq, C.nq, blk), blk, 0, s>>>(F, C, rf, rc);
 }
 
 void launch_prolong_add(const LevelDev& F, const LevelDev& C, const double* ec, double* xf,
                         cudaStream_t s) {
+  count_launches(1);
   dim3 blk(32, 8);
   k_prolong_add<<<grid2(F.nq, F.nq, blk), blk, 0, s>>>(F, C, ec, xf);
 }
 
 void launch_coarse(const double* G, int N0, const double* r, double* e, cudaStream_t s) {
+  count_launches(1);
   k_coarse<<<1, 256, N0 * sizeof(double), s>>>(G, N0, r, e);
 }
 

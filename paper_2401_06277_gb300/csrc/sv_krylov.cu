@@ -173,12 +173,15 @@ int grid_for(long long N, int nt) {
 
 }  // namespace
 
+std::atomic<long long> g_launches{0};
+
 int dot_blocks() { return DOT_BLOCKS; }
 
 void launch_multidot(const double* V, long long ld, int nk, const double* w, long long N,
                      double* partials, int npart, double* out, int accumulate, cudaStream_t s) {
   for (int k0 = 0; k0 < nk; k0 += DOT_KMAX) {
     const int kk = (nk - k0 < DOT_KMAX) ? nk - k0 : DOT_KMAX;
+    count_launches(2);
     k_multidot<<<npart, DOT_NT, 0, s>>>(V + k0 * ld, ld, kk, w, N, partials, npart);
     k_reduce<<<kk, 256, 0, s>>>(partials, npart, out + k0, accumulate);
   }
@@ -186,36 +189,44 @@ void launch_multidot(const double* V, long long ld, int nk, const double* w, lon
 
 void launch_multiaxpy(double* w, const double* V, long long ld, int nk, const double* coef,
                       double sign, long long N, cudaStream_t s) {
+  count_launches(1);
   k_multiaxpy<<<grid_for(N, 256), 256, 0, s>>>(w, V, ld, nk, coef, sign, N);
 }
 
 void launch_scale(double* y, const double* x, const double* den, double scal, long long N,
                   cudaStream_t s) {
+  count_launches(1);
   k_scale<<<grid_for(N, 256), 256, 0, s>>>(y, x, den, scal, N);
 }
 
 void launch_givens(double* H, int ldh, double* cs, double* sn, double* g, const double* hcol,
                    const double* hnorm, int j, double* est, cudaStream_t s) {
+  count_launches(1);
   k_givens<<<1, 32, 0, s>>>(H, ldh, cs, sn, g, hcol, hnorm, j, est);
 }
 
 void launch_backsolve(const double* H, int ldh, const double* g, int k, double* y, cudaStream_t s) {
+  count_launches(1);
   k_backsolve<<<1, 32, 0, s>>>(H, ldh, g, k, y);
 }
 
 void launch_fill(double* p, double v, long long N, cudaStream_t s) {
+  count_launches(1);
   k_fill<<<grid_for(N, 256), 256, 0, s>>>(p, v, N);
 }
 
 void launch_set_scalar(double* p, const double* src_sqrt, cudaStream_t s) {
+  count_launches(1);
   k_sqrt<<<1, 32, 0, s>>>(p, src_sqrt);
 }
 
 void launch_add_small(double* a, const double* b, int n, cudaStream_t s) {
+  count_launches(1);
   k_add_small<<<1, 64, 0, s>>>(a, b, n);
 }
 
 void launch_dirichlet_copy(const LevelDev& L, const double* src, double* dst, cudaStream_t s) {
+  count_launches(1);
   k_dirichlet_copy<<<grid_for(L.N, 256), 256, 0, s>>>(L, src, dst);
 }
 

@@ -37,6 +37,11 @@ class StokesError(RuntimeError):
         self.status = status
 
 
+class stokes_stats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_longlong), ("vcycles", ctypes.c_longlong),
+                ("sweeps_timed", ctypes.c_longlong), ("sweep_ms", ctypes.c_double)]
+
+
 class stokes_params(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("coarse_n", ctypes.c_int), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
@@ -79,6 +84,9 @@ def _load():
         "stokes_solve_adjoint": (I, [P, VP, VP, VP, IP, DP]),
         "stokes_rhs_transpose": (I, [P, VP, VP]),
         "stokes_batched_solve": (I, [ctypes.POINTER(P), I, ctypes.POINTER(VP), ctypes.POINTER(VP), IP, DP]),
+        "stokes_stats_enable_timing": (I, [P, I]),
+        "stokes_stats_reset": (I, [P]),
+        "stokes_stats_read": (I, [P, ctypes.POINTER(stokes_stats)]),
         "stokes_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -96,6 +104,7 @@ def exported_symbols() -> list[str]:
             "stokes_residual", "stokes_vanka_sweep", "stokes_restrict", "stokes_prolong_add",
             "stokes_coarse_solve", "stokes_initial_guess", "stokes_vcycle_apply", "stokes_fgmres_solve",
             "stokes_solve_adjoint", "stokes_rhs_transpose", "stokes_batched_solve",
+            "stokes_stats_enable_timing", "stokes_stats_reset", "stokes_stats_read",
             "stokes_last_error"]
 
 
@@ -250,6 +259,21 @@ def stokes_batched_solve(hs, bs, xs) -> tuple[list[int], list[float]]:
     rel = (ctypes.c_double * k)()
     _check(_load().stokes_batched_solve(H, k, B, X, it, rel))
     return list(it), list(rel)
+
+
+def stokes_stats_enable_timing(h, enable: bool) -> None:
+    _check(_load().stokes_stats_enable_timing(h, int(bool(enable))))
+
+
+def stokes_stats_reset(h) -> None:
+    _check(_load().stokes_stats_reset(h))
+
+
+def stokes_stats_read(h) -> dict:
+    st = stokes_stats()
+    _check(_load().stokes_stats_read(h, ctypes.byref(st)))
+    return {"kernel_launches": st.kernel_launches, "vcycles": st.vcycles,
+            "sweeps_timed": st.sweeps_timed, "sweep_ms": st.sweep_ms}
 
 
 def stokes_last_error() -> str:
