@@ -187,6 +187,28 @@ stokes_status stokes_stats_enable_timing(stokes_hierarchy* h, int enable);
 stokes_status stokes_stats_reset(stokes_hierarchy* h);
 stokes_status stokes_stats_read(stokes_hierarchy* h, stokes_stats* out);
 
+/* Largest grid accepted by stokes_residual_norm_noalloc. */
+#define STOKES_NOALLOC_MAX_N 8192
+
+/* ||b - A x||_2 on an n x n grid (1 <= n <= STOKES_NOALLOC_MAX_N) without
+ * allocating any memory and without a hierarchy.  The paper has no
+ * counterpart: this is a service for callers that cannot allocate device
+ * memory -- code whose device memory is all owned by another allocator, or a
+ * check that runs while another component records the stream into a CUDA
+ * graph (cudaMalloc is not allowed then).  b and x are device vectors of
+ * length N(n) in the layout above; *norm (device memory, one double) receives
+ * the norm when the stream reaches this work; stream is a cudaStream_t.
+ * Scratch: a fixed array of 3 * STOKES_NOALLOC_MAX_N + 2 doubles (196.6 KB)
+ * that every GPU using this library keeps until the process exits.  The
+ * first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress), so make one call per device before any stream
+ * capture.  Calls share the array: two calls whose kernels overlap on the
+ * GPU (different streams or host threads) race.  Each call overwrites every
+ * slot it later reads, so nothing is carried over from the previous call.
+ * Returns STOKES_ERR_ARG for n out of range or null pointers. */
+stokes_status stokes_residual_norm_noalloc(int n, double viscosity, const double* b,
+                                           const double* x, double* norm, void* stream);
+
 /* Message of the last failure on this thread ("" if none). */
 const char* stokes_last_error(void);
 

@@ -253,6 +253,10 @@ stokes_status fgmres(stokes_hierarchy* h, const double* b, double* x, int* iters
 
 }  // namespace
 
+namespace sv {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace sv
+
 extern "C" {
 
 void stokes_default_params(stokes_params* p) {

@@ -77,6 +77,9 @@ struct stokes_hierarchy {
 
 namespace sv {
 
+// message returned by stokes_last_error() on this thread
+void set_last_error(const std::string& msg);
+
 // kernels launched by this library (every launch_* adds its own count)
 extern std::atomic<long long> g_launches;
 inline void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }

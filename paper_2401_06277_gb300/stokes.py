@@ -87,6 +87,7 @@ def _load():
         "stokes_stats_enable_timing": (I, [P, I]),
         "stokes_stats_reset": (I, [P]),
         "stokes_stats_read": (I, [P, ctypes.POINTER(stokes_stats)]),
+        "stokes_residual_norm_noalloc": (I, [I, D, VP, VP, VP, VP]),
         "stokes_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -105,7 +106,7 @@ def exported_symbols() -> list[str]:
             "stokes_coarse_solve", "stokes_initial_guess", "stokes_vcycle_apply", "stokes_fgmres_solve",
             "stokes_solve_adjoint", "stokes_rhs_transpose", "stokes_batched_solve",
             "stokes_stats_enable_timing", "stokes_stats_reset", "stokes_stats_read",
-            "stokes_last_error"]
+            "stokes_residual_norm_noalloc", "stokes_last_error"]
 
 
 def _check(st: int, allow=()) -> int:
@@ -274,6 +275,15 @@ def stokes_stats_read(h) -> dict:
     _check(_load().stokes_stats_read(h, ctypes.byref(st)))
     return {"kernel_launches": st.kernel_launches, "vcycles": st.vcycles,
             "sweeps_timed": st.sweeps_timed, "sweep_ms": st.sweep_ms}
+
+
+def stokes_residual_norm_noalloc(n: int, viscosity: float, b, x, norm,
+                                 stream: torch.cuda.Stream | None = None) -> None:
+    """||b - A x|| into the one-element device tensor `norm`; allocates nothing (see the header)."""
+    N = vec_len(n)
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(_load().stokes_residual_norm_noalloc(int(n), float(viscosity), _ptr(b, N, "b"), _ptr(x, N, "x"),
+                                                _ptr(norm, 1, "norm"), ctypes.c_void_p(s)))
 
 
 def stokes_last_error() -> str:
