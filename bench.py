@@ -266,7 +266,8 @@ def run_ours(args) -> None:
                 "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock",
                 "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": sweep_bytes(n),
                 "hbm_gbs_achieved": round(sweep_bytes(n) / (sweep_ms * 1e-3) / 1e9, 1),
-                "launch_ms": round(sweep_ms, 4), "launches_timed": st["sweeps_timed"]}
+                "launch_ms": round(sweep_ms, 4), "launches_timed": st["sweeps_timed"],
+                "tile": ["8x8", "16x8", "16x16"][stokes.stokes_level_tile(H.handle, H.levels - 1)]}
 
     # ---- end-to-end through the public API with host buffers ----
     x_host = torch.empty(N, dtype=torch.float64).pin_memory()
@@ -367,7 +368,7 @@ def run_kernel(args) -> None:
 
     build.build()
     n = args.n
-    H = pkg.Hierarchy(n, restart=1)
+    H = pkg.Hierarchy(n, restart=1, tile=args.tile)
     lvl = H.levels - 1
     x = torch.from_numpy(si.random_vector(n, 1)).cuda()
     b = torch.from_numpy(si.random_vector(n, 2)).cuda()
@@ -392,7 +393,8 @@ def run_kernel(args) -> None:
     e1.record(s)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    rec = {"kernel": args.kernel, "n": n, "ms": ms}
+    rec = {"kernel": args.kernel, "n": n, "ms": ms,
+           "tile": ["8x8", "16x8", "16x16"][stokes.stokes_level_tile(H.handle, lvl)]}
     if fl:
         rec["gflops"] = fl / (ms * 1e-3) / 1e9
         rec["gbs"] = by / (ms * 1e-3) / 1e9
@@ -412,6 +414,7 @@ def main():
     ap.add_argument("--traffic", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-worker", action="store_true")
+    ap.add_argument("--tile", type=int, default=-1, help="Vanka tile shape (-1: autotuned)")
     ap.add_argument("--kernel", choices=["sweep", "residual", "vcycle"], default=None,
                     help="time one kernel alone on the finest level (profiling mode)")
     args = ap.parse_args()

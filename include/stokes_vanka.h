@@ -76,6 +76,8 @@ typedef struct {
   int maxit;        /* FGMRES iteration cap                            (1000) */
   double rtol;      /* stop when ||b - A x|| <= rtol ||b - A x0||      (1e-8) */
   stokes_precision prec;  /*                                          (FP64) */
+  int tile;         /* Vanka tile shape: -1 = chosen per level by timing at
+                       creation, 0 = 8x8, 1 = 16x8, 2 = 16x16 vertices (-1) */
 } stokes_params;
 
 typedef struct stokes_hierarchy stokes_hierarchy;
@@ -96,6 +98,8 @@ stokes_status stokes_hierarchy_destroy(stokes_hierarchy* h);
 /* Number of levels L and the grid size n_l of level l (0 = coarsest). */
 stokes_status stokes_level_info(const stokes_hierarchy* h, int* num_levels, int* n_finest);
 stokes_status stokes_level_n(const stokes_hierarchy* h, int level, int* n_level);
+/* Tile shape used by the Vanka sweep on a level (see stokes_params.tile). */
+stokes_status stokes_level_tile(const stokes_hierarchy* h, int level, int* tile);
 
 /* Right-hand side of the eliminated system (Section 2.2 with the boundary data
  * moved to the right): b = [M f - L_{.,D} u_D on free velocity rows ;

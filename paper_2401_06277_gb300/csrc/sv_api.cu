@@ -103,7 +103,7 @@ void timed_sweep(stokes_hierarchy* h, bool finest, sv::Level& L, const double* x
       cudaEventRecord(e0, h->stream);
     }
   }
-  sv::launch_vanka_f64(L.d, L.cd, x, b, xo, h->prm.omega, h->stream);
+  sv::launch_vanka_f64(L.d, L.cd, x, b, xo, h->prm.omega, L.vk_cfg, h->stream);
   if (e1) cudaEventRecord(e1, h->stream);
 }
 
@@ -251,6 +251,49 @@ stokes_status fgmres(stokes_hierarchy* h, const double* b, double* x, int* iters
   return STOKES_OK;
 }
 
+// Tile shape of the FP64 sweep per level: fixed by params.tile, or (tile = -1)
+// the fastest of the shapes on that level, timed with CUDA events on the
+// hierarchy's stream (levels below 64 x 64 use 8 x 8: too few tiles otherwise).
+cudaError_t choose_tiles(stokes_hierarchy* h) {
+  cudaStream_t s = h->stream;
+  for (sv::Level& L : h->lv) {
+    if (h->prm.tile >= 0) {
+      L.vk_cfg = h->prm.tile;
+      continue;
+    }
+    L.vk_cfg = 0;
+    if (L.d.n < 64) continue;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(L.x0, 0, L.d.N * sizeof(double), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(L.b, 0, L.d.N * sizeof(double), s)) != cudaSuccess) return e;
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      return e;
+    }
+    float best = 1e30f;
+    for (int c = 0; c < sv::VANKA_F64_NCFG; ++c) {
+      sv::launch_vanka_f64(L.d, L.cd, L.x0, L.b, L.x1, h->prm.omega, c, s);
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 3; ++r) sv::launch_vanka_f64(L.d, L.cd, L.x0, L.b, L.x1, h->prm.omega, c, s);
+      cudaEventRecord(e1, s);
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        L.vk_cfg = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace
 
 namespace sv {
@@ -269,6 +312,7 @@ void stokes_default_params(stokes_params* p) {
   p->maxit = 1000;
   p->rtol = 1e-8;
   p->prec = STOKES_FP64;
+  p->tile = -1;
 }
 
 const char* stokes_last_error(void) { return g_err.c_str(); }
@@ -287,6 +331,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   if (prm.nu1 < 0 || prm.nu2 < 0 || prm.maxit < 1 || !(prm.rtol >= 0.0) || !(prm.omega > 0.0))
     return fail(STOKES_ERR_ARG, "bad smoothing / iteration parameters");
   if (prm.prec != STOKES_FP64) return fail(STOKES_ERR_ARG, "precision mode not available in this build");
+  if (prm.tile < -1 || prm.tile >= sv::VANKA_F64_NCFG) return fail(STOKES_ERR_ARG, "tile must be -1..2");
   std::vector<int> sizes;
   {
     int m = n;
@@ -358,7 +403,19 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
     delete h;
     return cuda_fail(e, "Krylov workspace allocation");
   }
+  if ((e = choose_tiles(h)) != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return cuda_fail(e, "tile autotuning");
+  }
   *out = h;
+  return STOKES_OK;
+}
+
+stokes_status stokes_level_tile(const stokes_hierarchy* h, int level, int* tile) {
+  stokes_status st = check_level(h, level);
+  if (st != STOKES_OK) return st;
+  if (tile) *tile = h->lv[level].vk_cfg;
   return STOKES_OK;
 }
 
@@ -455,7 +512,7 @@ stokes_status stokes_vanka_sweep(stokes_hierarchy* h, int level, const double* x
   if (!b || !x_out) return fail(STOKES_ERR_ARG, "null vector");
   if (x_out == x || x_out == b) return fail(STOKES_ERR_ARG, "x_out must not alias x or b");
   sv::Level& L = h->lv[level];
-  sv::launch_vanka_f64(L.d, L.cd, x, b, x_out, h->prm.omega, h->stream);
+  sv::launch_vanka_f64(L.d, L.cd, x, b, x_out, h->prm.omega, L.vk_cfg, h->stream);
   return check_launch("vanka_sweep");
 }
 

@@ -44,6 +44,7 @@ struct Level {
   double* r = nullptr;    // residual scratch
   double* e = nullptr;    // V-cycle result of this level (coarse correction)
   double* cd = nullptr;   // NCLASS * CD_STRIDE class data (device)
+  int vk_cfg = 0;         // tile shape of the FP64 sweep on this level
   std::vector<double> cd_host;
   std::vector<double> full_inv_host;  // NCLASS * 51 * 51 dense inverses (host)
 };
@@ -99,8 +100,11 @@ void launch_apply(const LevelDev& L, const double* x, const double* b, double* y
                   cudaStream_t s);
 void launch_rhs(const LevelDev& L, const double* f, const double* ud, double* b, cudaStream_t s);
 void launch_rhs_transpose(const LevelDev& L, const double* lam, double* g, cudaStream_t s);
+// FP64 Vanka sweep (sv_vanka_f64.cu); cfg selects the tile shape (8x8, 16x8, 16x16 vertices)
+constexpr int VANKA_F64_NCFG = 3;
 void launch_vanka_f64(const LevelDev& L, const double* cd, const double* x, const double* b,
-                      double* xo, double omega, cudaStream_t s);
+                      double* xo, double omega, int cfg, cudaStream_t s);
+const char* vanka_f64_cfg_name(int cfg);
 void launch_restrict(const LevelDev& F, const LevelDev& C, const double* rf, double* rc,
                      cudaStream_t s);
 void launch_prolong_add(const LevelDev& F, const LevelDev& C, const double* ec, double* xf,

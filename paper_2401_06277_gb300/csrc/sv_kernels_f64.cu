@@ -191,205 +191,6 @@ __global__ void k_rhs_transpose(LevelDev L, const double* __restrict__ lam, doub
 }
 
 // ---------------------------------------------------------------------------
-// Fused additive Vanka sweep (FP64).  A CTA owns TX x TY vertices; it computes
-// the residual on the patch windows of those vertices plus a one-vertex halo,
-// solves every patch of the (TX+2) x (TY+2) region exactly (Schur-factored
-// class inverse), and writes x + omega * (sum of patch corrections) / m_j for
-// the dofs it owns.  Owned dofs of vertex (i, j): Q2 nodes (2i-1..2i) x
-// (2j-1..2j), both components, and p(i, j).  No atomics: deterministic.
-// ---------------------------------------------------------------------------
-template <int TX, int TY>
-struct VTile {
-  static constexpr int XW = 2 * TX + 11, XH = 2 * TY + 11;  // x window, Q2 nodes
-  static constexpr int PW = TX + 6, PH = TY + 6;            // x window, vertices
-  static constexpr int RW = 2 * TX + 7, RH = 2 * TY + 7;    // residual window, Q2 nodes
-  static constexpr int QW = TX + 2, QH = TY + 2;            // patches (and residual vertices)
-  static constexpr int NPATCH = QW * QH;
-  static constexpr int SX = 2 * XW * XH, SP = PW * PH, SR = 2 * RW * RH, SRP = NPATCH;
-  static constexpr int SD = NPATCH * 51;
-  static constexpr int TOTAL = SX + SP + SR + SRP + SD;
-};
-
-constexpr int VK_TX = 8, VK_TY = 8, VK_NT = 128;
-
-template <int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) k_vanka_f64(LevelDev L, const double* __restrict__ cd,
-                                                  const double* __restrict__ x,
-                                                  const double* __restrict__ b,
-                                                  double* __restrict__ xo, double omega) {
-  using T = VTile<TX, TY>;
-  extern __shared__ double smem[];
-  double* sx = smem;
-  double* sp = sx + T::SX;
-  double* sr = sp + T::SP;
-  double* srp = sr + T::SR;
-  double* sd = srp + T::SRP;
-  const int n = L.n, nq = L.nq, np = L.np;
-  const long long nv = L.nv;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int tid = threadIdx.x;
-
-  // 1. x window (Dirichlet and outside entries read as 0: their columns are dropped)
-  {
-    const int XI0 = 2 * i0 - 6, XJ0 = 2 * j0 - 6;
-    for (int t = tid; t < T::SX; t += NT) {
-      const int c = t / (T::XW * T::XH);
-      const int rem = t - c * T::XW * T::XH;
-      const int jj = rem / T::XW, ii = rem - jj * T::XW;
-      const int I = XI0 + ii, J = XJ0 + jj;
-      double v = 0.0;
-      if (x != nullptr && is_free(I, J, nq)) v = x[c * nv + static_cast<long long>(J) * nq + I];
-      sx[t] = v;
-    }
-    for (int t = tid; t < T::SP; t += NT) {
-      const int jj = t / T::PW, ii = t - jj * T::PW;
-      const int i = i0 - 3 + ii, j = j0 - 3 + jj;
-      double v = 0.0;
-      if (x != nullptr && i >= 0 && j >= 0 && i <= n && j <= n)
-        v = x[2 * nv + static_cast<long long>(j) * np + i];
-      sp[t] = v;
-    }
-  }
-  __syncthreads();
-
-  // 2. residual r = b - A x on the windows of the (TX+2) x (TY+2) patches
-  const double cl = L.nu / 90.0, cb = -L.h / 18.0;
-  {
-    const int RI0 = 2 * i0 - 4, RJ0 = 2 * j0 - 4;
-    for (int t = tid; t < T::SR; t += NT) {
-      const int c = t / (T::RW * T::RH);
-      const int rem = t - c * T::RW * T::RH;
-      const int jj = rem / T::RW, ii = rem - jj * T::RW;
-      const int I = RI0 + ii, J = RJ0 + jj;
-      double r = 0.0;
-      if (I >= 0 && J >= 0 && I < nq && J < nq) {
-        const long long k = c * nv + static_cast<long long>(J) * nq + I;
-        if (!is_free(I, J, nq)) {
-          r = b[k] - (x != nullptr ? x[k] : 0.0);
-        } else {
-          const double* xs = sx + c * T::XW * T::XH + (jj + 2) * T::XW + (ii + 2);
-          double s = 0.0;
-#pragma unroll
-          for (int dJ = -2; dJ <= 2; ++dJ) {
-            const double mJ = m1(J, dJ), kJ = k1(J, dJ);
-#pragma unroll
-            for (int dI = -2; dI <= 2; ++dI) {
-              const double cc = k1(I, dI) * mJ + m1(I, dI) * kJ;
-              if (cc != 0.0) s = fma(cc, xs[dJ * T::XW + dI], s);
-            }
-          }
-          double g = 0.0;
-#pragma unroll
-          for (int dj = -1; dj <= 1; ++dj) {
-            const int j = J / 2 + dj;
-#pragma unroll
-            for (int di = -1; di <= 1; ++di) {
-              const int i = I / 2 + di;
-              const double w = (c == 0) ? ccol(I, i) * ncol(J, j) : ncol(I, i) * ccol(J, j);
-              if (w != 0.0) g = fma(w, sp[(j - (j0 - 3)) * T::PW + (i - (i0 - 3))], g);
-            }
-          }
-          r = b[k] - (cl * s + cb * g);
-        }
-      }
-      sr[t] = r;
-    }
-    for (int t = tid; t < T::SRP; t += NT) {
-      const int jj = t / T::QW, ii = t - jj * T::QW;
-      const int i = i0 - 1 + ii, j = j0 - 1 + jj;
-      double r = 0.0;
-      if (i >= 0 && j >= 0 && i <= n && j <= n) {
-        double s = 0.0;
-        // window of vertex (i, j) in sx: Q2 (2i + dI) - (2 i0 - 6) = 2 ii + 4 + dI
-        const double* xs0 = sx + (2 * jj + 4) * T::XW + (2 * ii + 4);
-        const double* xs1 = xs0 + T::XW * T::XH;
-#pragma unroll
-        for (int dJ = -2; dJ <= 2; ++dJ) {
-#pragma unroll
-          for (int dI = -2; dI <= 2; ++dI) {
-            const double wx = crow(dI) * nrow(dJ), wy = nrow(dI) * crow(dJ);
-            if (wx != 0.0) s = fma(wx, xs0[dJ * T::XW + dI], s);
-            if (wy != 0.0) s = fma(wy, xs1[dJ * T::XW + dI], s);
-          }
-        }
-        r = b[2 * nv + static_cast<long long>(j) * np + i] - cb * s;
-      }
-      srp[t] = r;
-    }
-  }
-  __syncthreads();
-
-  // 3. exact patch solves, one thread per patch
-  for (int t = tid; t < T::NPATCH; t += NT) {
-    const int qj = t / T::QW, qi = t - qj * T::QW;
-    const int pi = i0 - 1 + qi, pj = j0 - 1 + qj;
-    if (pi < 0 || pj < 0 || pi > n || pj > n) continue;
-    const int cls = 5 * axis_class(pj, n) + axis_class(pi, n);
-    const double* C = cd + cls * CD_STRIDE;
-    double ru[50];
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-      for (int wj = 0; wj < 5; ++wj)
-#pragma unroll
-        for (int wi = 0; wi < 5; ++wi)
-          ru[c * 25 + wj * 5 + wi] = sr[c * T::RW * T::RH + (2 * qj + wj) * T::RW + 2 * qi + wi];
-    double zr = 0.0;
-#pragma unroll
-    for (int k = 0; k < 50; ++k) zr = fma(__ldg(C + CD_Z + k), ru[k], zr);
-    const double dp = (zr - srp[t]) * __ldg(C + CD_SINV);
-    double* D = sd + t * 51;
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-#pragma unroll 1
-      for (int o = 0; o < 25; ++o) {
-        const double* Kr = C + CD_KINV + o * 25;
-        double acc = 0.0;
-#pragma unroll
-        for (int k = 0; k < 25; ++k) acc = fma(__ldg(Kr + k), ru[c * 25 + k], acc);
-        D[c * 25 + o] = acc - __ldg(C + CD_Z + c * 25 + o) * dp;
-      }
-    }
-    D[50] = dp;
-  }
-  __syncthreads();
-
-  // 4. weighted additive update of the owned dofs
-  constexpr int OW = 2 * TX, OH = 2 * TY;
-  for (int t = tid; t < 2 * OW * OH + TX * TY; t += NT) {
-    if (t < 2 * OW * OH) {
-      const int c = t / (OW * OH);
-      const int rem = t - c * OW * OH;
-      const int oj = rem / OW, oi = rem - oj * OW;
-      const int I = 2 * i0 - 1 + oi, J = 2 * j0 - 1 + oj;
-      if (I < 0 || J < 0 || I >= nq || J >= nq) continue;
-      const int pil = I < 2 ? 0 : (I - 1) / 2, pih = min(n, (I + 2) / 2);
-      const int pjl = J < 2 ? 0 : (J - 1) / 2, pjh = min(n, (J + 2) / 2);
-      double acc = 0.0;
-      for (int pj = pjl; pj <= pjh; ++pj) {
-        for (int pi = pil; pi <= pih; ++pi) {
-          const int q = (pj - (j0 - 1)) * T::QW + (pi - (i0 - 1));
-          acc += sd[q * 51 + c * 25 + (J - 2 * pj + 2) * 5 + (I - 2 * pi + 2)];
-        }
-      }
-      const double m = static_cast<double>((pih - pil + 1) * (pjh - pjl + 1));
-      const long long k = c * nv + static_cast<long long>(J) * nq + I;
-      const double xold = x != nullptr ? x[k] : 0.0;
-      xo[k] = xold + omega * acc / m;
-    } else {
-      const int u = t - 2 * OW * OH;
-      const int vj = u / TX, vi = u - vj * TX;
-      const int i = i0 + vi, j = j0 + vj;
-      if (i > n || j > n) continue;
-      const int q = (vj + 1) * T::QW + (vi + 1);
-      const long long k = 2 * nv + static_cast<long long>(j) * np + i;
-      const double xold = x != nullptr ? x[k] : 0.0;
-      xo[k] = xold + omega * sd[q * 51 + 50];
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Restriction r_c = P^T r_f and prolongation x_f += P e_c (FE interpolation,
 // Dirichlet rows of P (fine) and columns (coarse) zero).
 // 1D Q2 weights: coarse node C even: fine 2C + {-3:-1/8, -1:3/8, 0:1, 1:3/8, 3:-1/8};
@@ -541,22 +342,6 @@ void launch_rhs_transpose(const LevelDev& L, const double* lam, double* g, cudaS
   count_launches(1);
   dim3 blk(32, 8);
   k_rhs_transpose<<<grid2(L.nq, L.nq, blk), blk, 0, s>>>(L, lam, g);
-}
-
-cudaError_t vanka_f64_prepare() {
-  using T = VTile<VK_TX, VK_TY>;
-  return cudaFuncSetAttribute(k_vanka_f64<VK_TX, VK_TY, VK_NT>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(T::TOTAL * sizeof(double)));
-}
-
-void launch_vanka_f64(const LevelDev& L, const double* cd, const double* x, const double* b,
-                      double* xo, double omega, cudaStream_t s) {
-  count_launches(1);
-  using T = VTile<VK_TX, VK_TY>;
-  dim3 grid((L.np + VK_TX - 1) / VK_TX, (L.np + VK_TY - 1) / VK_TY);
-  k_vanka_f64<VK_TX, VK_TY, VK_NT><<<grid, VK_NT, T::TOTAL * sizeof(double), s>>>(L, cd, x, b, xo,
-                                                                                  omega);
 }
 
 void launch_restrict(const LevelDev& F, const LevelDev& C, const double* rf, double* rc,

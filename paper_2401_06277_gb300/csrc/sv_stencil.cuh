@@ -24,9 +24,9 @@
 #pragma once
 
 #ifdef __CUDACC__
-#define SV_HD __host__ __device__ __forceinline__
+#define SV_HD __host__ __device__ __forceinline__ constexpr
 #else
-#define SV_HD inline
+#define SV_HD inline constexpr
 #endif
 
 namespace sv {

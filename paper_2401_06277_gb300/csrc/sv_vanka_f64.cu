@@ -1,0 +1,299 @@
+// sv_vanka_f64.cu -- fused additive Vanka sweep in FP64 (Section 3.2,
+// Algorithm 3; the shared patch inverses of Section 6.3).
+//
+//   x_out = x + sum_i V_i^T W_i A_i^-1 V_i (b - A x),  W_i = omega diag(1/m_j)
+//
+// A CTA owns TX x TY vertices.  It loads x and b for the windows of the
+// patches of those vertices plus a one-vertex halo, computes the residual
+// there (every stencil coefficient is a compile-time constant: a thread
+// handles one 2x2 cell of Q2 nodes, whose four node parities are fixed),
+// solves every patch of the (TX+2) x (TY+2) region exactly with its class's
+// Schur factors, keeps the corrections in shared memory, and writes
+// x + W (sum of corrections) for the dofs it owns: Q2 nodes
+// (2i-1..2i) x (2j-1..2j) of both components and p(i, j) for each owned
+// vertex (i, j).  The sum over patches runs in a fixed order (no atomics), so
+// the result is deterministic.
+//
+// The kernel is bound by the FP64 pipe on GB300 (2 DFMA / clk / SM); the
+// tile shape trades halo recomputation against shared memory per CTA and is
+// chosen per level by a timing autotuner at hierarchy creation.
+#include <cuda_runtime.h>
+
+#include "sv_internal.h"
+#include "sv_stencil.cuh"
+
+namespace sv {
+namespace {
+
+__device__ __forceinline__ bool vfree(int I, int J, int nq) {
+  return I > 0 && J > 0 && I < nq - 1 && J < nq - 1;
+}
+
+template <int TX, int TY>
+struct VT {
+  static constexpr int XW = 2 * TX + 12, XH = 2 * TY + 12;  // x, Q2 nodes, origin 2 i0 - 6
+  static constexpr int PW = TX + 6, PH = TY + 6;            // x, vertices,  origin i0 - 3
+  static constexpr int CW = TX + 4, CH = TY + 4;            // residual cells, origin 2 i0 - 4
+  static constexpr int RW = 2 * CW, RH = 2 * CH;            // residual, Q2 nodes
+  static constexpr int QW = TX + 2, QH = TY + 2;            // patches, origin i0 - 1
+  static constexpr int NPATCH = QW * QH;
+  static constexpr int SX = 2 * XW * XH, SP = PW * PH, SR = 2 * RW * RH, SRP = NPATCH;
+  static constexpr int SD = NPATCH * 51;
+  static constexpr int TOTAL = SX + SP + SR + SRP + SD;
+};
+
+// sum of nu (K (x) M + M (x) K) x / (nu/90) over the stencil of a node with
+// parities (PI, PJ); xs points at the node in the x window.
+template <int PI, int PJ, int XW>
+__device__ __forceinline__ double lap(const double* xs) {
+  double s = 0.0;
+#pragma unroll
+  for (int dJ = -2; dJ <= 2; ++dJ) {
+#pragma unroll
+    for (int dI = -2; dI <= 2; ++dI) {
+      const double c = k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ);
+      if (c != 0.0) s = fma(c, xs[dJ * XW + dI], s);
+    }
+  }
+  return s;
+}
+
+// (B^T p) / (-h/18) for velocity component COMP at a node with parities
+// (PI, PJ) of the cell whose vertex is (a, b); pc points at p(a, b).
+template <int PI, int PJ, int COMP, int PW>
+__device__ __forceinline__ double btp(const double* pc) {
+  double g = 0.0;
+#pragma unroll
+  for (int dj = -1; dj <= 1; ++dj) {
+#pragma unroll
+    for (int di = -1; di <= 1; ++di) {
+      const double w = COMP == 0 ? ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj)
+                                 : ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj);
+      if (w != 0.0) g = fma(w, pc[dj * PW + di], g);
+    }
+  }
+  return g;
+}
+
+template <int PI, int PJ, int TX, int TY>
+__device__ __forceinline__ void res_node(double* sr, const double* x0, const double* pc, int I, int J,
+                                         const LevelDev& L, const double* __restrict__ x, double cl,
+                                         double cb) {
+  using T = VT<TX, TY>;
+  const int nq = L.nq;
+  if (I < 0 || J < 0 || I >= nq || J >= nq) return;  // outside: r stays 0
+  if (!vfree(I, J, nq)) {                            // Dirichlet row: r = b - x
+    const long long k = static_cast<long long>(J) * nq + I;
+    sr[0] -= x[k];
+    sr[T::RW * T::RH] -= x[L.nv + k];
+    return;
+  }
+  const double* x1 = x0 + T::XW * T::XH;
+  sr[0] -= cl * lap<PI, PJ, T::XW>(x0) + cb * btp<PI, PJ, 0, T::PW>(pc);
+  sr[T::RW * T::RH] -= cl * lap<PI, PJ, T::XW>(x1) + cb * btp<PI, PJ, 1, T::PW>(pc);
+}
+
+__device__ __forceinline__ double inv_mult(int m) {
+  switch (m) {
+    case 1: return 1.0;
+    case 2: return 0.5;
+    case 3: return 1.0 / 3.0;
+    case 4: return 0.25;
+    case 6: return 1.0 / 6.0;
+    default: return 1.0 / 9.0;
+  }
+}
+
+template <int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) k_vanka_f64(LevelDev L, const double* __restrict__ cd,
+                                                  const double* __restrict__ x,
+                                                  const double* __restrict__ b,
+                                                  double* __restrict__ xo, double omega) {
+  using T = VT<TX, TY>;
+  extern __shared__ double smem[];
+  double* sx = smem;
+  double* sp = sx + T::SX;
+  double* sr = sp + T::SP;
+  double* srp = sr + T::SR;
+  double* sd = srp + T::SRP;
+  const int n = L.n, nq = L.nq, np = L.np;
+  const long long nv = L.nv;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int tid = threadIdx.x;
+  const int XI0 = 2 * i0 - 6, XJ0 = 2 * j0 - 6;
+  const int RI0 = 2 * i0 - 4, RJ0 = 2 * j0 - 4;
+
+  // 1. x windows (Dirichlet / outside entries read as 0: their columns are
+  //    dropped), b on the residual windows (0 outside).
+  if (x != nullptr) {
+    for (int t = tid; t < T::SX; t += NT) {
+      const int c = t / (T::XW * T::XH);
+      const int rem = t - c * T::XW * T::XH;
+      const int jj = rem / T::XW, ii = rem - jj * T::XW;
+      const int I = XI0 + ii, J = XJ0 + jj;
+      sx[t] = vfree(I, J, nq) ? x[c * nv + static_cast<long long>(J) * nq + I] : 0.0;
+    }
+    for (int t = tid; t < T::SP; t += NT) {
+      const int jj = t / T::PW, ii = t - jj * T::PW;
+      const int i = i0 - 3 + ii, j = j0 - 3 + jj;
+      sp[t] = (i >= 0 && j >= 0 && i <= n && j <= n) ? x[2 * nv + static_cast<long long>(j) * np + i] : 0.0;
+    }
+  }
+  for (int t = tid; t < T::SR; t += NT) {
+    const int c = t / (T::RW * T::RH);
+    const int rem = t - c * T::RW * T::RH;
+    const int jj = rem / T::RW, ii = rem - jj * T::RW;
+    const int I = RI0 + ii, J = RJ0 + jj;
+    sr[t] = (I >= 0 && J >= 0 && I < nq && J < nq) ? b[c * nv + static_cast<long long>(J) * nq + I] : 0.0;
+  }
+  for (int t = tid; t < T::SRP; t += NT) {
+    const int jj = t / T::QW, ii = t - jj * T::QW;
+    const int i = i0 - 1 + ii, j = j0 - 1 + jj;
+    srp[t] = (i >= 0 && j >= 0 && i <= n && j <= n) ? b[2 * nv + static_cast<long long>(j) * np + i] : 0.0;
+  }
+  __syncthreads();
+
+  // 2. residual r = b - A x (skipped for a zero initial guess: r = b)
+  const double cl = L.nu / 90.0, cb = -L.h / 18.0;
+  if (x != nullptr) {
+    for (int t = tid; t < T::CW * T::CH; t += NT) {
+      const int cy = t / T::CW, cx = t - cy * T::CW;
+      const int I0 = RI0 + 2 * cx, J0 = RJ0 + 2 * cy;
+      const double* x0 = sx + (2 * cy + 2) * T::XW + (2 * cx + 2);
+      const double* pc = sp + (cy + 1) * T::PW + (cx + 1);  // vertex (I0/2, J0/2)
+      double* r0 = sr + (2 * cy) * T::RW + 2 * cx;
+      res_node<0, 0, TX, TY>(r0, x0, pc, I0, J0, L, x, cl, cb);
+      res_node<1, 0, TX, TY>(r0 + 1, x0 + 1, pc, I0 + 1, J0, L, x, cl, cb);
+      res_node<0, 1, TX, TY>(r0 + T::RW, x0 + T::XW, pc, I0, J0 + 1, L, x, cl, cb);
+      res_node<1, 1, TX, TY>(r0 + T::RW + 1, x0 + T::XW + 1, pc, I0 + 1, J0 + 1, L, x, cl, cb);
+    }
+    for (int t = tid; t < T::SRP; t += NT) {
+      const int jj = t / T::QW, ii = t - jj * T::QW;
+      const int i = i0 - 1 + ii, j = j0 - 1 + jj;
+      if (i < 0 || j < 0 || i > n || j > n) continue;
+      // window of vertex (i, j): Q2 (2i + dI) - XI0 = 2 ii + 4 + dI
+      const double* xs0 = sx + (2 * jj + 4) * T::XW + (2 * ii + 4);
+      const double* xs1 = xs0 + T::XW * T::XH;
+      double s = 0.0;
+#pragma unroll
+      for (int dJ = -2; dJ <= 2; ++dJ) {
+#pragma unroll
+        for (int dI = -2; dI <= 2; ++dI) {
+          const double wx = crow(dI) * nrow(dJ), wy = nrow(dI) * crow(dJ);
+          if (wx != 0.0) s = fma(wx, xs0[dJ * T::XW + dI], s);
+          if (wy != 0.0) s = fma(wy, xs1[dJ * T::XW + dI], s);
+        }
+      }
+      srp[t] -= cb * s;
+    }
+  }
+  __syncthreads();
+
+  // 3. exact patch solves, one thread per patch (Schur-factored class inverse)
+  for (int t = tid; t < T::NPATCH; t += NT) {
+    const int qj = t / T::QW, qi = t - qj * T::QW;
+    const int pi = i0 - 1 + qi, pj = j0 - 1 + qj;
+    if (pi < 0 || pj < 0 || pi > n || pj > n) continue;
+    const int cls = 5 * axis_class(pj, n) + axis_class(pi, n);
+    const double* C = cd + cls * CD_STRIDE;
+    double ru[50];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int wj = 0; wj < 5; ++wj)
+#pragma unroll
+        for (int wi = 0; wi < 5; ++wi)
+          ru[c * 25 + wj * 5 + wi] = sr[c * T::RW * T::RH + (2 * qj + wj) * T::RW + 2 * qi + wi];
+    double zr = 0.0;
+#pragma unroll
+    for (int k = 0; k < 50; ++k) zr = fma(__ldg(C + CD_Z + k), ru[k], zr);
+    const double dp = (zr - srp[t]) * __ldg(C + CD_SINV);
+    double* D = sd + t * 51;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+#pragma unroll 1
+      for (int o = 0; o < 25; ++o) {
+        const double* Kr = C + CD_KINV + o * 25;
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < 25; ++k) acc = fma(__ldg(Kr + k), ru[c * 25 + k], acc);
+        D[c * 25 + o] = fma(-__ldg(C + CD_Z + c * 25 + o), dp, acc);
+      }
+    }
+    D[50] = dp;
+  }
+  __syncthreads();
+
+  // 4. weighted additive update of the owned dofs, W = omega / m_j
+  constexpr int OW = 2 * TX, OH = 2 * TY;
+  for (int t = tid; t < 2 * OW * OH + TX * TY; t += NT) {
+    if (t < 2 * OW * OH) {
+      const int c = t / (OW * OH);
+      const int rem = t - c * OW * OH;
+      const int oj = rem / OW, oi = rem - oj * OW;
+      const int I = 2 * i0 - 1 + oi, J = 2 * j0 - 1 + oj;
+      if (I < 0 || J < 0 || I >= nq || J >= nq) continue;
+      const int pil = I < 2 ? 0 : (I - 1) / 2, pih = min(n, (I + 2) / 2);
+      const int pjl = J < 2 ? 0 : (J - 1) / 2, pjh = min(n, (J + 2) / 2);
+      double acc = 0.0;
+      for (int pj = pjl; pj <= pjh; ++pj) {
+        for (int pi = pil; pi <= pih; ++pi) {
+          const int q = (pj - (j0 - 1)) * T::QW + (pi - (i0 - 1));
+          acc += sd[q * 51 + c * 25 + (J - 2 * pj + 2) * 5 + (I - 2 * pi + 2)];
+        }
+      }
+      const double w = omega * inv_mult((pih - pil + 1) * (pjh - pjl + 1));
+      const long long k = c * nv + static_cast<long long>(J) * nq + I;
+      const double xold = x != nullptr ? x[k] : 0.0;
+      xo[k] = fma(w, acc, xold);
+    } else {
+      const int u = t - 2 * OW * OH;
+      const int vj = u / TX, vi = u - vj * TX;
+      const int i = i0 + vi, j = j0 + vj;
+      if (i > n || j > n) continue;
+      const int q = (vj + 1) * T::QW + (vi + 1);
+      const long long k = 2 * nv + static_cast<long long>(j) * np + i;
+      const double xold = x != nullptr ? x[k] : 0.0;
+      xo[k] = fma(omega, sd[q * 51 + 50], xold);
+    }
+  }
+}
+
+template <int TX, int TY, int NT>
+void launch_t(const LevelDev& L, const double* cd, const double* x, const double* b, double* xo,
+              double omega, cudaStream_t s) {
+  dim3 grid((L.np + TX - 1) / TX, (L.np + TY - 1) / TY);
+  k_vanka_f64<TX, TY, NT><<<grid, NT, VT<TX, TY>::TOTAL * sizeof(double), s>>>(L, cd, x, b, xo, omega);
+}
+
+template <int TX, int TY, int NT>
+cudaError_t prepare_t() {
+  return cudaFuncSetAttribute(k_vanka_f64<TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(VT<TX, TY>::TOTAL * sizeof(double)));
+}
+
+}  // namespace
+
+cudaError_t vanka_f64_prepare() {
+  cudaError_t e;
+  if ((e = prepare_t<8, 8, 128>()) != cudaSuccess) return e;
+  if ((e = prepare_t<16, 8, 192>()) != cudaSuccess) return e;
+  return prepare_t<16, 16, 352>();
+}
+
+void launch_vanka_f64(const LevelDev& L, const double* cd, const double* x, const double* b,
+                      double* xo, double omega, int cfg, cudaStream_t s) {
+  count_launches(1);
+  switch (cfg) {
+    case 1: launch_t<16, 8, 192>(L, cd, x, b, xo, omega, s); break;
+    case 2: launch_t<16, 16, 352>(L, cd, x, b, xo, omega, s); break;
+    default: launch_t<8, 8, 128>(L, cd, x, b, xo, omega, s); break;
+  }
+}
+
+const char* vanka_f64_cfg_name(int cfg) {
+  static const char* names[VANKA_F64_NCFG] = {"8x8", "16x8", "16x16"};
+  return (cfg >= 0 && cfg < VANKA_F64_NCFG) ? names[cfg] : "?";
+}
+
+}  // namespace sv

@@ -45,7 +45,7 @@ class stokes_stats(ctypes.Structure):
 class stokes_params(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("coarse_n", ctypes.c_int), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
-                ("rtol", ctypes.c_double), ("prec", ctypes.c_int)]
+                ("rtol", ctypes.c_double), ("prec", ctypes.c_int), ("tile", ctypes.c_int)]
 
 
 _lib = None
@@ -71,6 +71,7 @@ def _load():
         "stokes_hierarchy_destroy": (I, [P]),
         "stokes_level_info": (I, [P, IP, IP]),
         "stokes_level_n": (I, [P, I, IP]),
+        "stokes_level_tile": (I, [P, I, IP]),
         "stokes_assemble_rhs": (I, [P, VP, VP, VP]),
         "stokes_apply_operator": (I, [P, I, VP, VP]),
         "stokes_residual": (I, [P, I, VP, VP, VP]),
@@ -101,7 +102,8 @@ def _load():
 def exported_symbols() -> list[str]:
     """Names of the C entry points the binding declares (all must resolve in the library)."""
     return ["stokes_default_params", "stokes_hierarchy_create", "stokes_hierarchy_destroy",
-            "stokes_level_info", "stokes_level_n", "stokes_assemble_rhs", "stokes_apply_operator",
+            "stokes_level_info", "stokes_level_n", "stokes_level_tile", "stokes_assemble_rhs",
+            "stokes_apply_operator",
             "stokes_residual", "stokes_vanka_sweep", "stokes_restrict", "stokes_prolong_add",
             "stokes_coarse_solve", "stokes_initial_guess", "stokes_vcycle_apply", "stokes_fgmres_solve",
             "stokes_solve_adjoint", "stokes_rhs_transpose", "stokes_batched_solve",
@@ -165,6 +167,12 @@ def stokes_level_info(h) -> tuple[int, int]:
 def stokes_level_n(h, level: int) -> int:
     v = ctypes.c_int()
     _check(_load().stokes_level_n(h, int(level), ctypes.byref(v)))
+    return v.value
+
+
+def stokes_level_tile(h, level: int) -> int:
+    v = ctypes.c_int()
+    _check(_load().stokes_level_tile(h, int(level), ctypes.byref(v)))
     return v.value
 
 
@@ -307,11 +315,13 @@ class Hierarchy:
     maxit: int = 1000
     rtol: float = 1e-8
     prec: int = STOKES_FP64
+    tile: int = -1
 
     def __post_init__(self):
         p = default_params()
         p.nu1, p.nu2, p.omega, p.coarse_n = self.nu1, self.nu2, self.omega, self.coarse_n
         p.restart, p.maxit, p.rtol, p.prec = self.restart, self.maxit, self.rtol, self.prec
+        p.tile = self.tile
         self.handle = stokes_hierarchy_create(self.n, self.viscosity, p)
         self.levels, _ = stokes_level_info(self.handle)
         self.N = vec_len(self.n)

@@ -110,6 +110,22 @@ def test_vanka_sweep(pkg, n):
         assert rel(host(out), ref0) <= 1e-12
 
 
+@pytest.mark.parametrize("tile", [0, 1, 2])
+@pytest.mark.parametrize("n", [8, 32, 64])
+def test_vanka_sweep_tile_shapes(pkg, n, tile):
+    """Every tile shape of the fused FP64 sweep (8x8, 16x8, 16x16 vertices) gives the same sweep."""
+    from paper_2401_06277_gb300 import stokes
+    H = gpu_h(pkg, n, tile=tile)
+    assert stokes.stokes_level_tile(H.handle, H.levels - 1) == tile
+    Ho = oracle_h(n)
+    for l in (H.levels - 1, max(H.levels - 2, 0)):
+        lv = Ho.levels[l]
+        x, b = rvec(lv.mesh.n, 50 + l), rvec(lv.mesh.n, 60 + l)
+        assert rel(host(H.sweep(dev(x), dev(b), level=l)), O.vanka_sweep(lv, x, b, 0.7)) <= 1e-12
+    r = rvec(n, 70)
+    assert rel(host(H.vcycle(dev(r))), O.vcycle(Ho, r)) <= 1e-12
+
+
 def test_vanka_sweep_rejects_aliasing(pkg):
     from paper_2401_06277_gb300 import stokes
     H = gpu_h(pkg, 8)
