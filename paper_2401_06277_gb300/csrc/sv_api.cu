@@ -103,7 +103,7 @@ void timed_sweep(stokes_hierarchy* h, bool finest, sv::Level& L, const double* x
       cudaEventRecord(e0, h->stream);
     }
   }
-  sv::launch_vanka_f64(L.d, L.cd, x, b, xo, h->prm.omega, L.vk_cfg, h->stream);
+  sv::launch_vanka_f64(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, L.vk_cfg, h->stream);
   if (e1) cudaEventRecord(e1, h->stream);
 }
 
@@ -274,9 +274,9 @@ cudaError_t choose_tiles(stokes_hierarchy* h) {
     }
     float best = 1e30f;
     for (int c = 0; c < sv::VANKA_F64_NCFG; ++c) {
-      sv::launch_vanka_f64(L.d, L.cd, L.x0, L.b, L.x1, h->prm.omega, c, s);
+      sv::launch_vanka_f64(L.d, L.cd, h->fd, L.x0, L.b, L.x1, h->prm.omega, c, s);
       cudaEventRecord(e0, s);
-      for (int r = 0; r < 3; ++r) sv::launch_vanka_f64(L.d, L.cd, L.x0, L.b, L.x1, h->prm.omega, c, s);
+      for (int r = 0; r < 3; ++r) sv::launch_vanka_f64(L.d, L.cd, h->fd, L.x0, L.b, L.x1, h->prm.omega, c, s);
       cudaEventRecord(e1, s);
       if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
       float ms = 0.0f;
@@ -350,6 +350,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   h->n = n;
   h->stream = static_cast<cudaStream_t>(stream);
   h->m = prm.restart;
+  h->fd = sv::interior_fast_diag(viscosity);
   cudaError_t e = sv::vanka_f64_prepare();
   if (e != cudaSuccess) {
     delete h;
@@ -512,7 +513,7 @@ stokes_status stokes_vanka_sweep(stokes_hierarchy* h, int level, const double* x
   if (!b || !x_out) return fail(STOKES_ERR_ARG, "null vector");
   if (x_out == x || x_out == b) return fail(STOKES_ERR_ARG, "x_out must not alias x or b");
   sv::Level& L = h->lv[level];
-  sv::launch_vanka_f64(L.d, L.cd, x, b, x_out, h->prm.omega, L.vk_cfg, h->stream);
+  sv::launch_vanka_f64(L.d, L.cd, h->fd, x, b, x_out, h->prm.omega, L.vk_cfg, h->stream);
   return check_launch("vanka_sweep");
 }
 

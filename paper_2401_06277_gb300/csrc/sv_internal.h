@@ -25,6 +25,16 @@ constexpr int CD_STRIDE = 680;  // doubles per class
 constexpr int NCLASS = 25;
 constexpr int INTERIOR_CLASS = 12;  // 5 * 2 + 2
 
+// Fast-diagonalisation factors of the interior patch block (see sv_setup.cu):
+// se[m*3+k]: symmetric eigenvector k at reduced index m (entries 0/4, 1/3, 2);
+// so[m*2+k]: antisymmetric eigenvector k at reduced index m (entries 0/-4, 1/-3);
+// dinv[a*5+b] = (90/nu) / (l_a + l_b), eigenvalues ordered sym 0..2, anti 0..1.
+struct FastDiag {
+  double se[9];
+  double so[4];
+  double dinv[25];
+};
+
 // Device-side description of one level (passed by value to kernels).
 struct LevelDev {
   int n;       // elements per axis
@@ -57,6 +67,7 @@ struct stokes_hierarchy {
   int n = 0;
   cudaStream_t stream = nullptr;
   std::vector<sv::Level> lv;     // lv[0] = coarsest
+  sv::FastDiag fd;               // interior patch factors (level independent)
   double* coarse_G = nullptr;    // N0 x N0 dense inverse of the bordered coarse system
   int N0 = 0;
   // FGMRES workspace
@@ -92,6 +103,8 @@ void build_class_data(int n, double nu, std::vector<double>& cd, std::vector<dou
 void dense_operator(int n, double nu, std::vector<double>& A);
 // G = leading N0 x N0 block of [[A, e], [e^T, 0]]^-1, e = (0, M_p 1).
 bool coarse_inverse(int n, double nu, std::vector<double>& G);
+// Interior-class fast-diagonalisation factors (level independent for constant nu).
+FastDiag interior_fast_diag(double nu);
 // In-place Gauss-Jordan inverse with partial pivoting; false if singular.
 bool invert_dense(std::vector<double>& a, int m);
 
@@ -102,8 +115,8 @@ void launch_rhs(const LevelDev& L, const double* f, const double* ud, double* b,
 void launch_rhs_transpose(const LevelDev& L, const double* lam, double* g, cudaStream_t s);
 // FP64 Vanka sweep (sv_vanka_f64.cu); cfg selects the tile shape (8x8, 16x8, 16x16 vertices)
 constexpr int VANKA_F64_NCFG = 3;
-void launch_vanka_f64(const LevelDev& L, const double* cd, const double* x, const double* b,
-                      double* xo, double omega, int cfg, cudaStream_t s);
+void launch_vanka_f64(const LevelDev& L, const double* cd, const FastDiag& fd, const double* x,
+                      const double* b, double* xo, double omega, int cfg, cudaStream_t s);
 const char* vanka_f64_cfg_name(int cfg);
 void launch_restrict(const LevelDev& F, const LevelDev& C, const double* rf, double* rc,
                      cudaStream_t s);

@@ -18,56 +18,101 @@ __device__ __forceinline__ bool is_free(int I, int J, int nq) {
 
 // ---------------------------------------------------------------------------
 // Operator: y = A x (residual = 0) or y = b - A x (residual = 1).
-// One thread per Q2 node (both velocity components) and one per vertex.
+// One thread per vertex (a, b): the four Q2 nodes (2a..2a+1) x (2b..2b+1) of
+// both velocity components and the pressure row of (a, b).  Away from the
+// boundary (2 <= a, b <= n-2) every tap is in the free interior and the
+// stencil coefficients are compile-time constants (node parities are fixed
+// per node); near the boundary a masked generic path drops Dirichlet columns.
 // ---------------------------------------------------------------------------
-__global__ void k_apply_vel(LevelDev L, const double* __restrict__ x, const double* __restrict__ b,
-                            double* __restrict__ y, int residual) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+template <int PI, int PJ>
+__device__ __forceinline__ double lap_g(const double* __restrict__ xs, int ld) {
+  double s = 0.0;
+#pragma unroll
+  for (int dJ = -2; dJ <= 2; ++dJ) {
+#pragma unroll
+    for (int dI = -2; dI <= 2; ++dI) {
+      const double c = k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ);
+      if (c != 0.0) s = fma(c, xs[dJ * ld + dI], s);
+    }
+  }
+  return s;
+}
+
+template <int PI, int PJ, int COMP>
+__device__ __forceinline__ double btp_g(const double* __restrict__ pc, int ld) {
+  double g = 0.0;
+#pragma unroll
+  for (int dj = -1; dj <= 1; ++dj) {
+#pragma unroll
+    for (int di = -1; di <= 1; ++di) {
+      const double w = COMP == 0 ? ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj)
+                                 : ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj);
+      if (w != 0.0) g = fma(w, pc[dj * ld + di], g);
+    }
+  }
+  return g;
+}
+
+// generic masked evaluation of (A x) at velocity node (I, J), both components
+__device__ __forceinline__ void apply_vel_node(const LevelDev& L, const double* __restrict__ x, int I,
+                                               int J, double& ax, double& ay) {
   const int nq = L.nq, np = L.np, n = L.n;
+  const long long nv = L.nv;
+  const long long k = static_cast<long long>(J) * nq + I;
+  if (!is_free(I, J, nq)) {
+    ax = x[k];
+    ay = x[nv + k];
+    return;
+  }
+  double sx = 0.0, sy = 0.0;
+  for (int dJ = -2; dJ <= 2; ++dJ) {
+    const int J2 = J + dJ;
+    if (J2 <= 0 || J2 >= nq - 1) continue;
+    const double mJ = m1(J, dJ), kJ = k1(J, dJ);
+    for (int dI = -2; dI <= 2; ++dI) {
+      const int I2 = I + dI;
+      if (I2 <= 0 || I2 >= nq - 1) continue;
+      const double c = k1(I, dI) * mJ + m1(I, dI) * kJ;
+      if (c == 0.0) continue;
+      const long long kk = static_cast<long long>(J2) * nq + I2;
+      sx = fma(c, x[kk], sx);
+      sy = fma(c, x[nv + kk], sy);
+    }
+  }
+  const double* p = x + 2 * nv;
+  double gx = 0.0, gy = 0.0;
+  for (int j = J / 2 - 1; j <= J / 2 + 1; ++j) {
+    if (j < 0 || j > n) continue;
+    for (int i = I / 2 - 1; i <= I / 2 + 1; ++i) {
+      if (i < 0 || i > n) continue;
+      const double wx = ccol(I, i) * ncol(J, j), wy = ncol(I, i) * ccol(J, j);
+      const double pv = p[static_cast<long long>(j) * np + i];
+      if (wx != 0.0) gx = fma(wx, pv, gx);
+      if (wy != 0.0) gy = fma(wy, pv, gy);
+    }
+  }
+  const double cl = L.nu / 90.0, cb = -L.h / 18.0;
+  ax = cl * sx + cb * gx;
+  ay = cl * sy + cb * gy;
+}
+
+template <int PI, int PJ>
+__device__ __forceinline__ void apply_node(const LevelDev& L, const double* __restrict__ x,
+                                           const double* __restrict__ b, double* __restrict__ y,
+                                           int residual, bool fast, int a, int bb) {
+  const int I = 2 * a + PI, J = 2 * bb + PJ;
+  const int nq = L.nq;
   if (I >= nq || J >= nq) return;
   const long long nv = L.nv;
   const long long k = static_cast<long long>(J) * nq + I;
   double ax, ay;
-  if (!is_free(I, J, nq)) {
-    ax = x[k];
-    ay = x[nv + k];
-  } else {
-    double sx = 0.0, sy = 0.0;
-#pragma unroll
-    for (int dJ = -2; dJ <= 2; ++dJ) {
-      const int J2 = J + dJ;
-      const double mJ = m1(J, dJ), kJ = k1(J, dJ);
-      if (J2 <= 0 || J2 >= nq - 1 || (mJ == 0.0 && kJ == 0.0)) continue;
-#pragma unroll
-      for (int dI = -2; dI <= 2; ++dI) {
-        const int I2 = I + dI;
-        if (I2 <= 0 || I2 >= nq - 1) continue;
-        const double c = k1(I, dI) * mJ + m1(I, dI) * kJ;
-        if (c == 0.0) continue;
-        const long long kk = static_cast<long long>(J2) * nq + I2;
-        sx = fma(c, x[kk], sx);
-        sy = fma(c, x[nv + kk], sy);
-      }
-    }
-    const double* p = x + 2 * nv;
-    double gx = 0.0, gy = 0.0;
-#pragma unroll
-    for (int dj = -1; dj <= 1; ++dj) {
-      const int j = J / 2 + dj;
-      if (j < 0 || j > n) continue;
-#pragma unroll
-      for (int di = -1; di <= 1; ++di) {
-        const int i = I / 2 + di;
-        if (i < 0 || i > n) continue;
-        const double pv = p[static_cast<long long>(j) * np + i];
-        gx = fma(ccol(I, i) * ncol(J, j), pv, gx);
-        gy = fma(ncol(I, i) * ccol(J, j), pv, gy);
-      }
-    }
+  if (fast) {
     const double cl = L.nu / 90.0, cb = -L.h / 18.0;
-    ax = cl * sx + cb * gx;
-    ay = cl * sy + cb * gy;
+    const double* pc = x + 2 * nv + static_cast<long long>(bb) * L.np + a;
+    ax = cl * lap_g<PI, PJ>(x + k, nq) + cb * btp_g<PI, PJ, 0>(pc, L.np);
+    ay = cl * lap_g<PI, PJ>(x + nv + k, nq) + cb * btp_g<PI, PJ, 1>(pc, L.np);
+  } else {
+    apply_vel_node(L, x, I, J, ax, ay);
   }
   if (residual) {
     y[k] = b[k] - ax;
@@ -78,31 +123,50 @@ __global__ void k_apply_vel(LevelDev L, const double* __restrict__ x, const doub
   }
 }
 
-__global__ void k_apply_p(LevelDev L, const double* __restrict__ x, const double* __restrict__ b,
-                          double* __restrict__ y, int residual) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int nq = L.nq, np = L.np;
-  if (i >= np || j >= np) return;
+__global__ void k_apply(LevelDev L, const double* __restrict__ x, const double* __restrict__ b,
+                        double* __restrict__ y, int residual) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int bb = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = L.n, nq = L.nq, np = L.np;
+  if (a > n || bb > n) return;
+  const bool fast = a >= 2 && a <= n - 2 && bb >= 2 && bb <= n - 2;
+  apply_node<0, 0>(L, x, b, y, residual, fast, a, bb);
+  apply_node<1, 0>(L, x, b, y, residual, fast, a, bb);
+  apply_node<0, 1>(L, x, b, y, residual, fast, a, bb);
+  apply_node<1, 1>(L, x, b, y, residual, fast, a, bb);
+  // pressure row of vertex (a, bb): (B u)
   const long long nv = L.nv;
   double s = 0.0;
+  if (fast) {
+    const double* u0 = x + static_cast<long long>(2 * bb) * nq + 2 * a;
 #pragma unroll
-  for (int dJ = -2; dJ <= 2; ++dJ) {
-    const int J = 2 * j + dJ;
-    if (J <= 0 || J >= nq - 1) continue;
+    for (int dJ = -2; dJ <= 2; ++dJ) {
 #pragma unroll
-    for (int dI = -2; dI <= 2; ++dI) {
-      const int I = 2 * i + dI;
-      if (I <= 0 || I >= nq - 1) continue;
-      const long long kk = static_cast<long long>(J) * nq + I;
-      const double cx = crow(dI) * nrow(dJ), cy = nrow(dI) * crow(dJ);
-      if (cx != 0.0) s = fma(cx, x[kk], s);
-      if (cy != 0.0) s = fma(cy, x[nv + kk], s);
+      for (int dI = -2; dI <= 2; ++dI) {
+        const double cx = crow(dI) * nrow(dJ), cy = nrow(dI) * crow(dJ);
+        if (cx != 0.0) s = fma(cx, u0[dJ * nq + dI], s);
+        if (cy != 0.0) s = fma(cy, u0[nv + dJ * nq + dI], s);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int dJ = -2; dJ <= 2; ++dJ) {
+      const int J = 2 * bb + dJ;
+      if (J <= 0 || J >= nq - 1) continue;
+#pragma unroll
+      for (int dI = -2; dI <= 2; ++dI) {
+        const int I = 2 * a + dI;
+        if (I <= 0 || I >= nq - 1) continue;
+        const long long kk = static_cast<long long>(J) * nq + I;
+        const double cx = crow(dI) * nrow(dJ), cy = nrow(dI) * crow(dJ);
+        if (cx != 0.0) s = fma(cx, x[kk], s);
+        if (cy != 0.0) s = fma(cy, x[nv + kk], s);
+      }
     }
   }
-  const double a = -L.h / 18.0 * s;
-  const long long k = 2 * nv + static_cast<long long>(j) * np + i;
-  y[k] = residual ? b[k] - a : a;
+  const double ap = -L.h / 18.0 * s;
+  const long long k = 2 * nv + static_cast<long long>(bb) * np + a;
+  y[k] = residual ? b[k] - ap : ap;
 }
 
 // ---------------------------------------------------------------------------
@@ -325,10 +389,9 @@ dim3 grid2(int nx, int ny, dim3 blk) {
 
 void launch_apply(const LevelDev& L, const double* x, const double* b, double* y, int residual,
                   cudaStream_t s) {
-  count_launches(2);
+  count_launches(1);
   dim3 blk(32, 8);
-  k_apply_vel<<<grid2(L.nq, L.nq, blk), blk, 0, s>>>(L, x, b, y, residual);
-  k_apply_p<<<grid2(L.np, L.np, blk), blk, 0, s>>>(L, x, b, y, residual);
+  k_apply<<<grid2(L.np, L.np, blk), blk, 0, s>>>(L, x, b, y, residual);
 }
 
 void launch_rhs(const LevelDev& L, const double* f, const double* ud, double* b, cudaStream_t s) {

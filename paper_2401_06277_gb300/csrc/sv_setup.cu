@@ -138,6 +138,135 @@ void build_class_data(int n, double nu, std::vector<double>& cd, std::vector<dou
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fast diagonalisation of the interior patch block.  On an interior patch the
+// velocity block is K = (nu/90) (k (x) m + m (x) k), with k and m the 5 x 5
+// restrictions of the 1D integer stiffness and mass rows to the window
+// (nodes 2i-2 .. 2i+2).  With the generalised eigenvectors k S = m S diag(l),
+// S^T m S = I:  K^-1 = (90/nu) (S (x) S) diag(1/(l_a + l_b)) (S (x) S)^T.
+// The window is symmetric under reflection, so the eigenvectors split into
+// three symmetric and two antisymmetric ones, computed in the reduced bases
+// {e0+e4, e1+e3, e2} and {e0-e4, e1-e3}.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Cyclic Jacobi eigenvalue iteration for a small symmetric matrix a (m x m,
+// row-major, destroyed); eigenvalues in w, eigenvectors in the columns of v.
+void jacobi_eig(double* a, int m, double* w, double* v) {
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) v[i * m + j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) off += a[p * m + q] * a[p * m + q];
+    if (off < 1e-34) break;
+    for (int p = 0; p < m; ++p) {
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = a[p * m + q];
+        if (apq == 0.0) continue;
+        const double theta = (a[q * m + q] - a[p * m + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < m; ++k) {  // columns p, q
+          const double akp = a[k * m + p], akq = a[k * m + q];
+          a[k * m + p] = c * akp - s * akq;
+          a[k * m + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {  // rows p, q
+          const double apk = a[p * m + k], aqk = a[q * m + k];
+          a[p * m + k] = c * apk - s * aqk;
+          a[q * m + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double vkp = v[k * m + p], vkq = v[k * m + q];
+          v[k * m + p] = c * vkp - s * vkq;
+          v[k * m + q] = s * vkp + c * vkq;
+        }
+      }
+    }
+  }
+  for (int i = 0; i < m; ++i) w[i] = a[i * m + i];
+}
+
+// Generalised symmetric eigenproblem A q = l B q, q^T B q = 1 (m <= 3): B = L L^T,
+// C = L^-1 A L^-T, C = Q diag(l) Q^T, q = L^-T Q.  Columns of out are the q.
+void gen_eig(const double* A, const double* B, int m, double* lam, double* out) {
+  double L[9] = {0}, Li[9] = {0}, C[9], T[9], Q[9];
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = B[i * m + j];
+      for (int k = 0; k < j; ++k) s -= L[i * m + k] * L[j * m + k];
+      L[i * m + j] = (i == j) ? std::sqrt(s) : s / L[j * m + j];
+    }
+  }
+  for (int c = 0; c < m; ++c) {  // Li = L^-1 by forward substitution
+    for (int i = 0; i < m; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= L[i * m + k] * Li[k * m + c];
+      Li[i * m + c] = s / L[i * m + i];
+    }
+  }
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s += Li[i * m + k] * A[k * m + j];
+      T[i * m + j] = s;
+    }
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s += T[i * m + k] * Li[j * m + k];
+      C[i * m + j] = s;
+    }
+  jacobi_eig(C, m, lam, Q);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < m; ++k) s += Li[k * m + i] * Q[k * m + j];
+      out[i * m + j] = s;
+    }
+}
+
+}  // namespace
+
+FastDiag interior_fast_diag(double nu) {
+  // window offsets -2..2 around an even (vertex) node; k1/m1 rows by parity
+  double kw[25], mw[25];
+  for (int r = 0; r < 5; ++r)
+    for (int c = 0; c < 5; ++c) {
+      kw[r * 5 + c] = k1(r & 1, c - r);   // node at offset r-2 has the parity of r
+      mw[r * 5 + c] = m1(r & 1, c - r);
+    }
+  // reduced bases: symmetric {e0+e4, e1+e3, e2}, antisymmetric {e0-e4, e1-e3}
+  const double Es[3][5] = {{1, 0, 0, 0, 1}, {0, 1, 0, 1, 0}, {0, 0, 1, 0, 0}};
+  const double Eo[2][5] = {{1, 0, 0, 0, -1}, {0, 1, 0, -1, 0}};
+  auto project = [&](const double (*E)[5], int m, const double* M, double* out) {
+    for (int a = 0; a < m; ++a)
+      for (int b = 0; b < m; ++b) {
+        double s = 0.0;
+        for (int r = 0; r < 5; ++r)
+          for (int c = 0; c < 5; ++c) s += E[a][r] * M[r * 5 + c] * E[b][c];
+        out[a * m + b] = s;
+      }
+  };
+  double ks[9], ms[9], ko[4], mo[4], ls[3], lo[2], qs[9], qo[4];
+  project(Es, 3, kw, ks);
+  project(Es, 3, mw, ms);
+  project(Eo, 2, kw, ko);
+  project(Eo, 2, mw, mo);
+  gen_eig(ks, ms, 3, ls, qs);
+  gen_eig(ko, mo, 2, lo, qo);
+  FastDiag f;
+  for (int mrow = 0; mrow < 3; ++mrow)
+    for (int k = 0; k < 3; ++k) f.se[mrow * 3 + k] = qs[mrow * 3 + k];
+  for (int mrow = 0; mrow < 2; ++mrow)
+    for (int k = 0; k < 2; ++k) f.so[mrow * 2 + k] = qo[mrow * 2 + k];
+  double lam[5] = {ls[0], ls[1], ls[2], lo[0], lo[1]};
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b) f.dinv[a * 5 + b] = (90.0 / nu) / (lam[a] + lam[b]);
+  return f;
+}
+
 void dense_operator(int n, double nu, std::vector<double>& A) {
   const int nq = 2 * n + 1, np = n + 1;
   const long long nv = static_cast<long long>(nq) * nq;

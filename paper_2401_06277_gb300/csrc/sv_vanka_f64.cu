@@ -8,7 +8,9 @@
 // there (every stencil coefficient is a compile-time constant: a thread
 // handles one 2x2 cell of Q2 nodes, whose four node parities are fixed),
 // solves every patch of the (TX+2) x (TY+2) region exactly with its class's
-// Schur factors, keeps the corrections in shared memory, and writes
+// Schur factors (interior patches apply K^-1 by fast diagonalisation of its
+// tensor-product structure, boundary classes their dense K^-1), keeps the
+// corrections in shared memory, and writes
 // x + W (sum of corrections) for the dofs it owns: Q2 nodes
 // (2i-1..2i) x (2j-1..2j) of both components and p(i, j) for each owned
 // vertex (i, j).  The sum over patches runs in a fixed order (no atomics), so
@@ -93,6 +95,58 @@ __device__ __forceinline__ void res_node(double* sr, const double* x0, const dou
   sr[T::RW * T::RH] -= cl * lap<PI, PJ, T::XW>(x1) + cb * btp<PI, PJ, 1, T::PW>(pc);
 }
 
+// Forward transform of one 5-vector into the generalised eigenbasis S^T v
+// (three symmetric, two antisymmetric eigenvectors; 4 add/sub + 13 FMA/MUL).
+__device__ __forceinline__ void fd_fwd(const FastDiag& f, double v0, double v1, double v2, double v3,
+                                       double v4, double* c) {
+  const double e0 = v0 + v4, e1 = v1 + v3, o0 = v0 - v4, o1 = v1 - v3;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) c[k] = fma(f.se[k], e0, fma(f.se[3 + k], e1, f.se[6 + k] * v2));
+#pragma unroll
+  for (int k = 0; k < 2; ++k) c[3 + k] = fma(f.so[k], o0, f.so[2 + k] * o1);
+}
+
+// Inverse transform S c of five eigen-coefficients (13 FMA/MUL + 4 add/sub).
+__device__ __forceinline__ void fd_inv(const FastDiag& f, const double* c, double* v) {
+  double E[3], Od[2];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) E[m] = fma(f.se[m * 3], c[0], fma(f.se[m * 3 + 1], c[1], f.se[m * 3 + 2] * c[2]));
+#pragma unroll
+  for (int m = 0; m < 2; ++m) Od[m] = fma(f.so[m * 2], c[3], f.so[m * 2 + 1] * c[4]);
+  v[0] = E[0] + Od[0];
+  v[4] = E[0] - Od[0];
+  v[1] = E[1] + Od[1];
+  v[3] = E[1] - Od[1];
+  v[2] = E[2];
+}
+
+// y = K^-1 r on an interior patch window (5 x 5, row-major [wj][wi]) by fast
+// diagonalisation: transform both axes, divide by l_a + l_b, transform back.
+__device__ __forceinline__ void fd_solve(const FastDiag& f, const double* r, double* y) {
+  double T[25], U[25];
+#pragma unroll
+  for (int wj = 0; wj < 5; ++wj)
+    fd_fwd(f, r[wj * 5], r[wj * 5 + 1], r[wj * 5 + 2], r[wj * 5 + 3], r[wj * 5 + 4], T + wj * 5);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    double c[5];
+    fd_fwd(f, T[k], T[5 + k], T[10 + k], T[15 + k], T[20 + k], c);
+#pragma unroll
+    for (int k2 = 0; k2 < 5; ++k2) U[k2 * 5 + k] = c[k2] * f.dinv[k2 * 5 + k];
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    double c[5], v[5];
+#pragma unroll
+    for (int k2 = 0; k2 < 5; ++k2) c[k2] = U[k2 * 5 + k];
+    fd_inv(f, c, v);
+#pragma unroll
+    for (int wj = 0; wj < 5; ++wj) T[wj * 5 + k] = v[wj];
+  }
+#pragma unroll
+  for (int wj = 0; wj < 5; ++wj) fd_inv(f, T + wj * 5, y + wj * 5);
+}
+
 __device__ __forceinline__ double inv_mult(int m) {
   switch (m) {
     case 1: return 1.0;
@@ -106,7 +160,7 @@ __device__ __forceinline__ double inv_mult(int m) {
 
 template <int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT) k_vanka_f64(LevelDev L, const double* __restrict__ cd,
-                                                  const double* __restrict__ x,
+                                                  const FastDiag fdg, const double* __restrict__ x,
                                                   const double* __restrict__ b,
                                                   double* __restrict__ xo, double omega) {
   using T = VT<TX, TY>;
@@ -209,15 +263,26 @@ __global__ void __launch_bounds__(NT) k_vanka_f64(LevelDev L, const double* __re
     for (int k = 0; k < 50; ++k) zr = fma(__ldg(C + CD_Z + k), ru[k], zr);
     const double dp = (zr - srp[t]) * __ldg(C + CD_SINV);
     double* D = sd + t * 51;
+    if (cls == INTERIOR_CLASS) {
+      // interior patch: K^-1 r_u by fast diagonalisation (exact up to rounding)
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
+      for (int c = 0; c < 2; ++c) {
+        double y[25];
+        fd_solve(fdg, ru + c * 25, y);
+#pragma unroll
+        for (int o = 0; o < 25; ++o) D[c * 25 + o] = fma(-__ldg(C + CD_Z + c * 25 + o), dp, y[o]);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
 #pragma unroll 1
-      for (int o = 0; o < 25; ++o) {
-        const double* Kr = C + CD_KINV + o * 25;
-        double acc = 0.0;
+        for (int o = 0; o < 25; ++o) {
+          const double* Kr = C + CD_KINV + o * 25;
+          double acc = 0.0;
 #pragma unroll
-        for (int k = 0; k < 25; ++k) acc = fma(__ldg(Kr + k), ru[c * 25 + k], acc);
-        D[c * 25 + o] = fma(-__ldg(C + CD_Z + c * 25 + o), dp, acc);
+          for (int k = 0; k < 25; ++k) acc = fma(__ldg(Kr + k), ru[c * 25 + k], acc);
+          D[c * 25 + o] = fma(-__ldg(C + CD_Z + c * 25 + o), dp, acc);
+        }
       }
     }
     D[50] = dp;
@@ -260,10 +325,11 @@ __global__ void __launch_bounds__(NT) k_vanka_f64(LevelDev L, const double* __re
 }
 
 template <int TX, int TY, int NT>
-void launch_t(const LevelDev& L, const double* cd, const double* x, const double* b, double* xo,
-              double omega, cudaStream_t s) {
+void launch_t(const LevelDev& L, const double* cd, const FastDiag& fd, const double* x, const double* b,
+              double* xo, double omega, cudaStream_t s) {
   dim3 grid((L.np + TX - 1) / TX, (L.np + TY - 1) / TY);
-  k_vanka_f64<TX, TY, NT><<<grid, NT, VT<TX, TY>::TOTAL * sizeof(double), s>>>(L, cd, x, b, xo, omega);
+  k_vanka_f64<TX, TY, NT><<<grid, NT, VT<TX, TY>::TOTAL * sizeof(double), s>>>(L, cd, fd, x, b, xo,
+                                                                               omega);
 }
 
 template <int TX, int TY, int NT>
@@ -281,13 +347,13 @@ cudaError_t vanka_f64_prepare() {
   return prepare_t<16, 16, 352>();
 }
 
-void launch_vanka_f64(const LevelDev& L, const double* cd, const double* x, const double* b,
-                      double* xo, double omega, int cfg, cudaStream_t s) {
+void launch_vanka_f64(const LevelDev& L, const double* cd, const FastDiag& fd, const double* x,
+                      const double* b, double* xo, double omega, int cfg, cudaStream_t s) {
   count_launches(1);
   switch (cfg) {
-    case 1: launch_t<16, 8, 192>(L, cd, x, b, xo, omega, s); break;
-    case 2: launch_t<16, 16, 352>(L, cd, x, b, xo, omega, s); break;
-    default: launch_t<8, 8, 128>(L, cd, x, b, xo, omega, s); break;
+    case 1: launch_t<16, 8, 192>(L, cd, fd, x, b, xo, omega, s); break;
+    case 2: launch_t<16, 16, 352>(L, cd, fd, x, b, xo, omega, s); break;
+    default: launch_t<8, 8, 128>(L, cd, fd, x, b, xo, omega, s); break;
   }
 }
 
