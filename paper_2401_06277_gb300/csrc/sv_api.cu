@@ -60,6 +60,12 @@ void free_all(stokes_hierarchy* h) {
     cudaFree(L.r);
     cudaFree(L.e);
     cudaFree(L.cd);
+    cudaFree(L.xf0);
+    cudaFree(L.xf1);
+    cudaFree(L.bf);
+    cudaFree(L.rf);
+    cudaFree(L.ef);
+    cudaFree(L.cdf);
   }
   h->lv.clear();
   cudaFree(h->coarse_G);
@@ -83,61 +89,124 @@ stokes_status check_level(const stokes_hierarchy* h, int level, int min_level = 
   return STOKES_OK;
 }
 
-// Launch one FP64 sweep; on the finest level, bracket it with a CUDA-event
-// pair when timing is on (events are pooled and summed in stokes_stats_read).
-void timed_sweep(stokes_hierarchy* h, bool finest, sv::Level& L, const double* x, const double* b,
-                 double* xo) {
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (h->timing && finest) {
-    if (h->ev_used + 2 > h->ev_pool.size()) {
-      for (int k = 0; k < 64; ++k) {
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) break;
-        h->ev_pool.push_back(e);
-      }
-    }
-    if (h->ev_used + 2 <= h->ev_pool.size()) {
-      e0 = h->ev_pool[h->ev_used];
-      e1 = h->ev_pool[h->ev_used + 1];
-      h->ev_used += 2;
-      cudaEventRecord(e0, h->stream);
+// Launch one sweep; on the finest level, bracket it with a CUDA-event pair
+// when timing is on (events are pooled and summed in stokes_stats_read).
+template <typename R>
+void timed_sweep(stokes_hierarchy* h, bool finest, sv::Level& L, const R* x, const R* b, R* xo);
+
+cudaEvent_t* timing_pair(stokes_hierarchy* h, bool finest) {
+  if (!(h->timing && finest)) return nullptr;
+  if (h->ev_used + 2 > h->ev_pool.size()) {
+    for (int k = 0; k < 64; ++k) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) break;
+      h->ev_pool.push_back(e);
     }
   }
-  sv::launch_vanka_f64(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, L.vk_cfg, h->stream);
-  if (e1) cudaEventRecord(e1, h->stream);
+  if (h->ev_used + 2 > h->ev_pool.size()) return nullptr;
+  cudaEvent_t* p = &h->ev_pool[h->ev_used];
+  h->ev_used += 2;
+  return p;
 }
 
-// ---- V-cycle (Algorithm 1), FP64 ----
-void vcycle_f64(stokes_hierarchy* h, int l, const double* b, double* out) {
+template <>
+void timed_sweep<double>(stokes_hierarchy* h, bool finest, sv::Level& L, const double* x, const double* b,
+                         double* xo) {
+  cudaEvent_t* ev = timing_pair(h, finest);
+  if (ev) cudaEventRecord(ev[0], h->stream);
+  sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, L.vk_cfg, h->stream);
+  if (ev) cudaEventRecord(ev[1], h->stream);
+}
+
+template <>
+void timed_sweep<float>(stokes_hierarchy* h, bool finest, sv::Level& L, const float* x, const float* b,
+                        float* xo) {
+  cudaEvent_t* ev = timing_pair(h, finest);
+  if (ev) cudaEventRecord(ev[0], h->stream);
+  sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, L.vk_cfg_f, h->stream);
+  if (ev) cudaEventRecord(ev[1], h->stream);
+}
+
+// ---- V-cycle (Algorithm 1) ----
+// Level buffers of the precision R: the FP64 set (x0, x1, b, r, e) or the
+// FP32 set of the mixed-precision preconditioner (xf0, xf1, bf, rf, ef).
+template <typename R>
+struct Buf;
+template <>
+struct Buf<double> {
+  static double* x0(sv::Level& L) { return L.x0; }
+  static double* x1(sv::Level& L) { return L.x1; }
+  static double* b(sv::Level& L) { return L.b; }
+  static double* r(sv::Level& L) { return L.r; }
+  static double* e(sv::Level& L) { return L.e; }
+};
+template <>
+struct Buf<float> {
+  static float* x0(sv::Level& L) { return L.xf0; }
+  static float* x1(sv::Level& L) { return L.xf1; }
+  static float* b(sv::Level& L) { return L.bf; }
+  static float* r(sv::Level& L) { return L.rf; }
+  static float* e(sv::Level& L) { return L.ef; }
+};
+
+// Exact coarse solve in FP64 (Algorithm 1, level 0), for either precision.
+void coarse_apply(stokes_hierarchy* h, const double* b, double* out) {
+  sv::launch_coarse(h->coarse_G, h->N0, b, out, h->stream);
+}
+void coarse_apply(stokes_hierarchy* h, const float* b, float* out) {
+  sv::Level& C = h->lv[0];
+  sv::launch_convert<float, double>(b, C.b, C.d.N, h->stream);
+  sv::launch_coarse(h->coarse_G, h->N0, C.b, C.e, h->stream);
+  sv::launch_convert<double, float>(C.e, out, C.d.N, h->stream);
+}
+
+template <typename R>
+void vcycle(stokes_hierarchy* h, int l, const R* b, R* out) {
   cudaStream_t s = h->stream;
   sv::Level& L = h->lv[l];
   if (l == 0) {
-    sv::launch_coarse(h->coarse_G, h->N0, b, out, s);
+    coarse_apply(h, b, out);
     return;
   }
-  const double w = h->prm.omega;
   const bool finest = (l == static_cast<int>(h->lv.size()) - 1);
-  double* cur = nullptr;  // nullptr = zero initial guess
+  R* X0 = Buf<R>::x0(L);
+  R* X1 = Buf<R>::x1(L);
+  R* cur = nullptr;  // nullptr = zero initial guess
   for (int it = 0; it < h->prm.nu1; ++it) {
-    double* dst = (cur == L.x0) ? L.x1 : L.x0;
-    timed_sweep(h, finest, L, cur, b, dst);
+    R* dst = (cur == X0) ? X1 : X0;
+    timed_sweep<R>(h, finest, L, cur, b, dst);
     cur = dst;
   }
   if (cur == nullptr) {
-    sv::launch_fill(L.x0, 0.0, L.d.N, s);
-    cur = L.x0;
+    cudaMemsetAsync(X0, 0, L.d.N * sizeof(R), s);
+    cur = X0;
   }
   sv::Level& C = h->lv[l - 1];
-  sv::launch_apply(L.d, cur, b, L.r, 1, s);
-  sv::launch_restrict(L.d, C.d, L.r, C.b, s);
-  vcycle_f64(h, l - 1, C.b, C.e);
-  sv::launch_prolong_add(L.d, C.d, C.e, cur, s);
+  sv::launch_apply<R>(L.d, cur, b, Buf<R>::r(L), 1, s);
+  sv::launch_restrict<R>(L.d, C.d, Buf<R>::r(L), Buf<R>::b(C), s);
+  vcycle<R>(h, l - 1, Buf<R>::b(C), Buf<R>::e(C));
+  sv::launch_prolong_add<R>(L.d, C.d, Buf<R>::e(C), cur, s);
   for (int it = 0; it < h->prm.nu2; ++it) {
-    double* dst = (it == h->prm.nu2 - 1) ? out : ((cur == L.x0) ? L.x1 : L.x0);
-    timed_sweep(h, finest, L, cur, b, dst);
+    R* dst = (it == h->prm.nu2 - 1) ? out : ((cur == X0) ? X1 : X0);
+    timed_sweep<R>(h, finest, L, cur, b, dst);
     cur = dst;
   }
-  if (h->prm.nu2 == 0) cudaMemcpyAsync(out, cur, L.d.N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (h->prm.nu2 == 0) cudaMemcpyAsync(out, cur, L.d.N * sizeof(R), cudaMemcpyDeviceToDevice, s);
+}
+
+// z = MG(r) on the finest level in the hierarchy's precision.  The mixed form
+// converts r to FP32, cycles in FP32 and converts the result back to FP64.
+void precondition(stokes_hierarchy* h, const double* r, double* z) {
+  const int top = static_cast<int>(h->lv.size()) - 1;
+  ++h->vcycles;
+  if (h->prm.prec == STOKES_FP64 || top == 0) {
+    vcycle<double>(h, top, r, z);
+    return;
+  }
+  sv::Level& F = h->lv[top];
+  sv::launch_convert<double, float>(r, F.bf, F.d.N, h->stream);
+  vcycle<float>(h, top, F.bf, F.ef);
+  sv::launch_convert<float, double>(F.ef, z, F.d.N, h->stream);
 }
 
 stokes_status read_scalar(stokes_hierarchy* h, const double* dev, double* out) {
@@ -195,7 +264,7 @@ stokes_status fgmres(stokes_hierarchy* h, const double* b, double* x, int* iters
   double beta0 = 0.0, beta = 0.0;
   stokes_status st;
 
-  sv::launch_apply(F.d, x, b, V, 1, s);
+  sv::launch_apply<double>(F.d, x, b, V, 1, s);
   if ((st = norm_host(h, V, N, sb.sc, &beta0)) != STOKES_OK) return st;
   if (!std::isfinite(beta0)) return fail(STOKES_ERR_NONFINITE, "initial residual is not finite");
   if (iters_out) *iters_out = 0;
@@ -213,9 +282,8 @@ stokes_status fgmres(stokes_hierarchy* h, const double* b, double* x, int* iters
       double* vj = V + j * ld;
       double* zj = Z + j * ld;
       double* w = V + (j + 1) * ld;
-      ++h->vcycles;
-      vcycle_f64(h, static_cast<int>(h->lv.size()) - 1, vj, zj);
-      sv::launch_apply(F.d, zj, nullptr, w, 0, s);
+      precondition(h, vj, zj);
+      sv::launch_apply<double>(F.d, zj, nullptr, w, 0, s);
       // classical Gram-Schmidt, twice
       sv::launch_multidot(V, ld, j + 1, w, N, h->partials, h->npart, sb.hcol, 0, s);
       sv::launch_multiaxpy(w, V, ld, j + 1, sb.hcol, -1.0, N, s);
@@ -236,7 +304,7 @@ stokes_status fgmres(stokes_hierarchy* h, const double* b, double* x, int* iters
     }
     sv::launch_backsolve(sb.H, m + 1, sb.g, k, sb.y, s);
     sv::launch_multiaxpy(x, Z, ld, k, sb.y, 1.0, N, s);
-    sv::launch_apply(F.d, x, b, V, 1, s);
+    sv::launch_apply<double>(F.d, x, b, V, 1, s);
     if ((st = norm_host(h, V, N, sb.sc, &beta)) != STOKES_OK) return st;
     if (!std::isfinite(beta)) return fail(STOKES_ERR_NONFINITE, "residual is not finite");
     if (beta <= tol) {
@@ -251,45 +319,64 @@ stokes_status fgmres(stokes_hierarchy* h, const double* b, double* x, int* iters
   return STOKES_OK;
 }
 
-// Tile shape of the FP64 sweep per level: fixed by params.tile, or (tile = -1)
-// the fastest of the shapes on that level, timed with CUDA events on the
-// hierarchy's stream (levels below 64 x 64 use 8 x 8: too few tiles otherwise).
-cudaError_t choose_tiles(stokes_hierarchy* h) {
+// Tile shape of the sweep per level and precision: fixed by params.tile, or
+// (tile = -1) the fastest of the shapes on that level, timed with CUDA events
+// on the hierarchy's stream (levels below 64 x 64 use 8 x 8: too few tiles
+// otherwise).
+template <typename R>
+cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
   cudaStream_t s = h->stream;
+  R* x = Buf<R>::x0(L);
+  R* b = Buf<R>::b(L);
+  R* xo = Buf<R>::x1(L);
+  const R* cd = nullptr;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(x, 0, L.d.N * sizeof(R), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(b, 0, L.d.N * sizeof(R), s)) != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return e;
+  }
+  float best = 1e30f;
+  for (int c = 0; c < sv::VANKA_NCFG; ++c) {
+    if constexpr (sizeof(R) == 8) {
+      sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, c, s);
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 3; ++r) sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, c, s);
+    } else {
+      sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, c, s);
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 3; ++r) sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, c, s);
+    }
+    cudaEventRecord(e1, s);
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      *cfg = c;
+    }
+  }
+  (void)cd;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t choose_tiles(stokes_hierarchy* h) {
   for (sv::Level& L : h->lv) {
     if (h->prm.tile >= 0) {
-      L.vk_cfg = h->prm.tile;
+      L.vk_cfg = L.vk_cfg_f = h->prm.tile;
       continue;
     }
-    L.vk_cfg = 0;
+    L.vk_cfg = L.vk_cfg_f = 0;
     if (L.d.n < 64) continue;
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(L.x0, 0, L.d.N * sizeof(double), s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(L.b, 0, L.d.N * sizeof(double), s)) != cudaSuccess) return e;
-    cudaEvent_t e0, e1;
-    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
-    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
-      cudaEventDestroy(e0);
-      return e;
-    }
-    float best = 1e30f;
-    for (int c = 0; c < sv::VANKA_F64_NCFG; ++c) {
-      sv::launch_vanka_f64(L.d, L.cd, h->fd, L.x0, L.b, L.x1, h->prm.omega, c, s);
-      cudaEventRecord(e0, s);
-      for (int r = 0; r < 3; ++r) sv::launch_vanka_f64(L.d, L.cd, h->fd, L.x0, L.b, L.x1, h->prm.omega, c, s);
-      cudaEventRecord(e1, s);
-      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-      float ms = 0.0f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) {
-        best = ms;
-        L.vk_cfg = c;
-      }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    cudaError_t e = tune_level<double>(h, L, &L.vk_cfg);
     if (e != cudaSuccess) return e;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (h->prm.prec != STOKES_FP64 && (e = tune_level<float>(h, L, &L.vk_cfg_f)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -330,8 +417,9 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   if (prm.restart < 1 || prm.restart > 64) return fail(STOKES_ERR_ARG, "restart must be in 1..64");
   if (prm.nu1 < 0 || prm.nu2 < 0 || prm.maxit < 1 || !(prm.rtol >= 0.0) || !(prm.omega > 0.0))
     return fail(STOKES_ERR_ARG, "bad smoothing / iteration parameters");
-  if (prm.prec != STOKES_FP64) return fail(STOKES_ERR_ARG, "precision mode not available in this build");
-  if (prm.tile < -1 || prm.tile >= sv::VANKA_F64_NCFG) return fail(STOKES_ERR_ARG, "tile must be -1..2");
+  if (prm.prec != STOKES_FP64 && prm.prec != STOKES_MIXED_FP32)
+    return fail(STOKES_ERR_ARG, "precision mode not available in this build");
+  if (prm.tile < -1 || prm.tile >= sv::VANKA_NCFG) return fail(STOKES_ERR_ARG, "tile must be -1..2");
   std::vector<int> sizes;
   {
     int m = n;
@@ -351,7 +439,10 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   h->stream = static_cast<cudaStream_t>(stream);
   h->m = prm.restart;
   h->fd = sv::interior_fast_diag(viscosity);
-  cudaError_t e = sv::vanka_f64_prepare();
+  for (int k = 0; k < 9; ++k) h->fdf.se[k] = static_cast<float>(h->fd.se[k]);
+  for (int k = 0; k < 4; ++k) h->fdf.so[k] = static_cast<float>(h->fd.so[k]);
+  for (int k = 0; k < 25; ++k) h->fdf.dinv[k] = static_cast<float>(h->fd.dinv[k]);
+  cudaError_t e = sv::vanka_prepare();
   if (e != cudaSuccess) {
     delete h;
     return cuda_fail(e, "kernel attributes");
@@ -372,10 +463,17 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
     }
     sv::build_class_data(nl, viscosity, L.cd_host, &L.full_inv_host);
     e = cudaMemcpy(L.cd, L.cd_host.data(), L.cd_host.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && prm.prec != STOKES_FP64) {
+      std::vector<float> cdf(L.cd_host.begin(), L.cd_host.end());
+      if ((e = dalloc(&L.xf0, N)) == cudaSuccess && (e = dalloc(&L.xf1, N)) == cudaSuccess &&
+          (e = dalloc(&L.bf, N)) == cudaSuccess && (e = dalloc(&L.rf, N)) == cudaSuccess &&
+          (e = dalloc(&L.ef, N)) == cudaSuccess && (e = dalloc(&L.cdf, cdf.size())) == cudaSuccess)
+        e = cudaMemcpy(L.cdf, cdf.data(), cdf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
       free_all(h);
       delete h;
-      return cuda_fail(e, "class data upload");
+      return cuda_fail(e, "level data allocation / upload");
     }
   }
   {
@@ -494,7 +592,7 @@ stokes_status stokes_apply_operator(stokes_hierarchy* h, int level, const double
   stokes_status st = check_level(h, level);
   if (st != STOKES_OK) return st;
   if (!x || !y) return fail(STOKES_ERR_ARG, "null vector");
-  sv::launch_apply(h->lv[level].d, x, nullptr, y, 0, h->stream);
+  sv::launch_apply<double>(h->lv[level].d, x, nullptr, y, 0, h->stream);
   return check_launch("apply_operator");
 }
 
@@ -502,7 +600,7 @@ stokes_status stokes_residual(stokes_hierarchy* h, int level, const double* b, c
   stokes_status st = check_level(h, level);
   if (st != STOKES_OK) return st;
   if (!x || !b || !r) return fail(STOKES_ERR_ARG, "null vector");
-  sv::launch_apply(h->lv[level].d, x, b, r, 1, h->stream);
+  sv::launch_apply<double>(h->lv[level].d, x, b, r, 1, h->stream);
   return check_launch("residual");
 }
 
@@ -513,7 +611,7 @@ stokes_status stokes_vanka_sweep(stokes_hierarchy* h, int level, const double* x
   if (!b || !x_out) return fail(STOKES_ERR_ARG, "null vector");
   if (x_out == x || x_out == b) return fail(STOKES_ERR_ARG, "x_out must not alias x or b");
   sv::Level& L = h->lv[level];
-  sv::launch_vanka_f64(L.d, L.cd, h->fd, x, b, x_out, h->prm.omega, L.vk_cfg, h->stream);
+  sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, x_out, h->prm.omega, L.vk_cfg, h->stream);
   return check_launch("vanka_sweep");
 }
 
@@ -521,7 +619,7 @@ stokes_status stokes_restrict(stokes_hierarchy* h, int level, const double* r_fi
   stokes_status st = check_level(h, level, 1);
   if (st != STOKES_OK) return st;
   if (!r_fine || !r_coarse) return fail(STOKES_ERR_ARG, "null vector");
-  sv::launch_restrict(h->lv[level].d, h->lv[level - 1].d, r_fine, r_coarse, h->stream);
+  sv::launch_restrict<double>(h->lv[level].d, h->lv[level - 1].d, r_fine, r_coarse, h->stream);
   return check_launch("restrict");
 }
 
@@ -529,7 +627,7 @@ stokes_status stokes_prolong_add(stokes_hierarchy* h, int level, const double* e
   stokes_status st = check_level(h, level, 1);
   if (st != STOKES_OK) return st;
   if (!e_coarse || !x_fine) return fail(STOKES_ERR_ARG, "null vector");
-  sv::launch_prolong_add(h->lv[level].d, h->lv[level - 1].d, e_coarse, x_fine, h->stream);
+  sv::launch_prolong_add<double>(h->lv[level].d, h->lv[level - 1].d, e_coarse, x_fine, h->stream);
   return check_launch("prolong_add");
 }
 
@@ -550,8 +648,7 @@ stokes_status stokes_initial_guess(stokes_hierarchy* h, const double* b, double*
 stokes_status stokes_vcycle_apply(stokes_hierarchy* h, const double* r, double* z) {
   if (!h || !r || !z) return fail(STOKES_ERR_ARG, "null argument");
   if (r == z) return fail(STOKES_ERR_ARG, "r and z must not alias");
-  ++h->vcycles;
-  vcycle_f64(h, static_cast<int>(h->lv.size()) - 1, r, z);
+  precondition(h, r, z);
   return check_launch("vcycle");
 }
 

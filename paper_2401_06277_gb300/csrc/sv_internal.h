@@ -29,11 +29,13 @@ constexpr int INTERIOR_CLASS = 12;  // 5 * 2 + 2
 // se[m*3+k]: symmetric eigenvector k at reduced index m (entries 0/4, 1/3, 2);
 // so[m*2+k]: antisymmetric eigenvector k at reduced index m (entries 0/-4, 1/-3);
 // dinv[a*5+b] = (90/nu) / (l_a + l_b), eigenvalues ordered sym 0..2, anti 0..1.
-struct FastDiag {
-  double se[9];
-  double so[4];
-  double dinv[25];
+template <typename T>
+struct FastDiagT {
+  T se[9];
+  T so[4];
+  T dinv[25];
 };
+using FastDiag = FastDiagT<double>;
 
 // Device-side description of one level (passed by value to kernels).
 struct LevelDev {
@@ -55,6 +57,14 @@ struct Level {
   double* e = nullptr;    // V-cycle result of this level (coarse correction)
   double* cd = nullptr;   // NCLASS * CD_STRIDE class data (device)
   int vk_cfg = 0;         // tile shape of the FP64 sweep on this level
+  // mixed-precision preconditioner (allocated when prec != STOKES_FP64)
+  float* xf0 = nullptr;
+  float* xf1 = nullptr;
+  float* bf = nullptr;
+  float* rf = nullptr;
+  float* ef = nullptr;
+  float* cdf = nullptr;   // class data in FP32
+  int vk_cfg_f = 0;       // tile shape of the FP32 sweep on this level
   std::vector<double> cd_host;
   std::vector<double> full_inv_host;  // NCLASS * 51 * 51 dense inverses (host)
 };
@@ -68,6 +78,7 @@ struct stokes_hierarchy {
   cudaStream_t stream = nullptr;
   std::vector<sv::Level> lv;     // lv[0] = coarsest
   sv::FastDiag fd;               // interior patch factors (level independent)
+  sv::FastDiagT<float> fdf;      // the same in FP32
   double* coarse_G = nullptr;    // N0 x N0 dense inverse of the bordered coarse system
   int N0 = 0;
   // FGMRES workspace
@@ -108,22 +119,26 @@ FastDiag interior_fast_diag(double nu);
 // In-place Gauss-Jordan inverse with partial pivoting; false if singular.
 bool invert_dense(std::vector<double>& a, int m);
 
-// ---- kernels (sv_kernels_f64.cu) ----
-void launch_apply(const LevelDev& L, const double* x, const double* b, double* y, int residual,
-                  cudaStream_t s);
+// ---- stencil kernels (sv_kernels.cu; T = double or float) ----
+template <typename T>
+void launch_apply(const LevelDev& L, const T* x, const T* b, T* y, int residual, cudaStream_t s);
 void launch_rhs(const LevelDev& L, const double* f, const double* ud, double* b, cudaStream_t s);
 void launch_rhs_transpose(const LevelDev& L, const double* lam, double* g, cudaStream_t s);
-// FP64 Vanka sweep (sv_vanka_f64.cu); cfg selects the tile shape (8x8, 16x8, 16x16 vertices)
-constexpr int VANKA_F64_NCFG = 3;
-void launch_vanka_f64(const LevelDev& L, const double* cd, const FastDiag& fd, const double* x,
-                      const double* b, double* xo, double omega, int cfg, cudaStream_t s);
-const char* vanka_f64_cfg_name(int cfg);
-void launch_restrict(const LevelDev& F, const LevelDev& C, const double* rf, double* rc,
-                     cudaStream_t s);
-void launch_prolong_add(const LevelDev& F, const LevelDev& C, const double* ec, double* xf,
-                        cudaStream_t s);
+// Fused Vanka sweep (sv_vanka.cu, R = double or float); cfg selects the tile
+// shape (8x8, 16x8, 16x16 vertices)
+constexpr int VANKA_NCFG = 3;
+template <typename R>
+void launch_vanka(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
+                  double omega, int cfg, cudaStream_t s);
+const char* vanka_cfg_name(int cfg);
+template <typename T>
+void launch_restrict(const LevelDev& F, const LevelDev& C, const T* rf, T* rc, cudaStream_t s);
+template <typename T>
+void launch_prolong_add(const LevelDev& F, const LevelDev& C, const T* ec, T* xf, cudaStream_t s);
+template <typename TI, typename TO>
+void launch_convert(const TI* in, TO* out, long long N, cudaStream_t s);
 void launch_coarse(const double* G, int N0, const double* r, double* e, cudaStream_t s);
-cudaError_t vanka_f64_prepare();
+cudaError_t vanka_prepare();
 
 // ---- Krylov kernels (sv_krylov.cu) ----
 int dot_blocks();

@@ -1,9 +1,11 @@
-// sv_kernels_f64.cu -- FP64 kernels of the hot path on sm_103a:
+// sv_kernels.cu -- stencil kernels of the hot path on sm_103a, templated on
+// the element type (double for the FP64 form and for FGMRES, float inside the
+// mixed-precision preconditioner):
 //   matrix-free Stokes operator / residual   (Section 2.2, Algorithm 1 residual)
-//   right-hand side assembly and its transpose (Section 2.2)
-//   fused additive Vanka sweep               (Section 3.2, Algorithm 3; Section 6.3)
 //   FE restriction P^T and prolongation P    (Section 3, Algorithm 1)
-//   dense coarse solve                       (Algorithm 1, level 0)
+//   precision conversions
+// and, in FP64 only: right-hand side assembly and its transpose (Section 2.2)
+// and the dense coarse solve (Algorithm 1, level 0).
 #include <cuda_runtime.h>
 
 #include "sv_internal.h"
@@ -24,38 +26,39 @@ __device__ __forceinline__ bool is_free(int I, int J, int nq) {
 // stencil coefficients are compile-time constants (node parities are fixed
 // per node); near the boundary a masked generic path drops Dirichlet columns.
 // ---------------------------------------------------------------------------
-template <int PI, int PJ>
-__device__ __forceinline__ double lap_g(const double* __restrict__ xs, int ld) {
-  double s = 0.0;
+template <typename T, int PI, int PJ>
+__device__ __forceinline__ T lap_g(const T* __restrict__ xs, int ld) {
+  T s = T(0);
 #pragma unroll
   for (int dJ = -2; dJ <= 2; ++dJ) {
 #pragma unroll
     for (int dI = -2; dI <= 2; ++dI) {
-      const double c = k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ);
-      if (c != 0.0) s = fma(c, xs[dJ * ld + dI], s);
+      const T c = T(k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ));
+      if (c != T(0)) s = fma(c, xs[dJ * ld + dI], s);
     }
   }
   return s;
 }
 
-template <int PI, int PJ, int COMP>
-__device__ __forceinline__ double btp_g(const double* __restrict__ pc, int ld) {
-  double g = 0.0;
+template <typename T, int PI, int PJ, int COMP>
+__device__ __forceinline__ T btp_g(const T* __restrict__ pc, int ld) {
+  T g = T(0);
 #pragma unroll
   for (int dj = -1; dj <= 1; ++dj) {
 #pragma unroll
     for (int di = -1; di <= 1; ++di) {
-      const double w = COMP == 0 ? ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj)
-                                 : ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj);
-      if (w != 0.0) g = fma(w, pc[dj * ld + di], g);
+      const T w = T(COMP == 0 ? ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj)
+                              : ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj));
+      if (w != T(0)) g = fma(w, pc[dj * ld + di], g);
     }
   }
   return g;
 }
 
 // generic masked evaluation of (A x) at velocity node (I, J), both components
-__device__ __forceinline__ void apply_vel_node(const LevelDev& L, const double* __restrict__ x, int I,
-                                               int J, double& ax, double& ay) {
+template <typename T>
+__device__ __forceinline__ void apply_vel_node(const LevelDev& L, const T* __restrict__ x, int I,
+                                               int J, T& ax, T& ay) {
   const int nq = L.nq, np = L.np, n = L.n;
   const long long nv = L.nv;
   const long long k = static_cast<long long>(J) * nq + I;
@@ -64,7 +67,7 @@ __device__ __forceinline__ void apply_vel_node(const LevelDev& L, const double* 
     ay = x[nv + k];
     return;
   }
-  double sx = 0.0, sy = 0.0;
+  T sx = T(0), sy = T(0);
   for (int dJ = -2; dJ <= 2; ++dJ) {
     const int J2 = J + dJ;
     if (J2 <= 0 || J2 >= nq - 1) continue;
@@ -72,47 +75,47 @@ __device__ __forceinline__ void apply_vel_node(const LevelDev& L, const double* 
     for (int dI = -2; dI <= 2; ++dI) {
       const int I2 = I + dI;
       if (I2 <= 0 || I2 >= nq - 1) continue;
-      const double c = k1(I, dI) * mJ + m1(I, dI) * kJ;
-      if (c == 0.0) continue;
+      const T c = T(k1(I, dI) * mJ + m1(I, dI) * kJ);
+      if (c == T(0)) continue;
       const long long kk = static_cast<long long>(J2) * nq + I2;
       sx = fma(c, x[kk], sx);
       sy = fma(c, x[nv + kk], sy);
     }
   }
-  const double* p = x + 2 * nv;
-  double gx = 0.0, gy = 0.0;
+  const T* p = x + 2 * nv;
+  T gx = T(0), gy = T(0);
   for (int j = J / 2 - 1; j <= J / 2 + 1; ++j) {
     if (j < 0 || j > n) continue;
     for (int i = I / 2 - 1; i <= I / 2 + 1; ++i) {
       if (i < 0 || i > n) continue;
-      const double wx = ccol(I, i) * ncol(J, j), wy = ncol(I, i) * ccol(J, j);
-      const double pv = p[static_cast<long long>(j) * np + i];
-      if (wx != 0.0) gx = fma(wx, pv, gx);
-      if (wy != 0.0) gy = fma(wy, pv, gy);
+      const T wx = T(ccol(I, i) * ncol(J, j)), wy = T(ncol(I, i) * ccol(J, j));
+      const T pv = p[static_cast<long long>(j) * np + i];
+      if (wx != T(0)) gx = fma(wx, pv, gx);
+      if (wy != T(0)) gy = fma(wy, pv, gy);
     }
   }
-  const double cl = L.nu / 90.0, cb = -L.h / 18.0;
+  const T cl = T(L.nu / 90.0), cb = T(-L.h / 18.0);
   ax = cl * sx + cb * gx;
   ay = cl * sy + cb * gy;
 }
 
-template <int PI, int PJ>
-__device__ __forceinline__ void apply_node(const LevelDev& L, const double* __restrict__ x,
-                                           const double* __restrict__ b, double* __restrict__ y,
+template <typename T, int PI, int PJ>
+__device__ __forceinline__ void apply_node(const LevelDev& L, const T* __restrict__ x,
+                                           const T* __restrict__ b, T* __restrict__ y,
                                            int residual, bool fast, int a, int bb) {
   const int I = 2 * a + PI, J = 2 * bb + PJ;
   const int nq = L.nq;
   if (I >= nq || J >= nq) return;
   const long long nv = L.nv;
   const long long k = static_cast<long long>(J) * nq + I;
-  double ax, ay;
+  T ax, ay;
   if (fast) {
-    const double cl = L.nu / 90.0, cb = -L.h / 18.0;
-    const double* pc = x + 2 * nv + static_cast<long long>(bb) * L.np + a;
-    ax = cl * lap_g<PI, PJ>(x + k, nq) + cb * btp_g<PI, PJ, 0>(pc, L.np);
-    ay = cl * lap_g<PI, PJ>(x + nv + k, nq) + cb * btp_g<PI, PJ, 1>(pc, L.np);
+    const T cl = T(L.nu / 90.0), cb = T(-L.h / 18.0);
+    const T* pc = x + 2 * nv + static_cast<long long>(bb) * L.np + a;
+    ax = cl * lap_g<T, PI, PJ>(x + k, nq) + cb * btp_g<T, PI, PJ, 0>(pc, L.np);
+    ay = cl * lap_g<T, PI, PJ>(x + nv + k, nq) + cb * btp_g<T, PI, PJ, 1>(pc, L.np);
   } else {
-    apply_vel_node(L, x, I, J, ax, ay);
+    apply_vel_node<T>(L, x, I, J, ax, ay);
   }
   if (residual) {
     y[k] = b[k] - ax;
@@ -123,29 +126,30 @@ __device__ __forceinline__ void apply_node(const LevelDev& L, const double* __re
   }
 }
 
-__global__ void k_apply(LevelDev L, const double* __restrict__ x, const double* __restrict__ b,
-                        double* __restrict__ y, int residual) {
+template <typename T>
+__global__ void k_apply(LevelDev L, const T* __restrict__ x, const T* __restrict__ b,
+                        T* __restrict__ y, int residual) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   const int bb = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = L.n, nq = L.nq, np = L.np;
   if (a > n || bb > n) return;
   const bool fast = a >= 2 && a <= n - 2 && bb >= 2 && bb <= n - 2;
-  apply_node<0, 0>(L, x, b, y, residual, fast, a, bb);
-  apply_node<1, 0>(L, x, b, y, residual, fast, a, bb);
-  apply_node<0, 1>(L, x, b, y, residual, fast, a, bb);
-  apply_node<1, 1>(L, x, b, y, residual, fast, a, bb);
+  apply_node<T, 0, 0>(L, x, b, y, residual, fast, a, bb);
+  apply_node<T, 1, 0>(L, x, b, y, residual, fast, a, bb);
+  apply_node<T, 0, 1>(L, x, b, y, residual, fast, a, bb);
+  apply_node<T, 1, 1>(L, x, b, y, residual, fast, a, bb);
   // pressure row of vertex (a, bb): (B u)
   const long long nv = L.nv;
-  double s = 0.0;
+  T s = T(0);
   if (fast) {
-    const double* u0 = x + static_cast<long long>(2 * bb) * nq + 2 * a;
+    const T* u0 = x + static_cast<long long>(2 * bb) * nq + 2 * a;
 #pragma unroll
     for (int dJ = -2; dJ <= 2; ++dJ) {
 #pragma unroll
       for (int dI = -2; dI <= 2; ++dI) {
-        const double cx = crow(dI) * nrow(dJ), cy = nrow(dI) * crow(dJ);
-        if (cx != 0.0) s = fma(cx, u0[dJ * nq + dI], s);
-        if (cy != 0.0) s = fma(cy, u0[nv + dJ * nq + dI], s);
+        const T cx = T(crow(dI) * nrow(dJ)), cy = T(nrow(dI) * crow(dJ));
+        if (cx != T(0)) s = fma(cx, u0[dJ * nq + dI], s);
+        if (cy != T(0)) s = fma(cy, u0[nv + dJ * nq + dI], s);
       }
     }
   } else {
@@ -158,13 +162,13 @@ __global__ void k_apply(LevelDev L, const double* __restrict__ x, const double* 
         const int I = 2 * a + dI;
         if (I <= 0 || I >= nq - 1) continue;
         const long long kk = static_cast<long long>(J) * nq + I;
-        const double cx = crow(dI) * nrow(dJ), cy = nrow(dI) * crow(dJ);
-        if (cx != 0.0) s = fma(cx, x[kk], s);
-        if (cy != 0.0) s = fma(cy, x[nv + kk], s);
+        const T cx = T(crow(dI) * nrow(dJ)), cy = T(nrow(dI) * crow(dJ));
+        if (cx != T(0)) s = fma(cx, x[kk], s);
+        if (cy != T(0)) s = fma(cy, x[nv + kk], s);
       }
     }
   }
-  const double ap = -L.h / 18.0 * s;
+  const T ap = T(-L.h / 18.0) * s;
   const long long k = 2 * nv + static_cast<long long>(bb) * np + a;
   y[k] = residual ? b[k] - ap : ap;
 }
@@ -273,14 +277,14 @@ __device__ __forceinline__ double rq1(int off) {
   return off == 0 ? 1.0 : ((off == 1 || off == -1) ? 0.5 : 0.0);
 }
 
-__global__ void k_restrict(LevelDev F, LevelDev C, const double* __restrict__ rf,
-                           double* __restrict__ rc) {
+template <typename T>
+__global__ void k_restrict(LevelDev F, LevelDev C, const T* __restrict__ rf, T* __restrict__ rc) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   // velocity part over the coarse Q2 grid, pressure over the coarse vertices
   if (I < C.nq && J < C.nq) {
     const long long k = static_cast<long long>(J) * C.nq + I;
-    double sx = 0.0, sy = 0.0;
+    T sx = T(0), sy = T(0);
     if (is_free(I, J, C.nq)) {
       for (int dJ = -3; dJ <= 3; ++dJ) {
         const double wJ = rq2(J, dJ);
@@ -291,8 +295,8 @@ __global__ void k_restrict(LevelDev F, LevelDev C, const double* __restrict__ rf
           const int FI = 2 * I + dI;
           if (wI == 0.0 || !(FI > 0 && FI < F.nq - 1)) continue;
           const long long kf = static_cast<long long>(FJ) * F.nq + FI;
-          sx = fma(wI * wJ, rf[kf], sx);
-          sy = fma(wI * wJ, rf[F.nv + kf], sy);
+          sx = fma(T(wI * wJ), rf[kf], sx);
+          sy = fma(T(wI * wJ), rf[F.nv + kf], sy);
         }
       }
     }
@@ -300,14 +304,14 @@ __global__ void k_restrict(LevelDev F, LevelDev C, const double* __restrict__ rf
     rc[C.nv + k] = sy;
   }
   if (I < C.np && J < C.np) {
-    double s = 0.0;
+    T s = T(0);
     for (int dj = -1; dj <= 1; ++dj) {
       const int fj = 2 * J + dj;
       if (fj < 0 || fj >= F.np) continue;
       for (int di = -1; di <= 1; ++di) {
         const int fi = 2 * I + di;
         if (fi < 0 || fi >= F.np) continue;
-        s = fma(rq1(di) * rq1(dj), rf[2 * F.nv + static_cast<long long>(fj) * F.np + fi], s);
+        s = fma(T(rq1(di) * rq1(dj)), rf[2 * F.nv + static_cast<long long>(fj) * F.np + fi], s);
       }
     }
     rc[2 * C.nv + static_cast<long long>(J) * C.np + I] = s;
@@ -325,14 +329,14 @@ __device__ __forceinline__ double pq2(int k, int a) {
   return W[k][a];
 }
 
-__global__ void k_prolong_add(LevelDev F, LevelDev C, const double* __restrict__ ec,
-                              double* __restrict__ xf) {
+template <typename T>
+__global__ void k_prolong_add(LevelDev F, LevelDev C, const T* __restrict__ ec, T* __restrict__ xf) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I < F.nq && J < F.nq && is_free(I, J, F.nq)) {
     const int ex = min(I / 4, C.n - 1), ey = min(J / 4, C.n - 1);
     const int kx = I - 4 * ex, ky = J - 4 * ey;
-    double sx = 0.0, sy = 0.0;
+    T sx = T(0), sy = T(0);
     for (int b = 0; b < 3; ++b) {
       const double wy = pq2(ky, b);
       const int CJ = 2 * ey + b;
@@ -342,8 +346,8 @@ __global__ void k_prolong_add(LevelDev F, LevelDev C, const double* __restrict__
         const int CI = 2 * ex + a;
         if (wx == 0.0 || !is_free(CI, CJ, C.nq)) continue;
         const long long kc = static_cast<long long>(CJ) * C.nq + CI;
-        sx = fma(wx * wy, ec[kc], sx);
-        sy = fma(wx * wy, ec[C.nv + kc], sy);
+        sx = fma(T(wx * wy), ec[kc], sx);
+        sy = fma(T(wx * wy), ec[C.nv + kc], sy);
       }
     }
     const long long k = static_cast<long long>(J) * F.nq + I;
@@ -353,18 +357,25 @@ __global__ void k_prolong_add(LevelDev F, LevelDev C, const double* __restrict__
   if (I < F.np && J < F.np) {
     const int ex = min(I / 2, C.n - 1), ey = min(J / 2, C.n - 1);
     const int kx = I - 2 * ex, ky = J - 2 * ey;
-    double s = 0.0;
+    T s = T(0);
     for (int b = 0; b < 2; ++b) {
       const double wy = (b == 0) ? (1.0 - 0.5 * ky) : 0.5 * ky;
       if (wy == 0.0) continue;
       for (int a = 0; a < 2; ++a) {
         const double wx = (a == 0) ? (1.0 - 0.5 * kx) : 0.5 * kx;
         if (wx == 0.0) continue;
-        s = fma(wx * wy, ec[2 * C.nv + static_cast<long long>(ey + b) * C.np + (ex + a)], s);
+        s = fma(T(wx * wy), ec[2 * C.nv + static_cast<long long>(ey + b) * C.np + (ex + a)], s);
       }
     }
     xf[2 * F.nv + static_cast<long long>(J) * F.np + I] += s;
   }
+}
+
+template <typename TI, typename TO>
+__global__ void k_convert(const TI* __restrict__ in, TO* __restrict__ out, long long N) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    out[i] = static_cast<TO>(in[i]);
 }
 
 // e = G r, G dense N0 x N0 (one CTA)
@@ -387,11 +398,11 @@ dim3 grid2(int nx, int ny, dim3 blk) {
 
 }  // namespace
 
-void launch_apply(const LevelDev& L, const double* x, const double* b, double* y, int residual,
-                  cudaStream_t s) {
+template <typename T>
+void launch_apply(const LevelDev& L, const T* x, const T* b, T* y, int residual, cudaStream_t s) {
   count_launches(1);
   dim3 blk(32, 8);
-  k_apply<<<grid2(L.np, L.np, blk), blk, 0, s>>>(L, x, b, y, residual);
+  k_apply<T><<<grid2(L.np, L.np, blk), blk, 0, s>>>(L, x, b, y, residual);
 }
 
 void launch_rhs(const LevelDev& L, const double* f, const double* ud, double* b, cudaStream_t s) {
@@ -407,23 +418,40 @@ void launch_rhs_transpose(const LevelDev& L, const double* lam, double* g, cudaS
   k_rhs_transpose<<<grid2(L.nq, L.nq, blk), blk, 0, s>>>(L, lam, g);
 }
 
-void launch_restrict(const LevelDev& F, const LevelDev& C, const double* rf, double* rc,
-                     cudaStream_t s) {
+template <typename T>
+void launch_restrict(const LevelDev& F, const LevelDev& C, const T* rf, T* rc, cudaStream_t s) {
   count_launches(1);
   dim3 blk(32, 8);
-  k_restrict<<<grid2(C.nq, C.nq, blk), blk, 0, s>>>(F, C, rf, rc);
+  k_restrict<T><<<grid2(C.nq, C.nq, blk), blk, 0, s>>>(F, C, rf, rc);
 }
 
-void launch_prolong_add(const LevelDev& F, const LevelDev& C, const double* ec, double* xf,
-                        cudaStream_t s) {
+template <typename T>
+void launch_prolong_add(const LevelDev& F, const LevelDev& C, const T* ec, T* xf, cudaStream_t s) {
   count_launches(1);
   dim3 blk(32, 8);
-  k_prolong_add<<<grid2(F.nq, F.nq, blk), blk, 0, s>>>(F, C, ec, xf);
+  k_prolong_add<T><<<grid2(F.nq, F.nq, blk), blk, 0, s>>>(F, C, ec, xf);
+}
+
+template <typename TI, typename TO>
+void launch_convert(const TI* in, TO* out, long long N, cudaStream_t s) {
+  count_launches(1);
+  long long blocks = (N + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_convert<TI, TO><<<static_cast<int>(blocks < 1 ? 1 : blocks), 256, 0, s>>>(in, out, N);
 }
 
 void launch_coarse(const double* G, int N0, const double* r, double* e, cudaStream_t s) {
   count_launches(1);
   k_coarse<<<1, 256, N0 * sizeof(double), s>>>(G, N0, r, e);
 }
+
+template void launch_apply<double>(const LevelDev&, const double*, const double*, double*, int, cudaStream_t);
+template void launch_apply<float>(const LevelDev&, const float*, const float*, float*, int, cudaStream_t);
+template void launch_restrict<double>(const LevelDev&, const LevelDev&, const double*, double*, cudaStream_t);
+template void launch_restrict<float>(const LevelDev&, const LevelDev&, const float*, float*, cudaStream_t);
+template void launch_prolong_add<double>(const LevelDev&, const LevelDev&, const double*, double*, cudaStream_t);
+template void launch_prolong_add<float>(const LevelDev&, const LevelDev&, const float*, float*, cudaStream_t);
+template void launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
 
 }  // namespace sv

@@ -1,5 +1,6 @@
-// sv_vanka_f64.cu -- fused additive Vanka sweep in FP64 (Section 3.2,
-// Algorithm 3; the shared patch inverses of Section 6.3).
+// sv_vanka.cu -- fused additive Vanka sweep (Section 3.2, Algorithm 3; the
+// shared patch inverses of Section 6.3), templated on the element type:
+// double for the FP64 form, float inside the mixed-precision preconditioner.
 //
 //   x_out = x + sum_i V_i^T W_i A_i^-1 V_i (b - A x),  W_i = omega diag(1/m_j)
 //
@@ -16,9 +17,9 @@
 // vertex (i, j).  The sum over patches runs in a fixed order (no atomics), so
 // the result is deterministic.
 //
-// The kernel is bound by the FP64 pipe on GB300 (2 DFMA / clk / SM); the
-// tile shape trades halo recomputation against shared memory per CTA and is
-// chosen per level by a timing autotuner at hierarchy creation.
+// In FP64 the kernel is bound by the FP64 pipe on GB300 (2 DFMA / clk / SM).
+// The tile shape trades halo recomputation against shared memory per CTA and
+// is chosen per level by a timing autotuner at hierarchy creation.
 #include <cuda_runtime.h>
 
 #include "sv_internal.h"
@@ -46,15 +47,15 @@ struct VT {
 
 // sum of nu (K (x) M + M (x) K) x / (nu/90) over the stencil of a node with
 // parities (PI, PJ); xs points at the node in the x window.
-template <int PI, int PJ, int XW>
-__device__ __forceinline__ double lap(const double* xs) {
-  double s = 0.0;
+template <typename T, int PI, int PJ, int XW>
+__device__ __forceinline__ T lap(const T* xs) {
+  T s = T(0);
 #pragma unroll
   for (int dJ = -2; dJ <= 2; ++dJ) {
 #pragma unroll
     for (int dI = -2; dI <= 2; ++dI) {
-      const double c = k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ);
-      if (c != 0.0) s = fma(c, xs[dJ * XW + dI], s);
+      const T c = T(k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ));
+      if (c != T(0)) s = fma(c, xs[dJ * XW + dI], s);
     }
   }
   return s;
@@ -62,44 +63,43 @@ __device__ __forceinline__ double lap(const double* xs) {
 
 // (B^T p) / (-h/18) for velocity component COMP at a node with parities
 // (PI, PJ) of the cell whose vertex is (a, b); pc points at p(a, b).
-template <int PI, int PJ, int COMP, int PW>
-__device__ __forceinline__ double btp(const double* pc) {
-  double g = 0.0;
+template <typename T, int PI, int PJ, int COMP, int PW>
+__device__ __forceinline__ T btp(const T* pc) {
+  T g = T(0);
 #pragma unroll
   for (int dj = -1; dj <= 1; ++dj) {
 #pragma unroll
     for (int di = -1; di <= 1; ++di) {
-      const double w = COMP == 0 ? ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj)
-                                 : ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj);
-      if (w != 0.0) g = fma(w, pc[dj * PW + di], g);
+      const T w = T(COMP == 0 ? ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj)
+                              : ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj));
+      if (w != T(0)) g = fma(w, pc[dj * PW + di], g);
     }
   }
   return g;
 }
 
-template <int PI, int PJ, int TX, int TY>
-__device__ __forceinline__ void res_node(double* sr, const double* x0, const double* pc, int I, int J,
-                                         const LevelDev& L, const double* __restrict__ x, double cl,
-                                         double cb) {
-  using T = VT<TX, TY>;
+template <typename T, int PI, int PJ, int TX, int TY>
+__device__ __forceinline__ void res_node(T* sr, const T* x0, const T* pc, int I, int J,
+                                         const LevelDev& L, const T* __restrict__ x, T cl, T cb) {
+  using V = VT<TX, TY>;
   const int nq = L.nq;
   if (I < 0 || J < 0 || I >= nq || J >= nq) return;  // outside: r stays 0
   if (!vfree(I, J, nq)) {                            // Dirichlet row: r = b - x
     const long long k = static_cast<long long>(J) * nq + I;
     sr[0] -= x[k];
-    sr[T::RW * T::RH] -= x[L.nv + k];
+    sr[V::RW * V::RH] -= x[L.nv + k];
     return;
   }
-  const double* x1 = x0 + T::XW * T::XH;
-  sr[0] -= cl * lap<PI, PJ, T::XW>(x0) + cb * btp<PI, PJ, 0, T::PW>(pc);
-  sr[T::RW * T::RH] -= cl * lap<PI, PJ, T::XW>(x1) + cb * btp<PI, PJ, 1, T::PW>(pc);
+  const T* x1 = x0 + V::XW * V::XH;
+  sr[0] -= cl * lap<T, PI, PJ, V::XW>(x0) + cb * btp<T, PI, PJ, 0, V::PW>(pc);
+  sr[V::RW * V::RH] -= cl * lap<T, PI, PJ, V::XW>(x1) + cb * btp<T, PI, PJ, 1, V::PW>(pc);
 }
 
 // Forward transform of one 5-vector into the generalised eigenbasis S^T v
 // (three symmetric, two antisymmetric eigenvectors; 4 add/sub + 13 FMA/MUL).
-__device__ __forceinline__ void fd_fwd(const FastDiag& f, double v0, double v1, double v2, double v3,
-                                       double v4, double* c) {
-  const double e0 = v0 + v4, e1 = v1 + v3, o0 = v0 - v4, o1 = v1 - v3;
+template <typename T>
+__device__ __forceinline__ void fd_fwd(const FastDiagT<T>& f, T v0, T v1, T v2, T v3, T v4, T* c) {
+  const T e0 = v0 + v4, e1 = v1 + v3, o0 = v0 - v4, o1 = v1 - v3;
 #pragma unroll
   for (int k = 0; k < 3; ++k) c[k] = fma(f.se[k], e0, fma(f.se[3 + k], e1, f.se[6 + k] * v2));
 #pragma unroll
@@ -107,8 +107,9 @@ __device__ __forceinline__ void fd_fwd(const FastDiag& f, double v0, double v1, 
 }
 
 // Inverse transform S c of five eigen-coefficients (13 FMA/MUL + 4 add/sub).
-__device__ __forceinline__ void fd_inv(const FastDiag& f, const double* c, double* v) {
-  double E[3], Od[2];
+template <typename T>
+__device__ __forceinline__ void fd_inv(const FastDiagT<T>& f, const T* c, T* v) {
+  T E[3], Od[2];
 #pragma unroll
   for (int m = 0; m < 3; ++m) E[m] = fma(f.se[m * 3], c[0], fma(f.se[m * 3 + 1], c[1], f.se[m * 3 + 2] * c[2]));
 #pragma unroll
@@ -122,54 +123,55 @@ __device__ __forceinline__ void fd_inv(const FastDiag& f, const double* c, doubl
 
 // y = K^-1 r on an interior patch window (5 x 5, row-major [wj][wi]) by fast
 // diagonalisation: transform both axes, divide by l_a + l_b, transform back.
-__device__ __forceinline__ void fd_solve(const FastDiag& f, const double* r, double* y) {
-  double T[25], U[25];
+template <typename T>
+__device__ __forceinline__ void fd_solve(const FastDiagT<T>& f, const T* r, T* y) {
+  T Tm[25], U[25];
 #pragma unroll
   for (int wj = 0; wj < 5; ++wj)
-    fd_fwd(f, r[wj * 5], r[wj * 5 + 1], r[wj * 5 + 2], r[wj * 5 + 3], r[wj * 5 + 4], T + wj * 5);
+    fd_fwd(f, r[wj * 5], r[wj * 5 + 1], r[wj * 5 + 2], r[wj * 5 + 3], r[wj * 5 + 4], Tm + wj * 5);
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    double c[5];
-    fd_fwd(f, T[k], T[5 + k], T[10 + k], T[15 + k], T[20 + k], c);
+    T c[5];
+    fd_fwd(f, Tm[k], Tm[5 + k], Tm[10 + k], Tm[15 + k], Tm[20 + k], c);
 #pragma unroll
     for (int k2 = 0; k2 < 5; ++k2) U[k2 * 5 + k] = c[k2] * f.dinv[k2 * 5 + k];
   }
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
-    double c[5], v[5];
+    T c[5], v[5];
 #pragma unroll
     for (int k2 = 0; k2 < 5; ++k2) c[k2] = U[k2 * 5 + k];
     fd_inv(f, c, v);
 #pragma unroll
-    for (int wj = 0; wj < 5; ++wj) T[wj * 5 + k] = v[wj];
+    for (int wj = 0; wj < 5; ++wj) Tm[wj * 5 + k] = v[wj];
   }
 #pragma unroll
-  for (int wj = 0; wj < 5; ++wj) fd_inv(f, T + wj * 5, y + wj * 5);
+  for (int wj = 0; wj < 5; ++wj) fd_inv(f, Tm + wj * 5, y + wj * 5);
 }
 
-__device__ __forceinline__ double inv_mult(int m) {
+template <typename T>
+__device__ __forceinline__ T inv_mult(int m) {
   switch (m) {
-    case 1: return 1.0;
-    case 2: return 0.5;
-    case 3: return 1.0 / 3.0;
-    case 4: return 0.25;
-    case 6: return 1.0 / 6.0;
-    default: return 1.0 / 9.0;
+    case 1: return T(1.0);
+    case 2: return T(0.5);
+    case 3: return T(1.0 / 3.0);
+    case 4: return T(0.25);
+    case 6: return T(1.0 / 6.0);
+    default: return T(1.0 / 9.0);
   }
 }
 
-template <int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) k_vanka_f64(LevelDev L, const double* __restrict__ cd,
-                                                  const FastDiag fdg, const double* __restrict__ x,
-                                                  const double* __restrict__ b,
-                                                  double* __restrict__ xo, double omega) {
+template <typename R, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ cd,
+                                              const FastDiagT<R> fdg, const R* __restrict__ x,
+                                              const R* __restrict__ b, R* __restrict__ xo, R omega) {
   using T = VT<TX, TY>;
-  extern __shared__ double smem[];
-  double* sx = smem;
-  double* sp = sx + T::SX;
-  double* sr = sp + T::SP;
-  double* srp = sr + T::SR;
-  double* sd = srp + T::SRP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sx = reinterpret_cast<R*>(smem_raw);
+  R* sp = sx + T::SX;
+  R* sr = sp + T::SP;
+  R* srp = sr + T::SR;
+  R* sd = srp + T::SRP;
   const int n = L.n, nq = L.nq, np = L.np;
   const long long nv = L.nv;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
@@ -185,12 +187,12 @@ __global__ void __launch_bounds__(NT) k_vanka_f64(LevelDev L, const double* __re
       const int rem = t - c * T::XW * T::XH;
       const int jj = rem / T::XW, ii = rem - jj * T::XW;
       const int I = XI0 + ii, J = XJ0 + jj;
-      sx[t] = vfree(I, J, nq) ? x[c * nv + static_cast<long long>(J) * nq + I] : 0.0;
+      sx[t] = vfree(I, J, nq) ? x[c * nv + static_cast<long long>(J) * nq + I] : R(0);
     }
     for (int t = tid; t < T::SP; t += NT) {
       const int jj = t / T::PW, ii = t - jj * T::PW;
       const int i = i0 - 3 + ii, j = j0 - 3 + jj;
-      sp[t] = (i >= 0 && j >= 0 && i <= n && j <= n) ? x[2 * nv + static_cast<long long>(j) * np + i] : 0.0;
+      sp[t] = (i >= 0 && j >= 0 && i <= n && j <= n) ? x[2 * nv + static_cast<long long>(j) * np + i] : R(0);
     }
   }
   for (int t = tid; t < T::SR; t += NT) {
@@ -198,44 +200,44 @@ __global__ void __launch_bounds__(NT) k_vanka_f64(LevelDev L, const double* __re
     const int rem = t - c * T::RW * T::RH;
     const int jj = rem / T::RW, ii = rem - jj * T::RW;
     const int I = RI0 + ii, J = RJ0 + jj;
-    sr[t] = (I >= 0 && J >= 0 && I < nq && J < nq) ? b[c * nv + static_cast<long long>(J) * nq + I] : 0.0;
+    sr[t] = (I >= 0 && J >= 0 && I < nq && J < nq) ? b[c * nv + static_cast<long long>(J) * nq + I] : R(0);
   }
   for (int t = tid; t < T::SRP; t += NT) {
     const int jj = t / T::QW, ii = t - jj * T::QW;
     const int i = i0 - 1 + ii, j = j0 - 1 + jj;
-    srp[t] = (i >= 0 && j >= 0 && i <= n && j <= n) ? b[2 * nv + static_cast<long long>(j) * np + i] : 0.0;
+    srp[t] = (i >= 0 && j >= 0 && i <= n && j <= n) ? b[2 * nv + static_cast<long long>(j) * np + i] : R(0);
   }
   __syncthreads();
 
   // 2. residual r = b - A x (skipped for a zero initial guess: r = b)
-  const double cl = L.nu / 90.0, cb = -L.h / 18.0;
+  const R cl = R(L.nu / 90.0), cb = R(-L.h / 18.0);
   if (x != nullptr) {
     for (int t = tid; t < T::CW * T::CH; t += NT) {
       const int cy = t / T::CW, cx = t - cy * T::CW;
       const int I0 = RI0 + 2 * cx, J0 = RJ0 + 2 * cy;
-      const double* x0 = sx + (2 * cy + 2) * T::XW + (2 * cx + 2);
-      const double* pc = sp + (cy + 1) * T::PW + (cx + 1);  // vertex (I0/2, J0/2)
-      double* r0 = sr + (2 * cy) * T::RW + 2 * cx;
-      res_node<0, 0, TX, TY>(r0, x0, pc, I0, J0, L, x, cl, cb);
-      res_node<1, 0, TX, TY>(r0 + 1, x0 + 1, pc, I0 + 1, J0, L, x, cl, cb);
-      res_node<0, 1, TX, TY>(r0 + T::RW, x0 + T::XW, pc, I0, J0 + 1, L, x, cl, cb);
-      res_node<1, 1, TX, TY>(r0 + T::RW + 1, x0 + T::XW + 1, pc, I0 + 1, J0 + 1, L, x, cl, cb);
+      const R* x0 = sx + (2 * cy + 2) * T::XW + (2 * cx + 2);
+      const R* pc = sp + (cy + 1) * T::PW + (cx + 1);  // vertex (I0/2, J0/2)
+      R* r0 = sr + (2 * cy) * T::RW + 2 * cx;
+      res_node<R, 0, 0, TX, TY>(r0, x0, pc, I0, J0, L, x, cl, cb);
+      res_node<R, 1, 0, TX, TY>(r0 + 1, x0 + 1, pc, I0 + 1, J0, L, x, cl, cb);
+      res_node<R, 0, 1, TX, TY>(r0 + T::RW, x0 + T::XW, pc, I0, J0 + 1, L, x, cl, cb);
+      res_node<R, 1, 1, TX, TY>(r0 + T::RW + 1, x0 + T::XW + 1, pc, I0 + 1, J0 + 1, L, x, cl, cb);
     }
     for (int t = tid; t < T::SRP; t += NT) {
       const int jj = t / T::QW, ii = t - jj * T::QW;
       const int i = i0 - 1 + ii, j = j0 - 1 + jj;
       if (i < 0 || j < 0 || i > n || j > n) continue;
       // window of vertex (i, j): Q2 (2i + dI) - XI0 = 2 ii + 4 + dI
-      const double* xs0 = sx + (2 * jj + 4) * T::XW + (2 * ii + 4);
-      const double* xs1 = xs0 + T::XW * T::XH;
-      double s = 0.0;
+      const R* xs0 = sx + (2 * jj + 4) * T::XW + (2 * ii + 4);
+      const R* xs1 = xs0 + T::XW * T::XH;
+      R s = R(0);
 #pragma unroll
       for (int dJ = -2; dJ <= 2; ++dJ) {
 #pragma unroll
         for (int dI = -2; dI <= 2; ++dI) {
-          const double wx = crow(dI) * nrow(dJ), wy = nrow(dI) * crow(dJ);
-          if (wx != 0.0) s = fma(wx, xs0[dJ * T::XW + dI], s);
-          if (wy != 0.0) s = fma(wy, xs1[dJ * T::XW + dI], s);
+          const R wx = R(crow(dI) * nrow(dJ)), wy = R(nrow(dI) * crow(dJ));
+          if (wx != R(0)) s = fma(wx, xs0[dJ * T::XW + dI], s);
+          if (wy != R(0)) s = fma(wy, xs1[dJ * T::XW + dI], s);
         }
       }
       srp[t] -= cb * s;
@@ -249,8 +251,8 @@ __global__ void __launch_bounds__(NT) k_vanka_f64(LevelDev L, const double* __re
     const int pi = i0 - 1 + qi, pj = j0 - 1 + qj;
     if (pi < 0 || pj < 0 || pi > n || pj > n) continue;
     const int cls = 5 * axis_class(pj, n) + axis_class(pi, n);
-    const double* C = cd + cls * CD_STRIDE;
-    double ru[50];
+    const R* C = cd + cls * CD_STRIDE;
+    R ru[50];
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
@@ -258,17 +260,17 @@ __global__ void __launch_bounds__(NT) k_vanka_f64(LevelDev L, const double* __re
 #pragma unroll
         for (int wi = 0; wi < 5; ++wi)
           ru[c * 25 + wj * 5 + wi] = sr[c * T::RW * T::RH + (2 * qj + wj) * T::RW + 2 * qi + wi];
-    double zr = 0.0;
+    R zr = R(0);
 #pragma unroll
     for (int k = 0; k < 50; ++k) zr = fma(__ldg(C + CD_Z + k), ru[k], zr);
-    const double dp = (zr - srp[t]) * __ldg(C + CD_SINV);
-    double* D = sd + t * 51;
+    const R dp = (zr - srp[t]) * __ldg(C + CD_SINV);
+    R* D = sd + t * 51;
     if (cls == INTERIOR_CLASS) {
       // interior patch: K^-1 r_u by fast diagonalisation (exact up to rounding)
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        double y[25];
-        fd_solve(fdg, ru + c * 25, y);
+        R y[25];
+        fd_solve<R>(fdg, ru + c * 25, y);
 #pragma unroll
         for (int o = 0; o < 25; ++o) D[c * 25 + o] = fma(-__ldg(C + CD_Z + c * 25 + o), dp, y[o]);
       }
@@ -277,8 +279,8 @@ __global__ void __launch_bounds__(NT) k_vanka_f64(LevelDev L, const double* __re
       for (int c = 0; c < 2; ++c) {
 #pragma unroll 1
         for (int o = 0; o < 25; ++o) {
-          const double* Kr = C + CD_KINV + o * 25;
-          double acc = 0.0;
+          const R* Kr = C + CD_KINV + o * 25;
+          R acc = R(0);
 #pragma unroll
           for (int k = 0; k < 25; ++k) acc = fma(__ldg(Kr + k), ru[c * 25 + k], acc);
           D[c * 25 + o] = fma(-__ldg(C + CD_Z + c * 25 + o), dp, acc);
@@ -300,16 +302,16 @@ __global__ void __launch_bounds__(NT) k_vanka_f64(LevelDev L, const double* __re
       if (I < 0 || J < 0 || I >= nq || J >= nq) continue;
       const int pil = I < 2 ? 0 : (I - 1) / 2, pih = min(n, (I + 2) / 2);
       const int pjl = J < 2 ? 0 : (J - 1) / 2, pjh = min(n, (J + 2) / 2);
-      double acc = 0.0;
+      R acc = R(0);
       for (int pj = pjl; pj <= pjh; ++pj) {
         for (int pi = pil; pi <= pih; ++pi) {
           const int q = (pj - (j0 - 1)) * T::QW + (pi - (i0 - 1));
           acc += sd[q * 51 + c * 25 + (J - 2 * pj + 2) * 5 + (I - 2 * pi + 2)];
         }
       }
-      const double w = omega * inv_mult((pih - pil + 1) * (pjh - pjl + 1));
+      const R w = omega * inv_mult<R>((pih - pil + 1) * (pjh - pjl + 1));
       const long long k = c * nv + static_cast<long long>(J) * nq + I;
-      const double xold = x != nullptr ? x[k] : 0.0;
+      const R xold = x != nullptr ? x[k] : R(0);
       xo[k] = fma(w, acc, xold);
     } else {
       const int u = t - 2 * OW * OH;
@@ -318,48 +320,61 @@ __global__ void __launch_bounds__(NT) k_vanka_f64(LevelDev L, const double* __re
       if (i > n || j > n) continue;
       const int q = (vj + 1) * T::QW + (vi + 1);
       const long long k = 2 * nv + static_cast<long long>(j) * np + i;
-      const double xold = x != nullptr ? x[k] : 0.0;
+      const R xold = x != nullptr ? x[k] : R(0);
       xo[k] = fma(omega, sd[q * 51 + 50], xold);
     }
   }
 }
 
-template <int TX, int TY, int NT>
-void launch_t(const LevelDev& L, const double* cd, const FastDiag& fd, const double* x, const double* b,
-              double* xo, double omega, cudaStream_t s) {
+template <typename R, int TX, int TY, int NT>
+void launch_t(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
+              R omega, cudaStream_t s) {
   dim3 grid((L.np + TX - 1) / TX, (L.np + TY - 1) / TY);
-  k_vanka_f64<TX, TY, NT><<<grid, NT, VT<TX, TY>::TOTAL * sizeof(double), s>>>(L, cd, fd, x, b, xo,
-                                                                               omega);
+  k_vanka<R, TX, TY, NT><<<grid, NT, VT<TX, TY>::TOTAL * sizeof(R), s>>>(L, cd, fd, x, b, xo, omega);
 }
 
-template <int TX, int TY, int NT>
+template <typename R, int TX, int TY, int NT>
 cudaError_t prepare_t() {
-  return cudaFuncSetAttribute(k_vanka_f64<TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(VT<TX, TY>::TOTAL * sizeof(double)));
+  return cudaFuncSetAttribute(k_vanka<R, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(VT<TX, TY>::TOTAL * sizeof(R)));
+}
+
+template <typename R>
+cudaError_t prepare_all() {
+  cudaError_t e;
+  if ((e = prepare_t<R, 8, 8, 128>()) != cudaSuccess) return e;
+  if ((e = prepare_t<R, 16, 8, 192>()) != cudaSuccess) return e;
+  return prepare_t<R, 16, 16, 352>();
 }
 
 }  // namespace
 
-cudaError_t vanka_f64_prepare() {
-  cudaError_t e;
-  if ((e = prepare_t<8, 8, 128>()) != cudaSuccess) return e;
-  if ((e = prepare_t<16, 8, 192>()) != cudaSuccess) return e;
-  return prepare_t<16, 16, 352>();
+cudaError_t vanka_prepare() {
+  cudaError_t e = prepare_all<double>();
+  if (e != cudaSuccess) return e;
+  return prepare_all<float>();
 }
 
-void launch_vanka_f64(const LevelDev& L, const double* cd, const FastDiag& fd, const double* x,
-                      const double* b, double* xo, double omega, int cfg, cudaStream_t s) {
+template <typename R>
+void launch_vanka(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
+                  double omega, int cfg, cudaStream_t s) {
   count_launches(1);
+  const R w = R(omega);
   switch (cfg) {
-    case 1: launch_t<16, 8, 192>(L, cd, fd, x, b, xo, omega, s); break;
-    case 2: launch_t<16, 16, 352>(L, cd, fd, x, b, xo, omega, s); break;
-    default: launch_t<8, 8, 128>(L, cd, fd, x, b, xo, omega, s); break;
+    case 1: launch_t<R, 16, 8, 192>(L, cd, fd, x, b, xo, w, s); break;
+    case 2: launch_t<R, 16, 16, 352>(L, cd, fd, x, b, xo, w, s); break;
+    default: launch_t<R, 8, 8, 128>(L, cd, fd, x, b, xo, w, s); break;
   }
 }
 
-const char* vanka_f64_cfg_name(int cfg) {
-  static const char* names[VANKA_F64_NCFG] = {"8x8", "16x8", "16x16"};
-  return (cfg >= 0 && cfg < VANKA_F64_NCFG) ? names[cfg] : "?";
+template void launch_vanka<double>(const LevelDev&, const double*, const FastDiagT<double>&, const double*,
+                                   const double*, double*, double, int, cudaStream_t);
+template void launch_vanka<float>(const LevelDev&, const float*, const FastDiagT<float>&, const float*,
+                                  const float*, float*, double, int, cudaStream_t);
+
+const char* vanka_cfg_name(int cfg) {
+  static const char* names[VANKA_NCFG] = {"8x8", "16x8", "16x16"};
+  return (cfg >= 0 && cfg < VANKA_NCFG) ? names[cfg] : "?";
 }
 
 }  // namespace sv

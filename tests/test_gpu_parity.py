@@ -283,3 +283,53 @@ def test_adjoint_gradient(pkg):
     lam, grad, it, rr = H.adjoint(g)
     grad = host(grad).reshape(grad_o.shape)
     assert rel(grad, grad_o) <= 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Mixed-precision preconditioner (FP32 vectors, residuals and patch solves;
+# FGMRES and the coarse solve in FP64)
+# ---------------------------------------------------------------------------
+MIXED = {}
+
+
+def mixed_h(pkg, n, **kw):
+    from paper_2401_06277_gb300 import stokes
+    return gpu_h(pkg, n, prec=stokes.STOKES_MIXED_FP32, **kw)
+
+
+@pytest.mark.parametrize("n", [8, 32, 64])
+def test_mixed_vcycle_close_to_fp64(pkg, n):
+    """The FP32 V-cycle agrees with the FP64 oracle's V-cycle to FP32 rounding.
+
+    Bar 1e-4 relative to max |z|: FP32 unit roundoff (6e-8) amplified by the
+    cancellation in b - A x after the pre-sweeps (|A x| / |r| up to ~1e2) and
+    compounded over up to five levels.  The mixed form is held to the
+    solution bar (1e-7 after FP64 FGMRES to 1e-8), tested below."""
+    H = mixed_h(pkg, n)
+    Ho = oracle_h(n)
+    lv = Ho.levels[-1]
+    b = O.assemble_rhs(lv, si.random_force(n, 21), si.manufactured_velocity(n))
+    err = rel(host(H.vcycle(dev(b))), O.vcycle(Ho, b))
+    MIXED[("vcycle", n)] = err
+    assert err <= 1e-4, err
+
+
+@pytest.mark.parametrize("n", [16, 64])
+def test_mixed_fgmres_solution(pkg, n):
+    """FGMRES (FP64) with the FP32 preconditioner reaches the same 1e-8 residual; the
+    solution is within 1e-7 of the FP64 oracle's solution at the same tolerance."""
+    H = mixed_h(pkg, n)
+    Ho = oracle_h(n)
+    lv = Ho.levels[-1]
+    b = O.assemble_rhs(lv, si.random_force(n, 31), si.manufactured_velocity(n))
+    x, it, rr = H.solve(dev(b))
+    res = O.solve(Ho, b)
+    xg = O.normalize_pressure(lv, host(x))
+    xo = O.normalize_pressure(lv, res.x)
+    err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    MIXED[("fgmres", n)] = (err, it, res.iters)
+    assert rr <= 1e-8
+    r0 = np.linalg.norm(b - lv.A @ O.initial_guess(lv, b))
+    assert np.linalg.norm(b - lv.A @ host(x)) / r0 <= 1.01e-8
+    assert it <= res.iters + 2
+    assert err <= 1e-7, err
