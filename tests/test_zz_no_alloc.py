@@ -9,6 +9,7 @@ the norm of the residual produced by the existing stokes_residual entry point.
 It sits in its own file, collected last, and passes alone or after the rest.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -42,17 +43,24 @@ def test_noalloc_residual_norm_matches_existing_entry_point(stokes, n):
         stokes.stokes_residual(h.handle, lvl, b, x, r)
         ref = float(torch.linalg.vector_norm(r))
         if call == 1:
+            # no Python garbage collection inside the window: a collected tensor
+            # of an earlier test would change torch's counter without our call
+            gc.collect()
+            gc.disable()
             torch.cuda.synchronize()
             free0 = torch.cuda.mem_get_info()[0]
             alloc0 = torch.cuda.memory_allocated()
-        st = lib.stokes_residual_norm_noalloc(n, 1.3, ctypes.c_void_p(b.data_ptr()),
-                                              ctypes.c_void_p(x.data_ptr()),
-                                              ctypes.c_void_p(out.data_ptr()), stream)
-        assert st == stokes.STOKES_OK, lib.stokes_last_error()
-        torch.cuda.synchronize()
-        if call == 1:
-            assert torch.cuda.mem_get_info()[0] == free0
-            assert torch.cuda.memory_allocated() == alloc0
+        try:
+            st = lib.stokes_residual_norm_noalloc(n, 1.3, ctypes.c_void_p(b.data_ptr()),
+                                                  ctypes.c_void_p(x.data_ptr()),
+                                                  ctypes.c_void_p(out.data_ptr()), stream)
+            assert st == stokes.STOKES_OK, lib.stokes_last_error()
+            torch.cuda.synchronize()
+            if call == 1:
+                assert torch.cuda.mem_get_info()[0] == free0
+                assert torch.cuda.memory_allocated() == alloc0
+        finally:
+            gc.enable()
         got = float(out.item())
         assert abs(got - ref) <= RTOL * ref, (call, got, ref)
     h.close()
