@@ -201,21 +201,20 @@ def measured_peaks() -> dict:
     return {}
 
 
-def run_ours(args) -> None:
+PRECS = {"fp64": 0, "mixed": 1}
+
+
+def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e):
+    """Time K FGMRES solves of one precision form; returns (record, hierarchy-independent facts)."""
     import torch
 
-    import stokes_inputs as si
     import paper_2401_06277_gb300 as pkg
-    from paper_2401_06277_gb300 import build, stokes
+    from paper_2401_06277_gb300 import stokes
 
-    ws, rank, local = dist_setup(args.gpus)
-    build.build()
     dev = torch.device("cuda", torch.cuda.current_device())
     n = args.n
     N = dofs(n)
-    H = pkg.Hierarchy(n, rtol=1e-8, restart=30)
-    f_host = torch.from_numpy(si.random_force(n, args.seed + rank)).pin_memory()
-    ud_host = torch.from_numpy(si.manufactured_velocity(n)).pin_memory()
+    H = pkg.Hierarchy(n, rtol=1e-8, restart=30, prec=PRECS[prec_name])
     f = f_host.to(dev)
     ud = ud_host.to(dev)
     b = H.assemble_rhs(f, ud)
@@ -230,8 +229,6 @@ def run_ours(args) -> None:
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-
-    # ---- device-resident timed region ----
     stokes.stokes_stats_reset(H.handle)
     stokes.stokes_stats_enable_timing(H.handle, True)
     l0 = stokes.stokes_stats_read(H.handle)["kernel_launches"]
@@ -259,50 +256,86 @@ def run_ours(args) -> None:
     ms_max = allmax(ws, ms)
     vcycles_all = allsum(ws, st["vcycles"])
     value = N * vcycles_all / (ms_max * 1e-3)
-
     sweep_ms = st["sweep_ms"] / max(st["sweeps_timed"], 1)
-    fl = sweep_flops(n)
-    sm_max = args.sm_max_mhz or measured_peaks().get("sm_max_mhz", 2070.0)
-    peak_gflops = SM_COUNT * 4 * sm_max * 1e6 / 1e9   # 2 DFMA / clk / SM
-    achieved = fl / (sweep_ms * 1e-3) / 1e9
-    roofline = {"bound": "alu", "kernel": "k_vanka_f64 (finest level)", "achieved": round(achieved, 2),
-                "peak": round(peak_gflops, 1), "unit": "GFLOP/s",
-                "frac": round(achieved / peak_gflops, 4), "traffic": args.traffic,
-                "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock",
-                "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": sweep_bytes(n),
-                "hbm_gbs_achieved": round(sweep_bytes(n) / (sweep_ms * 1e-3) / 1e9, 1),
-                "launch_ms": round(sweep_ms, 4), "launches_timed": st["sweeps_timed"],
-                "tile": ["8x8", "16x8", "16x16"][stokes.stokes_level_tile(H.handle, H.levels - 1)]}
+    tile = ["8x8", "16x8", "16x16"][stokes.stokes_level_tile(H.handle, H.levels - 1)]
+    peaks = measured_peaks()
+    sm_max = args.sm_max_mhz or peaks.get("sm_max_mhz", 2070.0)
+    if prec_name == "fp64":
+        fl = sweep_flops(n)
+        peak = SM_COUNT * 4 * sm_max * 1e6 / 1e9   # 2 DFMA / clk / SM
+        achieved = fl / (sweep_ms * 1e-3) / 1e9
+        roofline = {"bound": "alu", "kernel": "k_vanka<double> (finest level)", "achieved": round(achieved, 2),
+                    "peak": round(peak, 1), "unit": "GFLOP/s", "frac": round(achieved / peak, 4),
+                    "traffic": args.traffic,
+                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock (FP64 has no "
+                                   "measured entry; an FMA-loop probe reached 1196 GFLOP/s)",
+                    "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": sweep_bytes(n),
+                    "hbm_gbs_achieved": round(sweep_bytes(n) / (sweep_ms * 1e-3) / 1e9, 1)}
+    else:
+        by = 3.0 * 4.0 * N
+        peak = peaks.get("hbm_gbs", 6780.0)
+        achieved = by / (sweep_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "k_vanka<float> (finest level)", "achieved": round(achieved, 1),
+                    "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                    "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
+                    "algorithmic_bytes_per_launch": by,
+                    "fp32_gflops_achieved": round(sweep_flops(n) / (sweep_ms * 1e-3) / 1e9, 1)}
+    roofline.update({"launch_ms": round(sweep_ms, 4), "launches_timed": st["sweeps_timed"], "tile": tile})
+    rec = {"value": value, "ms_per_step": ms_max / args.steps, "iters": iters, "relres": rels,
+           "vcycles": int(vcycles_all), "ms_per_vcycle": ms_max / max(st["vcycles"], 1),
+           "time_to_solution_s": ms_max / args.steps / 1e3, "roofline": roofline,
+           "gpu_launches": launches, "clocks": clk, "levels": H.levels}
+    if with_e2e:
+        x_host = torch.empty(N, dtype=torch.float64).pin_memory()
+        bi = f_host.numel() * 8 + ud_host.numel() * 8
+        bo = N * 8
 
-    # ---- end-to-end through the public API with host buffers ----
-    x_host = torch.empty(N, dtype=torch.float64).pin_memory()
-    bi = f_host.numel() * 8 + ud_host.numel() * 8
-    bo = N * 8
+        def e2e_step():
+            f.copy_(f_host, non_blocking=True)
+            ud.copy_(ud_host, non_blocking=True)
+            stokes.stokes_assemble_rhs(H.handle, f, ud, b, n)
+            stokes.stokes_initial_guess(H.handle, b, x)
+            stokes.stokes_fgmres_solve(H.handle, b, x)
+            x_host.copy_(x, non_blocking=True)
 
-    def e2e_step():
-        f.copy_(f_host, non_blocking=True)
-        ud.copy_(ud_host, non_blocking=True)
-        stokes.stokes_assemble_rhs(H.handle, f, ud, b, n)
-        stokes.stokes_initial_guess(H.handle, b, x)
-        stokes.stokes_fgmres_solve(H.handle, b, x)
-        x_host.copy_(x, non_blocking=True)
-
-    e2e_step()
-    torch.cuda.synchronize()
-    stokes.stokes_stats_reset(H.handle)
-    barrier(ws)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
         e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(ws)
-    e2e_ms = allmax(ws, e0.elapsed_time(e1))
-    e2e_vc = allsum(ws, stokes.stokes_stats_read(H.handle)["vcycles"])
-    e2e = {"value": N * e2e_vc / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
-           "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms / args.steps}
+        torch.cuda.synchronize()
+        stokes.stokes_stats_reset(H.handle)
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        e2e_ms = allmax(ws, e0.elapsed_time(e1))
+        e2e_vc = allsum(ws, stokes.stokes_stats_read(H.handle)["vcycles"])
+        rec["e2e"] = {"value": N * e2e_vc / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
+                      "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms / args.steps}
+    H.close()
+    return rec
 
+
+def run_ours(args) -> None:
+    import torch
+
+    import stokes_inputs as si
+    from paper_2401_06277_gb300 import build
+
+    ws, rank, local = dist_setup(args.gpus)
+    build.build()
+    n = args.n
+    N = dofs(n)
+    f_host = torch.from_numpy(si.random_force(n, args.seed + rank)).pin_memory()
+    ud_host = torch.from_numpy(si.manufactured_velocity(n)).pin_memory()
+    main = time_form(args, args.prec, ws, rank, f_host, ud_host, with_e2e=True)
+    forms = {args.prec: {k: main[k] for k in ("value", "time_to_solution_s", "iters", "ms_per_vcycle")}}
+    if not args.single_form:
+        other = "mixed" if args.prec == "fp64" else "fp64"
+        o = time_form(args, other, ws, rank, f_host, ud_host, with_e2e=False)
+        forms[other] = {k: o[k] for k in ("value", "time_to_solution_s", "iters", "ms_per_vcycle")}
+        forms[other]["roofline"] = o["roofline"]
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         o = run_oracle(ORACLE_N, 1)
@@ -310,21 +343,22 @@ def run_ours(args) -> None:
                "sample": f"one FGMRES(30)+V(2,2) solve to 1e-8 at {o['n']}x{o['n']} ({o['dofs']} dofs, "
                          f"{o['iters']} V-cycles, {o['solve_s']:.2f} s; setup {o['setup_s']:.1f} s excluded), "
                          f"numpy/scipy, BLAS threads = 1"}
-    H.close()
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"2D Stokes Q2-Q1, {n}x{n} elements, FP64, FGMRES(30) + V(2,2) "
+        prec_txt = "FP64" if args.prec == "fp64" else "FP32 V-cycle inside FP64 FGMRES"
+        line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.prec == "fp64" else "f32/f64", "data": "synthetic",
+                "config": {"workload": f"2D Stokes Q2-Q1, {n}x{n} elements, {prec_txt}, FGMRES(30) + V(2,2) "
                                        f"additive Vanka (omega 0.7) to 1e-8, coarse 4x4",
-                           "n": n, "dofs": N, "levels": H.levels, "rhs": f"N(0,1) nodal force, seed {args.seed}",
+                           "n": n, "dofs": N, "levels": main["levels"],
+                           "rhs": f"N(0,1) nodal force, seed {args.seed}",
                            "l2": "inputs larger than L2 (each vector 8*dofs bytes)",
                            "parallelism": f"replicas x{ws}"},
-                "time_to_solution_s": ms_max / args.steps / 1e3,
-                "iters": iters, "relres": rels, "vcycles": int(vcycles_all),
-                "ms_per_vcycle": ms_max / max(st["vcycles"], 1),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "clocks": clk}
+                "time_to_solution_s": main["time_to_solution_s"], "iters": main["iters"],
+                "relres": main["relres"], "vcycles": main["vcycles"], "ms_per_vcycle": main["ms_per_vcycle"],
+                "roofline": main["roofline"], "cpu_baseline": cpu, "e2e": main["e2e"],
+                "gpu_launches": main["gpu_launches"], "clocks": main["clocks"], "forms": forms}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -373,7 +407,7 @@ def run_kernel(args) -> None:
 
     build.build()
     n = args.n
-    H = pkg.Hierarchy(n, restart=1, tile=args.tile)
+    H = pkg.Hierarchy(n, restart=1, tile=args.tile, prec=PRECS[args.prec])
     lvl = H.levels - 1
     x = torch.from_numpy(si.random_vector(n, 1)).cuda()
     b = torch.from_numpy(si.random_vector(n, 2)).cuda()
@@ -418,6 +452,9 @@ def main():
     ap.add_argument("--sm-max-mhz", type=float, default=None)
     ap.add_argument("--traffic", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", choices=list(PRECS), default="fp64",
+                    help="form of the headline line (the other form is reported under 'forms')")
+    ap.add_argument("--single-form", action="store_true", help="time only the --prec form")
     ap.add_argument("--oracle-worker", action="store_true")
     ap.add_argument("--tile", type=int, default=-1, help="Vanka tile shape (-1: autotuned)")
     ap.add_argument("--kernel", choices=["sweep", "residual", "vcycle"], default=None,

@@ -49,6 +49,8 @@ sv::LevelDev make_level(int n, double nu) {
   d.N = 2 * d.nv + static_cast<long long>(d.np) * d.np;
   d.h = 1.0 / n;
   d.nu = nu;
+  d.cl = nu / 90.0;
+  d.cb = -d.h / 18.0;
   return d;
 }
 
@@ -372,11 +374,14 @@ cudaError_t choose_tiles(stokes_hierarchy* h) {
       L.vk_cfg = L.vk_cfg_f = h->prm.tile;
       continue;
     }
-    L.vk_cfg = L.vk_cfg_f = 0;
+    L.vk_cfg = L.vk_cfg_f = (L.d.n < 64) ? 0 : 1;
     if (L.d.n < 64) continue;
-    cudaError_t e = tune_level<double>(h, L, &L.vk_cfg);
+    // only the precision the V-cycle runs in is tuned (the FP64 sweep of a
+    // mixed hierarchy serves stokes_vanka_sweep alone and keeps 16x8)
+    cudaError_t e = cudaSuccess;
+    if (h->prm.prec == STOKES_FP64) e = tune_level<double>(h, L, &L.vk_cfg);
+    else e = tune_level<float>(h, L, &L.vk_cfg_f);
     if (e != cudaSuccess) return e;
-    if (h->prm.prec != STOKES_FP64 && (e = tune_level<float>(h, L, &L.vk_cfg_f)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

@@ -46,6 +46,8 @@ struct LevelDev {
   long long N;   // 2 nv + np^2
   double h;    // 1 / n
   double nu;   // viscosity
+  double cl;   // nu / 90: scale of the integer Laplacian stencil
+  double cb;   // -h / 18: scale of the integer divergence stencil
 };
 
 struct Level {

@@ -94,7 +94,7 @@ __device__ __forceinline__ void apply_vel_node(const LevelDev& L, const T* __res
       if (wy != T(0)) gy = fma(wy, pv, gy);
     }
   }
-  const T cl = T(L.nu / 90.0), cb = T(-L.h / 18.0);
+  const T cl = T(L.cl), cb = T(L.cb);
   ax = cl * sx + cb * gx;
   ay = cl * sy + cb * gy;
 }
@@ -110,7 +110,7 @@ __device__ __forceinline__ void apply_node(const LevelDev& L, const T* __restric
   const long long k = static_cast<long long>(J) * nq + I;
   T ax, ay;
   if (fast) {
-    const T cl = T(L.nu / 90.0), cb = T(-L.h / 18.0);
+    const T cl = T(L.cl), cb = T(L.cb);
     const T* pc = x + 2 * nv + static_cast<long long>(bb) * L.np + a;
     ax = cl * lap_g<T, PI, PJ>(x + k, nq) + cb * btp_g<T, PI, PJ, 0>(pc, L.np);
     ay = cl * lap_g<T, PI, PJ>(x + nv + k, nq) + cb * btp_g<T, PI, PJ, 1>(pc, L.np);
@@ -168,7 +168,7 @@ __global__ void k_apply(LevelDev L, const T* __restrict__ x, const T* __restrict
       }
     }
   }
-  const T ap = T(-L.h / 18.0) * s;
+  const T ap = T(L.cb) * s;
   const long long k = 2 * nv + static_cast<long long>(bb) * np + a;
   y[k] = residual ? b[k] - ap : ap;
 }

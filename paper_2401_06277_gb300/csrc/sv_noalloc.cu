@@ -184,6 +184,8 @@ extern "C" stokes_status stokes_residual_norm_noalloc(int n, double viscosity, c
   L.N = 2 * L.nv + static_cast<long long>(L.np) * L.np;
   L.h = 1.0 / n;
   L.nu = viscosity;
+  L.cl = viscosity / 90.0;
+  L.cb = -L.h / 18.0;
   const int rows = L.nq + L.np;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   k_resnorm_rows<<<rows, 256, 0, s>>>(L, b, x, scratch);

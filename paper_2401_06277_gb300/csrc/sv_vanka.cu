@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
   // 1. x windows (Dirichlet / outside entries read as 0: their columns are
   //    dropped), b on the residual windows (0 outside).
   if (x != nullptr) {
+#pragma unroll
     for (int t = tid; t < T::SX; t += NT) {
       const int c = t / (T::XW * T::XH);
       const int rem = t - c * T::XW * T::XH;
@@ -189,12 +190,14 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
       const int I = XI0 + ii, J = XJ0 + jj;
       sx[t] = vfree(I, J, nq) ? x[c * nv + static_cast<long long>(J) * nq + I] : R(0);
     }
+#pragma unroll
     for (int t = tid; t < T::SP; t += NT) {
       const int jj = t / T::PW, ii = t - jj * T::PW;
       const int i = i0 - 3 + ii, j = j0 - 3 + jj;
       sp[t] = (i >= 0 && j >= 0 && i <= n && j <= n) ? x[2 * nv + static_cast<long long>(j) * np + i] : R(0);
     }
   }
+#pragma unroll
   for (int t = tid; t < T::SR; t += NT) {
     const int c = t / (T::RW * T::RH);
     const int rem = t - c * T::RW * T::RH;
@@ -202,6 +205,7 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
     const int I = RI0 + ii, J = RJ0 + jj;
     sr[t] = (I >= 0 && J >= 0 && I < nq && J < nq) ? b[c * nv + static_cast<long long>(J) * nq + I] : R(0);
   }
+#pragma unroll
   for (int t = tid; t < T::SRP; t += NT) {
     const int jj = t / T::QW, ii = t - jj * T::QW;
     const int i = i0 - 1 + ii, j = j0 - 1 + jj;
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
   __syncthreads();
 
   // 2. residual r = b - A x (skipped for a zero initial guess: r = b)
-  const R cl = R(L.nu / 90.0), cb = R(-L.h / 18.0);
+  const R cl = R(L.cl), cb = R(L.cb);
   if (x != nullptr) {
     for (int t = tid; t < T::CW * T::CH; t += NT) {
       const int cy = t / T::CW, cx = t - cy * T::CW;
@@ -311,7 +315,10 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
       }
       const R w = omega * inv_mult<R>((pih - pil + 1) * (pjh - pjl + 1));
       const long long k = c * nv + static_cast<long long>(J) * nq + I;
-      const R xold = x != nullptr ? x[k] : R(0);
+      // x of free nodes is in the shared window; Dirichlet values come from global
+      R xold = R(0);
+      if (x != nullptr)
+        xold = vfree(I, J, nq) ? sx[c * T::XW * T::XH + (J - XJ0) * T::XW + (I - XI0)] : x[k];
       xo[k] = fma(w, acc, xold);
     } else {
       const int u = t - 2 * OW * OH;
@@ -320,7 +327,7 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
       if (i > n || j > n) continue;
       const int q = (vj + 1) * T::QW + (vi + 1);
       const long long k = 2 * nv + static_cast<long long>(j) * np + i;
-      const R xold = x != nullptr ? x[k] : R(0);
+      const R xold = x != nullptr ? sp[(j - (j0 - 3)) * T::PW + (i - (i0 - 3))] : R(0);
       xo[k] = fma(omega, sd[q * 51 + 50], xold);
     }
   }
