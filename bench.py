@@ -201,7 +201,7 @@ def measured_peaks() -> dict:
     return {}
 
 
-PRECS = {"fp64": 0, "mixed": 1}
+PRECS = {"fp64": 0, "mixed": 1, "bf16": 2}
 
 
 def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e):

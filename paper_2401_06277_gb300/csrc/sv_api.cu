@@ -68,6 +68,7 @@ void free_all(stokes_hierarchy* h) {
     cudaFree(L.rf);
     cudaFree(L.ef);
     cudaFree(L.cdf);
+    cudaFree(L.tcB);
   }
   h->lv.clear();
   cudaFree(h->coarse_G);
@@ -75,6 +76,8 @@ void free_all(stokes_hierarchy* h) {
   cudaFree(h->Z);
   cudaFree(h->small);
   cudaFree(h->partials);
+  cudaFree(h->dev_err);
+  h->dev_err = nullptr;
   if (h->host_scalars) cudaFreeHost(h->host_scalars);
   h->coarse_G = h->V = h->Z = h->small = h->partials = h->host_scalars = nullptr;
 }
@@ -125,7 +128,14 @@ void timed_sweep<float>(stokes_hierarchy* h, bool finest, sv::Level& L, const fl
                         float* xo) {
   cudaEvent_t* ev = timing_pair(h, finest);
   if (ev) cudaEventRecord(ev[0], h->stream);
-  sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, L.vk_cfg_f, h->stream);
+  if (L.tcB != nullptr && L.tc_hi >= L.tc_lo) {
+    // interior tiles on the tensor cores, the ring of boundary tiles on the SIMT kernel
+    sv::launch_vanka_tc(L.d, L.tcB, x, b, xo, h->prm.omega, L.tc_lo, L.tc_hi, h->dev_err, h->stream);
+    sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, sv::VANKA_CFG_14, h->stream, L.tc_lo,
+                            L.tc_hi);
+  } else {
+    sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, L.vk_cfg_f, h->stream);
+  }
   if (ev) cudaEventRecord(ev[1], h->stream);
 }
 
@@ -214,8 +224,13 @@ void precondition(stokes_hierarchy* h, const double* r, double* z) {
 stokes_status read_scalar(stokes_hierarchy* h, const double* dev, double* out) {
   SV_TRY(cudaMemcpyAsync(h->host_scalars, dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream),
          "copy scalar");
+  SV_TRY(cudaMemcpyAsync(h->host_scalars + 1, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+         "copy error flag");
   SV_TRY(cudaStreamSynchronize(h->stream), "stream sync");
   *out = h->host_scalars[0];
+  int flag = 0;
+  std::memcpy(&flag, h->host_scalars + 1, sizeof(int));
+  if (flag != 0) return fail(STOKES_ERR_TIMEOUT, "a bounded device wait expired in the tensor-core sweep");
   return STOKES_OK;
 }
 
@@ -380,6 +395,7 @@ cudaError_t choose_tiles(stokes_hierarchy* h) {
     // mixed hierarchy serves stokes_vanka_sweep alone and keeps 16x8)
     cudaError_t e = cudaSuccess;
     if (h->prm.prec == STOKES_FP64) e = tune_level<double>(h, L, &L.vk_cfg);
+    else if (L.tcB != nullptr && L.tc_hi >= L.tc_lo) L.vk_cfg_f = sv::VANKA_CFG_14;
     else e = tune_level<float>(h, L, &L.vk_cfg_f);
     if (e != cudaSuccess) return e;
   }
@@ -422,9 +438,9 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   if (prm.restart < 1 || prm.restart > 64) return fail(STOKES_ERR_ARG, "restart must be in 1..64");
   if (prm.nu1 < 0 || prm.nu2 < 0 || prm.maxit < 1 || !(prm.rtol >= 0.0) || !(prm.omega > 0.0))
     return fail(STOKES_ERR_ARG, "bad smoothing / iteration parameters");
-  if (prm.prec != STOKES_FP64 && prm.prec != STOKES_MIXED_FP32)
-    return fail(STOKES_ERR_ARG, "precision mode not available in this build");
-  if (prm.tile < -1 || prm.tile >= sv::VANKA_NCFG) return fail(STOKES_ERR_ARG, "tile must be -1..2");
+  if (prm.prec != STOKES_FP64 && prm.prec != STOKES_MIXED_FP32 && prm.prec != STOKES_MIXED_BF16)
+    return fail(STOKES_ERR_ARG, "unknown precision mode");
+  if (prm.tile < -1 || prm.tile >= sv::VANKA_NCFG) return fail(STOKES_ERR_ARG, "tile must be -1..3");
   std::vector<int> sizes;
   {
     int m = n;
@@ -448,6 +464,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   for (int k = 0; k < 4; ++k) h->fdf.so[k] = static_cast<float>(h->fd.so[k]);
   for (int k = 0; k < 25; ++k) h->fdf.dinv[k] = static_cast<float>(h->fd.dinv[k]);
   cudaError_t e = sv::vanka_prepare();
+  if (e == cudaSuccess && prm.prec == STOKES_MIXED_BF16) e = sv::vanka_tc_prepare();
   if (e != cudaSuccess) {
     delete h;
     return cuda_fail(e, "kernel attributes");
@@ -468,6 +485,15 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
     }
     sv::build_class_data(nl, viscosity, L.cd_host, &L.full_inv_host);
     e = cudaMemcpy(L.cd, L.cd_host.data(), L.cd_host.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && prm.prec == STOKES_MIXED_BF16) {
+      sv::tc_interior_range(nl, &L.tc_lo, &L.tc_hi);
+      if (L.tc_hi >= L.tc_lo) {
+        std::vector<unsigned short> img(64 * 64);
+        sv::tc_pack_inverse(L.full_inv_host.data() + static_cast<size_t>(sv::INTERIOR_CLASS) * 51 * 51, img.data());
+        if ((e = cudaMalloc(&L.tcB, img.size() * sizeof(unsigned short))) == cudaSuccess)
+          e = cudaMemcpy(L.tcB, img.data(), img.size() * sizeof(unsigned short), cudaMemcpyHostToDevice);
+      }
+    }
     if (e == cudaSuccess && prm.prec != STOKES_FP64) {
       std::vector<float> cdf(L.cd_host.begin(), L.cd_host.end());
       if ((e = dalloc(&L.xf0, N)) == cudaSuccess && (e = dalloc(&L.xf1, N)) == cudaSuccess &&
@@ -502,6 +528,8 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   if ((e = dalloc(&h->V, Nf * (h->m + 1))) != cudaSuccess || (e = dalloc(&h->Z, Nf * h->m)) != cudaSuccess ||
       (e = dalloc(&h->small, small_size(h->m))) != cudaSuccess ||
       (e = dalloc(&h->partials, static_cast<size_t>(h->npart) * 64)) != cudaSuccess ||
+      (e = dalloc(&h->dev_err, 1)) != cudaSuccess ||
+      (e = cudaMemset(h->dev_err, 0, sizeof(int))) != cudaSuccess ||
       (e = cudaMallocHost(reinterpret_cast<void**>(&h->host_scalars), 8 * sizeof(double))) != cudaSuccess) {
     free_all(h);
     delete h;
@@ -519,7 +547,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
 stokes_status stokes_level_tile(const stokes_hierarchy* h, int level, int* tile) {
   stokes_status st = check_level(h, level);
   if (st != STOKES_OK) return st;
-  if (tile) *tile = h->lv[level].vk_cfg;
+  if (tile) *tile = (h->prm.prec == STOKES_FP64) ? h->lv[level].vk_cfg : h->lv[level].vk_cfg_f;
   return STOKES_OK;
 }
 

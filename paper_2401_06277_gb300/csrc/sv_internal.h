@@ -67,6 +67,9 @@ struct Level {
   float* ef = nullptr;
   float* cdf = nullptr;   // class data in FP32
   int vk_cfg_f = 0;       // tile shape of the FP32 sweep on this level
+  // tensor-core sweep (prec == STOKES_MIXED_BF16): interior tile range, BF16 inverse image
+  int tc_lo = 1, tc_hi = 0;
+  void* tcB = nullptr;
   std::vector<double> cd_host;
   std::vector<double> full_inv_host;  // NCLASS * 51 * 51 dense inverses (host)
 };
@@ -91,6 +94,7 @@ struct stokes_hierarchy {
   double* partials = nullptr;    // dot-product partial sums
   int npart = 0;                 // blocks of the dot kernels
   double* host_scalars = nullptr;  // pinned host mirror of a few scalars
+  int* dev_err = nullptr;          // set by kernels whose bounded waits expired
   // measurement
   bool timing = false;
   long long vcycles = 0;
@@ -127,11 +131,26 @@ void launch_apply(const LevelDev& L, const T* x, const T* b, T* y, int residual,
 void launch_rhs(const LevelDev& L, const double* f, const double* ud, double* b, cudaStream_t s);
 void launch_rhs_transpose(const LevelDev& L, const double* lam, double* g, cudaStream_t s);
 // Fused Vanka sweep (sv_vanka.cu, R = double or float); cfg selects the tile
-// shape (8x8, 16x8, 16x16 vertices)
-constexpr int VANKA_NCFG = 3;
+// shape (8x8, 16x8, 16x16, 14x14 vertices).  Tiles (bx, by) with both indices
+// in [skip_lo, skip_hi] are left to the tensor-core kernel (empty by default).
+constexpr int VANKA_NCFG = 4;
+constexpr int VANKA_CFG_14 = 3;
 template <typename R>
 void launch_vanka(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
-                  double omega, int cfg, cudaStream_t s);
+                  double omega, int cfg, cudaStream_t s, int skip_lo = 1, int skip_hi = 0);
+
+// Tensor-core sweep (sv_vanka_tc.cu, FP32 vectors, BF16 tcgen05 patch GEMM):
+// sweeps the 14 x 14 tiles [lo, hi]^2 whose patches are all of the interior
+// class; the remaining tiles go to launch_vanka<float> with cfg 14x14 and
+// skip range [lo, hi].  Bcanon: the interior inverse, 64 x 64 BF16 in the
+// core-matrix layout (8 KB).  err: set to 1 if a bounded device wait expired.
+constexpr int TC_TILE = 14;
+void tc_interior_range(int n, int* lo, int* hi);
+void launch_vanka_tc(const LevelDev& L, const void* Bcanon, const float* x, const float* b, float* xo,
+                     double omega, int lo, int hi, int* err, cudaStream_t s);
+cudaError_t vanka_tc_prepare();
+// 64 x 64 BF16 core-matrix image (uint16 bits) of a 51 x 51 row-major inverse
+void tc_pack_inverse(const double* inv51, unsigned short* out4096);
 const char* vanka_cfg_name(int cfg);
 template <typename T>
 void launch_restrict(const LevelDev& F, const LevelDev& C, const T* rf, T* rc, cudaStream_t s);

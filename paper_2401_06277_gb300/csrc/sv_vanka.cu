@@ -24,76 +24,15 @@
 
 #include "sv_internal.h"
 #include "sv_stencil.cuh"
+#include "sv_vanka_common.cuh"
 
 namespace sv {
 namespace {
 
-__device__ __forceinline__ bool vfree(int I, int J, int nq) {
-  return I > 0 && J > 0 && I < nq - 1 && J < nq - 1;
-}
-
-template <int TX, int TY>
-struct VT {
-  static constexpr int XW = 2 * TX + 12, XH = 2 * TY + 12;  // x, Q2 nodes, origin 2 i0 - 6
-  static constexpr int PW = TX + 6, PH = TY + 6;            // x, vertices,  origin i0 - 3
-  static constexpr int CW = TX + 4, CH = TY + 4;            // residual cells, origin 2 i0 - 4
-  static constexpr int RW = 2 * CW, RH = 2 * CH;            // residual, Q2 nodes
-  static constexpr int QW = TX + 2, QH = TY + 2;            // patches, origin i0 - 1
-  static constexpr int NPATCH = QW * QH;
-  static constexpr int SX = 2 * XW * XH, SP = PW * PH, SR = 2 * RW * RH, SRP = NPATCH;
-  static constexpr int SD = NPATCH * 51;
-  static constexpr int TOTAL = SX + SP + SR + SRP + SD;
-};
-
-// sum of nu (K (x) M + M (x) K) x / (nu/90) over the stencil of a node with
-// parities (PI, PJ); xs points at the node in the x window.
-template <typename T, int PI, int PJ, int XW>
-__device__ __forceinline__ T lap(const T* xs) {
-  T s = T(0);
-#pragma unroll
-  for (int dJ = -2; dJ <= 2; ++dJ) {
-#pragma unroll
-    for (int dI = -2; dI <= 2; ++dI) {
-      const T c = T(k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ));
-      if (c != T(0)) s = fma(c, xs[dJ * XW + dI], s);
-    }
-  }
-  return s;
-}
-
-// (B^T p) / (-h/18) for velocity component COMP at a node with parities
-// (PI, PJ) of the cell whose vertex is (a, b); pc points at p(a, b).
-template <typename T, int PI, int PJ, int COMP, int PW>
-__device__ __forceinline__ T btp(const T* pc) {
-  T g = T(0);
-#pragma unroll
-  for (int dj = -1; dj <= 1; ++dj) {
-#pragma unroll
-    for (int di = -1; di <= 1; ++di) {
-      const T w = T(COMP == 0 ? ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj)
-                              : ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj));
-      if (w != T(0)) g = fma(w, pc[dj * PW + di], g);
-    }
-  }
-  return g;
-}
-
-template <typename T, int PI, int PJ, int TX, int TY>
-__device__ __forceinline__ void res_node(T* sr, const T* x0, const T* pc, int I, int J,
-                                         const LevelDev& L, const T* __restrict__ x, T cl, T cb) {
-  using V = VT<TX, TY>;
-  const int nq = L.nq;
-  if (I < 0 || J < 0 || I >= nq || J >= nq) return;  // outside: r stays 0
-  if (!vfree(I, J, nq)) {                            // Dirichlet row: r = b - x
-    const long long k = static_cast<long long>(J) * nq + I;
-    sr[0] -= x[k];
-    sr[V::RW * V::RH] -= x[L.nv + k];
-    return;
-  }
-  const T* x1 = x0 + V::XW * V::XH;
-  sr[0] -= cl * lap<T, PI, PJ, V::XW>(x0) + cb * btp<T, PI, PJ, 0, V::PW>(pc);
-  sr[V::RW * V::RH] -= cl * lap<T, PI, PJ, V::XW>(x1) + cb * btp<T, PI, PJ, 1, V::PW>(pc);
-}
+using vk::VT;
+using vk::vfree;
+using vk::res_node;
+using vk::inv_mult;
 
 // Forward transform of one 5-vector into the generalised eigenbasis S^T v
 // (three symmetric, two antisymmetric eigenvectors; 4 add/sub + 13 FMA/MUL).
@@ -149,23 +88,16 @@ __device__ __forceinline__ void fd_solve(const FastDiagT<T>& f, const T* r, T* y
   for (int wj = 0; wj < 5; ++wj) fd_inv(f, Tm + wj * 5, y + wj * 5);
 }
 
-template <typename T>
-__device__ __forceinline__ T inv_mult(int m) {
-  switch (m) {
-    case 1: return T(1.0);
-    case 2: return T(0.5);
-    case 3: return T(1.0 / 3.0);
-    case 4: return T(0.25);
-    case 6: return T(1.0 / 6.0);
-    default: return T(1.0 / 9.0);
-  }
-}
-
 template <typename R, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ cd,
                                               const FastDiagT<R> fdg, const R* __restrict__ x,
-                                              const R* __restrict__ b, R* __restrict__ xo, R omega) {
+                                              const R* __restrict__ b, R* __restrict__ xo, R omega,
+                                              int skip_lo, int skip_hi) {
   using T = VT<TX, TY>;
+  // tiles inside [skip_lo, skip_hi]^2 are swept by the tensor-core kernel
+  if (static_cast<int>(blockIdx.x) >= skip_lo && static_cast<int>(blockIdx.x) <= skip_hi &&
+      static_cast<int>(blockIdx.y) >= skip_lo && static_cast<int>(blockIdx.y) <= skip_hi)
+    return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sx = reinterpret_cast<R*>(smem_raw);
   R* sp = sx + T::SX;
@@ -335,9 +267,10 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
 
 template <typename R, int TX, int TY, int NT>
 void launch_t(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
-              R omega, cudaStream_t s) {
+              R omega, int skip_lo, int skip_hi, cudaStream_t s) {
   dim3 grid((L.np + TX - 1) / TX, (L.np + TY - 1) / TY);
-  k_vanka<R, TX, TY, NT><<<grid, NT, VT<TX, TY>::TOTAL * sizeof(R), s>>>(L, cd, fd, x, b, xo, omega);
+  k_vanka<R, TX, TY, NT><<<grid, NT, VT<TX, TY>::TOTAL * sizeof(R), s>>>(L, cd, fd, x, b, xo, omega,
+                                                                         skip_lo, skip_hi);
 }
 
 template <typename R, int TX, int TY, int NT>
@@ -351,7 +284,8 @@ cudaError_t prepare_all() {
   cudaError_t e;
   if ((e = prepare_t<R, 8, 8, 128>()) != cudaSuccess) return e;
   if ((e = prepare_t<R, 16, 8, 192>()) != cudaSuccess) return e;
-  return prepare_t<R, 16, 16, 352>();
+  if ((e = prepare_t<R, 16, 16, 352>()) != cudaSuccess) return e;
+  return prepare_t<R, 14, 14, 256>();
 }
 
 }  // namespace
@@ -364,23 +298,24 @@ cudaError_t vanka_prepare() {
 
 template <typename R>
 void launch_vanka(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
-                  double omega, int cfg, cudaStream_t s) {
+                  double omega, int cfg, cudaStream_t s, int skip_lo, int skip_hi) {
   count_launches(1);
   const R w = R(omega);
   switch (cfg) {
-    case 1: launch_t<R, 16, 8, 192>(L, cd, fd, x, b, xo, w, s); break;
-    case 2: launch_t<R, 16, 16, 352>(L, cd, fd, x, b, xo, w, s); break;
-    default: launch_t<R, 8, 8, 128>(L, cd, fd, x, b, xo, w, s); break;
+    case 1: launch_t<R, 16, 8, 192>(L, cd, fd, x, b, xo, w, skip_lo, skip_hi, s); break;
+    case 2: launch_t<R, 16, 16, 352>(L, cd, fd, x, b, xo, w, skip_lo, skip_hi, s); break;
+    case 3: launch_t<R, 14, 14, 256>(L, cd, fd, x, b, xo, w, skip_lo, skip_hi, s); break;
+    default: launch_t<R, 8, 8, 128>(L, cd, fd, x, b, xo, w, skip_lo, skip_hi, s); break;
   }
 }
 
 template void launch_vanka<double>(const LevelDev&, const double*, const FastDiagT<double>&, const double*,
-                                   const double*, double*, double, int, cudaStream_t);
+                                   const double*, double*, double, int, cudaStream_t, int, int);
 template void launch_vanka<float>(const LevelDev&, const float*, const FastDiagT<float>&, const float*,
-                                  const float*, float*, double, int, cudaStream_t);
+                                  const float*, float*, double, int, cudaStream_t, int, int);
 
 const char* vanka_cfg_name(int cfg) {
-  static const char* names[VANKA_NCFG] = {"8x8", "16x8", "16x16"};
+  static const char* names[VANKA_NCFG] = {"8x8", "16x8", "16x16", "14x14"};
   return (cfg >= 0 && cfg < VANKA_NCFG) ? names[cfg] : "?";
 }
 

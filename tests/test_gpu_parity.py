@@ -333,3 +333,48 @@ def test_mixed_fgmres_solution(pkg, n):
     assert np.linalg.norm(b - lv.A @ host(x)) / r0 <= 1.01e-8
     assert it <= res.iters + 2
     assert err <= 1e-7, err
+
+
+# ---------------------------------------------------------------------------
+# BF16 tensor-core form (interior patch solves as tcgen05 GEMMs, FP32 vectors)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [32, 64, 128])
+def test_bf16_vcycle_close_to_fp64(pkg, n):
+    """BF16 patch GEMMs: the V-cycle agrees with the FP64 oracle's to BF16 rounding.
+
+    Bar 1e-2 relative to max |z|: BF16 keeps 8 significant bits (unit roundoff
+    2^-9 = 2e-3) in both the gathered residuals and the patch inverse, the
+    products are accumulated in FP32."""
+    from paper_2401_06277_gb300 import stokes
+    H = gpu_h(pkg, n, prec=stokes.STOKES_MIXED_BF16)
+    Ho = oracle_h(n)
+    lv = Ho.levels[-1]
+    b = O.assemble_rhs(lv, si.random_force(n, 21), si.manufactured_velocity(n))
+    err = rel(host(H.vcycle(dev(b))), O.vcycle(Ho, b))
+    assert err <= 1e-2, err
+
+
+@pytest.mark.parametrize("n", [64, 128])
+def test_bf16_fgmres_solution(pkg, n):
+    """FGMRES (FP64) with the BF16 tensor-core preconditioner: same 1e-8 residual,
+    solution within 1e-7 of the FP64 oracle's at the same tolerance."""
+    from paper_2401_06277_gb300 import stokes
+    H = gpu_h(pkg, n, prec=stokes.STOKES_MIXED_BF16)
+    Ho = oracle_h(n)
+    lv = Ho.levels[-1]
+    b = O.assemble_rhs(lv, si.random_force(n, 41), si.manufactured_velocity(n))
+    x, it, rr = H.solve(dev(b))
+    res = O.solve(Ho, b)
+    xg = O.normalize_pressure(lv, host(x))
+    xo = O.normalize_pressure(lv, res.x)
+    assert rr <= 1e-8 and it <= res.iters + 2
+    r0 = np.linalg.norm(b - lv.A @ O.initial_guess(lv, b))
+    assert np.linalg.norm(b - lv.A @ host(x)) / r0 <= 1.01e-8
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-7
+
+
+def test_bf16_uses_the_tensor_core_kernel(pkg):
+    """At 128^2 the finest level has interior tiles: the ring runs the 14x14 SIMT tile."""
+    from paper_2401_06277_gb300 import stokes
+    H = gpu_h(pkg, 128, prec=stokes.STOKES_MIXED_BF16)
+    assert stokes.stokes_level_tile(H.handle, H.levels - 1) == 3
