@@ -257,7 +257,7 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e):
     vcycles_all = allsum(ws, st["vcycles"])
     value = N * vcycles_all / (ms_max * 1e-3)
     sweep_ms = st["sweep_ms"] / max(st["sweeps_timed"], 1)
-    tile = ["8x8", "16x8", "16x16"][stokes.stokes_level_tile(H.handle, H.levels - 1)]
+    tile = ["8x8", "16x8", "16x16", "14x14"][stokes.stokes_level_tile(H.handle, H.levels - 1)]
     peaks = measured_peaks()
     sm_max = args.sm_max_mhz or peaks.get("sm_max_mhz", 2070.0)
     if prec_name == "fp64":
@@ -433,7 +433,7 @@ def run_kernel(args) -> None:
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     rec = {"kernel": args.kernel, "n": n, "ms": ms,
-           "tile": ["8x8", "16x8", "16x16"][stokes.stokes_level_tile(H.handle, lvl)]}
+           "tile": ["8x8", "16x8", "16x16", "14x14"][stokes.stokes_level_tile(H.handle, lvl)]}
     if fl:
         rec["gflops"] = fl / (ms * 1e-3) / 1e9
         rec["gbs"] = by / (ms * 1e-3) / 1e9

@@ -260,43 +260,76 @@ __global__ void k_rhs_transpose(LevelDev L, const double* __restrict__ lam, doub
 
 // ---------------------------------------------------------------------------
 // Restriction r_c = P^T r_f and prolongation x_f += P e_c (FE interpolation,
-// Dirichlet rows of P (fine) and columns (coarse) zero).
-// 1D Q2 weights: coarse node C even: fine 2C + {-3:-1/8, -1:3/8, 0:1, 1:3/8, 3:-1/8};
-// C odd: fine 2C + {-1:3/4, 0:1, 1:3/4}.  Q1: fine 2c + {-1:1/2, 0:1, 1:1/2}.
+// Dirichlet rows of P (fine) and columns (coarse) zero).  In 1D a fine Q2
+// node 2G coincides with coarse node G (weight 1); an odd fine node
+// 4e+1 / 4e+3 inside coarse element e takes the coarse quadratic at t = 1/4 /
+// 3/4: weights (3/8, 3/4, -1/8) / (-1/8, 3/4, 3/8) on coarse nodes 2e..2e+2.
+// Q1: fine vertex 2g <- coarse g; 2g+1 <- (1/2, 1/2) on g, g+1.  All weights
+// are computed in registers (no tables).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double rq2(int C, int off) {
-  if (C & 1) return off == 0 ? 1.0 : ((off == 1 || off == -1) ? 0.75 : 0.0);
-  switch (off) {
-    case 0: return 1.0;
-    case 1: case -1: return 0.375;
-    case 3: case -3: return -0.125;
-    default: return 0.0;
+
+// coarse nodes and weights feeding fine Q2 node F on one axis; returns the count (1 or 3)
+__device__ __forceinline__ int q2_interp(int F, int nc, int* G, double* w) {
+  if ((F & 1) == 0) {
+    G[0] = F >> 1;
+    w[0] = 1.0;
+    return 1;
   }
+  int e = F >> 2;
+  if (e > nc - 1) e = nc - 1;
+  const bool first = (F - 4 * e) == 1;
+  G[0] = 2 * e;
+  G[1] = 2 * e + 1;
+  G[2] = 2 * e + 2;
+  w[0] = first ? 0.375 : -0.125;
+  w[1] = 0.75;
+  w[2] = first ? -0.125 : 0.375;
+  return 3;
 }
-__device__ __forceinline__ double rq1(int off) {
-  return off == 0 ? 1.0 : ((off == 1 || off == -1) ? 0.5 : 0.0);
+
+// fine Q2 nodes fed by coarse Q2 node G on one axis (the transpose); returns the count (1, 3 or 5)
+__device__ __forceinline__ int q2_restrict(int G, int* F, double* w) {
+  if (G & 1) {  // coarse element midpoint: fine nodes 2G-1, 2G, 2G+1
+    F[0] = 2 * G - 1;
+    F[1] = 2 * G;
+    F[2] = 2 * G + 1;
+    w[0] = 0.75;
+    w[1] = 1.0;
+    w[2] = 0.75;
+    return 3;
+  }
+  F[0] = 2 * G - 3;  // coarse vertex: fine 2G-3, 2G-1, 2G, 2G+1, 2G+3
+  F[1] = 2 * G - 1;
+  F[2] = 2 * G;
+  F[3] = 2 * G + 1;
+  F[4] = 2 * G + 3;
+  w[0] = -0.125;
+  w[1] = 0.375;
+  w[2] = 1.0;
+  w[3] = 0.375;
+  w[4] = -0.125;
+  return 5;
 }
 
 template <typename T>
 __global__ void k_restrict(LevelDev F, LevelDev C, const T* __restrict__ rf, T* __restrict__ rc) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
-  // velocity part over the coarse Q2 grid, pressure over the coarse vertices
   if (I < C.nq && J < C.nq) {
     const long long k = static_cast<long long>(J) * C.nq + I;
     T sx = T(0), sy = T(0);
     if (is_free(I, J, C.nq)) {
-      for (int dJ = -3; dJ <= 3; ++dJ) {
-        const double wJ = rq2(J, dJ);
-        const int FJ = 2 * J + dJ;
-        if (wJ == 0.0 || !(FJ > 0 && FJ < F.nq - 1)) continue;
-        for (int dI = -3; dI <= 3; ++dI) {
-          const double wI = rq2(I, dI);
-          const int FI = 2 * I + dI;
-          if (wI == 0.0 || !(FI > 0 && FI < F.nq - 1)) continue;
-          const long long kf = static_cast<long long>(FJ) * F.nq + FI;
-          sx = fma(T(wI * wJ), rf[kf], sx);
-          sy = fma(T(wI * wJ), rf[F.nv + kf], sy);
+      int FI[5], FJ[5];
+      double wI[5], wJ[5];
+      const int ni = q2_restrict(I, FI, wI), nj = q2_restrict(J, FJ, wJ);
+      for (int b = 0; b < nj; ++b) {
+        if (FJ[b] <= 0 || FJ[b] >= F.nq - 1) continue;
+        for (int a = 0; a < ni; ++a) {
+          if (FI[a] <= 0 || FI[a] >= F.nq - 1) continue;
+          const long long kf = static_cast<long long>(FJ[b]) * F.nq + FI[a];
+          const T w = T(wI[a] * wJ[b]);
+          sx = fma(w, rf[kf], sx);
+          sy = fma(w, rf[F.nv + kf], sy);
         }
       }
     }
@@ -311,22 +344,12 @@ __global__ void k_restrict(LevelDev F, LevelDev C, const T* __restrict__ rf, T* 
       for (int di = -1; di <= 1; ++di) {
         const int fi = 2 * I + di;
         if (fi < 0 || fi >= F.np) continue;
-        s = fma(T(rq1(di) * rq1(dj)), rf[2 * F.nv + static_cast<long long>(fj) * F.np + fi], s);
+        const T w = T((di == 0 ? 1.0 : 0.5) * (dj == 0 ? 1.0 : 0.5));
+        s = fma(w, rf[2 * F.nv + static_cast<long long>(fj) * F.np + fi], s);
       }
     }
     rc[2 * C.nv + static_cast<long long>(J) * C.np + I] = s;
   }
-}
-
-// weights of the coarse element's local nodes at fine local position k/4 (Q2) or k/2 (Q1)
-__device__ __forceinline__ double pq2(int k, int a) {
-  // rows k = 0..4 (t = k/4), columns a = 0..2
-  const double W[5][3] = {{1.0, 0.0, 0.0},
-                          {0.375, 0.75, -0.125},
-                          {0.0, 1.0, 0.0},
-                          {-0.125, 0.75, 0.375},
-                          {0.0, 0.0, 1.0}};
-  return W[k][a];
 }
 
 template <typename T>
@@ -334,20 +357,18 @@ __global__ void k_prolong_add(LevelDev F, LevelDev C, const T* __restrict__ ec, 
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   if (I < F.nq && J < F.nq && is_free(I, J, F.nq)) {
-    const int ex = min(I / 4, C.n - 1), ey = min(J / 4, C.n - 1);
-    const int kx = I - 4 * ex, ky = J - 4 * ey;
+    int GI[3], GJ[3];
+    double wI[3], wJ[3];
+    const int ni = q2_interp(I, C.n, GI, wI), nj = q2_interp(J, C.n, GJ, wJ);
     T sx = T(0), sy = T(0);
-    for (int b = 0; b < 3; ++b) {
-      const double wy = pq2(ky, b);
-      const int CJ = 2 * ey + b;
-      if (wy == 0.0 || CJ <= 0 || CJ >= C.nq - 1) continue;  // coarse Dirichlet row
-      for (int a = 0; a < 3; ++a) {
-        const double wx = pq2(kx, a);
-        const int CI = 2 * ex + a;
-        if (wx == 0.0 || !is_free(CI, CJ, C.nq)) continue;
-        const long long kc = static_cast<long long>(CJ) * C.nq + CI;
-        sx = fma(T(wx * wy), ec[kc], sx);
-        sy = fma(T(wx * wy), ec[C.nv + kc], sy);
+    for (int b = 0; b < nj; ++b) {
+      if (GJ[b] <= 0 || GJ[b] >= C.nq - 1) continue;  // coarse Dirichlet row
+      for (int a = 0; a < ni; ++a) {
+        if (GI[a] <= 0 || GI[a] >= C.nq - 1) continue;
+        const long long kc = static_cast<long long>(GJ[b]) * C.nq + GI[a];
+        const T w = T(wI[a] * wJ[b]);
+        sx = fma(w, ec[kc], sx);
+        sy = fma(w, ec[C.nv + kc], sy);
       }
     }
     const long long k = static_cast<long long>(J) * F.nq + I;
@@ -355,18 +376,14 @@ __global__ void k_prolong_add(LevelDev F, LevelDev C, const T* __restrict__ ec, 
     xf[F.nv + k] += sy;
   }
   if (I < F.np && J < F.np) {
-    const int ex = min(I / 2, C.n - 1), ey = min(J / 2, C.n - 1);
-    const int kx = I - 2 * ex, ky = J - 2 * ey;
-    T s = T(0);
-    for (int b = 0; b < 2; ++b) {
-      const double wy = (b == 0) ? (1.0 - 0.5 * ky) : 0.5 * ky;
-      if (wy == 0.0) continue;
-      for (int a = 0; a < 2; ++a) {
-        const double wx = (a == 0) ? (1.0 - 0.5 * kx) : 0.5 * kx;
-        if (wx == 0.0) continue;
-        s = fma(T(wx * wy), ec[2 * C.nv + static_cast<long long>(ey + b) * C.np + (ex + a)], s);
-      }
-    }
+    // fine vertex (I, J) <- coarse vertices (I/2 .. (I+1)/2, J/2 .. (J+1)/2), weights 1 or 1/2 per axis
+    const int i0 = I >> 1, i1 = (I + 1) >> 1, j0 = J >> 1, j1 = (J + 1) >> 1;
+    const T wi = (I & 1) ? T(0.5) : T(1.0), wj = (J & 1) ? T(0.5) : T(1.0);
+    const T* p = ec + 2 * C.nv;
+    T s = wi * wj * p[static_cast<long long>(j0) * C.np + i0];
+    if (I & 1) s = fma(wi * wj, p[static_cast<long long>(j0) * C.np + i1], s);
+    if (J & 1) s = fma(wi * wj, p[static_cast<long long>(j1) * C.np + i0], s);
+    if ((I & 1) && (J & 1)) s = fma(wi * wj, p[static_cast<long long>(j1) * C.np + i1], s);
     xf[2 * F.nv + static_cast<long long>(J) * F.np + I] += s;
   }
 }

@@ -94,10 +94,27 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
                                               const R* __restrict__ b, R* __restrict__ xo, R omega,
                                               int skip_lo, int skip_hi) {
   using T = VT<TX, TY>;
-  // tiles inside [skip_lo, skip_hi]^2 are swept by the tensor-core kernel
-  if (static_cast<int>(blockIdx.x) >= skip_lo && static_cast<int>(blockIdx.x) <= skip_hi &&
-      static_cast<int>(blockIdx.y) >= skip_lo && static_cast<int>(blockIdx.y) <= skip_hi)
-    return;
+  // With a non-empty [skip_lo, skip_hi] the tensor-core kernel sweeps the tiles
+  // in that square and this launch enumerates the ring of tiles around it
+  // (1-D grid: rows below, the left/right parts of the middle rows, rows above).
+  int bx = blockIdx.x, by = blockIdx.y;
+  if (skip_hi >= skip_lo) {
+    const int gx = (L.np + TX - 1) / TX;
+    const int w = skip_hi - skip_lo + 1, mid_row = gx - w;
+    const int idx = blockIdx.x, n_bottom = skip_lo * gx, n_mid = w * mid_row;
+    if (idx < n_bottom) {
+      by = idx / gx;
+      bx = idx - by * gx;
+    } else if (idx < n_bottom + n_mid) {
+      const int k = idx - n_bottom, row = k / mid_row, c = k - row * mid_row;
+      by = skip_lo + row;
+      bx = c < skip_lo ? c : c + w;
+    } else {
+      const int k = idx - n_bottom - n_mid;
+      by = skip_hi + 1 + k / gx;
+      bx = k - (k / gx) * gx;
+    }
+  }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sx = reinterpret_cast<R*>(smem_raw);
   R* sp = sx + T::SX;
@@ -106,7 +123,7 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
   R* sd = srp + T::SRP;
   const int n = L.n, nq = L.nq, np = L.np;
   const long long nv = L.nv;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int i0 = bx * TX, j0 = by * TY;
   const int tid = threadIdx.x;
   const int XI0 = 2 * i0 - 6, XJ0 = 2 * j0 - 6;
   const int RI0 = 2 * i0 - 4, RJ0 = 2 * j0 - 4;
@@ -154,10 +171,7 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
       const R* x0 = sx + (2 * cy + 2) * T::XW + (2 * cx + 2);
       const R* pc = sp + (cy + 1) * T::PW + (cx + 1);  // vertex (I0/2, J0/2)
       R* r0 = sr + (2 * cy) * T::RW + 2 * cx;
-      res_node<R, 0, 0, TX, TY>(r0, x0, pc, I0, J0, L, x, cl, cb);
-      res_node<R, 1, 0, TX, TY>(r0 + 1, x0 + 1, pc, I0 + 1, J0, L, x, cl, cb);
-      res_node<R, 0, 1, TX, TY>(r0 + T::RW, x0 + T::XW, pc, I0, J0 + 1, L, x, cl, cb);
-      res_node<R, 1, 1, TX, TY>(r0 + T::RW + 1, x0 + T::XW + 1, pc, I0 + 1, J0 + 1, L, x, cl, cb);
+      vk::res_cell<R, TX, TY>(r0, x0, pc, I0, J0, L, x, cl, cb);
     }
     for (int t = tid; t < T::SRP; t += NT) {
       const int jj = t / T::QW, ii = t - jj * T::QW;
@@ -268,7 +282,12 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
 template <typename R, int TX, int TY, int NT>
 void launch_t(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
               R omega, int skip_lo, int skip_hi, cudaStream_t s) {
-  dim3 grid((L.np + TX - 1) / TX, (L.np + TY - 1) / TY);
+  const int gx = (L.np + TX - 1) / TX, gy = (L.np + TY - 1) / TY;
+  dim3 grid(gx, gy);
+  if (skip_hi >= skip_lo) {  // ring of tiles around the tensor-core square only
+    const int w = skip_hi - skip_lo + 1;
+    grid = dim3(gx * gy - w * w, 1);
+  }
   k_vanka<R, TX, TY, NT><<<grid, NT, VT<TX, TY>::TOTAL * sizeof(R), s>>>(L, cd, fd, x, b, xo, omega,
                                                                          skip_lo, skip_hi);
 }

@@ -76,6 +76,66 @@ __device__ __forceinline__ void res_node(T* sr, const T* x0, const T* pc, int I,
   sr[V::RW * V::RH] -= cl * lap<T, PI, PJ, V::XW>(x1) + cb * btp<T, PI, PJ, 1, V::PW>(pc);
 }
 
+// Residual of the 2x2 cell of Q2 nodes (I0..I0+1) x (J0..J0+1) (I0, J0 even),
+// both components.  When all four nodes are free, the 6x6 x neighbourhood of
+// each component and the 3x3 pressures are loaded into registers once and the
+// four stencils read them there; otherwise the per-node path handles the
+// Dirichlet rows.  r0 / x0 point at (I0, J0) in the residual / x windows of
+// component 0, pc at the pressure of vertex (I0/2, J0/2).
+template <typename T, int TX, int TY>
+__device__ __forceinline__ void res_cell(T* r0, const T* x0, const T* pc, int I0, int J0, const LevelDev& L,
+                                         const T* __restrict__ x, T cl, T cb) {
+  using V = VT<TX, TY>;
+  const int nq = L.nq;
+  if (I0 >= 1 && J0 >= 1 && I0 + 1 <= nq - 2 && J0 + 1 <= nq - 2) {
+    T P[3][3];
+#pragma unroll
+    for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+      for (int di = 0; di < 3; ++di) P[dj][di] = pc[(dj - 1) * V::PW + (di - 1)];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const T* xc = x0 + c * V::XW * V::XH;
+      T X[6][6];
+#pragma unroll
+      for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int bcol = 0; bcol < 6; ++bcol) X[a][bcol] = xc[(a - 2) * V::XW + (bcol - 2)];
+#pragma unroll
+      for (int PJ = 0; PJ < 2; ++PJ) {
+#pragma unroll
+        for (int PI = 0; PI < 2; ++PI) {
+          T sl = T(0);
+#pragma unroll
+          for (int dJ = -2; dJ <= 2; ++dJ) {
+#pragma unroll
+            for (int dI = -2; dI <= 2; ++dI) {
+              const T cf = T(k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ));
+              if (cf != T(0)) sl = fma(cf, X[PJ + dJ + 2][PI + dI + 2], sl);
+            }
+          }
+          T g = T(0);
+#pragma unroll
+          for (int dj = -1; dj <= 1; ++dj) {
+#pragma unroll
+            for (int di = -1; di <= 1; ++di) {
+              const T w = T(c == 0 ? ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj)
+                                   : ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj));
+              if (w != T(0)) g = fma(w, P[dj + 1][di + 1], g);
+            }
+          }
+          r0[c * V::RW * V::RH + PJ * V::RW + PI] -= cl * sl + cb * g;
+        }
+      }
+    }
+    return;
+  }
+  res_node<T, 0, 0, TX, TY>(r0, x0, pc, I0, J0, L, x, cl, cb);
+  res_node<T, 1, 0, TX, TY>(r0 + 1, x0 + 1, pc, I0 + 1, J0, L, x, cl, cb);
+  res_node<T, 0, 1, TX, TY>(r0 + V::RW, x0 + V::XW, pc, I0, J0 + 1, L, x, cl, cb);
+  res_node<T, 1, 1, TX, TY>(r0 + V::RW + 1, x0 + V::XW + 1, pc, I0 + 1, J0 + 1, L, x, cl, cb);
+}
+
 template <typename T>
 __device__ __forceinline__ T inv_mult(int m) {
   switch (m) {

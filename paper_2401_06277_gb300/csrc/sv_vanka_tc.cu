@@ -20,12 +20,11 @@
 //      matrix, LBO = 128 B along K, SBO = 1024 B along M);
 //   4. thread 0 issues 2 x 4 tcgen05.mma (kind::f16, M=128, N=64, K=16) into
 //      TMEM and commits them to an mbarrier;
-//   5. after the wait, warps read D back with tcgen05.ld (thread = patch row)
-//      and scatter the weighted corrections in nine colour phases (patches of
-//      equal colour (i mod 3, j mod 3) have disjoint windows), so the sums are
-//      deterministic, into a shared accumulator that reuses the residual
-//      buffer;
-//   6. x_out = x + (omega / m_j) * accumulated correction for the owned dofs.
+//   5. after the wait, each thread reads its patch row of D with tcgen05.ld and
+//      stores the 51 corrections in shared memory (over the dead R, B and
+//      residual buffers);
+//   6. x_out = x + (omega / m_j) * sum of the corrections of the patches that
+//      hold the dof, summed in a fixed order (deterministic, no atomics).
 // Every wait is bounded; on expiry the kernel sets *err, waits (bounded) for
 // its bulk copy, frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -42,7 +41,7 @@ namespace sv {
 namespace {
 
 using vk::inv_mult;
-using vk::res_node;
+using vk::res_cell;
 using vk::VT;
 using vk::vfree;
 
@@ -50,16 +49,20 @@ constexpr int TC_NT = 256;
 using TT = VT<TC_TILE, TC_TILE>;
 static_assert(TT::NPATCH == TC_NT, "one thread per patch");
 
-// shared-memory layout (bytes)
+// shared-memory layout (bytes).  The correction array D (256 x 51 FP32,
+// 52,224 B) overlays A, B, the residual and the pressure residual, which are
+// all dead once the MMAs have completed; the x windows stay live for x_old.
 constexpr int OFF_A = 0;                                   // 256 x 64 BF16 = 32 KB
 constexpr int OFF_B = OFF_A + 256 * 64 * 2;                // 64 x 64 BF16 = 8 KB
-constexpr int OFF_X = OFF_B + 64 * 64 * 2;                 // x window (FP32)
-constexpr int OFF_P = OFF_X + TT::SX * 4;                  // p window
-constexpr int OFF_R = OFF_P + TT::SP * 4;                  // residual / accumulator
+constexpr int OFF_R = OFF_B + 64 * 64 * 2;                 // residual (FP32)
 constexpr int OFF_RP = OFF_R + TT::SR * 4;                 // pressure residual
-constexpr int OFF_BAR = OFF_RP + TT::SRP * 4;              // two mbarriers
+constexpr int OFF_X = OFF_RP + TT::SRP * 4;                // x window
+constexpr int OFF_P = OFF_X + TT::SX * 4;                  // p window
+constexpr int OFF_BAR = OFF_P + TT::SP * 4;                // two mbarriers
 constexpr int OFF_TMEM = OFF_BAR + 16;                     // TMEM base address
 constexpr int SMEM_BYTES = OFF_TMEM + 16;
+constexpr int OFF_D = 0;                                   // corrections, after the MMAs
+static_assert(OFF_D + TT::NPATCH * 51 * 4 <= OFF_X, "corrections overlay only dead buffers");
 static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
 
 constexpr uint32_t TMEM_COLS = 128;
@@ -193,11 +196,7 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
       const float* x0 = sx + (2 * cy + 2) * TT::XW + (2 * cx + 2);
       const float* pc = sp + (cy + 1) * TT::PW + (cx + 1);
       float* r0 = sr + (2 * cy) * TT::RW + 2 * cx;
-      res_node<float, 0, 0, TC_TILE, TC_TILE>(r0, x0, pc, I0, J0, L, x, cl, cb);
-      res_node<float, 1, 0, TC_TILE, TC_TILE>(r0 + 1, x0 + 1, pc, I0 + 1, J0, L, x, cl, cb);
-      res_node<float, 0, 1, TC_TILE, TC_TILE>(r0 + TT::RW, x0 + TT::XW, pc, I0, J0 + 1, L, x, cl, cb);
-      res_node<float, 1, 1, TC_TILE, TC_TILE>(r0 + TT::RW + 1, x0 + TT::XW + 1, pc, I0 + 1, J0 + 1, L, x,
-                                              cl, cb);
+      res_cell<float, TC_TILE, TC_TILE>(r0, x0, pc, I0, J0, L, x, cl, cb);
     }
     {
       const int jj = tid / TT::QW, ii = tid - jj * TT::QW;
@@ -284,47 +283,50 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   if (ok) {
-    // 5. accumulate the corrections in colour phases (accumulator = residual buffer)
-    for (int t = tid; t < TT::SR; t += TC_NT) sr[t] = 0.0f;
-    __syncthreads();
-    const int pi = i0 - 1 + qi, pj = j0 - 1 + qj;
-    const int color = (pi % 3) + 3 * (pj % 3);
+    // 5. this thread's row of D -> shared corrections (thread = patch)
+    float* sd = reinterpret_cast<float*>(sm + OFF_D);
     const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + 64 * (warp >> 2);
-    for (int c = 0; c < 9; ++c) {
+    float d[64];
 #pragma unroll
-      for (int ch = 0; ch < 4; ++ch) {
-        float v[16];
-        tmem_ld16(taddr + 16 * ch, v);
-        if (color == c) {
+    for (int ch = 0; ch < 4; ++ch) tmem_ld16(taddr + 16 * ch, d + 16 * ch);
+    __syncthreads();  // every thread is done with R, B and the residual before they are overwritten
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int k = 16 * ch + j;
-            if (k < 50) {
-              const int comp = k / 25, w = k - 25 * comp;
-              sr[comp * TT::RW * TT::RH + (2 * qj + w / 5) * TT::RW + 2 * qi + (w % 5)] += v[j];
-            } else if (k == 50 && qi >= 1 && qi <= TC_TILE && qj >= 1 && qj <= TC_TILE) {
-              // pressure: one patch per dof (m = 1); owned vertex (pi, pj)
-              const long long kp = 2 * nv + static_cast<long long>(pj) * np + pi;
-              const float xold = x != nullptr ? sp[(pj - (j0 - 3)) * TT::PW + (pi - (i0 - 3))] : 0.0f;
-              xo[kp] = fmaf(omega, v[j], xold);
+    for (int k = 0; k < 51; ++k) sd[tid * 51 + k] = d[k];
+    __syncthreads();
+    // 6. weighted update of the owned dofs: one thread per owned vertex (vi, vj);
+    //    its Q2 nodes (2i-1..2i) x (2j-1..2j) take the corrections of the 9 / 6 /
+    //    6 / 4 patches around them at compile-time offsets (patch q + dq, slot s).
+    if (tid < TC_TILE * TC_TILE) {
+      const int vj = tid / TC_TILE, vi = tid - vj * TC_TILE;
+      const int i = i0 + vi, j = j0 + vj;
+      const float* dq = sd + ((vj + 1) * TT::QW + (vi + 1)) * 51;  // the vertex's own patch
+      const float* xs = sx + (2 * j - XJ0) * TT::XW + (2 * i - XI0);  // x window at node (2i, 2j)
+      const long long base = static_cast<long long>(2 * j) * nq + 2 * i;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+#pragma unroll
+        for (int nj = 0; nj < 2; ++nj) {      // node J = 2j - nj
+#pragma unroll
+          for (int ni = 0; ni < 2; ++ni) {    // node I = 2i - ni
+            float acc = 0.0f;
+            // patches (i + di, j + dj): di in {-1, 0, +1} for an even node, {-1, 0} for an odd one
+#pragma unroll
+            for (int dj = -1; dj <= 1; ++dj) {
+#pragma unroll
+              for (int di = -1; di <= 1; ++di) {
+                if ((ni == 1 && di == 1) || (nj == 1 && dj == 1)) continue;
+                const int wi = 2 - ni - 2 * di, wj = 2 - nj - 2 * dj;  // window offsets of the node
+                acc += dq[(dj * TT::QW + di) * 51 + c * 25 + wj * 5 + wi];
+              }
             }
+            const float w = omega * (ni ? 0.5f : (1.0f / 3.0f)) * (nj ? 0.5f : (1.0f / 3.0f));
+            const float xold = x != nullptr ? xs[c * TT::XW * TT::XH - nj * TT::XW - ni] : 0.0f;
+            xo[c * nv + base - static_cast<long long>(nj) * nq - ni] = fmaf(w, acc, xold);
           }
         }
       }
-      __syncthreads();
-    }
-    // 6. weighted update of the owned velocity dofs
-    constexpr int OW = 2 * TC_TILE, OH = 2 * TC_TILE;
-    for (int t = tid; t < 2 * OW * OH; t += TC_NT) {
-      const int c = t / (OW * OH);
-      const int rem = t - c * OW * OH;
-      const int oj = rem / OW, oi = rem - oj * OW;
-      const int I = 2 * i0 - 1 + oi, J = 2 * j0 - 1 + oj;
-      const int mx = (I & 1) ? 2 : 3, my = (J & 1) ? 2 : 3;
-      const float w = omega * inv_mult<float>(mx * my);
-      const float acc = sr[c * TT::RW * TT::RH + (J - RJ0) * TT::RW + (I - RI0)];
-      const float xold = x != nullptr ? sx[c * TT::XW * TT::XH + (J - XJ0) * TT::XW + (I - XI0)] : 0.0f;
-      xo[c * nv + static_cast<long long>(J) * nq + I] = fmaf(w, acc, xold);
+      const float xoldp = x != nullptr ? sp[(j - (j0 - 3)) * TT::PW + (i - (i0 - 3))] : 0.0f;
+      xo[2 * nv + static_cast<long long>(j) * np + i] = fmaf(omega, dq[50], xoldp);
     }
   } else if (tid == 0) {
     // the bulk copy and the MMAs may still be in flight: wait (bounded) before leaving
