@@ -157,11 +157,14 @@ stokes_status stokes_vcycle_apply(stokes_hierarchy* h, const double* r, double* 
 stokes_status stokes_fgmres_solve(stokes_hierarchy* h, const double* b, double* x, int* iters,
                                   double* relres);
 
-/* Adjoint solve A^T lambda = g (A is symmetric, so the same FGMRES + MG solve
- * with zero initial guess), then grad_f = R^T lambda where R maps nodal body
- * forces to right-hand sides (b = R f + lifting): grad_f[c, J, I] =
- * sum over free velocity rows k of M_(k),(I,J) lambda_k.  g has length N(n),
- * lambda length N(n), grad_f length 2 (2n+1)^2.  grad_f may be NULL. */
+/* Adjoint solve A^T lambda = g (A is symmetric, so the same FGMRES + MG solve),
+ * then grad_f = R^T lambda where R maps nodal body forces to right-hand sides
+ * (b = R f + lifting): grad_f[c, J, I] = sum over free velocity rows k of
+ * M_(k),(I,J) lambda_k.  A is singular with kernel (0, 1_p), so the pressure
+ * block of g is first shifted to zero mean (its component along the kernel of
+ * A^T removed); losses that ignore the pressure constant have such g already.
+ * lambda starts from g on Dirichlet rows and 0 elsewhere.  g has length N(n),
+ * lambda length N(n), grad_f length 2 (2n+1)^2 (may be NULL).  Synchronises. */
 stokes_status stokes_solve_adjoint(stokes_hierarchy* h, const double* g, double* lambda,
                                    double* grad_f, int* iters, double* relres);
 

@@ -5,3 +5,4 @@ include/stokes_vanka.h); this package only marshals arguments.
 """
 from .stokes import *  # noqa: F401,F403
 from .stokes import Hierarchy, StokesError, library_path, vec_len  # noqa: F401
+from .autograd import StokesSolve, stokes_solve  # noqa: F401

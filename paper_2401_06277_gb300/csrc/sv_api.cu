@@ -78,6 +78,8 @@ void free_all(stokes_hierarchy* h) {
   cudaFree(h->partials);
   cudaFree(h->dev_err);
   h->dev_err = nullptr;
+  cudaFree(h->aux);
+  h->aux = nullptr;
   if (h->host_scalars) cudaFreeHost(h->host_scalars);
   h->coarse_G = h->V = h->Z = h->small = h->partials = h->host_scalars = nullptr;
 }
@@ -528,7 +530,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   if ((e = dalloc(&h->V, Nf * (h->m + 1))) != cudaSuccess || (e = dalloc(&h->Z, Nf * h->m)) != cudaSuccess ||
       (e = dalloc(&h->small, small_size(h->m))) != cudaSuccess ||
       (e = dalloc(&h->partials, static_cast<size_t>(h->npart) * 64)) != cudaSuccess ||
-      (e = dalloc(&h->dev_err, 1)) != cudaSuccess ||
+      (e = dalloc(&h->dev_err, 1)) != cudaSuccess || (e = dalloc(&h->aux, Nf)) != cudaSuccess ||
       (e = cudaMemset(h->dev_err, 0, sizeof(int))) != cudaSuccess ||
       (e = cudaMallocHost(reinterpret_cast<void**>(&h->host_scalars), 8 * sizeof(double))) != cudaSuccess) {
     free_all(h);
@@ -695,12 +697,18 @@ stokes_status stokes_fgmres_solve(stokes_hierarchy* h, const double* b, double* 
 stokes_status stokes_solve_adjoint(stokes_hierarchy* h, const double* g, double* lambda, double* grad_f,
                                    int* iters, double* relres) {
   if (!h || !g || !lambda) return fail(STOKES_ERR_ARG, "null argument");
+  if (g == lambda) return fail(STOKES_ERR_ARG, "g and lambda must not alias");
+  g_err.clear();
+  sv::Level& F = h->lv.back();
+  // A^T = A is singular with kernel (0, 1_p): remove the component of g along it
+  double* sc = h->small + (h->m + 1) * h->m + 6 * h->m + 3;
+  sv::launch_project_pressure(F.d, g, h->aux, h->partials, h->npart, sc, h->stream);
   // initial guess: zero on free rows, g on Dirichlet rows (A has identity rows there)
-  sv::launch_dirichlet_copy(h->lv.back().d, g, lambda, h->stream);
-  stokes_status st = fgmres(h, g, lambda, iters, relres);
+  sv::launch_dirichlet_copy(F.d, h->aux, lambda, h->stream);
+  stokes_status st = fgmres(h, h->aux, lambda, iters, relres);
   if (st != STOKES_OK) return st;
   if (grad_f) {
-    sv::launch_rhs_transpose(h->lv.back().d, lambda, grad_f, h->stream);
+    sv::launch_rhs_transpose(F.d, lambda, grad_f, h->stream);
     return check_launch("rhs_transpose");
   }
   return STOKES_OK;

@@ -95,6 +95,7 @@ struct stokes_hierarchy {
   int npart = 0;                 // blocks of the dot kernels
   double* host_scalars = nullptr;  // pinned host mirror of a few scalars
   int* dev_err = nullptr;          // set by kernels whose bounded waits expired
+  double* aux = nullptr;           // finest-level vector: the projected adjoint right-hand side
   // measurement
   bool timing = false;
   long long vcycles = 0;
@@ -180,6 +181,10 @@ void launch_fill(double* p, double v, long long N, cudaStream_t s);
 void launch_set_scalar(double* p, const double* src_sqrt, cudaStream_t s);
 // a[k] += b[k], k < n (small device arrays)
 void launch_add_small(double* a, const double* b, int n, cudaStream_t s);
+// y = x with its pressure block shifted to zero (Euclidean) mean: the component
+// of x along ker A^T = (0, 1_p) is removed, so y is a consistent right-hand side
+void launch_project_pressure(const LevelDev& L, const double* x, double* y, double* partials, int npart,
+                             double* sum, cudaStream_t s);
 // dst = src on Dirichlet velocity rows, 0 elsewhere
 void launch_dirichlet_copy(const LevelDev& L, const double* src, double* dst, cudaStream_t s);
 

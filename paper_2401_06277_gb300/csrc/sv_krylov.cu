@@ -164,6 +164,33 @@ __global__ void k_dirichlet_copy(LevelDev L, const double* __restrict__ src, dou
   }
 }
 
+// partials[b] = sum over this block's elements of x (deterministic two-stage sum with k_reduce)
+__global__ void __launch_bounds__(DOT_NT) k_partial_sum(const double* __restrict__ x, long long N,
+                                                        double* __restrict__ partials) {
+  double acc = 0.0;
+  for (long long i = blockIdx.x * static_cast<long long>(DOT_NT) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * DOT_NT)
+    acc += x[i];
+  acc = warp_sum(acc);
+  __shared__ double red[DOT_NT / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < DOT_NT / 32; ++q) s += red[q];
+    partials[blockIdx.x] = s;
+  }
+}
+
+// y = x, with the pressure block shifted by -(*sum)/np2 (zero mean)
+__global__ void k_copy_shift_pressure(const double* __restrict__ x, double* __restrict__ y, long long N,
+                                      long long p0, const double* __restrict__ sum, double inv_np2) {
+  const double m = *sum * inv_np2;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    y[i] = (i >= p0) ? x[i] - m : x[i];
+}
+
 int grid_for(long long N, int nt) {
   long long b = (N + nt - 1) / nt;
   if (b > 152 * 8) b = 152 * 8;
@@ -223,6 +250,15 @@ void launch_set_scalar(double* p, const double* src_sqrt, cudaStream_t s) {
 void launch_add_small(double* a, const double* b, int n, cudaStream_t s) {
   count_launches(1);
   k_add_small<<<1, 64, 0, s>>>(a, b, n);
+}
+
+void launch_project_pressure(const LevelDev& L, const double* x, double* y, double* partials, int npart,
+                             double* sum, cudaStream_t s) {
+  count_launches(3);
+  const long long p0 = 2 * L.nv, np2 = static_cast<long long>(L.np) * L.np;
+  k_partial_sum<<<npart, DOT_NT, 0, s>>>(x + p0, np2, partials);
+  k_reduce<<<1, 256, 0, s>>>(partials, npart, sum, 0);
+  k_copy_shift_pressure<<<grid_for(L.N, 256), 256, 0, s>>>(x, y, L.N, p0, sum, 1.0 / static_cast<double>(np2));
 }
 
 void launch_dirichlet_copy(const LevelDev& L, const double* src, double* dst, cudaStream_t s) {
