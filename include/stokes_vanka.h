@@ -177,6 +177,29 @@ stokes_status stokes_rhs_transpose(stokes_hierarchy* h, const double* lambda, do
 stokes_status stokes_batched_solve(stokes_hierarchy* const* hs, int nprob, const double* const* b,
                                    double* const* x, int* iters, double* relres);
 
+/* A batch of independent problems (grid sizes may differ), e.g. many
+ * right-hand sides on one grid or a set of uneven grids, solved together:
+ * FGMRES (Section 6.8) runs in lockstep over the problems, and iteration j of
+ * all of them -- each problem's V-cycle (Algorithm 1, Algorithm 3), operator,
+ * Arnoldi and Givens rotation -- is one CUDA graph with one independent branch
+ * per problem, captured at the first solve and replayed (re-captured only when
+ * the set of unconverged problems changes).  The host synchronises once per
+ * iteration to read every residual estimate.  Each problem owns a hierarchy
+ * (params shared; tile shapes tuned once per grid size) on a stream of its
+ * own; stokes_batch_hierarchy gives access to it (e.g. for
+ * stokes_assemble_rhs).  stream: the caller's stream, synchronised when a
+ * solve starts.  n: nprob grid sizes. */
+typedef struct stokes_batch stokes_batch;
+stokes_status stokes_batch_create(int nprob, const int* n, double viscosity, const stokes_params* params,
+                                  void* stream, stokes_batch** out);
+stokes_status stokes_batch_destroy(stokes_batch* b);
+stokes_status stokes_batch_hierarchy(stokes_batch* b, int k, stokes_hierarchy** out);
+/* Solve problem k for rhs[k] into x[k] (x[k] holds x0 on entry, as in
+ * stokes_fgmres_solve).  iters / relres: nprob entries each (may be NULL).
+ * Returns STOKES_NOT_CONVERGED if any problem reached maxit.  Synchronises. */
+stokes_status stokes_batch_solve(stokes_batch* b, const double* const* rhs, double* const* x, int* iters,
+                                 double* relres);
+
 /* Counters for measurement (the paper reports per-kernel runtimes, Section 6.2,
  * and roofline positions, Section 6.7).  When timing is enabled the library
  * records a CUDA-event pair on its stream around every finest-level Vanka

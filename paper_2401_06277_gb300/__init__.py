@@ -4,5 +4,5 @@ The compute path is the CUDA library ``_lib/libstokes_vanka.so`` (C ABI in
 include/stokes_vanka.h); this package only marshals arguments.
 """
 from .stokes import *  # noqa: F401,F403
-from .stokes import Hierarchy, StokesError, library_path, vec_len  # noqa: F401
+from .stokes import Batch, Hierarchy, StokesError, library_path, vec_len  # noqa: F401
 from .autograd import StokesSolve, stokes_solve  # noqa: F401

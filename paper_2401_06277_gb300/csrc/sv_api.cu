@@ -257,34 +257,83 @@ SmallBuf small_layout(stokes_hierarchy* h) {
 // H ((m+1) m), g (m+1), cs (m), sn (m), hcol (m+1), h2 (m+1), y (m), 8 scalars
 size_t small_size(int m) { return static_cast<size_t>((m + 1) * m + 6 * m + 3 + 8); }
 
-// ||v||^2 into dev scalar, then the host value of ||v||
-stokes_status norm_host(stokes_hierarchy* h, const double* v, long long N, double* dev2, double* out) {
-  sv::launch_multidot(v, N, 1, v, N, h->partials, h->npart, dev2, 0, h->stream);
-  stokes_status st = check_launch("norm");
-  if (st != STOKES_OK) return st;
-  double v2;
-  st = read_scalar(h, dev2, &v2);
-  if (st != STOKES_OK) return st;
-  *out = std::sqrt(v2);
-  return STOKES_OK;
-}
 
-stokes_status fgmres(stokes_hierarchy* h, const double* b, double* x, int* iters_out,
-                     double* relres_out) {
-  cudaStream_t s = h->stream;
+}  // namespace
+
+// ---- FGMRES(m), right-preconditioned (Section 6.8), as stream-ordered pieces ----
+// The pieces launch on h->stream and never synchronise, so a batch can run
+// them on many streams and capture iterations into CUDA graphs.
+namespace sv {
+
+double* fg_scalars(stokes_hierarchy* h) { return small_layout(h).sc; }
+
+// V_0 = b - A x, sc[0] = ||V_0||^2
+void fg_residual(stokes_hierarchy* h, const double* b, const double* x) {
   sv::Level& F = h->lv.back();
   const long long N = F.d.N;
+  SmallBuf sb = small_layout(h);
+  sv::launch_apply<double>(F.d, x, b, h->V, 1, h->stream);
+  sv::launch_multidot(h->V, N, 1, h->V, N, h->partials, h->npart, sb.sc, 0, h->stream);
+}
+
+// V_0 /= beta, g = beta e_1 (beta known on the host)
+void fg_start_cycle(stokes_hierarchy* h, double beta) {
+  const long long N = h->lv.back().d.N;
+  SmallBuf sb = small_layout(h);
+  sv::launch_scale(h->V, h->V, nullptr, 1.0 / beta, N, h->stream);
+  sv::launch_fill(sb.g, 0.0, h->m + 1, h->stream);
+  sv::launch_fill(sb.g, beta, 1, h->stream);
+}
+
+// iteration j: Z_j = MG(V_j), w = A Z_j, CGS2 against V_0..V_j, V_{j+1} = w / ||w||,
+// Givens rotation j; sc[2] = |g_{j+1}| (the residual estimate)
+void fg_iteration(stokes_hierarchy* h, int j) {
+  cudaStream_t s = h->stream;
+  sv::Level& F = h->lv.back();
+  const long long N = F.d.N, ld = N;
   const int m = h->m;
   SmallBuf sb = small_layout(h);
   double* V = h->V;
-  double* Z = h->Z;
-  const long long ld = N;
-  int it = 0;
-  double beta0 = 0.0, beta = 0.0;
-  stokes_status st;
+  double* vj = V + j * ld;
+  double* zj = h->Z + j * ld;
+  double* w = V + (j + 1) * ld;
+  precondition(h, vj, zj);
+  sv::launch_apply<double>(F.d, zj, nullptr, w, 0, s);
+  // classical Gram-Schmidt, twice
+  sv::launch_multidot(V, ld, j + 1, w, N, h->partials, h->npart, sb.hcol, 0, s);
+  sv::launch_multiaxpy(w, V, ld, j + 1, sb.hcol, -1.0, N, s);
+  sv::launch_multidot(V, ld, j + 1, w, N, h->partials, h->npart, sb.h2, 0, s);
+  sv::launch_multiaxpy(w, V, ld, j + 1, sb.h2, -1.0, N, s);
+  sv::launch_add_small(sb.hcol, sb.h2, j + 1, s);
+  sv::launch_multidot(w, ld, 1, w, N, h->partials, h->npart, sb.sc, 0, s);
+  sv::launch_set_scalar(sb.sc + 1, sb.sc, s);
+  sv::launch_scale(w, w, sb.sc + 1, 0.0, N, s);
+  sv::launch_givens(sb.H, m + 1, sb.cs, sb.sn, sb.g, sb.hcol, sb.sc + 1, j, sb.sc + 2, s);
+}
 
-  sv::launch_apply<double>(F.d, x, b, V, 1, s);
-  if ((st = norm_host(h, V, N, sb.sc, &beta0)) != STOKES_OK) return st;
+// end of a cycle after k iterations: y = H_k^-1 g, x += Z y, then fg_residual
+void fg_finish_cycle(stokes_hierarchy* h, int k, const double* b, double* x) {
+  const long long N = h->lv.back().d.N;
+  SmallBuf sb = small_layout(h);
+  sv::launch_backsolve(sb.H, h->m + 1, sb.g, k, sb.y, h->stream);
+  sv::launch_multiaxpy(x, h->Z, N, k, sb.y, 1.0, N, h->stream);
+  fg_residual(h, b, x);
+}
+
+}  // namespace sv
+
+namespace {
+
+stokes_status fgmres(stokes_hierarchy* h, const double* b, double* x, int* iters_out,
+                     double* relres_out) {
+  double* sc = sv::fg_scalars(h);
+  int it = 0;
+  double beta0 = 0.0, beta = 0.0, v2 = 0.0;
+  stokes_status st;
+  sv::fg_residual(h, b, x);
+  if ((st = check_launch("fgmres residual")) != STOKES_OK) return st;
+  if ((st = read_scalar(h, sc, &v2)) != STOKES_OK) return st;
+  beta0 = std::sqrt(v2);
   if (!std::isfinite(beta0)) return fail(STOKES_ERR_NONFINITE, "initial residual is not finite");
   if (iters_out) *iters_out = 0;
   if (relres_out) *relres_out = 0.0;
@@ -293,38 +342,22 @@ stokes_status fgmres(stokes_hierarchy* h, const double* b, double* x, int* iters
   const double tol = h->prm.rtol * beta0;
   stokes_status result = STOKES_NOT_CONVERGED;
   while (true) {
-    sv::launch_scale(V, V, nullptr, 1.0 / beta, N, s);
-    sv::launch_fill(sb.g, 0.0, m + 1, s);
-    sv::launch_fill(sb.g, beta, 1, s);
+    sv::fg_start_cycle(h, beta);
     int k = 0;
-    for (int j = 0; j < m; ++j) {
-      double* vj = V + j * ld;
-      double* zj = Z + j * ld;
-      double* w = V + (j + 1) * ld;
-      precondition(h, vj, zj);
-      sv::launch_apply<double>(F.d, zj, nullptr, w, 0, s);
-      // classical Gram-Schmidt, twice
-      sv::launch_multidot(V, ld, j + 1, w, N, h->partials, h->npart, sb.hcol, 0, s);
-      sv::launch_multiaxpy(w, V, ld, j + 1, sb.hcol, -1.0, N, s);
-      sv::launch_multidot(V, ld, j + 1, w, N, h->partials, h->npart, sb.h2, 0, s);
-      sv::launch_multiaxpy(w, V, ld, j + 1, sb.h2, -1.0, N, s);
-      sv::launch_add_small(sb.hcol, sb.h2, j + 1, s);
-      sv::launch_multidot(w, ld, 1, w, N, h->partials, h->npart, sb.sc, 0, s);
-      sv::launch_set_scalar(sb.sc + 1, sb.sc, s);
-      sv::launch_scale(w, w, sb.sc + 1, 0.0, N, s);
-      sv::launch_givens(sb.H, m + 1, sb.cs, sb.sn, sb.g, sb.hcol, sb.sc + 1, j, sb.sc + 2, s);
+    for (int j = 0; j < h->m; ++j) {
+      sv::fg_iteration(h, j);
       if ((st = check_launch("fgmres iteration")) != STOKES_OK) return st;
       double est;
-      if ((st = read_scalar(h, sb.sc + 2, &est)) != STOKES_OK) return st;
+      if ((st = read_scalar(h, sc + 2, &est)) != STOKES_OK) return st;
       ++it;
       k = j + 1;
       if (!std::isfinite(est)) return fail(STOKES_ERR_NONFINITE, "residual estimate is not finite");
       if (est <= tol || it >= h->prm.maxit) break;
     }
-    sv::launch_backsolve(sb.H, m + 1, sb.g, k, sb.y, s);
-    sv::launch_multiaxpy(x, Z, ld, k, sb.y, 1.0, N, s);
-    sv::launch_apply<double>(F.d, x, b, V, 1, s);
-    if ((st = norm_host(h, V, N, sb.sc, &beta)) != STOKES_OK) return st;
+    sv::fg_finish_cycle(h, k, b, x);
+    if ((st = check_launch("fgmres update")) != STOKES_OK) return st;
+    if ((st = read_scalar(h, sc, &v2)) != STOKES_OK) return st;
+    beta = std::sqrt(v2);
     if (!std::isfinite(beta)) return fail(STOKES_ERR_NONFINITE, "residual is not finite");
     if (beta <= tol) {
       result = STOKES_OK;
@@ -477,9 +510,12 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
     const int nl = sizes[sizes.size() - 1 - k];
     L.d = make_level(nl, viscosity);
     const size_t N = static_cast<size_t>(L.d.N);
-    if ((e = dalloc(&L.x0, N)) != cudaSuccess || (e = dalloc(&L.x1, N)) != cudaSuccess ||
-        (e = dalloc(&L.b, N)) != cudaSuccess || (e = dalloc(&L.r, N)) != cudaSuccess ||
-        (e = dalloc(&L.e, N)) != cudaSuccess ||
+    // FP64 level vectors serve the FP64 V-cycle and, on level 0, the exact coarse
+    // solve of every form; a mixed-precision hierarchy needs them nowhere else
+    const bool f64 = (prm.prec == STOKES_FP64) || k == 0;
+    if ((f64 && ((e = dalloc(&L.x0, N)) != cudaSuccess || (e = dalloc(&L.x1, N)) != cudaSuccess ||
+                 (e = dalloc(&L.b, N)) != cudaSuccess || (e = dalloc(&L.r, N)) != cudaSuccess ||
+                 (e = dalloc(&L.e, N)) != cudaSuccess)) ||
         (e = dalloc(&L.cd, static_cast<size_t>(sv::NCLASS) * sv::CD_STRIDE)) != cudaSuccess) {
       free_all(h);
       delete h;

@@ -107,6 +107,15 @@ struct stokes_hierarchy {
 
 namespace sv {
 
+// FGMRES pieces (sv_api.cu): stream-ordered on h->stream, no host synchronisation.
+// fg_scalars: device scalars sc[0] = ||V_0||^2 after fg_residual / fg_finish_cycle,
+// sc[2] = residual estimate after fg_iteration.
+double* fg_scalars(stokes_hierarchy* h);
+void fg_residual(stokes_hierarchy* h, const double* b, const double* x);
+void fg_start_cycle(stokes_hierarchy* h, double beta);
+void fg_iteration(stokes_hierarchy* h, int j);
+void fg_finish_cycle(stokes_hierarchy* h, int k, const double* b, double* x);
+
 // message returned by stokes_last_error() on this thread
 void set_last_error(const std::string& msg);
 

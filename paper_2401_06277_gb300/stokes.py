@@ -89,6 +89,10 @@ def _load():
         "stokes_stats_reset": (I, [P]),
         "stokes_stats_read": (I, [P, ctypes.POINTER(stokes_stats)]),
         "stokes_residual_norm_noalloc": (I, [I, D, VP, VP, VP, VP]),
+        "stokes_batch_create": (I, [I, IP, D, ctypes.POINTER(stokes_params), VP, ctypes.POINTER(P)]),
+        "stokes_batch_destroy": (I, [P]),
+        "stokes_batch_hierarchy": (I, [P, I, ctypes.POINTER(P)]),
+        "stokes_batch_solve": (I, [P, ctypes.POINTER(VP), ctypes.POINTER(VP), IP, DP]),
         "stokes_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -108,7 +112,8 @@ def exported_symbols() -> list[str]:
             "stokes_coarse_solve", "stokes_initial_guess", "stokes_vcycle_apply", "stokes_fgmres_solve",
             "stokes_solve_adjoint", "stokes_rhs_transpose", "stokes_batched_solve",
             "stokes_stats_enable_timing", "stokes_stats_reset", "stokes_stats_read",
-            "stokes_residual_norm_noalloc", "stokes_last_error"]
+            "stokes_residual_norm_noalloc", "stokes_batch_create", "stokes_batch_destroy",
+            "stokes_batch_hierarchy", "stokes_batch_solve", "stokes_last_error"]
 
 
 def _check(st: int, allow=()) -> int:
@@ -292,6 +297,89 @@ def stokes_residual_norm_noalloc(n: int, viscosity: float, b, x, norm,
     s = (stream or torch.cuda.current_stream()).cuda_stream
     _check(_load().stokes_residual_norm_noalloc(int(n), float(viscosity), _ptr(b, N, "b"), _ptr(x, N, "x"),
                                                 _ptr(norm, 1, "norm"), ctypes.c_void_p(s)))
+
+
+def stokes_batch_create(ns, viscosity: float = 1.0, params: stokes_params | None = None,
+                        stream: torch.cuda.Stream | None = None):
+    lib = _load()
+    if params is None:
+        params = default_params()
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    arr = (ctypes.c_int * len(ns))(*[int(v) for v in ns])
+    out = ctypes.c_void_p()
+    _check(lib.stokes_batch_create(len(ns), arr, float(viscosity), ctypes.byref(params), ctypes.c_void_p(s),
+                                   ctypes.byref(out)))
+    return out
+
+
+def stokes_batch_destroy(bh) -> None:
+    _check(_load().stokes_batch_destroy(bh))
+
+
+def stokes_batch_hierarchy(bh, k: int):
+    out = ctypes.c_void_p()
+    _check(_load().stokes_batch_hierarchy(bh, int(k), ctypes.byref(out)))
+    return out
+
+
+def stokes_batch_solve(bh, rhs, xs, allow_not_converged: bool = False):
+    k = len(rhs)
+    for i, (b, x) in enumerate(zip(rhs, xs)):
+        h = stokes_batch_hierarchy(bh, i)
+        N = vec_len(stokes_level_info(h)[1])
+        _ptr(b, N, "rhs")
+        _ptr(x, N, "x")
+    B = (ctypes.c_void_p * k)(*[b.data_ptr() for b in rhs])
+    X = (ctypes.c_void_p * k)(*[x.data_ptr() for x in xs])
+    it = (ctypes.c_int * k)()
+    rel = (ctypes.c_double * k)()
+    st = _check(_load().stokes_batch_solve(bh, B, X, it, rel),
+                allow=(STOKES_NOT_CONVERGED,) if allow_not_converged else ())
+    return list(it), list(rel), st
+
+
+class Batch:
+    """Owns a stokes_batch: independent problems (sizes may differ) solved in lockstep."""
+
+    def __init__(self, ns, viscosity: float = 1.0, **kw):
+        p = default_params()
+        for key, val in kw.items():
+            setattr(p, key, val)
+        self.ns = list(ns)
+        self.handle = stokes_batch_create(self.ns, viscosity, p)
+
+    def hierarchy(self, k: int):
+        return stokes_batch_hierarchy(self.handle, k)
+
+    def assemble_rhs(self, k: int, f_nodal, u_dirichlet):
+        # problem k runs on a stream of its own: order it after torch's work and back
+        n = self.ns[k]
+        b = torch.empty(vec_len(n), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        stokes_assemble_rhs(self.hierarchy(k), f_nodal, u_dirichlet, b, n)
+        torch.cuda.synchronize()
+        return b
+
+    def solve(self, rhs, allow_not_converged: bool = False):
+        xs = []
+        for k, b in enumerate(rhs):
+            x = torch.empty_like(b)
+            stokes_initial_guess(self.hierarchy(k), b, x)
+            xs.append(x)
+        torch.cuda.synchronize()
+        it, rel, st = stokes_batch_solve(self.handle, rhs, xs, allow_not_converged)
+        return xs, it, rel
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            stokes_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def stokes_last_error() -> str:

@@ -450,3 +450,55 @@ def test_adjoint_projects_inconsistent_pressure_data(pkg):
     gp[2 * lv.mesh.nvel:] -= gp[2 * lv.mesh.nvel:].mean()
     assert rr <= 1e-12
     assert rel(lv.A @ host(lam), gp) <= 1e-10
+
+
+# ---------------------------------------------------------------------------
+# Batched form: problems of uneven size in lockstep, one CUDA graph per iteration
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [0, 2])
+def test_batch_uneven_sizes_match_single_solves(pkg, prec):
+    """A batch of problems of different sizes gives, problem by problem, the single-solve result."""
+    from paper_2401_06277_gb300 import stokes
+    ns = [16, 64, 32, 64] if prec == 0 else [32, 128, 64]
+    B = pkg.Batch(ns, prec=prec)
+    rhs, refs = [], []
+    for k, n in enumerate(ns):
+        f = dev(si.random_force(n, 500 + k))
+        ud = dev(si.manufactured_velocity(n))
+        rhs.append(B.assemble_rhs(k, f, ud))
+        H = gpu_h(pkg, n, prec=prec)
+        x, it, rr = H.solve(H.assemble_rhs(f, ud))
+        refs.append((host(x), it))
+    xs, its, rels = B.solve(rhs)
+    for k, n in enumerate(ns):
+        lv = oracle_h(n).levels[-1]
+        assert its[k] == refs[k][1]
+        assert rels[k] <= 1e-8
+        xb = O.normalize_pressure(lv, host(xs[k]))
+        xr = O.normalize_pressure(lv, refs[k][0])
+        assert np.linalg.norm(xb - xr) / np.linalg.norm(xr) <= 1e-12
+    B.close()
+
+
+def test_batch_many_rhs_one_grid(pkg):
+    """Eight right-hand sides on one grid (FP32 preconditioner): every solve reaches 1e-8
+    and matches the oracle's solution within 1e-7."""
+    from paper_2401_06277_gb300 import stokes
+    n = 32
+    ns = [n] * 8
+    B = pkg.Batch(ns, prec=stokes.STOKES_MIXED_FP32, restart=12)
+    Ho = oracle_h(n)
+    lv = Ho.levels[-1]
+    rhs, bo = [], []
+    for k in range(8):
+        f = si.random_force(n, 2000 + k)
+        ud = si.manufactured_velocity(n)
+        bo.append(O.assemble_rhs(lv, f, ud))
+        rhs.append(B.assemble_rhs(k, dev(f), dev(ud)))
+    xs, its, rels = B.solve(rhs)
+    for k in range(8):
+        assert rels[k] <= 1e-8
+        xo = O.normalize_pressure(lv, O.solve(Ho, bo[k]).x)
+        xg = O.normalize_pressure(lv, host(xs[k]))
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-7
+    B.close()
