@@ -317,6 +317,67 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e):
     return rec
 
 
+def time_batch(args, prec_name: str) -> dict:
+    """Batched form: (a) 64 right-hand sides (force seeds 1..64) on one 1024 x 1024 grid and
+    (b) 32 problems with sizes drawn from {128, 256, 512, 1024} (generator seed 1000, force
+    seeds 2000 + k), each set solved as one batch (lockstep FGMRES(12) to 1e-8, one CUDA graph
+    per iteration).  Also times the same problems solved one after another."""
+    import torch
+
+    import stokes_inputs as si
+    import paper_2401_06277_gb300 as pkg
+
+    out = {}
+    g = torch.Generator(device="cpu")
+    g.manual_seed(1000)
+    uneven = [int(v) for v in torch.tensor([128, 256, 512, 1024])[torch.randint(0, 4, (32,), generator=g)]]
+    sets = {"rhs64_1024": ([args.batch_n] * args.batch_rhs, [1 + k for k in range(args.batch_rhs)]),
+            "uneven32": (uneven, [2000 + k for k in range(32)])}
+    for name, (ns, seeds) in sets.items():
+        B = pkg.Batch(ns, prec=PRECS[prec_name], restart=12)
+        rhs = []
+        for k, (n, sd) in enumerate(zip(ns, seeds)):
+            f = torch.from_numpy(si.random_force(n, sd)).cuda()
+            ud = torch.from_numpy(si.manufactured_velocity(n)).cuda()
+            rhs.append(B.assemble_rhs(k, f, ud))
+            del f, ud
+        B.solve(rhs)          # warm-up: captures the iteration graphs
+        torch.cuda.synchronize()
+        times, its = [], None
+        for _ in range(max(1, args.batch_steps)):
+            t0 = time.perf_counter()
+            xs, its, rels = B.solve(rhs)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        dt = statistics.median(times)
+        units = sum(dofs(n) * it for n, it in zip(ns, its))
+        rec = {"problems": len(ns), "sizes": sorted(set(ns)), "solve_s": dt, "iters": its,
+               "max_relres": max(rels), "value": units / dt, "unit": UNIT}
+        B.close()
+        del B, rhs, xs
+        torch.cuda.empty_cache()
+        # the same problems one after another (one hierarchy per size, graph-free path)
+        seq = 0.0
+        hs = {}
+        for n, sd in zip(ns, seeds):
+            if n not in hs:
+                hs[n] = pkg.Hierarchy(n, prec=PRECS[prec_name], restart=12)
+            H = hs[n]
+            bb = H.assemble_rhs(torch.from_numpy(si.random_force(n, sd)).cuda(),
+                                torch.from_numpy(si.manufactured_velocity(n)).cuda())
+            H.solve(bb)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            H.solve(bb)
+            torch.cuda.synchronize()
+            seq += time.perf_counter() - t0
+        for H in hs.values():
+            H.close()
+        rec["sequential_s"] = seq
+        out[name] = rec
+    return out
+
+
 def run_ours(args) -> None:
     import torch
 
@@ -332,10 +393,15 @@ def run_ours(args) -> None:
     main = time_form(args, args.prec, ws, rank, f_host, ud_host, with_e2e=True)
     forms = {args.prec: {k: main[k] for k in ("value", "time_to_solution_s", "iters", "ms_per_vcycle")}}
     if not args.single_form:
-        other = "mixed" if args.prec == "fp64" else "fp64"
-        o = time_form(args, other, ws, rank, f_host, ud_host, with_e2e=False)
-        forms[other] = {k: o[k] for k in ("value", "time_to_solution_s", "iters", "ms_per_vcycle")}
-        forms[other]["roofline"] = o["roofline"]
+        for other in PRECS:
+            if other == args.prec:
+                continue
+            o = time_form(args, other, ws, rank, f_host, ud_host, with_e2e=False)
+            forms[other] = {k: o[k] for k in ("value", "time_to_solution_s", "iters", "ms_per_vcycle")}
+            forms[other]["roofline"] = o["roofline"]
+    batched = None
+    if not args.no_batch:
+        batched = time_batch(args, "mixed")
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         o = run_oracle(ORACLE_N, 1)
@@ -358,7 +424,8 @@ def run_ours(args) -> None:
                 "time_to_solution_s": main["time_to_solution_s"], "iters": main["iters"],
                 "relres": main["relres"], "vcycles": main["vcycles"], "ms_per_vcycle": main["ms_per_vcycle"],
                 "roofline": main["roofline"], "cpu_baseline": cpu, "e2e": main["e2e"],
-                "gpu_launches": main["gpu_launches"], "clocks": main["clocks"], "forms": forms}
+                "gpu_launches": main["gpu_launches"], "clocks": main["clocks"], "forms": forms,
+                "batched": batched}
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -455,6 +522,10 @@ def main():
     ap.add_argument("--prec", choices=list(PRECS), default="fp64",
                     help="form of the headline line (the other form is reported under 'forms')")
     ap.add_argument("--single-form", action="store_true", help="time only the --prec form")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-form timings")
+    ap.add_argument("--batch-n", type=int, default=1024)
+    ap.add_argument("--batch-rhs", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--oracle-worker", action="store_true")
     ap.add_argument("--tile", type=int, default=-1, help="Vanka tile shape (-1: autotuned)")
     ap.add_argument("--kernel", choices=["sweep", "residual", "vcycle"], default=None,
