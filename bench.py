@@ -170,24 +170,34 @@ def barrier(ws):
         dist.barrier()
 
 
-def allmax(ws, v: float) -> float:
+def _reduce(ws, v: float, op) -> float:
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def allmax(ws, v: float) -> float:
+    """Maximum over ranks (the slowest rank's time)."""
+    import torch.distributed as dist
+    return _reduce(ws, v, dist.ReduceOp.MAX if ws > 1 else None)
 
 
 def allsum(ws, v: float) -> float:
-    if ws == 1:
-        return v
-    import torch
+    """Sum over ranks (units processed by the whole job)."""
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(ws, v, dist.ReduceOp.SUM if ws > 1 else None)
+
+
+def job_throughput(ws, units_local: float, ms_local: float) -> tuple[float, float]:
+    """Whole-job units/s over replicas: units summed over ranks / max time over ranks."""
+    ms = allmax(ws, ms_local)
+    units = allsum(ws, units_local)
+    return units / (ms * 1e-3), ms
 
 
 # --------------------------------------------------------------------------
@@ -253,9 +263,8 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e):
     st = stokes.stokes_stats_read(H.handle)
     stokes.stokes_stats_enable_timing(H.handle, False)
     launches = st["kernel_launches"] - l0
-    ms_max = allmax(ws, ms)
+    value, ms_max = job_throughput(ws, N * st["vcycles"], ms)
     vcycles_all = allsum(ws, st["vcycles"])
-    value = N * vcycles_all / (ms_max * 1e-3)
     sweep_ms = st["sweep_ms"] / max(st["sweeps_timed"], 1)
     tile = ["8x8", "16x8", "16x16", "14x14"][stokes.stokes_level_tile(H.handle, H.levels - 1)]
     peaks = measured_peaks()

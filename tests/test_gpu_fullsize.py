@@ -1,0 +1,176 @@
+"""Parity at the benchmark's full size (2048 x 2048 elements, 10 levels) in the launch
+configuration bench.py times (the same hierarchy parameters and autotuned tiles).
+
+The oracle cannot assemble a 2048^2 problem, but one Vanka sweep, the operator and
+the grid transfers are local: a dof's output depends only on data within a few
+nodes.  A random pattern that vanishes outside a box in the middle of a 32^2 grid
+(and its Dirichlet margins) is embedded at an even node offset deep inside the
+2048^2 grid; there the GPU result must equal the oracle's 32^2 result element by
+element, after one exact rescaling: the velocity block L is independent of h in
+2D while B scales with h (Eq. 4), so with D = diag(I_u, s I_p) and s = h_big / h_small
+= 32 / 2048 (a power of two, exact in floating point) the big operator restricted
+to the window is D A_small D, and one additive Vanka sweep, whose patch matrices are
+R_i D A D R_i^T, satisfies  sweep_big(x, b) = D^-1 sweep_small(D x, D^-1 b).  The full
+solve is checked through properties that hold at any size: the true FP64 residual
+and the nodal error of the manufactured solution.
+"""
+import numpy as np
+import pytest
+import torch
+
+import stokes_inputs as si
+from oracle import stokes_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+NBIG = 2048
+NS = 32          # small grid of the oracle
+OFF = 1400       # vertex offset of the small grid inside the big one (Q2 offset 2 * OFF)
+
+
+@pytest.fixture(scope="module")
+def big():
+    import paper_2401_06277_gb300 as pkg
+    from paper_2401_06277_gb300 import build
+    build.build()
+    H = pkg.Hierarchy(NBIG, rtol=1e-8, restart=30)
+    yield H
+    H.close()
+
+
+def pattern(n, seed, box=(12, 20)):
+    """Random x with support in vertices [box) and Q2 nodes [2 box), zero elsewhere."""
+    rng = np.random.default_rng(seed)
+    nq, npr = 2 * n + 1, n + 1
+    u = np.zeros((2, nq, nq))
+    p = np.zeros((npr, npr))
+    a, b = box
+    u[:, 2 * a: 2 * b, 2 * a: 2 * b] = rng.standard_normal((2, 2 * (b - a), 2 * (b - a)))
+    p[a:b, a:b] = rng.standard_normal((b - a, b - a))
+    return np.concatenate([u.ravel(), p.ravel()])
+
+
+def embed(v_small, n_small, n_big, off):
+    """Place a small-grid vector at vertex offset `off` (Q2 offset 2 off) in a zero big-grid vector."""
+    nqs, nps, nqb, npb = 2 * n_small + 1, n_small + 1, 2 * n_big + 1, n_big + 1
+    us = v_small[: 2 * nqs * nqs].reshape(2, nqs, nqs)
+    ps = v_small[2 * nqs * nqs:].reshape(nps, nps)
+    ub = np.zeros((2, nqb, nqb))
+    pb = np.zeros((npb, npb))
+    ub[:, 2 * off: 2 * off + nqs, 2 * off: 2 * off + nqs] = us
+    pb[off: off + nps, off: off + nps] = ps
+    return np.concatenate([ub.ravel(), pb.ravel()])
+
+
+def window(v_big, n_small, n_big, off):
+    nqs, nps, nqb, npb = 2 * n_small + 1, n_small + 1, 2 * n_big + 1, n_big + 1
+    ub = v_big[: 2 * nqb * nqb].reshape(2, nqb, nqb)
+    pb = v_big[2 * nqb * nqb:].reshape(npb, npb)
+    return np.concatenate([ub[:, 2 * off: 2 * off + nqs, 2 * off: 2 * off + nqs].ravel(),
+                           pb[off: off + nps, off: off + nps].ravel()])
+
+
+def outside_norm(v_big, n_small, n_big, off):
+    """Largest magnitude outside the embedded window."""
+    nqs, nps, nqb, npb = 2 * n_small + 1, n_small + 1, 2 * n_big + 1, n_big + 1
+    ub = v_big[: 2 * nqb * nqb].reshape(2, nqb, nqb).copy()
+    pb = v_big[2 * nqb * nqb:].reshape(npb, npb).copy()
+    ub[:, 2 * off: 2 * off + nqs, 2 * off: 2 * off + nqs] = 0.0
+    pb[off: off + nps, off: off + nps] = 0.0
+    return max(np.abs(ub).max(), np.abs(pb).max())
+
+
+S = NS / NBIG    # h_big / h_small, exactly 2^-6
+
+
+def pscale(x, n, f):
+    """D x with D = diag(I_u, f I_p) on an n^2 grid vector."""
+    y = x.copy()
+    y[2 * (2 * n + 1) ** 2:] *= f
+    return y
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def cpu(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def test_fullsize_operator(big):
+    lv = O.build_level(NS, 1.0)
+    xs = pattern(NS, 1)
+    ref = pscale(lv.A @ pscale(xs, NS, S), NS, S)
+    y = cpu(big.apply(gpu(embed(xs, NS, NBIG, OFF))))
+    err = np.abs(window(y, NS, NBIG, OFF) - ref).max() / np.abs(ref).max()
+    assert err <= 1e-13, err
+    assert outside_norm(y, NS, NBIG, OFF) == 0.0
+
+
+def test_fullsize_vanka_sweep(big):
+    """One FP64 sweep on the finest 2048^2 level, with the tile shape the bench uses."""
+    lv = O.build_level(NS, 1.0)
+    xs, bs = pattern(NS, 2), pattern(NS, 3)
+    ref = pscale(O.vanka_sweep(lv, pscale(xs, NS, S), pscale(bs, NS, 1 / S), 0.7), NS, 1 / S)
+    out = cpu(big.sweep(gpu(embed(xs, NS, NBIG, OFF)), gpu(embed(bs, NS, NBIG, OFF))))
+    err = np.abs(window(out, NS, NBIG, OFF) - ref).max() / np.abs(ref).max()
+    assert err <= 1e-12, err
+    assert outside_norm(out, NS, NBIG, OFF) == 0.0
+
+
+def test_fullsize_transfers(big):
+    """Restriction and prolongation between the two finest levels (2048 -> 1024)."""
+    from paper_2401_06277_gb300 import stokes
+    lf, lc = O.build_level(2 * NS, 1.0), O.build_level(NS, 1.0)
+    P = O.prolongation(lf.mesh, lc.mesh)
+    L = big.levels - 1
+    offc = 700  # coarse vertex offset in the 1024 grid; the fine window sits at 2 offc in the 2048 grid
+    # restriction of a fine pattern
+    rf = pattern(2 * NS, 4, box=(24, 40))
+    rc_ref = P.T @ rf
+    rc = torch.zeros(si.sizes(NBIG // 2)[2], dtype=torch.float64, device="cuda")
+    stokes.stokes_restrict(big.handle, L, gpu(embed(rf, 2 * NS, NBIG, 2 * offc)), rc)
+    rc = cpu(rc)
+    assert np.abs(window(rc, NS, NBIG // 2, offc) - rc_ref).max() <= 1e-13 * np.abs(rc_ref).max()
+    assert outside_norm(rc, NS, NBIG // 2, offc) == 0.0
+    # prolongation of a coarse pattern
+    ec = pattern(NS, 5)
+    xf = torch.zeros(si.sizes(NBIG)[2], dtype=torch.float64, device="cuda")
+    stokes.stokes_prolong_add(big.handle, L, gpu(embed(ec, NS, NBIG // 2, offc)), xf)
+    xf = cpu(xf)
+    ref = P @ ec
+    assert np.abs(window(xf, 2 * NS, NBIG, 2 * offc) - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert outside_norm(xf, 2 * NS, NBIG, 2 * offc) == 0.0
+
+
+def test_fullsize_manufactured_solve(big):
+    """FGMRES + V(2,2) at 2048^2 on the manufactured field: true FP64 residual <= 1e-8 of the
+    initial one, nodal velocity error and (mean-free) pressure error small."""
+    n = NBIG
+    f = gpu(si.manufactured_force(n))
+    ud = gpu(si.manufactured_velocity(n))
+    b = big.assemble_rhs(f, ud)
+    x, it, rr = big.solve(b)
+    assert rr <= 1e-8 and it <= 12
+    # the true residual through an independent path: the allocation-free residual norm
+    from paper_2401_06277_gb300 import stokes
+    x0 = torch.empty_like(b)
+    stokes.stokes_initial_guess(big.handle, b, x0)
+    nrm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stokes.stokes_residual_norm_noalloc(n, 1.0, b, x, nrm)
+    r_end = float(nrm.item())
+    stokes.stokes_residual_norm_noalloc(n, 1.0, b, x0, nrm)
+    assert r_end <= 1.01e-8 * float(nrm.item()), (r_end, float(nrm.item()))
+    xv = cpu(x)
+    nq = 2 * n + 1
+    ue = si.manufactured_velocity(n).ravel()
+    eu = np.abs(xv[: 2 * nq * nq] - ue).max()
+    p = xv[2 * nq * nq:]
+    pe = si.manufactured_pressure(n).ravel()
+    ep = np.abs((p - p.mean()) - (pe - pe.mean())).max()
+    print(f"2048^2 manufactured: it={it} rr={rr:.3e} true={r_end / float(nrm.item()):.3e} "
+          f"max|u-u_e|={eu:.3e} max|p-p_e|={ep:.3e}")
+    assert eu <= 1e-6, eu
+    assert ep <= 1e-4, ep
