@@ -78,6 +78,8 @@ void free_all(stokes_hierarchy* h) {
   cudaFree(h->partials);
   cudaFree(h->dev_err);
   h->dev_err = nullptr;
+  cudaFree(h->ticket);
+  h->ticket = nullptr;
   cudaFree(h->aux);
   h->aux = nullptr;
   if (h->host_scalars) cudaFreeHost(h->host_scalars);
@@ -273,7 +275,8 @@ void fg_residual(stokes_hierarchy* h, const double* b, const double* x) {
   const long long N = F.d.N;
   SmallBuf sb = small_layout(h);
   sv::launch_apply<double>(F.d, x, b, h->V, 1, h->stream);
-  sv::launch_multidot(h->V, N, 1, h->V, N, h->partials, h->npart, sb.sc, 0, h->stream);
+  sv::launch_orth_dots(h->V, N, 0, h->V, N, h->partials, h->npart, h->ticket, nullptr, sb.sc, nullptr,
+                       h->stream);
 }
 
 // V_0 /= beta, g = beta e_1 (beta known on the host)
@@ -285,8 +288,11 @@ void fg_start_cycle(stokes_hierarchy* h, double beta) {
   sv::launch_fill(sb.g, beta, 1, h->stream);
 }
 
-// iteration j: Z_j = MG(V_j), w = A Z_j, CGS2 against V_0..V_j, V_{j+1} = w / ||w||,
-// Givens rotation j; sc[2] = |g_{j+1}| (the residual estimate)
+// iteration j: Z_j = MG(V_j), w = A Z_j, classical Gram-Schmidt against V_0..V_j
+// (a second pass when the first removed more than half of ||w||^2: the DGKS
+// test, taken on the device), V_{j+1} = w / ||w||, Givens rotation j;
+// sc[2] = |g_{j+1}| (the residual estimate).  Scalars: sc[0..1] = ||w||^2,
+// ||w||; sc[3..4] = ||A Z_j||^2 and its root; sc[5] = 1 if the second pass runs.
 void fg_iteration(stokes_hierarchy* h, int j) {
   cudaStream_t s = h->stream;
   sv::Level& F = h->lv.back();
@@ -299,14 +305,16 @@ void fg_iteration(stokes_hierarchy* h, int j) {
   double* w = V + (j + 1) * ld;
   precondition(h, vj, zj);
   sv::launch_apply<double>(F.d, zj, nullptr, w, 0, s);
-  // classical Gram-Schmidt, twice
-  sv::launch_multidot(V, ld, j + 1, w, N, h->partials, h->npart, sb.hcol, 0, s);
-  sv::launch_multiaxpy(w, V, ld, j + 1, sb.hcol, -1.0, N, s);
-  sv::launch_multidot(V, ld, j + 1, w, N, h->partials, h->npart, sb.h2, 0, s);
-  sv::launch_multiaxpy(w, V, ld, j + 1, sb.h2, -1.0, N, s);
-  sv::launch_add_small(sb.hcol, sb.h2, j + 1, s);
-  sv::launch_multidot(w, ld, 1, w, N, h->partials, h->npart, sb.sc, 0, s);
-  sv::launch_set_scalar(sb.sc + 1, sb.sc, s);
+  double* P = h->partials;
+  const int np = h->npart;
+  // pass 1: h = V^T w and ||w||^2; w -= V h with the new ||w||^2 and the DGKS flag
+  sv::launch_orth_dots(V, ld, j + 1, w, N, P, np, h->ticket, sb.hcol, sb.sc + 3, nullptr, s);
+  sv::launch_orth_update(w, V, ld, j + 1, sb.hcol, N, P, np, h->ticket, sb.sc, nullptr, sb.sc + 3,
+                         sb.sc + 5, nullptr, s);
+  // pass 2, only where flagged: h2 = V^T w, w -= V h2, h += h2
+  sv::launch_orth_dots(V, ld, j + 1, w, N, P, np, h->ticket, sb.h2, nullptr, sb.sc + 5, s);
+  sv::launch_orth_update(w, V, ld, j + 1, sb.h2, N, P, np, h->ticket, sb.sc, sb.sc + 5, nullptr, nullptr,
+                         sb.hcol, s);
   sv::launch_scale(w, w, sb.sc + 1, 0.0, N, s);
   sv::launch_givens(sb.H, m + 1, sb.cs, sb.sn, sb.g, sb.hcol, sb.sc + 1, j, sb.sc + 2, s);
 }
@@ -568,6 +576,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
       (e = dalloc(&h->partials, static_cast<size_t>(h->npart) * 64)) != cudaSuccess ||
       (e = dalloc(&h->dev_err, 1)) != cudaSuccess || (e = dalloc(&h->aux, Nf)) != cudaSuccess ||
       (e = cudaMemset(h->dev_err, 0, sizeof(int))) != cudaSuccess ||
+      (e = dalloc(&h->ticket, 1)) != cudaSuccess || (e = cudaMemset(h->ticket, 0, sizeof(unsigned))) != cudaSuccess ||
       (e = cudaMallocHost(reinterpret_cast<void**>(&h->host_scalars), 8 * sizeof(double))) != cudaSuccess) {
     free_all(h);
     delete h;

@@ -93,6 +93,7 @@ struct stokes_hierarchy {
   double* small = nullptr;       // H, g, cs, sn, hcol, h2, y, scalars
   double* partials = nullptr;    // dot-product partial sums
   int npart = 0;                 // blocks of the dot kernels
+  unsigned* ticket = nullptr;    // last-block counter of the fused Gram-Schmidt kernels
   double* host_scalars = nullptr;  // pinned host mirror of a few scalars
   int* dev_err = nullptr;          // set by kernels whose bounded waits expired
   double* aux = nullptr;           // finest-level vector: the projected adjoint right-hand side
@@ -173,9 +174,20 @@ cudaError_t vanka_prepare();
 
 // ---- Krylov kernels (sv_krylov.cu) ----
 int dot_blocks();
-// partial sums of <V_k, w> for k < nk, V_k = V + k * ld; out[k] = sum (deterministic)
-void launch_multidot(const double* V, long long ld, int nk, const double* w, long long N,
-                     double* partials, int npart, double* out, int accumulate, cudaStream_t s);
+// Gram-Schmidt pass 1 over V_k = V + k * ld, k < nk: dots[k] = <V_k, w>; if
+// norm2 != nullptr also norm2[0] = <w, w>, norm2[1] = sqrt(norm2[0]).  Does
+// nothing when gate != nullptr and *gate == 0.  partials holds
+// (ORTH_KMAX + 1) * npart doubles; ticket is a zeroed device counter, reset
+// by each launch before it ends (one stream at a time per ticket).
+void launch_orth_dots(const double* V, long long ld, int nk, const double* w, long long N, double* partials,
+                      int npart, unsigned* ticket, double* dots, double* norm2, const double* gate,
+                      cudaStream_t s);
+// Gram-Schmidt pass 2: w -= sum_k coef[k] V_k; norm2 as above for the updated
+// w; if dgks_ref != nullptr, *flag = (norm2[0] < *dgks_ref / 2) as 1.0 / 0.0;
+// if hacc != nullptr, hacc[k] += coef[k] for k < nk.  Gated like pass 1.
+void launch_orth_update(double* w, const double* V, long long ld, int nk, const double* coef, long long N,
+                        double* partials, int npart, unsigned* ticket, double* norm2, const double* gate,
+                        const double* dgks_ref, double* flag, double* hacc, cudaStream_t s);
 // w += sign * sum_k coef[k] V_k
 void launch_multiaxpy(double* w, const double* V, long long ld, int nk, const double* coef,
                       double sign, long long N, cudaStream_t s);
@@ -187,9 +199,6 @@ void launch_givens(double* H, int ldh, double* cs, double* sn, double* g, const 
                    const double* hnorm, int j, double* est, cudaStream_t s);
 void launch_backsolve(const double* H, int ldh, const double* g, int k, double* y, cudaStream_t s);
 void launch_fill(double* p, double v, long long N, cudaStream_t s);
-void launch_set_scalar(double* p, const double* src_sqrt, cudaStream_t s);
-// a[k] += b[k], k < n (small device arrays)
-void launch_add_small(double* a, const double* b, int n, cudaStream_t s);
 // y = x with its pressure block shifted to zero (Euclidean) mean: the component
 // of x along ker A^T = (0, 1_p) is removed, so y is a consistent right-hand side
 void launch_project_pressure(const LevelDev& L, const double* x, double* y, double* partials, int npart,

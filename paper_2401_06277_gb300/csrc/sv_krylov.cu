@@ -1,8 +1,11 @@
-// sv_krylov.cu -- FP64 kernels of FGMRES (Section 6.8): fused multi-dot
-// products (classical Gram-Schmidt, applied twice), fused multi-axpy, scaling,
-// Givens rotations and the small triangular solve.  Reductions are two-stage
-// (warp shuffles, then one CTA over the per-block partials in a fixed order),
-// so every result is deterministic.
+// sv_krylov.cu -- FP64 kernels of FGMRES (Section 6.8): the Arnoldi step's
+// classical Gram-Schmidt as two fused passes (all dots plus ||w||^2 in one
+// read of V and w; the update w -= V h plus the new ||w||^2 in another), with
+// a second pass only when the first lost more than half of ||w||^2 (the DGKS
+// test, decided on the device); scaling, Givens rotations and the small
+// triangular solve.  Every reduction is two-stage (warp shuffles, then the
+// last block to finish sums the per-block partials in block order), so each
+// result is deterministic.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -13,7 +16,7 @@ namespace sv {
 namespace {
 
 constexpr int DOT_NT = 256;
-constexpr int DOT_KMAX = 16;   // vectors per multi-dot pass
+constexpr int ORTH_KMAX = 16;  // basis vectors per fused Gram-Schmidt launch
 constexpr int DOT_BLOCKS = 152 * 4;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -22,35 +25,167 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// partials[k * npart + blockIdx.x] = sum over this block's elements of V_k[i] w[i]
-__global__ void __launch_bounds__(DOT_NT) k_multidot(const double* __restrict__ V, long long ld,
-                                                     int nk, const double* __restrict__ w,
-                                                     long long N, double* __restrict__ partials,
-                                                     int npart) {
-  double acc[DOT_KMAX];
-#pragma unroll
-  for (int k = 0; k < DOT_KMAX; ++k) acc[k] = 0.0;
-  for (long long i = blockIdx.x * static_cast<long long>(DOT_NT) + threadIdx.x; i < N;
-       i += static_cast<long long>(gridDim.x) * DOT_NT) {
-    const double wi = w[i];
-#pragma unroll
-    for (int k = 0; k < DOT_KMAX; ++k)
-      if (k < nk) acc[k] = fma(V[k * ld + i], wi, acc[k]);
-  }
-  __shared__ double red[DOT_NT / 32][DOT_KMAX];
+// ---- fused Gram-Schmidt passes ----
+// Loads kept in flight per thread: U elements of each of the K + 1 vectors.
+template <int K>
+constexpr int orth_unroll() { return K <= 1 ? 4 : (K <= 4 ? 2 : 1); }
+
+// Reduces acc[0..NO) over the block into partials[t * npart + blockIdx.x] and
+// returns, in every thread, whether this block is the last of the grid to
+// finish (its partials then see all others').  The last block resets *ticket.
+template <int NO>
+__device__ __forceinline__ bool block_partials(const double (&acc)[NO], double* __restrict__ partials,
+                                               int npart, unsigned* ticket) {
+  __shared__ double red[DOT_NT / 32][NO];
+  __shared__ unsigned last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < DOT_KMAX; ++k) {
-    if (k < nk) {
-      const double v = warp_sum(acc[k]);
-      if (lane == 0) red[wid][k] = v;
-    }
+  for (int k = 0; k < NO; ++k) {
+    const double v = warp_sum(acc[k]);
+    if (lane == 0) red[wid][k] = v;
   }
   __syncthreads();
-  if (threadIdx.x < nk) {
+  if (threadIdx.x < NO) {
     double s = 0.0;
+#pragma unroll
     for (int q = 0; q < DOT_NT / 32; ++q) s += red[q][threadIdx.x];
     partials[static_cast<long long>(threadIdx.x) * npart + blockIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1) ? 1u : 0u;
+  __syncthreads();
+  return last != 0u;
+}
+
+// In the last block: tot[t] = sum over blocks b (in a fixed order) of
+// partials[t * npart + b], t < NO; one warp per output.
+template <int NO>
+__device__ __forceinline__ void total_partials(const double* __restrict__ partials, int npart,
+                                               double (&tot)[NO]) {
+  __shared__ double sh[NO];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int t = wid; t < NO; t += DOT_NT / 32) {
+    double v = 0.0;
+    for (int b = lane; b < npart; b += 32) v += __ldcg(partials + static_cast<long long>(t) * npart + b);
+    v = warp_sum(v);
+    if (lane == 0) sh[t] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < NO; ++t) tot[t] = sh[t];
+}
+
+// Pass 1 of Gram-Schmidt: dots[k] = <V_k, w> (k < K) and, if NORM,
+// norm2[0] = <w, w>, norm2[1] = sqrt(norm2[0]).  Skipped when *gate == 0.
+template <int K, bool NORM>
+__global__ void __launch_bounds__(DOT_NT) k_orth_dots(const double* __restrict__ V, long long ld,
+                                                      const double* __restrict__ w, long long N,
+                                                      double* __restrict__ partials, int npart,
+                                                      unsigned* ticket, double* __restrict__ dots,
+                                                      double* __restrict__ norm2,
+                                                      const double* __restrict__ gate) {
+  if (gate != nullptr && *gate == 0.0) return;
+  constexpr int NO = K + (NORM ? 1 : 0);
+  constexpr int U = orth_unroll<K>();
+  double acc[NO];
+#pragma unroll
+  for (int k = 0; k < NO; ++k) acc[k] = 0.0;
+  const long long stride = static_cast<long long>(gridDim.x) * DOT_NT;
+  long long i = blockIdx.x * static_cast<long long>(DOT_NT) + threadIdx.x;
+  for (; i + (U - 1) * stride < N; i += U * stride) {
+    double wv[U], vv[U][K > 0 ? K : 1];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      wv[u] = w[i + u * stride];
+#pragma unroll
+      for (int k = 0; k < K; ++k) vv[u][k] = V[k * ld + i + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] = fma(vv[u][k], wv[u], acc[k]);
+      if (NORM) acc[NO - 1] = fma(wv[u], wv[u], acc[NO - 1]);
+    }
+  }
+  for (; i < N; i += stride) {
+    const double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = fma(V[k * ld + i], wi, acc[k]);
+    if (NORM) acc[NO - 1] = fma(wi, wi, acc[NO - 1]);
+  }
+  if (!block_partials<NO>(acc, partials, npart, ticket)) return;
+  double tot[NO];
+  total_partials<NO>(partials, npart, tot);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) dots[k] = tot[k];
+    if (NORM) {
+      norm2[0] = tot[NO - 1];
+      norm2[1] = sqrt(tot[NO - 1]);
+    }
+    *ticket = 0u;
+  }
+}
+
+// Pass 2 of Gram-Schmidt: w -= sum_{k<K} coef[k] V_k and, if NORM, norm2[0] =
+// <w, w> of the updated w, norm2[1] = its square root.  In the last block,
+// when dgks_ref is given, *flag = 1 if norm2[0] < dgks_ref / 2 (re-orthogonalise)
+// else 0; when hacc is given, hacc[t] += coef_all[t] for t < nacc.  Skipped
+// when *gate == 0.
+template <int K, bool NORM>
+__global__ void __launch_bounds__(DOT_NT) k_orth_update(double* __restrict__ w, const double* __restrict__ V,
+                                                        long long ld, const double* __restrict__ coef,
+                                                        long long N, double* __restrict__ partials, int npart,
+                                                        unsigned* ticket, double* __restrict__ norm2,
+                                                        const double* __restrict__ gate,
+                                                        const double* __restrict__ dgks_ref,
+                                                        double* __restrict__ flag, double* __restrict__ hacc,
+                                                        const double* __restrict__ coef_all, int nacc) {
+  if (gate != nullptr && *gate == 0.0) return;
+  constexpr int U = orth_unroll<K>();
+  double c[K > 0 ? K : 1];
+#pragma unroll
+  for (int k = 0; k < K; ++k) c[k] = coef[k];
+  double acc[1] = {0.0};
+  const long long stride = static_cast<long long>(gridDim.x) * DOT_NT;
+  long long i = blockIdx.x * static_cast<long long>(DOT_NT) + threadIdx.x;
+  for (; i + (U - 1) * stride < N; i += U * stride) {
+    double wv[U], vv[U][K > 0 ? K : 1];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      wv[u] = w[i + u * stride];
+#pragma unroll
+      for (int k = 0; k < K; ++k) vv[u][k] = V[k * ld + i + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      double x = wv[u];
+#pragma unroll
+      for (int k = 0; k < K; ++k) x = fma(-c[k], vv[u][k], x);
+      w[i + u * stride] = x;
+      if (NORM) acc[0] = fma(x, x, acc[0]);
+    }
+  }
+  for (; i < N; i += stride) {
+    double x = w[i];
+#pragma unroll
+    for (int k = 0; k < K; ++k) x = fma(-c[k], V[k * ld + i], x);
+    w[i] = x;
+    if (NORM) acc[0] = fma(x, x, acc[0]);
+  }
+  if (!block_partials<1>(acc, partials, npart, ticket)) return;
+  double tot[1];
+  total_partials<1>(partials, npart, tot);
+  if (threadIdx.x == 0) {
+    if (NORM) {
+      norm2[0] = tot[0];
+      norm2[1] = sqrt(tot[0]);
+      if (dgks_ref != nullptr) *flag = (tot[0] < 0.5 * *dgks_ref) ? 1.0 : 0.0;
+    }
+    if (hacc != nullptr)
+      for (int t = 0; t < nacc; ++t) hacc[t] += coef_all[t];
+    *ticket = 0u;
   }
 }
 
@@ -102,11 +237,6 @@ __global__ void k_fill(double* __restrict__ p, double v, long long N) {
     p[i] = v;
 }
 
-// *p = sqrt(*src)
-__global__ void k_sqrt(double* p, const double* src) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *p = sqrt(*src);
-}
-
 // Column j of the Hessenberg matrix: H[0..j] = hcol, H[j+1] = hnorm.  Apply the
 // previous rotations, build rotation j, update g; est = |g[j+1]|.
 __global__ void k_givens(double* H, int ldh, double* cs, double* sn, double* g,
@@ -144,10 +274,6 @@ __global__ void k_backsolve(const double* H, int ldh, const double* g, int k, do
     const double d = H[static_cast<long long>(i) * ldh + i];
     y[i] = (d != 0.0) ? s / d : 0.0;
   }
-}
-
-__global__ void k_add_small(double* a, const double* b, int n) {
-  if (threadIdx.x < n) a[threadIdx.x] += b[threadIdx.x];
 }
 
 __global__ void k_dirichlet_copy(LevelDev L, const double* __restrict__ src, double* __restrict__ dst) {
@@ -204,15 +330,83 @@ std::atomic<long long> g_launches{0};
 
 int dot_blocks() { return DOT_BLOCKS; }
 
-void launch_multidot(const double* V, long long ld, int nk, const double* w, long long N,
-                     double* partials, int npart, double* out, int accumulate, cudaStream_t s) {
-  for (int k0 = 0; k0 < nk; k0 += DOT_KMAX) {
-    const int kk = (nk - k0 < DOT_KMAX) ? nk - k0 : DOT_KMAX;
-    count_launches(2);
-    k_multidot<<<npart, DOT_NT, 0, s>>>(V + k0 * ld, ld, kk, w, N, partials, npart);
-    k_reduce<<<kk, 256, 0, s>>>(partials, npart, out + k0, accumulate);
+template <int K>
+void dots_k(bool norm, const double* V, long long ld, const double* w, long long N, double* partials,
+            int npart, unsigned* ticket, double* dots, double* norm2, const double* gate, cudaStream_t s) {
+  if constexpr (K == 0) {
+    (void)norm;   // zero vectors: only the norm (callers pass norm2)
+    k_orth_dots<0, true><<<npart, DOT_NT, 0, s>>>(V, ld, w, N, partials, npart, ticket, dots, norm2, gate);
+  } else if (norm) {
+    k_orth_dots<K, true><<<npart, DOT_NT, 0, s>>>(V, ld, w, N, partials, npart, ticket, dots, norm2, gate);
+  } else {
+    k_orth_dots<K, false><<<npart, DOT_NT, 0, s>>>(V, ld, w, N, partials, npart, ticket, dots, norm2, gate);
   }
 }
+
+template <int K>
+void update_k(bool norm, double* w, const double* V, long long ld, const double* coef, long long N,
+              double* partials, int npart, unsigned* ticket, double* norm2, const double* gate,
+              const double* dgks_ref, double* flag, double* hacc, const double* coef_all, int nacc,
+              cudaStream_t s) {
+  if (norm)
+    k_orth_update<K, true><<<npart, DOT_NT, 0, s>>>(w, V, ld, coef, N, partials, npart, ticket, norm2, gate,
+                                                    dgks_ref, flag, hacc, coef_all, nacc);
+  else
+    k_orth_update<K, false><<<npart, DOT_NT, 0, s>>>(w, V, ld, coef, N, partials, npart, ticket, norm2, gate,
+                                                     dgks_ref, flag, hacc, coef_all, nacc);
+}
+
+#define SV_ORTH_CASES(F, ...) \
+  switch (kk) {                                    \
+    case 0: F<0>(__VA_ARGS__); break;              \
+    case 1: F<1>(__VA_ARGS__); break;              \
+    case 2: F<2>(__VA_ARGS__); break;              \
+    case 3: F<3>(__VA_ARGS__); break;              \
+    case 4: F<4>(__VA_ARGS__); break;              \
+    case 5: F<5>(__VA_ARGS__); break;              \
+    case 6: F<6>(__VA_ARGS__); break;              \
+    case 7: F<7>(__VA_ARGS__); break;              \
+    case 8: F<8>(__VA_ARGS__); break;              \
+    case 9: F<9>(__VA_ARGS__); break;              \
+    case 10: F<10>(__VA_ARGS__); break;            \
+    case 11: F<11>(__VA_ARGS__); break;            \
+    case 12: F<12>(__VA_ARGS__); break;            \
+    case 13: F<13>(__VA_ARGS__); break;            \
+    case 14: F<14>(__VA_ARGS__); break;            \
+    case 15: F<15>(__VA_ARGS__); break;            \
+    default: F<16>(__VA_ARGS__); break;            \
+  }
+
+void launch_orth_dots(const double* V, long long ld, int nk, const double* w, long long N, double* partials,
+                      int npart, unsigned* ticket, double* dots, double* norm2, const double* gate,
+                      cudaStream_t s) {
+  // chunks of ORTH_KMAX vectors; the first chunk also takes ||w||^2
+  int k0 = 0;
+  do {
+    const int kk = (nk - k0 < ORTH_KMAX) ? nk - k0 : ORTH_KMAX;
+    const bool norm = (k0 == 0) && norm2 != nullptr;
+    count_launches(1);
+    SV_ORTH_CASES(dots_k, norm, V + k0 * ld, ld, w, N, partials, npart, ticket, dots + k0, norm2, gate, s)
+    k0 += kk;
+  } while (k0 < nk);
+}
+
+void launch_orth_update(double* w, const double* V, long long ld, int nk, const double* coef, long long N,
+                        double* partials, int npart, unsigned* ticket, double* norm2, const double* gate,
+                        const double* dgks_ref, double* flag, double* hacc, cudaStream_t s) {
+  // chunks of ORTH_KMAX vectors; the last chunk takes the norm, the flag and hacc
+  int k0 = 0;
+  do {
+    const int kk = (nk - k0 < ORTH_KMAX) ? nk - k0 : ORTH_KMAX;
+    const bool lastc = (k0 + kk >= nk);
+    count_launches(1);
+    SV_ORTH_CASES(update_k, lastc && norm2 != nullptr, w, V + k0 * ld, ld, coef + k0, N, partials, npart,
+                  ticket, norm2, gate, lastc ? dgks_ref : nullptr, flag, lastc ? hacc : nullptr, coef, nk, s)
+    k0 += kk;
+  } while (k0 < nk);
+}
+
+#undef SV_ORTH_CASES
 
 void launch_multiaxpy(double* w, const double* V, long long ld, int nk, const double* coef,
                       double sign, long long N, cudaStream_t s) {
@@ -240,16 +434,6 @@ void launch_backsolve(const double* H, int ldh, const double* g, int k, double* 
 void launch_fill(double* p, double v, long long N, cudaStream_t s) {
   count_launches(1);
   k_fill<<<grid_for(N, 256), 256, 0, s>>>(p, v, N);
-}
-
-void launch_set_scalar(double* p, const double* src_sqrt, cudaStream_t s) {
-  count_launches(1);
-  k_sqrt<<<1, 32, 0, s>>>(p, src_sqrt);
-}
-
-void launch_add_small(double* a, const double* b, int n, cudaStream_t s) {
-  count_launches(1);
-  k_add_small<<<1, 64, 0, s>>>(a, b, n);
 }
 
 void launch_project_pressure(const LevelDev& L, const double* x, double* y, double* partials, int npart,
