@@ -524,7 +524,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
     if ((f64 && ((e = dalloc(&L.x0, N)) != cudaSuccess || (e = dalloc(&L.x1, N)) != cudaSuccess ||
                  (e = dalloc(&L.b, N)) != cudaSuccess || (e = dalloc(&L.r, N)) != cudaSuccess ||
                  (e = dalloc(&L.e, N)) != cudaSuccess)) ||
-        (e = dalloc(&L.cd, static_cast<size_t>(sv::NCLASS) * sv::CD_STRIDE)) != cudaSuccess) {
+        (e = dalloc(&L.cd, static_cast<size_t>(sv::CD_TOTAL))) != cudaSuccess) {
       free_all(h);
       delete h;
       return cuda_fail(e, "level allocation");

@@ -18,12 +18,30 @@ namespace sv {
 // nodes carry identity rows of K and zero b entries.  With z = K^-1 [bx by]^T
 // and s = [bx by] z:  dp = (z . r_u - r_p) / s,  du = K^-1 r_u - z dp,
 // which equals A_i^-1 r exactly (block elimination).
-constexpr int CD_KINV = 0;      // 25 x 25, row-major
+constexpr int CD_KINV = 0;      // 25 x 25, row-major (set-up only: kernels use the fast-diagonalisation factors)
 constexpr int CD_Z = 625;       // 50: z for u_x slots, then u_y slots
 constexpr int CD_SINV = 675;    // 1 / s
 constexpr int CD_STRIDE = 680;  // doubles per class
 constexpr int NCLASS = 25;
 constexpr int INTERIOR_CLASS = 12;  // 5 * 2 + 2
+
+// Fast diagonalisation of every class (appended to the class data at CD_EDGE).
+// Per axis class a (vertex index 0, 1, interior, n-1, n) the free window slots
+// F_a are {3,4}, {1..4}, {0..4}, {0..3}, {0,1}; on the free sub-rectangle
+// F_ax x F_ay the block is K = (nu/90) (k_F (x) m_F + m_F (x) k_F) again, so
+// K^-1 = (90/nu) (S_x (x) S_y) diag(1/(l_x + l_y)) (S_x (x) S_y)^T with the
+// generalised eigenvectors k_F S = m_F S diag(l), S^T m_F S = I.  S is stored
+// padded to 5 x 5 (zero rows off F_a, zero columns beyond |F_a|); slots off the
+// free rectangle keep identity rows (Dirichlet nodes: correction = residual).
+constexpr int EDGE_S = 0;        // 5 axis classes x [slot * 5 + mode]
+constexpr int EDGE_DINV = 125;   // 25 classes x [mode_y * 5 + mode_x]: (90/nu) / (l_x + l_y), 0 if padded
+constexpr int EDGE_TAB = 750;
+constexpr int CD_EDGE = NCLASS * CD_STRIDE;
+constexpr int CD_TOTAL = CD_EDGE + EDGE_TAB;   // doubles (or floats) of class data per level
+// bit s set: window slot s of axis class a holds a free Q2 node
+__host__ __device__ constexpr int axis_free_mask(int a) {
+  return a == 0 ? 0x18 : a == 1 ? 0x1E : a == 2 ? 0x1F : a == 3 ? 0x0F : 0x03;
+}
 
 // Fast-diagonalisation factors of the interior patch block (see sv_setup.cu):
 // se[m*3+k]: symmetric eigenvector k at reduced index m (entries 0/4, 1/3, 2);
@@ -133,6 +151,8 @@ void dense_operator(int n, double nu, std::vector<double>& A);
 bool coarse_inverse(int n, double nu, std::vector<double>& G);
 // Interior-class fast-diagonalisation factors (level independent for constant nu).
 FastDiag interior_fast_diag(double nu);
+// The EDGE_TAB fast-diagonalisation table of every class (layout above).
+void edge_fast_diag(double nu, double* tab);
 // In-place Gauss-Jordan inverse with partial pivoting; false if singular.
 bool invert_dense(std::vector<double>& a, int m);
 

@@ -74,7 +74,8 @@ double lap_entry(int I, int J, int I2, int J2, double nu) {
 void build_class_data(int n, double nu, std::vector<double>& cd, std::vector<double>* full_inv) {
   const int nq = 2 * n + 1;
   const double h = 1.0 / n;
-  cd.assign(static_cast<size_t>(NCLASS) * CD_STRIDE, 0.0);
+  cd.assign(static_cast<size_t>(CD_TOTAL), 0.0);
+  edge_fast_diag(nu, cd.data() + CD_EDGE);
   if (full_inv) full_inv->assign(static_cast<size_t>(NCLASS) * 51 * 51, 0.0);
   for (int cy = 0; cy < 5; ++cy) {
     for (int cx = 0; cx < 5; ++cx) {
@@ -188,10 +189,10 @@ void jacobi_eig(double* a, int m, double* w, double* v) {
   for (int i = 0; i < m; ++i) w[i] = a[i * m + i];
 }
 
-// Generalised symmetric eigenproblem A q = l B q, q^T B q = 1 (m <= 3): B = L L^T,
+// Generalised symmetric eigenproblem A q = l B q, q^T B q = 1 (m <= 5): B = L L^T,
 // C = L^-1 A L^-T, C = Q diag(l) Q^T, q = L^-T Q.  Columns of out are the q.
 void gen_eig(const double* A, const double* B, int m, double* lam, double* out) {
-  double L[9] = {0}, Li[9] = {0}, C[9], T[9], Q[9];
+  double L[25] = {0}, Li[25] = {0}, C[25], T[25], Q[25];
   for (int i = 0; i < m; ++i) {
     for (int j = 0; j <= i; ++j) {
       double s = B[i * m + j];
@@ -265,6 +266,42 @@ FastDiag interior_fast_diag(double nu) {
   for (int a = 0; a < 5; ++a)
     for (int b = 0; b < 5; ++b) f.dinv[a * 5 + b] = (90.0 / nu) / (lam[a] + lam[b]);
   return f;
+}
+
+void edge_fast_diag(double nu, double* tab) {
+  double kw[25], mw[25];
+  for (int r = 0; r < 5; ++r)
+    for (int c = 0; c < 5; ++c) {
+      kw[r * 5 + c] = k1(r & 1, c - r);
+      mw[r * 5 + c] = m1(r & 1, c - r);
+    }
+  double lam[5][5];
+  int nf[5];
+  for (int a = 0; a < 5; ++a) {
+    int F[5], m = 0;
+    for (int s = 0; s < 5; ++s)
+      if (axis_free_mask(a) & (1 << s)) F[m++] = s;
+    nf[a] = m;
+    double ka[25], ma[25], q[25], l[5];
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        ka[i * m + j] = kw[F[i] * 5 + F[j]];
+        ma[i * m + j] = mw[F[i] * 5 + F[j]];
+      }
+    gen_eig(ka, ma, m, l, q);
+    double* S = tab + EDGE_S + a * 25;
+    for (int k = 0; k < 25; ++k) S[k] = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int k = 0; k < m; ++k) S[F[i] * 5 + k] = q[i * m + k];
+    for (int k = 0; k < 5; ++k) lam[a][k] = (k < m) ? l[k] : 0.0;
+  }
+  for (int ay = 0; ay < 5; ++ay)
+    for (int ax = 0; ax < 5; ++ax) {
+      double* D = tab + EDGE_DINV + (5 * ay + ax) * 25;
+      for (int ky = 0; ky < 5; ++ky)
+        for (int kx = 0; kx < 5; ++kx)
+          D[ky * 5 + kx] = (ky < nf[ay] && kx < nf[ax]) ? (90.0 / nu) / (lam[ay][ky] + lam[ax][kx]) : 0.0;
+    }
 }
 
 void dense_operator(int n, double nu, std::vector<double>& A) {

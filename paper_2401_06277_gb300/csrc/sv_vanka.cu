@@ -9,8 +9,9 @@
 // there (every stencil coefficient is a compile-time constant: a thread
 // handles one 2x2 cell of Q2 nodes, whose four node parities are fixed),
 // solves every patch of the (TX+2) x (TY+2) region exactly with its class's
-// Schur factors (interior patches apply K^-1 by fast diagonalisation of its
-// tensor-product structure, boundary classes their dense K^-1), keeps the
+// Schur factors (K^-1 by fast diagonalisation of its tensor-product
+// structure: the interior factors, or per-axis factors for boundary classes,
+// whose free nodes form a sub-rectangle of the window), keeps the
 // corrections in shared memory, and writes
 // x + W (sum of corrections) for the dofs it owns: Q2 nodes
 // (2i-1..2i) x (2j-1..2j) of both components and p(i, j) for each owned
@@ -88,6 +89,65 @@ __device__ __forceinline__ void fd_solve(const FastDiagT<T>& f, const T* r, T* y
   for (int wj = 0; wj < 5; ++wj) fd_inv(f, Tm + wj * 5, y + wj * 5);
 }
 
+// y = K^-1 r on the window of a patch of any class (ax, ay) by fast
+// diagonalisation with the padded per-axis factors (sx, sy: [slot * 5 + mode]),
+// dv = (90/nu) / (l_x + l_y) per mode pair (0 for padded modes); window slots
+// off the free rectangle (fmask bit wj * 5 + wi clear) keep identity rows
+// (y = r there).  r is read from the shared residual window (row stride rs);
+// y, 25 values, is built in place in shared memory (rows, columns, columns,
+// rows), which keeps few values live in registers.
+template <typename T>
+__device__ __forceinline__ void fd_solve_edge(const T* __restrict__ sx, const T* __restrict__ sy,
+                                              const T* __restrict__ dv, int fmask, const T* r, int rs,
+                                              T* y) {
+#pragma unroll 1
+  for (int wj = 0; wj < 5; ++wj) {
+    T v[5];
+#pragma unroll
+    for (int wi = 0; wi < 5; ++wi) v[wi] = r[wj * rs + wi];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      T a = T(0);
+#pragma unroll
+      for (int wi = 0; wi < 5; ++wi) a = fma(v[wi], sx[wi * 5 + k], a);
+      y[wj * 5 + k] = a;
+    }
+  }
+#pragma unroll 1
+  for (int k = 0; k < 5; ++k) {
+    T v[5], u[5];
+#pragma unroll
+    for (int wj = 0; wj < 5; ++wj) v[wj] = y[wj * 5 + k];
+#pragma unroll
+    for (int k2 = 0; k2 < 5; ++k2) {
+      T a = T(0);
+#pragma unroll
+      for (int wj = 0; wj < 5; ++wj) a = fma(sy[wj * 5 + k2], v[wj], a);
+      u[k2] = a * dv[k2 * 5 + k];
+    }
+#pragma unroll
+    for (int wj = 0; wj < 5; ++wj) {
+      T a = T(0);
+#pragma unroll
+      for (int k2 = 0; k2 < 5; ++k2) a = fma(sy[wj * 5 + k2], u[k2], a);
+      y[wj * 5 + k] = a;
+    }
+  }
+#pragma unroll 1
+  for (int wj = 0; wj < 5; ++wj) {
+    T v[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] = y[wj * 5 + k];
+#pragma unroll
+    for (int wi = 0; wi < 5; ++wi) {
+      T a = T(0);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) a = fma(sx[wi * 5 + k], v[k], a);
+      y[wj * 5 + wi] = ((fmask >> (wj * 5 + wi)) & 1) ? a : r[wj * rs + wi];
+    }
+  }
+}
+
 template <typename R, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ cd,
                                               const FastDiagT<R> fdg, const R* __restrict__ x,
@@ -121,12 +181,18 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
   R* sr = sp + T::SP;
   R* srp = sr + T::SR;
   R* sd = srp + T::SRP;
+  R* se = sd + T::SD;   // fast-diagonalisation table of all classes (boundary tiles only)
   const int n = L.n, nq = L.nq, np = L.np;
   const long long nv = L.nv;
   const int i0 = bx * TX, j0 = by * TY;
   const int tid = threadIdx.x;
   const int XI0 = 2 * i0 - 6, XJ0 = 2 * j0 - 6;
   const int RI0 = 2 * i0 - 4, RJ0 = 2 * j0 - 4;
+
+  // 0. tiles with patches of vertices 0, 1, n-1 or n stage the per-class factors
+  const bool edge_tile = (i0 <= 2) || (j0 <= 2) || (i0 + TX >= n - 1) || (j0 + TY >= n - 1);
+  if (edge_tile)
+    for (int t = tid; t < EDGE_TAB; t += NT) se[t] = cd[CD_EDGE + t];
 
   // 1. x windows (Dirichlet / outside entries read as 0: their columns are
   //    dropped), b on the residual windows (0 outside).
@@ -200,7 +266,8 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
     const int qj = t / T::QW, qi = t - qj * T::QW;
     const int pi = i0 - 1 + qi, pj = j0 - 1 + qj;
     if (pi < 0 || pj < 0 || pi > n || pj > n) continue;
-    const int cls = 5 * axis_class(pj, n) + axis_class(pi, n);
+    const int ax = axis_class(pi, n), ay = axis_class(pj, n);
+    const int cls = 5 * ay + ax;
     const R* C = cd + cls * CD_STRIDE;
     R ru[50];
 #pragma unroll
@@ -215,8 +282,11 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
     for (int k = 0; k < 50; ++k) zr = fma(__ldg(C + CD_Z + k), ru[k], zr);
     const R dp = (zr - srp[t]) * __ldg(C + CD_SINV);
     R* D = sd + t * 51;
-    if (cls == INTERIOR_CLASS) {
-      // interior patch: K^-1 r_u by fast diagonalisation (exact up to rounding)
+    // K^-1 r_u by fast diagonalisation (exact up to rounding): warps whose
+    // patches are all interior use the symmetric/antisymmetric split of the
+    // interior factors; a warp with any boundary-class patch takes the
+    // per-axis factors for all of its patches (one path per warp)
+    if (!__any_sync(__activemask(), cls != INTERIOR_CLASS)) {
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         R y[25];
@@ -225,16 +295,18 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
         for (int o = 0; o < 25; ++o) D[c * 25 + o] = fma(-__ldg(C + CD_Z + c * 25 + o), dp, y[o]);
       }
     } else {
+      const int fx = axis_free_mask(ax), fy = axis_free_mask(ay);
+      int fmask = 0;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
+      for (int wj = 0; wj < 5; ++wj)
+        if ((fy >> wj) & 1) fmask |= fx << (5 * wj);
 #pragma unroll 1
-        for (int o = 0; o < 25; ++o) {
-          const R* Kr = C + CD_KINV + o * 25;
-          R acc = R(0);
-#pragma unroll
-          for (int k = 0; k < 25; ++k) acc = fma(__ldg(Kr + k), ru[c * 25 + k], acc);
-          D[c * 25 + o] = fma(-__ldg(C + CD_Z + c * 25 + o), dp, acc);
-        }
+      for (int c = 0; c < 2; ++c) {
+        R* y = D + c * 25;
+        fd_solve_edge<R>(se + EDGE_S + ax * 25, se + EDGE_S + ay * 25, se + EDGE_DINV + cls * 25, fmask,
+                         sr + c * T::RW * T::RH + (2 * qj) * T::RW + 2 * qi, T::RW, y);
+#pragma unroll 5
+        for (int o = 0; o < 25; ++o) y[o] = fma(-__ldg(C + CD_Z + c * 25 + o), dp, y[o]);
       }
     }
     D[50] = dp;
@@ -288,14 +360,14 @@ void launch_t(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x
     const int w = skip_hi - skip_lo + 1;
     grid = dim3(gx * gy - w * w, 1);
   }
-  k_vanka<R, TX, TY, NT><<<grid, NT, VT<TX, TY>::TOTAL * sizeof(R), s>>>(L, cd, fd, x, b, xo, omega,
-                                                                         skip_lo, skip_hi);
+  k_vanka<R, TX, TY, NT><<<grid, NT, (VT<TX, TY>::TOTAL + EDGE_TAB) * sizeof(R), s>>>(L, cd, fd, x, b, xo,
+                                                                                    omega, skip_lo, skip_hi);
 }
 
 template <typename R, int TX, int TY, int NT>
 cudaError_t prepare_t() {
   return cudaFuncSetAttribute(k_vanka<R, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(VT<TX, TY>::TOTAL * sizeof(R)));
+                              static_cast<int>((VT<TX, TY>::TOTAL + EDGE_TAB) * sizeof(R)));
 }
 
 template <typename R>
