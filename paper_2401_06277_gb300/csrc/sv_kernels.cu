@@ -21,109 +21,91 @@ __device__ __forceinline__ bool is_free(int I, int J, int nq) {
 // ---------------------------------------------------------------------------
 // Operator: y = A x (residual = 0) or y = b - A x (residual = 1).
 // One thread per vertex (a, b): the four Q2 nodes (2a..2a+1) x (2b..2b+1) of
-// both velocity components and the pressure row of (a, b).  Away from the
-// boundary (2 <= a, b <= n-2) every tap is in the free interior and the
-// stencil coefficients are compile-time constants (node parities are fixed
-// per node); near the boundary a masked generic path drops Dirichlet columns.
+// both velocity components and the pressure row of (a, b).  Node parities
+// are fixed per node, so every stencil coefficient is a compile-time constant.
 // ---------------------------------------------------------------------------
-template <typename T, int PI, int PJ>
-__device__ __forceinline__ T lap_g(const T* __restrict__ xs, int ld) {
-  T s = T(0);
-#pragma unroll
-  for (int dJ = -2; dJ <= 2; ++dJ) {
-#pragma unroll
-    for (int dI = -2; dI <= 2; ++dI) {
-      const T c = T(k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ));
-      if (c != T(0)) s = fma(c, xs[dJ * ld + dI], s);
-    }
-  }
-  return s;
-}
-
-template <typename T, int PI, int PJ, int COMP>
-__device__ __forceinline__ T btp_g(const T* __restrict__ pc, int ld) {
-  T g = T(0);
-#pragma unroll
-  for (int dj = -1; dj <= 1; ++dj) {
-#pragma unroll
-    for (int di = -1; di <= 1; ++di) {
-      const T w = T(COMP == 0 ? ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj)
-                              : ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj));
-      if (w != T(0)) g = fma(w, pc[dj * ld + di], g);
-    }
-  }
-  return g;
-}
-
-// generic masked evaluation of (A x) at velocity node (I, J), both components
-template <typename T>
-__device__ __forceinline__ void apply_vel_node(const LevelDev& L, const T* __restrict__ x, int I,
-                                               int J, T& ax, T& ay) {
+// One vertex (a, bb): the 6 x 6 x neighbourhood of each component (Q2 nodes
+// 2a-2..2a+3 x 2bb-2..2bb+3) and the 3 x 3 pressures around (a, bb) are read
+// once into registers; the four velocity rows of the cell and the pressure row
+// of the vertex are evaluated there with compile-time coefficients.  With MASK
+// (vertices within two of the boundary) entries outside the grid or on
+// Dirichlet nodes read as 0 (eliminated columns) and Dirichlet rows are the
+// identity.
+template <typename T, bool MASK>
+__device__ __forceinline__ void apply_vertex(const LevelDev& L, const T* __restrict__ x,
+                                             const T* __restrict__ b, T* __restrict__ y, int residual,
+                                             int a, int bb) {
   const int nq = L.nq, np = L.np, n = L.n;
   const long long nv = L.nv;
-  const long long k = static_cast<long long>(J) * nq + I;
-  if (!is_free(I, J, nq)) {
-    ax = x[k];
-    ay = x[nv + k];
-    return;
-  }
-  T sx = T(0), sy = T(0);
-  for (int dJ = -2; dJ <= 2; ++dJ) {
-    const int J2 = J + dJ;
-    if (J2 <= 0 || J2 >= nq - 1) continue;
-    const double mJ = m1(J, dJ), kJ = k1(J, dJ);
-    for (int dI = -2; dI <= 2; ++dI) {
-      const int I2 = I + dI;
-      if (I2 <= 0 || I2 >= nq - 1) continue;
-      const T c = T(k1(I, dI) * mJ + m1(I, dI) * kJ);
-      if (c == T(0)) continue;
-      const long long kk = static_cast<long long>(J2) * nq + I2;
-      sx = fma(c, x[kk], sx);
-      sy = fma(c, x[nv + kk], sy);
-    }
-  }
-  const T* p = x + 2 * nv;
-  T gx = T(0), gy = T(0);
-  for (int j = J / 2 - 1; j <= J / 2 + 1; ++j) {
-    if (j < 0 || j > n) continue;
-    for (int i = I / 2 - 1; i <= I / 2 + 1; ++i) {
-      if (i < 0 || i > n) continue;
-      const T wx = T(ccol(I, i) * ncol(J, j)), wy = T(ncol(I, i) * ccol(J, j));
-      const T pv = p[static_cast<long long>(j) * np + i];
-      if (wx != T(0)) gx = fma(wx, pv, gx);
-      if (wy != T(0)) gy = fma(wy, pv, gy);
-    }
-  }
+  const int I0 = 2 * a, J0 = 2 * bb;
   const T cl = T(L.cl), cb = T(L.cb);
-  ax = cl * sx + cb * gx;
-  ay = cl * sy + cb * gy;
-}
-
-template <typename T, int PI, int PJ>
-__device__ __forceinline__ void apply_node(const LevelDev& L, const T* __restrict__ x,
-                                           const T* __restrict__ b, T* __restrict__ y,
-                                           int residual, bool fast, int a, int bb) {
-  const int I = 2 * a + PI, J = 2 * bb + PJ;
-  const int nq = L.nq;
-  if (I >= nq || J >= nq) return;
-  const long long nv = L.nv;
-  const long long k = static_cast<long long>(J) * nq + I;
-  T ax, ay;
-  if (fast) {
-    const T cl = T(L.cl), cb = T(L.cb);
-    const T* pc = x + 2 * nv + static_cast<long long>(bb) * L.np + a;
-    ax = cl * lap_g<T, PI, PJ>(x + k, nq) + cb * btp_g<T, PI, PJ, 0>(pc, L.np);
-    ay = cl * lap_g<T, PI, PJ>(x + nv + k, nq) + cb * btp_g<T, PI, PJ, 1>(pc, L.np);
-  } else {
-    apply_vel_node<T>(L, x, I, J, ax, ay);
+  const T* p = x + 2 * nv;
+  T P[3][3];
+#pragma unroll
+  for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+    for (int di = 0; di < 3; ++di) {
+      const int pi = a + di - 1, pj = bb + dj - 1;
+      const bool ok = !MASK || (pi >= 0 && pj >= 0 && pi <= n && pj <= n);
+      P[dj][di] = ok ? p[static_cast<long long>(pj) * np + pi] : T(0);
+    }
+  T bu = T(0);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const T* xc = x + c * nv;
+    T X[6][6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const int I = I0 - 2 + q, J = J0 - 2 + r;
+        const bool ok = !MASK || is_free(I, J, nq);
+        X[r][q] = ok ? xc[static_cast<long long>(J) * nq + I] : T(0);
+      }
+#pragma unroll
+    for (int PJ = 0; PJ < 2; ++PJ) {
+#pragma unroll
+      for (int PI = 0; PI < 2; ++PI) {
+        const int I = I0 + PI, J = J0 + PJ;
+        if (MASK && (I >= nq || J >= nq)) continue;
+        const long long k = c * nv + static_cast<long long>(J) * nq + I;
+        T v;
+        if (MASK && !is_free(I, J, nq)) {
+          v = xc[static_cast<long long>(J) * nq + I];   // Dirichlet row: identity
+        } else {
+          T sl = T(0), g = T(0);
+#pragma unroll
+          for (int dJ = -2; dJ <= 2; ++dJ)
+#pragma unroll
+            for (int dI = -2; dI <= 2; ++dI) {
+              const T cf = T(k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ));
+              if (cf != T(0)) sl = fma(cf, X[PJ + dJ + 2][PI + dI + 2], sl);
+            }
+#pragma unroll
+          for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+            for (int di = -1; di <= 1; ++di) {
+              const T w = T(c == 0 ? ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj)
+                                   : ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj));
+              if (w != T(0)) g = fma(w, P[dj + 1][di + 1], g);
+            }
+          v = cl * sl + cb * g;
+        }
+        y[k] = residual ? b[k] - v : v;
+      }
+    }
+    // pressure row of (a, bb): taps at Q2 nodes (2a + dI, 2bb + dJ)
+#pragma unroll
+    for (int dJ = -2; dJ <= 2; ++dJ)
+#pragma unroll
+      for (int dI = -2; dI <= 2; ++dI) {
+        const T w = T(c == 0 ? crow(dI) * nrow(dJ) : nrow(dI) * crow(dJ));
+        if (w != T(0)) bu = fma(w, X[dJ + 2][dI + 2], bu);
+      }
   }
-  if (residual) {
-    y[k] = b[k] - ax;
-    y[nv + k] = b[nv + k] - ay;
-  } else {
-    y[k] = ax;
-    y[nv + k] = ay;
-  }
+  const T ap = cb * bu;
+  const long long k = 2 * nv + static_cast<long long>(bb) * np + a;
+  y[k] = residual ? b[k] - ap : ap;
 }
 
 template <typename T>
@@ -131,46 +113,12 @@ __global__ void k_apply(LevelDev L, const T* __restrict__ x, const T* __restrict
                         T* __restrict__ y, int residual) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   const int bb = blockIdx.y * blockDim.y + threadIdx.y;
-  const int n = L.n, nq = L.nq, np = L.np;
+  const int n = L.n;
   if (a > n || bb > n) return;
-  const bool fast = a >= 2 && a <= n - 2 && bb >= 2 && bb <= n - 2;
-  apply_node<T, 0, 0>(L, x, b, y, residual, fast, a, bb);
-  apply_node<T, 1, 0>(L, x, b, y, residual, fast, a, bb);
-  apply_node<T, 0, 1>(L, x, b, y, residual, fast, a, bb);
-  apply_node<T, 1, 1>(L, x, b, y, residual, fast, a, bb);
-  // pressure row of vertex (a, bb): (B u)
-  const long long nv = L.nv;
-  T s = T(0);
-  if (fast) {
-    const T* u0 = x + static_cast<long long>(2 * bb) * nq + 2 * a;
-#pragma unroll
-    for (int dJ = -2; dJ <= 2; ++dJ) {
-#pragma unroll
-      for (int dI = -2; dI <= 2; ++dI) {
-        const T cx = T(crow(dI) * nrow(dJ)), cy = T(nrow(dI) * crow(dJ));
-        if (cx != T(0)) s = fma(cx, u0[dJ * nq + dI], s);
-        if (cy != T(0)) s = fma(cy, u0[nv + dJ * nq + dI], s);
-      }
-    }
-  } else {
-#pragma unroll
-    for (int dJ = -2; dJ <= 2; ++dJ) {
-      const int J = 2 * bb + dJ;
-      if (J <= 0 || J >= nq - 1) continue;
-#pragma unroll
-      for (int dI = -2; dI <= 2; ++dI) {
-        const int I = 2 * a + dI;
-        if (I <= 0 || I >= nq - 1) continue;
-        const long long kk = static_cast<long long>(J) * nq + I;
-        const T cx = T(crow(dI) * nrow(dJ)), cy = T(nrow(dI) * crow(dJ));
-        if (cx != T(0)) s = fma(cx, x[kk], s);
-        if (cy != T(0)) s = fma(cy, x[nv + kk], s);
-      }
-    }
-  }
-  const T ap = T(L.cb) * s;
-  const long long k = 2 * nv + static_cast<long long>(bb) * np + a;
-  y[k] = residual ? b[k] - ap : ap;
+  if (a >= 2 && a <= n - 2 && bb >= 2 && bb <= n - 2)
+    apply_vertex<T, false>(L, x, b, y, residual, a, bb);
+  else
+    apply_vertex<T, true>(L, x, b, y, residual, a, bb);
 }
 
 // ---------------------------------------------------------------------------
@@ -264,127 +212,157 @@ __global__ void k_rhs_transpose(LevelDev L, const double* __restrict__ lam, doub
 // node 2G coincides with coarse node G (weight 1); an odd fine node
 // 4e+1 / 4e+3 inside coarse element e takes the coarse quadratic at t = 1/4 /
 // 3/4: weights (3/8, 3/4, -1/8) / (-1/8, 3/4, 3/8) on coarse nodes 2e..2e+2.
-// Q1: fine vertex 2g <- coarse g; 2g+1 <- (1/2, 1/2) on g, g+1.  All weights
-// are computed in registers (no tables).
+// Q1: fine vertex 2g <- coarse g; 2g+1 <- (1/2, 1/2) on g, g+1.  The weights
+// are compile-time constants of the element type; both passes are separable
+// (x, then y) in registers.
 // ---------------------------------------------------------------------------
 
-// coarse nodes and weights feeding fine Q2 node F on one axis; returns the count (1 or 3)
-__device__ __forceinline__ int q2_interp(int F, int nc, int* G, double* w) {
-  if ((F & 1) == 0) {
-    G[0] = F >> 1;
-    w[0] = 1.0;
-    return 1;
-  }
-  int e = F >> 2;
-  if (e > nc - 1) e = nc - 1;
-  const bool first = (F - 4 * e) == 1;
-  G[0] = 2 * e;
-  G[1] = 2 * e + 1;
-  G[2] = 2 * e + 2;
-  w[0] = first ? 0.375 : -0.125;
-  w[1] = 0.75;
-  w[2] = first ? -0.125 : 0.375;
-  return 3;
+// Per axis, fine Q2 nodes 4e..4e+3 of coarse element e take coarse nodes
+// 2e..2e+2 with the weights PW[f][g] (rows f = 0..3); the transpose gives coarse
+// nodes 2e, 2e+1 from fine nodes 4e-3..4e+3 with RW[g][k], k = F - (4e - 3).
+// All weights are exact binary fractions.
+__host__ __device__ constexpr double pw(int f, int g) {
+  return f == 0 ? (g == 0 ? 1.0 : 0.0)
+       : f == 1 ? (g == 0 ? 0.375 : g == 1 ? 0.75 : -0.125)
+       : f == 2 ? (g == 1 ? 1.0 : 0.0)
+                : (g == 0 ? -0.125 : g == 1 ? 0.75 : 0.375);
+}
+__host__ __device__ constexpr double rw(int g, int k) {
+  // g = 0: fine 4e-3, 4e-1, 4e, 4e+1, 4e+3 -> k = 0, 2, 3, 4, 6 ; g = 1: fine 4e+1..4e+3 -> k = 4, 5, 6
+  return g == 0 ? (k == 0 || k == 6 ? -0.125 : k == 2 || k == 4 ? 0.375 : k == 3 ? 1.0 : 0.0)
+                : (k == 4 || k == 6 ? 0.75 : k == 5 ? 1.0 : 0.0);
 }
 
-// fine Q2 nodes fed by coarse Q2 node G on one axis (the transpose); returns the count (1, 3 or 5)
-__device__ __forceinline__ int q2_restrict(int G, int* F, double* w) {
-  if (G & 1) {  // coarse element midpoint: fine nodes 2G-1, 2G, 2G+1
-    F[0] = 2 * G - 1;
-    F[1] = 2 * G;
-    F[2] = 2 * G + 1;
-    w[0] = 0.75;
-    w[1] = 1.0;
-    w[2] = 0.75;
-    return 3;
-  }
-  F[0] = 2 * G - 3;  // coarse vertex: fine 2G-3, 2G-1, 2G, 2G+1, 2G+3
-  F[1] = 2 * G - 1;
-  F[2] = 2 * G;
-  F[3] = 2 * G + 1;
-  F[4] = 2 * G + 3;
-  w[0] = -0.125;
-  w[1] = 0.375;
-  w[2] = 1.0;
-  w[3] = 0.375;
-  w[4] = -0.125;
-  return 5;
-}
-
+// One thread per coarse element (ex, ey), ex, ey in 0..nc (the last one only
+// reaches the far boundary nodes): coarse Q2 nodes (2ex + gx, 2ey + gy),
+// g in {0, 1}, and coarse vertex (ex, ey).
 template <typename T>
 __global__ void k_restrict(LevelDev F, LevelDev C, const T* __restrict__ rf, T* __restrict__ rc) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J = blockIdx.y * blockDim.y + threadIdx.y;
-  if (I < C.nq && J < C.nq) {
-    const long long k = static_cast<long long>(J) * C.nq + I;
-    T sx = T(0), sy = T(0);
-    if (is_free(I, J, C.nq)) {
-      int FI[5], FJ[5];
-      double wI[5], wJ[5];
-      const int ni = q2_restrict(I, FI, wI), nj = q2_restrict(J, FJ, wJ);
-      for (int b = 0; b < nj; ++b) {
-        if (FJ[b] <= 0 || FJ[b] >= F.nq - 1) continue;
-        for (int a = 0; a < ni; ++a) {
-          if (FI[a] <= 0 || FI[a] >= F.nq - 1) continue;
-          const long long kf = static_cast<long long>(FJ[b]) * F.nq + FI[a];
-          const T w = T(wI[a] * wJ[b]);
-          sx = fma(w, rf[kf], sx);
-          sy = fma(w, rf[F.nv + kf], sy);
-        }
+  const int ex = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ey = blockIdx.y * blockDim.y + threadIdx.y;
+  if (ex > C.n || ey > C.n) return;
+  const int fq = F.nq, cq = C.nq;
+  const int F0x = 4 * ex - 3, F0y = 4 * ey - 3;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const T* r = rf + c * F.nv;
+    T H[7][2];
+#pragma unroll
+    for (int k2 = 0; k2 < 7; ++k2) {
+      const int J = F0y + k2;
+      T v[7];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const int I = F0x + k;
+        v[k] = (rw(0, k) != 0.0 || rw(1, k) != 0.0) && is_free(I, J, fq) ? r[static_cast<long long>(J) * fq + I]
+                                                                        : T(0);
+      }
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < 7; ++k)
+          if (rw(g, k) != 0.0) acc = fma(T(rw(g, k)), v[k], acc);
+        H[k2][g] = acc;
       }
     }
-    rc[k] = sx;
-    rc[C.nv + k] = sy;
-  }
-  if (I < C.np && J < C.np) {
-    T s = T(0);
-    for (int dj = -1; dj <= 1; ++dj) {
-      const int fj = 2 * J + dj;
-      if (fj < 0 || fj >= F.np) continue;
-      for (int di = -1; di <= 1; ++di) {
-        const int fi = 2 * I + di;
-        if (fi < 0 || fi >= F.np) continue;
-        const T w = T((di == 0 ? 1.0 : 0.5) * (dj == 0 ? 1.0 : 0.5));
-        s = fma(w, rf[2 * F.nv + static_cast<long long>(fj) * F.np + fi], s);
+#pragma unroll
+    for (int gy = 0; gy < 2; ++gy) {
+#pragma unroll
+      for (int gx = 0; gx < 2; ++gx) {
+        const int I = 2 * ex + gx, J = 2 * ey + gy;
+        if (I >= cq || J >= cq) continue;
+        T acc = T(0);
+#pragma unroll
+        for (int k2 = 0; k2 < 7; ++k2)
+          if (rw(gy, k2) != 0.0) acc = fma(T(rw(gy, k2)), H[k2][gx], acc);
+        rc[c * C.nv + static_cast<long long>(J) * cq + I] = is_free(I, J, cq) ? acc : T(0);
       }
     }
-    rc[2 * C.nv + static_cast<long long>(J) * C.np + I] = s;
   }
+  // Q1: coarse vertex (ex, ey) <- fine vertices 2e-1, 2e, 2e+1 per axis (1/2, 1, 1/2)
+  const T* pf = rf + 2 * F.nv;
+  T s = T(0);
+#pragma unroll
+  for (int dj = -1; dj <= 1; ++dj) {
+    const int fj = 2 * ey + dj;
+#pragma unroll
+    for (int di = -1; di <= 1; ++di) {
+      const int fi = 2 * ex + di;
+      if (fi < 0 || fj < 0 || fi >= F.np || fj >= F.np) continue;
+      s = fma(T((di == 0 ? 1.0 : 0.5) * (dj == 0 ? 1.0 : 0.5)), pf[static_cast<long long>(fj) * F.np + fi], s);
+    }
+  }
+  rc[2 * C.nv + static_cast<long long>(ey) * C.np + ex] = s;
 }
 
+// x_f += P e_c; one thread per coarse element (ex, ey), ex, ey in 0..nc: fine
+// Q2 nodes (4ex + fx, 4ey + fy), f in 0..3, and fine vertices (2ex + fx, 2ey + fy),
+// f in {0, 1}.  Coarse Dirichlet values read as 0; fine Dirichlet rows are untouched.
 template <typename T>
 __global__ void k_prolong_add(LevelDev F, LevelDev C, const T* __restrict__ ec, T* __restrict__ xf) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J = blockIdx.y * blockDim.y + threadIdx.y;
-  if (I < F.nq && J < F.nq && is_free(I, J, F.nq)) {
-    int GI[3], GJ[3];
-    double wI[3], wJ[3];
-    const int ni = q2_interp(I, C.n, GI, wI), nj = q2_interp(J, C.n, GJ, wJ);
-    T sx = T(0), sy = T(0);
-    for (int b = 0; b < nj; ++b) {
-      if (GJ[b] <= 0 || GJ[b] >= C.nq - 1) continue;  // coarse Dirichlet row
-      for (int a = 0; a < ni; ++a) {
-        if (GI[a] <= 0 || GI[a] >= C.nq - 1) continue;
-        const long long kc = static_cast<long long>(GJ[b]) * C.nq + GI[a];
-        const T w = T(wI[a] * wJ[b]);
-        sx = fma(w, ec[kc], sx);
-        sy = fma(w, ec[C.nv + kc], sy);
+  const int ex = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ey = blockIdx.y * blockDim.y + threadIdx.y;
+  if (ex > C.n || ey > C.n) return;
+  const int fq = F.nq, cq = C.nq;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const T* e = ec + c * C.nv;
+    T H[3][4];
+#pragma unroll
+    for (int gy = 0; gy < 3; ++gy) {
+      const int J = 2 * ey + gy;
+      T v[3];
+#pragma unroll
+      for (int gx = 0; gx < 3; ++gx) {
+        const int I = 2 * ex + gx;
+        v[gx] = is_free(I, J, cq) ? e[static_cast<long long>(J) * cq + I] : T(0);
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        T acc = T(0);
+#pragma unroll
+        for (int g = 0; g < 3; ++g)
+          if (pw(f, g) != 0.0) acc = fma(T(pw(f, g)), v[g], acc);
+        H[gy][f] = acc;
       }
     }
-    const long long k = static_cast<long long>(J) * F.nq + I;
-    xf[k] += sx;
-    xf[F.nv + k] += sy;
+#pragma unroll
+    for (int fy = 0; fy < 4; ++fy) {
+#pragma unroll
+      for (int fx = 0; fx < 4; ++fx) {
+        const int I = 4 * ex + fx, J = 4 * ey + fy;
+        if (!is_free(I, J, fq)) continue;
+        T acc = T(0);
+#pragma unroll
+        for (int g = 0; g < 3; ++g)
+          if (pw(fy, g) != 0.0) acc = fma(T(pw(fy, g)), H[g][fx], acc);
+        xf[c * F.nv + static_cast<long long>(J) * fq + I] += acc;
+      }
+    }
   }
-  if (I < F.np && J < F.np) {
-    // fine vertex (I, J) <- coarse vertices (I/2 .. (I+1)/2, J/2 .. (J+1)/2), weights 1 or 1/2 per axis
-    const int i0 = I >> 1, i1 = (I + 1) >> 1, j0 = J >> 1, j1 = (J + 1) >> 1;
-    const T wi = (I & 1) ? T(0.5) : T(1.0), wj = (J & 1) ? T(0.5) : T(1.0);
-    const T* p = ec + 2 * C.nv;
-    T s = wi * wj * p[static_cast<long long>(j0) * C.np + i0];
-    if (I & 1) s = fma(wi * wj, p[static_cast<long long>(j0) * C.np + i1], s);
-    if (J & 1) s = fma(wi * wj, p[static_cast<long long>(j1) * C.np + i0], s);
-    if ((I & 1) && (J & 1)) s = fma(wi * wj, p[static_cast<long long>(j1) * C.np + i1], s);
-    xf[2 * F.nv + static_cast<long long>(J) * F.np + I] += s;
+  // Q1: fine vertex 2e <- coarse e; 2e+1 <- (e + (e+1)) / 2, per axis
+  const T* p = ec + 2 * C.nv;
+  T P[2][2];
+#pragma unroll
+  for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+    for (int di = 0; di < 2; ++di) {
+      const int i = ex + di, j = ey + dj;
+      P[dj][di] = (i <= C.n && j <= C.n) ? p[static_cast<long long>(j) * C.np + i] : T(0);
+    }
+#pragma unroll
+  for (int fy = 0; fy < 2; ++fy) {
+#pragma unroll
+    for (int fx = 0; fx < 2; ++fx) {
+      const int I = 2 * ex + fx, J = 2 * ey + fy;
+      if (I >= F.np || J >= F.np) continue;
+      T v = P[0][0];
+      if (fx == 1 && fy == 0) v = T(0.5) * (P[0][0] + P[0][1]);
+      if (fx == 0 && fy == 1) v = T(0.5) * (P[0][0] + P[1][0]);
+      if (fx == 1 && fy == 1) v = T(0.25) * ((P[0][0] + P[0][1]) + (P[1][0] + P[1][1]));
+      xf[2 * F.nv + static_cast<long long>(J) * F.np + I] += v;
+    }
   }
 }
 
@@ -439,14 +417,14 @@ template <typename T>
 void launch_restrict(const LevelDev& F, const LevelDev& C, const T* rf, T* rc, cudaStream_t s) {
   count_launches(1);
   dim3 blk(32, 8);
-  k_restrict<T><<<grid2(C.nq, C.nq, blk), blk, 0, s>>>(F, C, rf, rc);
+  k_restrict<T><<<grid2(C.n + 1, C.n + 1, blk), blk, 0, s>>>(F, C, rf, rc);
 }
 
 template <typename T>
 void launch_prolong_add(const LevelDev& F, const LevelDev& C, const T* ec, T* xf, cudaStream_t s) {
   count_launches(1);
   dim3 blk(32, 8);
-  k_prolong_add<T><<<grid2(F.nq, F.nq, blk), blk, 0, s>>>(F, C, ec, xf);
+  k_prolong_add<T><<<grid2(C.n + 1, C.n + 1, blk), blk, 0, s>>>(F, C, ec, xf);
 }
 
 template <typename TI, typename TO>
