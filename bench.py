@@ -31,7 +31,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "Stokes DoF/s per Vanka V-cycle (FGMRES to 1e-8 residual)"
+METRIC = "Stokes DoF/s per Vanka V-cycle + FGMRES time-to-1e-8 residual, mixed vs FP64"
 UNIT = "DoF/s"
 SM_COUNT = 152
 ORACLE_N = 256
@@ -203,6 +203,19 @@ def job_throughput(ws, units_local: float, ms_local: float) -> tuple[float, floa
 # --------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the finest-level sweep
+# kernel at 1024 x 1024 (ncu --set full, summaries in profiles/); at other sizes the
+# bench scales them by the number of dofs (the traffic of a sweep is proportional)
+TRAFFIC_1024 = {
+    "fp64": {"bytes": 151381504 + 49990400, "tile": "16x16",
+             "source": "profiles/k_vanka_f64_n1024.md (k_vanka<double,16,16>; writes still in L2 at kernel end "
+                       "are not counted)"},
+    "bf16": {"bytes": 74839040 + 12048384, "tile": "14x14",
+             "source": "profiles/k_vanka_tc_n1024.md (k_vanka_tc interior tiles; the ring launch is not "
+                       "included; writes still in L2 at kernel end are not counted)"},
+}
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -224,7 +237,7 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e):
     dev = torch.device("cuda", torch.cuda.current_device())
     n = args.n
     N = dofs(n)
-    H = pkg.Hierarchy(n, rtol=1e-8, restart=30, prec=PRECS[prec_name])
+    H = pkg.Hierarchy(n, rtol=1e-8, restart=30, prec=PRECS[prec_name], tile=args.tile)
     f = f_host.to(dev)
     ud = ud_host.to(dev)
     b = H.assemble_rhs(f, ud)
@@ -284,16 +297,40 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e):
         by = 3.0 * 4.0 * N
         peak = peaks.get("hbm_gbs", 6780.0)
         achieved = by / (sweep_ms * 1e-3) / 1e9
-        roofline = {"bound": "hbm", "kernel": "k_vanka<float> (finest level)", "achieved": round(achieved, 1),
+        kname = ("k_vanka_tc interior tiles + k_vanka<float,14,14> ring (finest level)" if prec_name == "bf16"
+                 else "k_vanka<float> (finest level)")
+        roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                     "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
                     "algorithmic_bytes_per_launch": by,
                     "fp32_gflops_achieved": round(sweep_flops(n) / (sweep_ms * 1e-3) / 1e9, 1)}
-    roofline.update({"launch_ms": round(sweep_ms, 4), "launches_timed": st["sweeps_timed"], "tile": tile})
+    names = ["8x8", "16x8", "16x16", "14x14"]
+    tiles = [names[stokes.stokes_level_tile(H.handle, lv)] for lv in range(H.levels - 1, 0, -1)]
+    roofline.update({"launch_ms": round(sweep_ms, 4), "launches_timed": st["sweeps_timed"], "tile": tile,
+                     "tiles_fine_to_coarse": tiles})
+    tr = TRAFFIC_1024.get(prec_name)
+    if tr is not None and tile == tr["tile"]:
+        # DRAM bytes of one launch of the same kernel at 1024^2 (ncu capture), scaled by dofs
+        roofline["traffic"] = round(tr["bytes"] * dofs(n) / dofs(1024))
+        roofline["traffic_source"] = tr["source"]
     rec = {"value": value, "ms_per_step": ms_max / args.steps, "iters": iters, "relres": rels,
            "vcycles": int(vcycles_all), "ms_per_vcycle": ms_max / max(st["vcycles"], 1),
            "time_to_solution_s": ms_max / args.steps / 1e3, "roofline": roofline,
            "gpu_launches": launches, "clocks": clk, "levels": H.levels}
+    # the V-cycle alone (dofs per second of one preconditioner application), after the timed
+    # region: 10 applications to the assembled right-hand side, CUDA events on the stream
+    z = torch.empty_like(b)
+    for _ in range(2):
+        stokes.stokes_vcycle_apply(H.handle, b, z)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(10):
+        stokes.stokes_vcycle_apply(H.handle, b, z)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    vc_ms = allmax(ws, e0.elapsed_time(e1) / 10)
+    rec["vcycle_only"] = {"ms": vc_ms, "value": ws * N / (vc_ms * 1e-3), "unit": UNIT}
+    del z
     if with_e2e:
         x_host = torch.empty(N, dtype=torch.float64).pin_memory()
         bi = f_host.numel() * 8 + ud_host.numel() * 8
@@ -400,13 +437,14 @@ def run_ours(args) -> None:
     f_host = torch.from_numpy(si.random_force(n, args.seed + rank)).pin_memory()
     ud_host = torch.from_numpy(si.manufactured_velocity(n)).pin_memory()
     main = time_form(args, args.prec, ws, rank, f_host, ud_host, with_e2e=True)
-    forms = {args.prec: {k: main[k] for k in ("value", "time_to_solution_s", "iters", "ms_per_vcycle")}}
+    keys = ("value", "time_to_solution_s", "iters", "ms_per_vcycle", "vcycle_only")
+    forms = {args.prec: {k: main[k] for k in keys}}
     if not args.single_form:
         for other in PRECS:
             if other == args.prec:
                 continue
             o = time_form(args, other, ws, rank, f_host, ud_host, with_e2e=False)
-            forms[other] = {k: o[k] for k in ("value", "time_to_solution_s", "iters", "ms_per_vcycle")}
+            forms[other] = {k: o[k] for k in keys}
             forms[other]["roofline"] = o["roofline"]
     batched = None
     if not args.no_batch:
@@ -432,6 +470,7 @@ def run_ours(args) -> None:
                            "parallelism": f"replicas x{ws}"},
                 "time_to_solution_s": main["time_to_solution_s"], "iters": main["iters"],
                 "relres": main["relres"], "vcycles": main["vcycles"], "ms_per_vcycle": main["ms_per_vcycle"],
+                "vcycle_only": main["vcycle_only"],
                 "roofline": main["roofline"], "cpu_baseline": cpu, "e2e": main["e2e"],
                 "gpu_launches": main["gpu_launches"], "clocks": main["clocks"], "forms": forms,
                 "batched": batched}

@@ -124,40 +124,71 @@ __global__ void k_apply(LevelDev L, const T* __restrict__ x, const T* __restrict
 // ---------------------------------------------------------------------------
 // Right-hand side b = [M f - L_{.,D} u_D ; u_D on D ; -B_{.,D} u_D].
 // ---------------------------------------------------------------------------
-__global__ void k_rhs_vel(LevelDev L, const double* __restrict__ f, const double* __restrict__ ud,
-                          double* __restrict__ b) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x;
-  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+// One vertex (a, bb): the four Q2 nodes (2a + PI, 2bb + PJ) of both components.
+// b = (h/30)^2 (m (x) m) f on free rows, minus nu/90 (k (x) m + m (x) k) u_D over
+// the Dirichlet columns (MASK: vertices within two of the boundary only), and
+// b = u_D on Dirichlet rows.  The 6 x 6 f (and u_D) neighbourhood of each
+// component is read once; coefficients are compile-time constants.
+template <bool MASK>
+__device__ __forceinline__ void rhs_vertex(const LevelDev& L, const double* __restrict__ f,
+                                           const double* __restrict__ ud, double* __restrict__ b, int a,
+                                           int bb) {
   const int nq = L.nq;
-  if (I >= nq || J >= nq) return;
   const long long nv = L.nv;
-  const long long k = static_cast<long long>(J) * nq + I;
-  if (!is_free(I, J, nq)) {
-    b[k] = ud[k];
-    b[nv + k] = ud[nv + k];
-    return;
-  }
-  double mx = 0.0, my = 0.0, lx = 0.0, ly = 0.0;
-  for (int dJ = -2; dJ <= 2; ++dJ) {
-    const int J2 = J + dJ;
-    if (J2 < 0 || J2 >= nq) continue;
-    for (int dI = -2; dI <= 2; ++dI) {
-      const int I2 = I + dI;
-      if (I2 < 0 || I2 >= nq) continue;
-      const long long kk = static_cast<long long>(J2) * nq + I2;
-      const double mm = m1(I, dI) * m1(J, dJ);
-      mx = fma(mm, f[kk], mx);
-      my = fma(mm, f[nv + kk], my);
-      if (!is_free(I2, J2, nq)) {
-        const double c = k1(I, dI) * m1(J, dJ) + m1(I, dI) * k1(J, dJ);
-        lx = fma(c, ud[kk], lx);
-        ly = fma(c, ud[nv + kk], ly);
+  const int I0 = 2 * a, J0 = 2 * bb;
+  const double cm = (L.h / 30.0) * (L.h / 30.0), cl = L.nu / 90.0;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    double F[6][6], U[6][6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const int I = I0 - 2 + q, J = J0 - 2 + r;
+        const bool in = !MASK || (I >= 0 && J >= 0 && I < nq && J < nq);
+        const long long k = c * nv + static_cast<long long>(J) * nq + I;
+        F[r][q] = in ? f[k] : 0.0;
+        U[r][q] = (MASK && in && !is_free(I, J, nq)) ? ud[k] : 0.0;
+      }
+#pragma unroll
+    for (int PJ = 0; PJ < 2; ++PJ) {
+#pragma unroll
+      for (int PI = 0; PI < 2; ++PI) {
+        const int I = I0 + PI, J = J0 + PJ;
+        if (MASK && (I >= nq || J >= nq)) continue;
+        const long long k = c * nv + static_cast<long long>(J) * nq + I;
+        if (MASK && !is_free(I, J, nq)) {
+          b[k] = ud[k];
+          continue;
+        }
+        double sm = 0.0, sl = 0.0;
+#pragma unroll
+        for (int dJ = -2; dJ <= 2; ++dJ)
+#pragma unroll
+          for (int dI = -2; dI <= 2; ++dI) {
+            const double mm = m1(PI, dI) * m1(PJ, dJ);
+            if (mm != 0.0) sm = fma(mm, F[PJ + dJ + 2][PI + dI + 2], sm);
+            if (MASK) {
+              const double cf = k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ);
+              if (cf != 0.0) sl = fma(cf, U[PJ + dJ + 2][PI + dI + 2], sl);
+            }
+          }
+        b[k] = cm * sm - cl * sl;
       }
     }
   }
-  const double cm = (L.h / 30.0) * (L.h / 30.0), cl = L.nu / 90.0;
-  b[k] = cm * mx - cl * lx;
-  b[nv + k] = cm * my - cl * ly;
+}
+
+__global__ void k_rhs_vel(LevelDev L, const double* __restrict__ f, const double* __restrict__ ud,
+                          double* __restrict__ b) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int bb = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = L.n;
+  if (a > n || bb > n) return;
+  if (a >= 2 && a <= n - 2 && bb >= 2 && bb <= n - 2)
+    rhs_vertex<false>(L, f, ud, b, a, bb);
+  else
+    rhs_vertex<true>(L, f, ud, b, a, bb);
 }
 
 __global__ void k_rhs_p(LevelDev L, const double* __restrict__ ud, double* __restrict__ b) {
@@ -373,18 +404,18 @@ __global__ void k_convert(const TI* __restrict__ in, TO* __restrict__ out, long 
     out[i] = static_cast<TO>(in[i]);
 }
 
-// e = G r, G dense N0 x N0 (one CTA)
+// e = G r, G dense N0 x N0: one warp per row, lanes along the row (coalesced),
+// summed by a fixed shuffle tree (deterministic)
 __global__ void k_coarse(const double* __restrict__ G, int N0, const double* __restrict__ r,
                          double* __restrict__ e) {
-  extern __shared__ double sr_[];
-  for (int k = threadIdx.x; k < N0; k += blockDim.x) sr_[k] = r[k];
-  __syncthreads();
-  for (int row = threadIdx.x; row < N0; row += blockDim.x) {
-    double s = 0.0;
-    const double* g = G + static_cast<long long>(row) * N0;
-    for (int k = 0; k < N0; ++k) s = fma(g[k], sr_[k], s);
-    e[row] = s;
-  }
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= N0) return;
+  const double* g = G + static_cast<long long>(row) * N0;
+  double s = 0.0;
+  for (int k = lane; k < N0; k += 32) s = fma(g[k], __ldg(r + k), s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) e[row] = s;
 }
 
 dim3 grid2(int nx, int ny, dim3 blk) {
@@ -403,7 +434,7 @@ void launch_apply(const LevelDev& L, const T* x, const T* b, T* y, int residual,
 void launch_rhs(const LevelDev& L, const double* f, const double* ud, double* b, cudaStream_t s) {
   count_launches(2);
   dim3 blk(32, 8);
-  k_rhs_vel<<<grid2(L.nq, L.nq, blk), blk, 0, s>>>(L, f, ud, b);
+  k_rhs_vel<<<grid2(L.np, L.np, blk), blk, 0, s>>>(L, f, ud, b);
   k_rhs_p<<<grid2(L.np, L.np, blk), blk, 0, s>>>(L, ud, b);
 }
 
@@ -437,7 +468,7 @@ void launch_convert(const TI* in, TO* out, long long N, cudaStream_t s) {
 
 void launch_coarse(const double* G, int N0, const double* r, double* e, cudaStream_t s) {
   count_launches(1);
-  k_coarse<<<1, 256, N0 * sizeof(double), s>>>(G, N0, r, e);
+  k_coarse<<<(N0 + 7) / 8, 256, 0, s>>>(G, N0, r, e);
 }
 
 template void launch_apply<double>(const LevelDev&, const double*, const double*, double*, int, cudaStream_t);
