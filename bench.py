@@ -46,14 +46,15 @@ def sweep_flops(n: int) -> float:
 
     Per vertex (one patch, and one cell of owned dofs: 4 Q2 nodes x 2
     components + 1 pressure): residual 2 (2 (64 + 12) + 24) + 9 = 361 and
-    weighted update 2 (9 + 6 + 6 + 4) + 16 + 2 = 68.  Patch solve: the
-    Schur-factored dense class inverse costs 2 (2 * 625 + 50 + 50) + 2 = 2702
-    on the 8n - 8 boundary patches; the (n - 3)^2 interior patches apply K^-1
-    by fast diagonalisation, 2 x (4 stages x 5 vectors x 25 + 25) = 1050,
-    plus 102 for dp and 100 for the z-correction: 1252."""
+    weighted update 2 (9 + 6 + 6 + 4) + 16 + 2 = 68.  Patch solve (Schur
+    factored, K^-1 by fast diagonalisation): the (n - 3)^2 interior patches use
+    the symmetric / antisymmetric split, 2 x (4 stages x 5 vectors x 25 + 25)
+    = 1050, plus 102 for dp and 100 for the z-correction: 1252; the 8n - 8
+    boundary patches use full 5 x 5 per-axis factors, 2 x (4 x 25 x 10 + 25)
+    = 2050, plus 202: 2252."""
     nv = (n + 1) ** 2
     ni = (n - 3) ** 2 if n >= 4 else 0
-    return nv * (361.0 + 68.0) + ni * 1252.0 + (nv - ni) * 2702.0
+    return nv * (361.0 + 68.0) + ni * 1252.0 + (nv - ni) * 2252.0
 
 
 def sweep_bytes(n: int) -> float:

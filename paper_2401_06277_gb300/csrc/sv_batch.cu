@@ -1,7 +1,7 @@
 // sv_batch.cu -- many independent Stokes problems (same or different grid
 // sizes) solved together: right-preconditioned FGMRES (Section 6.8) in
 // lockstep over the problems, with iteration j of every problem -- its V-cycle
-// (Algorithm 1 with additive Vanka, Algorithm 3), operator, CGS2 Arnoldi and
+// (Algorithm 1 with additive Vanka, Algorithm 3), operator, Gram-Schmidt Arnoldi and
 // Givens rotation -- recorded once as a CUDA graph with one branch per
 // problem.  Branches are independent, so the GPU runs the many small
 // coarse-level kernels of all problems concurrently; the host synchronises
