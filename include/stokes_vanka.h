@@ -78,7 +78,20 @@ typedef struct {
   stokes_precision prec;  /*                                          (FP64) */
   int tile;         /* Vanka tile shape: -1 = chosen per level by timing at
                        creation, 0 = 8x8, 1 = 16x8, 2 = 16x16 vertices (-1) */
+  int smoother;     /* stokes_smoother below                             (0)  */
 } stokes_params;
+
+/* How each Vanka patch solve A_i^-1 r_i is applied (Section 4, Section 6.2). */
+typedef enum {
+  /* "tuned" Vanka: patches of equal matrix share one factorisation (25
+   * classes per level, Section 6.3); memory independent of n. */
+  STOKES_SMOOTHER_SHARED = 0,
+  /* "simple" Vanka: an explicit 51 x 51 inverse for every patch of every
+   * level, computed at creation by Gauss-Jordan on the device and streamed
+   * from HBM at every sweep (2601 doubles per vertex: 87 GB on the finest
+   * 2048^2 level).  FP64 form only. */
+  STOKES_SMOOTHER_PER_PATCH = 1
+} stokes_smoother;
 
 typedef struct stokes_hierarchy stokes_hierarchy;
 

@@ -69,7 +69,10 @@ void free_all(stokes_hierarchy* h) {
     cudaFree(L.ef);
     cudaFree(L.cdf);
     cudaFree(L.tcB);
+    cudaFree(L.pinv);
   }
+  cudaFree(h->delta);
+  h->delta = nullptr;
   h->lv.clear();
   cudaFree(h->coarse_G);
   cudaFree(h->V);
@@ -118,12 +121,22 @@ cudaEvent_t* timing_pair(stokes_hierarchy* h, bool finest) {
   return p;
 }
 
+// One FP64 sweep with the hierarchy's smoother (shared class factors, or the
+// stored per-patch inverses, whose sweep uses L.r as residual scratch: L.r is
+// free whenever a sweep runs).
+void sweep_f64(stokes_hierarchy* h, sv::Level& L, const double* x, const double* b, double* xo) {
+  if (h->prm.smoother == STOKES_SMOOTHER_PER_PATCH)
+    sv::launch_simple_sweep(L.d, L.pinv, h->delta, L.r, x, b, xo, h->prm.omega, h->stream);
+  else
+    sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, L.vk_cfg, h->stream);
+}
+
 template <>
 void timed_sweep<double>(stokes_hierarchy* h, bool finest, sv::Level& L, const double* x, const double* b,
                          double* xo) {
   cudaEvent_t* ev = timing_pair(h, finest);
   if (ev) cudaEventRecord(ev[0], h->stream);
-  sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, L.vk_cfg, h->stream);
+  sweep_f64(h, L, x, b, xo);
   if (ev) cudaEventRecord(ev[1], h->stream);
 }
 
@@ -428,8 +441,8 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
 
 cudaError_t choose_tiles(stokes_hierarchy* h) {
   for (sv::Level& L : h->lv) {
-    if (h->prm.tile >= 0) {
-      L.vk_cfg = L.vk_cfg_f = h->prm.tile;
+    if (h->prm.tile >= 0 || h->prm.smoother == STOKES_SMOOTHER_PER_PATCH) {
+      L.vk_cfg = L.vk_cfg_f = h->prm.tile >= 0 ? h->prm.tile : 1;   // no tiled sweep runs with per-patch inverses
       continue;
     }
     L.vk_cfg = L.vk_cfg_f = (L.d.n < 64) ? 0 : 1;
@@ -464,6 +477,7 @@ void stokes_default_params(stokes_params* p) {
   p->rtol = 1e-8;
   p->prec = STOKES_FP64;
   p->tile = -1;
+  p->smoother = STOKES_SMOOTHER_SHARED;
 }
 
 const char* stokes_last_error(void) { return g_err.c_str(); }
@@ -484,6 +498,10 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   if (prm.prec != STOKES_FP64 && prm.prec != STOKES_MIXED_FP32 && prm.prec != STOKES_MIXED_BF16)
     return fail(STOKES_ERR_ARG, "unknown precision mode");
   if (prm.tile < -1 || prm.tile >= sv::VANKA_NCFG) return fail(STOKES_ERR_ARG, "tile must be -1..3");
+  if (prm.smoother != STOKES_SMOOTHER_SHARED && prm.smoother != STOKES_SMOOTHER_PER_PATCH)
+    return fail(STOKES_ERR_ARG, "unknown smoother");
+  if (prm.smoother == STOKES_SMOOTHER_PER_PATCH && prm.prec != STOKES_FP64)
+    return fail(STOKES_ERR_ARG, "per-patch inverses (simple Vanka) are FP64 only");
   std::vector<int> sizes;
   {
     int m = n;
@@ -507,6 +525,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   for (int k = 0; k < 4; ++k) h->fdf.so[k] = static_cast<float>(h->fd.so[k]);
   for (int k = 0; k < 25; ++k) h->fdf.dinv[k] = static_cast<float>(h->fd.dinv[k]);
   cudaError_t e = sv::vanka_prepare();
+  if (e == cudaSuccess) e = sv::simple_prepare();
   if (e == cudaSuccess && prm.prec == STOKES_MIXED_BF16) e = sv::vanka_tc_prepare();
   if (e != cudaSuccess) {
     delete h;
@@ -539,6 +558,15 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
         if ((e = cudaMalloc(&L.tcB, img.size() * sizeof(unsigned short))) == cudaSuccess)
           e = cudaMemcpy(L.tcB, img.data(), img.size() * sizeof(unsigned short), cudaMemcpyHostToDevice);
       }
+    }
+    if (e == cudaSuccess && prm.smoother == STOKES_SMOOTHER_PER_PATCH) {
+      // simple Vanka: assemble and invert every patch of this level on the device
+      if ((e = dalloc(&L.pinv, sv::patch_inverse_doubles(L.d))) == cudaSuccess) {
+        sv::launch_patch_inverse(L.d, L.pinv, h->stream);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess && k + 1 == sizes.size())
+        e = dalloc(&h->delta, sv::patch_delta_doubles(L.d));
     }
     if (e == cudaSuccess && prm.prec != STOKES_FP64) {
       std::vector<float> cdf(L.cd_host.begin(), L.cd_host.end());
@@ -691,7 +719,7 @@ stokes_status stokes_vanka_sweep(stokes_hierarchy* h, int level, const double* x
   if (!b || !x_out) return fail(STOKES_ERR_ARG, "null vector");
   if (x_out == x || x_out == b) return fail(STOKES_ERR_ARG, "x_out must not alias x or b");
   sv::Level& L = h->lv[level];
-  sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, x_out, h->prm.omega, L.vk_cfg, h->stream);
+  sweep_f64(h, L, x, b, x_out);
   return check_launch("vanka_sweep");
 }
 

@@ -88,6 +88,8 @@ struct Level {
   // tensor-core sweep (prec == STOKES_MIXED_BF16): interior tile range, BF16 inverse image
   int tc_lo = 1, tc_hi = 0;
   void* tcB = nullptr;
+  // simple Vanka (smoother == STOKES_SMOOTHER_PER_PATCH): per-patch inverses, entry-major
+  double* pinv = nullptr;
   std::vector<double> cd_host;
   std::vector<double> full_inv_host;  // NCLASS * 51 * 51 dense inverses (host)
 };
@@ -112,6 +114,7 @@ struct stokes_hierarchy {
   double* partials = nullptr;    // dot-product partial sums
   int npart = 0;                 // blocks of the dot kernels
   unsigned* ticket = nullptr;    // last-block counter of the fused Gram-Schmidt kernels
+  double* delta = nullptr;       // patch corrections of the simple-Vanka sweep (finest-level size)
   double* host_scalars = nullptr;  // pinned host mirror of a few scalars
   int* dev_err = nullptr;          // set by kernels whose bounded waits expired
   double* aux = nullptr;           // finest-level vector: the projected adjoint right-hand side
@@ -191,6 +194,18 @@ template <typename TI, typename TO>
 void launch_convert(const TI* in, TO* out, long long N, cudaStream_t s);
 void launch_coarse(const double* G, int N0, const double* r, double* e, cudaStream_t s);
 cudaError_t vanka_prepare();
+
+// ---- simple Vanka (sv_simple.cu): per-patch inverses, FP64 ----
+int patch_stride(const LevelDev& L);                 // patch count rounded up to 32
+size_t patch_inverse_doubles(const LevelDev& L);     // 51 * 51 * stride
+size_t patch_delta_doubles(const LevelDev& L);       // 51 * stride
+cudaError_t simple_prepare();
+void launch_patch_inverse(const LevelDev& L, double* inv, cudaStream_t s);
+// xo = x + sum_i V_i^T W_i A_i^-1 V_i (b - A x) with the stored inverses; x may
+// be nullptr (zero guess); rscratch (level size) receives b - A x; delta
+// (patch_delta_doubles) the corrections
+void launch_simple_sweep(const LevelDev& L, const double* inv, double* delta, double* rscratch, const double* x,
+                         const double* b, double* xo, double omega, cudaStream_t s);
 
 // ---- Krylov kernels (sv_krylov.cu) ----
 int dot_blocks();

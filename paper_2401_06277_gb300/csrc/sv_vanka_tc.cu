@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
   const long long nv = L.nv;
   const int i0 = (tile0 + static_cast<int>(blockIdx.x)) * TC_TILE;
   const int j0 = (tile0 + static_cast<int>(blockIdx.y)) * TC_TILE;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int XI0 = 2 * i0 - 6, XJ0 = 2 * j0 - 6;
   const int RI0 = 2 * i0 - 4, RJ0 = 2 * j0 - 4;
 

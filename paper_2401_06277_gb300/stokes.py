@@ -26,6 +26,8 @@ STOKES_ERR_TIMEOUT = 6
 STOKES_FP64 = 0
 STOKES_MIXED_FP32 = 1
 STOKES_MIXED_BF16 = 2
+STOKES_SMOOTHER_SHARED = 0
+STOKES_SMOOTHER_PER_PATCH = 1
 
 _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NONFINITE",
            5: "NOT_CONVERGED", 6: "ERR_TIMEOUT"}
@@ -45,7 +47,8 @@ class stokes_stats(ctypes.Structure):
 class stokes_params(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("coarse_n", ctypes.c_int), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
-                ("rtol", ctypes.c_double), ("prec", ctypes.c_int), ("tile", ctypes.c_int)]
+                ("rtol", ctypes.c_double), ("prec", ctypes.c_int), ("tile", ctypes.c_int),
+                ("smoother", ctypes.c_int)]
 
 
 _lib = None
@@ -404,12 +407,14 @@ class Hierarchy:
     rtol: float = 1e-8
     prec: int = STOKES_FP64
     tile: int = -1
+    smoother: int = STOKES_SMOOTHER_SHARED
 
     def __post_init__(self):
         p = default_params()
         p.nu1, p.nu2, p.omega, p.coarse_n = self.nu1, self.nu2, self.omega, self.coarse_n
         p.restart, p.maxit, p.rtol, p.prec = self.restart, self.maxit, self.rtol, self.prec
         p.tile = self.tile
+        p.smoother = self.smoother
         self.handle = stokes_hierarchy_create(self.n, self.viscosity, p)
         self.levels, _ = stokes_level_info(self.handle)
         self.N = vec_len(self.n)
