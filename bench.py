@@ -228,8 +228,9 @@ def measured_peaks() -> dict:
 PRECS = {"fp64": 0, "mixed": 1, "bf16": 2}
 
 
-def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e):
-    """Time K FGMRES solves of one precision form; returns (record, hierarchy-independent facts)."""
+def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0):
+    """Time K FGMRES solves of one precision form (smoother 1: per-patch inverses, the
+    paper's simple Vanka); returns the record."""
     import torch
 
     import paper_2401_06277_gb300 as pkg
@@ -238,7 +239,11 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e):
     dev = torch.device("cuda", torch.cuda.current_device())
     n = args.n
     N = dofs(n)
-    H = pkg.Hierarchy(n, rtol=1e-8, restart=30, prec=PRECS[prec_name], tile=args.tile)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
+    H = pkg.Hierarchy(n, rtol=1e-8, restart=30, prec=PRECS[prec_name], tile=args.tile, smoother=smoother)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
     f = f_host.to(dev)
     ud = ud_host.to(dev)
     b = H.assemble_rhs(f, ud)
@@ -283,7 +288,21 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e):
     tile = ["8x8", "16x8", "16x16", "14x14"][stokes.stokes_level_tile(H.handle, H.levels - 1)]
     peaks = measured_peaks()
     sm_max = args.sm_max_mhz or peaks.get("sm_max_mhz", 2070.0)
-    if prec_name == "fp64":
+    if smoother == 1:
+        # per vertex: residual 361, dense 51 x 51 patch inverse 5202, update 68 flops;
+        # bytes: the inverse (2601 doubles), x, b, x_out and the 51 corrections written and read
+        fl = (n + 1) ** 2 * (361.0 + 5202.0 + 68.0)
+        by = (n + 1) ** 2 * 8.0 * (2601 + 2 * 51) + sweep_bytes(n)
+        peak = SM_COUNT * 4 * sm_max * 1e6 / 1e9
+        achieved = fl / (sweep_ms * 1e-3) / 1e9
+        roofline = {"bound": "alu", "kernel": "simple Vanka sweep (k_apply + k_patch_solve + k_patch_update, finest)",
+                    "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "GFLOP/s",
+                    "frac": round(achieved / peak, 4), "traffic": None,
+                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock",
+                    "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
+                    "hbm_gbs_achieved": round(by / (sweep_ms * 1e-3) / 1e9, 1),
+                    "hbm_frac": round(by / (sweep_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6780.0), 4)}
+    elif prec_name == "fp64":
         fl = sweep_flops(n)
         peak = SM_COUNT * 4 * sm_max * 1e6 / 1e9   # 2 DFMA / clk / SM
         achieved = fl / (sweep_ms * 1e-3) / 1e9
@@ -309,7 +328,7 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e):
     tiles = [names[stokes.stokes_level_tile(H.handle, lv)] for lv in range(H.levels - 1, 0, -1)]
     roofline.update({"launch_ms": round(sweep_ms, 4), "launches_timed": st["sweeps_timed"], "tile": tile,
                      "tiles_fine_to_coarse": tiles})
-    tr = TRAFFIC_1024.get(prec_name)
+    tr = TRAFFIC_1024.get(prec_name) if smoother == 0 else None
     if tr is not None and tile == tr["tile"]:
         # DRAM bytes of one launch of the same kernel at 1024^2 (ncu capture), scaled by dofs
         roofline["traffic"] = round(tr["bytes"] * dofs(n) / dofs(1024))
@@ -317,7 +336,7 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e):
     rec = {"value": value, "ms_per_step": ms_max / args.steps, "iters": iters, "relres": rels,
            "vcycles": int(vcycles_all), "ms_per_vcycle": ms_max / max(st["vcycles"], 1),
            "time_to_solution_s": ms_max / args.steps / 1e3, "roofline": roofline,
-           "gpu_launches": launches, "clocks": clk, "levels": H.levels}
+           "gpu_launches": launches, "clocks": clk, "levels": H.levels, "setup_s": t_setup}
     # the V-cycle alone (dofs per second of one preconditioner application), after the timed
     # region: 10 applications to the assembled right-hand side, CUDA events on the stream
     z = torch.empty_like(b)
@@ -438,7 +457,7 @@ def run_ours(args) -> None:
     f_host = torch.from_numpy(si.random_force(n, args.seed + rank)).pin_memory()
     ud_host = torch.from_numpy(si.manufactured_velocity(n)).pin_memory()
     main = time_form(args, args.prec, ws, rank, f_host, ud_host, with_e2e=True)
-    keys = ("value", "time_to_solution_s", "iters", "ms_per_vcycle", "vcycle_only")
+    keys = ("value", "time_to_solution_s", "iters", "ms_per_vcycle", "vcycle_only", "setup_s")
     forms = {args.prec: {k: main[k] for k in keys}}
     if not args.single_form:
         for other in PRECS:
@@ -447,6 +466,10 @@ def run_ours(args) -> None:
             o = time_form(args, other, ws, rank, f_host, ud_host, with_e2e=False)
             forms[other] = {k: o[k] for k in keys}
             forms[other]["roofline"] = o["roofline"]
+        # the paper's simple Vanka (an explicit inverse per patch) in the FP64 form
+        o = time_form(args, "fp64", ws, rank, f_host, ud_host, with_e2e=False, smoother=1)
+        forms["fp64_simple_vanka"] = {k: o[k] for k in keys}
+        forms["fp64_simple_vanka"]["roofline"] = o["roofline"]
     batched = None
     if not args.no_batch:
         batched = time_batch(args, "mixed")

@@ -257,14 +257,22 @@ FastDiag interior_fast_diag(double nu) {
   project(Eo, 2, mw, mo);
   gen_eig(ks, ms, 3, ls, qs);
   gen_eig(ko, mo, 2, lo, qo);
+  // Each eigenvector is rescaled so that its entry on the pair {0, 4} (reduced
+  // index 0) is 1: S = S' diag(g) with g_k that entry, so
+  // K^-1 = (90/nu) (S' (x) S') diag(g_a^2 g_b^2 / (l_a + l_b)) (S' (x) S')^T, and
+  // the transforms skip one multiply per coefficient (the kernels take the
+  // reduced-index-0 row as 1; every |g_k| is above 0.45 of its column's largest entry).
   FastDiag f;
+  double g[5];
+  for (int k = 0; k < 3; ++k) g[k] = qs[0 * 3 + k];
+  for (int k = 0; k < 2; ++k) g[3 + k] = qo[0 * 2 + k];
   for (int mrow = 0; mrow < 3; ++mrow)
-    for (int k = 0; k < 3; ++k) f.se[mrow * 3 + k] = qs[mrow * 3 + k];
+    for (int k = 0; k < 3; ++k) f.se[mrow * 3 + k] = qs[mrow * 3 + k] / g[k];
   for (int mrow = 0; mrow < 2; ++mrow)
-    for (int k = 0; k < 2; ++k) f.so[mrow * 2 + k] = qo[mrow * 2 + k];
+    for (int k = 0; k < 2; ++k) f.so[mrow * 2 + k] = qo[mrow * 2 + k] / g[3 + k];
   double lam[5] = {ls[0], ls[1], ls[2], lo[0], lo[1]};
   for (int a = 0; a < 5; ++a)
-    for (int b = 0; b < 5; ++b) f.dinv[a * 5 + b] = (90.0 / nu) / (lam[a] + lam[b]);
+    for (int b = 0; b < 5; ++b) f.dinv[a * 5 + b] = (90.0 / nu) * (g[a] * g[a]) * (g[b] * g[b]) / (lam[a] + lam[b]);
   return f;
 }
 

@@ -36,24 +36,27 @@ using vk::res_node;
 using vk::inv_mult;
 
 // Forward transform of one 5-vector into the generalised eigenbasis S^T v
-// (three symmetric, two antisymmetric eigenvectors; 4 add/sub + 13 FMA/MUL).
+// (three symmetric, two antisymmetric eigenvectors, each scaled to 1 on the
+// pair {0, 4}, so the first term needs no multiply: 4 add/sub + 8 FMA).
 template <typename T>
 __device__ __forceinline__ void fd_fwd(const FastDiagT<T>& f, T v0, T v1, T v2, T v3, T v4, T* c) {
   const T e0 = v0 + v4, e1 = v1 + v3, o0 = v0 - v4, o1 = v1 - v3;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) c[k] = fma(f.se[k], e0, fma(f.se[3 + k], e1, f.se[6 + k] * v2));
+  for (int k = 0; k < 3; ++k) c[k] = fma(f.se[3 + k], e1, fma(f.se[6 + k], v2, e0));
 #pragma unroll
-  for (int k = 0; k < 2; ++k) c[3 + k] = fma(f.so[k], o0, f.so[2 + k] * o1);
+  for (int k = 0; k < 2; ++k) c[3 + k] = fma(f.so[2 + k], o1, o0);
 }
 
-// Inverse transform S c of five eigen-coefficients (13 FMA/MUL + 4 add/sub).
+// Inverse transform S c of five eigen-coefficients (rows of the pair {0, 4}
+// are all ones: 7 add/sub + 8 FMA/MUL).
 template <typename T>
 __device__ __forceinline__ void fd_inv(const FastDiagT<T>& f, const T* c, T* v) {
   T E[3], Od[2];
+  E[0] = (c[0] + c[1]) + c[2];
 #pragma unroll
-  for (int m = 0; m < 3; ++m) E[m] = fma(f.se[m * 3], c[0], fma(f.se[m * 3 + 1], c[1], f.se[m * 3 + 2] * c[2]));
-#pragma unroll
-  for (int m = 0; m < 2; ++m) Od[m] = fma(f.so[m * 2], c[3], f.so[m * 2 + 1] * c[4]);
+  for (int m = 1; m < 3; ++m) E[m] = fma(f.se[m * 3], c[0], fma(f.se[m * 3 + 1], c[1], f.se[m * 3 + 2] * c[2]));
+  Od[0] = c[3] + c[4];
+  Od[1] = fma(f.so[2], c[3], f.so[3] * c[4]);
   v[0] = E[0] + Od[0];
   v[4] = E[0] - Od[0];
   v[1] = E[1] + Od[1];
@@ -287,12 +290,23 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
     // interior factors; a warp with any boundary-class patch takes the
     // per-axis factors for all of its patches (one path per warp)
     if (!__any_sync(__activemask(), cls != INTERIOR_CLASS)) {
+      // du = K^-1 r_u - z dp = K^-1 (r_u - b^T dp): the coupling b^T of an interior
+      // patch is the compile-time stencil cb (C (x) N) / cb (N (x) C), 12 entries per component
+      const R q = cb * dp;
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int w = 0; w < 25; ++w) {
+          const int dI = w % 5 - 2, dJ = w / 5 - 2;
+          const R bw = R(c == 0 ? crow(dI) * nrow(dJ) : nrow(dI) * crow(dJ));
+          if (bw != R(0)) ru[c * 25 + w] = fma(-bw, q, ru[c * 25 + w]);
+        }
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         R y[25];
         fd_solve<R>(fdg, ru + c * 25, y);
 #pragma unroll
-        for (int o = 0; o < 25; ++o) D[c * 25 + o] = fma(-__ldg(C + CD_Z + c * 25 + o), dp, y[o]);
+        for (int o = 0; o < 25; ++o) D[c * 25 + o] = y[o];
       }
     } else {
       const int fx = axis_free_mask(ax), fy = axis_free_mask(ay);
