@@ -226,6 +226,9 @@ def measured_peaks() -> dict:
 
 
 PRECS = {"fp64": 0, "mixed": 1, "bf16": 2}
+# sweep configurations by stokes_level_tile: fused tiles of TX x TY vertices, or (4, FP64
+# only) the split sweep: 16 x 16 own-patch solves writing the corrections, then the update
+TILE_NAMES = ["8x8", "16x8", "16x16", "14x14", "split16x16"]
 
 
 def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0):
@@ -285,7 +288,7 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0):
     value, ms_max = job_throughput(ws, N * st["vcycles"], ms)
     vcycles_all = allsum(ws, st["vcycles"])
     sweep_ms = st["sweep_ms"] / max(st["sweeps_timed"], 1)
-    tile = ["8x8", "16x8", "16x16", "14x14"][stokes.stokes_level_tile(H.handle, H.levels - 1)]
+    tile = TILE_NAMES[stokes.stokes_level_tile(H.handle, H.levels - 1)]
     peaks = measured_peaks()
     sm_max = args.sm_max_mhz or peaks.get("sm_max_mhz", 2070.0)
     if smoother == 1:
@@ -306,7 +309,9 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0):
         fl = sweep_flops(n)
         peak = SM_COUNT * 4 * sm_max * 1e6 / 1e9   # 2 DFMA / clk / SM
         achieved = fl / (sweep_ms * 1e-3) / 1e9
-        roofline = {"bound": "alu", "kernel": "k_vanka<double> (finest level)", "achieved": round(achieved, 2),
+        kname = ("k_vanka_own<double,16,16> + k_patch_update (split sweep, finest level)" if tile == "split16x16"
+                 else "k_vanka<double> (finest level)")
+        roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 2),
                     "peak": round(peak, 1), "unit": "GFLOP/s", "frac": round(achieved / peak, 4),
                     "traffic": args.traffic,
                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock (FP64 has no "
@@ -324,7 +329,7 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0):
                     "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
                     "algorithmic_bytes_per_launch": by,
                     "fp32_gflops_achieved": round(sweep_flops(n) / (sweep_ms * 1e-3) / 1e9, 1)}
-    names = ["8x8", "16x8", "16x16", "14x14"]
+    names = TILE_NAMES
     tiles = [names[stokes.stokes_level_tile(H.handle, lv)] for lv in range(H.levels - 1, 0, -1)]
     roofline.update({"launch_ms": round(sweep_ms, 4), "launches_timed": st["sweeps_timed"], "tile": tile,
                      "tiles_fine_to_coarse": tiles})
@@ -572,7 +577,7 @@ def run_kernel(args) -> None:
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     rec = {"kernel": args.kernel, "n": n, "ms": ms,
-           "tile": ["8x8", "16x8", "16x16", "14x14"][stokes.stokes_level_tile(H.handle, lvl)]}
+           "tile": TILE_NAMES[stokes.stokes_level_tile(H.handle, lvl)]}
     if fl:
         rec["gflops"] = fl / (ms * 1e-3) / 1e9
         rec["gbs"] = by / (ms * 1e-3) / 1e9
@@ -599,7 +604,7 @@ def main():
     ap.add_argument("--batch-rhs", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--oracle-worker", action="store_true")
-    ap.add_argument("--tile", type=int, default=-1, help="Vanka tile shape (-1: autotuned)")
+    ap.add_argument("--tile", type=int, default=-1, help="Vanka sweep configuration (-1: autotuned; 0..3 fused 8x8/16x8/16x16/14x14, 4 split 16x16, FP64)")
     ap.add_argument("--kernel", choices=["sweep", "residual", "vcycle"], default=None,
                     help="time one kernel alone on the finest level (profiling mode)")
     args = ap.parse_args()

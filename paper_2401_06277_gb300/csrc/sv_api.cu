@@ -127,6 +127,8 @@ cudaEvent_t* timing_pair(stokes_hierarchy* h, bool finest) {
 void sweep_f64(stokes_hierarchy* h, sv::Level& L, const double* x, const double* b, double* xo) {
   if (h->prm.smoother == STOKES_SMOOTHER_PER_PATCH)
     sv::launch_simple_sweep(L.d, L.pinv, h->delta, L.r, x, b, xo, h->prm.omega, h->stream);
+  else if (L.vk_cfg == sv::VANKA_CFG_SPLIT)
+    sv::launch_vanka_split(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, h->delta, h->stream);
   else
     sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, L.vk_cfg, h->stream);
 }
@@ -413,16 +415,22 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
     return e;
   }
   float best = 1e30f;
-  for (int c = 0; c < sv::VANKA_NCFG; ++c) {
-    if constexpr (sizeof(R) == 8) {
-      sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, c, s);
-      cudaEventRecord(e0, s);
-      for (int r = 0; r < 3; ++r) sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, c, s);
-    } else {
-      sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, c, s);
-      cudaEventRecord(e0, s);
-      for (int r = 0; r < 3; ++r) sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, c, s);
-    }
+  // candidates: the fused tile shapes, and in FP64 also the split sweep
+  const int ncand = (sizeof(R) == 8) ? sv::VANKA_CFG_SPLIT + 1 : sv::VANKA_NCFG;
+  for (int c = 0; c < ncand; ++c) {
+    auto run = [&]() {
+      if constexpr (sizeof(R) == 8) {
+        if (c == sv::VANKA_CFG_SPLIT)
+          sv::launch_vanka_split(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, h->delta, s);
+        else
+          sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, c, s);
+      } else {
+        sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, c, s);
+      }
+    };
+    run();
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3; ++r) run();
     cudaEventRecord(e1, s);
     if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
     float ms = 0.0f;
@@ -497,7 +505,9 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
     return fail(STOKES_ERR_ARG, "bad smoothing / iteration parameters");
   if (prm.prec != STOKES_FP64 && prm.prec != STOKES_MIXED_FP32 && prm.prec != STOKES_MIXED_BF16)
     return fail(STOKES_ERR_ARG, "unknown precision mode");
-  if (prm.tile < -1 || prm.tile >= sv::VANKA_NCFG) return fail(STOKES_ERR_ARG, "tile must be -1..3");
+  if (prm.tile < -1 || prm.tile > sv::VANKA_CFG_SPLIT) return fail(STOKES_ERR_ARG, "tile must be -1..4");
+  if (prm.tile == sv::VANKA_CFG_SPLIT && prm.prec != STOKES_FP64)
+    return fail(STOKES_ERR_ARG, "tile 4 (split sweep) is FP64 only");
   if (prm.smoother != STOKES_SMOOTHER_SHARED && prm.smoother != STOKES_SMOOTHER_PER_PATCH)
     return fail(STOKES_ERR_ARG, "unknown smoother");
   if (prm.smoother == STOKES_SMOOTHER_PER_PATCH && prm.prec != STOKES_FP64)
@@ -565,9 +575,10 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
         sv::launch_patch_inverse(L.d, L.pinv, h->stream);
         e = cudaGetLastError();
       }
-      if (e == cudaSuccess && k + 1 == sizes.size())
-        e = dalloc(&h->delta, sv::patch_delta_doubles(L.d));
     }
+    // patch corrections of the per-patch-inverse and the split FP64 sweeps (finest-level size)
+    if (e == cudaSuccess && prm.prec == STOKES_FP64 && k + 1 == sizes.size())
+      e = dalloc(&h->delta, sv::patch_delta_doubles(L.d));
     if (e == cudaSuccess && prm.prec != STOKES_FP64) {
       std::vector<float> cdf(L.cd_host.begin(), L.cd_host.end());
       if ((e = dalloc(&L.xf0, N)) == cudaSuccess && (e = dalloc(&L.xf1, N)) == cudaSuccess &&

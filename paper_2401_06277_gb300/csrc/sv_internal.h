@@ -169,6 +169,7 @@ void launch_rhs_transpose(const LevelDev& L, const double* lam, double* g, cudaS
 // in [skip_lo, skip_hi] are left to the tensor-core kernel (empty by default).
 constexpr int VANKA_NCFG = 4;
 constexpr int VANKA_CFG_14 = 3;
+constexpr int VANKA_CFG_SPLIT = 4;   // FP64 only: own-patch solves + separate update (launch_vanka_split)
 template <typename R>
 void launch_vanka(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
                   double omega, int cfg, cudaStream_t s, int skip_lo = 1, int skip_hi = 0);
@@ -204,6 +205,13 @@ void launch_patch_inverse(const LevelDev& L, double* inv, cudaStream_t s);
 // xo = x + sum_i V_i^T W_i A_i^-1 V_i (b - A x) with the stored inverses; x may
 // be nullptr (zero guess); rscratch (level size) receives b - A x; delta
 // (patch_delta_doubles) the corrections
+// x_out = x + sum over patches of (omega / m_j) delta (entry-major corrections, stride P)
+void launch_patch_update(const LevelDev& L, int P, const double* delta, const double* x, double* xo, double omega,
+                         cudaStream_t s);
+// FP64 sweep in two kernels: own-patch solves (16 x 16 tiles, no halo patches)
+// writing delta (patch_delta_doubles), then launch_patch_update
+void launch_vanka_split(const LevelDev& L, const double* cd, const FastDiag& fd, const double* x, const double* b,
+                        double* xo, double omega, double* delta, cudaStream_t s);
 void launch_simple_sweep(const LevelDev& L, const double* inv, double* delta, double* rscratch, const double* x,
                          const double* b, double* xo, double omega, cudaStream_t s);
 

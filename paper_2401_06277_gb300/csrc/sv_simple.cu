@@ -19,6 +19,7 @@
 
 #include "sv_internal.h"
 #include "sv_stencil.cuh"
+#include "sv_vanka_common.cuh"
 
 namespace sv {
 namespace {
@@ -131,7 +132,7 @@ __device__ __forceinline__ void update_node(const LevelDev& L, int P, const doub
   if (I >= nq || J >= nq) return;
   const int pil = max(0, a - (PI ? 0 : 1)), pih = min(n, a + 1);
   const int pjl = max(0, b - (PJ ? 0 : 1)), pjh = min(n, b + 1);
-  const double w = omega / static_cast<double>((pih - pil + 1) * (pjh - pjl + 1));
+  const double w = omega * vk::inv_mult<double>((pih - pil + 1) * (pjh - pjl + 1));
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
     double acc = 0.0;
@@ -182,6 +183,13 @@ void launch_patch_inverse(const LevelDev& L, double* inv, cudaStream_t s) {
       L, patch_stride(L), inv);
 }
 
+void launch_patch_update(const LevelDev& L, int P, const double* delta, const double* x, double* xo, double omega,
+                         cudaStream_t s) {
+  count_launches(1);
+  dim3 blk(32, 8);
+  k_patch_update<<<dim3((L.np + 31) / 32, (L.np + 7) / 8), blk, 0, s>>>(L, P, delta, x, xo, omega);
+}
+
 void launch_simple_sweep(const LevelDev& L, const double* inv, double* delta, double* rscratch, const double* x,
                          const double* b, double* xo, double omega, cudaStream_t s) {
   const int P = patch_stride(L), npatch = L.np * L.np;
@@ -190,10 +198,9 @@ void launch_simple_sweep(const LevelDev& L, const double* inv, double* delta, do
     launch_apply<double>(L, x, b, rscratch, 1, s);
     r = rscratch;
   }
-  count_launches(2);
+  count_launches(1);
   k_patch_solve<<<(npatch + 127) / 128, 128, 0, s>>>(L, P, inv, r, delta);
-  dim3 blk(32, 8);
-  k_patch_update<<<dim3((L.np + 31) / 32, (L.np + 7) / 8), blk, 0, s>>>(L, P, delta, x, xo, omega);
+  launch_patch_update(L, P, delta, x, xo, omega, s);
 }
 
 }  // namespace sv

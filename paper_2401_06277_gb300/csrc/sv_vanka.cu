@@ -102,7 +102,12 @@ __device__ __forceinline__ void fd_solve(const FastDiagT<T>& f, const T* r, T* y
 template <typename T>
 __device__ __forceinline__ void fd_solve_edge(const T* __restrict__ sx, const T* __restrict__ sy,
                                               const T* __restrict__ dv, int fmask, const T* r, int rs,
-                                              T* y) {
+                                              T* y_, long long ys = 1) {
+  struct Y {   // y[i] at stride ys (1: a shared-memory row; the split sweep's global delta: P)
+    T* p;
+    long long s;
+    __device__ T& operator[](int i) const { return p[i * s]; }
+  } y{y_, ys};
 #pragma unroll 1
   for (int wj = 0; wj < 5; ++wj) {
     T v[5];
@@ -240,7 +245,7 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
       const R* x0 = sx + (2 * cy + 2) * T::XW + (2 * cx + 2);
       const R* pc = sp + (cy + 1) * T::PW + (cx + 1);  // vertex (I0/2, J0/2)
       R* r0 = sr + (2 * cy) * T::RW + 2 * cx;
-      vk::res_cell<R, TX, TY>(r0, x0, pc, I0, J0, L, x, cl, cb);
+      vk::res_cell<R, T>(r0, x0, pc, I0, J0, L, x, cl, cb);
     }
     for (int t = tid; t < T::SRP; t += NT) {
       const int jj = t / T::QW, ii = t - jj * T::QW;
@@ -365,6 +370,167 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Split sweep: a CTA solves only the TX x TY patches of the vertices it owns
+// (no halo patches; the residual is needed on a one-vertex halo only) and
+// writes their 51 corrections to a global, entry-major delta (slot * P +
+// patch); a second kernel (k_patch_update, shared with the per-patch-inverse
+// smoother) forms x + W sum of the corrections.  Against the fused kernel this
+// trades 1.27x halo patch solves and 1.56x halo residuals for one write and one
+// read of delta: the better trade where the FP64 pipe, not HBM, is the bound.
+// ---------------------------------------------------------------------------
+template <int TX, int TY>
+struct VO {
+  static constexpr int XW = 2 * TX + 8, XH = 2 * TY + 8;   // x, Q2 nodes, origin 2 i0 - 4
+  static constexpr int PW = TX + 4, PH = TY + 4;           // x, vertices,  origin i0 - 2
+  static constexpr int CW = TX + 2, CH = TY + 2;           // residual cells, origin 2 i0 - 2
+  static constexpr int RW = 2 * CW, RH = 2 * CH;           // residual, Q2 nodes
+  static constexpr int NPATCH = TX * TY;                   // own patches, origin i0
+  static constexpr int SX = 2 * XW * XH, SP = PW * PH, SR = 2 * RW * RH, SRP = NPATCH;
+  static constexpr int TOTAL = SX + SP + SR + SRP;
+};
+
+template <typename R, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) k_vanka_own(LevelDev L, const R* __restrict__ cd,
+                                                  const FastDiagT<R> fdg, const R* __restrict__ x,
+                                                  const R* __restrict__ b, R* __restrict__ delta, int P) {
+  using T = VO<TX, TY>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sx = reinterpret_cast<R*>(smem_raw);
+  R* sp = sx + T::SX;
+  R* sr = sp + T::SP;
+  R* srp = sr + T::SR;
+  R* se = srp + T::SRP;
+  const int n = L.n, nq = L.nq, np = L.np;
+  const long long nv = L.nv;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int tid = threadIdx.x;
+  const int XI0 = 2 * i0 - 4, XJ0 = 2 * j0 - 4;
+  const int RI0 = 2 * i0 - 2, RJ0 = 2 * j0 - 2;
+
+  const bool edge_tile = (i0 <= 1) || (j0 <= 1) || (i0 + TX - 1 >= n - 1) || (j0 + TY - 1 >= n - 1);
+  if (edge_tile)
+    for (int t = tid; t < EDGE_TAB; t += NT) se[t] = cd[CD_EDGE + t];
+  if (x != nullptr) {
+#pragma unroll
+    for (int t = tid; t < T::SX; t += NT) {
+      const int c = t / (T::XW * T::XH);
+      const int rem = t - c * T::XW * T::XH;
+      const int jj = rem / T::XW, ii = rem - jj * T::XW;
+      const int I = XI0 + ii, J = XJ0 + jj;
+      sx[t] = vfree(I, J, nq) ? x[c * nv + static_cast<long long>(J) * nq + I] : R(0);
+    }
+#pragma unroll
+    for (int t = tid; t < T::SP; t += NT) {
+      const int jj = t / T::PW, ii = t - jj * T::PW;
+      const int i = i0 - 2 + ii, j = j0 - 2 + jj;
+      sp[t] = (i >= 0 && j >= 0 && i <= n && j <= n) ? x[2 * nv + static_cast<long long>(j) * np + i] : R(0);
+    }
+  }
+#pragma unroll
+  for (int t = tid; t < T::SR; t += NT) {
+    const int c = t / (T::RW * T::RH);
+    const int rem = t - c * T::RW * T::RH;
+    const int jj = rem / T::RW, ii = rem - jj * T::RW;
+    const int I = RI0 + ii, J = RJ0 + jj;
+    sr[t] = (I >= 0 && J >= 0 && I < nq && J < nq) ? b[c * nv + static_cast<long long>(J) * nq + I] : R(0);
+  }
+#pragma unroll
+  for (int t = tid; t < T::SRP; t += NT) {
+    const int jj = t / TX, ii = t - jj * TX;
+    const int i = i0 + ii, j = j0 + jj;
+    srp[t] = (i <= n && j <= n) ? b[2 * nv + static_cast<long long>(j) * np + i] : R(0);
+  }
+  __syncthreads();
+
+  const R cl = R(L.cl), cb = R(L.cb);
+  if (x != nullptr) {
+    for (int t = tid; t < T::CW * T::CH; t += NT) {
+      const int cy = t / T::CW, cx = t - cy * T::CW;
+      const int I0 = RI0 + 2 * cx, J0 = RJ0 + 2 * cy;
+      const R* x0 = sx + (2 * cy + 2) * T::XW + (2 * cx + 2);
+      const R* pc = sp + (cy + 1) * T::PW + (cx + 1);
+      R* r0 = sr + (2 * cy) * T::RW + 2 * cx;
+      vk::res_cell<R, T>(r0, x0, pc, I0, J0, L, x, cl, cb);
+    }
+    for (int t = tid; t < T::SRP; t += NT) {
+      const int jj = t / TX, ii = t - jj * TX;
+      if (i0 + ii > n || j0 + jj > n) continue;
+      const R* xs0 = sx + (2 * jj + 4) * T::XW + (2 * ii + 4);
+      const R* xs1 = xs0 + T::XW * T::XH;
+      R s = R(0);
+#pragma unroll
+      for (int dJ = -2; dJ <= 2; ++dJ) {
+#pragma unroll
+        for (int dI = -2; dI <= 2; ++dI) {
+          const R wx = R(crow(dI) * nrow(dJ)), wy = R(nrow(dI) * crow(dJ));
+          if (wx != R(0)) s = fma(wx, xs0[dJ * T::XW + dI], s);
+          if (wy != R(0)) s = fma(wy, xs1[dJ * T::XW + dI], s);
+        }
+      }
+      srp[t] -= cb * s;
+    }
+  }
+  __syncthreads();
+
+  for (int t = tid; t < T::NPATCH; t += NT) {
+    const int qj = t / TX, qi = t - qj * TX;
+    const int pi = i0 + qi, pj = j0 + qj;
+    if (pi > n || pj > n) continue;
+    const int ax = axis_class(pi, n), ay = axis_class(pj, n);
+    const int cls = 5 * ay + ax;
+    const R* C = cd + cls * CD_STRIDE;
+    R ru[50];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int wj = 0; wj < 5; ++wj)
+#pragma unroll
+        for (int wi = 0; wi < 5; ++wi)
+          ru[c * 25 + wj * 5 + wi] = sr[c * T::RW * T::RH + (2 * qj + wj) * T::RW + 2 * qi + wi];
+    R zr = R(0);
+#pragma unroll
+    for (int k = 0; k < 50; ++k) zr = fma(__ldg(C + CD_Z + k), ru[k], zr);
+    const R dp = (zr - srp[t]) * __ldg(C + CD_SINV);
+    const int p = pj * np + pi;
+    R* D = delta + p;
+    if (!__any_sync(__activemask(), cls != INTERIOR_CLASS)) {
+      const R q = cb * dp;
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int w = 0; w < 25; ++w) {
+          const int dI = w % 5 - 2, dJ = w / 5 - 2;
+          const R bw = R(c == 0 ? crow(dI) * nrow(dJ) : nrow(dI) * crow(dJ));
+          if (bw != R(0)) ru[c * 25 + w] = fma(-bw, q, ru[c * 25 + w]);
+        }
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        R y[25];
+        fd_solve<R>(fdg, ru + c * 25, y);
+#pragma unroll
+        for (int o = 0; o < 25; ++o) D[static_cast<long long>(c * 25 + o) * P] = y[o];
+      }
+    } else {
+      const int fx = axis_free_mask(ax), fy = axis_free_mask(ay);
+      int fmask = 0;
+#pragma unroll
+      for (int wj = 0; wj < 5; ++wj)
+        if ((fy >> wj) & 1) fmask |= fx << (5 * wj);
+#pragma unroll 1
+      for (int c = 0; c < 2; ++c) {
+        R* y = D + static_cast<long long>(c * 25) * P;
+        fd_solve_edge<R>(se + EDGE_S + ax * 25, se + EDGE_S + ay * 25, se + EDGE_DINV + cls * 25, fmask,
+                            sr + c * T::RW * T::RH + (2 * qj) * T::RW + 2 * qi, T::RW, y, P);
+#pragma unroll 5
+        for (int o = 0; o < 25; ++o)
+          y[static_cast<long long>(o) * P] = fma(-__ldg(C + CD_Z + c * 25 + o), dp, y[static_cast<long long>(o) * P]);
+      }
+    }
+    D[static_cast<long long>(50) * P] = dp;
+  }
+}
+
 template <typename R, int TX, int TY, int NT>
 void launch_t(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
               R omega, int skip_lo, int skip_hi, cudaStream_t s) {
@@ -396,7 +562,9 @@ cudaError_t prepare_all() {
 }  // namespace
 
 cudaError_t vanka_prepare() {
-  cudaError_t e = prepare_all<double>();
+  cudaError_t e = cudaFuncSetAttribute(k_vanka_own<double, 16, 16, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>((VO<16, 16>::TOTAL + EDGE_TAB) * sizeof(double)));
+  if (e == cudaSuccess) e = prepare_all<double>();
   if (e != cudaSuccess) return e;
   return prepare_all<float>();
 }
@@ -412,6 +580,16 @@ void launch_vanka(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const 
     case 3: launch_t<R, 14, 14, 256>(L, cd, fd, x, b, xo, w, skip_lo, skip_hi, s); break;
     default: launch_t<R, 8, 8, 128>(L, cd, fd, x, b, xo, w, skip_lo, skip_hi, s); break;
   }
+}
+
+void launch_vanka_split(const LevelDev& L, const double* cd, const FastDiag& fd, const double* x, const double* b,
+                        double* xo, double omega, double* delta, cudaStream_t s) {
+  count_launches(1);
+  const int P = patch_stride(L);
+  dim3 grid((L.np + 15) / 16, (L.np + 15) / 16);
+  k_vanka_own<double, 16, 16, 256><<<grid, 256, (VO<16, 16>::TOTAL + EDGE_TAB) * sizeof(double), s>>>(
+      L, cd, fd, x, b, delta, P);
+  launch_patch_update(L, P, delta, x, xo, omega, s);
 }
 
 template void launch_vanka<double>(const LevelDev&, const double*, const FastDiagT<double>&, const double*,

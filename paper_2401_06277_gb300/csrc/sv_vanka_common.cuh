@@ -59,10 +59,11 @@ __device__ __forceinline__ T btp(const T* pc) {
   return g;
 }
 
-template <typename T, int PI, int PJ, int TX, int TY>
+// G: window geometry (XW, XH, PW, RW, RH), e.g. VT<TX, TY>
+template <typename T, int PI, int PJ, typename G>
 __device__ __forceinline__ void res_node(T* sr, const T* x0, const T* pc, int I, int J,
                                          const LevelDev& L, const T* __restrict__ x, T cl, T cb) {
-  using V = VT<TX, TY>;
+  using V = G;
   const int nq = L.nq;
   if (I < 0 || J < 0 || I >= nq || J >= nq) return;  // outside: r stays 0
   if (!vfree(I, J, nq)) {                            // Dirichlet row: r = b - x
@@ -82,10 +83,10 @@ __device__ __forceinline__ void res_node(T* sr, const T* x0, const T* pc, int I,
 // four stencils read them there; otherwise the per-node path handles the
 // Dirichlet rows.  r0 / x0 point at (I0, J0) in the residual / x windows of
 // component 0, pc at the pressure of vertex (I0/2, J0/2).
-template <typename T, int TX, int TY>
+template <typename T, typename G>
 __device__ __forceinline__ void res_cell(T* r0, const T* x0, const T* pc, int I0, int J0, const LevelDev& L,
                                          const T* __restrict__ x, T cl, T cb) {
-  using V = VT<TX, TY>;
+  using V = G;
   const int nq = L.nq;
   if (I0 >= 1 && J0 >= 1 && I0 + 1 <= nq - 2 && J0 + 1 <= nq - 2) {
     T P[3][3];
@@ -130,10 +131,10 @@ __device__ __forceinline__ void res_cell(T* r0, const T* x0, const T* pc, int I0
     }
     return;
   }
-  res_node<T, 0, 0, TX, TY>(r0, x0, pc, I0, J0, L, x, cl, cb);
-  res_node<T, 1, 0, TX, TY>(r0 + 1, x0 + 1, pc, I0 + 1, J0, L, x, cl, cb);
-  res_node<T, 0, 1, TX, TY>(r0 + V::RW, x0 + V::XW, pc, I0, J0 + 1, L, x, cl, cb);
-  res_node<T, 1, 1, TX, TY>(r0 + V::RW + 1, x0 + V::XW + 1, pc, I0 + 1, J0 + 1, L, x, cl, cb);
+  res_node<T, 0, 0, G>(r0, x0, pc, I0, J0, L, x, cl, cb);
+  res_node<T, 1, 0, G>(r0 + 1, x0 + 1, pc, I0 + 1, J0, L, x, cl, cb);
+  res_node<T, 0, 1, G>(r0 + V::RW, x0 + V::XW, pc, I0, J0 + 1, L, x, cl, cb);
+  res_node<T, 1, 1, G>(r0 + V::RW + 1, x0 + V::XW + 1, pc, I0 + 1, J0 + 1, L, x, cl, cb);
 }
 
 template <typename T>

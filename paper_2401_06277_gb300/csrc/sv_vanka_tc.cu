@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
       const float* x0 = sx + (2 * cy + 2) * TT::XW + (2 * cx + 2);
       const float* pc = sp + (cy + 1) * TT::PW + (cx + 1);
       float* r0 = sr + (2 * cy) * TT::RW + 2 * cx;
-      res_cell<float, TC_TILE, TC_TILE>(r0, x0, pc, I0, J0, L, x, cl, cb);
+      res_cell<float, TT>(r0, x0, pc, I0, J0, L, x, cl, cb);
     }
     {
       const int jj = tid / TT::QW, ii = tid - jj * TT::QW;

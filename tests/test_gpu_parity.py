@@ -110,10 +110,12 @@ def test_vanka_sweep(pkg, n):
         assert rel(host(out), ref0) <= 1e-12
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("n", [8, 32, 64])
 def test_vanka_sweep_tile_shapes(pkg, n, tile):
-    """Every tile shape of the fused FP64 sweep (8x8, 16x8, 16x16 vertices) gives the same sweep."""
+    """Every configuration of the FP64 sweep gives the same sweep: fused tiles of 8x8, 16x8,
+    16x16 and 14x14 vertices, and the split sweep (own-patch solves writing the corrections,
+    then the update kernel)."""
     from paper_2401_06277_gb300 import stokes
     H = gpu_h(pkg, n, tile=tile)
     assert stokes.stokes_level_tile(H.handle, H.levels - 1) == tile
