@@ -226,9 +226,10 @@ def measured_peaks() -> dict:
 
 
 PRECS = {"fp64": 0, "mixed": 1, "bf16": 2}
-# sweep configurations by stokes_level_tile: fused tiles of TX x TY vertices, or (4, FP64
+# sweep configurations by stokes_level_tile: fused tiles of TX x TY vertices, or (4, 5; FP64
 # only) the split sweep: 16 x 16 own-patch solves writing the corrections, then the update
-TILE_NAMES = ["8x8", "16x8", "16x16", "14x14", "split16x16"]
+# (5: compiled for two CTAs per SM)
+TILE_NAMES = ["8x8", "16x8", "16x16", "14x14", "split16x16", "split16x16x2"]
 
 
 def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0):
@@ -309,7 +310,7 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0):
         fl = sweep_flops(n)
         peak = SM_COUNT * 4 * sm_max * 1e6 / 1e9   # 2 DFMA / clk / SM
         achieved = fl / (sweep_ms * 1e-3) / 1e9
-        kname = ("k_vanka_own<double,16,16> + k_patch_update (split sweep, finest level)" if tile == "split16x16"
+        kname = ("k_vanka_own<double,16,16> + k_patch_update (split sweep, finest level)" if tile.startswith("split")
                  else "k_vanka<double> (finest level)")
         roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 2),
                     "peak": round(peak, 1), "unit": "GFLOP/s", "frac": round(achieved / peak, 4),
@@ -604,7 +605,7 @@ def main():
     ap.add_argument("--batch-rhs", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--oracle-worker", action="store_true")
-    ap.add_argument("--tile", type=int, default=-1, help="Vanka sweep configuration (-1: autotuned; 0..3 fused 8x8/16x8/16x16/14x14, 4 split 16x16, FP64)")
+    ap.add_argument("--tile", type=int, default=-1, help="Vanka sweep configuration (-1: autotuned; 0..3 fused 8x8/16x8/16x16/14x14, 4/5 split 16x16, FP64)")
     ap.add_argument("--kernel", choices=["sweep", "residual", "vcycle"], default=None,
                     help="time one kernel alone on the finest level (profiling mode)")
     args = ap.parse_args()

@@ -76,8 +76,12 @@ typedef struct {
   int maxit;        /* FGMRES iteration cap                            (1000) */
   double rtol;      /* stop when ||b - A x|| <= rtol ||b - A x0||      (1e-8) */
   stokes_precision prec;  /*                                          (FP64) */
-  int tile;         /* Vanka tile shape: -1 = chosen per level by timing at
-                       creation, 0 = 8x8, 1 = 16x8, 2 = 16x16 vertices (-1) */
+  int tile;         /* Vanka sweep configuration: -1 = chosen per level by
+                       timing at creation; fused tiles of 0 = 8x8, 1 = 16x8,
+                       2 = 16x16, 3 = 14x14 vertices; FP64 only: 4 = split
+                       sweep (16x16 own-patch solves writing the corrections,
+                       then a separate update), 5 = the same compiled for two
+                       CTAs per SM                                     (-1) */
   int smoother;     /* stokes_smoother below                             (0)  */
 } stokes_params;
 

@@ -127,8 +127,9 @@ cudaEvent_t* timing_pair(stokes_hierarchy* h, bool finest) {
 void sweep_f64(stokes_hierarchy* h, sv::Level& L, const double* x, const double* b, double* xo) {
   if (h->prm.smoother == STOKES_SMOOTHER_PER_PATCH)
     sv::launch_simple_sweep(L.d, L.pinv, h->delta, L.r, x, b, xo, h->prm.omega, h->stream);
-  else if (L.vk_cfg == sv::VANKA_CFG_SPLIT)
-    sv::launch_vanka_split(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, h->delta, h->stream);
+  else if (L.vk_cfg >= sv::VANKA_CFG_SPLIT)
+    sv::launch_vanka_split(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, h->delta, L.vk_cfg == sv::VANKA_CFG_SPLIT2,
+                           h->stream);
   else
     sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, L.vk_cfg, h->stream);
 }
@@ -416,12 +417,12 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
   }
   float best = 1e30f;
   // candidates: the fused tile shapes, and in FP64 also the split sweep
-  const int ncand = (sizeof(R) == 8) ? sv::VANKA_CFG_SPLIT + 1 : sv::VANKA_NCFG;
+  const int ncand = (sizeof(R) == 8) ? sv::VANKA_CFG_SPLIT2 + 1 : sv::VANKA_NCFG;
   for (int c = 0; c < ncand; ++c) {
     auto run = [&]() {
       if constexpr (sizeof(R) == 8) {
-        if (c == sv::VANKA_CFG_SPLIT)
-          sv::launch_vanka_split(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, h->delta, s);
+        if (c >= sv::VANKA_CFG_SPLIT)
+          sv::launch_vanka_split(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, h->delta, c == sv::VANKA_CFG_SPLIT2, s);
         else
           sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, c, s);
       } else {
@@ -505,9 +506,9 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
     return fail(STOKES_ERR_ARG, "bad smoothing / iteration parameters");
   if (prm.prec != STOKES_FP64 && prm.prec != STOKES_MIXED_FP32 && prm.prec != STOKES_MIXED_BF16)
     return fail(STOKES_ERR_ARG, "unknown precision mode");
-  if (prm.tile < -1 || prm.tile > sv::VANKA_CFG_SPLIT) return fail(STOKES_ERR_ARG, "tile must be -1..4");
-  if (prm.tile == sv::VANKA_CFG_SPLIT && prm.prec != STOKES_FP64)
-    return fail(STOKES_ERR_ARG, "tile 4 (split sweep) is FP64 only");
+  if (prm.tile < -1 || prm.tile > sv::VANKA_CFG_SPLIT2) return fail(STOKES_ERR_ARG, "tile must be -1..5");
+  if (prm.tile >= sv::VANKA_CFG_SPLIT && prm.prec != STOKES_FP64)
+    return fail(STOKES_ERR_ARG, "tiles 4 and 5 (split sweep) are FP64 only");
   if (prm.smoother != STOKES_SMOOTHER_SHARED && prm.smoother != STOKES_SMOOTHER_PER_PATCH)
     return fail(STOKES_ERR_ARG, "unknown smoother");
   if (prm.smoother == STOKES_SMOOTHER_PER_PATCH && prm.prec != STOKES_FP64)

@@ -170,6 +170,7 @@ void launch_rhs_transpose(const LevelDev& L, const double* lam, double* g, cudaS
 constexpr int VANKA_NCFG = 4;
 constexpr int VANKA_CFG_14 = 3;
 constexpr int VANKA_CFG_SPLIT = 4;   // FP64 only: own-patch solves + separate update (launch_vanka_split)
+constexpr int VANKA_CFG_SPLIT2 = 5;  // the same, compiled for two CTAs per SM (at most 128 registers)
 template <typename R>
 void launch_vanka(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
                   double omega, int cfg, cudaStream_t s, int skip_lo = 1, int skip_hi = 0);
@@ -211,7 +212,7 @@ void launch_patch_update(const LevelDev& L, int P, const double* delta, const do
 // FP64 sweep in two kernels: own-patch solves (16 x 16 tiles, no halo patches)
 // writing delta (patch_delta_doubles), then launch_patch_update
 void launch_vanka_split(const LevelDev& L, const double* cd, const FastDiag& fd, const double* x, const double* b,
-                        double* xo, double omega, double* delta, cudaStream_t s);
+                        double* xo, double omega, double* delta, int two_per_sm, cudaStream_t s);
 void launch_simple_sweep(const LevelDev& L, const double* inv, double* delta, double* rscratch, const double* x,
                          const double* b, double* xo, double omega, cudaStream_t s);
 

@@ -390,8 +390,8 @@ struct VO {
   static constexpr int TOTAL = SX + SP + SR + SRP;
 };
 
-template <typename R, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) k_vanka_own(LevelDev L, const R* __restrict__ cd,
+template <typename R, int TX, int TY, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __restrict__ cd,
                                                   const FastDiagT<R> fdg, const R* __restrict__ x,
                                                   const R* __restrict__ b, R* __restrict__ delta, int P) {
   using T = VO<TX, TY>;
@@ -562,8 +562,12 @@ cudaError_t prepare_all() {
 }  // namespace
 
 cudaError_t vanka_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(k_vanka_own<double, 16, 16, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>((VO<16, 16>::TOTAL + EDGE_TAB) * sizeof(double)));
+  const int smem_own = static_cast<int>((VO<16, 16>::TOTAL + EDGE_TAB) * sizeof(double));
+  cudaError_t e = cudaFuncSetAttribute(k_vanka_own<double, 16, 16, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem_own);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_vanka_own<double, 16, 16, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_own);
   if (e == cudaSuccess) e = prepare_all<double>();
   if (e != cudaSuccess) return e;
   return prepare_all<float>();
@@ -583,12 +587,15 @@ void launch_vanka(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const 
 }
 
 void launch_vanka_split(const LevelDev& L, const double* cd, const FastDiag& fd, const double* x, const double* b,
-                        double* xo, double omega, double* delta, cudaStream_t s) {
+                        double* xo, double omega, double* delta, int two_per_sm, cudaStream_t s) {
   count_launches(1);
   const int P = patch_stride(L);
   dim3 grid((L.np + 15) / 16, (L.np + 15) / 16);
-  k_vanka_own<double, 16, 16, 256><<<grid, 256, (VO<16, 16>::TOTAL + EDGE_TAB) * sizeof(double), s>>>(
-      L, cd, fd, x, b, delta, P);
+  constexpr size_t smem = (VO<16, 16>::TOTAL + EDGE_TAB) * sizeof(double);
+  if (two_per_sm)
+    k_vanka_own<double, 16, 16, 256, 2><<<grid, 256, smem, s>>>(L, cd, fd, x, b, delta, P);
+  else
+    k_vanka_own<double, 16, 16, 256, 1><<<grid, 256, smem, s>>>(L, cd, fd, x, b, delta, P);
   launch_patch_update(L, P, delta, x, xo, omega, s);
 }
 

@@ -110,7 +110,7 @@ def test_vanka_sweep(pkg, n):
         assert rel(host(out), ref0) <= 1e-12
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("n", [8, 32, 64])
 def test_vanka_sweep_tile_shapes(pkg, n, tile):
     """Every configuration of the FP64 sweep gives the same sweep: fused tiles of 8x8, 16x8,
