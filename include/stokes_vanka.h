@@ -83,6 +83,14 @@ typedef struct {
                        then a separate update), 5 = the same compiled for two
                        CTAs per SM                                     (-1) */
   int smoother;     /* stokes_smoother below                             (0)  */
+  /* Braess-Sarazin relaxation (smoother 2; Section 3.1, Algorithm 2): D =
+   * diag(L) scaled by bs_t, S = -(1/bs_t) B D^-1 B^T relaxed by bs_jacobi_iters
+   * weighted-Jacobi steps of weight bs_jacobi_weight from zero, the update
+   * damped by bs_omega.  The paper leaves them to experiment.       */
+  double bs_t;             /*                                       (1.0)  */
+  double bs_omega;         /*                                       (1.0)  */
+  double bs_jacobi_weight; /*                                       (1.0)  */
+  int bs_jacobi_iters;     /* >= 1                                  (2)    */
 } stokes_params;
 
 /* How each Vanka patch solve A_i^-1 r_i is applied (Section 4, Section 6.2). */
@@ -94,7 +102,12 @@ typedef enum {
    * level, computed at creation by Gauss-Jordan on the device and streamed
    * from HBM at every sweep (2601 doubles per vertex: 87 GB on the finest
    * 2048^2 level).  FP64 form only. */
-  STOKES_SMOOTHER_PER_PATCH = 1
+  STOKES_SMOOTHER_PER_PATCH = 1,
+  /* Braess-Sarazin relaxation instead of Vanka (Section 3.1, Algorithm 2, the
+   * inexact variant), matrix-free, in the V-cycle's precision (FP64 or
+   * STOKES_MIXED_FP32; not with STOKES_MIXED_BF16, whose tensor-core path is
+   * Vanka's patch GEMM). */
+  STOKES_SMOOTHER_BRAESS_SARAZIN = 2
 } stokes_smoother;
 
 typedef struct stokes_hierarchy stokes_hierarchy;

@@ -73,6 +73,8 @@ void free_all(stokes_hierarchy* h) {
   }
   cudaFree(h->delta);
   h->delta = nullptr;
+  cudaFree(h->bs_buf);
+  h->bs_buf = nullptr;
   h->lv.clear();
   cudaFree(h->coarse_G);
   cudaFree(h->V);
@@ -125,7 +127,9 @@ cudaEvent_t* timing_pair(stokes_hierarchy* h, bool finest) {
 // stored per-patch inverses, whose sweep uses L.r as residual scratch: L.r is
 // free whenever a sweep runs).
 void sweep_f64(stokes_hierarchy* h, sv::Level& L, const double* x, const double* b, double* xo) {
-  if (h->prm.smoother == STOKES_SMOOTHER_PER_PATCH)
+  if (h->prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN)
+    sv::launch_bs_sweep<double>(L.d, h->bs, static_cast<double*>(h->bs_buf), L.r, x, b, xo, h->stream);
+  else if (h->prm.smoother == STOKES_SMOOTHER_PER_PATCH)
     sv::launch_simple_sweep(L.d, L.pinv, h->delta, L.r, x, b, xo, h->prm.omega, h->stream);
   else if (L.vk_cfg >= sv::VANKA_CFG_SPLIT)
     sv::launch_vanka_split(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, h->delta, L.vk_cfg == sv::VANKA_CFG_SPLIT2,
@@ -148,7 +152,9 @@ void timed_sweep<float>(stokes_hierarchy* h, bool finest, sv::Level& L, const fl
                         float* xo) {
   cudaEvent_t* ev = timing_pair(h, finest);
   if (ev) cudaEventRecord(ev[0], h->stream);
-  if (L.tcB != nullptr && L.tc_hi >= L.tc_lo) {
+  if (h->prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN) {
+    sv::launch_bs_sweep<float>(L.d, h->bs, static_cast<float*>(h->bs_buf), L.rf, x, b, xo, h->stream);
+  } else if (L.tcB != nullptr && L.tc_hi >= L.tc_lo) {
     // interior tiles on the tensor cores, the ring of boundary tiles on the SIMT kernel
     sv::launch_vanka_tc(L.d, L.tcB, x, b, xo, h->prm.omega, L.tc_lo, L.tc_hi, h->dev_err, h->stream);
     sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, sv::VANKA_CFG_14, h->stream, L.tc_lo,
@@ -450,7 +456,7 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
 
 cudaError_t choose_tiles(stokes_hierarchy* h) {
   for (sv::Level& L : h->lv) {
-    if (h->prm.tile >= 0 || h->prm.smoother == STOKES_SMOOTHER_PER_PATCH) {
+    if (h->prm.tile >= 0 || h->prm.smoother != STOKES_SMOOTHER_SHARED) {
       L.vk_cfg = L.vk_cfg_f = h->prm.tile >= 0 ? h->prm.tile : 1;   // no tiled sweep runs with per-patch inverses
       continue;
     }
@@ -487,6 +493,10 @@ void stokes_default_params(stokes_params* p) {
   p->prec = STOKES_FP64;
   p->tile = -1;
   p->smoother = STOKES_SMOOTHER_SHARED;
+  p->bs_t = 1.0;
+  p->bs_omega = 1.0;
+  p->bs_jacobi_weight = 1.0;
+  p->bs_jacobi_iters = 2;
 }
 
 const char* stokes_last_error(void) { return g_err.c_str(); }
@@ -509,8 +519,13 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   if (prm.tile < -1 || prm.tile > sv::VANKA_CFG_SPLIT2) return fail(STOKES_ERR_ARG, "tile must be -1..5");
   if (prm.tile >= sv::VANKA_CFG_SPLIT && prm.prec != STOKES_FP64)
     return fail(STOKES_ERR_ARG, "tiles 4 and 5 (split sweep) are FP64 only");
-  if (prm.smoother != STOKES_SMOOTHER_SHARED && prm.smoother != STOKES_SMOOTHER_PER_PATCH)
+  if (prm.smoother != STOKES_SMOOTHER_SHARED && prm.smoother != STOKES_SMOOTHER_PER_PATCH &&
+      prm.smoother != STOKES_SMOOTHER_BRAESS_SARAZIN)
     return fail(STOKES_ERR_ARG, "unknown smoother");
+  if (prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN &&
+      (prm.prec == STOKES_MIXED_BF16 || !(prm.bs_t > 0.0) || !(prm.bs_omega > 0.0) ||
+       !(prm.bs_jacobi_weight > 0.0) || prm.bs_jacobi_iters < 1 || prm.bs_jacobi_iters > 64))
+    return fail(STOKES_ERR_ARG, "Braess-Sarazin: FP64 or mixed FP32, t, omega, weight > 0, 1..64 Jacobi steps");
   if (prm.smoother == STOKES_SMOOTHER_PER_PATCH && prm.prec != STOKES_FP64)
     return fail(STOKES_ERR_ARG, "per-patch inverses (simple Vanka) are FP64 only");
   std::vector<int> sizes;
@@ -527,6 +542,10 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   auto* h = new (std::nothrow) stokes_hierarchy();
   if (!h) return fail(STOKES_ERR_OOM, "host allocation failed");
   h->prm = prm;
+  h->bs.t = prm.bs_t;
+  h->bs.omega = prm.bs_omega;
+  h->bs.jacobi_weight = prm.bs_jacobi_weight;
+  h->bs.jacobi_iters = prm.bs_jacobi_iters;
   h->nu = viscosity;
   h->n = n;
   h->stream = static_cast<cudaStream_t>(stream);
@@ -580,6 +599,10 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
     // patch corrections of the per-patch-inverse and the split FP64 sweeps (finest-level size)
     if (e == cudaSuccess && prm.prec == STOKES_FP64 && k + 1 == sizes.size())
       e = dalloc(&h->delta, sv::patch_delta_doubles(L.d));
+    if (e == cudaSuccess && prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN && k + 1 == sizes.size()) {
+      const size_t el = sv::bs_scratch_elems(L.d) * (prm.prec == STOKES_FP64 ? sizeof(double) : sizeof(float));
+      e = cudaMalloc(&h->bs_buf, el);
+    }
     if (e == cudaSuccess && prm.prec != STOKES_FP64) {
       std::vector<float> cdf(L.cd_host.begin(), L.cd_host.end());
       if ((e = dalloc(&L.xf0, N)) == cudaSuccess && (e = dalloc(&L.xf1, N)) == cudaSuccess &&

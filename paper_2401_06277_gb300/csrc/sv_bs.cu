@@ -1,0 +1,222 @@
+// sv_bs.cu -- Braess-Sarazin relaxation (Section 3.1, Algorithm 2: the inexact
+// variant), matrix-free, templated on the V-cycle's element type.  With
+// D = diag(L) and S = -(1/t) B D^-1 B^T one sweep is
+//
+//   r = b - A x                                              (k_apply)
+//   g = r_p - (1/t) B D^-1 r_u,  diag(S),  dp = w_J g / diag(S)   (k_bs_rhs)
+//   repeat jacobi_iters - 1 times:
+//     q = D^-1 B^T dp                                        (k_bs_dinv_btp)
+//     dp += w_J (g - S dp) / diag(S),  S dp = -(1/t) B q      (k_bs_jacobi)
+//   du = (1/t) D^-1 (r_u - B^T dp);  x_out = x + omega_BS (du, dp)   (k_bs_update)
+//
+// On a uniform grid diag(L) depends only on the parities of a node's indices:
+// nu/90 times 224 (vertex), 352 (edge midpoints) or 512 (cell centre), so D^-1
+// is a compile-time constant per stencil tap, as are all B and B^T weights.
+// Dirichlet nodes have identity rows in L and zero columns in B: their D is 1,
+// they carry no B coupling, and du = r_u / t there.
+#include <cuda_runtime.h>
+
+#include "sv_internal.h"
+#include "sv_stencil.cuh"
+
+namespace sv {
+namespace {
+
+__device__ __forceinline__ bool bs_free(int I, int J, int nq) { return I > 0 && J > 0 && I < nq - 1 && J < nq - 1; }
+
+// diag(L) / (nu/90) at a free node of parities (PI, PJ)
+__host__ __device__ constexpr double dcoef(int PI, int PJ) { return k1(PI, 0) * m1(PJ, 0) + m1(PI, 0) * k1(PJ, 0); }
+
+// Pressure rows: g, diag(S) and the first Jacobi step.  One thread per vertex
+// (a, b); taps at Q2 nodes (2a + dI, 2b + dJ), parities (dI & 1, dJ & 1).
+template <typename T, bool MASK>
+__device__ __forceinline__ void bs_rhs_vertex(const LevelDev& L, const T* __restrict__ r, T* __restrict__ g,
+                                              T* __restrict__ ds, T* __restrict__ dp, T inv_t, T wj, int a, int b) {
+  const int nq = L.nq;
+  const long long nv = L.nv;
+  const T cb = T(L.cb), icl = T(1.0 / L.cl);
+  T s = T(0), d = T(0);
+#pragma unroll
+  for (int dJ = -2; dJ <= 2; ++dJ)
+#pragma unroll
+    for (int dI = -2; dI <= 2; ++dI) {
+      const double wx = crow(dI) * nrow(dJ), wy = nrow(dI) * crow(dJ);
+      if (wx == 0.0 && wy == 0.0) continue;
+      const int I = 2 * a + dI, J = 2 * b + dJ;
+      if (MASK && !bs_free(I, J, nq)) continue;
+      const T id = T(1.0 / dcoef(dI & 1, dJ & 1));
+      const long long k = static_cast<long long>(J) * nq + I;
+      if (wx != 0.0) s = fma(T(wx) * id, r[k], s);
+      if (wy != 0.0) s = fma(T(wy) * id, r[nv + k], s);
+      d = fma(T(wx * wx + wy * wy), id, d);
+    }
+  const int p = b * L.np + a;
+  const T gv = r[2 * nv + p] - inv_t * cb * icl * s;
+  const T dsv = -inv_t * cb * cb * icl * d;
+  g[p] = gv;
+  ds[p] = dsv;
+  dp[p] = wj * gv / dsv;
+}
+
+template <typename T>
+__global__ void k_bs_rhs(LevelDev L, const T* __restrict__ r, T* __restrict__ g, T* __restrict__ ds,
+                         T* __restrict__ dp, T inv_t, T wj) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = L.n;
+  if (a > n || b > n) return;
+  if (a >= 2 && a <= n - 2 && b >= 2 && b <= n - 2)
+    bs_rhs_vertex<T, false>(L, r, g, ds, dp, inv_t, wj, a, b);
+  else
+    bs_rhs_vertex<T, true>(L, r, g, ds, dp, inv_t, wj, a, b);
+}
+
+// (B^T p) / (cb) at node (2a + PI, 2b + PJ), component C, from the 3 x 3 pressures P around (a, b)
+template <typename T, int PI, int PJ, int C>
+__device__ __forceinline__ T btp3(const T (&P)[3][3]) {
+  T s = T(0);
+#pragma unroll
+  for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+    for (int di = -1; di <= 1; ++di) {
+      const double w = C == 0 ? ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj) : ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj);
+      if (w != 0.0) s = fma(T(w), P[dj + 1][di + 1], s);
+    }
+  return s;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_p3(const LevelDev& L, const T* __restrict__ p, int a, int b, T (&P)[3][3]) {
+#pragma unroll
+  for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+    for (int di = 0; di < 3; ++di) {
+      const int i = a + di - 1, j = b + dj - 1;
+      P[dj][di] = (i >= 0 && j >= 0 && i <= L.n && j <= L.n) ? p[static_cast<long long>(j) * L.np + i] : T(0);
+    }
+}
+
+// q = D^-1 B^T dp on the velocity nodes of vertex (a, b) (0 on Dirichlet nodes)
+template <typename T, int PI, int PJ>
+__device__ __forceinline__ void dinv_btp_node(const LevelDev& L, const T (&P)[3][3], T* __restrict__ q, int a, int b) {
+  const int I = 2 * a + PI, J = 2 * b + PJ, nq = L.nq;
+  if (I >= nq || J >= nq) return;
+  const long long k = static_cast<long long>(J) * nq + I;
+  const bool fr = bs_free(I, J, nq);
+  const T f = T(L.cb / (L.cl * dcoef(PI, PJ)));
+  q[k] = fr ? f * btp3<T, PI, PJ, 0>(P) : T(0);
+  q[L.nv + k] = fr ? f * btp3<T, PI, PJ, 1>(P) : T(0);
+}
+
+template <typename T>
+__global__ void k_bs_dinv_btp(LevelDev L, const T* __restrict__ dp, T* __restrict__ q) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
+  if (a > L.n || b > L.n) return;
+  T P[3][3];
+  load_p3(L, dp, a, b, P);
+  dinv_btp_node<T, 0, 0>(L, P, q, a, b);
+  dinv_btp_node<T, 1, 0>(L, P, q, a, b);
+  dinv_btp_node<T, 0, 1>(L, P, q, a, b);
+  dinv_btp_node<T, 1, 1>(L, P, q, a, b);
+}
+
+// dp += w_J (g - S dp) / diag(S),  S dp = -(1/t) B q
+template <typename T>
+__global__ void k_bs_jacobi(LevelDev L, const T* __restrict__ q, const T* __restrict__ g, const T* __restrict__ ds,
+                            T* __restrict__ dp, T inv_t, T wj) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = L.n, nq = L.nq;
+  if (a > n || b > n) return;
+  const long long nv = L.nv;
+  T s = T(0);
+#pragma unroll
+  for (int dJ = -2; dJ <= 2; ++dJ)
+#pragma unroll
+    for (int dI = -2; dI <= 2; ++dI) {
+      const double wx = crow(dI) * nrow(dJ), wy = nrow(dI) * crow(dJ);
+      if (wx == 0.0 && wy == 0.0) continue;
+      const int I = 2 * a + dI, J = 2 * b + dJ;
+      if (I < 0 || J < 0 || I >= nq || J >= nq) continue;   // q is 0 on Dirichlet nodes
+      const long long k = static_cast<long long>(J) * nq + I;
+      if (wx != 0.0) s = fma(T(wx), q[k], s);
+      if (wy != 0.0) s = fma(T(wy), q[nv + k], s);
+    }
+  const int p = b * L.np + a;
+  const T sdp = -inv_t * T(L.cb) * s;
+  dp[p] = fma(wj, (g[p] - sdp) / ds[p], dp[p]);
+}
+
+// du = (1/t) D^-1 (r_u - B^T dp); x_out = x + omega (du, dp)
+template <typename T, int PI, int PJ>
+__device__ __forceinline__ void bs_update_node(const LevelDev& L, const T (&P)[3][3], const T* __restrict__ r,
+                                               const T* __restrict__ x, T* __restrict__ xo, T inv_t, T om, int a,
+                                               int b) {
+  const int I = 2 * a + PI, J = 2 * b + PJ, nq = L.nq;
+  if (I >= nq || J >= nq) return;
+  const long long k = static_cast<long long>(J) * nq + I;
+  const bool fr = bs_free(I, J, nq);
+  const T cb = T(L.cb), sc = inv_t * T(1.0 / (L.cl * dcoef(PI, PJ)));
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const long long kc = c * L.nv + k;
+    T du;
+    if (fr) {
+      const T bt = c == 0 ? btp3<T, PI, PJ, 0>(P) : btp3<T, PI, PJ, 1>(P);
+      du = sc * (r[kc] - cb * bt);
+    } else {
+      du = inv_t * r[kc];
+    }
+    xo[kc] = fma(om, du, x != nullptr ? x[kc] : T(0));
+  }
+}
+
+template <typename T>
+__global__ void k_bs_update(LevelDev L, const T* __restrict__ r, const T* __restrict__ dp, const T* __restrict__ x,
+                            T* __restrict__ xo, T inv_t, T om) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
+  if (a > L.n || b > L.n) return;
+  T P[3][3];
+  load_p3(L, dp, a, b, P);
+  bs_update_node<T, 0, 0>(L, P, r, x, xo, inv_t, om, a, b);
+  bs_update_node<T, 1, 0>(L, P, r, x, xo, inv_t, om, a, b);
+  bs_update_node<T, 0, 1>(L, P, r, x, xo, inv_t, om, a, b);
+  bs_update_node<T, 1, 1>(L, P, r, x, xo, inv_t, om, a, b);
+  const long long kp = 2 * L.nv + static_cast<long long>(b) * L.np + a;
+  xo[kp] = fma(om, P[1][1], x != nullptr ? x[kp] : T(0));
+}
+
+}  // namespace
+
+size_t bs_scratch_elems(const LevelDev& L) {
+  return static_cast<size_t>(2 * L.nv) + 3 * static_cast<size_t>(L.np) * L.np;
+}
+
+template <typename T>
+void launch_bs_sweep(const LevelDev& L, const BSParams& prm, T* scratch, T* rbuf, const T* x, const T* b, T* xo,
+                     cudaStream_t s) {
+  const long long np2 = static_cast<long long>(L.np) * L.np;
+  T* q = scratch;                 // 2 nv
+  T* g = q + 2 * L.nv;            // np^2 each
+  T* ds = g + np2;
+  T* dp = ds + np2;
+  const T* r = b;
+  if (x != nullptr) {
+    launch_apply<T>(L, x, b, rbuf, 1, s);
+    r = rbuf;
+  }
+  const T inv_t = T(1.0 / prm.t), wj = T(prm.jacobi_weight), om = T(prm.omega);
+  dim3 blk(32, 8), grid((L.np + 31) / 32, (L.np + 7) / 8);
+  count_launches(2 + 2 * (prm.jacobi_iters - 1));
+  k_bs_rhs<T><<<grid, blk, 0, s>>>(L, r, g, ds, dp, inv_t, wj);
+  for (int it = 1; it < prm.jacobi_iters; ++it) {
+    k_bs_dinv_btp<T><<<grid, blk, 0, s>>>(L, dp, q);
+    k_bs_jacobi<T><<<grid, blk, 0, s>>>(L, q, g, ds, dp, inv_t, wj);
+  }
+  k_bs_update<T><<<grid, blk, 0, s>>>(L, r, dp, x, xo, inv_t, om);
+}
+
+template void launch_bs_sweep<double>(const LevelDev&, const BSParams&, double*, double*, const double*,
+                                      const double*, double*, cudaStream_t);
+template void launch_bs_sweep<float>(const LevelDev&, const BSParams&, float*, float*, const float*, const float*,
+                                     float*, cudaStream_t);
+
+}  // namespace sv

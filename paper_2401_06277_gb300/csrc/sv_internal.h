@@ -55,6 +55,12 @@ struct FastDiagT {
 };
 using FastDiag = FastDiagT<double>;
 
+// Braess-Sarazin parameters (Section 3.1, Algorithm 2; see stokes_params).
+struct BSParams {
+  double t = 1.0, omega = 1.0, jacobi_weight = 1.0;
+  int jacobi_iters = 2;
+};
+
 // Device-side description of one level (passed by value to kernels).
 struct LevelDev {
   int n;       // elements per axis
@@ -115,6 +121,8 @@ struct stokes_hierarchy {
   int npart = 0;                 // blocks of the dot kernels
   unsigned* ticket = nullptr;    // last-block counter of the fused Gram-Schmidt kernels
   double* delta = nullptr;       // patch corrections of the simple-Vanka sweep (finest-level size)
+  void* bs_buf = nullptr;        // Braess-Sarazin scratch in the V-cycle precision (finest-level size)
+  sv::BSParams bs;
   double* host_scalars = nullptr;  // pinned host mirror of a few scalars
   int* dev_err = nullptr;          // set by kernels whose bounded waits expired
   double* aux = nullptr;           // finest-level vector: the projected adjoint right-hand side
@@ -196,6 +204,14 @@ template <typename TI, typename TO>
 void launch_convert(const TI* in, TO* out, long long N, cudaStream_t s);
 void launch_coarse(const double* G, int N0, const double* r, double* e, cudaStream_t s);
 cudaError_t vanka_prepare();
+
+// ---- Braess-Sarazin relaxation (sv_bs.cu) ----
+size_t bs_scratch_elems(const LevelDev& L);   // 2 nv + 3 np^2
+// x_out = x + omega (du, dp) (Algorithm 2); x may be nullptr (zero guess);
+// rbuf (level size) receives b - A x; scratch holds bs_scratch_elems(L)
+template <typename T>
+void launch_bs_sweep(const LevelDev& L, const BSParams& prm, T* scratch, T* rbuf, const T* x, const T* b, T* xo,
+                     cudaStream_t s);
 
 // ---- simple Vanka (sv_simple.cu): per-patch inverses, FP64 ----
 int patch_stride(const LevelDev& L);                 // patch count rounded up to 32

@@ -28,6 +28,7 @@ STOKES_MIXED_FP32 = 1
 STOKES_MIXED_BF16 = 2
 STOKES_SMOOTHER_SHARED = 0
 STOKES_SMOOTHER_PER_PATCH = 1
+STOKES_SMOOTHER_BRAESS_SARAZIN = 2
 
 _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NONFINITE",
            5: "NOT_CONVERGED", 6: "ERR_TIMEOUT"}
@@ -48,7 +49,8 @@ class stokes_params(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("coarse_n", ctypes.c_int), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("rtol", ctypes.c_double), ("prec", ctypes.c_int), ("tile", ctypes.c_int),
-                ("smoother", ctypes.c_int)]
+                ("smoother", ctypes.c_int), ("bs_t", ctypes.c_double), ("bs_omega", ctypes.c_double),
+                ("bs_jacobi_weight", ctypes.c_double), ("bs_jacobi_iters", ctypes.c_int)]
 
 
 _lib = None
@@ -408,6 +410,10 @@ class Hierarchy:
     prec: int = STOKES_FP64
     tile: int = -1
     smoother: int = STOKES_SMOOTHER_SHARED
+    bs_t: float = 1.0
+    bs_omega: float = 1.0
+    bs_jacobi_weight: float = 1.0
+    bs_jacobi_iters: int = 2
 
     def __post_init__(self):
         p = default_params()
@@ -415,6 +421,8 @@ class Hierarchy:
         p.restart, p.maxit, p.rtol, p.prec = self.restart, self.maxit, self.rtol, self.prec
         p.tile = self.tile
         p.smoother = self.smoother
+        p.bs_t, p.bs_omega = self.bs_t, self.bs_omega
+        p.bs_jacobi_weight, p.bs_jacobi_iters = self.bs_jacobi_weight, self.bs_jacobi_iters
         self.handle = stokes_hierarchy_create(self.n, self.viscosity, p)
         self.levels, _ = stokes_level_info(self.handle)
         self.N = vec_len(self.n)
