@@ -292,7 +292,32 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0):
     tile = TILE_NAMES[stokes.stokes_level_tile(H.handle, H.levels - 1)]
     peaks = measured_peaks()
     sm_max = args.sm_max_mhz or peaks.get("sm_max_mhz", 2070.0)
-    if smoother == 1:
+    if smoother == 2:
+        # Braess-Sarazin (two Jacobi steps) per vertex: residual 361, g and diag(S) 2 x 48,
+        # D^-1 B^T dp 2 x 4 x 9 + 8, B q 48 + 4, du 2 x 4 x (9 + 3) + 2 x 9: ~700 flops.  Vector
+        # passes: residual 3 (x, b -> r); g 1 + 3 pressure (-> g, diag(S), dp); D^-1 B^T dp
+        # 1 pressure + 2 velocity components; Jacobi 2 components + 4 pressure; update 3 + 1 pressure
+        esz = 8.0 if prec_name == "fp64" else 4.0
+        fl = (n + 1) ** 2 * 700.0
+        by = esz * (7.0 * dofs(n) + 4.0 * (2 * n + 1) ** 2 + 9.0 * (n + 1) ** 2)
+        if prec_name == "fp64":
+            peak = SM_COUNT * 4 * sm_max * 1e6 / 1e9
+            achieved = fl / (sweep_ms * 1e-3) / 1e9
+            roofline = {"bound": "alu", "kernel": "Braess-Sarazin sweep (k_apply + k_bs_*, finest level)",
+                        "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "GFLOP/s",
+                        "frac": round(achieved / peak, 4), "traffic": None,
+                        "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock",
+                        "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
+                        "hbm_gbs_achieved": round(by / (sweep_ms * 1e-3) / 1e9, 1)}
+        else:
+            peak = peaks.get("hbm_gbs", 6780.0)
+            achieved = by / (sweep_ms * 1e-3) / 1e9
+            roofline = {"bound": "hbm", "kernel": "Braess-Sarazin sweep (k_apply + k_bs_*, finest level, FP32)",
+                        "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(achieved / peak, 4), "traffic": None,
+                        "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",
+                        "algorithmic_bytes_per_launch": by}
+    elif smoother == 1:
         # per vertex: residual 361, dense 51 x 51 patch inverse 5202, update 68 flops;
         # bytes: the inverse (2601 doubles), x, b, x_out and the 51 corrections written and read
         fl = (n + 1) ** 2 * (361.0 + 5202.0 + 68.0)
@@ -472,10 +497,13 @@ def run_ours(args) -> None:
             o = time_form(args, other, ws, rank, f_host, ud_host, with_e2e=False)
             forms[other] = {k: o[k] for k in keys}
             forms[other]["roofline"] = o["roofline"]
-        # the paper's simple Vanka (an explicit inverse per patch) in the FP64 form
-        o = time_form(args, "fp64", ws, rank, f_host, ud_host, with_e2e=False, smoother=1)
-        forms["fp64_simple_vanka"] = {k: o[k] for k in keys}
-        forms["fp64_simple_vanka"]["roofline"] = o["roofline"]
+        # the paper's simple Vanka (an explicit inverse per patch) in the FP64 form, and
+        # Braess-Sarazin relaxation (the paper's comparison, Section 6.8) in FP64 and mixed FP32
+        for name, pn, sm in (("fp64_simple_vanka", "fp64", 1), ("fp64_braess_sarazin", "fp64", 2),
+                             ("mixed_braess_sarazin", "mixed", 2)):
+            o = time_form(args, pn, ws, rank, f_host, ud_host, with_e2e=False, smoother=sm)
+            forms[name] = {k: o[k] for k in keys}
+            forms[name]["roofline"] = o["roofline"]
     batched = None
     if not args.no_batch:
         batched = time_batch(args, "mixed")
