@@ -91,6 +91,9 @@ typedef struct {
   double bs_omega;         /*                                       (1.0)  */
   double bs_jacobi_weight; /*                                       (1.0)  */
   int bs_jacobi_iters;     /* >= 1                                  (2)    */
+  int cycle;        /* coarse-grid corrections per level (Algorithm 1): 1 =
+                       V-cycle, 2 = W-cycle (the coarse problem is cycled twice;
+                       the second time on the updated residual)           (1)  */
 } stokes_params;
 
 /* How each Vanka patch solve A_i^-1 r_i is applied (Section 4, Section 6.2). */

@@ -492,6 +492,7 @@ class Hierarchy:
     weights: str = "multiplicity"
     smoother: str = "vanka"          # or "bs" (Braess-Sarazin, Algorithm 2)
     bs: BSParams = None
+    gamma: int = 1                   # coarse-grid cycles per level: 1 = V-cycle, 2 = W-cycle
 
 
 def build_level(n: int, nu: float, per_patch: bool = False) -> Level:
@@ -514,7 +515,7 @@ def bordered_matrix(level: Level) -> sp.csr_matrix:
 def build_hierarchy(n: int, nu: float = 1.0, coarse_n: int = 4, omega: float = 0.7,
                     nu1: int = 2, nu2: int = 2, per_patch: bool = False,
                     weights: str = "multiplicity", smoother: str = "vanka",
-                    bs: BSParams | None = None) -> Hierarchy:
+                    bs: BSParams | None = None, gamma: int = 1) -> Hierarchy:
     """Rediscretised levels n, n/2, ..., coarse_n (Section 3: geometric multigrid)."""
     sizes = []
     m = n
@@ -528,7 +529,7 @@ def build_hierarchy(n: int, nu: float = 1.0, coarse_n: int = 4, omega: float = 0
     for l in range(1, len(levels)):
         levels[l].P = prolongation(levels[l].mesh, levels[l - 1].mesh)
     H = Hierarchy(levels=levels, nu=nu, omega=omega, nu1=nu1, nu2=nu2, weights=weights,
-                  smoother=smoother, bs=bs if bs is not None else BSParams())
+                  smoother=smoother, bs=bs if bs is not None else BSParams(), gamma=gamma)
     Kb = bordered_matrix(levels[0]).toarray()
     H.coarse_lu = sla.lu_factor(Kb)
     return H
@@ -541,7 +542,9 @@ def coarse_solve(H: Hierarchy, r: np.ndarray) -> np.ndarray:
 
 
 def vcycle(H: Hierarchy, b: np.ndarray, l: int | None = None) -> np.ndarray:
-    """Algorithm 1 with a zero initial guess: nu1 sweeps, restrict, recurse, correct, nu2 sweeps."""
+    """Algorithm 1 with a zero initial guess: nu1 sweeps, restrict, recurse, correct, nu2 sweeps.
+    With H.gamma = 2 the coarse problem A_c e = r_c is iterated twice (W-cycle): the second
+    cycle starts from the first's result, e += cycle(r_c - A_c e)."""
     if l is None:
         l = len(H.levels) - 1
     if l == 0:
@@ -552,7 +555,13 @@ def vcycle(H: Hierarchy, b: np.ndarray, l: int | None = None) -> np.ndarray:
         x = relax(H, lv, x, b)
     r = b - lv.A @ x
     rc = lv.P.T @ r
-    ec = coarse_solve(H, rc) if l == 1 else vcycle(H, rc, l - 1)
+    if l == 1:
+        ec = coarse_solve(H, rc)
+    else:
+        ec = vcycle(H, rc, l - 1)
+        Ac = H.levels[l - 1].A
+        for _ in range(H.gamma - 1):
+            ec = ec + vcycle(H, rc - Ac @ ec, l - 1)
     x = x + lv.P @ ec
     for _ in range(H.nu2):
         x = relax(H, lv, x, b)

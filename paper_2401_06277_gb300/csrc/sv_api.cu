@@ -220,10 +220,16 @@ void vcycle(stokes_hierarchy* h, int l, const R* b, R* out) {
     cur = X0;
   }
   sv::Level& C = h->lv[l - 1];
-  sv::launch_apply<R>(L.d, cur, b, Buf<R>::r(L), 1, s);
-  sv::launch_restrict<R>(L.d, C.d, Buf<R>::r(L), Buf<R>::b(C), s);
-  vcycle<R>(h, l - 1, Buf<R>::b(C), Buf<R>::e(C));
-  sv::launch_prolong_add<R>(L.d, C.d, Buf<R>::e(C), cur, s);
+  // coarse-grid correction, cycle times (W-cycle: 2) below the coarsest-but-one level;
+  // restricting the updated fine residual gives the coarse residual r_c - A_c e_c
+  // (Galerkin: P^T A_f P = A_c), so each pass starts the coarse cycle from zero
+  const int passes = (l - 1 == 0) ? 1 : h->prm.cycle;
+  for (int g = 0; g < passes; ++g) {
+    sv::launch_apply<R>(L.d, cur, b, Buf<R>::r(L), 1, s);
+    sv::launch_restrict<R>(L.d, C.d, Buf<R>::r(L), Buf<R>::b(C), s);
+    vcycle<R>(h, l - 1, Buf<R>::b(C), Buf<R>::e(C));
+    sv::launch_prolong_add<R>(L.d, C.d, Buf<R>::e(C), cur, s);
+  }
   for (int it = 0; it < h->prm.nu2; ++it) {
     R* dst = (it == h->prm.nu2 - 1) ? out : ((cur == X0) ? X1 : X0);
     timed_sweep<R>(h, finest, L, cur, b, dst);
@@ -497,6 +503,7 @@ void stokes_default_params(stokes_params* p) {
   p->bs_omega = 1.0;
   p->bs_jacobi_weight = 1.0;
   p->bs_jacobi_iters = 2;
+  p->cycle = 1;
 }
 
 const char* stokes_last_error(void) { return g_err.c_str(); }
@@ -519,6 +526,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   if (prm.tile < -1 || prm.tile > sv::VANKA_CFG_SPLIT2) return fail(STOKES_ERR_ARG, "tile must be -1..5");
   if (prm.tile >= sv::VANKA_CFG_SPLIT && prm.prec != STOKES_FP64)
     return fail(STOKES_ERR_ARG, "tiles 4 and 5 (split sweep) are FP64 only");
+  if (prm.cycle < 1 || prm.cycle > 2) return fail(STOKES_ERR_ARG, "cycle must be 1 (V) or 2 (W)");
   if (prm.smoother != STOKES_SMOOTHER_SHARED && prm.smoother != STOKES_SMOOTHER_PER_PATCH &&
       prm.smoother != STOKES_SMOOTHER_BRAESS_SARAZIN)
     return fail(STOKES_ERR_ARG, "unknown smoother");

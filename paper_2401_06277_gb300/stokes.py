@@ -50,7 +50,8 @@ class stokes_params(ctypes.Structure):
                 ("coarse_n", ctypes.c_int), ("restart", ctypes.c_int), ("maxit", ctypes.c_int),
                 ("rtol", ctypes.c_double), ("prec", ctypes.c_int), ("tile", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("bs_t", ctypes.c_double), ("bs_omega", ctypes.c_double),
-                ("bs_jacobi_weight", ctypes.c_double), ("bs_jacobi_iters", ctypes.c_int)]
+                ("bs_jacobi_weight", ctypes.c_double), ("bs_jacobi_iters", ctypes.c_int),
+                ("cycle", ctypes.c_int)]
 
 
 _lib = None
@@ -414,6 +415,7 @@ class Hierarchy:
     bs_omega: float = 1.0
     bs_jacobi_weight: float = 1.0
     bs_jacobi_iters: int = 2
+    cycle: int = 1
 
     def __post_init__(self):
         p = default_params()
@@ -423,6 +425,7 @@ class Hierarchy:
         p.smoother = self.smoother
         p.bs_t, p.bs_omega = self.bs_t, self.bs_omega
         p.bs_jacobi_weight, p.bs_jacobi_iters = self.bs_jacobi_weight, self.bs_jacobi_iters
+        p.cycle = self.cycle
         self.handle = stokes_hierarchy_create(self.n, self.viscosity, p)
         self.levels, _ = stokes_level_info(self.handle)
         self.N = vec_len(self.n)

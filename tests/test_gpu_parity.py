@@ -504,3 +504,18 @@ def test_batch_many_rhs_one_grid(pkg):
         xg = O.normalize_pressure(lv, host(xs[k]))
         assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-7
     B.close()
+
+
+@pytest.mark.parametrize("smoother", [0, 2])
+@pytest.mark.parametrize("n", [16, 32])
+def test_wcycle(pkg, n, smoother):
+    """W-cycle (two coarse-grid corrections per level) with Vanka or Braess-Sarazin relaxation."""
+    H = pkg.Hierarchy(n, cycle=2, smoother=smoother)
+    Ho = O.build_hierarchy(n, gamma=2, smoother="bs" if smoother == 2 else "vanka")
+    r = rvec(n, 44)
+    assert rel(host(H.vcycle(dev(r))), O.vcycle(Ho, r)) <= 1e-12
+    lv = Ho.levels[-1]
+    b = O.assemble_rhs(lv, si.random_force(n, 45), si.manufactured_velocity(n))
+    x, it, rr = H.solve(dev(b))
+    assert rr <= 1e-8 and it == O.solve(Ho, b).iters
+    H.close()

@@ -153,3 +153,53 @@ def test_adjoint_gradient_matches_finite_differences():
         assert abs(fd - an) <= 1e-7 * max(1.0, abs(an)), (fd, an)
     # the gradient vanishes on nodes that only touch Dirichlet rows' test functions
     assert J > 0
+
+
+# ---- W-cycle (Algorithm 1 with the coarse problem cycled twice) ----
+
+def test_wcycle_equals_vcycle_on_two_levels():
+    """With the coarse level solved exactly, a second coarse cycle has nothing left to correct."""
+    r = si.random_vector(8, 41)
+    Hv, Hw = O.build_hierarchy(8), O.build_hierarchy(8, gamma=2)
+    assert len(Hv.levels) == 2
+    zv, zw = O.vcycle(Hv, r), O.vcycle(Hw, r)
+    assert np.abs(zv - zw).max() <= 1e-14 * np.abs(zv).max()
+
+
+def test_wcycle_contracts_at_least_as_well_and_h_independently():
+    rates = {}
+    for gamma in (1, 2):
+        for n in (16, 32):
+            H = O.build_hierarchy(n, gamma=gamma)
+            lv = H.levels[-1]
+            nv2 = 2 * lv.mesh.nvel
+            e = si.random_vector(n, 42)
+            e[lv.dmask] = 0.0
+            e[nv2:] -= e[nv2:].mean()
+            for _ in range(6):
+                e2 = e - O.vcycle(H, lv.A @ e)
+                e2[nv2:] -= e2[nv2:].mean()
+                rate = np.linalg.norm(e2) / np.linalg.norm(e)
+                e = e2
+            rates[gamma, n] = rate
+    # the asymptotic rate is set by the smoother (about 0.36 for both cycles here);
+    # the second coarse correction can only make the coarse-grid error smaller
+    assert rates[2, 16] <= 1.01 * rates[1, 16] and rates[2, 32] <= 1.01 * rates[1, 32], rates
+    assert abs(rates[2, 16] - rates[2, 32]) < 0.05, rates
+
+
+def test_wcycle_second_pass_from_the_restricted_updated_residual():
+    """Restricting the fine residual after the first coarse correction gives the coarse
+    residual r_c - A_c e_c (Galerkin identity), so the two-pass form equals the cycle
+    on the coarse residual up to rounding."""
+    n = 16
+    H = O.build_hierarchy(n, gamma=2)
+    lv, C = H.levels[-1], H.levels[-2]
+    b = si.random_vector(n, 43)
+    x = O.relax(H, lv, np.zeros_like(b), b)
+    rc = lv.P.T @ (b - lv.A @ x)
+    e1 = O.vcycle(H, rc, len(H.levels) - 2)
+    x1 = x + lv.P @ e1
+    rc2 = lv.P.T @ (b - lv.A @ x1)
+    ref = rc - C.A @ e1
+    assert np.abs(rc2 - ref).max() <= 1e-12 * np.abs(ref).max()
