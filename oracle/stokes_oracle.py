@@ -476,6 +476,34 @@ def braess_sarazin_sweep(level: Level, x: np.ndarray, b: np.ndarray, prm: BSPara
     return x + prm.omega * np.concatenate([du, dp])
 
 
+def schur_uzawa_sweep(level: Level, x: np.ndarray, b: np.ndarray, prm: BSParams,
+                      schur: str = "jacobi") -> np.ndarray:
+    """One Schur-Uzawa step (Section 3.3, Algorithm 4), the block lower-triangular
+    approximation [[tD, 0], [B, S]] [du; dp] = [r_u; r_p] with S = -(1/t) B D^-1 B^T:
+      1. du = (1/t) D^-1 r_u,
+      2. approximately solve S dp = r_p - B du (weighted Jacobi from 0, or the
+         minimum-norm exact solve),
+      3. u += omega du, p += omega dp (the paper's algorithm is undamped: omega = 1).
+    The paper's prose writes the Schur equation as S dp = B du - r_p; with its
+    S = -(1/t) B D^-1 B^T that contradicts the block system it is derived from, which
+    is followed here."""
+    nv2 = 2 * level.mesh.nvel
+    _, B, D = bs_blocks(level)
+    r = b - level.A @ x
+    ru, rp = r[:nv2], r[nv2:]
+    du = (1.0 / prm.t) * ru / D
+    g = rp - B @ du
+    S = bs_schur(level, prm.t)
+    if schur == "exact":
+        dp = np.linalg.lstsq(S.toarray(), g, rcond=None)[0]
+    else:
+        dS = S.diagonal()
+        dp = np.zeros_like(g)
+        for _ in range(prm.jacobi_iters):
+            dp = dp + prm.jacobi_weight * (g - S @ dp) / dS
+    return x + prm.omega * np.concatenate([du, dp])
+
+
 # ----------------------------------------------------------------------------
 # Hierarchy, coarse solve, V-cycle (Algorithm 1)
 # ----------------------------------------------------------------------------
@@ -490,7 +518,7 @@ class Hierarchy:
     nu2: int
     coarse_lu: tuple = None
     weights: str = "multiplicity"
-    smoother: str = "vanka"          # or "bs" (Braess-Sarazin, Algorithm 2)
+    smoother: str = "vanka"          # or "bs" (Braess-Sarazin, Algorithm 2), "su" (Schur-Uzawa, Algorithm 4)
     bs: BSParams = None
     gamma: int = 1                   # coarse-grid cycles per level: 1 = V-cycle, 2 = W-cycle
 
@@ -569,9 +597,12 @@ def vcycle(H: Hierarchy, b: np.ndarray, l: int | None = None) -> np.ndarray:
 
 
 def relax(H: Hierarchy, lv: Level, x: np.ndarray, b: np.ndarray) -> np.ndarray:
-    """One sweep of the hierarchy's relaxation: additive Vanka (Algorithm 3) or Braess-Sarazin (Algorithm 2)."""
+    """One sweep of the hierarchy's relaxation: additive Vanka (Algorithm 3), Braess-Sarazin
+    (Algorithm 2) or Schur-Uzawa (Algorithm 4)."""
     if H.smoother == "bs":
         return braess_sarazin_sweep(lv, x, b, H.bs)
+    if H.smoother == "su":
+        return schur_uzawa_sweep(lv, x, b, H.bs)
     return vanka_sweep(lv, x, b, H.omega, H.weights)
 
 

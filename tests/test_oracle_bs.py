@@ -88,3 +88,34 @@ def test_bs_preconditioned_fgmres_reaches_the_direct_solution(n):
     xd = O.normalize_pressure(lv, O.direct_solve(lv, b))
     xg = O.normalize_pressure(lv, res.x)
     assert res.converged and np.linalg.norm(xg - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+# ---- Schur-Uzawa (Section 3.3, Algorithm 4) ----
+
+SU = O.BSParams(t=1.0, omega=1.0, jacobi_weight=0.4, jacobi_iters=1)   # the paper's t and Jacobi weight
+
+
+def test_exact_schur_uzawa_step_is_the_block_lower_triangular_solve():
+    """With the Schur system solved exactly the step is omega [[tD, 0], [B, S]]^+ r (Eq. uzblock)."""
+    n, t, om = 8, 1.2, 0.8
+    lv = O.build_level(n, 1.0)
+    nv2 = 2 * lv.mesh.nvel
+    _, B, D = O.bs_blocks(lv)
+    S = O.bs_schur(lv, t).toarray()
+    x, b = si.random_vector(n, 11), si.random_vector(n, 12)
+    got = O.schur_uzawa_sweep(lv, x, b, O.BSParams(t=t, omega=om), schur="exact") - x
+    K = np.block([[t * np.diag(D), np.zeros((nv2, S.shape[0]))], [B.toarray(), S]])
+    ref = om * np.linalg.lstsq(K, b - lv.A @ x, rcond=None)[0]
+    assert np.abs(got[:nv2] - ref[:nv2]).max() <= 1e-10 * np.abs(ref[:nv2]).max()
+    dp, dr = got[nv2:], ref[nv2:]
+    assert np.abs((dp - dp.mean()) - (dr - dr.mean())).max() <= 1e-10 * np.abs(dr).max()
+
+
+def test_su_preconditioned_fgmres_reaches_the_direct_solution():
+    n = 16
+    H = O.build_hierarchy(n, smoother="su", bs=SU)
+    lv = H.levels[-1]
+    b = O.assemble_rhs(lv, si.random_force(n, 13), si.manufactured_velocity(n))
+    res = O.solve(H, b, rtol=1e-12, maxit=300)
+    xd = O.normalize_pressure(lv, O.direct_solve(lv, b))
+    assert res.converged and np.linalg.norm(O.normalize_pressure(lv, res.x) - xd) <= 1e-9 * np.linalg.norm(xd)
