@@ -232,7 +232,7 @@ PRECS = {"fp64": 0, "mixed": 1, "bf16": 2}
 TILE_NAMES = ["8x8", "16x8", "16x16", "14x14", "split16x16", "split16x16x2"]
 
 
-def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0):
+def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0, hkw=None):
     """Time K FGMRES solves of one precision form (smoother 1: per-patch inverses, the
     paper's simple Vanka); returns the record."""
     import torch
@@ -245,7 +245,8 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0):
     N = dofs(n)
     torch.cuda.synchronize()
     t_setup = time.perf_counter()
-    H = pkg.Hierarchy(n, rtol=1e-8, restart=30, prec=PRECS[prec_name], tile=args.tile, smoother=smoother)
+    H = pkg.Hierarchy(n, rtol=1e-8, restart=30, prec=PRECS[prec_name], tile=args.tile, smoother=smoother,
+                      **(hkw or {}))
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     f = f_host.to(dev)
@@ -292,7 +293,7 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0):
     tile = TILE_NAMES[stokes.stokes_level_tile(H.handle, H.levels - 1)]
     peaks = measured_peaks()
     sm_max = args.sm_max_mhz or peaks.get("sm_max_mhz", 2070.0)
-    if smoother == 2:
+    if smoother in (2, 3):
         # Braess-Sarazin (two Jacobi steps) per vertex: residual 361, g and diag(S) 2 x 48,
         # D^-1 B^T dp 2 x 4 x 9 + 8, B q 48 + 4, du 2 x 4 x (9 + 3) + 2 x 9: ~700 flops.  Vector
         # passes: residual 3 (x, b -> r); g 1 + 3 pressure (-> g, diag(S), dp); D^-1 B^T dp
@@ -499,9 +500,11 @@ def run_ours(args) -> None:
             forms[other]["roofline"] = o["roofline"]
         # the paper's simple Vanka (an explicit inverse per patch) in the FP64 form, and
         # Braess-Sarazin relaxation (the paper's comparison, Section 6.8) in FP64 and mixed FP32
-        for name, pn, sm in (("fp64_simple_vanka", "fp64", 1), ("fp64_braess_sarazin", "fp64", 2),
-                             ("mixed_braess_sarazin", "mixed", 2)):
-            o = time_form(args, pn, ws, rank, f_host, ud_host, with_e2e=False, smoother=sm)
+        # and Schur-Uzawa with the paper's parameters (t = 1, Jacobi weight 0.4, one step)
+        su = dict(bs_t=1.0, bs_omega=1.0, bs_jacobi_weight=0.4, bs_jacobi_iters=1)
+        for name, pn, sm, kw in (("fp64_simple_vanka", "fp64", 1, None), ("fp64_braess_sarazin", "fp64", 2, None),
+                                 ("mixed_braess_sarazin", "mixed", 2, None), ("fp64_schur_uzawa", "fp64", 3, su)):
+            o = time_form(args, pn, ws, rank, f_host, ud_host, with_e2e=False, smoother=sm, hkw=kw)
             forms[name] = {k: o[k] for k in keys}
             forms[name]["roofline"] = o["roofline"]
     batched = None

@@ -83,7 +83,7 @@ typedef struct {
                        then a separate update), 5 = the same compiled for two
                        CTAs per SM                                     (-1) */
   int smoother;     /* stokes_smoother below                             (0)  */
-  /* Braess-Sarazin relaxation (smoother 2; Section 3.1, Algorithm 2): D =
+  /* Braess-Sarazin / Schur-Uzawa relaxation (smoothers 2, 3; Sections 3.1, 3.3): D =
    * diag(L) scaled by bs_t, S = -(1/bs_t) B D^-1 B^T relaxed by bs_jacobi_iters
    * weighted-Jacobi steps of weight bs_jacobi_weight from zero, the update
    * damped by bs_omega.  The paper leaves them to experiment.       */
@@ -110,7 +110,12 @@ typedef enum {
    * inexact variant), matrix-free, in the V-cycle's precision (FP64 or
    * STOKES_MIXED_FP32; not with STOKES_MIXED_BF16, whose tensor-core path is
    * Vanka's patch GEMM). */
-  STOKES_SMOOTHER_BRAESS_SARAZIN = 2
+  STOKES_SMOOTHER_BRAESS_SARAZIN = 2,
+  /* Schur-Uzawa relaxation (Section 3.3, Algorithm 4): the block lower-
+   * triangular step du = (1/t) D^-1 r_u, Jacobi on S dp = r_p - B du, with the
+   * bs_* parameters (the paper's values: bs_t = 1, bs_jacobi_weight = 0.4 with
+   * one Jacobi step, bs_omega = 1).  Same precisions as Braess-Sarazin. */
+  STOKES_SMOOTHER_SCHUR_UZAWA = 3
 } stokes_smoother;
 
 typedef struct stokes_hierarchy stokes_hierarchy;

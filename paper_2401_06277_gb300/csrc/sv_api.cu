@@ -127,7 +127,7 @@ cudaEvent_t* timing_pair(stokes_hierarchy* h, bool finest) {
 // stored per-patch inverses, whose sweep uses L.r as residual scratch: L.r is
 // free whenever a sweep runs).
 void sweep_f64(stokes_hierarchy* h, sv::Level& L, const double* x, const double* b, double* xo) {
-  if (h->prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN)
+  if (h->prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN || h->prm.smoother == STOKES_SMOOTHER_SCHUR_UZAWA)
     sv::launch_bs_sweep<double>(L.d, h->bs, static_cast<double*>(h->bs_buf), L.r, x, b, xo, h->stream);
   else if (h->prm.smoother == STOKES_SMOOTHER_PER_PATCH)
     sv::launch_simple_sweep(L.d, L.pinv, h->delta, L.r, x, b, xo, h->prm.omega, h->stream);
@@ -152,7 +152,7 @@ void timed_sweep<float>(stokes_hierarchy* h, bool finest, sv::Level& L, const fl
                         float* xo) {
   cudaEvent_t* ev = timing_pair(h, finest);
   if (ev) cudaEventRecord(ev[0], h->stream);
-  if (h->prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN) {
+  if (h->prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN || h->prm.smoother == STOKES_SMOOTHER_SCHUR_UZAWA) {
     sv::launch_bs_sweep<float>(L.d, h->bs, static_cast<float*>(h->bs_buf), L.rf, x, b, xo, h->stream);
   } else if (L.tcB != nullptr && L.tc_hi >= L.tc_lo) {
     // interior tiles on the tensor cores, the ring of boundary tiles on the SIMT kernel
@@ -527,13 +527,12 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   if (prm.tile >= sv::VANKA_CFG_SPLIT && prm.prec != STOKES_FP64)
     return fail(STOKES_ERR_ARG, "tiles 4 and 5 (split sweep) are FP64 only");
   if (prm.cycle < 1 || prm.cycle > 2) return fail(STOKES_ERR_ARG, "cycle must be 1 (V) or 2 (W)");
-  if (prm.smoother != STOKES_SMOOTHER_SHARED && prm.smoother != STOKES_SMOOTHER_PER_PATCH &&
-      prm.smoother != STOKES_SMOOTHER_BRAESS_SARAZIN)
+  if (prm.smoother < STOKES_SMOOTHER_SHARED || prm.smoother > STOKES_SMOOTHER_SCHUR_UZAWA)
     return fail(STOKES_ERR_ARG, "unknown smoother");
-  if (prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN &&
+  if ((prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN || prm.smoother == STOKES_SMOOTHER_SCHUR_UZAWA) &&
       (prm.prec == STOKES_MIXED_BF16 || !(prm.bs_t > 0.0) || !(prm.bs_omega > 0.0) ||
        !(prm.bs_jacobi_weight > 0.0) || prm.bs_jacobi_iters < 1 || prm.bs_jacobi_iters > 64))
-    return fail(STOKES_ERR_ARG, "Braess-Sarazin: FP64 or mixed FP32, t, omega, weight > 0, 1..64 Jacobi steps");
+    return fail(STOKES_ERR_ARG, "Braess-Sarazin / Schur-Uzawa: FP64 or mixed FP32, t, omega, weight > 0, 1..64 Jacobi steps");
   if (prm.smoother == STOKES_SMOOTHER_PER_PATCH && prm.prec != STOKES_FP64)
     return fail(STOKES_ERR_ARG, "per-patch inverses (simple Vanka) are FP64 only");
   std::vector<int> sizes;
@@ -554,6 +553,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   h->bs.omega = prm.bs_omega;
   h->bs.jacobi_weight = prm.bs_jacobi_weight;
   h->bs.jacobi_iters = prm.bs_jacobi_iters;
+  h->bs.uzawa = (prm.smoother == STOKES_SMOOTHER_SCHUR_UZAWA);
   h->nu = viscosity;
   h->n = n;
   h->stream = static_cast<cudaStream_t>(stream);
@@ -607,7 +607,8 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
     // patch corrections of the per-patch-inverse and the split FP64 sweeps (finest-level size)
     if (e == cudaSuccess && prm.prec == STOKES_FP64 && k + 1 == sizes.size())
       e = dalloc(&h->delta, sv::patch_delta_doubles(L.d));
-    if (e == cudaSuccess && prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN && k + 1 == sizes.size()) {
+    if (e == cudaSuccess && (prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN ||
+                             prm.smoother == STOKES_SMOOTHER_SCHUR_UZAWA) && k + 1 == sizes.size()) {
       const size_t el = sv::bs_scratch_elems(L.d) * (prm.prec == STOKES_FP64 ? sizeof(double) : sizeof(float));
       e = cudaMalloc(&h->bs_buf, el);
     }

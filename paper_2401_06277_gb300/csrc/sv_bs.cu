@@ -1,5 +1,6 @@
 // sv_bs.cu -- Braess-Sarazin relaxation (Section 3.1, Algorithm 2: the inexact
-// variant), matrix-free, templated on the V-cycle's element type.  With
+// variant) and Schur-Uzawa relaxation (Section 3.3, Algorithm 4), matrix-free,
+// templated on the V-cycle's element type.  With
 // D = diag(L) and S = -(1/t) B D^-1 B^T one sweep is
 //
 //   r = b - A x                                              (k_apply)
@@ -8,6 +9,10 @@
 //     q = D^-1 B^T dp                                        (k_bs_dinv_btp)
 //     dp += w_J (g - S dp) / diag(S),  S dp = -(1/t) B q      (k_bs_jacobi)
 //   du = (1/t) D^-1 (r_u - B^T dp);  x_out = x + omega_BS (du, dp)   (k_bs_update)
+//
+// Schur-Uzawa solves the block lower-triangular system [[tD, 0], [B, S]]: its
+// Schur right-hand side r_p - B du with du = (1/t) D^-1 r_u is the same g, and
+// its velocity update drops the B^T dp term.
 //
 // On a uniform grid diag(L) depends only on the parities of a node's indices:
 // nu/90 times 224 (vertex), 352 (edge midpoints) or 512 (cell centre), so D^-1
@@ -145,8 +150,9 @@ __global__ void k_bs_jacobi(LevelDev L, const T* __restrict__ q, const T* __rest
   dp[p] = fma(wj, (g[p] - sdp) / ds[p], dp[p]);
 }
 
-// du = (1/t) D^-1 (r_u - B^T dp); x_out = x + omega (du, dp)
-template <typename T, int PI, int PJ>
+// du = (1/t) D^-1 (r_u - B^T dp) (Braess-Sarazin) or (1/t) D^-1 r_u (Schur-Uzawa, UZ);
+// x_out = x + omega (du, dp)
+template <typename T, int PI, int PJ, bool UZ>
 __device__ __forceinline__ void bs_update_node(const LevelDev& L, const T (&P)[3][3], const T* __restrict__ r,
                                                const T* __restrict__ x, T* __restrict__ xo, T inv_t, T om, int a,
                                                int b) {
@@ -160,8 +166,12 @@ __device__ __forceinline__ void bs_update_node(const LevelDev& L, const T (&P)[3
     const long long kc = c * L.nv + k;
     T du;
     if (fr) {
-      const T bt = c == 0 ? btp3<T, PI, PJ, 0>(P) : btp3<T, PI, PJ, 1>(P);
-      du = sc * (r[kc] - cb * bt);
+      if (UZ) {
+        du = sc * r[kc];
+      } else {
+        const T bt = c == 0 ? btp3<T, PI, PJ, 0>(P) : btp3<T, PI, PJ, 1>(P);
+        du = sc * (r[kc] - cb * bt);
+      }
     } else {
       du = inv_t * r[kc];
     }
@@ -169,17 +179,17 @@ __device__ __forceinline__ void bs_update_node(const LevelDev& L, const T (&P)[3
   }
 }
 
-template <typename T>
+template <typename T, bool UZ>
 __global__ void k_bs_update(LevelDev L, const T* __restrict__ r, const T* __restrict__ dp, const T* __restrict__ x,
                             T* __restrict__ xo, T inv_t, T om) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
   if (a > L.n || b > L.n) return;
   T P[3][3];
   load_p3(L, dp, a, b, P);
-  bs_update_node<T, 0, 0>(L, P, r, x, xo, inv_t, om, a, b);
-  bs_update_node<T, 1, 0>(L, P, r, x, xo, inv_t, om, a, b);
-  bs_update_node<T, 0, 1>(L, P, r, x, xo, inv_t, om, a, b);
-  bs_update_node<T, 1, 1>(L, P, r, x, xo, inv_t, om, a, b);
+  bs_update_node<T, 0, 0, UZ>(L, P, r, x, xo, inv_t, om, a, b);
+  bs_update_node<T, 1, 0, UZ>(L, P, r, x, xo, inv_t, om, a, b);
+  bs_update_node<T, 0, 1, UZ>(L, P, r, x, xo, inv_t, om, a, b);
+  bs_update_node<T, 1, 1, UZ>(L, P, r, x, xo, inv_t, om, a, b);
   const long long kp = 2 * L.nv + static_cast<long long>(b) * L.np + a;
   xo[kp] = fma(om, P[1][1], x != nullptr ? x[kp] : T(0));
 }
@@ -211,7 +221,10 @@ void launch_bs_sweep(const LevelDev& L, const BSParams& prm, T* scratch, T* rbuf
     k_bs_dinv_btp<T><<<grid, blk, 0, s>>>(L, dp, q);
     k_bs_jacobi<T><<<grid, blk, 0, s>>>(L, q, g, ds, dp, inv_t, wj);
   }
-  k_bs_update<T><<<grid, blk, 0, s>>>(L, r, dp, x, xo, inv_t, om);
+  if (prm.uzawa)
+    k_bs_update<T, true><<<grid, blk, 0, s>>>(L, r, dp, x, xo, inv_t, om);
+  else
+    k_bs_update<T, false><<<grid, blk, 0, s>>>(L, r, dp, x, xo, inv_t, om);
 }
 
 template void launch_bs_sweep<double>(const LevelDev&, const BSParams&, double*, double*, const double*,

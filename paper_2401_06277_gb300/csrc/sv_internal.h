@@ -55,10 +55,11 @@ struct FastDiagT {
 };
 using FastDiag = FastDiagT<double>;
 
-// Braess-Sarazin parameters (Section 3.1, Algorithm 2; see stokes_params).
+// Braess-Sarazin / Schur-Uzawa parameters (Sections 3.1, 3.3; see stokes_params).
 struct BSParams {
   double t = 1.0, omega = 1.0, jacobi_weight = 1.0;
   int jacobi_iters = 2;
+  bool uzawa = false;   // Schur-Uzawa (Algorithm 4): no B^T dp in the velocity update
 };
 
 // Device-side description of one level (passed by value to kernels).

@@ -29,6 +29,7 @@ STOKES_MIXED_BF16 = 2
 STOKES_SMOOTHER_SHARED = 0
 STOKES_SMOOTHER_PER_PATCH = 1
 STOKES_SMOOTHER_BRAESS_SARAZIN = 2
+STOKES_SMOOTHER_SCHUR_UZAWA = 3
 
 _STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NONFINITE",
            5: "NOT_CONVERGED", 6: "ERR_TIMEOUT"}

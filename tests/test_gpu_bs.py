@@ -105,3 +105,35 @@ def test_bs_rejects_bf16_and_bad_parameters(pkg):
         pkg.Hierarchy(16, smoother=pkg.STOKES_SMOOTHER_BRAESS_SARAZIN, prec=pkg.STOKES_MIXED_BF16)
     with pytest.raises(stokes.StokesError):
         pkg.Hierarchy(16, smoother=pkg.STOKES_SMOOTHER_BRAESS_SARAZIN, bs_jacobi_iters=0)
+
+
+# ---- Schur-Uzawa (Section 3.3, Algorithm 4) ----
+
+SU_KW = dict(bs_t=1.0, bs_omega=1.0, bs_jacobi_weight=0.4, bs_jacobi_iters=1)
+SU = O.BSParams(t=1.0, omega=1.0, jacobi_weight=0.4, jacobi_iters=1)
+
+
+@pytest.mark.parametrize("n", [8, 32])
+def test_su_sweep_and_vcycle(pkg, n):
+    from paper_2401_06277_gb300 import stokes
+    H = pkg.Hierarchy(n, smoother=pkg.STOKES_SMOOTHER_SCHUR_UZAWA, **SU_KW)
+    for l in range(H.levels):
+        nl = stokes.stokes_level_n(H.handle, l)
+        lv = O.build_level(nl, 1.0)
+        x, b = si.random_vector(nl, 50 + l), si.random_vector(nl, 60 + l)
+        assert rel(host(H.sweep(dev(x), dev(b), level=l)), O.schur_uzawa_sweep(lv, x, b, SU)) <= 1e-12
+    Ho = O.build_hierarchy(n, smoother="su", bs=SU)
+    r = si.random_vector(n, 70)
+    assert rel(host(H.vcycle(dev(r))), O.vcycle(Ho, r)) <= 1e-12
+    H.close()
+
+
+def test_su_solve(pkg):
+    n = 16
+    H = pkg.Hierarchy(n, smoother=pkg.STOKES_SMOOTHER_SCHUR_UZAWA, rtol=1e-13, **SU_KW)
+    lv = O.build_level(n, 1.0)
+    b = O.assemble_rhs(lv, si.random_force(n, 71), si.manufactured_velocity(n))
+    x, it, rr = H.solve(dev(b))
+    xd = O.normalize_pressure(lv, O.direct_solve(lv, b))
+    assert np.linalg.norm(O.normalize_pressure(lv, host(x)) - xd) <= 1e-10 * np.linalg.norm(xd)
+    H.close()
