@@ -607,6 +607,81 @@ def relax(H: Hierarchy, lv: Level, x: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------
+# Block-triangular preconditioner (Section 3.4, Algorithm 5)
+# ----------------------------------------------------------------------------
+
+
+@dataclass
+class BTParams:
+    """Section 6.8's settings: 3 V(3,3) cycles per block, weighted Jacobi of weight
+    0.6 on the pressure mass matrix and 1.0 on the velocity Laplacian."""
+    cycles: int = 3
+    nu1: int = 3
+    nu2: int = 3
+    omega_p: float = 0.6
+    omega_u: float = 1.0
+
+
+def scalar_vcycle(mats: list, prols: list, b: np.ndarray, l: int, omega: float, nu1: int, nu2: int,
+                  coarse_inv: np.ndarray, x0: np.ndarray | None = None) -> np.ndarray:
+    """One V(nu1, nu2) cycle of multigrid on the SPD matrices mats[l] (level 0 coarsest),
+    weighted-Jacobi smoothing, prolongations prols[l] (level l-1 -> l), exact coarse solve."""
+    if l == 0:
+        return coarse_inv @ b
+    A = mats[l]
+    dinv = 1.0 / A.diagonal()
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    for _ in range(nu1):
+        x = x + omega * dinv * (b - A @ x)
+    P = prols[l]
+    x = x + P @ scalar_vcycle(mats, prols, P.T @ (b - A @ x), l - 1, omega, nu1, nu2, coarse_inv)
+    for _ in range(nu2):
+        x = x + omega * dinv * (b - A @ x)
+    return x
+
+
+def block_triangular_setup(H: Hierarchy) -> dict:
+    """Per level: the velocity Laplacian block L (eliminated: identity on Dirichlet rows),
+    the pressure mass matrix M, B, and the blocks of the prolongation."""
+    out = {"L": [], "M": [], "B": [], "PL": [None], "PM": [None]}
+    for l, lv in enumerate(H.levels):
+        nv2 = 2 * lv.mesh.nvel
+        A = lv.A.tocsr()
+        out["L"].append(A[:nv2, :nv2].tocsr())
+        out["B"].append(A[nv2:, :nv2].tocsr())
+        out["M"].append(lv.Mp.tocsr())
+        if l > 0:
+            P = lv.P.tocsr()
+            out["PL"].append(P[:nv2, :2 * H.levels[l - 1].mesh.nvel].tocsr())
+            out["PM"].append(P[nv2:, 2 * H.levels[l - 1].mesh.nvel:].tocsr())
+    out["Linv0"] = np.linalg.inv(out["L"][0].toarray())
+    out["Minv0"] = np.linalg.inv(out["M"][0].toarray())
+    return out
+
+
+def block_triangular_apply(H: Hierarchy, bt: dict, r: np.ndarray, prm: BTParams = BTParams(),
+                           exact: bool = False) -> np.ndarray:
+    """Algorithm 5: approximately solve M dp = -r_p, then L du = r_u - B^T dp, each by
+    `cycles` multigrid V(nu1, nu2) cycles (iterative refinement from zero), or exactly."""
+    top = len(H.levels) - 1
+    nv2 = 2 * H.levels[top].mesh.nvel
+    ru, rp = r[:nv2], r[nv2:]
+    M, L, B = bt["M"][top], bt["L"][top], bt["B"][top]
+
+    def solve(mats, prols, rhs, omega, cinv):
+        if exact:
+            return spla.spsolve(mats[top].tocsc(), rhs)
+        x = np.zeros_like(rhs)
+        for _ in range(prm.cycles):
+            x = x + scalar_vcycle(mats, prols, rhs - mats[top] @ x, top, omega, prm.nu1, prm.nu2, cinv)
+        return x
+
+    dp = solve(bt["M"], bt["PM"], -rp, prm.omega_p, bt["Minv0"])
+    du = solve(bt["L"], bt["PL"], ru - B.T @ dp, prm.omega_u, bt["Linv0"])
+    return np.concatenate([du, dp])
+
+
+# ----------------------------------------------------------------------------
 # FGMRES(m), right-preconditioned (Saad's flexible GMRES)
 # ----------------------------------------------------------------------------
 
