@@ -293,7 +293,13 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0, 
     tile = TILE_NAMES[stokes.stokes_level_tile(H.handle, H.levels - 1)]
     peaks = measured_peaks()
     sm_max = args.sm_max_mhz or peaks.get("sm_max_mhz", 2070.0)
-    if smoother in (2, 3):
+    if (hkw or {}).get("precond") == 1:
+        # no relaxation sweeps: the preconditioner is 2 x 3 V(3,3) cycles of scalar
+        # multigrid (Jacobi on L and M); its cost per application is vcycle_only below
+        roofline = {"bound": "hbm", "kernel": "block-triangular preconditioner (scalar multigrid on L and M)",
+                    "achieved": None, "peak": peaks.get("hbm_gbs", 6780.0), "unit": "GB/s", "frac": None,
+                    "traffic": None, "note": "no Vanka/Braess-Sarazin sweep to time; see vcycle_only"}
+    elif smoother in (2, 3):
         # Braess-Sarazin (two Jacobi steps) per vertex: residual 361, g and diag(S) 2 x 48,
         # D^-1 B^T dp 2 x 4 x 9 + 8, B q 48 + 4, du 2 x 4 x (9 + 3) + 2 x 9: ~700 flops.  Vector
         # passes: residual 3 (x, b -> r); g 1 + 3 pressure (-> g, diag(S), dp); D^-1 B^T dp
@@ -358,8 +364,8 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0, 
                     "fp32_gflops_achieved": round(sweep_flops(n) / (sweep_ms * 1e-3) / 1e9, 1)}
     names = TILE_NAMES
     tiles = [names[stokes.stokes_level_tile(H.handle, lv)] for lv in range(H.levels - 1, 0, -1)]
-    roofline.update({"launch_ms": round(sweep_ms, 4), "launches_timed": st["sweeps_timed"], "tile": tile,
-                     "tiles_fine_to_coarse": tiles})
+    roofline.update({"launch_ms": round(sweep_ms, 4) if st["sweeps_timed"] else None,
+                     "launches_timed": st["sweeps_timed"], "tile": tile, "tiles_fine_to_coarse": tiles})
     tr = TRAFFIC_1024.get(prec_name) if smoother == 0 else None
     if tr is not None and tile == tr["tile"]:
         # DRAM bytes of one launch of the same kernel at 1024^2 (ncu capture), scaled by dofs
@@ -502,8 +508,10 @@ def run_ours(args) -> None:
         # Braess-Sarazin relaxation (the paper's comparison, Section 6.8) in FP64 and mixed FP32
         # and Schur-Uzawa with the paper's parameters (t = 1, Jacobi weight 0.4, one step)
         su = dict(bs_t=1.0, bs_omega=1.0, bs_jacobi_weight=0.4, bs_jacobi_iters=1)
+        # and the block-triangular preconditioner (three V(3,3) cycles per block, Section 6.8)
         for name, pn, sm, kw in (("fp64_simple_vanka", "fp64", 1, None), ("fp64_braess_sarazin", "fp64", 2, None),
-                                 ("mixed_braess_sarazin", "mixed", 2, None), ("fp64_schur_uzawa", "fp64", 3, su)):
+                                 ("mixed_braess_sarazin", "mixed", 2, None), ("fp64_schur_uzawa", "fp64", 3, su),
+                                 ("fp64_block_triangular", "fp64", 0, {"precond": 1})):
             o = time_form(args, pn, ws, rank, f_host, ud_host, with_e2e=False, smoother=sm, hkw=kw)
             forms[name] = {k: o[k] for k in keys}
             forms[name]["roofline"] = o["roofline"]

@@ -94,6 +94,15 @@ typedef struct {
   int cycle;        /* coarse-grid corrections per level (Algorithm 1): 1 =
                        V-cycle, 2 = W-cycle (the coarse problem is cycled twice;
                        the second time on the updated residual)           (1)  */
+  int precond;      /* FGMRES preconditioner: 0 = monolithic multigrid (the
+                       smoother above), 1 = block-triangular (Section 3.4,
+                       Algorithm 5: M dp = -r_p, then L du = r_u - B^T dp, each
+                       by bt_cycles V(bt_nu, bt_nu) cycles of scalar multigrid
+                       with weighted Jacobi; FP64 only)                   (0)  */
+  int bt_cycles;           /*                                       (3)    */
+  int bt_nu;               /*                                       (3)    */
+  double bt_omega_u;       /* Jacobi weight on L                    (1.0)  */
+  double bt_omega_p;       /* Jacobi weight on M                    (0.6)  */
 } stokes_params;
 
 /* How each Vanka patch solve A_i^-1 r_i is applied (Section 4, Section 6.2). */
@@ -182,7 +191,10 @@ stokes_status stokes_coarse_solve(stokes_hierarchy* h, const double* r, double* 
 stokes_status stokes_initial_guess(stokes_hierarchy* h, const double* b, double* x0);
 
 /* z = MG(r): one V(nu1, nu2) cycle on the finest level with zero initial
- * guess (Algorithm 1).  r and z have length N(n); they must not alias. */
+ * guess (Algorithm 1; a W-cycle with params.cycle = 2), or, with
+ * params.precond = 1, one application of the block-triangular preconditioner
+ * (Section 3.4, Algorithm 5) -- the preconditioner FGMRES applies.  r and z
+ * have length N(n); they must not alias. */
 stokes_status stokes_vcycle_apply(stokes_hierarchy* h, const double* r, double* z);
 
 /* Solve A x = b by FGMRES(restart) right-preconditioned with the V-cycle

@@ -75,6 +75,10 @@ void free_all(stokes_hierarchy* h) {
   h->delta = nullptr;
   cudaFree(h->bs_buf);
   h->bs_buf = nullptr;
+  cudaFree(h->bt_GL);
+  cudaFree(h->bt_GM);
+  cudaFree(h->bt_buf);
+  h->bt_GL = h->bt_GM = h->bt_buf = nullptr;
   h->lv.clear();
   cudaFree(h->coarse_G);
   cudaFree(h->V);
@@ -238,11 +242,96 @@ void vcycle(stokes_hierarchy* h, int l, const R* b, R* out) {
   if (h->prm.nu2 == 0) cudaMemcpyAsync(out, cur, L.d.N * sizeof(R), cudaMemcpyDeviceToDevice, s);
 }
 
+// ---- block-triangular preconditioner (Section 3.4, Algorithm 5) ----
+// One V(nu, nu) cycle of scalar multigrid on block blk (0: velocity Laplacian L,
+// 1: pressure mass M) with weighted Jacobi, zero initial guess, exact coarse solve.
+// Vectors keep the full [u_x | u_y | p] layout with the other block at zero; the
+// velocity residual uses the Stokes operator, whose B^T p term then vanishes.
+void bt_vcycle(stokes_hierarchy* h, int blk, int l, const double* b, double* out) {
+  cudaStream_t s = h->stream;
+  sv::Level& L = h->lv[l];
+  if (l == 0) {
+    cudaMemsetAsync(out, 0, L.d.N * sizeof(double), s);
+    if (blk == 0)
+      sv::launch_coarse(h->bt_GL, h->bt_nL, b, out, s);
+    else
+      sv::launch_coarse(h->bt_GM, h->bt_nM, b + 2 * L.d.nv, out + 2 * L.d.nv, s);
+    return;
+  }
+  const double om = (blk == 0) ? h->prm.bt_omega_u : h->prm.bt_omega_p;
+  auto resid = [&](const double* x, double* r) {
+    if (blk == 0)
+      sv::launch_apply<double>(L.d, x, b, r, 1, s);
+    else
+      sv::launch_mass_resid(L.d, x, b, r, s);
+  };
+  auto smooth = [&](double*& cur, double* dst) {
+    if (cur == nullptr) {
+      sv::launch_block_jacobi(L.d, blk, nullptr, b, dst, om, s);
+    } else {
+      resid(cur, L.r);
+      sv::launch_block_jacobi(L.d, blk, cur, L.r, dst, om, s);
+    }
+    cur = dst;
+  };
+  double* cur = nullptr;
+  for (int it = 0; it < h->prm.bt_nu; ++it) smooth(cur, (cur == L.x0) ? L.x1 : L.x0);
+  if (cur == nullptr) {
+    cudaMemsetAsync(L.x0, 0, L.d.N * sizeof(double), s);
+    cur = L.x0;
+  }
+  sv::Level& C = h->lv[l - 1];
+  resid(cur, L.r);
+  sv::launch_restrict<double>(L.d, C.d, L.r, C.b, s);
+  bt_vcycle(h, blk, l - 1, C.b, C.e);
+  sv::launch_prolong_add<double>(L.d, C.d, C.e, cur, s);
+  for (int it = 0; it < h->prm.bt_nu; ++it) smooth(cur, (it == h->prm.bt_nu - 1) ? out : ((cur == L.x0) ? L.x1 : L.x0));
+  if (h->prm.bt_nu == 0) cudaMemcpyAsync(out, cur, L.d.N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+
+// z = P_BT^-1 r: dp from bt_cycles cycles on M dp = -r_p, then du from bt_cycles
+// cycles on L du = r_u - B^T dp (iterative refinement from zero).
+void bt_precondition(stokes_hierarchy* h, const double* r, double* z) {
+  cudaStream_t s = h->stream;
+  const int top = static_cast<int>(h->lv.size()) - 1;
+  sv::Level& F = h->lv[top];
+  const long long N = F.d.N, nvel = 2 * F.d.nv;
+  double* rhs = h->bt_buf;
+  double* tmp = rhs + N;
+  double* acc = tmp + N;
+  // 1. M dp = -r_p (rhs = (0, -r_p)), accumulated in z = (0, dp)
+  sv::launch_scale(rhs, r, nullptr, -1.0, N, s);
+  cudaMemsetAsync(rhs, 0, nvel * sizeof(double), s);
+  cudaMemsetAsync(z, 0, N * sizeof(double), s);
+  for (int c = 0; c < h->prm.bt_cycles; ++c) {
+    sv::launch_mass_resid(F.d, c == 0 ? nullptr : z, rhs, tmp, s);
+    bt_vcycle(h, 1, top, tmp, F.e);
+    sv::launch_add(z, F.e, N, s);
+  }
+  // 2. L du = r_u - B^T dp: rhs = r - A (0, dp) on the velocity rows
+  sv::launch_apply<double>(F.d, z, r, rhs, 1, s);
+  cudaMemsetAsync(acc, 0, N * sizeof(double), s);
+  for (int c = 0; c < h->prm.bt_cycles; ++c) {
+    const double* in = rhs;
+    if (c > 0) {
+      sv::launch_apply<double>(F.d, acc, rhs, tmp, 1, s);
+      in = tmp;
+    }
+    bt_vcycle(h, 0, top, in, F.e);
+    sv::launch_add(acc, F.e, N, s);
+  }
+  cudaMemcpyAsync(z, acc, nvel * sizeof(double), cudaMemcpyDeviceToDevice, s);
+}
+
 // z = MG(r) on the finest level in the hierarchy's precision.  The mixed form
 // converts r to FP32, cycles in FP32 and converts the result back to FP64.
 void precondition(stokes_hierarchy* h, const double* r, double* z) {
   const int top = static_cast<int>(h->lv.size()) - 1;
   ++h->vcycles;
+  if (h->prm.precond == 1) {
+    bt_precondition(h, r, z);
+    return;
+  }
   if (h->prm.prec == STOKES_FP64 || top == 0) {
     vcycle<double>(h, top, r, z);
     return;
@@ -462,7 +551,7 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
 
 cudaError_t choose_tiles(stokes_hierarchy* h) {
   for (sv::Level& L : h->lv) {
-    if (h->prm.tile >= 0 || h->prm.smoother != STOKES_SMOOTHER_SHARED) {
+    if (h->prm.tile >= 0 || h->prm.smoother != STOKES_SMOOTHER_SHARED || h->prm.precond == 1) {
       L.vk_cfg = L.vk_cfg_f = h->prm.tile >= 0 ? h->prm.tile : 1;   // no tiled sweep runs with per-patch inverses
       continue;
     }
@@ -504,6 +593,11 @@ void stokes_default_params(stokes_params* p) {
   p->bs_jacobi_weight = 1.0;
   p->bs_jacobi_iters = 2;
   p->cycle = 1;
+  p->precond = 0;
+  p->bt_cycles = 3;
+  p->bt_nu = 3;
+  p->bt_omega_u = 1.0;
+  p->bt_omega_p = 0.6;
 }
 
 const char* stokes_last_error(void) { return g_err.c_str(); }
@@ -527,6 +621,10 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   if (prm.tile >= sv::VANKA_CFG_SPLIT && prm.prec != STOKES_FP64)
     return fail(STOKES_ERR_ARG, "tiles 4 and 5 (split sweep) are FP64 only");
   if (prm.cycle < 1 || prm.cycle > 2) return fail(STOKES_ERR_ARG, "cycle must be 1 (V) or 2 (W)");
+  if (prm.precond < 0 || prm.precond > 1) return fail(STOKES_ERR_ARG, "precond must be 0 or 1");
+  if (prm.precond == 1 && (prm.prec != STOKES_FP64 || prm.bt_cycles < 1 || prm.bt_nu < 0 ||
+                           !(prm.bt_omega_u > 0.0) || !(prm.bt_omega_p > 0.0)))
+    return fail(STOKES_ERR_ARG, "block-triangular preconditioner: FP64, bt_cycles >= 1, bt_nu >= 0, weights > 0");
   if (prm.smoother < STOKES_SMOOTHER_SHARED || prm.smoother > STOKES_SMOOTHER_SCHUR_UZAWA)
     return fail(STOKES_ERR_ARG, "unknown smoother");
   if ((prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN || prm.smoother == STOKES_SMOOTHER_SCHUR_UZAWA) &&
@@ -639,6 +737,25 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
       free_all(h);
       delete h;
       return cuda_fail(e, "coarse inverse upload");
+    }
+  }
+  if (prm.precond == 1) {
+    std::vector<double> GL, GM;
+    if (!sv::bt_coarse_inverses(prm.coarse_n, viscosity, GL, GM)) {
+      free_all(h);
+      delete h;
+      return fail(STOKES_ERR_ARG, "coarse Laplacian or mass matrix is singular");
+    }
+    h->bt_nL = static_cast<int>(2 * h->lv[0].d.nv);
+    h->bt_nM = h->lv[0].d.np * h->lv[0].d.np;
+    const size_t Nf = static_cast<size_t>(h->lv.back().d.N);
+    if ((e = dalloc(&h->bt_GL, GL.size())) != cudaSuccess || (e = dalloc(&h->bt_GM, GM.size())) != cudaSuccess ||
+        (e = dalloc(&h->bt_buf, 3 * Nf)) != cudaSuccess ||
+        (e = cudaMemcpy(h->bt_GL, GL.data(), GL.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(h->bt_GM, GM.data(), GM.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      free_all(h);
+      delete h;
+      return cuda_fail(e, "block-triangular set-up");
     }
   }
   const size_t Nf = static_cast<size_t>(h->lv.back().d.N);

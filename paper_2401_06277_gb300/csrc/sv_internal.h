@@ -123,6 +123,11 @@ struct stokes_hierarchy {
   unsigned* ticket = nullptr;    // last-block counter of the fused Gram-Schmidt kernels
   double* delta = nullptr;       // patch corrections of the simple-Vanka sweep (finest-level size)
   void* bs_buf = nullptr;        // Braess-Sarazin scratch in the V-cycle precision (finest-level size)
+  // block-triangular preconditioner: dense inverses of the coarsest L and M, 3 finest vectors
+  double* bt_GL = nullptr;
+  double* bt_GM = nullptr;
+  int bt_nL = 0, bt_nM = 0;
+  double* bt_buf = nullptr;
   sv::BSParams bs;
   double* host_scalars = nullptr;  // pinned host mirror of a few scalars
   int* dev_err = nullptr;          // set by kernels whose bounded waits expired
@@ -213,6 +218,16 @@ size_t bs_scratch_elems(const LevelDev& L);   // 2 nv + 3 np^2
 template <typename T>
 void launch_bs_sweep(const LevelDev& L, const BSParams& prm, T* scratch, T* rbuf, const T* x, const T* b, T* xo,
                      cudaStream_t s);
+
+// ---- block-triangular preconditioner kernels (sv_bt.cu), FP64 ----
+// y_p = b_p - M x_p (x may be nullptr), y_u = 0
+void launch_mass_resid(const LevelDev& L, const double* x, const double* b, double* y, cudaStream_t s);
+// xo = x + omega D^-1 r on block (0 velocity / diag L, 1 pressure / diag M), 0 on the other
+void launch_block_jacobi(const LevelDev& L, int block, const double* x, const double* r, double* xo, double omega,
+                         cudaStream_t s);
+void launch_add(double* y, const double* x, long long N, cudaStream_t s);   // y += x
+// host: dense inverses of the coarsest velocity Laplacian block and pressure mass matrix
+bool bt_coarse_inverses(int n, double nu, std::vector<double>& GL, std::vector<double>& GM);
 
 // ---- simple Vanka (sv_simple.cu): per-patch inverses, FP64 ----
 int patch_stride(const LevelDev& L);                 // patch count rounded up to 32

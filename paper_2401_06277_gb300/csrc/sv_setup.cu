@@ -389,4 +389,34 @@ bool coarse_inverse(int n, double nu, std::vector<double>& G) {
   return true;
 }
 
+// Dense inverses of the coarsest level's velocity Laplacian block (Dirichlet
+// rows identity, 2 (2n+1)^2) and Q1 pressure mass matrix ((n+1)^2), for the
+// exact coarse solves of the block-triangular preconditioner.
+bool bt_coarse_inverses(int n, double nu, std::vector<double>& GL, std::vector<double>& GM) {
+  std::vector<double> A;
+  dense_operator(n, nu, A);
+  const int nq = 2 * n + 1, np = n + 1;
+  const int nL = 2 * nq * nq, N = nL + np * np;
+  GL.assign(static_cast<size_t>(nL) * nL, 0.0);
+  for (int i = 0; i < nL; ++i)
+    for (int j = 0; j < nL; ++j) GL[static_cast<size_t>(i) * nL + j] = A[static_cast<size_t>(i) * N + j];
+  const double h = 1.0 / n, c = (h / 6.0) * (h / 6.0);
+  auto m = [n](int i, int d) -> double {
+    if (d == 0) return (i == 0 || i == n) ? 2.0 : 4.0;
+    const int k = i + d;
+    return (k < 0 || k > n || (d != 1 && d != -1)) ? 0.0 : 1.0;
+  };
+  const int nM = np * np;
+  GM.assign(static_cast<size_t>(nM) * nM, 0.0);
+  for (int j = 0; j < np; ++j)
+    for (int i = 0; i < np; ++i)
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di) {
+          const int i2 = i + di, j2 = j + dj;
+          if (i2 < 0 || j2 < 0 || i2 > n || j2 > n) continue;
+          GM[static_cast<size_t>(j * np + i) * nM + (j2 * np + i2)] = c * m(i, di) * m(j, dj);
+        }
+  return invert_dense(GL, nL) && invert_dense(GM, nM);
+}
+
 }  // namespace sv

@@ -52,7 +52,8 @@ class stokes_params(ctypes.Structure):
                 ("rtol", ctypes.c_double), ("prec", ctypes.c_int), ("tile", ctypes.c_int),
                 ("smoother", ctypes.c_int), ("bs_t", ctypes.c_double), ("bs_omega", ctypes.c_double),
                 ("bs_jacobi_weight", ctypes.c_double), ("bs_jacobi_iters", ctypes.c_int),
-                ("cycle", ctypes.c_int)]
+                ("cycle", ctypes.c_int), ("precond", ctypes.c_int), ("bt_cycles", ctypes.c_int),
+                ("bt_nu", ctypes.c_int), ("bt_omega_u", ctypes.c_double), ("bt_omega_p", ctypes.c_double)]
 
 
 _lib = None
@@ -417,6 +418,11 @@ class Hierarchy:
     bs_jacobi_weight: float = 1.0
     bs_jacobi_iters: int = 2
     cycle: int = 1
+    precond: int = 0
+    bt_cycles: int = 3
+    bt_nu: int = 3
+    bt_omega_u: float = 1.0
+    bt_omega_p: float = 0.6
 
     def __post_init__(self):
         p = default_params()
@@ -427,6 +433,8 @@ class Hierarchy:
         p.bs_t, p.bs_omega = self.bs_t, self.bs_omega
         p.bs_jacobi_weight, p.bs_jacobi_iters = self.bs_jacobi_weight, self.bs_jacobi_iters
         p.cycle = self.cycle
+        p.precond, p.bt_cycles, p.bt_nu = self.precond, self.bt_cycles, self.bt_nu
+        p.bt_omega_u, p.bt_omega_p = self.bt_omega_u, self.bt_omega_p
         self.handle = stokes_hierarchy_create(self.n, self.viscosity, p)
         self.levels, _ = stokes_level_info(self.handle)
         self.N = vec_len(self.n)
