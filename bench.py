@@ -226,13 +226,15 @@ def measured_peaks() -> dict:
 
 
 PRECS = {"fp64": 0, "mixed": 1, "bf16": 2}
+# share of the finest-level sweeps of a V(2,2) cycle that start from a zero guess
+ZERO_GUESS_SHARE = 1.0 / 4.0
 # sweep configurations by stokes_level_tile: fused tiles of TX x TY vertices, or (4, 5; FP64
 # only) the split sweep: 16 x 16 own-patch solves writing the corrections, then the update
 # (5: compiled for two CTAs per SM)
 TILE_NAMES = ["8x8", "16x8", "16x16", "14x14", "split16x16", "split16x16x2"]
 
 
-def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0, hkw=None):
+def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0, hkw=None, n=None):
     """Time K FGMRES solves of one precision form (smoother 1: per-patch inverses, the
     paper's simple Vanka); returns the record."""
     import torch
@@ -241,7 +243,12 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0, 
     from paper_2401_06277_gb300 import stokes
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    n = args.n
+    if n is None:
+        n = args.n
+    else:   # a secondary form timed at another size: its own seeded inputs
+        import stokes_inputs as si
+        f_host = torch.from_numpy(si.random_force(n, args.seed + rank))
+        ud_host = torch.from_numpy(si.manufactured_velocity(n))
     N = dofs(n)
     torch.cuda.synchronize()
     t_setup = time.perf_counter()
@@ -339,7 +346,9 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0, 
                     "hbm_gbs_achieved": round(by / (sweep_ms * 1e-3) / 1e9, 1),
                     "hbm_frac": round(by / (sweep_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6780.0), 4)}
     elif prec_name == "fp64":
-        fl = sweep_flops(n)
+        # the first pre-smoothing sweep of each cycle starts from zero (no residual: 361 flops
+        # per vertex fewer); the timed launches average over all nu1 + nu2 sweeps
+        fl = sweep_flops(n) - ZERO_GUESS_SHARE * 361.0 * (n + 1) ** 2
         peak = SM_COUNT * 4 * sm_max * 1e6 / 1e9   # 2 DFMA / clk / SM
         achieved = fl / (sweep_ms * 1e-3) / 1e9
         kname = ("k_vanka_own<double,16,16> + k_patch_update (split sweep, finest level)" if tile.startswith("split")
@@ -349,10 +358,12 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0, 
                     "traffic": args.traffic,
                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock (FP64 has no "
                                    "measured entry; an FMA-loop probe reached 1196 GFLOP/s)",
-                    "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": sweep_bytes(n),
-                    "hbm_gbs_achieved": round(sweep_bytes(n) / (sweep_ms * 1e-3) / 1e9, 1)}
+                    "algorithmic_flops_per_launch": fl,
+                    "algorithmic_bytes_per_launch": sweep_bytes(n) * (3.0 - ZERO_GUESS_SHARE) / 3.0,
+                    "hbm_gbs_achieved": round(sweep_bytes(n) * (3.0 - ZERO_GUESS_SHARE) / 3.0 / (sweep_ms * 1e-3) / 1e9, 1)}
     else:
-        by = 3.0 * 4.0 * N
+        # read x and b, write x (FP32); the zero-guess sweeps do not read x
+        by = (3.0 - ZERO_GUESS_SHARE) * 4.0 * N
         peak = peaks.get("hbm_gbs", 6780.0)
         achieved = by / (sweep_ms * 1e-3) / 1e9
         kname = ("k_vanka_tc interior tiles + k_vanka<float,14,14> ring (finest level)" if prec_name == "bf16"
@@ -509,12 +520,18 @@ def run_ours(args) -> None:
         # and Schur-Uzawa with the paper's parameters (t = 1, Jacobi weight 0.4, one step)
         su = dict(bs_t=1.0, bs_omega=1.0, bs_jacobi_weight=0.4, bs_jacobi_iters=1)
         # and the block-triangular preconditioner (three V(3,3) cycles per block, Section 6.8)
-        for name, pn, sm, kw in (("fp64_simple_vanka", "fp64", 1, None), ("fp64_braess_sarazin", "fp64", 2, None),
-                                 ("mixed_braess_sarazin", "mixed", 2, None), ("fp64_schur_uzawa", "fp64", 3, su),
-                                 ("fp64_block_triangular", "fp64", 0, {"precond": 1})):
-            o = time_form(args, pn, ws, rank, f_host, ud_host, with_e2e=False, smoother=sm, hkw=kw)
+        # Schur-Uzawa is not h-robust with the paper's parameters (FGMRES iterations 18 / 25 /
+        # 280 at 64^2 / 256^2 / 1024^2, no convergence in 300 at 2048^2), so it is timed at 256^2
+        for name, pn, sm, kw, nn in (("fp64_simple_vanka", "fp64", 1, None, None),
+                                     ("fp64_braess_sarazin", "fp64", 2, None, None),
+                                     ("mixed_braess_sarazin", "mixed", 2, None, None),
+                                     ("fp64_block_triangular", "fp64", 0, {"precond": 1}, None),
+                                     ("fp64_schur_uzawa_256", "fp64", 3, su, 256)):
+            o = time_form(args, pn, ws, rank, f_host, ud_host, with_e2e=False, smoother=sm, hkw=kw, n=nn)
             forms[name] = {k: o[k] for k in keys}
             forms[name]["roofline"] = o["roofline"]
+            if nn is not None:
+                forms[name]["n"] = nn
     batched = None
     if not args.no_batch:
         batched = time_batch(args, "mixed")
