@@ -428,8 +428,20 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0, 
         e2e_vc = allsum(ws, stokes.stokes_stats_read(H.handle)["vcycles"])
         rec["e2e"] = {"value": N * e2e_vc / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
                       "d2h_bytes_per_step": bo, "ms_per_step": e2e_ms / args.steps}
+    if n == args.n:
+        rec["_x"] = x.cpu()   # the last solve's solution, for the comparison across forms
     H.close()
     return rec
+
+
+def solution_difference(x: "torch.Tensor", ref: "torch.Tensor", n: int) -> float:
+    """max |x - ref| / max |ref| with both pressures shifted to zero mean (the pressure is
+    defined up to a constant)."""
+    p0 = 2 * (2 * n + 1) ** 2
+    a, r = x.clone(), ref.clone()
+    a[p0:] -= a[p0:].mean()
+    r[p0:] -= r[p0:].mean()
+    return float((a - r).abs().max() / r.abs().max())
 
 
 def time_batch(args, prec_name: str) -> dict:
@@ -506,8 +518,16 @@ def run_ours(args) -> None:
     f_host = torch.from_numpy(si.random_force(n, args.seed + rank)).pin_memory()
     ud_host = torch.from_numpy(si.manufactured_velocity(n)).pin_memory()
     main = time_form(args, args.prec, ws, rank, f_host, ud_host, with_e2e=True)
+    x_ref = main.pop("_x")
     keys = ("value", "time_to_solution_s", "iters", "ms_per_vcycle", "vcycle_only", "setup_s")
     forms = {args.prec: {k: main[k] for k in keys}}
+
+    def compare(name, o):
+        # every other form solves the same right-hand side to the same tolerance: its
+        # solution's difference from the headline form's (FP64: parity-tested against the oracle)
+        xo = o.pop("_x", None)
+        if xo is not None:
+            forms[name]["solution_diff_vs_" + args.prec] = solution_difference(xo, x_ref, n)
     if not args.single_form:
         for other in PRECS:
             if other == args.prec:
@@ -515,6 +535,7 @@ def run_ours(args) -> None:
             o = time_form(args, other, ws, rank, f_host, ud_host, with_e2e=False)
             forms[other] = {k: o[k] for k in keys}
             forms[other]["roofline"] = o["roofline"]
+            compare(other, o)
         # the paper's simple Vanka (an explicit inverse per patch) in the FP64 form, and
         # Braess-Sarazin relaxation (the paper's comparison, Section 6.8) in FP64 and mixed FP32
         # and Schur-Uzawa with the paper's parameters (t = 1, Jacobi weight 0.4, one step)
@@ -530,6 +551,7 @@ def run_ours(args) -> None:
             o = time_form(args, pn, ws, rank, f_host, ud_host, with_e2e=False, smoother=sm, hkw=kw, n=nn)
             forms[name] = {k: o[k] for k in keys}
             forms[name]["roofline"] = o["roofline"]
+            compare(name, o)
             if nn is not None:
                 forms[name]["n"] = nn
     batched = None
