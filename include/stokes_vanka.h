@@ -145,7 +145,10 @@ stokes_status stokes_hierarchy_destroy(stokes_hierarchy* h);
 /* Number of levels L and the grid size n_l of level l (0 = coarsest). */
 stokes_status stokes_level_info(const stokes_hierarchy* h, int* num_levels, int* n_finest);
 stokes_status stokes_level_n(const stokes_hierarchy* h, int level, int* n_level);
-/* Tile shape used by the Vanka sweep on a level (see stokes_params.tile). */
+/* Sweep configuration used on a level (see stokes_params.tile).  In the BF16
+ * form, 3 on a level where the tensor-core tile fits means the tensor-core
+ * sweep (interior tiles) with its 14x14 SIMT ring; the autotuner may choose a
+ * SIMT shape (0..2) there instead. */
 stokes_status stokes_level_tile(const stokes_hierarchy* h, int level, int* tile);
 
 /* Right-hand side of the eliminated system (Section 2.2 with the boundary data

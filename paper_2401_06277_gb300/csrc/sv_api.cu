@@ -158,7 +158,7 @@ void timed_sweep<float>(stokes_hierarchy* h, bool finest, sv::Level& L, const fl
   if (ev) cudaEventRecord(ev[0], h->stream);
   if (h->prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN || h->prm.smoother == STOKES_SMOOTHER_SCHUR_UZAWA) {
     sv::launch_bs_sweep<float>(L.d, h->bs, static_cast<float*>(h->bs_buf), L.rf, x, b, xo, h->stream);
-  } else if (L.tcB != nullptr && L.tc_hi >= L.tc_lo) {
+  } else if (L.tcB != nullptr && L.tc_hi >= L.tc_lo && L.tc_on) {
     // interior tiles on the tensor cores, the ring of boundary tiles on the SIMT kernel
     sv::launch_vanka_tc(L.d, L.tcB, x, b, xo, h->prm.omega, L.tc_lo, L.tc_hi, h->dev_err, h->stream);
     sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, sv::VANKA_CFG_14, h->stream, L.tc_lo,
@@ -517,9 +517,13 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
     return e;
   }
   float best = 1e30f;
-  // candidates: the fused tile shapes, and in FP64 also the split sweep
-  const int ncand = (sizeof(R) == 8) ? sv::VANKA_CFG_SPLIT2 + 1 : sv::VANKA_NCFG;
+  // candidates: the fused tile shapes; in FP64 also the split sweep; in the BF16
+  // form (tensor-core image present) also the tensor-core sweep with its ring
+  const bool tc = (sizeof(R) == 4) && L.tcB != nullptr && L.tc_hi >= L.tc_lo;
+  const int ncand = (sizeof(R) == 8) ? sv::VANKA_CFG_SPLIT2 + 1 : sv::VANKA_NCFG + (tc ? 1 : 0);
+  int best_c = 0;
   for (int c = 0; c < ncand; ++c) {
+    if (tc && c == sv::VANKA_CFG_14) continue;   // where the tensor-core tile fits, 14x14 means tensor cores
     auto run = [&]() {
       if constexpr (sizeof(R) == 8) {
         if (c >= sv::VANKA_CFG_SPLIT)
@@ -527,7 +531,13 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
         else
           sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, c, s);
       } else {
-        sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, c, s);
+        if (c == sv::VANKA_NCFG) {
+          sv::launch_vanka_tc(L.d, L.tcB, x, b, xo, h->prm.omega, L.tc_lo, L.tc_hi, h->dev_err, s);
+          sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, sv::VANKA_CFG_14, s, L.tc_lo,
+                                  L.tc_hi);
+        } else {
+          sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, c, s);
+        }
       }
     };
     run();
@@ -539,8 +549,14 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best) {
       best = ms;
-      *cfg = c;
+      best_c = c;
     }
+  }
+  if (tc) {   // tensor cores, or the fastest SIMT shape
+    L.tc_on = (best_c == sv::VANKA_NCFG);
+    *cfg = L.tc_on ? sv::VANKA_CFG_14 : best_c;
+  } else {
+    *cfg = best_c;
   }
   (void)cd;
   cudaEventDestroy(e0);
@@ -556,13 +572,13 @@ cudaError_t choose_tiles(stokes_hierarchy* h) {
       continue;
     }
     L.vk_cfg = L.vk_cfg_f = (L.d.n < 64) ? 0 : 1;
-    if (L.d.n < 64) continue;
+    const bool tc_level = h->prm.prec == STOKES_MIXED_BF16 && L.tcB != nullptr && L.tc_hi >= L.tc_lo;
+    if (L.d.n < 64 && !tc_level) continue;
     // only the precision the V-cycle runs in is tuned (the FP64 sweep of a
     // mixed hierarchy serves stokes_vanka_sweep alone and keeps 16x8)
     cudaError_t e = cudaSuccess;
     if (h->prm.prec == STOKES_FP64) e = tune_level<double>(h, L, &L.vk_cfg);
-    else if (L.tcB != nullptr && L.tc_hi >= L.tc_lo) L.vk_cfg_f = sv::VANKA_CFG_14;
-    else e = tune_level<float>(h, L, &L.vk_cfg_f);
+    else e = tune_level<float>(h, L, &L.vk_cfg_f);   // BF16: tensor cores vs SIMT shapes
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

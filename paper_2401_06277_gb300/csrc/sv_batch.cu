@@ -165,6 +165,7 @@ stokes_status stokes_batch_create(int nprob, const int* n, double viscosity, con
       for (size_t l = 0; l < ref->lv.size(); ++l) {
         b->hs[k]->lv[l].vk_cfg = ref->lv[l].vk_cfg;
         b->hs[k]->lv[l].vk_cfg_f = ref->lv[l].vk_cfg_f;
+        b->hs[k]->lv[l].tc_on = ref->lv[l].tc_on;
       }
     }
   }

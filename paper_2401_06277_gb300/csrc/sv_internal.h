@@ -94,6 +94,7 @@ struct Level {
   int vk_cfg_f = 0;       // tile shape of the FP32 sweep on this level
   // tensor-core sweep (prec == STOKES_MIXED_BF16): interior tile range, BF16 inverse image
   int tc_lo = 1, tc_hi = 0;
+  bool tc_on = true;      // the autotuner may prefer the SIMT sweep on small levels
   void* tcB = nullptr;
   // simple Vanka (smoother == STOKES_SMOOTHER_PER_PATCH): per-patch inverses, entry-major
   double* pinv = nullptr;

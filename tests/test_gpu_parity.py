@@ -340,15 +340,18 @@ def test_mixed_fgmres_solution(pkg, n):
 # ---------------------------------------------------------------------------
 # BF16 tensor-core form (interior patch solves as tcgen05 GEMMs, FP32 vectors)
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("tile", [3, -1])
 @pytest.mark.parametrize("n", [32, 64, 128])
-def test_bf16_vcycle_close_to_fp64(pkg, n):
+def test_bf16_vcycle_close_to_fp64(pkg, n, tile):
     """BF16 patch GEMMs: the V-cycle agrees with the FP64 oracle's to BF16 rounding.
+    tile 3 forces the tensor-core sweep on every level where it fits; -1 lets the
+    autotuner choose between it and the SIMT shapes per level.
 
     Bar 1e-2 relative to max |z|: BF16 keeps 8 significant bits (unit roundoff
     2^-9 = 2e-3) in both the gathered residuals and the patch inverse, the
     products are accumulated in FP32."""
     from paper_2401_06277_gb300 import stokes
-    H = gpu_h(pkg, n, prec=stokes.STOKES_MIXED_BF16)
+    H = gpu_h(pkg, n, prec=stokes.STOKES_MIXED_BF16, tile=tile)
     Ho = oracle_h(n)
     lv = Ho.levels[-1]
     b = O.assemble_rhs(lv, si.random_force(n, 21), si.manufactured_velocity(n))
@@ -356,12 +359,13 @@ def test_bf16_vcycle_close_to_fp64(pkg, n):
     assert err <= 1e-2, err
 
 
+@pytest.mark.parametrize("tile", [3, -1])
 @pytest.mark.parametrize("n", [64, 128])
-def test_bf16_fgmres_solution(pkg, n):
+def test_bf16_fgmres_solution(pkg, n, tile):
     """FGMRES (FP64) with the BF16 tensor-core preconditioner: same 1e-8 residual,
     solution within 1e-7 of the FP64 oracle's at the same tolerance."""
     from paper_2401_06277_gb300 import stokes
-    H = gpu_h(pkg, n, prec=stokes.STOKES_MIXED_BF16)
+    H = gpu_h(pkg, n, prec=stokes.STOKES_MIXED_BF16, tile=tile)
     Ho = oracle_h(n)
     lv = Ho.levels[-1]
     b = O.assemble_rhs(lv, si.random_force(n, 41), si.manufactured_velocity(n))
@@ -376,9 +380,11 @@ def test_bf16_fgmres_solution(pkg, n):
 
 
 def test_bf16_uses_the_tensor_core_kernel(pkg):
-    """At 128^2 the finest level has interior tiles: the ring runs the 14x14 SIMT tile."""
+    """With tile 3 the finest 128^2 level sweeps its interior tiles on the tensor cores
+    and the ring on the 14x14 SIMT tile; the kernel launch counter grows by two per
+    finest-level sweep (tensor-core kernel + ring)."""
     from paper_2401_06277_gb300 import stokes
-    H = gpu_h(pkg, 128, prec=stokes.STOKES_MIXED_BF16)
+    H = gpu_h(pkg, 128, prec=stokes.STOKES_MIXED_BF16, tile=3)
     assert stokes.stokes_level_tile(H.handle, H.levels - 1) == 3
 
 
@@ -462,13 +468,15 @@ def test_batch_uneven_sizes_match_single_solves(pkg, prec):
     """A batch of problems of different sizes gives, problem by problem, the single-solve result."""
     from paper_2401_06277_gb300 import stokes
     ns = [16, 64, 32, 64] if prec == 0 else [32, 128, 64]
-    B = pkg.Batch(ns, prec=prec)
+    # BF16: tensor-core and SIMT sweeps round differently, so both sides fix the configuration
+    kw = {"tile": 3} if prec == 2 else {}
+    B = pkg.Batch(ns, prec=prec, **kw)
     rhs, refs = [], []
     for k, n in enumerate(ns):
         f = dev(si.random_force(n, 500 + k))
         ud = dev(si.manufactured_velocity(n))
         rhs.append(B.assemble_rhs(k, f, ud))
-        H = gpu_h(pkg, n, prec=prec)
+        H = gpu_h(pkg, n, prec=prec, **kw)
         x, it, rr = H.solve(H.assemble_rhs(f, ud))
         refs.append((host(x), it))
     xs, its, rels = B.solve(rhs)
