@@ -78,10 +78,11 @@ typedef struct {
   stokes_precision prec;  /*                                          (FP64) */
   int tile;         /* Vanka sweep configuration: -1 = chosen per level by
                        timing at creation; fused tiles of 0 = 8x8, 1 = 16x8,
-                       2 = 16x16, 3 = 14x14 vertices; FP64 only: 4 = split
-                       sweep (16x16 own-patch solves writing the corrections,
-                       then a separate update), 5 = the same compiled for two
-                       CTAs per SM                                     (-1) */
+                       2 = 16x16, 3 = 14x14 vertices (BF16 form: 3 = the
+                       tensor-core sweep where it fits); 4 = split sweep
+                       (16x16 own-patch solves writing the corrections, then a
+                       separate update), 5 = the same compiled for two CTAs
+                       per SM                                          (-1) */
   int smoother;     /* stokes_smoother below                             (0)  */
   /* Braess-Sarazin / Schur-Uzawa relaxation (smoothers 2, 3; Sections 3.1, 3.3): D =
    * diag(L) scaled by bs_t, S = -(1/bs_t) B D^-1 B^T relaxed by bs_jacobi_iters

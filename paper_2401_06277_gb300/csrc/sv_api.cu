@@ -73,6 +73,8 @@ void free_all(stokes_hierarchy* h) {
   }
   cudaFree(h->delta);
   h->delta = nullptr;
+  cudaFree(h->deltaf);
+  h->deltaf = nullptr;
   cudaFree(h->bs_buf);
   h->bs_buf = nullptr;
   cudaFree(h->bt_GL);
@@ -136,7 +138,7 @@ void sweep_f64(stokes_hierarchy* h, sv::Level& L, const double* x, const double*
   else if (h->prm.smoother == STOKES_SMOOTHER_PER_PATCH)
     sv::launch_simple_sweep(L.d, L.pinv, h->delta, L.r, x, b, xo, h->prm.omega, h->stream);
   else if (L.vk_cfg >= sv::VANKA_CFG_SPLIT)
-    sv::launch_vanka_split(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, h->delta, L.vk_cfg == sv::VANKA_CFG_SPLIT2,
+    sv::launch_vanka_split<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, h->delta, L.vk_cfg == sv::VANKA_CFG_SPLIT2,
                            h->stream);
   else
     sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, L.vk_cfg, h->stream);
@@ -163,6 +165,9 @@ void timed_sweep<float>(stokes_hierarchy* h, bool finest, sv::Level& L, const fl
     sv::launch_vanka_tc(L.d, L.tcB, x, b, xo, h->prm.omega, L.tc_lo, L.tc_hi, h->dev_err, h->stream);
     sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, sv::VANKA_CFG_14, h->stream, L.tc_lo,
                             L.tc_hi);
+  } else if (L.vk_cfg_f >= sv::VANKA_CFG_SPLIT) {
+    sv::launch_vanka_split<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, h->deltaf,
+                                  L.vk_cfg_f == sv::VANKA_CFG_SPLIT2, h->stream);
   } else {
     sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, L.vk_cfg_f, h->stream);
   }
@@ -520,21 +525,26 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
   // candidates: the fused tile shapes; in FP64 also the split sweep; in the BF16
   // form (tensor-core image present) also the tensor-core sweep with its ring
   const bool tc = (sizeof(R) == 4) && L.tcB != nullptr && L.tc_hi >= L.tc_lo;
-  const int ncand = (sizeof(R) == 8) ? sv::VANKA_CFG_SPLIT2 + 1 : sv::VANKA_NCFG + (tc ? 1 : 0);
+  constexpr int CAND_TC = sv::VANKA_CFG_SPLIT2 + 1;   // the tensor-core sweep (BF16 form), tuning index only
+  const int ncand = tc ? CAND_TC + 1 : sv::VANKA_CFG_SPLIT2 + 1;
   int best_c = 0;
   for (int c = 0; c < ncand; ++c) {
     if (tc && c == sv::VANKA_CFG_14) continue;   // where the tensor-core tile fits, 14x14 means tensor cores
     auto run = [&]() {
       if constexpr (sizeof(R) == 8) {
         if (c >= sv::VANKA_CFG_SPLIT)
-          sv::launch_vanka_split(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, h->delta, c == sv::VANKA_CFG_SPLIT2, s);
+          sv::launch_vanka_split<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, h->delta,
+                                         c == sv::VANKA_CFG_SPLIT2, s);
         else
           sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, c, s);
       } else {
-        if (c == sv::VANKA_NCFG) {
+        if (c == CAND_TC) {
           sv::launch_vanka_tc(L.d, L.tcB, x, b, xo, h->prm.omega, L.tc_lo, L.tc_hi, h->dev_err, s);
           sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, sv::VANKA_CFG_14, s, L.tc_lo,
                                   L.tc_hi);
+        } else if (c >= sv::VANKA_CFG_SPLIT) {
+          sv::launch_vanka_split<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, h->deltaf,
+                                        c == sv::VANKA_CFG_SPLIT2, s);
         } else {
           sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, c, s);
         }
@@ -552,8 +562,8 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
       best_c = c;
     }
   }
-  if (tc) {   // tensor cores, or the fastest SIMT shape
-    L.tc_on = (best_c == sv::VANKA_NCFG);
+  if (tc) {   // tensor cores, or the fastest SIMT configuration
+    L.tc_on = (best_c == CAND_TC);
     *cfg = L.tc_on ? sv::VANKA_CFG_14 : best_c;
   } else {
     *cfg = best_c;
@@ -569,6 +579,7 @@ cudaError_t choose_tiles(stokes_hierarchy* h) {
   for (sv::Level& L : h->lv) {
     if (h->prm.tile >= 0 || h->prm.smoother != STOKES_SMOOTHER_SHARED || h->prm.precond == 1) {
       L.vk_cfg = L.vk_cfg_f = h->prm.tile >= 0 ? h->prm.tile : 1;   // no tiled sweep runs with per-patch inverses
+      L.tc_on = (h->prm.tile == sv::VANKA_CFG_14 || h->prm.tile < 0);
       continue;
     }
     L.vk_cfg = L.vk_cfg_f = (L.d.n < 64) ? 0 : 1;
@@ -634,8 +645,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   if (prm.prec != STOKES_FP64 && prm.prec != STOKES_MIXED_FP32 && prm.prec != STOKES_MIXED_BF16)
     return fail(STOKES_ERR_ARG, "unknown precision mode");
   if (prm.tile < -1 || prm.tile > sv::VANKA_CFG_SPLIT2) return fail(STOKES_ERR_ARG, "tile must be -1..5");
-  if (prm.tile >= sv::VANKA_CFG_SPLIT && prm.prec != STOKES_FP64)
-    return fail(STOKES_ERR_ARG, "tiles 4 and 5 (split sweep) are FP64 only");
+
   if (prm.cycle < 1 || prm.cycle > 2) return fail(STOKES_ERR_ARG, "cycle must be 1 (V) or 2 (W)");
   if (prm.precond < 0 || prm.precond > 1) return fail(STOKES_ERR_ARG, "precond must be 0 or 1");
   if (prm.precond == 1 && (prm.prec != STOKES_FP64 || prm.bt_cycles < 1 || prm.bt_nu < 0 ||
@@ -718,9 +728,11 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
         e = cudaGetLastError();
       }
     }
-    // patch corrections of the per-patch-inverse and the split FP64 sweeps (finest-level size)
+    // patch corrections of the per-patch-inverse and the split sweeps (finest-level size)
     if (e == cudaSuccess && prm.prec == STOKES_FP64 && k + 1 == sizes.size())
       e = dalloc(&h->delta, sv::patch_delta_doubles(L.d));
+    if (e == cudaSuccess && prm.prec != STOKES_FP64 && k + 1 == sizes.size())
+      e = dalloc(&h->deltaf, sv::patch_delta_doubles(L.d));
     if (e == cudaSuccess && (prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN ||
                              prm.smoother == STOKES_SMOOTHER_SCHUR_UZAWA) && k + 1 == sizes.size()) {
       const size_t el = sv::bs_scratch_elems(L.d) * (prm.prec == STOKES_FP64 ? sizeof(double) : sizeof(float));

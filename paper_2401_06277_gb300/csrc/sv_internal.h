@@ -123,6 +123,7 @@ struct stokes_hierarchy {
   int npart = 0;                 // blocks of the dot kernels
   unsigned* ticket = nullptr;    // last-block counter of the fused Gram-Schmidt kernels
   double* delta = nullptr;       // patch corrections of the simple-Vanka sweep (finest-level size)
+  float* deltaf = nullptr;       // the same for the FP32 split sweep of the mixed forms
   void* bs_buf = nullptr;        // Braess-Sarazin scratch in the V-cycle precision (finest-level size)
   // block-triangular preconditioner: dense inverses of the coarsest L and M, 3 finest vectors
   double* bt_GL = nullptr;
@@ -240,12 +241,13 @@ void launch_patch_inverse(const LevelDev& L, double* inv, cudaStream_t s);
 // be nullptr (zero guess); rscratch (level size) receives b - A x; delta
 // (patch_delta_doubles) the corrections
 // x_out = x + sum over patches of (omega / m_j) delta (entry-major corrections, stride P)
-void launch_patch_update(const LevelDev& L, int P, const double* delta, const double* x, double* xo, double omega,
-                         cudaStream_t s);
+template <typename T>
+void launch_patch_update(const LevelDev& L, int P, const T* delta, const T* x, T* xo, double omega, cudaStream_t s);
 // FP64 sweep in two kernels: own-patch solves (16 x 16 tiles, no halo patches)
 // writing delta (patch_delta_doubles), then launch_patch_update
-void launch_vanka_split(const LevelDev& L, const double* cd, const FastDiag& fd, const double* x, const double* b,
-                        double* xo, double omega, double* delta, int two_per_sm, cudaStream_t s);
+template <typename R>
+void launch_vanka_split(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
+                        double omega, R* delta, int two_per_sm, cudaStream_t s);
 void launch_simple_sweep(const LevelDev& L, const double* inv, double* delta, double* rscratch, const double* x,
                          const double* b, double* xo, double omega, cudaStream_t s);
 

@@ -124,40 +124,40 @@ __global__ void __launch_bounds__(128) k_patch_solve(LevelDev L, int P, const do
 // One thread per vertex (a, b): Q2 nodes (2a + PI, 2b + PJ) of both components
 // and p(a, b).  A node 2a + PI lies in the windows of patches a - 1 .. a + 1
 // (PI = 0) or a .. a + 1 (PI = 1) on each axis, where they exist.
-template <int PI, int PJ>
-__device__ __forceinline__ void update_node(const LevelDev& L, int P, const double* __restrict__ delta,
-                                            const double* __restrict__ x, double* __restrict__ xo, double omega,
-                                            int a, int b) {
+template <typename T, int PI, int PJ>
+__device__ __forceinline__ void update_node(const LevelDev& L, int P, const T* __restrict__ delta,
+                                            const T* __restrict__ x, T* __restrict__ xo, T omega, int a, int b) {
   const int I = 2 * a + PI, J = 2 * b + PJ, nq = L.nq, n = L.n, np = L.np;
   if (I >= nq || J >= nq) return;
   const int pil = max(0, a - (PI ? 0 : 1)), pih = min(n, a + 1);
   const int pjl = max(0, b - (PJ ? 0 : 1)), pjh = min(n, b + 1);
-  const double w = omega * vk::inv_mult<double>((pih - pil + 1) * (pjh - pjl + 1));
+  const T w = omega * vk::inv_mult<T>((pih - pil + 1) * (pjh - pjl + 1));
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
-    double acc = 0.0;
+    T acc = T(0);
     for (int pj = pjl; pj <= pjh; ++pj)
       for (int pi = pil; pi <= pih; ++pi) {
         const int slot = c * 25 + (J - 2 * pj + 2) * 5 + (I - 2 * pi + 2);
         acc += delta[static_cast<long long>(slot) * P + pj * np + pi];
       }
     const long long k = c * L.nv + static_cast<long long>(J) * nq + I;
-    xo[k] = fma(w, acc, x != nullptr ? x[k] : 0.0);
+    xo[k] = fma(w, acc, x != nullptr ? x[k] : T(0));
   }
 }
 
-__global__ void k_patch_update(LevelDev L, int P, const double* __restrict__ delta, const double* __restrict__ x,
-                               double* __restrict__ xo, double omega) {
+template <typename T>
+__global__ void k_patch_update(LevelDev L, int P, const T* __restrict__ delta, const T* __restrict__ x,
+                               T* __restrict__ xo, T omega) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y * blockDim.y + threadIdx.y;
   if (a > L.n || b > L.n) return;
-  update_node<0, 0>(L, P, delta, x, xo, omega, a, b);
-  update_node<1, 0>(L, P, delta, x, xo, omega, a, b);
-  update_node<0, 1>(L, P, delta, x, xo, omega, a, b);
-  update_node<1, 1>(L, P, delta, x, xo, omega, a, b);
+  update_node<T, 0, 0>(L, P, delta, x, xo, omega, a, b);
+  update_node<T, 1, 0>(L, P, delta, x, xo, omega, a, b);
+  update_node<T, 0, 1>(L, P, delta, x, xo, omega, a, b);
+  update_node<T, 1, 1>(L, P, delta, x, xo, omega, a, b);
   const int p = b * L.np + a;
   const long long k = 2 * L.nv + p;
-  xo[k] = fma(omega, delta[static_cast<long long>(NS - 1) * P + p], x != nullptr ? x[k] : 0.0);
+  xo[k] = fma(omega, delta[static_cast<long long>(NS - 1) * P + p], x != nullptr ? x[k] : T(0));
 }
 
 }  // namespace
@@ -183,12 +183,16 @@ void launch_patch_inverse(const LevelDev& L, double* inv, cudaStream_t s) {
       L, patch_stride(L), inv);
 }
 
-void launch_patch_update(const LevelDev& L, int P, const double* delta, const double* x, double* xo, double omega,
-                         cudaStream_t s) {
+template <typename T>
+void launch_patch_update(const LevelDev& L, int P, const T* delta, const T* x, T* xo, double omega, cudaStream_t s) {
   count_launches(1);
   dim3 blk(32, 8);
-  k_patch_update<<<dim3((L.np + 31) / 32, (L.np + 7) / 8), blk, 0, s>>>(L, P, delta, x, xo, omega);
+  k_patch_update<T><<<dim3((L.np + 31) / 32, (L.np + 7) / 8), blk, 0, s>>>(L, P, delta, x, xo, T(omega));
 }
+template void launch_patch_update<double>(const LevelDev&, int, const double*, const double*, double*, double,
+                                          cudaStream_t);
+template void launch_patch_update<float>(const LevelDev&, int, const float*, const float*, float*, double,
+                                         cudaStream_t);
 
 void launch_simple_sweep(const LevelDev& L, const double* inv, double* delta, double* rscratch, const double* x,
                          const double* b, double* xo, double omega, cudaStream_t s) {

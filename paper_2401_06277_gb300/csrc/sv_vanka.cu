@@ -568,6 +568,12 @@ cudaError_t vanka_prepare() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_vanka_own<double, 16, 16, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              smem_own);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_vanka_own<float, 16, 16, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_own / 2);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_vanka_own<float, 16, 16, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_own / 2);
   if (e == cudaSuccess) e = prepare_all<double>();
   if (e != cudaSuccess) return e;
   return prepare_all<float>();
@@ -586,18 +592,23 @@ void launch_vanka(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const 
   }
 }
 
-void launch_vanka_split(const LevelDev& L, const double* cd, const FastDiag& fd, const double* x, const double* b,
-                        double* xo, double omega, double* delta, int two_per_sm, cudaStream_t s) {
+template <typename R>
+void launch_vanka_split(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
+                        double omega, R* delta, int two_per_sm, cudaStream_t s) {
   count_launches(1);
   const int P = patch_stride(L);
   dim3 grid((L.np + 15) / 16, (L.np + 15) / 16);
-  constexpr size_t smem = (VO<16, 16>::TOTAL + EDGE_TAB) * sizeof(double);
+  constexpr size_t smem = (VO<16, 16>::TOTAL + EDGE_TAB) * sizeof(R);
   if (two_per_sm)
-    k_vanka_own<double, 16, 16, 256, 2><<<grid, 256, smem, s>>>(L, cd, fd, x, b, delta, P);
+    k_vanka_own<R, 16, 16, 256, 2><<<grid, 256, smem, s>>>(L, cd, fd, x, b, delta, P);
   else
-    k_vanka_own<double, 16, 16, 256, 1><<<grid, 256, smem, s>>>(L, cd, fd, x, b, delta, P);
-  launch_patch_update(L, P, delta, x, xo, omega, s);
+    k_vanka_own<R, 16, 16, 256, 1><<<grid, 256, smem, s>>>(L, cd, fd, x, b, delta, P);
+  launch_patch_update<R>(L, P, delta, x, xo, omega, s);
 }
+template void launch_vanka_split<double>(const LevelDev&, const double*, const FastDiag&, const double*,
+                                         const double*, double*, double, double*, int, cudaStream_t);
+template void launch_vanka_split<float>(const LevelDev&, const float*, const FastDiagT<float>&, const float*,
+                                        const float*, float*, double, float*, int, cudaStream_t);
 
 template void launch_vanka<double>(const LevelDev&, const double*, const FastDiagT<double>&, const double*,
                                    const double*, double*, double, int, cudaStream_t, int, int);

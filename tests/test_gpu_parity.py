@@ -299,15 +299,17 @@ def mixed_h(pkg, n, **kw):
     return gpu_h(pkg, n, prec=stokes.STOKES_MIXED_FP32, **kw)
 
 
+@pytest.mark.parametrize("tile", [-1, 4, 5])
 @pytest.mark.parametrize("n", [8, 32, 64])
-def test_mixed_vcycle_close_to_fp64(pkg, n):
+def test_mixed_vcycle_close_to_fp64(pkg, n, tile):
     """The FP32 V-cycle agrees with the FP64 oracle's V-cycle to FP32 rounding.
 
     Bar 1e-4 relative to max |z|: FP32 unit roundoff (6e-8) amplified by the
     cancellation in b - A x after the pre-sweeps (|A x| / |r| up to ~1e2) and
     compounded over up to five levels.  The mixed form is held to the
-    solution bar (1e-7 after FP64 FGMRES to 1e-8), tested below."""
-    H = mixed_h(pkg, n)
+    solution bar (1e-7 after FP64 FGMRES to 1e-8), tested below.  tile -1: tuned;
+    4 / 5: the split FP32 sweep on every level."""
+    H = mixed_h(pkg, n, tile=tile)
     Ho = oracle_h(n)
     lv = Ho.levels[-1]
     b = O.assemble_rhs(lv, si.random_force(n, 21), si.manufactured_velocity(n))
@@ -316,11 +318,12 @@ def test_mixed_vcycle_close_to_fp64(pkg, n):
     assert err <= 1e-4, err
 
 
+@pytest.mark.parametrize("tile", [-1, 5])
 @pytest.mark.parametrize("n", [16, 64])
-def test_mixed_fgmres_solution(pkg, n):
+def test_mixed_fgmres_solution(pkg, n, tile):
     """FGMRES (FP64) with the FP32 preconditioner reaches the same 1e-8 residual; the
     solution is within 1e-7 of the FP64 oracle's solution at the same tolerance."""
-    H = mixed_h(pkg, n)
+    H = mixed_h(pkg, n, tile=tile)
     Ho = oracle_h(n)
     lv = Ho.levels[-1]
     b = O.assemble_rhs(lv, si.random_force(n, 31), si.manufactured_velocity(n))
