@@ -51,6 +51,8 @@ sv::LevelDev make_level(int n, double nu) {
   d.nu = nu;
   d.cl = nu / 90.0;
   d.cb = -d.h / 18.0;
+  d.clf = static_cast<float>(d.cl);
+  d.cbf = static_cast<float>(d.cb);
   return d;
 }
 

@@ -29,6 +29,13 @@ namespace {
 
 __device__ __forceinline__ bool bs_free(int I, int J, int nq) { return I > 0 && J > 0 && I < nq - 1 && J < nq - 1; }
 
+// Level constants in the element type, formed once on the host (no FP64
+// arithmetic in the FP32 kernels): B weight, 1 / (nu/90), 1/t, Jacobi weight, omega.
+template <typename T>
+struct BSC {
+  T cb, icl, inv_t, wj, om;
+};
+
 // diag(L) / (nu/90) at a free node of parities (PI, PJ)
 __host__ __device__ constexpr double dcoef(int PI, int PJ) { return k1(PI, 0) * m1(PJ, 0) + m1(PI, 0) * k1(PJ, 0); }
 
@@ -36,10 +43,10 @@ __host__ __device__ constexpr double dcoef(int PI, int PJ) { return k1(PI, 0) * 
 // (a, b); taps at Q2 nodes (2a + dI, 2b + dJ), parities (dI & 1, dJ & 1).
 template <typename T, bool MASK>
 __device__ __forceinline__ void bs_rhs_vertex(const LevelDev& L, const T* __restrict__ r, T* __restrict__ g,
-                                              T* __restrict__ ds, T* __restrict__ dp, T inv_t, T wj, int a, int b) {
+                                              T* __restrict__ ds, T* __restrict__ dp, BSC<T> k, int a, int b) {
   const int nq = L.nq;
   const long long nv = L.nv;
-  const T cb = T(L.cb), icl = T(1.0 / L.cl);
+  const T cb = k.cb, icl = k.icl, inv_t = k.inv_t, wj = k.wj;
   T s = T(0), d = T(0);
 #pragma unroll
   for (int dJ = -2; dJ <= 2; ++dJ)
@@ -65,14 +72,14 @@ __device__ __forceinline__ void bs_rhs_vertex(const LevelDev& L, const T* __rest
 
 template <typename T>
 __global__ void k_bs_rhs(LevelDev L, const T* __restrict__ r, T* __restrict__ g, T* __restrict__ ds,
-                         T* __restrict__ dp, T inv_t, T wj) {
+                         T* __restrict__ dp, BSC<T> k) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = L.n;
   if (a > n || b > n) return;
   if (a >= 2 && a <= n - 2 && b >= 2 && b <= n - 2)
-    bs_rhs_vertex<T, false>(L, r, g, ds, dp, inv_t, wj, a, b);
+    bs_rhs_vertex<T, false>(L, r, g, ds, dp, k, a, b);
   else
-    bs_rhs_vertex<T, true>(L, r, g, ds, dp, inv_t, wj, a, b);
+    bs_rhs_vertex<T, true>(L, r, g, ds, dp, k, a, b);
 }
 
 // (B^T p) / (cb) at node (2a + PI, 2b + PJ), component C, from the 3 x 3 pressures P around (a, b)
@@ -102,32 +109,35 @@ __device__ __forceinline__ void load_p3(const LevelDev& L, const T* __restrict__
 
 // q = D^-1 B^T dp on the velocity nodes of vertex (a, b) (0 on Dirichlet nodes)
 template <typename T, int PI, int PJ>
-__device__ __forceinline__ void dinv_btp_node(const LevelDev& L, const T (&P)[3][3], T* __restrict__ q, int a, int b) {
+__device__ __forceinline__ void dinv_btp_node(const LevelDev& L, const T (&P)[3][3], T* __restrict__ q, T cbicl,
+                                              int a, int b) {
   const int I = 2 * a + PI, J = 2 * b + PJ, nq = L.nq;
   if (I >= nq || J >= nq) return;
   const long long k = static_cast<long long>(J) * nq + I;
   const bool fr = bs_free(I, J, nq);
-  const T f = T(L.cb / (L.cl * dcoef(PI, PJ)));
+  const T f = cbicl * T(1.0 / dcoef(PI, PJ));
   q[k] = fr ? f * btp3<T, PI, PJ, 0>(P) : T(0);
   q[L.nv + k] = fr ? f * btp3<T, PI, PJ, 1>(P) : T(0);
 }
 
 template <typename T>
-__global__ void k_bs_dinv_btp(LevelDev L, const T* __restrict__ dp, T* __restrict__ q) {
+__global__ void k_bs_dinv_btp(LevelDev L, const T* __restrict__ dp, T* __restrict__ q, BSC<T> k) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
   if (a > L.n || b > L.n) return;
   T P[3][3];
   load_p3(L, dp, a, b, P);
-  dinv_btp_node<T, 0, 0>(L, P, q, a, b);
-  dinv_btp_node<T, 1, 0>(L, P, q, a, b);
-  dinv_btp_node<T, 0, 1>(L, P, q, a, b);
-  dinv_btp_node<T, 1, 1>(L, P, q, a, b);
+  const T cbicl = k.cb * k.icl;
+  dinv_btp_node<T, 0, 0>(L, P, q, cbicl, a, b);
+  dinv_btp_node<T, 1, 0>(L, P, q, cbicl, a, b);
+  dinv_btp_node<T, 0, 1>(L, P, q, cbicl, a, b);
+  dinv_btp_node<T, 1, 1>(L, P, q, cbicl, a, b);
 }
 
 // dp += w_J (g - S dp) / diag(S),  S dp = -(1/t) B q
 template <typename T>
 __global__ void k_bs_jacobi(LevelDev L, const T* __restrict__ q, const T* __restrict__ g, const T* __restrict__ ds,
-                            T* __restrict__ dp, T inv_t, T wj) {
+                            T* __restrict__ dp, BSC<T> kc) {
+  const T inv_t = kc.inv_t, wj = kc.wj;
   const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = L.n, nq = L.nq;
   if (a > n || b > n) return;
@@ -146,7 +156,7 @@ __global__ void k_bs_jacobi(LevelDev L, const T* __restrict__ q, const T* __rest
       if (wy != 0.0) s = fma(T(wy), q[nv + k], s);
     }
   const int p = b * L.np + a;
-  const T sdp = -inv_t * T(L.cb) * s;
+  const T sdp = -inv_t * kc.cb * s;
   dp[p] = fma(wj, (g[p] - sdp) / ds[p], dp[p]);
 }
 
@@ -154,13 +164,14 @@ __global__ void k_bs_jacobi(LevelDev L, const T* __restrict__ q, const T* __rest
 // x_out = x + omega (du, dp)
 template <typename T, int PI, int PJ, bool UZ>
 __device__ __forceinline__ void bs_update_node(const LevelDev& L, const T (&P)[3][3], const T* __restrict__ r,
-                                               const T* __restrict__ x, T* __restrict__ xo, T inv_t, T om, int a,
-                                               int b) {
+                                               const T* __restrict__ x, T* __restrict__ xo, const BSC<T>& kc,
+                                               int a, int b) {
   const int I = 2 * a + PI, J = 2 * b + PJ, nq = L.nq;
   if (I >= nq || J >= nq) return;
   const long long k = static_cast<long long>(J) * nq + I;
   const bool fr = bs_free(I, J, nq);
-  const T cb = T(L.cb), sc = inv_t * T(1.0 / (L.cl * dcoef(PI, PJ)));
+  const T inv_t = kc.inv_t, om = kc.om, cb = kc.cb;
+  const T sc = inv_t * kc.icl * T(1.0 / dcoef(PI, PJ));
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
     const long long kc = c * L.nv + k;
@@ -181,17 +192,17 @@ __device__ __forceinline__ void bs_update_node(const LevelDev& L, const T (&P)[3
 
 template <typename T, bool UZ>
 __global__ void k_bs_update(LevelDev L, const T* __restrict__ r, const T* __restrict__ dp, const T* __restrict__ x,
-                            T* __restrict__ xo, T inv_t, T om) {
+                            T* __restrict__ xo, BSC<T> kc) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
   if (a > L.n || b > L.n) return;
   T P[3][3];
   load_p3(L, dp, a, b, P);
-  bs_update_node<T, 0, 0, UZ>(L, P, r, x, xo, inv_t, om, a, b);
-  bs_update_node<T, 1, 0, UZ>(L, P, r, x, xo, inv_t, om, a, b);
-  bs_update_node<T, 0, 1, UZ>(L, P, r, x, xo, inv_t, om, a, b);
-  bs_update_node<T, 1, 1, UZ>(L, P, r, x, xo, inv_t, om, a, b);
+  bs_update_node<T, 0, 0, UZ>(L, P, r, x, xo, kc, a, b);
+  bs_update_node<T, 1, 0, UZ>(L, P, r, x, xo, kc, a, b);
+  bs_update_node<T, 0, 1, UZ>(L, P, r, x, xo, kc, a, b);
+  bs_update_node<T, 1, 1, UZ>(L, P, r, x, xo, kc, a, b);
   const long long kp = 2 * L.nv + static_cast<long long>(b) * L.np + a;
-  xo[kp] = fma(om, P[1][1], x != nullptr ? x[kp] : T(0));
+  xo[kp] = fma(kc.om, P[1][1], x != nullptr ? x[kp] : T(0));
 }
 
 }  // namespace
@@ -213,18 +224,18 @@ void launch_bs_sweep(const LevelDev& L, const BSParams& prm, T* scratch, T* rbuf
     launch_apply<T>(L, x, b, rbuf, 1, s);
     r = rbuf;
   }
-  const T inv_t = T(1.0 / prm.t), wj = T(prm.jacobi_weight), om = T(prm.omega);
+  const BSC<T> k{T(L.cb), T(1.0 / L.cl), T(1.0 / prm.t), T(prm.jacobi_weight), T(prm.omega)};
   dim3 blk(32, 8), grid((L.np + 31) / 32, (L.np + 7) / 8);
   count_launches(2 + 2 * (prm.jacobi_iters - 1));
-  k_bs_rhs<T><<<grid, blk, 0, s>>>(L, r, g, ds, dp, inv_t, wj);
+  k_bs_rhs<T><<<grid, blk, 0, s>>>(L, r, g, ds, dp, k);
   for (int it = 1; it < prm.jacobi_iters; ++it) {
-    k_bs_dinv_btp<T><<<grid, blk, 0, s>>>(L, dp, q);
-    k_bs_jacobi<T><<<grid, blk, 0, s>>>(L, q, g, ds, dp, inv_t, wj);
+    k_bs_dinv_btp<T><<<grid, blk, 0, s>>>(L, dp, q, k);
+    k_bs_jacobi<T><<<grid, blk, 0, s>>>(L, q, g, ds, dp, k);
   }
   if (prm.uzawa)
-    k_bs_update<T, true><<<grid, blk, 0, s>>>(L, r, dp, x, xo, inv_t, om);
+    k_bs_update<T, true><<<grid, blk, 0, s>>>(L, r, dp, x, xo, k);
   else
-    k_bs_update<T, false><<<grid, blk, 0, s>>>(L, r, dp, x, xo, inv_t, om);
+    k_bs_update<T, false><<<grid, blk, 0, s>>>(L, r, dp, x, xo, k);
 }
 
 template void launch_bs_sweep<double>(const LevelDev&, const BSParams&, double*, double*, const double*,

@@ -73,7 +73,22 @@ struct LevelDev {
   double nu;   // viscosity
   double cl;   // nu / 90: scale of the integer Laplacian stencil
   double cb;   // -h / 18: scale of the integer divergence stencil
+  float clf, cbf;   // the same in FP32 (formed on the host: FP32 kernels do no FP64 arithmetic)
 };
+
+// cl and cb in the element type
+template <typename T>
+__host__ __device__ inline T level_cl(const LevelDev& L);
+template <>
+__host__ __device__ inline double level_cl<double>(const LevelDev& L) { return L.cl; }
+template <>
+__host__ __device__ inline float level_cl<float>(const LevelDev& L) { return L.clf; }
+template <typename T>
+__host__ __device__ inline T level_cb(const LevelDev& L);
+template <>
+__host__ __device__ inline double level_cb<double>(const LevelDev& L) { return L.cb; }
+template <>
+__host__ __device__ inline float level_cb<float>(const LevelDev& L) { return L.cbf; }
 
 struct Level {
   LevelDev d;

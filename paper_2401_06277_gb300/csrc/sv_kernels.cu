@@ -38,7 +38,7 @@ __device__ __forceinline__ void apply_vertex(const LevelDev& L, const T* __restr
   const int nq = L.nq, np = L.np, n = L.n;
   const long long nv = L.nv;
   const int I0 = 2 * a, J0 = 2 * bb;
-  const T cl = T(L.cl), cb = T(L.cb);
+  const T cl = level_cl<T>(L), cb = level_cb<T>(L);
   const T* p = x + 2 * nv;
   T P[3][3];
 #pragma unroll

@@ -186,6 +186,8 @@ extern "C" stokes_status stokes_residual_norm_noalloc(int n, double viscosity, c
   L.nu = viscosity;
   L.cl = viscosity / 90.0;
   L.cb = -L.h / 18.0;
+  L.clf = static_cast<float>(L.cl);
+  L.cbf = static_cast<float>(L.cb);
   const int rows = L.nq + L.np;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   k_resnorm_rows<<<rows, 256, 0, s>>>(L, b, x, scratch);

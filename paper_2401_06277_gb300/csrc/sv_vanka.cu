@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
   __syncthreads();
 
   // 2. residual r = b - A x (skipped for a zero initial guess: r = b)
-  const R cl = R(L.cl), cb = R(L.cb);
+  const R cl = level_cl<R>(L), cb = level_cb<R>(L);
   if (x != nullptr) {
     for (int t = tid; t < T::CW * T::CH; t += NT) {
       const int cy = t / T::CW, cx = t - cy * T::CW;
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __r
   }
   __syncthreads();
 
-  const R cl = R(L.cl), cb = R(L.cb);
+  const R cl = level_cl<R>(L), cb = level_cb<R>(L);
   if (x != nullptr) {
     for (int t = tid; t < T::CW * T::CH; t += NT) {
       const int cy = t / T::CW, cx = t - cy * T::CW;

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
     srp[tid] = b[2 * nv + static_cast<long long>(j) * np + i];
   }
   __syncthreads();
-  const float cl = static_cast<float>(L.cl), cb = static_cast<float>(L.cb);
+  const float cl = L.clf, cb = L.cbf;
   if (x != nullptr) {
     for (int t = tid; t < TT::CW * TT::CH; t += TC_NT) {
       const int cy = t / TT::CW, cx = t - cy * TT::CW;
