@@ -630,7 +630,7 @@ def run_kernel(args) -> None:
 
     build.build()
     n = args.n
-    H = pkg.Hierarchy(n, restart=1, tile=args.tile, prec=PRECS[args.prec])
+    H = pkg.Hierarchy(n, restart=1, tile=args.tile, prec=PRECS[args.prec], smoother=args.smoother)
     lvl = H.levels - 1
     x = torch.from_numpy(si.random_vector(n, 1)).cuda()
     b = torch.from_numpy(si.random_vector(n, 2)).cuda()
@@ -686,6 +686,8 @@ def main():
     ap.add_argument("--tile", type=int, default=-1, help="Vanka sweep configuration (-1: autotuned; 0..3 fused 8x8/16x8/16x16/14x14, 4/5 split 16x16, FP64)")
     ap.add_argument("--kernel", choices=["sweep", "residual", "vcycle"], default=None,
                     help="time one kernel alone on the finest level (profiling mode)")
+    ap.add_argument("--smoother", type=int, choices=[0, 1, 2, 3], default=0,
+                    help="profiling mode: 0 shared-inverse Vanka, 1 simple Vanka, 2 Braess-Sarazin, 3 Schur-Uzawa")
     args = ap.parse_args()
     if args.kernel:
         run_kernel(args)

@@ -95,6 +95,14 @@ void free_all(stokes_hierarchy* h) {
   h->ticket = nullptr;
   cudaFree(h->aux);
   h->aux = nullptr;
+  if (h->ring_stream) {
+    cudaStreamSynchronize(h->ring_stream);
+    cudaStreamDestroy(h->ring_stream);
+  }
+  if (h->ring_fork) cudaEventDestroy(h->ring_fork);
+  if (h->ring_join) cudaEventDestroy(h->ring_join);
+  h->ring_stream = nullptr;
+  h->ring_fork = h->ring_join = nullptr;
   if (h->host_scalars) cudaFreeHost(h->host_scalars);
   h->coarse_G = h->V = h->Z = h->small = h->partials = h->host_scalars = nullptr;
 }
@@ -146,6 +154,20 @@ void sweep_f64(stokes_hierarchy* h, sv::Level& L, const double* x, const double*
     sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, L.vk_cfg, h->stream);
 }
 
+// BF16-form sweep of a level with tensor-core tiles: the interior tiles on the
+// tensor cores (stream s), the ring of boundary tiles on the SIMT kernel
+// (ring_stream), concurrently -- both read x and b and write disjoint owned
+// dofs of xo.  Fork and join are event waits, valid eagerly and under capture.
+void tc_sweep(stokes_hierarchy* h, sv::Level& L, const float* x, const float* b, float* xo, cudaStream_t s) {
+  cudaEventRecord(h->ring_fork, s);
+  cudaStreamWaitEvent(h->ring_stream, h->ring_fork, 0);
+  sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, sv::VANKA_CFG_14, h->ring_stream, L.tc_lo,
+                          L.tc_hi);
+  sv::launch_vanka_tc(L.d, L.tcB, x, b, xo, h->prm.omega, L.tc_lo, L.tc_hi, h->dev_err, s);
+  cudaEventRecord(h->ring_join, h->ring_stream);
+  cudaStreamWaitEvent(s, h->ring_join, 0);
+}
+
 template <>
 void timed_sweep<double>(stokes_hierarchy* h, bool finest, sv::Level& L, const double* x, const double* b,
                          double* xo) {
@@ -163,10 +185,7 @@ void timed_sweep<float>(stokes_hierarchy* h, bool finest, sv::Level& L, const fl
   if (h->prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN || h->prm.smoother == STOKES_SMOOTHER_SCHUR_UZAWA) {
     sv::launch_bs_sweep<float>(L.d, h->bs, static_cast<float*>(h->bs_buf), L.rf, x, b, xo, h->stream);
   } else if (L.tcB != nullptr && L.tc_hi >= L.tc_lo && L.tc_on) {
-    // interior tiles on the tensor cores, the ring of boundary tiles on the SIMT kernel
-    sv::launch_vanka_tc(L.d, L.tcB, x, b, xo, h->prm.omega, L.tc_lo, L.tc_hi, h->dev_err, h->stream);
-    sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, sv::VANKA_CFG_14, h->stream, L.tc_lo,
-                            L.tc_hi);
+    tc_sweep(h, L, x, b, xo, h->stream);
   } else if (L.vk_cfg_f >= sv::VANKA_CFG_SPLIT) {
     sv::launch_vanka_split<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, h->deltaf,
                                   L.vk_cfg_f == sv::VANKA_CFG_SPLIT2, h->stream);
@@ -431,12 +450,16 @@ void fg_iteration(stokes_hierarchy* h, int j) {
   sv::launch_apply<double>(F.d, zj, nullptr, w, 0, s);
   double* P = h->partials;
   const int np = h->npart;
-  // pass 1: h = V^T w and ||w||^2; w -= V h with the new ||w||^2 and the DGKS flag
+  // pass 1: h = V^T w and ||w||^2; w -= V h with the new ||w||^2 and the DGKS
+  // flag, fused (up to 16 basis vectors) with pass 2's dots h2 = V^T w
   sv::launch_orth_dots(V, ld, j + 1, w, N, P, np, h->ticket, sb.hcol, sb.sc + 3, nullptr, s);
-  sv::launch_orth_update(w, V, ld, j + 1, sb.hcol, N, P, np, h->ticket, sb.sc, nullptr, sb.sc + 3,
-                         sb.sc + 5, nullptr, s);
-  // pass 2, only where flagged: h2 = V^T w, w -= V h2, h += h2
-  sv::launch_orth_dots(V, ld, j + 1, w, N, P, np, h->ticket, sb.h2, nullptr, sb.sc + 5, s);
+  if (!sv::launch_orth_update_dots(w, V, ld, j + 1, sb.hcol, N, P, np, h->ticket, sb.h2, sb.sc, sb.sc + 3,
+                                   sb.sc + 5, s)) {
+    sv::launch_orth_update(w, V, ld, j + 1, sb.hcol, N, P, np, h->ticket, sb.sc, nullptr, sb.sc + 3,
+                           sb.sc + 5, nullptr, s);
+    sv::launch_orth_dots(V, ld, j + 1, w, N, P, np, h->ticket, sb.h2, nullptr, sb.sc + 5, s);
+  }
+  // pass 2, only where flagged: w -= V h2, h += h2
   sv::launch_orth_update(w, V, ld, j + 1, sb.h2, N, P, np, h->ticket, sb.sc, sb.sc + 5, nullptr, nullptr,
                          sb.hcol, s);
   sv::launch_scale(w, w, sb.sc + 1, 0.0, N, s);
@@ -541,9 +564,7 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
           sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, c, s);
       } else {
         if (c == CAND_TC) {
-          sv::launch_vanka_tc(L.d, L.tcB, x, b, xo, h->prm.omega, L.tc_lo, L.tc_hi, h->dev_err, s);
-          sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, sv::VANKA_CFG_14, s, L.tc_lo,
-                                  L.tc_hi);
+          tc_sweep(h, L, x, b, xo, s);
         } else if (c >= sv::VANKA_CFG_SPLIT) {
           sv::launch_vanka_split<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, h->deltaf,
                                         c == sv::VANKA_CFG_SPLIT2, s);
@@ -691,7 +712,13 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   cudaError_t e = sv::vanka_prepare();
   if (e == cudaSuccess) e = sv::simple_prepare();
   if (e == cudaSuccess && prm.prec == STOKES_MIXED_BF16) e = sv::vanka_tc_prepare();
+  if (e == cudaSuccess && prm.prec == STOKES_MIXED_BF16) {
+    e = cudaStreamCreateWithFlags(&h->ring_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ring_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ring_join, cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
+    free_all(h);
     delete h;
     return cuda_fail(e, "kernel attributes");
   }

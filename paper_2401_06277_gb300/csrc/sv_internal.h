@@ -148,6 +148,10 @@ struct stokes_hierarchy {
   sv::BSParams bs;
   double* host_scalars = nullptr;  // pinned host mirror of a few scalars
   int* dev_err = nullptr;          // set by kernels whose bounded waits expired
+  // BF16 form: the SIMT ring of boundary tiles runs on ring_stream while the
+  // tensor-core kernel sweeps the interior tiles on stream (fork / join events)
+  cudaStream_t ring_stream = nullptr;
+  cudaEvent_t ring_fork = nullptr, ring_join = nullptr;
   double* aux = nullptr;           // finest-level vector: the projected adjoint right-hand side
   // measurement
   bool timing = false;
@@ -282,6 +286,11 @@ void launch_orth_dots(const double* V, long long ld, int nk, const double* w, lo
 void launch_orth_update(double* w, const double* V, long long ld, int nk, const double* coef, long long N,
                         double* partials, int npart, unsigned* ticket, double* norm2, const double* gate,
                         const double* dgks_ref, double* flag, double* hacc, cudaStream_t s);
+// Pass 1's update and pass 2's dots in one launch (see k_orth_update_dots);
+// returns false, launching nothing, when nk is outside 1..16.
+bool launch_orth_update_dots(double* w, const double* V, long long ld, int nk, const double* coef, long long N,
+                             double* partials, int npart, unsigned* ticket, double* dots, double* norm2,
+                             const double* dgks_ref, double* flag, cudaStream_t s);
 // w += sign * sum_k coef[k] V_k
 void launch_multiaxpy(double* w, const double* V, long long ld, int nk, const double* coef,
                       double sign, long long N, cudaStream_t s);

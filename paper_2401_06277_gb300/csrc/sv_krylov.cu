@@ -189,6 +189,75 @@ __global__ void __launch_bounds__(DOT_NT) k_orth_update(double* __restrict__ w, 
   }
 }
 
+// Pass 1's update fused with pass 2's dots: w' = w - sum_{k<K} coef[k] V_k,
+// dots[k] = <V_k, w'>, norm2[0] = <w', w'>, norm2[1] = its square root, and
+// *flag = 1 if norm2[0] < dgks_ref / 2 (re-orthogonalise) else 0.  Each w'
+// element is formed in registers next to the V elements that it is dotted with,
+// so V is read once for both; the values equal those of the two passes run
+// apart.
+template <int K>
+__global__ void __launch_bounds__(DOT_NT) k_orth_update_dots(double* __restrict__ w, const double* __restrict__ V,
+                                                             long long ld, const double* __restrict__ coef,
+                                                             long long N, double* __restrict__ partials,
+                                                             int npart, unsigned* ticket,
+                                                             double* __restrict__ dots,
+                                                             double* __restrict__ norm2,
+                                                             const double* __restrict__ dgks_ref,
+                                                             double* __restrict__ flag) {
+  constexpr int NO = K + 1;
+  constexpr int U = orth_unroll<K>();
+  double c[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) c[k] = coef[k];
+  double acc[NO];
+#pragma unroll
+  for (int k = 0; k < NO; ++k) acc[k] = 0.0;
+  const long long stride = static_cast<long long>(gridDim.x) * DOT_NT;
+  long long i = blockIdx.x * static_cast<long long>(DOT_NT) + threadIdx.x;
+  for (; i + (U - 1) * stride < N; i += U * stride) {
+    double wv[U], vv[U][K];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      wv[u] = w[i + u * stride];
+#pragma unroll
+      for (int k = 0; k < K; ++k) vv[u][k] = V[k * ld + i + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      double x = wv[u];
+#pragma unroll
+      for (int k = 0; k < K; ++k) x = fma(-c[k], vv[u][k], x);
+      w[i + u * stride] = x;
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] = fma(vv[u][k], x, acc[k]);
+      acc[K] = fma(x, x, acc[K]);
+    }
+  }
+  for (; i < N; i += stride) {
+    double vk[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) vk[k] = V[k * ld + i];
+    double x = w[i];
+#pragma unroll
+    for (int k = 0; k < K; ++k) x = fma(-c[k], vk[k], x);
+    w[i] = x;
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = fma(vk[k], x, acc[k]);
+    acc[K] = fma(x, x, acc[K]);
+  }
+  if (!block_partials<NO>(acc, partials, npart, ticket)) return;
+  double tot[NO];
+  total_partials<NO>(partials, npart, tot);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) dots[k] = tot[k];
+    norm2[0] = tot[K];
+    norm2[1] = sqrt(tot[K]);
+    *flag = (tot[K] < 0.5 * *dgks_ref) ? 1.0 : 0.0;
+    *ticket = 0u;
+  }
+}
+
 // out[k] (+)= sum_b partials[k * npart + b]; one CTA per k
 __global__ void k_reduce(const double* __restrict__ partials, int npart, double* __restrict__ out,
                          int accumulate) {
@@ -356,6 +425,18 @@ void update_k(bool norm, double* w, const double* V, long long ld, const double*
                                                      dgks_ref, flag, hacc, coef_all, nacc);
 }
 
+template <int K>
+void update_dots_k(double* w, const double* V, long long ld, const double* coef, long long N, double* partials,
+                   int npart, unsigned* ticket, double* dots, double* norm2, const double* dgks_ref, double* flag,
+                   cudaStream_t s) {
+  if constexpr (K == 0) {
+    (void)w;   // never launched: the caller passes at least one vector
+  } else {
+    k_orth_update_dots<K><<<npart, DOT_NT, 0, s>>>(w, V, ld, coef, N, partials, npart, ticket, dots, norm2,
+                                                   dgks_ref, flag);
+  }
+}
+
 #define SV_ORTH_CASES(F, ...) \
   switch (kk) {                                    \
     case 0: F<0>(__VA_ARGS__); break;              \
@@ -404,6 +485,16 @@ void launch_orth_update(double* w, const double* V, long long ld, int nk, const 
                   ticket, norm2, gate, lastc ? dgks_ref : nullptr, flag, lastc ? hacc : nullptr, coef, nk, s)
     k0 += kk;
   } while (k0 < nk);
+}
+
+bool launch_orth_update_dots(double* w, const double* V, long long ld, int nk, const double* coef, long long N,
+                             double* partials, int npart, unsigned* ticket, double* dots, double* norm2,
+                             const double* dgks_ref, double* flag, cudaStream_t s) {
+  if (nk < 1 || nk > ORTH_KMAX) return false;   // one launch holds at most ORTH_KMAX vectors
+  const int kk = nk;
+  count_launches(1);
+  SV_ORTH_CASES(update_dots_k, w, V, ld, coef, N, partials, npart, ticket, dots, norm2, dgks_ref, flag, s)
+  return true;
 }
 
 #undef SV_ORTH_CASES
