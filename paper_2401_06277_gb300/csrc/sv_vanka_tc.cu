@@ -13,11 +13,17 @@
 //   1. warp 0 allocates 128 TMEM columns; thread 0 starts a bulk (TMA) copy of
 //      the 8 KB BF16 inverse, already in the UMMA core-matrix layout, into
 //      shared memory, completing on an mbarrier;
-//   2. x and b windows are loaded and the FP32 residual is computed with
-//      compile-time stencils (shared code with the SIMT sweep);
+//   2. the x and p windows are loaded; one thread per 2x2 cell of Q2 nodes
+//      reads b from global memory and forms the FP32 residual of its four
+//      nodes (compile-time stencils) and, from the same registers, the
+//      pressure residual of the cell's vertex;
 //   3. each thread writes its patch row of R, converted to BF16, into the
 //      K-major no-swizzle core-matrix layout (8 rows x 16 bytes per core
 //      matrix, LBO = 128 B along K, SBO = 1024 B along M);
+// The x and residual windows are stored column-parity split (the even nodes of
+// a row, then the odd ones) with row pitches for which the 16 cells or patches
+// of a half-warp row and the next row fall in disjoint banks, so the stencil
+// and patch-gather loads are free of bank conflicts.
 //   4. thread 0 issues 2 x 4 tcgen05.mma (kind::f16, M=128, N=64, K=16) into
 //      TMEM and commits them to an mbarrier;
 //   5. after the wait, each thread reads its patch row of D with tcgen05.ld and
@@ -41,13 +47,30 @@ namespace sv {
 namespace {
 
 using vk::inv_mult;
-using vk::res_cell;
 using vk::VT;
 using vk::vfree;
 
 constexpr int TC_NT = 256;
 using TT = VT<TC_TILE, TC_TILE>;
 static_assert(TT::NPATCH == TC_NT, "one thread per patch");
+static_assert(TC_TILE % 2 == 0 && TC_TILE / 2 <= TC_NT / 32 && 2 * TC_TILE <= 32, "update: two vertex rows per warp");
+
+// Windows (origins as in the SIMT sweep: x at Q2 node 2 i0 - 6, residual at
+// 2 i0 - 4, p at vertex i0 - 3).  A row of the x window holds its 20 even
+// nodes, then its 20 odd ones; a residual row its 18 even, then 18 odd nodes.
+// Pitches: the residual cells are taken row-major, 18 per row (item t = 18 cy
+// + cx), and x rows two apart (one cell row) are 2 XP = 82 = 18 (mod 32) words
+// apart, so the bank of every stencil load is t + const (mod 32): conflict-free
+// for any 32 consecutive cells; likewise p rows (pitch 50 = 18).  The patch
+// gather takes 16 patches per row, and residual rows two apart are 2 RP = 80 =
+// 16 (mod 32) words apart: two patch rows of a warp fall in disjoint banks.
+constexpr int XP = 41, XHALF = 20, XS = XP * TT::XH;       // x: 2 x 40 rows of 40 (+1 pad)
+constexpr int RP = 40, RHALF = 18, RS = RP * TT::RH;       // residual: 2 x 36 rows of 36 (+4 pad)
+constexpr int PP = 50;                                     // p: 20 rows of 20
+static_assert(TT::XW == 2 * XHALF && TT::XW <= XP && TT::RW == 2 * RHALF && TT::RW <= RP && TT::PW <= PP,
+              "window widths");
+static_assert((2 * XP) % 32 == TT::CW && PP % 32 == TT::CW && (2 * RP) % 32 == TT::QW, "bank schedule");
+__device__ __forceinline__ int xcol(int ii) { return (ii & 1) * XHALF + (ii >> 1); }
 
 // shared-memory layout (bytes).  The correction array D (256 x 51 FP32,
 // 52,224 B) overlays A, B, the residual and the pressure residual, which are
@@ -55,10 +78,10 @@ static_assert(TT::NPATCH == TC_NT, "one thread per patch");
 constexpr int OFF_A = 0;                                   // 256 x 64 BF16 = 32 KB
 constexpr int OFF_B = OFF_A + 256 * 64 * 2;                // 64 x 64 BF16 = 8 KB
 constexpr int OFF_R = OFF_B + 64 * 64 * 2;                 // residual (FP32)
-constexpr int OFF_RP = OFF_R + TT::SR * 4;                 // pressure residual
+constexpr int OFF_RP = OFF_R + 2 * RS * 4;                 // pressure residual
 constexpr int OFF_X = OFF_RP + TT::SRP * 4;                // x window
-constexpr int OFF_P = OFF_X + TT::SX * 4;                  // p window
-constexpr int OFF_BAR = OFF_P + TT::SP * 4;                // two mbarriers
+constexpr int OFF_P = OFF_X + 2 * XS * 4;                  // p window
+constexpr int OFF_BAR = OFF_P + TT::PH * PP * 4;           // two mbarriers
 constexpr int OFF_TMEM = OFF_BAR + 16;                     // TMEM base address
 constexpr int SMEM_BYTES = OFF_TMEM + 16;
 constexpr int OFF_D = 0;                                   // corrections, after the MMAs
@@ -127,7 +150,7 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
   const long long nv = L.nv;
   const int i0 = (tile0 + static_cast<int>(blockIdx.x)) * TC_TILE;
   const int j0 = (tile0 + static_cast<int>(blockIdx.y)) * TC_TILE;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int XI0 = 2 * i0 - 6, XJ0 = 2 * j0 - 6;
   const int RI0 = 2 * i0 - 4, RJ0 = 2 * j0 - 4;
 
@@ -157,63 +180,123 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
         : "memory");
   }
 
-  // 2. windows and FP32 residual (all windows lie in the free interior here)
+  // 2. x and p windows (x of Dirichlet or outside nodes reads as 0: those
+  //    columns are eliminated); residual of every cell (all cells of an
+  //    interior tile are free), b read from global memory
   if (x != nullptr) {
+    // warp w fills window rows w, w + 8, ..., lane k word k of a row (even
+    // nodes first, then odd): row validity and address once per row, all loads
+    // issued before the stores (fully unrolled), stores over 32 banks
+    constexpr int XROWS = 2 * TT::XH / (TC_NT / 32);
+    static_assert(2 * TT::XH % (TC_NT / 32) == 0 && TT::XW > 32 && TT::XW <= 64, "x window rows per warp");
+    float xv[XROWS][2];
 #pragma unroll
-    for (int t = tid; t < TT::SX; t += TC_NT) {
-      const int c = t / (TT::XW * TT::XH);
-      const int rem = t - c * TT::XW * TT::XH;
-      const int jj = rem / TT::XW, ii = rem - jj * TT::XW;
-      const int I = XI0 + ii, J = XJ0 + jj;
-      sx[t] = vfree(I, J, nq) ? x[c * nv + static_cast<long long>(J) * nq + I] : 0.0f;
+    for (int k = 0; k < XROWS; ++k) {
+      const int r = warp + k * (TC_NT / 32);
+      const int c = r >= TT::XH ? 1 : 0, jj = r - c * TT::XH;
+      const int J = XJ0 + jj;
+      const bool jfree = J > 0 && J < nq - 1;
+      const float* xr = x + c * nv + static_cast<long long>(jfree ? J : 0) * nq;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int pos = lane + 32 * h;
+        const int I = XI0 + (pos < XHALF ? 2 * pos : 2 * (pos - XHALF) + 1);
+        xv[k][h] = (jfree && pos < TT::XW && I > 0 && I < nq - 1) ? xr[I] : 0.0f;
+      }
     }
+#pragma unroll
+    for (int k = 0; k < XROWS; ++k) {
+      const int r = warp + k * (TC_NT / 32);
+      const int c = r >= TT::XH ? 1 : 0, jj = r - c * TT::XH;
+      float* dst = sx + c * XS + jj * XP;
+      dst[lane] = xv[k][0];
+      if (lane + 32 < TT::XW) dst[lane + 32] = xv[k][1];
+    }
+    // p window: 20 x 20 vertices, flat over the CTA
 #pragma unroll
     for (int t = tid; t < TT::SP; t += TC_NT) {
       const int jj = t / TT::PW, ii = t - jj * TT::PW;
       const int i = i0 - 3 + ii, j = j0 - 3 + jj;
-      sp[t] = (i >= 0 && j >= 0 && i < np && j < np) ? x[2 * nv + static_cast<long long>(j) * np + i] : 0.0f;
+      sp[jj * PP + ii] = (i >= 0 && j >= 0 && i < np && j < np) ? x[2 * nv + static_cast<long long>(j) * np + i] : 0.0f;
     }
-  }
-#pragma unroll
-  for (int t = tid; t < TT::SR; t += TC_NT) {
-    const int c = t / (TT::RW * TT::RH);
-    const int rem = t - c * TT::RW * TT::RH;
-    const int jj = rem / TT::RW, ii = rem - jj * TT::RW;
-    const int I = RI0 + ii, J = RJ0 + jj;
-    sr[t] = (I >= 0 && J >= 0 && I < nq && J < nq) ? b[c * nv + static_cast<long long>(J) * nq + I] : 0.0f;
-  }
-  {
-    const int jj = tid / TT::QW, ii = tid - jj * TT::QW;
-    const int i = i0 - 1 + ii, j = j0 - 1 + jj;
-    srp[tid] = b[2 * nv + static_cast<long long>(j) * np + i];
   }
   __syncthreads();
   const float cl = L.clf, cb = L.cbf;
-  if (x != nullptr) {
-    for (int t = tid; t < TT::CW * TT::CH; t += TC_NT) {
-      const int cy = t / TT::CW, cx = t - cy * TT::CW;
-      const int I0 = RI0 + 2 * cx, J0 = RJ0 + 2 * cy;
-      const float* x0 = sx + (2 * cy + 2) * TT::XW + (2 * cx + 2);
-      const float* pc = sp + (cy + 1) * TT::PW + (cx + 1);
-      float* r0 = sr + (2 * cy) * TT::RW + 2 * cx;
-      res_cell<float, TT>(r0, x0, pc, I0, J0, L, x, cl, cb);
-    }
-    {
-      const int jj = tid / TT::QW, ii = tid - jj * TT::QW;
-      const float* xs0 = sx + (2 * jj + 4) * TT::XW + (2 * ii + 4);
-      const float* xs1 = xs0 + TT::XW * TT::XH;
-      float s = 0.0f;
+  // cell (cx, cy) of the 18 x 18 residual cells: nodes (RI0 + 2 cx + PI, RJ0 + 2 cy + PJ),
+  // taken row-major (t = 18 cy + cx)
+  for (int t = tid; t < TT::CW * TT::CH; t += TC_NT) {
+    const int cy = t / TT::CW, cx = t - cy * TT::CW;
+    const int I0 = RI0 + 2 * cx, J0 = RJ0 + 2 * cy;
+    const bool own_p = cx >= 1 && cy >= 1 && cx <= TT::QW && cy <= TT::QH;   // the vertex carries a patch
+    float rp = own_p ? b[2 * nv + static_cast<long long>(J0 >> 1) * np + (I0 >> 1)] : 0.0f;
+    float r[2][2][2];
 #pragma unroll
-      for (int dJ = -2; dJ <= 2; ++dJ) {
+    for (int c = 0; c < 2; ++c)
 #pragma unroll
-        for (int dI = -2; dI <= 2; ++dI) {
-          const float wx = static_cast<float>(crow(dI) * nrow(dJ)), wy = static_cast<float>(nrow(dI) * crow(dJ));
-          if (wx != 0.0f) s = fmaf(wx, xs0[dJ * TT::XW + dI], s);
-          if (wy != 0.0f) s = fmaf(wy, xs1[dJ * TT::XW + dI], s);
+      for (int PJ = 0; PJ < 2; ++PJ)
+#pragma unroll
+        for (int PI = 0; PI < 2; ++PI) r[c][PJ][PI] = b[c * nv + static_cast<long long>(J0 + PJ) * nq + I0 + PI];
+    if (x != nullptr) {
+      float P[3][3];
+#pragma unroll
+      for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+        for (int di = 0; di < 3; ++di) P[dj][di] = sp[(cy + dj) * PP + cx + di];
+      float sdiv = 0.0f;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        // X[a][bb] = x_c at node (I0 - 2 + bb, J0 - 2 + a): window column 2 cx + bb, row 2 cy + a
+        const float* xc = sx + c * XS + 2 * cy * XP + cx;
+        float X[6][6];
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+          for (int bb = 0; bb < 6; ++bb) X[a][bb] = xc[a * XP + (bb & 1) * XHALF + (bb >> 1)];
+#pragma unroll
+        for (int PJ = 0; PJ < 2; ++PJ) {
+#pragma unroll
+          for (int PI = 0; PI < 2; ++PI) {
+            float sl = 0.0f;
+#pragma unroll
+            for (int dJ = -2; dJ <= 2; ++dJ) {
+#pragma unroll
+              for (int dI = -2; dI <= 2; ++dI) {
+                const float cf = static_cast<float>(k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ));
+                if (cf != 0.0f) sl = fmaf(cf, X[PJ + dJ + 2][PI + dI + 2], sl);
+              }
+            }
+            float g = 0.0f;
+#pragma unroll
+            for (int dj = -1; dj <= 1; ++dj) {
+#pragma unroll
+              for (int di = -1; di <= 1; ++di) {
+                const float w = static_cast<float>(c == 0 ? ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj)
+                                                          : ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj));
+                if (w != 0.0f) g = fmaf(w, P[dj + 1][di + 1], g);
+              }
+            }
+            r[c][PJ][PI] -= cl * sl + cb * g;
+          }
+        }
+        // divergence row of the vertex (node (I0, J0) = X[2][2]): -int p div u
+#pragma unroll
+        for (int dJ = -2; dJ <= 2; ++dJ) {
+#pragma unroll
+          for (int dI = -2; dI <= 2; ++dI) {
+            const float w = static_cast<float>(c == 0 ? crow(dI) * nrow(dJ) : nrow(dI) * crow(dJ));
+            if (w != 0.0f) sdiv = fmaf(w, X[2 + dJ][2 + dI], sdiv);
+          }
         }
       }
-      srp[tid] -= cb * s;
+      rp -= cb * sdiv;
     }
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int PJ = 0; PJ < 2; ++PJ)
+#pragma unroll
+        for (int PI = 0; PI < 2; ++PI) sr[c * RS + (2 * cy + PJ) * RP + PI * RHALF + cx] = r[c][PJ][PI];
+    if (own_p) srp[(cy - 1) * TT::QW + (cx - 1)] = rp;
   }
   __syncthreads();
 
@@ -227,7 +310,7 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
       for (int wj = 0; wj < 5; ++wj)
 #pragma unroll
         for (int wi = 0; wi < 5; ++wi)
-          row[c * 25 + wj * 5 + wi] = sr[c * TT::RW * TT::RH + (2 * qj + wj) * TT::RW + 2 * qi + wi];
+          row[c * 25 + wj * 5 + wi] = sr[c * RS + (2 * qj + wj) * RP + (wi & 1) * RHALF + qi + (wi >> 1)];
     row[50] = srp[tid];
 #pragma unroll
     for (int k = 51; k < 64; ++k) row[k] = 0.0f;
@@ -296,11 +379,15 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
     // 6. weighted update of the owned dofs: one thread per owned vertex (vi, vj);
     //    its Q2 nodes (2i-1..2i) x (2j-1..2j) take the corrections of the 9 / 6 /
     //    6 / 4 patches around them at compile-time offsets (patch q + dq, slot s).
-    if (tid < TC_TILE * TC_TILE) {
-      const int vj = tid / TC_TILE, vi = tid - vj * TC_TILE;
+    //    Warp w takes vertex rows 2w and 2w + 1 (lanes 0..27): their patches q
+    //    lie in two rows of 16, distinct modulo 32, so the reads of D (pitch 51,
+    //    odd) and of the x window (rows 16 banks apart) are free of conflicts.
+    const int uw = tid >> 5, ul = tid & 31;
+    if (uw < TC_TILE / 2 && ul < 2 * TC_TILE) {
+      const int vj = 2 * uw + (ul >= TC_TILE ? 1 : 0), vi = ul - (ul >= TC_TILE ? TC_TILE : 0);
       const int i = i0 + vi, j = j0 + vj;
       const float* dq = sd + ((vj + 1) * TT::QW + (vi + 1)) * 51;  // the vertex's own patch
-      const float* xs = sx + (2 * j - XJ0) * TT::XW + (2 * i - XI0);  // x window at node (2i, 2j)
+      const int xj = 2 * j - XJ0, xi = 2 * i - XI0;                  // x window at node (2i, 2j)
       const long long base = static_cast<long long>(2 * j) * nq + 2 * i;
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
@@ -320,12 +407,12 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
               }
             }
             const float w = omega * (ni ? 0.5f : (1.0f / 3.0f)) * (nj ? 0.5f : (1.0f / 3.0f));
-            const float xold = x != nullptr ? xs[c * TT::XW * TT::XH - nj * TT::XW - ni] : 0.0f;
+            const float xold = x != nullptr ? sx[c * XS + (xj - nj) * XP + xcol(xi - ni)] : 0.0f;
             xo[c * nv + base - static_cast<long long>(nj) * nq - ni] = fmaf(w, acc, xold);
           }
         }
       }
-      const float xoldp = x != nullptr ? sp[(j - (j0 - 3)) * TT::PW + (i - (i0 - 3))] : 0.0f;
+      const float xoldp = x != nullptr ? sp[(j - (j0 - 3)) * PP + (i - (i0 - 3))] : 0.0f;
       xo[2 * nv + static_cast<long long>(j) * np + i] = fmaf(omega, dq[50], xoldp);
     }
   } else if (tid == 0) {
