@@ -211,7 +211,7 @@ TRAFFIC_1024 = {
     "fp64": {"bytes": 155136512 + 377818880 + 505986560 + 66044672, "tile": "split16x16x2",
              "source": "profiles/k_vanka_own_f64_n1024.md (k_vanka_own<double,16,16,256,2> + k_patch_update; "
                        "writes still in L2 at kernel end are not counted)"},
-    "bf16": {"bytes": 74807552 + 11877120, "tile": "14x14",
+    "bf16": {"bytes": 74803712 + 12058880, "tile": "14x14",
              "source": "profiles/k_vanka_tc_n1024.md (k_vanka_tc interior tiles; the ring launch is not "
                        "included; writes still in L2 at kernel end are not counted)"},
 }

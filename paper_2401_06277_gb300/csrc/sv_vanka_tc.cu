@@ -20,10 +20,11 @@
 //   3. each thread writes its patch row of R, converted to BF16, into the
 //      K-major no-swizzle core-matrix layout (8 rows x 16 bytes per core
 //      matrix, LBO = 128 B along K, SBO = 1024 B along M);
-// The x and residual windows are stored column-parity split (the even nodes of
-// a row, then the odd ones) with row pitches for which the 16 cells or patches
-// of a half-warp row and the next row fall in disjoint banks, so the stencil
-// and patch-gather loads are free of bank conflicts.
+// The x and residual windows hold (u_x, u_y) pairs (float2), so a stencil tap
+// of both components is one 64-bit load and one packed FP32 FMA (FFMA2; the
+// two components share the Laplacian stencil), and are stored column-parity
+// split (the even nodes of a row, then the odd ones) with row pitches for which
+// the stencil, patch-gather and update loads are free of bank conflicts.
 //   4. thread 0 issues 2 x 4 tcgen05.mma (kind::f16, M=128, N=64, K=16) into
 //      TMEM and commits them to an mbarrier;
 //   5. after the wait, each thread reads its patch row of D with tcgen05.ld and
@@ -56,20 +57,23 @@ static_assert(TT::NPATCH == TC_NT, "one thread per patch");
 static_assert(TC_TILE % 2 == 0 && TC_TILE / 2 <= TC_NT / 32 && 2 * TC_TILE <= 32, "update: two vertex rows per warp");
 
 // Windows (origins as in the SIMT sweep: x at Q2 node 2 i0 - 6, residual at
-// 2 i0 - 4, p at vertex i0 - 3).  A row of the x window holds its 20 even
-// nodes, then its 20 odd ones; a residual row its 18 even, then 18 odd nodes.
-// Pitches: the residual cells are taken row-major, 18 per row (item t = 18 cy
-// + cx), and x rows two apart (one cell row) are 2 XP = 82 = 18 (mod 32) words
-// apart, so the bank of every stencil load is t + const (mod 32): conflict-free
-// for any 32 consecutive cells; likewise p rows (pitch 50 = 18).  The patch
-// gather takes 16 patches per row, and residual rows two apart are 2 RP = 80 =
-// 16 (mod 32) words apart: two patch rows of a warp fall in disjoint banks.
-constexpr int XP = 41, XHALF = 20, XS = XP * TT::XH;       // x: 2 x 40 rows of 40 (+1 pad)
-constexpr int RP = 40, RHALF = 18, RS = RP * TT::RH;       // residual: 2 x 36 rows of 36 (+4 pad)
+// 2 i0 - 4, p at vertex i0 - 3).  A row of the x window holds the (u_x, u_y)
+// pairs of its 20 even nodes, then of its 20 odd ones; a residual row those of
+// its 18 even, then 18 odd nodes.  A half-warp's 64-bit accesses are free of
+// bank conflicts when its 16 addresses differ modulo 16 pairs.  The residual
+// cells are taken row-major, 18 per row (item t = 18 cy + cx); x rows two apart
+// (one cell row) are 2 XP = 82 = 18 = 2 (mod 16) pairs apart, so the pair index
+// of every stencil load is t + const (mod 16), and the same holds for the cell
+// stores into the residual window (RP = 41); the patch gather reads one row of
+// 16 patches per half-warp.  p (scalar) rows have pitch 50 = 18 (mod 32): the
+// bank of a p load is t + const (mod 32).
+constexpr int XP = 41, XHALF = 20;                         // x: 40 rows of 40 pairs (+1 pad)
+constexpr int RP = 41, RHALF = 18;                         // residual: 36 rows of 36 pairs (+5 pad)
 constexpr int PP = 50;                                     // p: 20 rows of 20
 static_assert(TT::XW == 2 * XHALF && TT::XW <= XP && TT::RW == 2 * RHALF && TT::RW <= RP && TT::PW <= PP,
               "window widths");
-static_assert((2 * XP) % 32 == TT::CW && PP % 32 == TT::CW && (2 * RP) % 32 == TT::QW, "bank schedule");
+static_assert((2 * XP) % 16 == TT::CW % 16 && (2 * RP) % 16 == TT::CW % 16 && PP % 32 == TT::CW,
+              "bank schedule");
 __device__ __forceinline__ int xcol(int ii) { return (ii & 1) * XHALF + (ii >> 1); }
 
 // shared-memory layout (bytes).  The correction array D (256 x 51 FP32,
@@ -77,16 +81,16 @@ __device__ __forceinline__ int xcol(int ii) { return (ii & 1) * XHALF + (ii >> 1
 // all dead once the MMAs have completed; the x windows stay live for x_old.
 constexpr int OFF_A = 0;                                   // 256 x 64 BF16 = 32 KB
 constexpr int OFF_B = OFF_A + 256 * 64 * 2;                // 64 x 64 BF16 = 8 KB
-constexpr int OFF_R = OFF_B + 64 * 64 * 2;                 // residual (FP32)
-constexpr int OFF_RP = OFF_R + 2 * RS * 4;                 // pressure residual
-constexpr int OFF_X = OFF_RP + TT::SRP * 4;                // x window
-constexpr int OFF_P = OFF_X + 2 * XS * 4;                  // p window
+constexpr int OFF_R = OFF_B + 64 * 64 * 2;                 // residual pairs (FP32)
+constexpr int OFF_RP = OFF_R + TT::RH * RP * 8;            // pressure residual
+constexpr int OFF_X = OFF_RP + TT::SRP * 4;                // x window pairs
+constexpr int OFF_P = OFF_X + TT::XH * XP * 8;             // p window
 constexpr int OFF_BAR = OFF_P + TT::PH * PP * 4;           // two mbarriers
 constexpr int OFF_TMEM = OFF_BAR + 16;                     // TMEM base address
 constexpr int SMEM_BYTES = OFF_TMEM + 16;
 constexpr int OFF_D = 0;                                   // corrections, after the MMAs
 static_assert(OFF_D + TT::NPATCH * 51 * 4 <= OFF_X, "corrections overlay only dead buffers");
-static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
+static_assert(OFF_BAR % 8 == 0 && OFF_R % 8 == 0 && OFF_X % 8 == 0, "mbarrier and float2 alignment");
 
 constexpr uint32_t TMEM_COLS = 128;
 constexpr int WAIT_LIMIT = 1 << 22;
@@ -139,9 +143,9 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
                                                      const float* __restrict__ b, float* __restrict__ xo,
                                                      float omega, int tile0, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  float* sx = reinterpret_cast<float*>(sm + OFF_X);
+  float2* sx = reinterpret_cast<float2*>(sm + OFF_X);
   float* sp = reinterpret_cast<float*>(sm + OFF_P);
-  float* sr = reinterpret_cast<float*>(sm + OFF_R);
+  float2* sr = reinterpret_cast<float2*>(sm + OFF_R);
   float* srp = reinterpret_cast<float*>(sm + OFF_RP);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + OFF_TMEM);
@@ -184,31 +188,29 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
   //    columns are eliminated); residual of every cell (all cells of an
   //    interior tile are free), b read from global memory
   if (x != nullptr) {
-    // warp w fills window rows w, w + 8, ..., lane k word k of a row (even
+    // warp w fills window rows w, w + 8, ..., lane k pair k of a row (even
     // nodes first, then odd): row validity and address once per row, all loads
-    // issued before the stores (fully unrolled), stores over 32 banks
-    constexpr int XROWS = 2 * TT::XH / (TC_NT / 32);
-    static_assert(2 * TT::XH % (TC_NT / 32) == 0 && TT::XW > 32 && TT::XW <= 64, "x window rows per warp");
-    float xv[XROWS][2];
+    // issued before the stores (fully unrolled)
+    constexpr int XROWS = TT::XH / (TC_NT / 32);
+    static_assert(TT::XH % (TC_NT / 32) == 0 && TT::XW > 32 && TT::XW <= 64, "x window rows per warp");
+    float2 xv[XROWS][2];
 #pragma unroll
     for (int k = 0; k < XROWS; ++k) {
-      const int r = warp + k * (TC_NT / 32);
-      const int c = r >= TT::XH ? 1 : 0, jj = r - c * TT::XH;
+      const int jj = warp + k * (TC_NT / 32);
       const int J = XJ0 + jj;
       const bool jfree = J > 0 && J < nq - 1;
-      const float* xr = x + c * nv + static_cast<long long>(jfree ? J : 0) * nq;
+      const float* xr = x + static_cast<long long>(jfree ? J : 0) * nq;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int pos = lane + 32 * h;
         const int I = XI0 + (pos < XHALF ? 2 * pos : 2 * (pos - XHALF) + 1);
-        xv[k][h] = (jfree && pos < TT::XW && I > 0 && I < nq - 1) ? xr[I] : 0.0f;
+        const bool ok = jfree && pos < TT::XW && I > 0 && I < nq - 1;
+        xv[k][h] = ok ? make_float2(xr[I], xr[nv + I]) : make_float2(0.0f, 0.0f);
       }
     }
 #pragma unroll
     for (int k = 0; k < XROWS; ++k) {
-      const int r = warp + k * (TC_NT / 32);
-      const int c = r >= TT::XH ? 1 : 0, jj = r - c * TT::XH;
-      float* dst = sx + c * XS + jj * XP;
+      float2* dst = sx + (warp + k * (TC_NT / 32)) * XP;
       dst[lane] = xv[k][0];
       if (lane + 32 < TT::XW) dst[lane + 32] = xv[k][1];
     }
@@ -229,73 +231,83 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
     const int I0 = RI0 + 2 * cx, J0 = RJ0 + 2 * cy;
     const bool own_p = cx >= 1 && cy >= 1 && cx <= TT::QW && cy <= TT::QH;   // the vertex carries a patch
     float rp = own_p ? b[2 * nv + static_cast<long long>(J0 >> 1) * np + (I0 >> 1)] : 0.0f;
-    float r[2][2][2];
+    float2 r[2][2];   // [PJ][PI]: (u_x, u_y) residual of node (I0 + PI, J0 + PJ)
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+    for (int PJ = 0; PJ < 2; ++PJ)
 #pragma unroll
-      for (int PJ = 0; PJ < 2; ++PJ)
-#pragma unroll
-        for (int PI = 0; PI < 2; ++PI) r[c][PJ][PI] = b[c * nv + static_cast<long long>(J0 + PJ) * nq + I0 + PI];
+      for (int PI = 0; PI < 2; ++PI) {
+        const long long k = static_cast<long long>(J0 + PJ) * nq + I0 + PI;
+        r[PJ][PI] = make_float2(b[k], b[nv + k]);
+      }
     if (x != nullptr) {
       float P[3][3];
 #pragma unroll
       for (int dj = 0; dj < 3; ++dj)
 #pragma unroll
         for (int di = 0; di < 3; ++di) P[dj][di] = sp[(cy + dj) * PP + cx + di];
-      float sdiv = 0.0f;
+      // rows a = 0..5 of the 6 x 6 pair neighbourhood (node (I0 - 2 + bb, J0 - 2 + a))
+      // stream through registers: each feeds the Laplacian of the nodes it reaches
+      // and, for a <= 4, the divergence row of the vertex (node (I0, J0))
+      const float2* xc = sx + 2 * cy * XP + cx;
+      float2 sl[2][2];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        // X[a][bb] = x_c at node (I0 - 2 + bb, J0 - 2 + a): window column 2 cx + bb, row 2 cy + a
-        const float* xc = sx + c * XS + 2 * cy * XP + cx;
-        float X[6][6];
+      for (int PJ = 0; PJ < 2; ++PJ)
 #pragma unroll
-        for (int a = 0; a < 6; ++a)
+        for (int PI = 0; PI < 2; ++PI) sl[PJ][PI] = make_float2(0.0f, 0.0f);
+      float2 sdiv = make_float2(0.0f, 0.0f);
 #pragma unroll
-          for (int bb = 0; bb < 6; ++bb) X[a][bb] = xc[a * XP + (bb & 1) * XHALF + (bb >> 1)];
+      for (int a = 0; a < 6; ++a) {
+        float2 Xa[6];
+#pragma unroll
+        for (int bb = 0; bb < 6; ++bb) Xa[bb] = xc[a * XP + (bb & 1) * XHALF + (bb >> 1)];
 #pragma unroll
         for (int PJ = 0; PJ < 2; ++PJ) {
 #pragma unroll
           for (int PI = 0; PI < 2; ++PI) {
-            float sl = 0.0f;
 #pragma unroll
-            for (int dJ = -2; dJ <= 2; ++dJ) {
-#pragma unroll
-              for (int dI = -2; dI <= 2; ++dI) {
-                const float cf = static_cast<float>(k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ));
-                if (cf != 0.0f) sl = fmaf(cf, X[PJ + dJ + 2][PI + dI + 2], sl);
-              }
+            for (int bb = 0; bb < 6; ++bb) {
+              const int dJ = a - 2 - PJ, dI = bb - 2 - PI;
+              const float cf = (dJ < -2 || dJ > 2 || dI < -2 || dI > 2)
+                                   ? 0.0f
+                                   : static_cast<float>(k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ));
+              if (cf != 0.0f) sl[PJ][PI] = __ffma2_rn(make_float2(cf, cf), Xa[bb], sl[PJ][PI]);
             }
-            float g = 0.0f;
-#pragma unroll
-            for (int dj = -1; dj <= 1; ++dj) {
-#pragma unroll
-              for (int di = -1; di <= 1; ++di) {
-                const float w = static_cast<float>(c == 0 ? ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj)
-                                                          : ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj));
-                if (w != 0.0f) g = fmaf(w, P[dj + 1][di + 1], g);
-              }
-            }
-            r[c][PJ][PI] -= cl * sl + cb * g;
           }
         }
-        // divergence row of the vertex (node (I0, J0) = X[2][2]): -int p div u
+        if (a <= 4) {   // -int p div u of the vertex: C (x) N on u_x, N (x) C on u_y
 #pragma unroll
-        for (int dJ = -2; dJ <= 2; ++dJ) {
-#pragma unroll
-          for (int dI = -2; dI <= 2; ++dI) {
-            const float w = static_cast<float>(c == 0 ? crow(dI) * nrow(dJ) : nrow(dI) * crow(dJ));
-            if (w != 0.0f) sdiv = fmaf(w, X[2 + dJ][2 + dI], sdiv);
+          for (int bb = 0; bb < 5; ++bb) {
+            const float wx = static_cast<float>(crow(bb - 2) * nrow(a - 2));
+            const float wy = static_cast<float>(nrow(bb - 2) * crow(a - 2));
+            if (wx != 0.0f || wy != 0.0f) sdiv = __ffma2_rn(make_float2(wx, wy), Xa[bb], sdiv);
           }
         }
       }
-      rp -= cb * sdiv;
+#pragma unroll
+      for (int PJ = 0; PJ < 2; ++PJ) {
+#pragma unroll
+        for (int PI = 0; PI < 2; ++PI) {
+          float g0 = 0.0f, g1 = 0.0f;   // (B^T p) / (-h/18) for u_x, u_y
+#pragma unroll
+          for (int dj = -1; dj <= 1; ++dj) {
+#pragma unroll
+            for (int di = -1; di <= 1; ++di) {
+              const float w0 = static_cast<float>(ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj));
+              const float w1 = static_cast<float>(ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj));
+              if (w0 != 0.0f) g0 = fmaf(w0, P[dj + 1][di + 1], g0);
+              if (w1 != 0.0f) g1 = fmaf(w1, P[dj + 1][di + 1], g1);
+            }
+          }
+          r[PJ][PI].x -= cl * sl[PJ][PI].x + cb * g0;
+          r[PJ][PI].y -= cl * sl[PJ][PI].y + cb * g1;
+        }
+      }
+      rp -= cb * (sdiv.x + sdiv.y);
     }
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+    for (int PJ = 0; PJ < 2; ++PJ)
 #pragma unroll
-      for (int PJ = 0; PJ < 2; ++PJ)
-#pragma unroll
-        for (int PI = 0; PI < 2; ++PI) sr[c * RS + (2 * cy + PJ) * RP + PI * RHALF + cx] = r[c][PJ][PI];
+      for (int PI = 0; PI < 2; ++PI) sr[(2 * cy + PJ) * RP + PI * RHALF + cx] = r[PJ][PI];
     if (own_p) srp[(cy - 1) * TT::QW + (cx - 1)] = rp;
   }
   __syncthreads();
@@ -305,12 +317,13 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
   {
     float row[64];
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+    for (int wj = 0; wj < 5; ++wj)
 #pragma unroll
-      for (int wj = 0; wj < 5; ++wj)
-#pragma unroll
-        for (int wi = 0; wi < 5; ++wi)
-          row[c * 25 + wj * 5 + wi] = sr[c * RS + (2 * qj + wj) * RP + (wi & 1) * RHALF + qi + (wi >> 1)];
+      for (int wi = 0; wi < 5; ++wi) {
+        const float2 v = sr[(2 * qj + wj) * RP + (wi & 1) * RHALF + qi + (wi >> 1)];
+        row[wj * 5 + wi] = v.x;
+        row[25 + wj * 5 + wi] = v.y;
+      }
     row[50] = srp[tid];
 #pragma unroll
     for (int k = 51; k < 64; ++k) row[k] = 0.0f;
@@ -381,7 +394,7 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
     //    6 / 4 patches around them at compile-time offsets (patch q + dq, slot s).
     //    Warp w takes vertex rows 2w and 2w + 1 (lanes 0..27): their patches q
     //    lie in two rows of 16, distinct modulo 32, so the reads of D (pitch 51,
-    //    odd) and of the x window (rows 16 banks apart) are free of conflicts.
+    //    odd) are free of bank conflicts.
     const int uw = tid >> 5, ul = tid & 31;
     if (uw < TC_TILE / 2 && ul < 2 * TC_TILE) {
       const int vj = 2 * uw + (ul >= TC_TILE ? 1 : 0), vi = ul - (ul >= TC_TILE ? TC_TILE : 0);
@@ -390,11 +403,12 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
       const int xj = 2 * j - XJ0, xi = 2 * i - XI0;                  // x window at node (2i, 2j)
       const long long base = static_cast<long long>(2 * j) * nq + 2 * i;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
+      for (int nj = 0; nj < 2; ++nj) {        // node J = 2j - nj
 #pragma unroll
-        for (int nj = 0; nj < 2; ++nj) {      // node J = 2j - nj
+        for (int ni = 0; ni < 2; ++ni) {      // node I = 2i - ni
+          const float2 xold = x != nullptr ? sx[(xj - nj) * XP + xcol(xi - ni)] : make_float2(0.0f, 0.0f);
 #pragma unroll
-          for (int ni = 0; ni < 2; ++ni) {    // node I = 2i - ni
+          for (int c = 0; c < 2; ++c) {
             float acc = 0.0f;
             // patches (i + di, j + dj): di in {-1, 0, +1} for an even node, {-1, 0} for an odd one
 #pragma unroll
@@ -407,8 +421,7 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
               }
             }
             const float w = omega * (ni ? 0.5f : (1.0f / 3.0f)) * (nj ? 0.5f : (1.0f / 3.0f));
-            const float xold = x != nullptr ? sx[c * XS + (xj - nj) * XP + xcol(xi - ni)] : 0.0f;
-            xo[c * nv + base - static_cast<long long>(nj) * nq - ni] = fmaf(w, acc, xold);
+            xo[c * nv + base - static_cast<long long>(nj) * nq - ni] = fmaf(w, acc, c == 0 ? xold.x : xold.y);
           }
         }
       }
