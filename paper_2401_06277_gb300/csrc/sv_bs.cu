@@ -73,6 +73,7 @@ __device__ __forceinline__ void bs_rhs_vertex(const LevelDev& L, const T* __rest
 template <typename T>
 __global__ void k_bs_rhs(LevelDev L, const T* __restrict__ r, T* __restrict__ g, T* __restrict__ ds,
                          T* __restrict__ dp, BSC<T> k) {
+  pdl_begin();
   const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = L.n;
   if (a > n || b > n) return;
@@ -122,6 +123,7 @@ __device__ __forceinline__ void dinv_btp_node(const LevelDev& L, const T (&P)[3]
 
 template <typename T>
 __global__ void k_bs_dinv_btp(LevelDev L, const T* __restrict__ dp, T* __restrict__ q, BSC<T> k) {
+  pdl_begin();
   const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
   if (a > L.n || b > L.n) return;
   T P[3][3];
@@ -137,6 +139,7 @@ __global__ void k_bs_dinv_btp(LevelDev L, const T* __restrict__ dp, T* __restric
 template <typename T>
 __global__ void k_bs_jacobi(LevelDev L, const T* __restrict__ q, const T* __restrict__ g, const T* __restrict__ ds,
                             T* __restrict__ dp, BSC<T> kc) {
+  pdl_begin();
   const T inv_t = kc.inv_t, wj = kc.wj;
   const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = L.n, nq = L.nq;
@@ -193,6 +196,7 @@ __device__ __forceinline__ void bs_update_node(const LevelDev& L, const T (&P)[3
 template <typename T, bool UZ>
 __global__ void k_bs_update(LevelDev L, const T* __restrict__ r, const T* __restrict__ dp, const T* __restrict__ x,
                             T* __restrict__ xo, BSC<T> kc) {
+  pdl_begin();
   const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
   if (a > L.n || b > L.n) return;
   T P[3][3];
@@ -227,15 +231,15 @@ void launch_bs_sweep(const LevelDev& L, const BSParams& prm, T* scratch, T* rbuf
   const BSC<T> k{T(L.cb), T(1.0 / L.cl), T(1.0 / prm.t), T(prm.jacobi_weight), T(prm.omega)};
   dim3 blk(32, 8), grid((L.np + 31) / 32, (L.np + 7) / 8);
   count_launches(2 + 2 * (prm.jacobi_iters - 1));
-  k_bs_rhs<T><<<grid, blk, 0, s>>>(L, r, g, ds, dp, k);
+  launch_pdl(k_bs_rhs<T>, dim3(grid), dim3(blk), 0, s, L, r, g, ds, dp, k);
   for (int it = 1; it < prm.jacobi_iters; ++it) {
-    k_bs_dinv_btp<T><<<grid, blk, 0, s>>>(L, dp, q, k);
-    k_bs_jacobi<T><<<grid, blk, 0, s>>>(L, q, g, ds, dp, k);
+    launch_pdl(k_bs_dinv_btp<T>, dim3(grid), dim3(blk), 0, s, L, dp, q, k);
+    launch_pdl(k_bs_jacobi<T>, dim3(grid), dim3(blk), 0, s, L, q, g, ds, dp, k);
   }
   if (prm.uzawa)
-    k_bs_update<T, true><<<grid, blk, 0, s>>>(L, r, dp, x, xo, k);
+    launch_pdl(k_bs_update<T, true>, dim3(grid), dim3(blk), 0, s, L, r, dp, x, xo, k);
   else
-    k_bs_update<T, false><<<grid, blk, 0, s>>>(L, r, dp, x, xo, k);
+    launch_pdl(k_bs_update<T, false>, dim3(grid), dim3(blk), 0, s, L, r, dp, x, xo, k);
 }
 
 template void launch_bs_sweep<double>(const LevelDev&, const BSParams&, double*, double*, const double*,

@@ -26,6 +26,7 @@ __device__ __forceinline__ double q1m(int i, int d, int n) {
 // y_p = b_p - M x_p (x may be nullptr: y_p = b_p); y_u = 0
 __global__ void k_mass_resid(LevelDev L, const double* __restrict__ x, const double* __restrict__ b,
                              double* __restrict__ y) {
+  pdl_begin();
   const long long N = L.N, p0 = 2 * L.nv;
   const int n = L.n, np = L.np;
   const double c = (L.h / 6.0) * (L.h / 6.0);
@@ -54,6 +55,7 @@ __global__ void k_mass_resid(LevelDev L, const double* __restrict__ x, const dou
 // block 0: velocity (D = diag L), block 1: pressure (D = diag M)
 __global__ void k_block_jacobi(LevelDev L, int block, const double* __restrict__ x, const double* __restrict__ r,
                                double* __restrict__ xo, double omega) {
+  pdl_begin();
   const long long N = L.N, p0 = 2 * L.nv;
   const int n = L.n, np = L.np, nq = L.nq;
   const double cm = (L.h / 6.0) * (L.h / 6.0);
@@ -79,6 +81,7 @@ __global__ void k_block_jacobi(LevelDev L, int block, const double* __restrict__
 }
 
 __global__ void k_add(double* __restrict__ y, const double* __restrict__ x, long long N) {
+  pdl_begin();
   for (long long k = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; k < N;
        k += static_cast<long long>(gridDim.x) * blockDim.x)
     y[k] += x[k];
@@ -94,18 +97,18 @@ int grid_for_bt(long long N) {
 
 void launch_mass_resid(const LevelDev& L, const double* x, const double* b, double* y, cudaStream_t s) {
   count_launches(1);
-  k_mass_resid<<<grid_for_bt(L.N), 256, 0, s>>>(L, x, b, y);
+  launch_pdl(k_mass_resid, dim3(grid_for_bt(L.N)), dim3(256), 0, s, L, x, b, y);
 }
 
 void launch_block_jacobi(const LevelDev& L, int block, const double* x, const double* r, double* xo, double omega,
                          cudaStream_t s) {
   count_launches(1);
-  k_block_jacobi<<<grid_for_bt(L.N), 256, 0, s>>>(L, block, x, r, xo, omega);
+  launch_pdl(k_block_jacobi, dim3(grid_for_bt(L.N)), dim3(256), 0, s, L, block, x, r, xo, omega);
 }
 
 void launch_add(double* y, const double* x, long long N, cudaStream_t s) {
   count_launches(1);
-  k_add<<<grid_for_bt(N), 256, 0, s>>>(y, x, N);
+  launch_pdl(k_add, dim3(grid_for_bt(N)), dim3(256), 0, s, y, x, N);
 }
 
 }  // namespace sv

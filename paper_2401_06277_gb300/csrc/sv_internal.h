@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <utility>
+
 #include <atomic>
 #include <cstddef>
 #include <string>
@@ -11,6 +13,35 @@
 #include "stokes_vanka.h"
 
 namespace sv {
+
+// ---- programmatic dependent launch (Hopper and later) ----
+// Every kernel of the library begins with pdl_begin(), which waits until the
+// previous kernel of the stream has completed with its memory operations
+// visible; nothing is read or written before it.  A kernel started by
+// launch_pdl may be launched once every CTA of its predecessor has exited
+// (the implicit trigger), so its launch overlaps the predecessor's completion
+// instead of following it; launched plainly, the wait returns at once.  There
+// is no early trigger: dependents scheduled while their predecessor still
+// runs would be placed unevenly over the SMs, which slows the kernels bound by
+// the per-SM FP64 pipe.
+__device__ __forceinline__ void pdl_begin() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);   // errors surface in cudaGetLastError
+}
+
 
 // Per-class patch data for the Schur-factored exact patch solve.  A patch
 // matrix is A_i = [[K, 0, bx^T], [0, K, by^T], [bx, by, 0]] in slot order

@@ -111,6 +111,7 @@ __device__ __forceinline__ void apply_vertex(const LevelDev& L, const T* __restr
 template <typename T>
 __global__ void k_apply(LevelDev L, const T* __restrict__ x, const T* __restrict__ b,
                         T* __restrict__ y, int residual) {
+  pdl_begin();
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   const int bb = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = L.n;
@@ -181,6 +182,7 @@ __device__ __forceinline__ void rhs_vertex(const LevelDev& L, const double* __re
 
 __global__ void k_rhs_vel(LevelDev L, const double* __restrict__ f, const double* __restrict__ ud,
                           double* __restrict__ b) {
+  pdl_begin();
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   const int bb = blockIdx.y * blockDim.y + threadIdx.y;
   const int n = L.n;
@@ -192,6 +194,7 @@ __global__ void k_rhs_vel(LevelDev L, const double* __restrict__ f, const double
 }
 
 __global__ void k_rhs_p(LevelDev L, const double* __restrict__ ud, double* __restrict__ b) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int nq = L.nq, np = L.np, n = L.n;
@@ -213,6 +216,7 @@ __global__ void k_rhs_p(LevelDev L, const double* __restrict__ ud, double* __res
 
 // grad_f = R^T lambda: sum over free velocity rows k of (M)_{k,(I,J)} lambda_k.
 __global__ void k_rhs_transpose(LevelDev L, const double* __restrict__ lam, double* __restrict__ g) {
+  pdl_begin();
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   const int J = blockIdx.y * blockDim.y + threadIdx.y;
   const int nq = L.nq;
@@ -269,6 +273,7 @@ __host__ __device__ constexpr double rw(int g, int k) {
 // g in {0, 1}, and coarse vertex (ex, ey).
 template <typename T>
 __global__ void k_restrict(LevelDev F, LevelDev C, const T* __restrict__ rf, T* __restrict__ rc) {
+  pdl_begin();
   const int ex = blockIdx.x * blockDim.x + threadIdx.x;
   const int ey = blockIdx.y * blockDim.y + threadIdx.y;
   if (ex > C.n || ey > C.n) return;
@@ -332,6 +337,7 @@ __global__ void k_restrict(LevelDev F, LevelDev C, const T* __restrict__ rf, T* 
 // f in {0, 1}.  Coarse Dirichlet values read as 0; fine Dirichlet rows are untouched.
 template <typename T>
 __global__ void k_prolong_add(LevelDev F, LevelDev C, const T* __restrict__ ec, T* __restrict__ xf) {
+  pdl_begin();
   const int ex = blockIdx.x * blockDim.x + threadIdx.x;
   const int ey = blockIdx.y * blockDim.y + threadIdx.y;
   if (ex > C.n || ey > C.n) return;
@@ -399,6 +405,7 @@ __global__ void k_prolong_add(LevelDev F, LevelDev C, const T* __restrict__ ec, 
 
 template <typename TI, typename TO>
 __global__ void k_convert(const TI* __restrict__ in, TO* __restrict__ out, long long N) {
+  pdl_begin();
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
        i += static_cast<long long>(gridDim.x) * blockDim.x)
     out[i] = static_cast<TO>(in[i]);
@@ -408,6 +415,7 @@ __global__ void k_convert(const TI* __restrict__ in, TO* __restrict__ out, long 
 // summed by a fixed shuffle tree (deterministic)
 __global__ void k_coarse(const double* __restrict__ G, int N0, const double* __restrict__ r,
                          double* __restrict__ e) {
+  pdl_begin();
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (row >= N0) return;
   const double* g = G + static_cast<long long>(row) * N0;
@@ -428,34 +436,34 @@ template <typename T>
 void launch_apply(const LevelDev& L, const T* x, const T* b, T* y, int residual, cudaStream_t s) {
   count_launches(1);
   dim3 blk(32, 8);
-  k_apply<T><<<grid2(L.np, L.np, blk), blk, 0, s>>>(L, x, b, y, residual);
+  launch_pdl(k_apply<T>, dim3(grid2(L.np, L.np, blk)), dim3(blk), 0, s, L, x, b, y, residual);
 }
 
 void launch_rhs(const LevelDev& L, const double* f, const double* ud, double* b, cudaStream_t s) {
   count_launches(2);
   dim3 blk(32, 8);
-  k_rhs_vel<<<grid2(L.np, L.np, blk), blk, 0, s>>>(L, f, ud, b);
-  k_rhs_p<<<grid2(L.np, L.np, blk), blk, 0, s>>>(L, ud, b);
+  launch_pdl(k_rhs_vel, dim3(grid2(L.np, L.np, blk)), dim3(blk), 0, s, L, f, ud, b);
+  launch_pdl(k_rhs_p, dim3(grid2(L.np, L.np, blk)), dim3(blk), 0, s, L, ud, b);
 }
 
 void launch_rhs_transpose(const LevelDev& L, const double* lam, double* g, cudaStream_t s) {
   count_launches(1);
   dim3 blk(32, 8);
-  k_rhs_transpose<<<grid2(L.nq, L.nq, blk), blk, 0, s>>>(L, lam, g);
+  launch_pdl(k_rhs_transpose, dim3(grid2(L.nq, L.nq, blk)), dim3(blk), 0, s, L, lam, g);
 }
 
 template <typename T>
 void launch_restrict(const LevelDev& F, const LevelDev& C, const T* rf, T* rc, cudaStream_t s) {
   count_launches(1);
   dim3 blk(32, 8);
-  k_restrict<T><<<grid2(C.n + 1, C.n + 1, blk), blk, 0, s>>>(F, C, rf, rc);
+  launch_pdl(k_restrict<T>, dim3(grid2(C.n + 1, C.n + 1, blk)), dim3(blk), 0, s, F, C, rf, rc);
 }
 
 template <typename T>
 void launch_prolong_add(const LevelDev& F, const LevelDev& C, const T* ec, T* xf, cudaStream_t s) {
   count_launches(1);
   dim3 blk(32, 8);
-  k_prolong_add<T><<<grid2(C.n + 1, C.n + 1, blk), blk, 0, s>>>(F, C, ec, xf);
+  launch_pdl(k_prolong_add<T>, dim3(grid2(C.n + 1, C.n + 1, blk)), dim3(blk), 0, s, F, C, ec, xf);
 }
 
 template <typename TI, typename TO>
@@ -463,12 +471,13 @@ void launch_convert(const TI* in, TO* out, long long N, cudaStream_t s) {
   count_launches(1);
   long long blocks = (N + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_convert<TI, TO><<<static_cast<int>(blocks < 1 ? 1 : blocks), 256, 0, s>>>(in, out, N);
+  if (blocks < 1) blocks = 1;
+  launch_pdl(k_convert<TI, TO>, dim3(static_cast<int>(blocks)), dim3(256), 0, s, in, out, N);
 }
 
 void launch_coarse(const double* G, int N0, const double* r, double* e, cudaStream_t s) {
   count_launches(1);
-  k_coarse<<<(N0 + 7) / 8, 256, 0, s>>>(G, N0, r, e);
+  launch_pdl(k_coarse, dim3((N0 + 7) / 8), dim3(256), 0, s, G, N0, r, e);
 }
 
 template void launch_apply<double>(const LevelDev&, const double*, const double*, double*, int, cudaStream_t);

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(DOT_NT) k_orth_dots(const double* __restrict__
                                                       unsigned* ticket, double* __restrict__ dots,
                                                       double* __restrict__ norm2,
                                                       const double* __restrict__ gate) {
+  pdl_begin();
   if (gate != nullptr && *gate == 0.0) return;
   constexpr int NO = K + (NORM ? 1 : 0);
   constexpr int U = orth_unroll<K>();
@@ -142,6 +143,7 @@ __global__ void __launch_bounds__(DOT_NT) k_orth_update(double* __restrict__ w, 
                                                         const double* __restrict__ dgks_ref,
                                                         double* __restrict__ flag, double* __restrict__ hacc,
                                                         const double* __restrict__ coef_all, int nacc) {
+  pdl_begin();
   if (gate != nullptr && *gate == 0.0) return;
   constexpr int U = orth_unroll<K>();
   double c[K > 0 ? K : 1];
@@ -204,6 +206,7 @@ __global__ void __launch_bounds__(DOT_NT) k_orth_update_dots(double* __restrict_
                                                              double* __restrict__ norm2,
                                                              const double* __restrict__ dgks_ref,
                                                              double* __restrict__ flag) {
+  pdl_begin();
   constexpr int NO = K + 1;
   constexpr int U = orth_unroll<K>();
   double c[K];
@@ -261,6 +264,7 @@ __global__ void __launch_bounds__(DOT_NT) k_orth_update_dots(double* __restrict_
 // out[k] (+)= sum_b partials[k * npart + b]; one CTA per k
 __global__ void k_reduce(const double* __restrict__ partials, int npart, double* __restrict__ out,
                          int accumulate) {
+  pdl_begin();
   const int k = blockIdx.x;
   double s = 0.0;
   for (int b = threadIdx.x; b < npart; b += blockDim.x) s += partials[static_cast<long long>(k) * npart + b];
@@ -277,6 +281,7 @@ __global__ void k_reduce(const double* __restrict__ partials, int npart, double*
 
 __global__ void k_multiaxpy(double* __restrict__ w, const double* __restrict__ V, long long ld,
                             int nk, const double* __restrict__ coef, double sign, long long N) {
+  pdl_begin();
   __shared__ double c[64];
   if (threadIdx.x < nk) c[threadIdx.x] = sign * coef[threadIdx.x];
   __syncthreads();
@@ -290,6 +295,7 @@ __global__ void k_multiaxpy(double* __restrict__ w, const double* __restrict__ V
 
 __global__ void k_scale(double* __restrict__ y, const double* __restrict__ x,
                         const double* __restrict__ den, double scal, long long N) {
+  pdl_begin();
   double f = scal;
   if (den != nullptr) {
     const double d = *den;
@@ -301,6 +307,7 @@ __global__ void k_scale(double* __restrict__ y, const double* __restrict__ x,
 }
 
 __global__ void k_fill(double* __restrict__ p, double v, long long N) {
+  pdl_begin();
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
        i += static_cast<long long>(gridDim.x) * blockDim.x)
     p[i] = v;
@@ -310,6 +317,7 @@ __global__ void k_fill(double* __restrict__ p, double v, long long N) {
 // previous rotations, build rotation j, update g; est = |g[j+1]|.
 __global__ void k_givens(double* H, int ldh, double* cs, double* sn, double* g,
                          const double* hcol, const double* hnorm, int j, double* est) {
+  pdl_begin();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double* h = H + static_cast<long long>(j) * ldh;
   for (int i = 0; i <= j; ++i) h[i] = hcol[i];
@@ -336,6 +344,7 @@ __global__ void k_givens(double* H, int ldh, double* cs, double* sn, double* g,
 
 // Solve the k x k upper-triangular system H y = g (columns of H have stride ldh).
 __global__ void k_backsolve(const double* H, int ldh, const double* g, int k, double* y) {
+  pdl_begin();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int i = k - 1; i >= 0; --i) {
     double s = g[i];
@@ -346,6 +355,7 @@ __global__ void k_backsolve(const double* H, int ldh, const double* g, int k, do
 }
 
 __global__ void k_dirichlet_copy(LevelDev L, const double* __restrict__ src, double* __restrict__ dst) {
+  pdl_begin();
   const long long N = L.N;
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
        i += static_cast<long long>(gridDim.x) * blockDim.x) {
@@ -362,6 +372,7 @@ __global__ void k_dirichlet_copy(LevelDev L, const double* __restrict__ src, dou
 // partials[b] = sum over this block's elements of x (deterministic two-stage sum with k_reduce)
 __global__ void __launch_bounds__(DOT_NT) k_partial_sum(const double* __restrict__ x, long long N,
                                                         double* __restrict__ partials) {
+  pdl_begin();
   double acc = 0.0;
   for (long long i = blockIdx.x * static_cast<long long>(DOT_NT) + threadIdx.x; i < N;
        i += static_cast<long long>(gridDim.x) * DOT_NT)
@@ -380,6 +391,7 @@ __global__ void __launch_bounds__(DOT_NT) k_partial_sum(const double* __restrict
 // y = x, with the pressure block shifted by -(*sum)/np2 (zero mean)
 __global__ void k_copy_shift_pressure(const double* __restrict__ x, double* __restrict__ y, long long N,
                                       long long p0, const double* __restrict__ sum, double inv_np2) {
+  pdl_begin();
   const double m = *sum * inv_np2;
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
        i += static_cast<long long>(gridDim.x) * blockDim.x)
@@ -404,11 +416,11 @@ void dots_k(bool norm, const double* V, long long ld, const double* w, long long
             int npart, unsigned* ticket, double* dots, double* norm2, const double* gate, cudaStream_t s) {
   if constexpr (K == 0) {
     (void)norm;   // zero vectors: only the norm (callers pass norm2)
-    k_orth_dots<0, true><<<npart, DOT_NT, 0, s>>>(V, ld, w, N, partials, npart, ticket, dots, norm2, gate);
+    launch_pdl(k_orth_dots<0, true>, dim3(npart), dim3(DOT_NT), 0, s, V, ld, w, N, partials, npart, ticket, dots, norm2, gate);
   } else if (norm) {
-    k_orth_dots<K, true><<<npart, DOT_NT, 0, s>>>(V, ld, w, N, partials, npart, ticket, dots, norm2, gate);
+    launch_pdl(k_orth_dots<K, true>, dim3(npart), dim3(DOT_NT), 0, s, V, ld, w, N, partials, npart, ticket, dots, norm2, gate);
   } else {
-    k_orth_dots<K, false><<<npart, DOT_NT, 0, s>>>(V, ld, w, N, partials, npart, ticket, dots, norm2, gate);
+    launch_pdl(k_orth_dots<K, false>, dim3(npart), dim3(DOT_NT), 0, s, V, ld, w, N, partials, npart, ticket, dots, norm2, gate);
   }
 }
 
@@ -418,10 +430,10 @@ void update_k(bool norm, double* w, const double* V, long long ld, const double*
               const double* dgks_ref, double* flag, double* hacc, const double* coef_all, int nacc,
               cudaStream_t s) {
   if (norm)
-    k_orth_update<K, true><<<npart, DOT_NT, 0, s>>>(w, V, ld, coef, N, partials, npart, ticket, norm2, gate,
+    launch_pdl(k_orth_update<K, true>, dim3(npart), dim3(DOT_NT), 0, s, w, V, ld, coef, N, partials, npart, ticket, norm2, gate,
                                                     dgks_ref, flag, hacc, coef_all, nacc);
   else
-    k_orth_update<K, false><<<npart, DOT_NT, 0, s>>>(w, V, ld, coef, N, partials, npart, ticket, norm2, gate,
+    launch_pdl(k_orth_update<K, false>, dim3(npart), dim3(DOT_NT), 0, s, w, V, ld, coef, N, partials, npart, ticket, norm2, gate,
                                                      dgks_ref, flag, hacc, coef_all, nacc);
 }
 
@@ -432,7 +444,7 @@ void update_dots_k(double* w, const double* V, long long ld, const double* coef,
   if constexpr (K == 0) {
     (void)w;   // never launched: the caller passes at least one vector
   } else {
-    k_orth_update_dots<K><<<npart, DOT_NT, 0, s>>>(w, V, ld, coef, N, partials, npart, ticket, dots, norm2,
+    launch_pdl(k_orth_update_dots<K>, dim3(npart), dim3(DOT_NT), 0, s, w, V, ld, coef, N, partials, npart, ticket, dots, norm2,
                                                    dgks_ref, flag);
   }
 }
@@ -502,43 +514,43 @@ bool launch_orth_update_dots(double* w, const double* V, long long ld, int nk, c
 void launch_multiaxpy(double* w, const double* V, long long ld, int nk, const double* coef,
                       double sign, long long N, cudaStream_t s) {
   count_launches(1);
-  k_multiaxpy<<<grid_for(N, 256), 256, 0, s>>>(w, V, ld, nk, coef, sign, N);
+  launch_pdl(k_multiaxpy, dim3(grid_for(N, 256)), dim3(256), 0, s, w, V, ld, nk, coef, sign, N);
 }
 
 void launch_scale(double* y, const double* x, const double* den, double scal, long long N,
                   cudaStream_t s) {
   count_launches(1);
-  k_scale<<<grid_for(N, 256), 256, 0, s>>>(y, x, den, scal, N);
+  launch_pdl(k_scale, dim3(grid_for(N, 256)), dim3(256), 0, s, y, x, den, scal, N);
 }
 
 void launch_givens(double* H, int ldh, double* cs, double* sn, double* g, const double* hcol,
                    const double* hnorm, int j, double* est, cudaStream_t s) {
   count_launches(1);
-  k_givens<<<1, 32, 0, s>>>(H, ldh, cs, sn, g, hcol, hnorm, j, est);
+  launch_pdl(k_givens, dim3(1), dim3(32), 0, s, H, ldh, cs, sn, g, hcol, hnorm, j, est);
 }
 
 void launch_backsolve(const double* H, int ldh, const double* g, int k, double* y, cudaStream_t s) {
   count_launches(1);
-  k_backsolve<<<1, 32, 0, s>>>(H, ldh, g, k, y);
+  launch_pdl(k_backsolve, dim3(1), dim3(32), 0, s, H, ldh, g, k, y);
 }
 
 void launch_fill(double* p, double v, long long N, cudaStream_t s) {
   count_launches(1);
-  k_fill<<<grid_for(N, 256), 256, 0, s>>>(p, v, N);
+  launch_pdl(k_fill, dim3(grid_for(N, 256)), dim3(256), 0, s, p, v, N);
 }
 
 void launch_project_pressure(const LevelDev& L, const double* x, double* y, double* partials, int npart,
                              double* sum, cudaStream_t s) {
   count_launches(3);
   const long long p0 = 2 * L.nv, np2 = static_cast<long long>(L.np) * L.np;
-  k_partial_sum<<<npart, DOT_NT, 0, s>>>(x + p0, np2, partials);
-  k_reduce<<<1, 256, 0, s>>>(partials, npart, sum, 0);
-  k_copy_shift_pressure<<<grid_for(L.N, 256), 256, 0, s>>>(x, y, L.N, p0, sum, 1.0 / static_cast<double>(np2));
+  launch_pdl(k_partial_sum, dim3(npart), dim3(DOT_NT), 0, s, x + p0, np2, partials);
+  launch_pdl(k_reduce, dim3(1), dim3(256), 0, s, partials, npart, sum, 0);
+  launch_pdl(k_copy_shift_pressure, dim3(grid_for(L.N, 256)), dim3(256), 0, s, x, y, L.N, p0, sum, 1.0 / static_cast<double>(np2));
 }
 
 void launch_dirichlet_copy(const LevelDev& L, const double* src, double* dst, cudaStream_t s) {
   count_launches(1);
-  k_dirichlet_copy<<<grid_for(L.N, 256), 256, 0, s>>>(L, src, dst);
+  launch_pdl(k_dirichlet_copy, dim3(grid_for(L.N, 256)), dim3(256), 0, s, L, src, dst);
 }
 
 }  // namespace sv

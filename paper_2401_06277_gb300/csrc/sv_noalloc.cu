@@ -56,6 +56,7 @@ __device__ __forceinline__ double na_block_sum(double v) {
 // block r >= nq: squared residual of vertex row j = r - nq.  Partial -> scratch[r].
 __global__ void k_resnorm_rows(sv::LevelDev L, const double* __restrict__ b,
                                const double* __restrict__ x, double* __restrict__ scratch) {
+  sv::pdl_begin();
   const int r = blockIdx.x;
   const int nq = L.nq, np = L.np, n = L.n;
   const long long nv = L.nv;
@@ -127,6 +128,7 @@ __global__ void k_resnorm_rows(sv::LevelDev L, const double* __restrict__ b,
 
 // norm = sqrt(sum of the rows' partials), summed in a fixed order by one CTA.
 __global__ void k_resnorm_final(const double* __restrict__ scratch, int rows, double* __restrict__ norm) {
+  sv::pdl_begin();
   double s = 0.0;
   for (int r = threadIdx.x; r < rows; r += blockDim.x) s += scratch[r];
   const double t = na_block_sum(s);
@@ -190,8 +192,8 @@ extern "C" stokes_status stokes_residual_norm_noalloc(int n, double viscosity, c
   L.cbf = static_cast<float>(L.cb);
   const int rows = L.nq + L.np;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_resnorm_rows<<<rows, 256, 0, s>>>(L, b, x, scratch);
-  k_resnorm_final<<<1, 1024, 0, s>>>(scratch, rows, norm);
+  sv::launch_pdl(k_resnorm_rows, dim3(rows), dim3(256), 0, s, L, b, x, scratch);
+  sv::launch_pdl(k_resnorm_final, dim3(1), dim3(1024), 0, s, scratch, rows, norm);
   sv::count_launches(2);
   e = cudaGetLastError();
   if (e != cudaSuccess) {

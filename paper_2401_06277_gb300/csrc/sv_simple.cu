@@ -61,6 +61,7 @@ __device__ double patch_entry(const LevelDev& L, int pi, int pj, int s, int t) {
 // last pivot is minus the Schur complement b K^-1 b^T, so no pivoting is
 // needed), then the CTA writes its INV_WARPS inverses entry-major.
 __global__ void __launch_bounds__(32 * INV_WARPS) k_patch_inverse(LevelDev L, int P, double* __restrict__ inv) {
+  pdl_begin();
   extern __shared__ double sa[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int np = L.np, npatch = np * np;
@@ -97,6 +98,7 @@ __global__ void __launch_bounds__(32 * INV_WARPS) k_patch_inverse(LevelDev L, in
 // residual vector, delta is entry-major like the inverses.
 __global__ void __launch_bounds__(128) k_patch_solve(LevelDev L, int P, const double* __restrict__ inv,
                                                      const double* __restrict__ r, double* __restrict__ delta) {
+  pdl_begin();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const int np = L.np, nq = L.nq;
   if (p >= np * np) return;
@@ -148,6 +150,7 @@ __device__ __forceinline__ void update_node(const LevelDev& L, int P, const T* _
 template <typename T>
 __global__ void k_patch_update(LevelDev L, int P, const T* __restrict__ delta, const T* __restrict__ x,
                                T* __restrict__ xo, T omega) {
+  pdl_begin();
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y * blockDim.y + threadIdx.y;
   if (a > L.n || b > L.n) return;
@@ -179,7 +182,7 @@ cudaError_t simple_prepare() {
 void launch_patch_inverse(const LevelDev& L, double* inv, cudaStream_t s) {
   count_launches(1);
   const int npatch = L.np * L.np;
-  k_patch_inverse<<<(npatch + INV_WARPS - 1) / INV_WARPS, 32 * INV_WARPS, INV_WARPS * NS * NS * sizeof(double), s>>>(
+  launch_pdl(k_patch_inverse, dim3((npatch + INV_WARPS - 1) / INV_WARPS), dim3(32 * INV_WARPS), INV_WARPS * NS * NS * sizeof(double), s, 
       L, patch_stride(L), inv);
 }
 
@@ -187,7 +190,7 @@ template <typename T>
 void launch_patch_update(const LevelDev& L, int P, const T* delta, const T* x, T* xo, double omega, cudaStream_t s) {
   count_launches(1);
   dim3 blk(32, 8);
-  k_patch_update<T><<<dim3((L.np + 31) / 32, (L.np + 7) / 8), blk, 0, s>>>(L, P, delta, x, xo, T(omega));
+  launch_pdl(k_patch_update<T>, dim3(dim3((L.np + 31) / 32, (L.np + 7) / 8)), dim3(blk), 0, s, L, P, delta, x, xo, T(omega));
 }
 template void launch_patch_update<double>(const LevelDev&, int, const double*, const double*, double*, double,
                                           cudaStream_t);
@@ -203,7 +206,7 @@ void launch_simple_sweep(const LevelDev& L, const double* inv, double* delta, do
     r = rscratch;
   }
   count_launches(1);
-  k_patch_solve<<<(npatch + 127) / 128, 128, 0, s>>>(L, P, inv, r, delta);
+  launch_pdl(k_patch_solve, dim3((npatch + 127) / 128), dim3(128), 0, s, L, P, inv, r, delta);
   launch_patch_update(L, P, delta, x, xo, omega, s);
 }
 

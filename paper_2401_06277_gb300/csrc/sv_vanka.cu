@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
                                               const FastDiagT<R> fdg, const R* __restrict__ x,
                                               const R* __restrict__ b, R* __restrict__ xo, R omega,
                                               int skip_lo, int skip_hi) {
+  pdl_begin();
   using T = VT<TX, TY>;
   // With a non-empty [skip_lo, skip_hi] the tensor-core kernel sweeps the tiles
   // in that square and this launch enumerates the ring of tiles around it
@@ -394,6 +395,7 @@ template <typename R, int TX, int TY, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __restrict__ cd,
                                                   const FastDiagT<R> fdg, const R* __restrict__ x,
                                                   const R* __restrict__ b, R* __restrict__ delta, int P) {
+  pdl_begin();
   using T = VO<TX, TY>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sx = reinterpret_cast<R*>(smem_raw);
@@ -540,7 +542,7 @@ void launch_t(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x
     const int w = skip_hi - skip_lo + 1;
     grid = dim3(gx * gy - w * w, 1);
   }
-  k_vanka<R, TX, TY, NT><<<grid, NT, (VT<TX, TY>::TOTAL + EDGE_TAB) * sizeof(R), s>>>(L, cd, fd, x, b, xo,
+  launch_pdl(k_vanka<R, TX, TY, NT>, dim3(grid), dim3(NT), (VT<TX, TY>::TOTAL + EDGE_TAB) * sizeof(R), s, L, cd, fd, x, b, xo,
                                                                                     omega, skip_lo, skip_hi);
 }
 
@@ -600,9 +602,9 @@ void launch_vanka_split(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, 
   dim3 grid((L.np + 15) / 16, (L.np + 15) / 16);
   constexpr size_t smem = (VO<16, 16>::TOTAL + EDGE_TAB) * sizeof(R);
   if (two_per_sm)
-    k_vanka_own<R, 16, 16, 256, 2><<<grid, 256, smem, s>>>(L, cd, fd, x, b, delta, P);
+    launch_pdl(k_vanka_own<R, 16, 16, 256, 2>, dim3(grid), dim3(256), smem, s, L, cd, fd, x, b, delta, P);
   else
-    k_vanka_own<R, 16, 16, 256, 1><<<grid, 256, smem, s>>>(L, cd, fd, x, b, delta, P);
+    launch_pdl(k_vanka_own<R, 16, 16, 256, 1>, dim3(grid), dim3(256), smem, s, L, cd, fd, x, b, delta, P);
   launch_patch_update<R>(L, P, delta, x, xo, omega, s);
 }
 template void launch_vanka_split<double>(const LevelDev&, const double*, const FastDiag&, const double*,

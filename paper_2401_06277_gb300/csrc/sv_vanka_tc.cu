@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
                                                      const float* __restrict__ x,
                                                      const float* __restrict__ b, float* __restrict__ xo,
                                                      float omega, int tile0, int* __restrict__ err) {
+  pdl_begin();
   extern __shared__ __align__(1024) unsigned char sm[];
   float2* sx = reinterpret_cast<float2*>(sm + OFF_X);
   float* sp = reinterpret_cast<float*>(sm + OFF_P);
@@ -460,7 +461,7 @@ void launch_vanka_tc(const LevelDev& L, const void* Bcanon, const float* x, cons
   if (hi < lo) return;
   count_launches(1);
   const int g = hi - lo + 1;
-  k_vanka_tc<<<dim3(g, g), TC_NT, SMEM_BYTES, s>>>(L, static_cast<const uint4*>(Bcanon), x, b, xo,
+  launch_pdl(k_vanka_tc, dim3(dim3(g, g)), dim3(TC_NT), SMEM_BYTES, s, L, static_cast<const uint4*>(Bcanon), x, b, xo,
                                                    static_cast<float>(omega), lo, err);
 }
 
