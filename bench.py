@@ -150,6 +150,28 @@ def run_oracle(n: int, reps: int) -> dict:
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def run_oracle_all_cores(n: int, procs: int) -> dict:
+    """The oracle on every host core: `procs` single-threaded worker processes
+    (spawned, not forked) each solve the same n x n problem at the same time;
+    the aggregate is procs x dofs x V-cycles over the slowest worker's solve."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--n", str(n), "--steps", "1"]
+    ps = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT)
+          for _ in range(procs)]
+    outs = []
+    for p in ps:
+        so, se = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("oracle worker failed:\n" + se[-2000:])
+        outs.append(json.loads(so.strip().splitlines()[-1]))
+    slowest = max(o["solve_s"] for o in outs)
+    o = outs[0]
+    return {"n": n, "dofs": o["dofs"], "iters": o["iters"], "procs": procs, "solve_s_max": slowest,
+            "value": procs * o["dofs"] * o["iters"] / slowest}
+
+
 # --------------------------------------------------------------------------
 # distributed helpers
 # --------------------------------------------------------------------------
@@ -557,13 +579,19 @@ def run_ours(args) -> None:
     batched = None
     if not args.no_batch:
         batched = time_batch(args, "mixed")
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         o = run_oracle(ORACLE_N, 1)
         cpu = {"value": o["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"one FGMRES(30)+V(2,2) solve to 1e-8 at {o['n']}x{o['n']} ({o['dofs']} dofs, "
                          f"{o['iters']} V-cycles, {o['solve_s']:.2f} s; setup {o['setup_s']:.1f} s excluded), "
                          f"numpy/scipy, BLAS threads = 1"}
+        procs = os.cpu_count() or 1
+        oa = run_oracle_all_cores(ORACLE_N, procs)
+        cpu_all = {"value": oa["value"], "unit": UNIT, "cores": procs, "kind": "oracle",
+                   "sample": f"{procs} concurrent single-threaded oracle processes, one FGMRES(30)+V(2,2) solve "
+                             f"to 1e-8 at {oa['n']}x{oa['n']} each ({oa['iters']} V-cycles; slowest solve "
+                             f"{oa['solve_s_max']:.2f} s)"}
     if rank == 0:
         prec_txt = "FP64" if args.prec == "fp64" else "FP32 V-cycle inside FP64 FGMRES"
         line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -579,7 +607,8 @@ def run_ours(args) -> None:
                 "time_to_solution_s": main["time_to_solution_s"], "iters": main["iters"],
                 "relres": main["relres"], "vcycles": main["vcycles"], "ms_per_vcycle": main["ms_per_vcycle"],
                 "vcycle_only": main["vcycle_only"],
-                "roofline": main["roofline"], "cpu_baseline": cpu, "e2e": main["e2e"],
+                "roofline": main["roofline"], "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
+                "e2e": main["e2e"],
                 "gpu_launches": main["gpu_launches"], "clocks": main["clocks"], "forms": forms,
                 "batched": batched}
         print(json.dumps(line))
