@@ -256,9 +256,26 @@ ZERO_GUESS_SHARE = 1.0 / 4.0
 TILE_NAMES = ["8x8", "16x8", "16x16", "14x14", "split16x16", "split16x16x2"]
 
 
+VC_REPS = 20   # graph replays of the bare V-cycle (median reported)
+
+
 def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0, hkw=None, n=None):
     """Time K FGMRES solves of one precision form (smoother 1: per-patch inverses, the
-    paper's simple Vanka); returns the record."""
+    paper's simple Vanka); returns the record.  The form runs on a stream of its own
+    (not the legacy default stream), so that its bare V-cycle can be captured as a
+    CUDA graph."""
+    import torch
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        rec = _time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother, hkw, n)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    return rec
+
+
+def _time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother, hkw, n):
     import torch
 
     import paper_2401_06277_gb300 as pkg
@@ -409,19 +426,27 @@ def time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother=0, 
            "time_to_solution_s": ms_max / args.steps / 1e3, "roofline": roofline,
            "gpu_launches": launches, "clocks": clk, "levels": H.levels, "setup_s": t_setup}
     # the V-cycle alone (dofs per second of one preconditioner application), after the timed
-    # region: 10 applications to the assembled right-hand side, CUDA events on the stream
+    # region: one application to the assembled right-hand side captured as a CUDA graph,
+    # replayed VC_REPS times after warm-up, CUDA events between replays, median interval
     z = torch.empty_like(b)
     for _ in range(2):
         stokes.stokes_vcycle_apply(H.handle, b, z)
     torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(10):
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
         stokes.stokes_vcycle_apply(H.handle, b, z)
-    e1.record(stream)
+    for _ in range(3):
+        graph.replay()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(VC_REPS + 1)]
+    evs[0].record(stream)
+    for k in range(VC_REPS):
+        graph.replay()
+        evs[k + 1].record(stream)
     torch.cuda.synchronize()
-    vc_ms = allmax(ws, e0.elapsed_time(e1) / 10)
-    rec["vcycle_only"] = {"ms": vc_ms, "value": ws * N / (vc_ms * 1e-3), "unit": UNIT}
-    del z
+    vc_ms = allmax(ws, statistics.median(evs[k].elapsed_time(evs[k + 1]) for k in range(VC_REPS)))
+    rec["vcycle_only"] = {"ms": vc_ms, "value": ws * N / (vc_ms * 1e-3), "unit": UNIT,
+                          "timing": f"median of {VC_REPS} replays of a captured CUDA graph"}
+    del graph, z
     if with_e2e:
         x_host = torch.empty(N, dtype=torch.float64).pin_memory()
         bi = f_host.numel() * 8 + ud_host.numel() * 8
