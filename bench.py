@@ -594,7 +594,8 @@ def run_ours(args) -> None:
                                      ("fp64_braess_sarazin", "fp64", 2, None, None),
                                      ("mixed_braess_sarazin", "mixed", 2, None, None),
                                      ("fp64_block_triangular", "fp64", 0, {"precond": 1}, None),
-                                     ("fp64_schur_uzawa_256", "fp64", 3, su, 256)):
+                                     ("fp64_schur_uzawa_256", "fp64", 3, su, 256),
+                                     ("bf16_wcycle", "bf16", 0, {"cycle": 2}, None)):
             o = time_form(args, pn, ws, rank, f_host, ud_host, with_e2e=False, smoother=sm, hkw=kw, n=nn)
             forms[name] = {k: o[k] for k in keys}
             forms[name]["roofline"] = o["roofline"]
