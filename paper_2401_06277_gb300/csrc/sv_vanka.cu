@@ -35,6 +35,18 @@ using vk::vfree;
 using vk::res_node;
 using vk::inv_mult;
 
+// Packed FP32 arithmetic on (u_x, u_y) pairs (sm_100 and later): both velocity
+// components of a patch go through the same fast-diagonalisation transforms,
+// so the FP32 sweep runs them as one pass of FFMA2 / FADD2 / FMUL2, each lane
+// rounded exactly as the scalar operation (a - b as b * -1 + a).
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
+using ::fma;   // keep the scalar overloads visible beside the pair one
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 // Forward transform of one 5-vector into the generalised eigenbasis S^T v
 // (three symmetric, two antisymmetric eigenvectors, each scaled to 1 on the
 // pair {0, 4}, so the first term needs no multiply: 4 add/sub + 8 FMA).
@@ -158,7 +170,8 @@ __device__ __forceinline__ void fd_solve_edge(const T* __restrict__ sx, const T*
 
 template <typename R, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ cd,
-                                              const FastDiagT<R> fdg, const R* __restrict__ x,
+                                              const FastDiagT<R> fdg, const FastDiagT<float2> fdp,
+                                              const R* __restrict__ x,
                                               const R* __restrict__ b, R* __restrict__ xo, R omega,
                                               int skip_lo, int skip_hi) {
   pdl_begin();
@@ -307,12 +320,24 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
           const R bw = R(c == 0 ? crow(dI) * nrow(dJ) : nrow(dI) * crow(dJ));
           if (bw != R(0)) ru[c * 25 + w] = fma(-bw, q, ru[c * 25 + w]);
         }
+      if constexpr (sizeof(R) == 4) {   // FP32: both components in one packed pass
+        float2 r2[25], y2[25];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        R y[25];
-        fd_solve<R>(fdg, ru + c * 25, y);
+        for (int w = 0; w < 25; ++w) r2[w] = make_float2(ru[w], ru[25 + w]);
+        fd_solve<float2>(fdp, r2, y2);
 #pragma unroll
-        for (int o = 0; o < 25; ++o) D[c * 25 + o] = y[o];
+        for (int o = 0; o < 25; ++o) {
+          D[o] = y2[o].x;
+          D[25 + o] = y2[o].y;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          R y[25];
+          fd_solve<R>(fdg, ru + c * 25, y);
+#pragma unroll
+          for (int o = 0; o < 25; ++o) D[c * 25 + o] = y[o];
+        }
       }
     } else {
       const int fx = axis_free_mask(ax), fy = axis_free_mask(ay);
@@ -542,7 +567,14 @@ void launch_t(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x
     const int w = skip_hi - skip_lo + 1;
     grid = dim3(gx * gy - w * w, 1);
   }
-  launch_pdl(k_vanka<R, TX, TY, NT>, dim3(grid), dim3(NT), (VT<TX, TY>::TOTAL + EDGE_TAB) * sizeof(R), s, L, cd, fd, x, b, xo,
+  FastDiagT<float2> fp{};   // (v, v) pairs of the FP32 table for the packed interior solves
+  if constexpr (sizeof(R) == 4) {
+    for (int k = 0; k < 9; ++k) fp.se[k] = make_float2(static_cast<float>(fd.se[k]), static_cast<float>(fd.se[k]));
+    for (int k = 0; k < 4; ++k) fp.so[k] = make_float2(static_cast<float>(fd.so[k]), static_cast<float>(fd.so[k]));
+    for (int k = 0; k < 25; ++k)
+      fp.dinv[k] = make_float2(static_cast<float>(fd.dinv[k]), static_cast<float>(fd.dinv[k]));
+  }
+  launch_pdl(k_vanka<R, TX, TY, NT>, dim3(grid), dim3(NT), (VT<TX, TY>::TOTAL + EDGE_TAB) * sizeof(R), s, L, cd, fd, fp, x, b, xo,
                                                                                     omega, skip_lo, skip_hi);
 }
 
