@@ -20,11 +20,6 @@
 //   3. each thread writes its patch row of R, converted to BF16, into the
 //      K-major no-swizzle core-matrix layout (8 rows x 16 bytes per core
 //      matrix, LBO = 128 B along K, SBO = 1024 B along M);
-// The x and residual windows hold (u_x, u_y) pairs (float2), so a stencil tap
-// of both components is one 64-bit load and one packed FP32 FMA (FFMA2; the
-// two components share the Laplacian stencil), and are stored column-parity
-// split (the even nodes of a row, then the odd ones) with row pitches for which
-// the stencil, patch-gather and update loads are free of bank conflicts.
 //   4. thread 0 issues 2 x 4 tcgen05.mma (kind::f16, M=128, N=64, K=16) into
 //      TMEM and commits them to an mbarrier;
 //   5. after the wait, each thread reads its patch row of D with tcgen05.ld and
@@ -32,6 +27,11 @@
 //      residual buffers);
 //   6. x_out = x + (omega / m_j) * sum of the corrections of the patches that
 //      hold the dof, summed in a fixed order (deterministic, no atomics).
+// The x and residual windows hold (u_x, u_y) pairs (float2), so a stencil tap
+// of both components is one 64-bit load and one packed FP32 FMA (FFMA2; the
+// two components share the Laplacian stencil), and are stored column-parity
+// split (the even nodes of a row, then the odd ones) with row pitches for which
+// the stencil, patch-gather and update loads are free of bank conflicts.
 // Every wait is bounded; on expiry the kernel sets *err, waits (bounded) for
 // its bulk copy, frees its TMEM and returns.
 #include <cuda_bf16.h>
