@@ -230,10 +230,10 @@ def job_throughput(ws, units_local: float, ms_local: float) -> tuple[float, floa
 # kernel at 1024 x 1024 (ncu --set full, summaries in profiles/); at other sizes the
 # bench scales them by the number of dofs (the traffic of a sweep is proportional)
 TRAFFIC_1024 = {
-    "fp64": {"bytes": 155136512 + 377818880 + 505986560 + 66044672, "tile": "split16x16x2",
+    "fp64": {"bytes": 155278848 + 378243840 + 506067200 + 66107392, "tile": "split16x16x2",
              "source": "profiles/k_vanka_own_f64_n1024.md (k_vanka_own<double,16,16,256,2> + k_patch_update; "
                        "writes still in L2 at kernel end are not counted)"},
-    "bf16": {"bytes": 74803712 + 12058880, "tile": "14x14",
+    "bf16": {"bytes": 74801408 + 11694592, "tile": "14x14",
              "source": "profiles/k_vanka_tc_n1024.md (k_vanka_tc interior tiles; the ring launch is not "
                        "included; writes still in L2 at kernel end are not counted)"},
 }
