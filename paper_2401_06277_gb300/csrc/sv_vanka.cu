@@ -168,6 +168,36 @@ __device__ __forceinline__ void fd_solve_edge(const T* __restrict__ sx, const T*
   }
 }
 
+// Load a ROWS x WIDTH window (row-major, pitch WIDTH) of src (row stride ld):
+// element (jj, ii) is src[(J0 + jj) ld + I0 + ii] where ok(I, J), else 0.  Warp w
+// takes rows w, w + NW, ...; lane k columns k, k + 32: the row's validity and
+// address are formed once, and with compile-time extents every load is issued
+// before the stores.
+template <typename R, int ROWS, int WIDTH, int NW, typename OK>
+__device__ __forceinline__ void load_window(R* __restrict__ dst, const R* __restrict__ src, long long ld, int I0,
+                                            int J0, int warp, int lane, OK ok) {
+  constexpr int RPW = (ROWS + NW - 1) / NW, CPL = (WIDTH + 31) / 32;
+  R v[RPW][CPL];
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int jj = warp + k * NW, J = J0 + jj;
+#pragma unroll
+    for (int h = 0; h < CPL; ++h) {
+      const int ii = lane + 32 * h, I = I0 + ii;
+      v[k][h] = (jj < ROWS && ii < WIDTH && ok(I, J)) ? src[static_cast<long long>(J) * ld + I] : R(0);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < RPW; ++k) {
+    const int jj = warp + k * NW;
+#pragma unroll
+    for (int h = 0; h < CPL; ++h) {
+      const int ii = lane + 32 * h;
+      if (jj < ROWS && ii < WIDTH) dst[jj * WIDTH + ii] = v[k][h];
+    }
+  }
+}
+
 template <typename R, int TX, int TY, int NT>
 __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ cd,
                                               const FastDiagT<R> fdg, const FastDiagT<float2> fdp,
@@ -218,15 +248,15 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
 
   // 1. x windows (Dirichlet / outside entries read as 0: their columns are
   //    dropped), b on the residual windows (0 outside).
+  constexpr int NW = NT / 32;
+  static_assert(NT % 32 == 0, "whole warps");
+  const int warp = tid >> 5, lane = tid & 31;
+  const auto free_node = [nq](int I, int J) { return vfree(I, J, nq); };
+  const auto in_grid = [nq](int I, int J) { return I >= 0 && J >= 0 && I < nq && J < nq; };
   if (x != nullptr) {
 #pragma unroll
-    for (int t = tid; t < T::SX; t += NT) {
-      const int c = t / (T::XW * T::XH);
-      const int rem = t - c * T::XW * T::XH;
-      const int jj = rem / T::XW, ii = rem - jj * T::XW;
-      const int I = XI0 + ii, J = XJ0 + jj;
-      sx[t] = vfree(I, J, nq) ? x[c * nv + static_cast<long long>(J) * nq + I] : R(0);
-    }
+    for (int c = 0; c < 2; ++c)
+      load_window<R, T::XH, T::XW, NW>(sx + c * T::XW * T::XH, x + c * nv, nq, XI0, XJ0, warp, lane, free_node);
 #pragma unroll
     for (int t = tid; t < T::SP; t += NT) {
       const int jj = t / T::PW, ii = t - jj * T::PW;
@@ -235,13 +265,8 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
     }
   }
 #pragma unroll
-  for (int t = tid; t < T::SR; t += NT) {
-    const int c = t / (T::RW * T::RH);
-    const int rem = t - c * T::RW * T::RH;
-    const int jj = rem / T::RW, ii = rem - jj * T::RW;
-    const int I = RI0 + ii, J = RJ0 + jj;
-    sr[t] = (I >= 0 && J >= 0 && I < nq && J < nq) ? b[c * nv + static_cast<long long>(J) * nq + I] : R(0);
-  }
+  for (int c = 0; c < 2; ++c)
+    load_window<R, T::RH, T::RW, NW>(sr + c * T::RW * T::RH, b + c * nv, nq, RI0, RJ0, warp, lane, in_grid);
 #pragma unroll
   for (int t = tid; t < T::SRP; t += NT) {
     const int jj = t / T::QW, ii = t - jj * T::QW;
@@ -358,7 +383,46 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
   }
   __syncthreads();
 
-  // 4. weighted additive update of the owned dofs, W = omega / m_j
+  // 4. weighted additive update of the owned dofs, W = omega / m_j.  In a tile
+  //    whose owned vertices all lie in 1..n-1 every owned node is free and is
+  //    held by all 9 / 6 / 6 / 4 patches around it: one thread per owned vertex
+  //    sums them at compile-time slot offsets (patch q + (dj, di), slot of the
+  //    node), in the order of the general loop below, which serves the others.
+  if (i0 >= 1 && j0 >= 1 && i0 + TX <= n && j0 + TY <= n) {
+    static_assert(NT >= TX * TY, "one thread per owned vertex");
+    if (tid < TX * TY) {
+      const int vj = tid / TX, vi = tid - vj * TX;
+      const int i = i0 + vi, j = j0 + vj;
+      const R* dq = sd + ((vj + 1) * T::QW + (vi + 1)) * 51;   // the vertex's own patch
+      const int xj = 2 * j - XJ0, xi = 2 * i - XI0;              // x window at node (2i, 2j)
+      const long long base = static_cast<long long>(2 * j) * nq + 2 * i;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+#pragma unroll
+        for (int nj = 0; nj < 2; ++nj) {      // node J = 2j - nj
+#pragma unroll
+          for (int ni = 0; ni < 2; ++ni) {    // node I = 2i - ni
+            R acc = R(0);
+#pragma unroll
+            for (int dj = -1; dj <= 1; ++dj) {
+#pragma unroll
+              for (int di = -1; di <= 1; ++di) {
+                if ((ni == 1 && di == 1) || (nj == 1 && dj == 1)) continue;
+                const int wi = 2 - ni - 2 * di, wj = 2 - nj - 2 * dj;   // window offsets of the node
+                acc += dq[(dj * T::QW + di) * 51 + c * 25 + wj * 5 + wi];
+              }
+            }
+            const R w = omega * inv_mult<R>((ni ? 2 : 3) * (nj ? 2 : 3));
+            const R xold = x != nullptr ? sx[c * T::XW * T::XH + (xj - nj) * T::XW + (xi - ni)] : R(0);
+            xo[c * nv + base - static_cast<long long>(nj) * nq - ni] = fma(w, acc, xold);
+          }
+        }
+      }
+      const R xoldp = x != nullptr ? sp[(j - (j0 - 3)) * T::PW + (i - (i0 - 3))] : R(0);
+      xo[2 * nv + static_cast<long long>(j) * np + i] = fma(omega, dq[50], xoldp);
+    }
+    return;
+  }
   constexpr int OW = 2 * TX, OH = 2 * TY;
   for (int t = tid; t < 2 * OW * OH + TX * TY; t += NT) {
     if (t < 2 * OW * OH) {
