@@ -147,6 +147,31 @@ __device__ __forceinline__ void update_node(const LevelDev& L, int P, const T* _
   }
 }
 
+// The same for a vertex (a, b) with 1 <= a, b <= n - 1: every patch around its
+// nodes exists, so the patch ranges, the slots of the node and the multiplicity
+// are compile-time constants; the sum runs in the order of update_node.
+template <typename T, int PI, int PJ>
+__device__ __forceinline__ void update_node_interior(const LevelDev& L, int P, const T* __restrict__ delta,
+                                                     const T* __restrict__ x, T* __restrict__ xo, T omega, int a,
+                                                     int b) {
+  const int I = 2 * a + PI, J = 2 * b + PJ, nq = L.nq, np = L.np;
+  const T w = omega * vk::inv_mult<T>((PI ? 2 : 3) * (PJ ? 2 : 3));
+  const T* d0 = delta + static_cast<long long>(b) * np + a;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    T acc = T(0);
+#pragma unroll
+    for (int dj = (PJ ? 0 : -1); dj <= 1; ++dj)
+#pragma unroll
+      for (int di = (PI ? 0 : -1); di <= 1; ++di) {
+        const int slot = c * 25 + (PJ - 2 * dj + 2) * 5 + (PI - 2 * di + 2);
+        acc += d0[static_cast<long long>(slot) * P + dj * np + di];
+      }
+    const long long k = c * L.nv + static_cast<long long>(J) * nq + I;
+    xo[k] = fma(w, acc, x != nullptr ? x[k] : T(0));
+  }
+}
+
 template <typename T>
 __global__ void k_patch_update(LevelDev L, int P, const T* __restrict__ delta, const T* __restrict__ x,
                                T* __restrict__ xo, T omega) {
@@ -154,10 +179,17 @@ __global__ void k_patch_update(LevelDev L, int P, const T* __restrict__ delta, c
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   const int b = blockIdx.y * blockDim.y + threadIdx.y;
   if (a > L.n || b > L.n) return;
-  update_node<T, 0, 0>(L, P, delta, x, xo, omega, a, b);
-  update_node<T, 1, 0>(L, P, delta, x, xo, omega, a, b);
-  update_node<T, 0, 1>(L, P, delta, x, xo, omega, a, b);
-  update_node<T, 1, 1>(L, P, delta, x, xo, omega, a, b);
+  if (a >= 1 && b >= 1 && a <= L.n - 1 && b <= L.n - 1) {
+    update_node_interior<T, 0, 0>(L, P, delta, x, xo, omega, a, b);
+    update_node_interior<T, 1, 0>(L, P, delta, x, xo, omega, a, b);
+    update_node_interior<T, 0, 1>(L, P, delta, x, xo, omega, a, b);
+    update_node_interior<T, 1, 1>(L, P, delta, x, xo, omega, a, b);
+  } else {
+    update_node<T, 0, 0>(L, P, delta, x, xo, omega, a, b);
+    update_node<T, 1, 0>(L, P, delta, x, xo, omega, a, b);
+    update_node<T, 0, 1>(L, P, delta, x, xo, omega, a, b);
+    update_node<T, 1, 1>(L, P, delta, x, xo, omega, a, b);
+  }
   const int p = b * L.np + a;
   const long long k = 2 * L.nv + p;
   xo[k] = fma(omega, delta[static_cast<long long>(NS - 1) * P + p], x != nullptr ? x[k] : T(0));
