@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -40,6 +41,20 @@ stokes_status check_launch(const char* where) {
   return STOKES_OK;
 }
 
+struct UnitSchur {
+  double z[50];
+  double s;
+};
+
+const UnitSchur& unit_schur() {
+  static const UnitSchur u = [] {
+    UnitSchur v{};
+    sv::interior_unit_schur(v.z, &v.s);
+    return v;
+  }();
+  return u;
+}
+
 sv::LevelDev make_level(int n, double nu) {
   sv::LevelDev d;
   d.n = n;
@@ -53,6 +68,10 @@ sv::LevelDev make_level(int n, double nu) {
   d.cb = -d.h / 18.0;
   d.clf = static_cast<float>(d.cl);
   d.cbf = static_cast<float>(d.cb);
+  d.zs = d.cb / d.cl;
+  d.zsinv = 1.0 / (d.cb * d.zs * unit_schur().s);
+  d.zsf = static_cast<float>(d.zs);
+  d.zsinvf = static_cast<float>(d.zsinv);
   return d;
 }
 
@@ -711,6 +730,12 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   for (int k = 0; k < 25; ++k) h->fdf.dinv[k] = static_cast<float>(h->fd.dinv[k]);
   cudaError_t e = sv::vanka_prepare();
   if (e == cudaSuccess) e = sv::simple_prepare();
+  if (e == cudaSuccess) {
+    static std::once_flag z_once;
+    static cudaError_t z_err = cudaSuccess;
+    std::call_once(z_once, [] { z_err = sv::set_interior_unit_z(unit_schur().z); });
+    e = z_err;
+  }
   if (e == cudaSuccess && prm.prec == STOKES_MIXED_BF16) e = sv::vanka_tc_prepare();
   if (e == cudaSuccess && prm.prec == STOKES_MIXED_BF16) {
     e = cudaStreamCreateWithFlags(&h->ring_stream, cudaStreamNonBlocking);

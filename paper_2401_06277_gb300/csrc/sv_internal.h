@@ -105,6 +105,10 @@ struct LevelDev {
   double cl;   // nu / 90: scale of the integer Laplacian stencil
   double cb;   // -h / 18: scale of the integer divergence stencil
   float clf, cbf;   // the same in FP32 (formed on the host: FP32 kernels do no FP64 arithmetic)
+  // interior patches: z = K^-1 b^T = zs z_u with z_u the universal vector of the
+  // integer stencils (interior_unit_schur), 1 / s = zsinv
+  double zs, zsinv;
+  float zsf, zsinvf;
 };
 
 // cl and cb in the element type
@@ -120,6 +124,18 @@ template <>
 __host__ __device__ inline double level_cb<double>(const LevelDev& L) { return L.cb; }
 template <>
 __host__ __device__ inline float level_cb<float>(const LevelDev& L) { return L.cbf; }
+template <typename T>
+__host__ __device__ inline T level_zs(const LevelDev& L);
+template <>
+__host__ __device__ inline double level_zs<double>(const LevelDev& L) { return L.zs; }
+template <>
+__host__ __device__ inline float level_zs<float>(const LevelDev& L) { return L.zsf; }
+template <typename T>
+__host__ __device__ inline T level_zsinv(const LevelDev& L);
+template <>
+__host__ __device__ inline double level_zsinv<double>(const LevelDev& L) { return L.zsinv; }
+template <>
+__host__ __device__ inline float level_zsinv<float>(const LevelDev& L) { return L.zsinvf; }
 
 struct Level {
   LevelDev d;
@@ -214,6 +230,13 @@ inline void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_re
 // ---- host setup (sv_setup.cu) ----
 // Class data (Schur factors) for a level, and the 51 x 51 dense inverses.
 void build_class_data(int n, double nu, std::vector<double>& cd, std::vector<double>* full_inv);
+// The Schur data of an interior patch in the integer units of the stencils
+// (Section 6.3: all interior patches share one matrix): z_u = K_u^-1 b_u^T with
+// K_u = k (x) m + m (x) k and b_u = (C (x) N, N (x) C), s_u = b_u z_u.  A level
+// scales them: z = (cb / cl) z_u, s = cb (cb / cl) s_u.
+void interior_unit_schur(double* z50, double* s_unit);
+// Uploads z_u to the constant memory of the Vanka sweep kernels (once per process).
+cudaError_t set_interior_unit_z(const double* z50);
 // Dense N0 x N0 operator of a level (Dirichlet-eliminated), row-major.
 void dense_operator(int n, double nu, std::vector<double>& A);
 // G = leading N0 x N0 block of [[A, e], [e^T, 0]]^-1, e = (0, M_p 1).

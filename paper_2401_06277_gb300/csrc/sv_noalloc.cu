@@ -178,7 +178,7 @@ extern "C" stokes_status stokes_residual_norm_noalloc(int n, double viscosity, c
                        cudaGetErrorString(e));
     return STOKES_ERR_CUDA;
   }
-  sv::LevelDev L;
+  sv::LevelDev L{};   // fields this residual kernel does not use stay zero
   L.n = n;
   L.nq = 2 * n + 1;
   L.np = n + 1;

@@ -71,6 +71,34 @@ double lap_entry(int I, int J, int I2, int J2, double nu) {
 
 }  // namespace
 
+void interior_unit_schur(double* z50, double* s_unit) {
+  // slot s of the window: offset (s % 5 - 2, s / 5 - 2) from the vertex node, whose
+  // coordinates are even, so the node parities are those of s % 5 and s / 5
+  std::vector<double> K(625, 0.0);
+  for (int a = 0; a < 25; ++a)
+    for (int t = 0; t < 25; ++t) {
+      const int PI = (a % 5) & 1, PJ = (a / 5) & 1, dI = t % 5 - a % 5, dJ = t / 5 - a / 5;
+      K[a * 25 + t] = k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ);
+    }
+  invert_dense(K, 25);
+  double sum = 0.0;
+  for (int o = 0; o < 25; ++o) {
+    double zx = 0.0, zy = 0.0;
+    for (int k = 0; k < 25; ++k) {
+      const int dI = k % 5 - 2, dJ = k / 5 - 2;
+      zx += K[o * 25 + k] * (crow(dI) * nrow(dJ));
+      zy += K[o * 25 + k] * (nrow(dI) * crow(dJ));
+    }
+    z50[o] = zx;
+    z50[25 + o] = zy;
+  }
+  for (int k = 0; k < 25; ++k) {
+    const int dI = k % 5 - 2, dJ = k / 5 - 2;
+    sum += crow(dI) * nrow(dJ) * z50[k] + nrow(dI) * crow(dJ) * z50[25 + k];
+  }
+  *s_unit = sum;
+}
+
 void build_class_data(int n, double nu, std::vector<double>& cd, std::vector<double>* full_inv) {
   const int nq = 2 * n + 1;
   const double h = 1.0 / n;

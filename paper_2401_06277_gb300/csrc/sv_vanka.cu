@@ -35,6 +35,36 @@ using vk::vfree;
 using vk::res_node;
 using vk::inv_mult;
 
+// z_u of the interior patches (interior_unit_schur), in each precision: indexed
+// by compile-time slots, it is read as a constant-bank operand of the FMAs.
+__constant__ double c_zu[50];
+__constant__ float c_zu_f[50];
+template <typename R>
+__device__ __forceinline__ R zu(int k);
+template <>
+__device__ __forceinline__ double zu<double>(int k) { return c_zu[k]; }
+template <>
+__device__ __forceinline__ float zu<float>(int k) { return c_zu_f[k]; }
+
+// dp of a patch (Schur step, Section 6.3): (z . r_u - r_p) / s.  In FP32 a warp
+// whose patches are all interior takes z = zs z_u from constant memory (50 fewer
+// loads per patch); otherwise, and in FP64 (where the loads run beside the busy
+// FP64 pipe and the constant path measured slower), z and 1 / s come from the
+// patch's class data.
+template <typename R>
+__device__ __forceinline__ R schur_dp(bool warp_interior, const LevelDev& L, const R* __restrict__ C,
+                                      const R (&ru)[50], R rp) {
+  R zr = R(0);
+  if (sizeof(R) == 4 && warp_interior) {
+#pragma unroll
+    for (int k = 0; k < 50; ++k) zr = fma(zu<R>(k), ru[k], zr);
+    return (level_zs<R>(L) * zr - rp) * level_zsinv<R>(L);
+  }
+#pragma unroll
+  for (int k = 0; k < 50; ++k) zr = fma(__ldg(C + CD_Z + k), ru[k], zr);
+  return (zr - rp) * __ldg(C + CD_SINV);
+}
+
 // Packed FP32 arithmetic on (u_x, u_y) pairs (sm_100 and later): both velocity
 // components of a patch go through the same fast-diagonalisation transforms,
 // so the FP32 sweep runs them as one pass of FFMA2 / FADD2 / FMUL2, each lane
@@ -324,16 +354,14 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
 #pragma unroll
         for (int wi = 0; wi < 5; ++wi)
           ru[c * 25 + wj * 5 + wi] = sr[c * T::RW * T::RH + (2 * qj + wj) * T::RW + 2 * qi + wi];
-    R zr = R(0);
-#pragma unroll
-    for (int k = 0; k < 50; ++k) zr = fma(__ldg(C + CD_Z + k), ru[k], zr);
-    const R dp = (zr - srp[t]) * __ldg(C + CD_SINV);
+    const bool warp_interior = !__any_sync(__activemask(), cls != INTERIOR_CLASS);
+    const R dp = schur_dp<R>(warp_interior, L, C, ru, srp[t]);
     R* D = sd + t * 51;
     // K^-1 r_u by fast diagonalisation (exact up to rounding): warps whose
     // patches are all interior use the symmetric/antisymmetric split of the
     // interior factors; a warp with any boundary-class patch takes the
     // per-axis factors for all of its patches (one path per warp)
-    if (!__any_sync(__activemask(), cls != INTERIOR_CLASS)) {
+    if (warp_interior) {
       // du = K^-1 r_u - z dp = K^-1 (r_u - b^T dp): the coupling b^T of an interior
       // patch is the compile-time stencil cb (C (x) N) / cb (N (x) C), 12 entries per component
       const R q = cb * dp;
@@ -579,13 +607,11 @@ __global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __r
 #pragma unroll
         for (int wi = 0; wi < 5; ++wi)
           ru[c * 25 + wj * 5 + wi] = sr[c * T::RW * T::RH + (2 * qj + wj) * T::RW + 2 * qi + wi];
-    R zr = R(0);
-#pragma unroll
-    for (int k = 0; k < 50; ++k) zr = fma(__ldg(C + CD_Z + k), ru[k], zr);
-    const R dp = (zr - srp[t]) * __ldg(C + CD_SINV);
+    const bool warp_interior = !__any_sync(__activemask(), cls != INTERIOR_CLASS);
+    const R dp = schur_dp<R>(warp_interior, L, C, ru, srp[t]);
     const int p = pj * np + pi;
     R* D = delta + p;
-    if (!__any_sync(__activemask(), cls != INTERIOR_CLASS)) {
+    if (warp_interior) {
       const R q = cb * dp;
 #pragma unroll
       for (int c = 0; c < 2; ++c)
@@ -658,6 +684,14 @@ cudaError_t prepare_all() {
 }
 
 }  // namespace
+
+cudaError_t set_interior_unit_z(const double* z50) {
+  float zf[50];
+  for (int k = 0; k < 50; ++k) zf[k] = static_cast<float>(z50[k]);
+  cudaError_t e = cudaMemcpyToSymbol(c_zu, z50, 50 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_zu_f, zf, 50 * sizeof(float));
+  return e;
+}
 
 cudaError_t vanka_prepare() {
   const int smem_own = static_cast<int>((VO<16, 16>::TOTAL + EDGE_TAB) * sizeof(double));
