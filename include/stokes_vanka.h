@@ -138,7 +138,11 @@ void stokes_default_params(stokes_params* p);
  * (Section 6.3) and the coarse-grid inverse.  n must be coarse_n * 2^k with
  * coarse_n >= 4.  viscosity > 0.  params may be NULL (defaults).  stream is a
  * cudaStream_t (NULL = legacy default stream).  The Krylov workspace
- * (2 restart + 1 vectors of N(n) doubles) is allocated here. */
+ * (2 restart + 1 vectors of N(n) doubles) is allocated here.  A BF16
+ * hierarchy also owns a second (non-blocking) stream and two events: each
+ * sweep forks the SIMT ring of boundary tiles onto that stream and joins it
+ * back, so every call stays ordered on `stream` (also under stream capture);
+ * stokes_hierarchy_destroy synchronises and releases them. */
 stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_params* params,
                                       void* stream, stokes_hierarchy** out);
 stokes_status stokes_hierarchy_destroy(stokes_hierarchy* h);
@@ -149,7 +153,7 @@ stokes_status stokes_level_n(const stokes_hierarchy* h, int level, int* n_level)
 /* Sweep configuration used on a level (see stokes_params.tile).  In the BF16
  * form, 3 on a level where the tensor-core tile fits means the tensor-core
  * sweep (interior tiles) with its 14x14 SIMT ring; the autotuner may choose a
- * SIMT shape (0..2) there instead. */
+ * SIMT shape (0..2, or the split sweep 4, 5) there instead. */
 stokes_status stokes_level_tile(const stokes_hierarchy* h, int level, int* tile);
 
 /* Right-hand side of the eliminated system (Section 2.2 with the boundary data
