@@ -21,6 +21,16 @@
 // In FP64 the kernel is bound by the FP64 pipe on GB300 (2 DFMA / clk / SM).
 // The tile shape trades halo recomputation against shared memory per CTA and
 // is chosen per level by a timing autotuner at hierarchy creation.
+//
+// Issue-slot economies: window rows load one warp per row with compile-time
+// extents; on tiles whose owned vertices lie in 1..n-1 the update sums each
+// node's patch corrections at compile-time slot offsets; in FP32 the interior
+// patch solves of u_x and u_y run as one packed pass (FFMA2 on component
+// pairs) and the interior Schur vector is read from constant memory.
+//
+// The split sweep below (k_vanka_own + k_patch_update) solves only a tile's
+// own patches and passes the corrections through HBM: the better trade where
+// the FP64 pipe is the bound.
 #include <cuda_runtime.h>
 
 #include "sv_internal.h"
