@@ -350,12 +350,12 @@ def _time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother, h
                     "traffic": None, "note": "no Vanka/Braess-Sarazin sweep to time; see vcycle_only"}
     elif smoother in (2, 3):
         # Braess-Sarazin (two Jacobi steps) per vertex: residual 361, g and diag(S) 2 x 48,
-        # D^-1 B^T dp 2 x 4 x 9 + 8, B q 48 + 4, du 2 x 4 x (9 + 3) + 2 x 9: ~700 flops.  Vector
-        # passes: residual 3 (x, b -> r); g 1 + 3 pressure (-> g, diag(S), dp); D^-1 B^T dp
-        # 1 pressure + 2 velocity components; Jacobi 2 components + 4 pressure; update 3 + 1 pressure
+        # Jacobi step with S dp as a 21-tap vertex stencil 2 x 21 + 4, du 2 x 4 x (9 + 3) + 2 x 9:
+        # ~620 flops.  Vector passes: residual 3 (x, b -> r); g 1 + 3 pressure (-> g, diag(S),
+        # dp); Jacobi 4 pressure (dp, g, diag(S) -> dp); update 3 + 1 pressure
         esz = 8.0 if prec_name == "fp64" else 4.0
-        fl = (n + 1) ** 2 * 700.0
-        by = esz * (7.0 * dofs(n) + 4.0 * (2 * n + 1) ** 2 + 9.0 * (n + 1) ** 2)
+        fl = (n + 1) ** 2 * 620.0
+        by = esz * (7.0 * dofs(n) + 8.0 * (n + 1) ** 2)
         if prec_name == "fp64":
             peak = SM_COUNT * 4 * sm_max * 1e6 / 1e9
             achieved = fl / (sweep_ms * 1e-3) / 1e9

@@ -6,8 +6,8 @@
 //   r = b - A x                                              (k_apply)
 //   g = r_p - (1/t) B D^-1 r_u,  diag(S),  dp = w_J g / diag(S)   (k_bs_rhs)
 //   repeat jacobi_iters - 1 times:
-//     q = D^-1 B^T dp                                        (k_bs_dinv_btp)
-//     dp += w_J (g - S dp) / diag(S),  S dp = -(1/t) B q      (k_bs_jacobi)
+//     dp += w_J (g - S dp) / diag(S)                         (k_bs_jacobi_s: S dp
+//       from dp directly, a 5 x 5 vertex stencil away from the boundary)
 //   du = (1/t) D^-1 (r_u - B^T dp);  x_out = x + omega_BS (du, dp)   (k_bs_update)
 //
 // Schur-Uzawa solves the block lower-triangular system [[tD, 0], [B, S]]: its
@@ -108,59 +108,74 @@ __device__ __forceinline__ void load_p3(const LevelDev& L, const T* __restrict__
     }
 }
 
-// q = D^-1 B^T dp on the velocity nodes of vertex (a, b) (0 on Dirichlet nodes)
-template <typename T, int PI, int PJ>
-__device__ __forceinline__ void dinv_btp_node(const LevelDev& L, const T (&P)[3][3], T* __restrict__ q, T cbicl,
-                                              int a, int b) {
-  const int I = 2 * a + PI, J = 2 * b + PJ, nq = L.nq;
-  if (I >= nq || J >= nq) return;
-  const long long k = static_cast<long long>(J) * nq + I;
-  const bool fr = bs_free(I, J, nq);
-  const T f = cbicl * T(1.0 / dcoef(PI, PJ));
-  q[k] = fr ? f * btp3<T, PI, PJ, 0>(P) : T(0);
-  q[L.nv + k] = fr ? f * btp3<T, PI, PJ, 1>(P) : T(0);
-}
-
-template <typename T>
-__global__ void k_bs_dinv_btp(LevelDev L, const T* __restrict__ dp, T* __restrict__ q, BSC<T> k) {
-  pdl_begin();
-  const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
-  if (a > L.n || b > L.n) return;
-  T P[3][3];
-  load_p3(L, dp, a, b, P);
-  const T cbicl = k.cb * k.icl;
-  dinv_btp_node<T, 0, 0>(L, P, q, cbicl, a, b);
-  dinv_btp_node<T, 1, 0>(L, P, q, cbicl, a, b);
-  dinv_btp_node<T, 0, 1>(L, P, q, cbicl, a, b);
-  dinv_btp_node<T, 1, 1>(L, P, q, cbicl, a, b);
-}
-
-// dp += w_J (g - S dp) / diag(S),  S dp = -(1/t) B q
-template <typename T>
-__global__ void k_bs_jacobi(LevelDev L, const T* __restrict__ q, const T* __restrict__ g, const T* __restrict__ ds,
-                            T* __restrict__ dp, BSC<T> kc) {
-  pdl_begin();
-  const T inv_t = kc.inv_t, wj = kc.wj;
-  const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
-  const int n = L.n, nq = L.nq;
-  if (a > n || b > n) return;
-  const long long nv = L.nv;
-  T s = T(0);
-#pragma unroll
-  for (int dJ = -2; dJ <= 2; ++dJ)
-#pragma unroll
-    for (int dI = -2; dI <= 2; ++dI) {
-      const double wx = crow(dI) * nrow(dJ), wy = nrow(dI) * crow(dJ);
-      if (wx == 0.0 && wy == 0.0) continue;
-      const int I = 2 * a + dI, J = 2 * b + dJ;
-      if (I < 0 || J < 0 || I >= nq || J >= nq) continue;   // q is 0 on Dirichlet nodes
-      const long long k = static_cast<long long>(J) * nq + I;
-      if (wx != 0.0) s = fma(T(wx), q[k], s);
-      if (wy != 0.0) s = fma(T(wy), q[nv + k], s);
+// Entry (v, v + o) of S / (-(1/t) cb^2 / cl) for a vertex v whose 5 x 5 node
+// window is free: sum over the window's nodes n (offset from node 2v) of
+// (w_x(n) w_x(n - 2o) + w_y(n) w_y(n - 2o)) / dcoef(parities of n), with
+// w_x = C (x) N and w_y = N (x) C the integer B weights.  o = 0 gives diag(S).
+__host__ __device__ constexpr double s_coef(int ox, int oy) {
+  double s = 0.0;
+  for (int nJ = -2; nJ <= 2; ++nJ)
+    for (int nI = -2; nI <= 2; ++nI) {
+      const int mI = nI - 2 * ox, mJ = nJ - 2 * oy;
+      if (mI < -2 || mI > 2 || mJ < -2 || mJ > 2) continue;
+      const double id = 1.0 / dcoef(nI & 1, nJ & 1);
+      s += (crow(nI) * nrow(nJ) * crow(mI) * nrow(mJ) + nrow(nI) * crow(nJ) * nrow(mI) * crow(mJ)) * id;
     }
-  const int p = b * L.np + a;
-  const T sdp = -inv_t * kc.cb * s;
-  dp[p] = fma(wj, (g[p] - sdp) / ds[p], dp[p]);
+  return s;
+}
+
+// One Jacobi step on S with S dp formed directly from dp: dp_out = dp_in + w_J (g -
+// S dp_in) / diag(S).  Vertices 2..n-2 apply the 5 x 5 vertex stencil s_coef
+// (compile-time); the others compose S = -(1/t) B D^-1 B^T over their free
+// nodes.  Replaces q = D^-1 B^T dp through HBM (two velocity components) and a
+// second pass; dp_out must not alias dp_in.
+template <typename T>
+__global__ void k_bs_jacobi_s(LevelDev L, const T* __restrict__ dpi, const T* __restrict__ g,
+                              const T* __restrict__ ds, T* __restrict__ dpo, BSC<T> kc) {
+  pdl_begin();
+  const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = L.n, nq = L.nq, np = L.np;
+  if (a > n || b > n) return;
+  T s = T(0);
+  if (a >= 2 && a <= n - 2 && b >= 2 && b <= n - 2) {
+    const T* d0 = dpi + static_cast<long long>(b) * np + a;
+#pragma unroll
+    for (int oy = -2; oy <= 2; ++oy)
+#pragma unroll
+      for (int ox = -2; ox <= 2; ++ox) {
+        const double c = s_coef(ox, oy);
+        if (c != 0.0) s = fma(T(c), d0[oy * np + ox], s);
+      }
+  } else {
+#pragma unroll
+    for (int dJ = -2; dJ <= 2; ++dJ)
+#pragma unroll
+      for (int dI = -2; dI <= 2; ++dI) {
+        const double wx = crow(dI) * nrow(dJ), wy = nrow(dI) * crow(dJ);
+        if (wx == 0.0 && wy == 0.0) continue;
+        const int I = 2 * a + dI, J = 2 * b + dJ;
+        if (!bs_free(I, J, nq)) continue;   // D^-1 B^T dp is 0 on Dirichlet nodes
+        T qx = T(0), qy = T(0);
+#pragma unroll
+        for (int oy = -2; oy <= 2; ++oy)
+#pragma unroll
+          for (int ox = -2; ox <= 2; ++ox) {
+            const int mI = dI - 2 * ox, mJ = dJ - 2 * oy;
+            if (mI < -2 || mI > 2 || mJ < -2 || mJ > 2) continue;
+            const double vx = crow(mI) * nrow(mJ), vy = nrow(mI) * crow(mJ);
+            if (vx == 0.0 && vy == 0.0) continue;
+            const int i = a + ox, j = b + oy;
+            if (i < 0 || j < 0 || i > n || j > n) continue;
+            const T pv = dpi[static_cast<long long>(j) * np + i];
+            if (vx != 0.0) qx = fma(T(vx), pv, qx);
+            if (vy != 0.0) qy = fma(T(vy), pv, qy);
+          }
+        s = fma(T(1.0 / dcoef(dI & 1, dJ & 1)), T(wx) * qx + T(wy) * qy, s);
+      }
+  }
+  const int p = b * np + a;
+  const T sdp = -kc.inv_t * kc.cb * kc.cb * kc.icl * s;
+  dpo[p] = fma(kc.wj, (g[p] - sdp) / ds[p], dpi[p]);
 }
 
 // du = (1/t) D^-1 (r_u - B^T dp) (Braess-Sarazin) or (1/t) D^-1 r_u (Schur-Uzawa, UZ);
@@ -219,7 +234,7 @@ template <typename T>
 void launch_bs_sweep(const LevelDev& L, const BSParams& prm, T* scratch, T* rbuf, const T* x, const T* b, T* xo,
                      cudaStream_t s) {
   const long long np2 = static_cast<long long>(L.np) * L.np;
-  T* q = scratch;                 // 2 nv
+  T* q = scratch;                 // 2 nv: the second dp buffer of the Jacobi steps
   T* g = q + 2 * L.nv;            // np^2 each
   T* ds = g + np2;
   T* dp = ds + np2;
@@ -230,11 +245,15 @@ void launch_bs_sweep(const LevelDev& L, const BSParams& prm, T* scratch, T* rbuf
   }
   const BSC<T> k{T(L.cb), T(1.0 / L.cl), T(1.0 / prm.t), T(prm.jacobi_weight), T(prm.omega)};
   dim3 blk(32, 8), grid((L.np + 31) / 32, (L.np + 7) / 8);
-  count_launches(2 + 2 * (prm.jacobi_iters - 1));
+  count_launches(2 + (prm.jacobi_iters - 1));
   launch_pdl(k_bs_rhs<T>, dim3(grid), dim3(blk), 0, s, L, r, g, ds, dp, k);
+  T* dp_other = q;
   for (int it = 1; it < prm.jacobi_iters; ++it) {
-    launch_pdl(k_bs_dinv_btp<T>, dim3(grid), dim3(blk), 0, s, L, dp, q, k);
-    launch_pdl(k_bs_jacobi<T>, dim3(grid), dim3(blk), 0, s, L, q, g, ds, dp, k);
+    launch_pdl(k_bs_jacobi_s<T>, dim3(grid), dim3(blk), 0, s, L, static_cast<const T*>(dp), static_cast<const T*>(g),
+               static_cast<const T*>(ds), dp_other, k);
+    T* t = dp;
+    dp = dp_other;
+    dp_other = t;
   }
   if (prm.uzawa)
     launch_pdl(k_bs_update<T, true>, dim3(grid), dim3(blk), 0, s, L, r, dp, x, xo, k);
