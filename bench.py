@@ -256,7 +256,7 @@ ZERO_GUESS_SHARE = 1.0 / 4.0
 # sweep configurations by stokes_level_tile: fused tiles of TX x TY vertices, or (4, 5; FP64
 # only) the split sweep: 16 x 16 own-patch solves writing the corrections, then the update
 # (5: compiled for two CTAs per SM)
-TILE_NAMES = ["8x8", "16x8", "16x16", "14x14", "split16x16", "split16x16x2"]
+TILE_NAMES = ["8x8", "16x8", "16x16", "14x14", "split16x16", "split16x16x2", "4x4"]
 
 
 VC_REPS = 20   # graph replays of the bare V-cycle (median reported)
@@ -741,7 +741,7 @@ def main():
     ap.add_argument("--batch-rhs", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--oracle-worker", action="store_true")
-    ap.add_argument("--tile", type=int, default=-1, help="Vanka sweep configuration (-1: autotuned; 0..3 fused 8x8/16x8/16x16/14x14, 4/5 split 16x16, FP64)")
+    ap.add_argument("--tile", type=int, default=-1, help="Vanka sweep configuration (-1: autotuned; 0..3 fused 8x8/16x8/16x16/14x14, 4/5 split 16x16, 6 fused 4x4)")
     ap.add_argument("--kernel", choices=["sweep", "residual", "vcycle"], default=None,
                     help="time one kernel alone on the finest level (profiling mode)")
     ap.add_argument("--smoother", type=int, choices=[0, 1, 2, 3], default=0,

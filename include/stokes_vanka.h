@@ -82,7 +82,8 @@ typedef struct {
                        tensor-core sweep where it fits); 4 = split sweep
                        (16x16 own-patch solves writing the corrections, then a
                        separate update), 5 = the same compiled for two CTAs
-                       per SM                                          (-1) */
+                       per SM, 6 = fused 4x4 tiles (small levels: more
+                       CTAs)                                           (-1) */
   int smoother;     /* stokes_smoother below                             (0)  */
   /* Braess-Sarazin / Schur-Uzawa relaxation (smoothers 2, 3; Sections 3.1, 3.3): D =
    * diag(L) scaled by bs_t, S = -(1/bs_t) B D^-1 B^T relaxed by bs_jacobi_iters
@@ -153,7 +154,7 @@ stokes_status stokes_level_n(const stokes_hierarchy* h, int level, int* n_level)
 /* Sweep configuration used on a level (see stokes_params.tile).  In the BF16
  * form, 3 on a level where the tensor-core tile fits means the tensor-core
  * sweep (interior tiles) with its 14x14 SIMT ring; the autotuner may choose a
- * SIMT shape (0..2, or the split sweep 4, 5) there instead. */
+ * SIMT shape (0..2, 6, or the split sweep 4, 5) there instead. */
 stokes_status stokes_level_tile(const stokes_hierarchy* h, int level, int* tile);
 
 /* Right-hand side of the eliminated system (Section 2.2 with the boundary data

@@ -166,7 +166,7 @@ void sweep_f64(stokes_hierarchy* h, sv::Level& L, const double* x, const double*
     sv::launch_bs_sweep<double>(L.d, h->bs, static_cast<double*>(h->bs_buf), L.r, x, b, xo, h->stream);
   else if (h->prm.smoother == STOKES_SMOOTHER_PER_PATCH)
     sv::launch_simple_sweep(L.d, L.pinv, h->delta, L.r, x, b, xo, h->prm.omega, h->stream);
-  else if (L.vk_cfg >= sv::VANKA_CFG_SPLIT)
+  else if (sv::vanka_cfg_split(L.vk_cfg))
     sv::launch_vanka_split<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, h->delta, L.vk_cfg == sv::VANKA_CFG_SPLIT2,
                            h->stream);
   else
@@ -205,7 +205,7 @@ void timed_sweep<float>(stokes_hierarchy* h, bool finest, sv::Level& L, const fl
     sv::launch_bs_sweep<float>(L.d, h->bs, static_cast<float*>(h->bs_buf), L.rf, x, b, xo, h->stream);
   } else if (L.tcB != nullptr && L.tc_hi >= L.tc_lo && L.tc_on) {
     tc_sweep(h, L, x, b, xo, h->stream);
-  } else if (L.vk_cfg_f >= sv::VANKA_CFG_SPLIT) {
+  } else if (sv::vanka_cfg_split(L.vk_cfg_f)) {
     sv::launch_vanka_split<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, h->deltaf,
                                   L.vk_cfg_f == sv::VANKA_CFG_SPLIT2, h->stream);
   } else {
@@ -547,8 +547,8 @@ stokes_status fgmres(stokes_hierarchy* h, const double* b, double* x, int* iters
 
 // Tile shape of the sweep per level and precision: fixed by params.tile, or
 // (tile = -1) the fastest of the shapes on that level, timed with CUDA events
-// on the hierarchy's stream (levels below 64 x 64 use 8 x 8: too few tiles
-// otherwise).
+// on the hierarchy's stream.  Every level with sweeps is tuned: on the small
+// ones the 4 x 4 tile spreads the FP64 patch solves over more SMs.
 template <typename R>
 cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
   cudaStream_t s = h->stream;
@@ -569,14 +569,14 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
   // candidates: the fused tile shapes; in FP64 also the split sweep; in the BF16
   // form (tensor-core image present) also the tensor-core sweep with its ring
   const bool tc = (sizeof(R) == 4) && L.tcB != nullptr && L.tc_hi >= L.tc_lo;
-  constexpr int CAND_TC = sv::VANKA_CFG_SPLIT2 + 1;   // the tensor-core sweep (BF16 form), tuning index only
-  const int ncand = tc ? CAND_TC + 1 : sv::VANKA_CFG_SPLIT2 + 1;
+  constexpr int CAND_TC = sv::VANKA_CFG_4 + 1;   // the tensor-core sweep (BF16 form), tuning index only
+  const int ncand = tc ? CAND_TC + 1 : sv::VANKA_CFG_4 + 1;
   int best_c = 0;
   for (int c = 0; c < ncand; ++c) {
     if (tc && c == sv::VANKA_CFG_14) continue;   // where the tensor-core tile fits, 14x14 means tensor cores
     auto run = [&]() {
       if constexpr (sizeof(R) == 8) {
-        if (c >= sv::VANKA_CFG_SPLIT)
+        if (sv::vanka_cfg_split(c))
           sv::launch_vanka_split<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, h->delta,
                                          c == sv::VANKA_CFG_SPLIT2, s);
         else
@@ -584,7 +584,7 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
       } else {
         if (c == CAND_TC) {
           tc_sweep(h, L, x, b, xo, s);
-        } else if (c >= sv::VANKA_CFG_SPLIT) {
+        } else if (sv::vanka_cfg_split(c)) {
           sv::launch_vanka_split<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, h->deltaf,
                                         c == sv::VANKA_CFG_SPLIT2, s);
         } else {
@@ -625,8 +625,7 @@ cudaError_t choose_tiles(stokes_hierarchy* h) {
       continue;
     }
     L.vk_cfg = L.vk_cfg_f = (L.d.n < 64) ? 0 : 1;
-    const bool tc_level = h->prm.prec == STOKES_MIXED_BF16 && L.tcB != nullptr && L.tc_hi >= L.tc_lo;
-    if (L.d.n < 64 && !tc_level) continue;
+    if (&L == &h->lv.front()) continue;   // the coarsest level is solved exactly: no sweeps
     // only the precision the V-cycle runs in is tuned (the FP64 sweep of a
     // mixed hierarchy serves stokes_vanka_sweep alone and keeps 16x8)
     cudaError_t e = cudaSuccess;
@@ -686,7 +685,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
     return fail(STOKES_ERR_ARG, "bad smoothing / iteration parameters");
   if (prm.prec != STOKES_FP64 && prm.prec != STOKES_MIXED_FP32 && prm.prec != STOKES_MIXED_BF16)
     return fail(STOKES_ERR_ARG, "unknown precision mode");
-  if (prm.tile < -1 || prm.tile > sv::VANKA_CFG_SPLIT2) return fail(STOKES_ERR_ARG, "tile must be -1..5");
+  if (prm.tile < -1 || prm.tile > sv::VANKA_CFG_4) return fail(STOKES_ERR_ARG, "tile must be -1..6");
 
   if (prm.cycle < 1 || prm.cycle > 2) return fail(STOKES_ERR_ARG, "cycle must be 1 (V) or 2 (W)");
   if (prm.precond < 0 || prm.precond > 1) return fail(STOKES_ERR_ARG, "precond must be 0 or 1");

@@ -260,6 +260,8 @@ constexpr int VANKA_NCFG = 4;
 constexpr int VANKA_CFG_14 = 3;
 constexpr int VANKA_CFG_SPLIT = 4;   // FP64 only: own-patch solves + separate update (launch_vanka_split)
 constexpr int VANKA_CFG_SPLIT2 = 5;  // the same, compiled for two CTAs per SM (at most 128 registers)
+constexpr int VANKA_CFG_4 = 6;       // fused 4x4 tiles: small levels, spread over more SMs
+inline bool vanka_cfg_split(int cfg) { return cfg == VANKA_CFG_SPLIT || cfg == VANKA_CFG_SPLIT2; }
 template <typename R>
 void launch_vanka(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
                   double omega, int cfg, cudaStream_t s, int skip_lo = 1, int skip_hi = 0);

@@ -690,6 +690,7 @@ cudaError_t prepare_all() {
   if ((e = prepare_t<R, 8, 8, 128>()) != cudaSuccess) return e;
   if ((e = prepare_t<R, 16, 8, 192>()) != cudaSuccess) return e;
   if ((e = prepare_t<R, 16, 16, 352>()) != cudaSuccess) return e;
+  if ((e = prepare_t<R, 4, 4, 64>()) != cudaSuccess) return e;
   return prepare_t<R, 14, 14, 256>();
 }
 
@@ -730,6 +731,7 @@ void launch_vanka(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const 
     case 1: launch_t<R, 16, 8, 192>(L, cd, fd, x, b, xo, w, skip_lo, skip_hi, s); break;
     case 2: launch_t<R, 16, 16, 352>(L, cd, fd, x, b, xo, w, skip_lo, skip_hi, s); break;
     case 3: launch_t<R, 14, 14, 256>(L, cd, fd, x, b, xo, w, skip_lo, skip_hi, s); break;
+    case VANKA_CFG_4: launch_t<R, 4, 4, 64>(L, cd, fd, x, b, xo, w, skip_lo, skip_hi, s); break;
     default: launch_t<R, 8, 8, 128>(L, cd, fd, x, b, xo, w, skip_lo, skip_hi, s); break;
   }
 }

@@ -110,7 +110,7 @@ def test_vanka_sweep(pkg, n):
         assert rel(host(out), ref0) <= 1e-12
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("n", [8, 32, 64])
 def test_vanka_sweep_tile_shapes(pkg, n, tile):
     """Every configuration of the FP64 sweep gives the same sweep: fused tiles of 8x8, 16x8,
@@ -299,7 +299,7 @@ def mixed_h(pkg, n, **kw):
     return gpu_h(pkg, n, prec=stokes.STOKES_MIXED_FP32, **kw)
 
 
-@pytest.mark.parametrize("tile", [-1, 4, 5])
+@pytest.mark.parametrize("tile", [-1, 4, 5, 6])
 @pytest.mark.parametrize("n", [8, 32, 64])
 def test_mixed_vcycle_close_to_fp64(pkg, n, tile):
     """The FP32 V-cycle agrees with the FP64 oracle's V-cycle to FP32 rounding.
