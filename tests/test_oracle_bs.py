@@ -3,7 +3,8 @@
 Each check is against something other than the oracle's own formula: the
 exact Braess-Sarazin step it approximates (a dense solve of the block system
 [[tD, B^T], [B, 0]]), the limit of many Jacobi steps, the null space of the
-Schur complement, the multigrid contraction, and the direct solve.
+Schur complement, its interior rows against the vertex stencil that closed-form
+1D integrals give, the multigrid contraction, and the direct solve.
 """
 import numpy as np
 import pytest
@@ -119,3 +120,51 @@ def test_su_preconditioned_fgmres_reaches_the_direct_solution():
     res = O.solve(H, b, rtol=1e-12, maxit=300)
     xd = O.normalize_pressure(lv, O.direct_solve(lv, b))
     assert res.converged and np.linalg.norm(O.normalize_pressure(lv, res.x) - xd) <= 1e-9 * np.linalg.norm(xd)
+
+
+def test_schur_complement_interior_rows_are_the_closed_form_vertex_stencil():
+    """Away from the boundary S = -(1/t) B D^-1 B^T is a translation-invariant 5 x 5
+    vertex stencil that follows from closed-form 1D integrals alone: Q1 hat q_a
+    against the Q2 basis derivative, C(a, 2a + k) = (-1, -4, 0, 4, 1)[k + 2] / 6, and
+    against the Q2 basis, N(a, 2a + k) = h (0, 1, 1, 1, 0)[k + 2] / 3 (B_x = -C (x) N,
+    B_y = -N (x) C), and diag(L) = nu/90 (k m + m k) with the diagonals of the 1D Q2
+    stiffness (x 1/(3h)) k = 14 / 16 and mass (x h/30) m = 8 / 16 at a vertex / midpoint
+    node.  The oracle assembles B and L by quadrature; its S must equal the stencil
+    (21 nonzero entries) on every vertex at distance >= 2 from the boundary."""
+    c1 = {-2: -1.0, -1: -4.0, 1: 4.0, 2: 1.0}
+    n1 = {-1: 1.0, 0: 1.0, 1: 1.0}
+    kd = {0: 14.0, 1: 16.0}
+    md = {0: 8.0, 1: 16.0}
+
+    def wx(dI, dJ):
+        return c1.get(dI, 0.0) * n1.get(dJ, 0.0)
+
+    def wy(dI, dJ):
+        return n1.get(dI, 0.0) * c1.get(dJ, 0.0)
+
+    def s(ox, oy):
+        acc = 0.0
+        for nJ in range(-2, 3):
+            for nI in range(-2, 3):
+                mI, mJ = nI - 2 * ox, nJ - 2 * oy
+                if abs(mI) > 2 or abs(mJ) > 2:
+                    continue
+                d = kd[nI & 1] * md[nJ & 1] + md[nI & 1] * kd[nJ & 1]
+                acc += (wx(nI, nJ) * wx(mI, mJ) + wy(nI, nJ) * wy(mI, mJ)) / d
+        return acc
+
+    stencil = {(ox, oy): s(ox, oy) for ox in range(-2, 3) for oy in range(-2, 3)}
+    assert sum(1 for v in stencil.values() if v != 0.0) == 21
+    for n, t, nu in ((8, 1.0, 1.0), (16, 1.7, 0.3)):
+        lv = O.build_level(n, nu)
+        S = O.bs_schur(lv, t).toarray()
+        h = 1.0 / n
+        scale = -(1.0 / t) * (h / 18.0) ** 2 * (90.0 / nu)
+        npv = n + 1
+        for b in range(2, n - 1):
+            for a in range(2, n - 1):
+                v = b * npv + a
+                row = np.zeros(npv * npv)
+                for (ox, oy), c in stencil.items():
+                    row[(b + oy) * npv + (a + ox)] = scale * c
+                assert np.abs(S[v] - row).max() <= 1e-13 * np.abs(row).max(), (n, a, b)
