@@ -180,6 +180,20 @@ stokes_status stokes_residual(stokes_hierarchy* h, int level, const double* b, c
 stokes_status stokes_vanka_sweep(stokes_hierarchy* h, int level, const double* x,
                                  const double* b, double* x_out);
 
+/* One relaxation sweep of the V-cycle's smoother on level `level`, in the
+ * arithmetic the hierarchy's V-cycle uses (Algorithm 3 for Vanka; Algorithms 2
+ * and 4 for the Braess-Sarazin and Schur-Uzawa smoothers): FP64 hierarchies as
+ * stokes_vanka_sweep; STOKES_MIXED_FP32 rounds x and b to FP32, sweeps in FP32
+ * and widens x_out; STOKES_MIXED_BF16 does the same with the interior patch
+ * solves as BF16 tensor-core GEMMs on the tiles where they fit (the tile
+ * configuration of the level, stokes_level_tile).  This is the sweep the
+ * V-cycle applies, exposed so that it can be compared dof by dof with an FP64
+ * sweep.  x == NULL means x = 0; x_out must not alias x or b.  Uses the
+ * level's FP32 work vectors, so it must not overlap a V-cycle of the same
+ * hierarchy (it is ordered on the creation stream like every call). */
+stokes_status stokes_relaxation_sweep(stokes_hierarchy* h, int level, const double* x,
+                                      const double* b, double* x_out);
+
 /* r_coarse = P^T r_fine, from level `level` (>= 1) to level-1 (Algorithm 1,
  * restriction).  P is the FE interpolation with Dirichlet rows/columns zero. */
 stokes_status stokes_restrict(stokes_hierarchy* h, int level, const double* r_fine,
@@ -270,11 +284,34 @@ typedef struct {
   long long vcycles;        /* V-cycles applied by this hierarchy since the last reset */
   long long sweeps_timed;   /* finest-level sweeps timed since the last reset          */
   double sweep_ms;          /* their summed durations (CUDA events)                    */
+  long long tc_launches;    /* launches of the tensor-core (tcgen05) sweep kernel among
+                               kernel_launches (all hierarchies, since load)           */
 } stokes_stats;
 
 stokes_status stokes_stats_enable_timing(stokes_hierarchy* h, int enable);
 stokes_status stokes_stats_reset(stokes_hierarchy* h);
 stokes_status stokes_stats_read(stokes_hierarchy* h, stokes_stats* out);
+
+/* Device-side failures of asynchronous work: synchronises the creation
+ * stream and returns STOKES_ERR_TIMEOUT if a bounded device wait (the
+ * tensor-core sweep's mbarrier waits) expired in work queued since the last
+ * report, else STOKES_OK.  The flag is cleared when reported, so the
+ * hierarchy stays usable.  stokes_fgmres_solve and the other synchronising
+ * solves check the same flag at every iteration. */
+stokes_status stokes_device_status(stokes_hierarchy* h);
+
+/* Test hooks: failures made on purpose, without faulting or hanging a GPU.
+ *  - stokes_test_set_wait_limit: number of polls of the tensor-core sweep's
+ *    first bounded wait (the mbarrier of the bulk copy of the patch inverse).
+ *    0 makes that wait expire at once: the kernel sets the hierarchy's error
+ *    flag, still waits for its copy with the full limit, frees its tensor
+ *    memory and returns without writing x_out; the next synchronising call
+ *    returns STOKES_ERR_TIMEOUT.  A negative value restores the default.
+ *  - stokes_test_set_alloc_limit: cap on the device bytes one
+ *    stokes_hierarchy_create (on any thread) may allocate; beyond it the
+ *    creation frees what it holds and returns STOKES_ERR_OOM.  0 removes it. */
+stokes_status stokes_test_set_wait_limit(stokes_hierarchy* h, int polls);
+void stokes_test_set_alloc_limit(long long bytes);
 
 /* Largest grid accepted by stokes_residual_norm_noalloc. */
 #define STOKES_NOALLOC_MAX_N 8192

@@ -4,7 +4,9 @@
 // vector operation on the device.  Only scalars of the convergence test cross
 // to the host (one 8-byte copy per iteration).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -126,9 +128,26 @@ void free_all(stokes_hierarchy* h) {
   h->coarse_G = h->V = h->Z = h->small = h->partials = h->host_scalars = nullptr;
 }
 
+// Device allocations of stokes_hierarchy_create go through dalloc.  A test hook
+// (stokes_test_set_alloc_limit) caps the bytes one creation may allocate, so the
+// STOKES_ERR_OOM path runs without exhausting the GPU.
+std::atomic<long long> g_alloc_cap{0};      // 0: no cap
+thread_local long long t_alloc_used = 0;    // bytes allocated by the creation running on this thread
+
+cudaError_t dalloc_bytes(void** p, size_t bytes) {
+  const long long cap = g_alloc_cap.load();
+  if (cap > 0 && t_alloc_used + static_cast<long long>(bytes) > cap) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) t_alloc_used += static_cast<long long>(bytes);
+  return e;
+}
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t count) {
-  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  return dalloc_bytes(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 
 stokes_status check_level(const stokes_hierarchy* h, int level, int min_level = 0) {
@@ -182,7 +201,7 @@ void tc_sweep(stokes_hierarchy* h, sv::Level& L, const float* x, const float* b,
   cudaStreamWaitEvent(h->ring_stream, h->ring_fork, 0);
   sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, sv::VANKA_CFG_14, h->ring_stream, L.tc_lo,
                           L.tc_hi);
-  sv::launch_vanka_tc(L.d, L.tcB, x, b, xo, h->prm.omega, L.tc_lo, L.tc_hi, h->dev_err, s);
+  sv::launch_vanka_tc(L.d, L.tcB, x, b, xo, h->prm.omega, L.tc_lo, L.tc_hi, h->dev_err, s, h->tc_wait_limit);
   cudaEventRecord(h->ring_join, h->ring_stream);
   cudaStreamWaitEvent(s, h->ring_join, 0);
 }
@@ -247,8 +266,26 @@ void coarse_apply(stokes_hierarchy* h, const float* b, float* out) {
   sv::launch_convert<double, float>(C.e, out, C.d.N, h->stream);
 }
 
+// NVTX range names of the levels (host-side markers for profilers; free when no
+// tool is attached): "mg level <l> n=<n>"
+const char* level_range_name(const sv::Level& L, int l) {
+  static thread_local char buf[48];
+  std::snprintf(buf, sizeof(buf), "mg level %d n=%d", l, L.d.n);
+  return buf;
+}
+
+template <typename R>
+void vcycle_level(stokes_hierarchy* h, int l, const R* b, R* out);
+
 template <typename R>
 void vcycle(stokes_hierarchy* h, int l, const R* b, R* out) {
+  nvtxRangePushA(level_range_name(h->lv[l], l));
+  vcycle_level<R>(h, l, b, out);
+  nvtxRangePop();
+}
+
+template <typename R>
+void vcycle_level(stokes_hierarchy* h, int l, const R* b, R* out) {
   cudaStream_t s = h->stream;
   sv::Level& L = h->lv[l];
   if (l == 0) {
@@ -396,7 +433,11 @@ stokes_status read_scalar(stokes_hierarchy* h, const double* dev, double* out) {
   *out = h->host_scalars[0];
   int flag = 0;
   std::memcpy(&flag, h->host_scalars + 1, sizeof(int));
-  if (flag != 0) return fail(STOKES_ERR_TIMEOUT, "a bounded device wait expired in the tensor-core sweep");
+  if (flag != 0) {
+    // reported once: the flag is cleared so that the hierarchy stays usable
+    cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream);
+    return fail(STOKES_ERR_TIMEOUT, "a bounded device wait expired in the tensor-core sweep");
+  }
   return STOKES_OK;
 }
 
@@ -713,6 +754,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   }
   auto* h = new (std::nothrow) stokes_hierarchy();
   if (!h) return fail(STOKES_ERR_OOM, "host allocation failed");
+  t_alloc_used = 0;
   h->prm = prm;
   h->bs.t = prm.bs_t;
   h->bs.omega = prm.bs_omega;
@@ -770,7 +812,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
       if (L.tc_hi >= L.tc_lo) {
         std::vector<unsigned short> img(64 * 64);
         sv::tc_pack_inverse(L.full_inv_host.data() + static_cast<size_t>(sv::INTERIOR_CLASS) * 51 * 51, img.data());
-        if ((e = cudaMalloc(&L.tcB, img.size() * sizeof(unsigned short))) == cudaSuccess)
+        if ((e = dalloc_bytes(&L.tcB, img.size() * sizeof(unsigned short))) == cudaSuccess)
           e = cudaMemcpy(L.tcB, img.data(), img.size() * sizeof(unsigned short), cudaMemcpyHostToDevice);
       }
     }
@@ -789,7 +831,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
     if (e == cudaSuccess && (prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN ||
                              prm.smoother == STOKES_SMOOTHER_SCHUR_UZAWA) && k + 1 == sizes.size()) {
       const size_t el = sv::bs_scratch_elems(L.d) * (prm.prec == STOKES_FP64 ? sizeof(double) : sizeof(float));
-      e = cudaMalloc(&h->bs_buf, el);
+      e = dalloc_bytes(&h->bs_buf, el);
     }
     if (e == cudaSuccess && prm.prec != STOKES_FP64) {
       std::vector<float> cdf(L.cd_host.begin(), L.cd_host.end());
@@ -895,6 +937,7 @@ stokes_status stokes_stats_read(stokes_hierarchy* h, stokes_stats* out) {
   }
   h->ev_used = 0;
   out->kernel_launches = sv::g_launches.load();
+  out->tc_launches = sv::g_tc_launches.load();
   out->vcycles = h->vcycles;
   out->sweeps_timed = h->sweeps_timed;
   out->sweep_ms = h->sweep_ms;
@@ -964,6 +1007,48 @@ stokes_status stokes_vanka_sweep(stokes_hierarchy* h, int level, const double* x
   sweep_f64(h, L, x, b, x_out);
   return check_launch("vanka_sweep");
 }
+
+stokes_status stokes_relaxation_sweep(stokes_hierarchy* h, int level, const double* x, const double* b,
+                                      double* x_out) {
+  stokes_status st = check_level(h, level);
+  if (st != STOKES_OK) return st;
+  if (!b || !x_out) return fail(STOKES_ERR_ARG, "null vector");
+  if (x_out == x || x_out == b) return fail(STOKES_ERR_ARG, "x_out must not alias x or b");
+  sv::Level& L = h->lv[level];
+  if (h->prm.prec == STOKES_FP64) {
+    sweep_f64(h, L, x, b, x_out);
+    return check_launch("relaxation_sweep");
+  }
+  // the mixed forms: round x and b to FP32, sweep in the V-cycle's arithmetic, widen the result
+  const long long N = L.d.N;
+  sv::launch_convert<double, float>(b, L.bf, N, h->stream);
+  if (x) sv::launch_convert<double, float>(x, L.xf0, N, h->stream);
+  timed_sweep<float>(h, false, L, x ? L.xf0 : nullptr, L.bf, L.xf1);
+  sv::launch_convert<float, double>(L.xf1, x_out, N, h->stream);
+  return check_launch("relaxation_sweep");
+}
+
+stokes_status stokes_device_status(stokes_hierarchy* h) {
+  if (!h) return fail(STOKES_ERR_ARG, "null hierarchy");
+  SV_TRY(cudaMemcpyAsync(h->host_scalars + 1, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream),
+         "copy error flag");
+  SV_TRY(cudaStreamSynchronize(h->stream), "stream sync");
+  int flag = 0;
+  std::memcpy(&flag, h->host_scalars + 1, sizeof(int));
+  if (flag != 0) {
+    SV_TRY(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream), "clear error flag");
+    return fail(STOKES_ERR_TIMEOUT, "a bounded device wait expired in the tensor-core sweep");
+  }
+  return STOKES_OK;
+}
+
+stokes_status stokes_test_set_wait_limit(stokes_hierarchy* h, int polls) {
+  if (!h) return fail(STOKES_ERR_ARG, "null hierarchy");
+  h->tc_wait_limit = (polls < 0 || polls > sv::TC_WAIT_LIMIT) ? sv::TC_WAIT_LIMIT : polls;
+  return STOKES_OK;
+}
+
+void stokes_test_set_alloc_limit(long long bytes) { g_alloc_cap.store(bytes > 0 ? bytes : 0); }
 
 stokes_status stokes_restrict(stokes_hierarchy* h, int level, const double* r_fine, double* r_coarse) {
   stokes_status st = check_level(h, level, 1);

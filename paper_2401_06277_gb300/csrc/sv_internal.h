@@ -87,6 +87,8 @@ struct FastDiagT {
 using FastDiag = FastDiagT<double>;
 
 // Braess-Sarazin / Schur-Uzawa parameters (Sections 3.1, 3.3; see stokes_params).
+constexpr int TC_WAIT_LIMIT = 1 << 22;   // polls of an mbarrier before a tensor-core sweep's wait gives up
+
 struct BSParams {
   double t = 1.0, omega = 1.0, jacobi_weight = 1.0;
   int jacobi_iters = 2;
@@ -195,6 +197,7 @@ struct stokes_hierarchy {
   sv::BSParams bs;
   double* host_scalars = nullptr;  // pinned host mirror of a few scalars
   int* dev_err = nullptr;          // set by kernels whose bounded waits expired
+  int tc_wait_limit = sv::TC_WAIT_LIMIT;   // first bounded wait of the tensor-core sweep (test hook)
   // BF16 form: the SIMT ring of boundary tiles runs on ring_stream while the
   // tensor-core kernel sweeps the interior tiles on stream (fork / join events)
   cudaStream_t ring_stream = nullptr;
@@ -225,6 +228,7 @@ void set_last_error(const std::string& msg);
 
 // kernels launched by this library (every launch_* adds its own count)
 extern std::atomic<long long> g_launches;
+extern std::atomic<long long> g_tc_launches;   // tensor-core sweep kernels among them
 inline void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // ---- host setup (sv_setup.cu) ----
@@ -273,8 +277,11 @@ void launch_vanka(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const 
 // core-matrix layout (8 KB).  err: set to 1 if a bounded device wait expired.
 constexpr int TC_TILE = 14;
 void tc_interior_range(int n, int* lo, int* hi);
+// first_wait_limit: polls of the wait for the inverse's bulk copy (0: it expires
+// at once -- a test hook; the kernel then reports through *err and still waits
+// for its copy with the full limit before it exits)
 void launch_vanka_tc(const LevelDev& L, const void* Bcanon, const float* x, const float* b, float* xo,
-                     double omega, int lo, int hi, int* err, cudaStream_t s);
+                     double omega, int lo, int hi, int* err, cudaStream_t s, int first_wait_limit = TC_WAIT_LIMIT);
 cudaError_t vanka_tc_prepare();
 // 64 x 64 BF16 core-matrix image (uint16 bits) of a 51 x 51 row-major inverse
 void tc_pack_inverse(const double* inv51, unsigned short* out4096);

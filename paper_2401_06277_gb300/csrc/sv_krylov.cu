@@ -408,6 +408,7 @@ int grid_for(long long N, int nt) {
 }  // namespace
 
 std::atomic<long long> g_launches{0};
+std::atomic<long long> g_tc_launches{0};
 
 int dot_blocks() { return DOT_BLOCKS; }
 

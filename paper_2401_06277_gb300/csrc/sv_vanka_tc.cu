@@ -32,8 +32,10 @@
 // two components share the Laplacian stencil), and are stored column-parity
 // split (the even nodes of a row, then the odd ones) with row pitches for which
 // the stencil, patch-gather and update loads are free of bank conflicts.
-// Every wait is bounded; on expiry the kernel sets *err, waits (bounded) for
-// its bulk copy, frees its TMEM and returns.
+// Every wait is bounded; on expiry the kernel sets *err, waits (bounded, with
+// the full limit) for its bulk copy and MMAs, frees its TMEM and returns.  The
+// limit of the first wait (the inverse's bulk copy) is a launch argument, so a
+// test can make it expire (0 polls) without faulting or hanging anything.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -93,7 +95,7 @@ static_assert(OFF_D + TT::NPATCH * 51 * 4 <= OFF_X, "corrections overlay only de
 static_assert(OFF_BAR % 8 == 0 && OFF_R % 8 == 0 && OFF_X % 8 == 0, "mbarrier and float2 alignment");
 
 constexpr uint32_t TMEM_COLS = 128;
-constexpr int WAIT_LIMIT = 1 << 22;
+constexpr int WAIT_LIMIT = TC_WAIT_LIMIT;
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -112,8 +114,8 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
 // instruction descriptor: D FP32, A/B BF16, both K-major, N = 64, M = 128
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-  for (int it = 0; it < WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int limit = WAIT_LIMIT) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -141,7 +143,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __restrict__ Bg,
                                                      const float* __restrict__ x,
                                                      const float* __restrict__ b, float* __restrict__ xo,
-                                                     float omega, int tile0, int* __restrict__ err) {
+                                                     float omega, int tile0, int* __restrict__ err,
+                                                     int first_wait_limit) {
   pdl_begin();
   extern __shared__ __align__(1024) unsigned char sm[];
   float2* sx = reinterpret_cast<float2*>(sm + OFF_X);
@@ -352,7 +355,7 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
   // 4. the GEMM: D[t] (128 x 64, FP32, TMEM columns 64 t) = R[t] B^T
   __shared__ int ok_s;
   if (tid == 0) {
-    int ok = mbar_wait(bar_b, 0) ? 1 : 0;
+    int ok = mbar_wait(bar_b, 0, first_wait_limit) ? 1 : 0;
     if (ok) {
       const uint32_t a0 = su32(sm + OFF_A), b0 = su32(sm + OFF_B);
 #pragma unroll
@@ -457,12 +460,13 @@ cudaError_t vanka_tc_prepare() {
 }
 
 void launch_vanka_tc(const LevelDev& L, const void* Bcanon, const float* x, const float* b, float* xo,
-                     double omega, int lo, int hi, int* err, cudaStream_t s) {
+                     double omega, int lo, int hi, int* err, cudaStream_t s, int first_wait_limit) {
   if (hi < lo) return;
   count_launches(1);
+  g_tc_launches.fetch_add(1, std::memory_order_relaxed);
   const int g = hi - lo + 1;
   launch_pdl(k_vanka_tc, dim3(dim3(g, g)), dim3(TC_NT), SMEM_BYTES, s, L, static_cast<const uint4*>(Bcanon), x, b, xo,
-                                                   static_cast<float>(omega), lo, err);
+                                                   static_cast<float>(omega), lo, err, first_wait_limit);
 }
 
 void tc_pack_inverse(const double* inv51, unsigned short* out) {

@@ -43,7 +43,8 @@ class StokesError(RuntimeError):
 
 class stokes_stats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_longlong), ("vcycles", ctypes.c_longlong),
-                ("sweeps_timed", ctypes.c_longlong), ("sweep_ms", ctypes.c_double)]
+                ("sweeps_timed", ctypes.c_longlong), ("sweep_ms", ctypes.c_double),
+                ("tc_launches", ctypes.c_longlong)]
 
 
 class stokes_params(ctypes.Structure):
@@ -84,6 +85,10 @@ def _load():
         "stokes_apply_operator": (I, [P, I, VP, VP]),
         "stokes_residual": (I, [P, I, VP, VP, VP]),
         "stokes_vanka_sweep": (I, [P, I, VP, VP, VP]),
+        "stokes_relaxation_sweep": (I, [P, I, VP, VP, VP]),
+        "stokes_device_status": (I, [P]),
+        "stokes_test_set_wait_limit": (I, [P, I]),
+        "stokes_test_set_alloc_limit": (None, [ctypes.c_longlong]),
         "stokes_restrict": (I, [P, I, VP, VP]),
         "stokes_prolong_add": (I, [P, I, VP, VP]),
         "stokes_coarse_solve": (I, [P, VP, VP]),
@@ -116,7 +121,8 @@ def exported_symbols() -> list[str]:
     return ["stokes_default_params", "stokes_hierarchy_create", "stokes_hierarchy_destroy",
             "stokes_level_info", "stokes_level_n", "stokes_level_tile", "stokes_assemble_rhs",
             "stokes_apply_operator",
-            "stokes_residual", "stokes_vanka_sweep", "stokes_restrict", "stokes_prolong_add",
+            "stokes_residual", "stokes_vanka_sweep", "stokes_relaxation_sweep", "stokes_device_status",
+            "stokes_test_set_wait_limit", "stokes_test_set_alloc_limit", "stokes_restrict", "stokes_prolong_add",
             "stokes_coarse_solve", "stokes_initial_guess", "stokes_vcycle_apply", "stokes_fgmres_solve",
             "stokes_solve_adjoint", "stokes_rhs_transpose", "stokes_batched_solve",
             "stokes_stats_enable_timing", "stokes_stats_reset", "stokes_stats_read",
@@ -212,6 +218,24 @@ def stokes_vanka_sweep(h, level: int, x, b, x_out) -> None:
                                       _ptr(x_out, N, "x_out")))
 
 
+def stokes_relaxation_sweep(h, level: int, x, b, x_out) -> None:
+    N = vec_len(stokes_level_n(h, level))
+    _check(_load().stokes_relaxation_sweep(h, int(level), _ptr(x, N, "x"), _ptr(b, N, "b"),
+                                           _ptr(x_out, N, "x_out")))
+
+
+def stokes_device_status(h, allow_timeout: bool = False) -> int:
+    return _check(_load().stokes_device_status(h), allow=(STOKES_ERR_TIMEOUT,) if allow_timeout else ())
+
+
+def stokes_test_set_wait_limit(h, polls: int) -> None:
+    _check(_load().stokes_test_set_wait_limit(h, int(polls)))
+
+
+def stokes_test_set_alloc_limit(nbytes: int) -> None:
+    _load().stokes_test_set_alloc_limit(int(nbytes))
+
+
 def stokes_restrict(h, level: int, r_fine, r_coarse) -> None:
     Nf = vec_len(stokes_level_n(h, level))
     Nc = vec_len(stokes_level_n(h, level - 1))
@@ -295,7 +319,7 @@ def stokes_stats_read(h) -> dict:
     st = stokes_stats()
     _check(_load().stokes_stats_read(h, ctypes.byref(st)))
     return {"kernel_launches": st.kernel_launches, "vcycles": st.vcycles,
-            "sweeps_timed": st.sweeps_timed, "sweep_ms": st.sweep_ms}
+            "sweeps_timed": st.sweeps_timed, "sweep_ms": st.sweep_ms, "tc_launches": st.tc_launches}
 
 
 def stokes_residual_norm_noalloc(n: int, viscosity: float, b, x, norm,
@@ -478,6 +502,13 @@ class Hierarchy:
         level = self.levels - 1 if level is None else level
         out = torch.empty_like(b)
         stokes_vanka_sweep(self.handle, level, x, b, out)
+        return out
+
+    def relax(self, x, b, level=None):
+        """One sweep of the V-cycle's smoother in the hierarchy's arithmetic (x None: zero guess)."""
+        level = self.levels - 1 if level is None else level
+        out = torch.empty_like(b)
+        stokes_relaxation_sweep(self.handle, level, x, b, out)
         return out
 
     def vcycle(self, r):

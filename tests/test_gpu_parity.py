@@ -384,11 +384,19 @@ def test_bf16_fgmres_solution(pkg, n, tile):
 
 def test_bf16_uses_the_tensor_core_kernel(pkg):
     """With tile 3 the finest 128^2 level sweeps its interior tiles on the tensor cores
-    and the ring on the 14x14 SIMT tile; the kernel launch counter grows by two per
-    finest-level sweep (tensor-core kernel + ring)."""
+    and the ring on the 14x14 SIMT tile: a finest-level sweep is two launches (the
+    tensor-core kernel and the ring), one of them the tensor-core kernel."""
     from paper_2401_06277_gb300 import stokes
     H = gpu_h(pkg, 128, prec=stokes.STOKES_MIXED_BF16, tile=3)
     assert stokes.stokes_level_tile(H.handle, H.levels - 1) == 3
+    b = dev(si.random_vector(128, 3))
+    out = torch.empty_like(b)
+    torch.cuda.synchronize()
+    s0 = stokes.stokes_stats_read(H.handle)
+    stokes.stokes_relaxation_sweep(H.handle, H.levels - 1, None, b, out)   # zero guess: b -> FP32, sweep, widen
+    s1 = stokes.stokes_stats_read(H.handle)
+    assert s1["tc_launches"] - s0["tc_launches"] == 1
+    assert s1["kernel_launches"] - s0["kernel_launches"] == 2 + 2
 
 
 # ---------------------------------------------------------------------------
