@@ -85,14 +85,17 @@ def sweep_error_bound(level: Level, x: np.ndarray | None, b: np.ndarray, omega: 
 
 
 def tensor_core_dofs(n: int, tile: int = 14) -> np.ndarray:
-    """Mask of the dofs whose sweep update a 14 x 14-vertex tensor-core tile computes.
+    """Mask of the dofs whose sweep update the tensor-core kernel computes.
 
-    Tile (bx, by) covers vertices [tile bx, tile (bx + 1)) per axis and is swept on
-    the tensor cores when 1 <= bx, by <= hi with hi = (n - 2 - tile) // tile (every
-    patch it touches is then of the interior class, Section 6.3).  Vertex (i, j)
-    owns the Q2 nodes (2i - 1 .. 2i) x (2j - 1 .. 2j) and its own pressure."""
+    Tile (bx, by) covers vertices [tile bx, tile (bx + 1)) per axis; tiles with
+    1 <= bx, by <= hi, hi = (n - 2 - tile) // tile, touch only patches of the
+    interior class (Section 6.3).  The kernel sweeps strips two tiles wide, so it
+    takes an even number of those tiles per axis (1 .. hi, less one if the count is
+    odd; none below two).  Vertex (i, j) owns the Q2 nodes (2i - 1 .. 2i) x
+    (2j - 1 .. 2j) and its own pressure."""
     nq, npv = 2 * n + 1, n + 1
     hi = (n - 2 - tile) // tile if n >= 2 + 2 * tile else 0
+    hi = hi - (hi % 2) if hi >= 2 else 0
     vt = np.arange(npv) // tile
     vin = (vt >= 1) & (vt <= hi)                      # per-axis vertex in a tensor-core tile
     node_owner = (np.arange(nq) + 1) // 2             # vertex owning Q2 index I on one axis

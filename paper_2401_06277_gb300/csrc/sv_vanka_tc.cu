@@ -1,41 +1,49 @@
-// sv_vanka_tc.cu -- additive Vanka sweep with the interior patch solves as one
-// BF16 GEMM per tile on the 5th-generation tensor cores (tcgen05), for the
-// mixed-precision preconditioner (FP32 vectors, FP32 accumulation).
+// sv_vanka_tc.cu -- additive Vanka sweep with the interior patch solves as BF16
+// GEMMs on the 5th-generation tensor cores (tcgen05), for the mixed-precision
+// preconditioner (FP32 vectors, FP32 accumulation).
 //
 // Section 6.3 of the paper observes that on a uniform grid all interior patches
-// share one patch matrix A_int.  The solves delta_i = A_int^-1 r_i of a tile's
-// 256 patches are therefore the product D = R A_int^-T with R the 256 x 51
-// matrix of gathered patch residuals (Algorithm 3, Section 3.2): M = 256
-// (two M=128 MMAs), N = K = 51, padded to 64.
+// share one patch matrix A_int.  The solves delta_i = A_int^-1 r_i of a group of
+// patches are therefore one product D = R A_int^-T, with R the matrix of gathered
+// patch residuals (Algorithm 3, Section 3.2): one tcgen05.mma (kind::f16,
+// BF16 x BF16 -> FP32 in tensor memory) of M = 128 patches, N = K = 51 padded
+// to 64.
 //
-// One CTA per 14 x 14 vertex tile (256 threads, one per patch of the 16 x 16
-// patch region including the one-vertex halo):
-//   1. warp 0 allocates 128 TMEM columns; thread 0 starts a bulk (TMA) copy of
-//      the 8 KB BF16 inverse, already in the UMMA core-matrix layout, into
-//      shared memory, completing on an mbarrier;
-//   2. the x and p windows are loaded; one thread per 2x2 cell of Q2 nodes
-//      reads b from global memory and forms the FP32 residual of its four
-//      nodes (compile-time stencils) and, from the same registers, the
-//      pressure residual of the cell's vertex;
-//   3. each thread writes its patch row of R, converted to BF16, into the
-//      K-major no-swizzle core-matrix layout (8 rows x 16 bytes per core
-//      matrix, LBO = 128 B along K, SBO = 1024 B along M);
-//   4. thread 0 issues 2 x 4 tcgen05.mma (kind::f16, M=128, N=64, K=16) into
-//      TMEM and commits them to an mbarrier;
-//   5. after the wait, each thread reads its patch row of D with tcgen05.ld and
-//      stores the 51 corrections in shared memory (over the dead R, B and
-//      residual buffers);
-//   6. x_out = x + (omega / m_j) * sum of the corrections of the patches that
-//      hold the dof, summed in a fixed order (deterministic, no atomics).
-// The x and residual windows hold (u_x, u_y) pairs (float2), so a stencil tap
-// of both components is one 64-bit load and one packed FP32 FMA (FFMA2; the
-// two components share the Laplacian stencil), and are stored column-parity
-// split (the even nodes of a row, then the odd ones) with row pitches for which
-// the stencil, patch-gather and update loads are free of bank conflicts.
+// Work decomposition.  A CTA (128 threads, warp r <-> row r of a step) sweeps a
+// segment of a strip: 28 owned vertex columns [i0, i0 + 28) and S owned vertex
+// rows [j0, j0 + S), S a multiple of 4.  It walks up the segment in steps of 4
+// rows, keeping the rows it still needs in shared-memory rings, so a residual
+// cell or a patch is computed once per strip instead of once per square tile
+// (halo overhead 32/28 in cells and 30/28 in patches, against 18^2/14^2 and
+// 16^2/14^2 for a 14 x 14 tile).  Step t, three phases separated by barriers:
+//   A. the residual b - A x of cell row group t (32 x 4 cells: one 2x2 cell of
+//      Q2 nodes and its vertex per thread, compile-time stencils, (u_x, u_y)
+//      pairs with packed FP32 FMAs) into the residual ring; the weighted
+//      update of vertex rows j0 + 4t - 12 .. j0 + 4t - 9 from the partial-sum
+//      ring; the loads of x, p and b for step t + 1 are issued here and
+//      stored in phase C, so their latency overlaps the step's work;
+//   B. the patch rows of group t (30 x 4 patches: one per thread, lanes 30 and
+//      31 of each warp padding) gathered from the residual ring into the
+//      K-major BF16 operand (core matrices of 8 rows x 16 bytes);
+//   C. one thread issues the MMA of group t into one of two tensor-memory
+//      buffers; every warp reads its patch row of group t - 1 from the other
+//      buffer (tcgen05.ld: lane = patch), adds the corrections of the patches
+//      that share a Q2 node column with warp shuffles, and stores per-node
+//      partial sums (one float4 per node-pair and window row) in the
+//      partial-sum ring; the prefetched rows are stored.
+// Update: x_out = x + (omega / m_j) * (sum of the corrections of the patches
+// that hold dof j): the 3 (or 2) partial sums of a node's row, added in a fixed
+// order (deterministic, no atomics).
+//
+// Slot order of a patch row (the K dimension of R and both dimensions of the
+// inverse image): the (u_x, u_y) pair of window node s = 5 wj + wi at 2s, 2s + 1
+// (so that one BF16x2 conversion packs one node), the pressure at 50.
+//
 // Every wait is bounded; on expiry the kernel sets *err, waits (bounded, with
-// the full limit) for its bulk copy and MMAs, frees its TMEM and returns.  The
-// limit of the first wait (the inverse's bulk copy) is a launch argument, so a
-// test can make it expire (0 polls) without faulting or hanging anything.
+// the full limit) for its bulk copy and the last MMA it issued, frees its tensor
+// memory and returns.  The limit of the first wait (the inverse's bulk copy) is
+// a launch argument, so a test can make it expire (0 polls) without faulting or
+// hanging anything.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -49,52 +57,44 @@
 namespace sv {
 namespace {
 
-using vk::inv_mult;
-using vk::VT;
-using vk::vfree;
+constexpr int SW = 2 * TC_TILE;     // owned vertex columns of a strip (28)
+constexpr int NPC = SW + 2;         // patches per row of a step (30)
+constexpr int NCC = SW + 4;         // residual cells per row (32)
+constexpr int XN = 2 * SW + 12;     // x window nodes per row (68)
+constexpr int NPW = SW + 6;         // p window vertices per row (34)
+constexpr int GR = 4;               // vertex rows per step
+constexpr int NT = 128;             // threads
+constexpr int SEG_MAX = 4;          // segment length in 14-vertex tiles: 4 (56 rows) or 2 (28)
+static_assert(NCC == 32 && NPC <= 32 && GR * 32 == NT, "warp r <-> row r, lane <-> column");
 
-constexpr int TC_NT = 256;
-using TT = VT<TC_TILE, TC_TILE>;
-static_assert(TT::NPATCH == TC_NT, "one thread per patch");
-static_assert(TC_TILE % 2 == 0 && TC_TILE / 2 <= TC_NT / 32 && 2 * TC_TILE <= 32, "update: two vertex rows per warp");
+// Rings (row index taken modulo the ring size; each holds exactly the rows that are
+// alive across a phase boundary).  x: node rows, (u_x, u_y) pairs, column-parity
+// split (even nodes at pair c/2, odd nodes at XHO + c/2): the stencil loads of a
+// warp read 32 consecutive pairs; the prefetch stores of a half-warp (8 even, 8
+// odd nodes) hit disjoint banks since XHO = 40 = 8 (mod 16).
+constexpr int XR = 12, XHO = 40, XPP = XHO + XN / 2;        // 12 node rows of 74 pairs
+constexpr int RR = 12, RHO = 32, RPP = 64;                  // residual: 12 node rows of 64 pairs
+constexpr int CRR = 8;                                      // cell rows (pressure residual)
+constexpr int PRR = 6, PPW = 36;                            // p: 6 vertex rows of 34 (+2)
+constexpr int SRR = 6;                                      // partial sums: 6 patch rows
+static_assert(XN / 2 <= XHO && (2 * XHO) % 32 == 16, "x ring layout");
 
-// Windows (origins as in the SIMT sweep: x at Q2 node 2 i0 - 6, residual at
-// 2 i0 - 4, p at vertex i0 - 3).  A row of the x window holds the (u_x, u_y)
-// pairs of its 20 even nodes, then of its 20 odd ones; a residual row those of
-// its 18 even, then 18 odd nodes.  A half-warp's 64-bit accesses are free of
-// bank conflicts when its 16 addresses differ modulo 16 pairs.  The residual
-// cells are taken row-major, 18 per row (item t = 18 cy + cx); x rows two apart
-// (one cell row) are 2 XP = 82 = 18 = 2 (mod 16) pairs apart, so the pair index
-// of every stencil load is t + const (mod 16), and the same holds for the cell
-// stores into the residual window (RP = 41); the patch gather reads one row of
-// 16 patches per half-warp.  p (scalar) rows have pitch 50 = 18 (mod 32): the
-// bank of a p load is t + const (mod 32).
-constexpr int XP = 41, XHALF = 20;                         // x: 40 rows of 40 pairs (+1 pad)
-constexpr int RP = 41, RHALF = 18;                         // residual: 36 rows of 36 pairs (+5 pad)
-constexpr int PP = 50;                                     // p: 20 rows of 20
-static_assert(TT::XW == 2 * XHALF && TT::XW <= XP && TT::RW == 2 * RHALF && TT::RW <= RP && TT::PW <= PP,
-              "window widths");
-static_assert((2 * XP) % 16 == TT::CW % 16 && (2 * RP) % 16 == TT::CW % 16 && PP % 32 == TT::CW,
-              "bank schedule");
-__device__ __forceinline__ int xcol(int ii) { return (ii & 1) * XHALF + (ii >> 1); }
+constexpr int OFF_A = 0;                                    // 128 x 64 BF16 = 16 KB
+constexpr int OFF_B = OFF_A + 128 * 64 * 2;                 // 64 x 64 BF16 = 8 KB
+constexpr int OFF_X = OFF_B + 64 * 64 * 2;
+constexpr int OFF_R = OFF_X + XR * XPP * 8;
+constexpr int OFF_RPR = OFF_R + RR * RPP * 8;
+constexpr int OFF_P = OFF_RPR + CRR * NCC * 4;
+constexpr int OFF_PS = OFF_P + PRR * PPW * 4;               // [row][wj][lane] float4
+constexpr int OFF_PSP = OFF_PS + SRR * 5 * 32 * 16;         // [row][lane] pressure corrections
+constexpr int OFF_BAR = OFF_PSP + SRR * 32 * 4;             // bulk-copy and MMA mbarriers
+constexpr int OFF_TMEM = OFF_BAR + 16;
+constexpr int OFF_FLAG = OFF_TMEM + 4;
+constexpr int SMEM_BYTES = OFF_FLAG + 12;
+static_assert(OFF_X % 16 == 0 && OFF_PS % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+static_assert(4 * (SMEM_BYTES + 1024) <= 228 * 1024, "four CTAs per SM");
 
-// shared-memory layout (bytes).  The correction array D (256 x 51 FP32,
-// 52,224 B) overlays A, B, the residual and the pressure residual, which are
-// all dead once the MMAs have completed; the x windows stay live for x_old.
-constexpr int OFF_A = 0;                                   // 256 x 64 BF16 = 32 KB
-constexpr int OFF_B = OFF_A + 256 * 64 * 2;                // 64 x 64 BF16 = 8 KB
-constexpr int OFF_R = OFF_B + 64 * 64 * 2;                 // residual pairs (FP32)
-constexpr int OFF_RP = OFF_R + TT::RH * RP * 8;            // pressure residual
-constexpr int OFF_X = OFF_RP + TT::SRP * 4;                // x window pairs
-constexpr int OFF_P = OFF_X + TT::XH * XP * 8;             // p window
-constexpr int OFF_BAR = OFF_P + TT::PH * PP * 4;           // two mbarriers
-constexpr int OFF_TMEM = OFF_BAR + 16;                     // TMEM base address
-constexpr int SMEM_BYTES = OFF_TMEM + 16;
-constexpr int OFF_D = 0;                                   // corrections, after the MMAs
-static_assert(OFF_D + TT::NPATCH * 51 * 4 <= OFF_X, "corrections overlay only dead buffers");
-static_assert(OFF_BAR % 8 == 0 && OFF_R % 8 == 0 && OFF_X % 8 == 0, "mbarrier and float2 alignment");
-
-constexpr uint32_t TMEM_COLS = 128;
+constexpr uint32_t TMEM_COLS = 128;   // two 64-column accumulators (4 CTAs per SM: all 512 columns)
 constexpr int WAIT_LIMIT = TC_WAIT_LIMIT;
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -128,51 +128,103 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, int limi
   return false;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// this lane's 52 accumulator columns (32 + 16 + 4) from tensor memory
+__device__ __forceinline__ void tmem_ld52(uint32_t taddr, float* v) {
+  uint32_t r[52];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+      : "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+      : "r"(taddr + 32));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51])
+               : "r"(taddr + 48));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+  for (int j = 0; j < 52; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-__global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __restrict__ Bg,
-                                                     const float* __restrict__ x,
-                                                     const float* __restrict__ b, float* __restrict__ xo,
-                                                     float omega, int tile0, int* __restrict__ err,
-                                                     int first_wait_limit) {
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  uint32_t u;
+  memcpy(&u, &h, 4);
+  return u;
+}
+
+// A global load issued where it is written: the memory clobber keeps the compiler
+// from sinking it towards its first use (the prefetches of a step are issued at the
+// top of phase A and consumed a phase or a step later, which hides their latency).
+__device__ __forceinline__ float ldg_early(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ bool free_node(int I, int J, int nq) {
+  return I > 0 && J > 0 && I < nq - 1 && J < nq - 1;
+}
+
+__global__ void __launch_bounds__(NT, 4) k_vanka_tc(LevelDev L, const uint4* __restrict__ Bg,
+                                                    const float* __restrict__ x,
+                                                    const float* __restrict__ b, float* __restrict__ xo,
+                                                    float omega, int lo, int hi, int seg_tiles,
+                                                    int* __restrict__ err, int first_wait_limit) {
   pdl_begin();
   extern __shared__ __align__(1024) unsigned char sm[];
   float2* sx = reinterpret_cast<float2*>(sm + OFF_X);
-  float* sp = reinterpret_cast<float*>(sm + OFF_P);
   float2* sr = reinterpret_cast<float2*>(sm + OFF_R);
-  float* srp = reinterpret_cast<float*>(sm + OFF_RP);
+  float* srp = reinterpret_cast<float*>(sm + OFF_RPR);
+  float* sp = reinterpret_cast<float*>(sm + OFF_P);
+  float4* sps = reinterpret_cast<float4*>(sm + OFF_PS);
+  float* spp = reinterpret_cast<float*>(sm + OFF_PSP);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + OFF_TMEM);
+  volatile int* s_fail = reinterpret_cast<volatile int*>(sm + OFF_FLAG);
   const uint32_t bar_b = su32(bars), bar_mma = su32(bars + 1);
   const int nq = L.nq, np = L.np;
   const long long nv = L.nv;
-  const int i0 = (tile0 + static_cast<int>(blockIdx.x)) * TC_TILE;
-  const int j0 = (tile0 + static_cast<int>(blockIdx.y)) * TC_TILE;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int XI0 = 2 * i0 - 6, XJ0 = 2 * j0 - 6;
-  const int RI0 = 2 * i0 - 4, RJ0 = 2 * j0 - 4;
+  const int tid = threadIdx.x, r = tid >> 5, l = tid & 31;
+  const int i0 = TC_TILE * (lo + 2 * static_cast<int>(blockIdx.x));
+  const int seg0 = lo + seg_tiles * static_cast<int>(blockIdx.y);
+  const int j0 = TC_TILE * seg0;
+  const int S = TC_TILE * min(seg_tiles, hi + 1 - seg0);   // owned rows, a multiple of 28
+  const int T = S / GR;                                     // steps with cells / patches
+  const int XI0 = 2 * i0 - 6;                               // x window origin (Q2 column)
+  const bool has_x = x != nullptr;
+  const float cl = L.clf, cb = L.cbf;
 
-  // 1. barriers, TMEM, bulk copy of the BF16 inverse
+  // ---- set-up: barriers, tensor memory, bulk copy of the BF16 inverse, zero pad rows ----
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_b), "r"(1));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_mma), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *s_fail = 0;
   }
   __syncwarp();
-  if (warp == 0) {
+  if (r == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
                  "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // A: lanes 30, 31 of every 32-row group are padding patches (zero rows); the K
+  // chunk 7 (slots 56..63) of every row is zero
+  {
+    unsigned char* arow = sm + OFF_A + (tid >> 3) * 1024 + (tid & 7) * 16;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    if (l >= NPC) {
+#pragma unroll
+      for (int kg = 0; kg < 8; ++kg) *reinterpret_cast<uint4*>(arow + kg * 128) = z;
+    } else {
+      *reinterpret_cast<uint4*>(arow + 7 * 128) = z;
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -188,271 +240,384 @@ __global__ void __launch_bounds__(TC_NT) k_vanka_tc(LevelDev L, const uint4* __r
         : "memory");
   }
 
-  // 2. x and p windows (x of Dirichlet or outside nodes reads as 0: those
-  //    columns are eliminated); residual of every cell (all cells of an
-  //    interior tile are free), b read from global memory
-  if (x != nullptr) {
-    // warp w fills window rows w, w + 8, ..., lane k pair k of a row (even
-    // nodes first, then odd): row validity and address once per row, all loads
-    // issued before the stores (fully unrolled)
-    constexpr int XROWS = TT::XH / (TC_NT / 32);
-    static_assert(TT::XH % (TC_NT / 32) == 0 && TT::XW > 32 && TT::XW <= 64, "x window rows per warp");
-    float2 xv[XROWS][2];
+  // ---- loaders (warp r takes rows r, r + 4, ...) ----
+  // x node row J: lane l takes the window-column pairs (2 q, 2 q + 1), q = l and l + 32
+  // (< 34), i.e. nodes XI0 + 2 q (even half, pair q) and XI0 + 2 q + 1 (odd half, pair
+  // q): [k] = (u_x, u_y) of node XI0 + 2 q + k; 0 on Dirichlet / outside nodes
+  struct XPair {
+    float2 v[2];
+  };
+  auto x_pair = [&](int J, int q) -> XPair {
+    XPair o;
+    const bool jok = J > 0 && J < nq - 1;
+    const float* xr = x + static_cast<long long>(jok ? J : 1) * nq + XI0 + 2 * q;
 #pragma unroll
-    for (int k = 0; k < XROWS; ++k) {
-      const int jj = warp + k * (TC_NT / 32);
-      const int J = XJ0 + jj;
-      const bool jfree = J > 0 && J < nq - 1;
-      const float* xr = x + static_cast<long long>(jfree ? J : 0) * nq;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int pos = lane + 32 * h;
-        const int I = XI0 + (pos < XHALF ? 2 * pos : 2 * (pos - XHALF) + 1);
-        const bool ok = jfree && pos < TT::XW && I > 0 && I < nq - 1;
-        xv[k][h] = ok ? make_float2(xr[I], xr[nv + I]) : make_float2(0.0f, 0.0f);
-      }
+    for (int k = 0; k < 2; ++k) {
+      const int I = XI0 + 2 * q + k;
+      o.v[k] = (jok && I > 0 && I < nq - 1) ? make_float2(ldg_early(xr + k), ldg_early(xr + nv + k))
+                                            : make_float2(0.0f, 0.0f);
     }
-#pragma unroll
-    for (int k = 0; k < XROWS; ++k) {
-      float2* dst = sx + (warp + k * (TC_NT / 32)) * XP;
-      dst[lane] = xv[k][0];
-      if (lane + 32 < TT::XW) dst[lane + 32] = xv[k][1];
-    }
-    // p window: 20 x 20 vertices, flat over the CTA
-#pragma unroll
-    for (int t = tid; t < TT::SP; t += TC_NT) {
-      const int jj = t / TT::PW, ii = t - jj * TT::PW;
-      const int i = i0 - 3 + ii, j = j0 - 3 + jj;
-      sp[jj * PP + ii] = (i >= 0 && j >= 0 && i < np && j < np) ? x[2 * nv + static_cast<long long>(j) * np + i] : 0.0f;
-    }
-  }
-  __syncthreads();
-  const float cl = L.clf, cb = L.cbf;
-  // cell (cx, cy) of the 18 x 18 residual cells: nodes (RI0 + 2 cx + PI, RJ0 + 2 cy + PJ),
-  // taken row-major (t = 18 cy + cx)
-  for (int t = tid; t < TT::CW * TT::CH; t += TC_NT) {
-    const int cy = t / TT::CW, cx = t - cy * TT::CW;
-    const int I0 = RI0 + 2 * cx, J0 = RJ0 + 2 * cy;
-    const bool own_p = cx >= 1 && cy >= 1 && cx <= TT::QW && cy <= TT::QH;   // the vertex carries a patch
-    float rp = own_p ? b[2 * nv + static_cast<long long>(J0 >> 1) * np + (I0 >> 1)] : 0.0f;
-    float2 r[2][2];   // [PJ][PI]: (u_x, u_y) residual of node (I0 + PI, J0 + PJ)
+    return o;
+  };
+  auto x_pair_store = [&](int J, int q, const XPair& v) {
+    float2* row = sx + (J % XR) * XPP;
+    row[q] = v.v[0];
+    row[XHO + q] = v.v[1];
+  };
+  // p vertex row j (vertices i0 - 3 .. i0 + 30), window column c
+  auto p_item = [&](int j, int c) -> float {
+    const int i = i0 - 3 + c;
+    return (i >= 0 && j >= 0 && i < np && j < np) ? ldg_early(x + 2 * nv + static_cast<long long>(j) * np + i) : 0.0f;
+  };
+  // b of this thread's cell (column l, row cy): [PJ][PI] pairs and the vertex's pressure row
+  struct BCell {
+    float2 v[2][2];
+    float p;
+  };
+  auto b_load = [&](int cy) -> BCell {
+    BCell o;
+    const int cx = i0 - 2 + l;
 #pragma unroll
     for (int PJ = 0; PJ < 2; ++PJ)
 #pragma unroll
       for (int PI = 0; PI < 2; ++PI) {
-        const long long k = static_cast<long long>(J0 + PJ) * nq + I0 + PI;
-        r[PJ][PI] = make_float2(b[k], b[nv + k]);
+        const long long k = static_cast<long long>(2 * cy + PJ) * nq + 2 * cx + PI;
+        o.v[PJ][PI] = make_float2(ldg_early(b + k), ldg_early(b + nv + k));
       }
-    if (x != nullptr) {
-      float P[3][3];
+    o.p = ldg_early(b + 2 * nv + static_cast<long long>(cy) * np + cx);
+    return o;
+  };
+
+  // prologue: x rows 2 j0 - 6 .. 2 j0 + 5, p rows j0 - 3 .. j0 + 2, b of step 0
+  if (has_x) {
+    for (int rr = r; rr < 12; rr += GR) {
+      const int J = 2 * j0 - 6 + rr;
 #pragma unroll
-      for (int dj = 0; dj < 3; ++dj)
+      for (int k = 0; k < 2; ++k) {
+        const int q = l + 32 * k;
+        if (q < XN / 2) x_pair_store(J, q, x_pair(J, q));
+      }
+    }
+    for (int rr = r; rr < 6; rr += GR) {
+      const int j = j0 - 3 + rr;
 #pragma unroll
-        for (int di = 0; di < 3; ++di) P[dj][di] = sp[(cy + dj) * PP + cx + di];
-      // rows a = 0..5 of the 6 x 6 pair neighbourhood (node (I0 - 2 + bb, J0 - 2 + a))
-      // stream through registers: each feeds the Laplacian of the nodes it reaches
-      // and, for a <= 4, the divergence row of the vertex (node (I0, J0))
-      const float2* xc = sx + 2 * cy * XP + cx;
-      float2 sl[2][2];
+      for (int k = 0; k < 2; ++k) {
+        const int c = l + 32 * k;
+        if (c < NPW) sp[(j % PRR) * PPW + c] = p_item(j, c);
+      }
+    }
+  }
+  // b of this step's cells (bc) and of the next step's (bn), loaded two steps ahead
+  BCell bc = b_load(j0 - 2 + r);
+  BCell bn = b_load(j0 + 2 + r);
+  __syncthreads();
+
+  // prefetch registers (step t + 1): x rows 2 j0 + 8 t + 6 + {r, r + 4} x 2 column-pair
+  // chunks, p row j0 + 4 t + 3 + r x 2 chunks
+  XPair xpf[2][2];
+  float ppf[2];
+  float xold[9];   // x at the dofs of this step's update (loaded a step earlier; 0 for a zero guess)
+#pragma unroll
+  for (int k = 0; k < 9; ++k) xold[k] = 0.0f;
+  uint32_t mma_phase = 0;
+
+  for (int t = 0; t <= T + 2; ++t) {
+    // ================= phase A: residual of cell rows t, update, prefetch =================
+    const bool pf = (t + 1 <= T);
+    // the update of this step (vertex row vb) and, loaded a step ahead, the next
+    // step's x_old (9 values per vertex; in L2: its rows were loaded into the window)
+    const int vb = j0 + 4 * t - 12 + r;
+    const bool upd = vb >= j0 && vb < j0 + S && l >= 1 && l <= SW;
+    const int vi = i0 + l - 1;
+    const long long ke = static_cast<long long>(2 * vb) * nq + 2 * vi;   // node (2 vi, 2 vb)
+    const long long ko = ke - nq;                                         // node (2 vi, 2 vb - 1)
+    const long long kp = 2 * nv + static_cast<long long>(vb) * np + vi;
+    float xold_n[9];
+    {
+      const int vbn = vb + GR;
+      if (has_x && vbn >= j0 && vbn < j0 + S && l >= 1 && l <= SW) {
+        const long long ken = ke + 2LL * GR * nq, kon = ken - nq, kpn = kp + static_cast<long long>(GR) * np;
+        xold_n[0] = ldg_early(x + ken);
+        xold_n[1] = ldg_early(x + nv + ken);
+        xold_n[2] = ldg_early(x + ken - 1);
+        xold_n[3] = ldg_early(x + nv + ken - 1);
+        xold_n[4] = ldg_early(x + kon);
+        xold_n[5] = ldg_early(x + nv + kon);
+        xold_n[6] = ldg_early(x + kon - 1);
+        xold_n[7] = ldg_early(x + nv + kon - 1);
+        xold_n[8] = ldg_early(x + kpn);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) xold_n[k] = 0.0f;
+      }
+    }
+    BCell bn2;
+    if (t + 2 <= T) bn2 = b_load(j0 + 4 * t + 6 + r);
+    if (pf) {
+      if (has_x) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int J = 2 * j0 + 8 * t + 6 + r + 4 * h;
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const int q = l + 32 * k;
+            if (q < XN / 2) xpf[h][k] = x_pair(J, q);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int c = l + 32 * k;
+          if (c < NPW) ppf[k] = p_item(j0 + 4 * t + 3 + r, c);
+        }
+      }
+    }
+    if (t <= T) {
+      // cell (cx, cy) = (i0 - 2 + l, j0 - 2 + 4 t + r): Q2 nodes (2 cx + PI, 2 cy + PJ)
+      const int cy = j0 - 2 + 4 * t + r;
+      float2 res[2][2];
 #pragma unroll
       for (int PJ = 0; PJ < 2; ++PJ)
 #pragma unroll
-        for (int PI = 0; PI < 2; ++PI) sl[PJ][PI] = make_float2(0.0f, 0.0f);
-      float2 sdiv = make_float2(0.0f, 0.0f);
+        for (int PI = 0; PI < 2; ++PI) res[PJ][PI] = bc.v[PJ][PI];
+      float rp = bc.p;
+      if (has_x) {
+        float P[3][3];
 #pragma unroll
-      for (int a = 0; a < 6; ++a) {
-        float2 Xa[6];
+        for (int dj = 0; dj < 3; ++dj)
 #pragma unroll
-        for (int bb = 0; bb < 6; ++bb) Xa[bb] = xc[a * XP + (bb & 1) * XHALF + (bb >> 1)];
+          for (int di = 0; di < 3; ++di) P[dj][di] = sp[((cy - 1 + dj) % PRR) * PPW + l + di];
+        float2 slap[2][2];
+#pragma unroll
+        for (int PJ = 0; PJ < 2; ++PJ)
+#pragma unroll
+          for (int PI = 0; PI < 2; ++PI) slap[PJ][PI] = make_float2(0.0f, 0.0f);
+        float2 sdiv = make_float2(0.0f, 0.0f);
+        // rows a = 0..5 of the 6 x 6 pair neighbourhood (node (2 cx - 2 + bb, 2 cy - 2 + a))
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+          const float2* xrow = sx + ((2 * cy - 2 + a) % XR) * XPP + l;
+          float2 Xa[6];
+#pragma unroll
+          for (int bb = 0; bb < 6; ++bb) Xa[bb] = xrow[(bb & 1) * XHO + (bb >> 1)];
+#pragma unroll
+          for (int PJ = 0; PJ < 2; ++PJ) {
+#pragma unroll
+            for (int PI = 0; PI < 2; ++PI) {
+#pragma unroll
+              for (int bb = 0; bb < 6; ++bb) {
+                const int dJ = a - 2 - PJ, dI = bb - 2 - PI;
+                const float cf = (dJ < -2 || dJ > 2 || dI < -2 || dI > 2)
+                                     ? 0.0f
+                                     : static_cast<float>(k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ));
+                if (cf != 0.0f) slap[PJ][PI] = __ffma2_rn(make_float2(cf, cf), Xa[bb], slap[PJ][PI]);
+              }
+            }
+          }
+          if (a <= 4) {   // -int p div u of the vertex: C (x) N on u_x, N (x) C on u_y
+#pragma unroll
+            for (int bb = 0; bb < 5; ++bb) {
+              const float wx = static_cast<float>(crow(bb - 2) * nrow(a - 2));
+              const float wy = static_cast<float>(nrow(bb - 2) * crow(a - 2));
+              if (wx != 0.0f || wy != 0.0f) sdiv = __ffma2_rn(make_float2(wx, wy), Xa[bb], sdiv);
+            }
+          }
+        }
 #pragma unroll
         for (int PJ = 0; PJ < 2; ++PJ) {
 #pragma unroll
           for (int PI = 0; PI < 2; ++PI) {
-#pragma unroll
-            for (int bb = 0; bb < 6; ++bb) {
-              const int dJ = a - 2 - PJ, dI = bb - 2 - PI;
-              const float cf = (dJ < -2 || dJ > 2 || dI < -2 || dI > 2)
-                                   ? 0.0f
-                                   : static_cast<float>(k1(PI, dI) * m1(PJ, dJ) + m1(PI, dI) * k1(PJ, dJ));
-              if (cf != 0.0f) sl[PJ][PI] = __ffma2_rn(make_float2(cf, cf), Xa[bb], sl[PJ][PI]);
-            }
-          }
-        }
-        if (a <= 4) {   // -int p div u of the vertex: C (x) N on u_x, N (x) C on u_y
-#pragma unroll
-          for (int bb = 0; bb < 5; ++bb) {
-            const float wx = static_cast<float>(crow(bb - 2) * nrow(a - 2));
-            const float wy = static_cast<float>(nrow(bb - 2) * crow(a - 2));
-            if (wx != 0.0f || wy != 0.0f) sdiv = __ffma2_rn(make_float2(wx, wy), Xa[bb], sdiv);
-          }
-        }
-      }
-#pragma unroll
-      for (int PJ = 0; PJ < 2; ++PJ) {
-#pragma unroll
-        for (int PI = 0; PI < 2; ++PI) {
-          float g0 = 0.0f, g1 = 0.0f;   // (B^T p) / (-h/18) for u_x, u_y
-#pragma unroll
-          for (int dj = -1; dj <= 1; ++dj) {
-#pragma unroll
-            for (int di = -1; di <= 1; ++di) {
-              const float w0 = static_cast<float>(ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj));
-              const float w1 = static_cast<float>(ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj));
-              if (w0 != 0.0f) g0 = fmaf(w0, P[dj + 1][di + 1], g0);
-              if (w1 != 0.0f) g1 = fmaf(w1, P[dj + 1][di + 1], g1);
-            }
-          }
-          r[PJ][PI].x -= cl * sl[PJ][PI].x + cb * g0;
-          r[PJ][PI].y -= cl * sl[PJ][PI].y + cb * g1;
-        }
-      }
-      rp -= cb * (sdiv.x + sdiv.y);
-    }
-#pragma unroll
-    for (int PJ = 0; PJ < 2; ++PJ)
-#pragma unroll
-      for (int PI = 0; PI < 2; ++PI) sr[(2 * cy + PJ) * RP + PI * RHALF + cx] = r[PJ][PI];
-    if (own_p) srp[(cy - 1) * TT::QW + (cx - 1)] = rp;
-  }
-  __syncthreads();
-
-  // 3. this thread's patch row of R (BF16, core-matrix layout)
-  const int qj = tid / TT::QW, qi = tid - qj * TT::QW;
-  {
-    float row[64];
-#pragma unroll
-    for (int wj = 0; wj < 5; ++wj)
-#pragma unroll
-      for (int wi = 0; wi < 5; ++wi) {
-        const float2 v = sr[(2 * qj + wj) * RP + (wi & 1) * RHALF + qi + (wi >> 1)];
-        row[wj * 5 + wi] = v.x;
-        row[25 + wj * 5 + wi] = v.y;
-      }
-    row[50] = srp[tid];
-#pragma unroll
-    for (int k = 51; k < 64; ++k) row[k] = 0.0f;
-    unsigned char* arow = sm + OFF_A + (tid >> 3) * 1024 + (tid & 7) * 16;
-#pragma unroll
-    for (int kg = 0; kg < 8; ++kg) {
-      uint4 v;
-      __nv_bfloat162 h0 = __floats2bfloat162_rn(row[8 * kg + 0], row[8 * kg + 1]);
-      __nv_bfloat162 h1 = __floats2bfloat162_rn(row[8 * kg + 2], row[8 * kg + 3]);
-      __nv_bfloat162 h2 = __floats2bfloat162_rn(row[8 * kg + 4], row[8 * kg + 5]);
-      __nv_bfloat162 h3 = __floats2bfloat162_rn(row[8 * kg + 6], row[8 * kg + 7]);
-      memcpy(&v.x, &h0, 4);
-      memcpy(&v.y, &h1, 4);
-      memcpy(&v.z, &h2, 4);
-      memcpy(&v.w, &h3, 4);
-      *reinterpret_cast<uint4*>(arow + kg * 128) = v;
-    }
-  }
-  // make the generic-proxy writes of R visible to the tensor cores
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-  // 4. the GEMM: D[t] (128 x 64, FP32, TMEM columns 64 t) = R[t] B^T
-  __shared__ int ok_s;
-  if (tid == 0) {
-    int ok = mbar_wait(bar_b, 0, first_wait_limit) ? 1 : 0;
-    if (ok) {
-      const uint32_t a0 = su32(sm + OFF_A), b0 = su32(sm + OFF_B);
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const uint64_t da = umma_desc(a0 + t * 16384 + s * 256);
-          const uint64_t db = umma_desc(b0 + s * 256);
-          const uint32_t acc = s > 0 ? 1u : 0u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + t * 64),
-              "l"(da), "l"(db), "r"(IDESC), "r"(acc));
-        }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_mma)
-                   : "memory");
-    }
-    ok_s = ok;
-  }
-  __syncthreads();
-  bool ok = ok_s != 0 && mbar_wait(bar_mma, 0);
-  if (!ok && tid == 0) atomicExch(err, 1);
-  ok = __syncthreads_and(ok);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-  if (ok) {
-    // 5. this thread's row of D -> shared corrections (thread = patch)
-    float* sd = reinterpret_cast<float*>(sm + OFF_D);
-    const uint32_t taddr = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + 64 * (warp >> 2);
-    float d[64];
-#pragma unroll
-    for (int ch = 0; ch < 4; ++ch) tmem_ld16(taddr + 16 * ch, d + 16 * ch);
-    __syncthreads();  // every thread is done with R, B and the residual before they are overwritten
-#pragma unroll
-    for (int k = 0; k < 51; ++k) sd[tid * 51 + k] = d[k];
-    __syncthreads();
-    // 6. weighted update of the owned dofs: one thread per owned vertex (vi, vj);
-    //    its Q2 nodes (2i-1..2i) x (2j-1..2j) take the corrections of the 9 / 6 /
-    //    6 / 4 patches around them at compile-time offsets (patch q + dq, slot s).
-    //    Warp w takes vertex rows 2w and 2w + 1 (lanes 0..27): their patches q
-    //    lie in two rows of 16, distinct modulo 32, so the reads of D (pitch 51,
-    //    odd) are free of bank conflicts.
-    const int uw = tid >> 5, ul = tid & 31;
-    if (uw < TC_TILE / 2 && ul < 2 * TC_TILE) {
-      const int vj = 2 * uw + (ul >= TC_TILE ? 1 : 0), vi = ul - (ul >= TC_TILE ? TC_TILE : 0);
-      const int i = i0 + vi, j = j0 + vj;
-      const float* dq = sd + ((vj + 1) * TT::QW + (vi + 1)) * 51;  // the vertex's own patch
-      const int xj = 2 * j - XJ0, xi = 2 * i - XI0;                  // x window at node (2i, 2j)
-      const long long base = static_cast<long long>(2 * j) * nq + 2 * i;
-#pragma unroll
-      for (int nj = 0; nj < 2; ++nj) {        // node J = 2j - nj
-#pragma unroll
-        for (int ni = 0; ni < 2; ++ni) {      // node I = 2i - ni
-          const float2 xold = x != nullptr ? sx[(xj - nj) * XP + xcol(xi - ni)] : make_float2(0.0f, 0.0f);
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            float acc = 0.0f;
-            // patches (i + di, j + dj): di in {-1, 0, +1} for an even node, {-1, 0} for an odd one
+            float2 g = make_float2(0.0f, 0.0f);   // (B^T p) / (-h/18) for (u_x, u_y)
 #pragma unroll
             for (int dj = -1; dj <= 1; ++dj) {
 #pragma unroll
               for (int di = -1; di <= 1; ++di) {
-                if ((ni == 1 && di == 1) || (nj == 1 && dj == 1)) continue;
-                const int wi = 2 - ni - 2 * di, wj = 2 - nj - 2 * dj;  // window offsets of the node
-                acc += dq[(dj * TT::QW + di) * 51 + c * 25 + wj * 5 + wi];
+                const float w0 = static_cast<float>(ccol(2 + PI, 1 + di) * ncol(2 + PJ, 1 + dj));
+                const float w1 = static_cast<float>(ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj));
+                const float pv = P[dj + 1][di + 1];
+                if (w0 != 0.0f || w1 != 0.0f) g = __ffma2_rn(make_float2(w0, w1), make_float2(pv, pv), g);
               }
             }
-            const float w = omega * (ni ? 0.5f : (1.0f / 3.0f)) * (nj ? 0.5f : (1.0f / 3.0f));
-            xo[c * nv + base - static_cast<long long>(nj) * nq - ni] = fmaf(w, acc, c == 0 ? xold.x : xold.y);
+            const float2 ax = __ffma2_rn(make_float2(cl, cl), slap[PJ][PI], __fmul2_rn(make_float2(cb, cb), g));
+            res[PJ][PI] = __fadd2_rn(res[PJ][PI], make_float2(-ax.x, -ax.y));
           }
         }
+        rp -= cb * (sdiv.x + sdiv.y);
       }
-      const float xoldp = x != nullptr ? sp[(j - (j0 - 3)) * PP + (i - (i0 - 3))] : 0.0f;
-      xo[2 * nv + static_cast<long long>(j) * np + i] = fmaf(omega, dq[50], xoldp);
+#pragma unroll
+      for (int PJ = 0; PJ < 2; ++PJ) {
+        float2* rrow = sr + ((2 * cy + PJ) % RR) * RPP;
+        rrow[l] = res[PJ][0];
+        rrow[RHO + l] = res[PJ][1];
+      }
+      srp[(cy & (CRR - 1)) * NCC + l] = rp;
     }
-  } else if (tid == 0) {
-    // the bulk copy and the MMAs may still be in flight: wait (bounded) before leaving
-    mbar_wait(bar_b, 0);
-    if (ok_s) mbar_wait(bar_mma, 0);
+    // weighted update of vertex row vb (partial sums of patch rows vb - 1 .. vb + 1)
+    if (upd) {
+      const float4* pm = sps + ((vb - 1) % SRR) * 160 + l;
+      const float4* p0 = sps + (vb % SRR) * 160 + l;
+      const float4* pp = sps + ((vb + 1) % SRR) * 160 + l;
+      const float4 e4 = pm[4 * 32], e2 = p0[2 * 32], e0 = pp[0];   // node row 2 vb
+      const float4 o3 = pm[3 * 32], o1 = p0[1 * 32];               // node row 2 vb - 1
+      const float dp = spp[(vb % SRR) * 32 + l];
+      // (odd column 2 vi - 1, even column 2 vi) x (even row, odd row)
+      const float2 s_oe = __fadd2_rn(__fadd2_rn(make_float2(e4.x, e4.y), make_float2(e2.x, e2.y)),
+                                     make_float2(e0.x, e0.y));
+      const float2 s_ee = __fadd2_rn(__fadd2_rn(make_float2(e4.z, e4.w), make_float2(e2.z, e2.w)),
+                                     make_float2(e0.z, e0.w));
+      const float2 s_oo = __fadd2_rn(make_float2(o3.x, o3.y), make_float2(o1.x, o1.y));
+      const float2 s_eo = __fadd2_rn(make_float2(o3.z, o3.w), make_float2(o1.z, o1.w));
+      const float w9 = omega * (1.0f / 9.0f), w6 = omega * (1.0f / 6.0f), w4 = omega * 0.25f;
+      xo[ke] = fmaf(w9, s_ee.x, xold[0]);
+      xo[nv + ke] = fmaf(w9, s_ee.y, xold[1]);
+      xo[ke - 1] = fmaf(w6, s_oe.x, xold[2]);
+      xo[nv + ke - 1] = fmaf(w6, s_oe.y, xold[3]);
+      xo[ko] = fmaf(w6, s_eo.x, xold[4]);
+      xo[nv + ko] = fmaf(w6, s_eo.y, xold[5]);
+      xo[ko - 1] = fmaf(w4, s_oo.x, xold[6]);
+      xo[nv + ko - 1] = fmaf(w4, s_oo.y, xold[7]);
+      xo[kp] = fmaf(omega, dp, xold[8]);
+    }
+    // the MMA of step t - 1 must be complete before its operand is overwritten and
+    // its accumulator read (issued a whole phase A earlier); the inverse's bulk copy
+    // before the first MMA
+    if (tid == 0) {
+      bool ok = true;
+      if (t == 0) ok = mbar_wait(bar_b, 0, first_wait_limit);
+      if (ok && t >= 1 && t - 1 <= T) {
+        ok = mbar_wait(bar_mma, mma_phase);
+        mma_phase ^= 1u;
+      }
+      if (!ok) *s_fail = t == 0 ? 1 : 2;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (*s_fail) break;
+
+    // ================= phase B: gather the patch rows of group t =================
+    if (t <= T && l < NPC) {
+      // patch (pi, pj) = (i0 - 1 + l, j0 + 4 t - 3 + r); window node (2 pi - 2 + wi, 2 pj - 2 + wj)
+      // sits at residual column 2 l + wi (even: pair l + wi/2, odd: RHO + l + (wi-1)/2)
+      const int pj = j0 + 4 * t - 3 + r;
+      uint32_t w[26];
+#pragma unroll
+      for (int wj = 0; wj < 5; ++wj) {
+        const float2* rrow = sr + ((2 * pj - 2 + wj) % RR) * RPP + l;
+#pragma unroll
+        for (int wi = 0; wi < 5; ++wi) {
+          const float2 v = rrow[(wi & 1) * RHO + (wi >> 1)];
+          w[wj * 5 + wi] = pack_bf16x2(v.x, v.y);
+        }
+      }
+      w[25] = pack_bf16x2(srp[(pj & (CRR - 1)) * NCC + l + 1], 0.0f);
+      unsigned char* arow = sm + OFF_A + (tid >> 3) * 1024 + (tid & 7) * 16;
+#pragma unroll
+      for (int kg = 0; kg < 7; ++kg) {
+        const uint32_t a0 = 4 * kg < 26 ? w[4 * kg] : 0u;
+        const uint32_t a1 = 4 * kg + 1 < 26 ? w[4 * kg + 1] : 0u;
+        const uint32_t a2 = 4 * kg + 2 < 26 ? w[4 * kg + 2] : 0u;
+        const uint32_t a3 = 4 * kg + 3 < 26 ? w[4 * kg + 3] : 0u;
+        *reinterpret_cast<uint4*>(arow + kg * 128) = make_uint4(a0, a1, a2, a3);
+      }
+    }
+    // make the generic-proxy writes of R visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    // ================= phase C: MMA of group t; corrections of group t - 1 =================
+    if (tid == 0 && t <= T) {
+      const uint32_t a0 = su32(sm + OFF_A), b0 = su32(sm + OFF_B), acc = tmem + 64 * (t & 1);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const uint64_t da = umma_desc(a0 + s * 256);
+        const uint64_t db = umma_desc(b0 + s * 256);
+        const uint32_t accum = s > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
+            "l"(da), "l"(db), "r"(IDESC), "r"(accum));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_mma)
+                   : "memory");
+    }
+    __syncwarp();
+    if (t >= 1 && t - 1 <= T) {
+      // patch row pj = j0 + 4 (t - 1) - 3 + r, lane l = patch pi = i0 - 1 + l; the node
+      // columns 2 pi - 1 (odd) and 2 pi (even) of window row wj take
+      //   odd:  D[pi - 1](wi = 3) + D[pi](wi = 1)
+      //   even: D[pi - 1](wi = 4) + D[pi](wi = 2) + D[pi + 1](wi = 0)
+      const int pj = j0 + 4 * (t - 1) - 3 + r;
+      float d[52];
+      tmem_ld52(tmem + (static_cast<uint32_t>(32 * r) << 16) + 64 * ((t - 1) & 1), d);
+      float4* dst = sps + (pj % SRR) * 160 + l;
+#pragma unroll
+      for (int wj = 0; wj < 5; ++wj) {
+        const float* dw = d + 10 * wj;
+        const float u3x = __shfl_up_sync(0xffffffffu, dw[6], 1), u3y = __shfl_up_sync(0xffffffffu, dw[7], 1);
+        const float u4x = __shfl_up_sync(0xffffffffu, dw[8], 1), u4y = __shfl_up_sync(0xffffffffu, dw[9], 1);
+        const float d0x = __shfl_down_sync(0xffffffffu, dw[0], 1), d0y = __shfl_down_sync(0xffffffffu, dw[1], 1);
+        const float2 odd = __fadd2_rn(make_float2(u3x, u3y), make_float2(dw[2], dw[3]));
+        const float2 even = __fadd2_rn(__fadd2_rn(make_float2(u4x, u4y), make_float2(dw[4], dw[5])),
+                                       make_float2(d0x, d0y));
+        dst[wj * 32] = make_float4(odd.x, odd.y, even.x, even.y);
+      }
+      spp[(pj % SRR) * 32 + l] = d[50];
+    }
+    if (pf) {
+      if (has_x) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int J = 2 * j0 + 8 * t + 6 + r + 4 * h;
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const int q = l + 32 * k;
+            if (q < XN / 2) x_pair_store(J, q, xpf[h][k]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int c = l + 32 * k;
+          if (c < NPW) sp[((j0 + 4 * t + 3 + r) % PRR) * PPW + c] = ppf[k];
+        }
+      }
+      bc = bn;
+      bn = bn2;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) xold[k] = xold_n[k];
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
 
-  // teardown: free TMEM
+  const int fail = *s_fail;
+  if (fail && tid == 0) {
+    atomicExch(err, 1);
+    // the bulk copy, and an MMA issued before the failed wait, may still be in flight
+    mbar_wait(bar_b, 0);
+    if (fail == 2) mbar_wait(bar_mma, mma_phase ^ 1u);
+  }
+  // teardown: free tensor memory
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  if (r == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
 }  // namespace
 
-// Interior 14 x 14 tiles: origin i0 = 14 bx with 3 <= i0 and i0 + 14 <= n - 2,
-// so every patch (vertex i0-1 .. i0+14) is of the interior class.
+// Interior 14 x 14 tiles [lo, hi]^2 (both axes): origin i0 = 14 bx with 3 <= i0
+// and i0 + 14 <= n - 2, so every patch (vertex i0-1 .. i0+14) is of the interior
+// class.  Strips are two tiles wide, so the range holds an even number of tiles
+// (a last odd tile goes to the SIMT ring); no range below two tiles.
 void tc_interior_range(int n, int* lo, int* hi) {
   *lo = 1;
-  *hi = (n - 2 - TC_TILE) / TC_TILE;
-  if (n < 2 + 2 * TC_TILE) *hi = 0;  // no interior tile
+  int h = (n - 2 - TC_TILE) / TC_TILE;
+  if (n < 2 + 2 * TC_TILE) h = 0;
+  const int cnt = h - *lo + 1;
+  *hi = (cnt >= 2) ? *lo + (cnt & ~1) - 1 : 0;
 }
 
 cudaError_t vanka_tc_prepare() {
@@ -461,21 +626,33 @@ cudaError_t vanka_tc_prepare() {
 
 void launch_vanka_tc(const LevelDev& L, const void* Bcanon, const float* x, const float* b, float* xo,
                      double omega, int lo, int hi, int* err, cudaStream_t s, int first_wait_limit) {
-  if (hi < lo) return;
+  const int cnt = hi - lo + 1;
+  if (cnt < 2 || (cnt & 1)) return;
   count_launches(1);
   g_tc_launches.fetch_add(1, std::memory_order_relaxed);
-  const int g = hi - lo + 1;
-  launch_pdl(k_vanka_tc, dim3(dim3(g, g)), dim3(TC_NT), SMEM_BYTES, s, L, static_cast<const uint4*>(Bcanon), x, b, xo,
-                                                   static_cast<float>(omega), lo, err, first_wait_limit);
+  // segments of 4 tiles (fewer prologue steps) when that still gives the GPU
+  // several waves of CTAs, else of 2 tiles
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int seg = ((cnt / 2) * ((cnt + SEG_MAX - 1) / SEG_MAX) >= 16 * sms) ? SEG_MAX : 2;
+  const dim3 grid(cnt / 2, (cnt + seg - 1) / seg);
+  launch_pdl(k_vanka_tc, grid, dim3(NT), SMEM_BYTES, s, L, static_cast<const uint4*>(Bcanon), x, b, xo,
+             static_cast<float>(omega), lo, hi, seg, err, first_wait_limit);
 }
 
+// slot of the dense 51 x 51 inverse (u_x window 0..24, u_y window 25..49, p 50)
+// at position k of the kernel's patch row: (u_x, u_y) of window node s at 2 s, 2 s + 1
+static int tc_slot(int k) { return k == 50 ? 50 : (k & 1) * 25 + (k >> 1); }
+
 void tc_pack_inverse(const double* inv51, unsigned short* out) {
-  // B[n][k] = A_int^-1[n][k] (N = output slot, K = input slot), zero padded to 64 x 64,
-  // stored K-major in 8 x 8 core matrices: byte offset (n/8)*1024 + (k/8)*128 + (n%8)*16 + (k%8)*2
+  // B[n][k] = A_int^-1[slot(n)][slot(k)] (N = output position, K = input position),
+  // zero padded to 64 x 64, stored K-major in 8 x 8 core matrices: byte offset
+  // (n/8)*1024 + (k/8)*128 + (n%8)*16 + (k%8)*2
   for (int i = 0; i < 64 * 64; ++i) out[i] = 0;
   for (int nn = 0; nn < 51; ++nn) {
     for (int k = 0; k < 51; ++k) {
-      const float v = static_cast<float>(inv51[nn * 51 + k]);
+      const float v = static_cast<float>(inv51[tc_slot(nn) * 51 + tc_slot(k)]);
       const __nv_bfloat16 h = __float2bfloat16_rn(v);
       unsigned short bits;
       memcpy(&bits, &h, 2);

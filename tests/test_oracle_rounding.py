@@ -60,17 +60,19 @@ def ratio(a, b, bound):
 
 
 def test_tensor_core_mask_counts():
-    """Tiles 1..hi of 14 vertices per axis, hi = (n - 16) // 14: at n = 64 tiles 1..3 hold
-    vertices 14..55; the Q2 nodes they own are 2 * 14 - 1 .. 2 * 55 per axis."""
+    """Tiles 1..hi of 14 vertices per axis, hi = (n - 16) // 14 rounded down to an even
+    count: at n = 64 (hi = 3 -> 2) tiles 1..2 hold vertices 14..41; the Q2 nodes they own
+    are 2 * 14 - 1 .. 2 * 41 per axis.  At n = 128 tiles 1..8, at n = 32 none (one tile)."""
     m = RB.tensor_core_dofs(64)
     nq, npv = 129, 65
     q = m[:nq * nq].reshape(nq, nq)
     idx = np.flatnonzero(q[64])
-    assert idx[0] == 27 and idx[-1] == 110 and len(idx) == 84
+    assert idx[0] == 27 and idx[-1] == 82 and len(idx) == 56
     assert np.array_equal(m[:nq * nq], m[nq * nq:2 * nq * nq])
     p = m[2 * nq * nq:].reshape(npv, npv)
-    assert p.sum() == 42 * 42 and p[14, 14] and not p[13, 14] and p[55, 55] and not p[56, 55]
-    assert not RB.tensor_core_dofs(16).any()
+    assert p.sum() == 28 * 28 and p[14, 14] and not p[13, 14] and p[41, 41] and not p[42, 41]
+    assert RB.tensor_core_dofs(128)[2 * 257 * 257:].sum() == 112 * 112
+    assert not RB.tensor_core_dofs(32).any() and not RB.tensor_core_dofs(16).any()
 
 
 @pytest.mark.parametrize("zero_guess", [False, True])
