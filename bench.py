@@ -242,6 +242,39 @@ TRAFFIC_1024 = {
 }
 
 
+def fp64_peak(dev) -> dict:
+    """The FP64 peak of this GPU, measured in this run: the library's FMA-chain probe
+    (stokes_measure_fp64_peak) and a cuBLAS DGEMM (4096^3, through torch.matmul),
+    best of three each; the larger is the roofline denominator of the FP64 kernels."""
+    import torch
+
+    from paper_2401_06277_gb300 import stokes
+    probe = stokes.stokes_measure_fp64_peak()
+    n = 4096
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    a = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    dgemm = 2.0 * n ** 3 / (best * 1e-3) / 1e9
+    del a, b
+    return {"peak": max(probe, dgemm), "fma_probe_gflops": round(probe, 1), "dgemm_gflops": round(dgemm, 1),
+            "source": "measured in this run: FP64 FMA-chain probe (stokes_measure_fp64_peak) and cuBLAS "
+                      "DGEMM 4096^3 (torch.matmul), best of three each; the larger of the two"}
+
+
+FP64_PEAK = None   # set once per run by run_ours
+
+
 def measured_peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -357,12 +390,12 @@ def _time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother, h
         fl = (n + 1) ** 2 * 620.0
         by = esz * (7.0 * dofs(n) + 8.0 * (n + 1) ** 2)
         if prec_name == "fp64":
-            peak = SM_COUNT * 4 * sm_max * 1e6 / 1e9
+            peak = FP64_PEAK["peak"]
             achieved = fl / (sweep_ms * 1e-3) / 1e9
             roofline = {"bound": "alu", "kernel": "Braess-Sarazin sweep (k_apply + k_bs_*, finest level)",
                         "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "GFLOP/s",
                         "frac": round(achieved / peak, 4), "traffic": None,
-                        "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock",
+                        "peak_source": FP64_PEAK["source"],
                         "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
                         "hbm_gbs_achieved": round(by / (sweep_ms * 1e-3) / 1e9, 1)}
         else:
@@ -378,12 +411,12 @@ def _time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother, h
         # bytes: the inverse (2601 doubles), x, b, x_out and the 51 corrections written and read
         fl = (n + 1) ** 2 * (361.0 + 5202.0 + 68.0)
         by = (n + 1) ** 2 * 8.0 * (2601 + 2 * 51) + sweep_bytes(n)
-        peak = SM_COUNT * 4 * sm_max * 1e6 / 1e9
+        peak = FP64_PEAK["peak"]
         achieved = fl / (sweep_ms * 1e-3) / 1e9
         roofline = {"bound": "alu", "kernel": "simple Vanka sweep (k_apply + k_patch_solve + k_patch_update, finest)",
                     "achieved": round(achieved, 2), "peak": round(peak, 1), "unit": "GFLOP/s",
                     "frac": round(achieved / peak, 4), "traffic": None,
-                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock",
+                    "peak_source": FP64_PEAK["source"],
                     "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
                     "hbm_gbs_achieved": round(by / (sweep_ms * 1e-3) / 1e9, 1),
                     "hbm_frac": round(by / (sweep_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6780.0), 4)}
@@ -391,15 +424,16 @@ def _time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother, h
         # the first pre-smoothing sweep of each cycle starts from zero (no residual: 361 flops
         # per vertex fewer); the timed launches average over all nu1 + nu2 sweeps
         fl = sweep_flops(n) - ZERO_GUESS_SHARE * 361.0 * (n + 1) ** 2
-        peak = SM_COUNT * 4 * sm_max * 1e6 / 1e9   # 2 DFMA / clk / SM
+        peak = FP64_PEAK["peak"]
         achieved = fl / (sweep_ms * 1e-3) / 1e9
         kname = ("k_vanka_own<double,16,16> + k_patch_update (split sweep, finest level)" if tile.startswith("split")
                  else "k_vanka<double> (finest level)")
         roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 2),
                     "peak": round(peak, 1), "unit": "GFLOP/s", "frac": round(achieved / peak, 4),
                     "traffic": args.traffic,
-                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock (FP64 has no "
-                                   "measured entry; an FMA-loop probe reached 1196 GFLOP/s)",
+                    "peak_source": FP64_PEAK["source"],
+                    "fp64_peaks": {k: FP64_PEAK[k] for k in ("fma_probe_gflops", "dgemm_gflops")},
+                    "nominal_gflops": round(SM_COUNT * 4 * sm_max * 1e6 / 1e9, 1),
                     "algorithmic_flops_per_launch": fl,
                     "algorithmic_bytes_per_launch": sweep_bytes(n) * (3.0 - ZERO_GUESS_SHARE) / 3.0,
                     "hbm_gbs_achieved": round(sweep_bytes(n) * (3.0 - ZERO_GUESS_SHARE) / 3.0 / (sweep_ms * 1e-3) / 1e9, 1)}
@@ -563,6 +597,8 @@ def run_ours(args) -> None:
 
     ws, rank, local = dist_setup(args.gpus)
     build.build()
+    global FP64_PEAK
+    FP64_PEAK = fp64_peak(torch.device("cuda", torch.cuda.current_device()))
     n = args.n
     N = dofs(n)
     f_host = torch.from_numpy(si.random_force(n, args.seed + rank)).pin_memory()
@@ -699,6 +735,17 @@ def run_kernel(args) -> None:
     elif args.kernel == "residual":
         fn = lambda: stokes.stokes_residual(H.handle, lvl, b, x, out)
         fl, by = 361.0 * (n + 1) ** 2, sweep_bytes(n)
+    elif args.kernel == "solve":
+        # one FGMRES(30) solve to 1e-8 of the seeded N(0,1)-force problem
+        H.close()
+        H = pkg.Hierarchy(n, tile=args.tile, prec=PRECS[args.prec], smoother=args.smoother)
+        bb = H.assemble_rhs(torch.from_numpy(si.random_force(n, 0)).cuda(),
+                            torch.from_numpy(si.manufactured_velocity(n)).cuda())
+
+        def fn():
+            stokes.stokes_initial_guess(H.handle, bb, out)
+            stokes.stokes_fgmres_solve(H.handle, bb, out)
+        fl, by = None, None
     else:
         fn = lambda: stokes.stokes_vcycle_apply(H.handle, b, out)
         fl, by = None, None
@@ -742,7 +789,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--oracle-worker", action="store_true")
     ap.add_argument("--tile", type=int, default=-1, help="Vanka sweep configuration (-1: autotuned; 0..3 fused 8x8/16x8/16x16/14x14, 4/5 split 16x16, 6 fused 4x4)")
-    ap.add_argument("--kernel", choices=["sweep", "residual", "vcycle"], default=None,
+    ap.add_argument("--kernel", choices=["sweep", "residual", "vcycle", "solve"], default=None,
                     help="time one kernel alone on the finest level (profiling mode)")
     ap.add_argument("--smoother", type=int, choices=[0, 1, 2, 3], default=0,
                     help="profiling mode: 0 shared-inverse Vanka, 1 simple Vanka, 2 Braess-Sarazin, 3 Schur-Uzawa")

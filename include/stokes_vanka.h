@@ -288,6 +288,14 @@ typedef struct {
                                kernel_launches (all hierarchies, since load)           */
 } stokes_stats;
 
+/* The FP64 FMA throughput of the current device in GFLOP/s, measured: a kernel
+ * of independent FMA chains on every SM, timed with CUDA events on `stream`
+ * (best of three launches, about 10 ms each; synchronises).  The FP64 form is
+ * bound by the FP64 pipe, and this is the peak its roofline fraction uses (the
+ * paper's roofline, Section 6.7, likewise uses measured peaks).  gflops must
+ * not be NULL. */
+stokes_status stokes_measure_fp64_peak(void* stream, double* gflops);
+
 stokes_status stokes_stats_enable_timing(stokes_hierarchy* h, int enable);
 stokes_status stokes_stats_reset(stokes_hierarchy* h);
 stokes_status stokes_stats_read(stokes_hierarchy* h, stokes_stats* out);

@@ -98,6 +98,7 @@ def _load():
         "stokes_solve_adjoint": (I, [P, VP, VP, VP, IP, DP]),
         "stokes_rhs_transpose": (I, [P, VP, VP]),
         "stokes_batched_solve": (I, [ctypes.POINTER(P), I, ctypes.POINTER(VP), ctypes.POINTER(VP), IP, DP]),
+        "stokes_measure_fp64_peak": (I, [VP, DP]),
         "stokes_stats_enable_timing": (I, [P, I]),
         "stokes_stats_reset": (I, [P]),
         "stokes_stats_read": (I, [P, ctypes.POINTER(stokes_stats)]),
@@ -125,7 +126,7 @@ def exported_symbols() -> list[str]:
             "stokes_test_set_wait_limit", "stokes_test_set_alloc_limit", "stokes_restrict", "stokes_prolong_add",
             "stokes_coarse_solve", "stokes_initial_guess", "stokes_vcycle_apply", "stokes_fgmres_solve",
             "stokes_solve_adjoint", "stokes_rhs_transpose", "stokes_batched_solve",
-            "stokes_stats_enable_timing", "stokes_stats_reset", "stokes_stats_read",
+            "stokes_measure_fp64_peak", "stokes_stats_enable_timing", "stokes_stats_reset", "stokes_stats_read",
             "stokes_residual_norm_noalloc", "stokes_batch_create", "stokes_batch_destroy",
             "stokes_batch_hierarchy", "stokes_batch_solve", "stokes_last_error"]
 
@@ -305,6 +306,14 @@ def stokes_batched_solve(hs, bs, xs) -> tuple[list[int], list[float]]:
     rel = (ctypes.c_double * k)()
     _check(_load().stokes_batched_solve(H, k, B, X, it, rel))
     return list(it), list(rel)
+
+
+def stokes_measure_fp64_peak(stream: torch.cuda.Stream | None = None) -> float:
+    """FP64 FMA throughput of the current device in GFLOP/s (measured; synchronises)."""
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    g = ctypes.c_double(0.0)
+    _check(_load().stokes_measure_fp64_peak(ctypes.c_void_p(s), ctypes.byref(g)))
+    return g.value
 
 
 def stokes_stats_enable_timing(h, enable: bool) -> None:

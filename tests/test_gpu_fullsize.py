@@ -209,3 +209,49 @@ def test_fullsize_mixed_solutions_as_accurate_as_fp64(big):
         print(f"2048^2 prec {prec}: iters {it}, error vs 1e-11 solve {em:.3e} (FP64 at 1e-8: {e64:.3e}), "
               f"difference to the FP64 form {d:.3e}")
         assert rr <= 1e-8 and em <= 2.0 * e64 + 1e-8, (prec, em, e64)
+
+
+def test_fullsize_mixed_gap_is_the_tolerance(big):
+    """The benchmark's 2048^2 problem (N(0,1) nodal force, seed 0) solved in FP64, mixed
+    FP32 and mixed BF16 at rtol 1e-8 and 1e-10, and in FP64 at 1e-11.  Two solves stopped
+    at a residual tolerance differ by up to the operator's conditioning times that
+    tolerance, so the gap between a mixed solution and the FP64 one must shrink with the
+    tolerance: at rtol 1e-10 both mixed solutions are within 1e-7 (max norm, relative,
+    pressures at zero mean) of the FP64 solution at 1e-10.  The table is printed."""
+    import paper_2401_06277_gb300 as pkg
+    n = NBIG
+    f = gpu(si.random_force(n, 0))
+    ud = gpu(si.manufactured_velocity(n))
+    b = big.assemble_rhs(f, ud)
+    sol = {}
+    for prec in (0, 1, 2):
+        for rtol in (1e-8, 1e-10):
+            H = pkg.Hierarchy(n, rtol=rtol, restart=30, prec=prec)
+            x, it, rr = H.solve(b)
+            H.close()
+            assert rr <= rtol, (prec, rtol, rr)
+            sol[(prec, rtol)] = (x, it)
+    H = pkg.Hierarchy(n, rtol=1e-11, restart=30)
+    xref, _, rr = H.solve(b)
+    H.close()
+    assert rr <= 1e-11
+    names = {0: "FP64", 1: "FP32", 2: "BF16"}
+    rows = []
+    for rtol in (1e-8, 1e-10):
+        x64 = sol[(0, rtol)][0]
+        for prec in (0, 1, 2):
+            x, it = sol[(prec, rtol)]
+            d = _zero_mean_diff(x, x64, n)
+            e = _zero_mean_diff(x, xref, n)
+            rows.append((rtol, names[prec], it, d, e))
+    print("\nrtol   form  iters  diff-to-FP64-same-rtol  diff-to-FP64-1e-11")
+    for rtol, nm, it, d, e in rows:
+        print(f"{rtol:.0e}  {nm}  {it:5d}  {d:22.3e}  {e:18.3e}")
+    for rtol, nm, it, d, e in rows:
+        if rtol == 1e-10 and nm != "FP64":
+            assert d <= 1e-7, (nm, d)
+    # the gap shrinks with the tolerance
+    for prec in (1, 2):
+        d8 = _zero_mean_diff(sol[(prec, 1e-8)][0], sol[(0, 1e-8)][0], n)
+        d10 = _zero_mean_diff(sol[(prec, 1e-10)][0], sol[(0, 1e-10)][0], n)
+        assert d10 <= 0.1 * d8, (prec, d8, d10)
