@@ -139,6 +139,28 @@ def oracle_worker(n: int, reps: int) -> None:
                       "value": dofs(n) * it / per}))
 
 
+def oracle_vcycle(n: int) -> None:
+    """Time the CPU oracle's set-up and one V(2,2) cycle at n x n (single thread; prints
+    one JSON object).  At 2048^2 this takes minutes of set-up and about a minute per
+    V-cycle, too long for the bounded CPU sample of the default run: run it on demand."""
+    import resource
+
+    import stokes_inputs as si
+    from oracle import stokes_oracle as O
+
+    t0 = time.perf_counter()
+    H = O.build_hierarchy(n)
+    lv = H.levels[-1]
+    b = O.assemble_rhs(lv, si.random_force(n, 0), si.manufactured_velocity(n))
+    setup = time.perf_counter() - t0
+    t = time.perf_counter()
+    O.vcycle(H, b)
+    vc = time.perf_counter() - t
+    print(json.dumps({"n": n, "dofs": dofs(n), "levels": len(H.levels), "setup_s": setup, "vcycle_s": vc,
+                      "value": dofs(n) / vc, "unit": UNIT, "cores": 1,
+                      "max_rss_gb": resource.getrusage(resource.RUSAGE_SELF).ru_maxrss / 1e6}))
+
+
 def run_oracle(n: int, reps: int) -> dict:
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
@@ -788,6 +810,8 @@ def main():
     ap.add_argument("--batch-rhs", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--oracle-worker", action="store_true")
+    ap.add_argument("--oracle-vcycle", type=int, default=None, metavar="N",
+                    help="time the CPU oracle's set-up and one V-cycle at N x N (single thread) and exit")
     ap.add_argument("--tile", type=int, default=-1, help="Vanka sweep configuration (-1: autotuned; 0..3 fused 8x8/16x8/16x16/14x14, 4/5 split 16x16, 6 fused 4x4)")
     ap.add_argument("--kernel", choices=["sweep", "residual", "vcycle", "solve"], default=None,
                     help="time one kernel alone on the finest level (profiling mode)")
@@ -799,6 +823,9 @@ def main():
         return
     if args.oracle_worker:
         oracle_worker(args.n, args.steps)
+        return
+    if args.oracle_vcycle:
+        oracle_vcycle(args.oracle_vcycle)
         return
     if args.impl == "reference":
         run_reference(args)

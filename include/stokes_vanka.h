@@ -105,6 +105,17 @@ typedef struct {
   int bt_nu;               /*                                       (3)    */
   double bt_omega_u;       /* Jacobi weight on L                    (1.0)  */
   double bt_omega_p;       /* Jacobi weight on M                    (0.6)  */
+  int tail_n;       /* mixed forms with Vanka relaxation: the levels with n <=
+                       tail_n below the finest one run the whole cycle there
+                       (sweeps, residuals, transfers, coarse solve; V or W) as
+                       one persistent cooperative launch with grid barriers,
+                       with the 8 x 8 SIMT sweep tile; 0 = launch kernel by
+                       kernel; negative (a test mode): the same kernel and steps
+                       for n <= -tail_n, one launch per step.  Off by default:
+                       on GB300 the coarse levels are bound by the latency of
+                       a tile's patch solves, which the launch does not remove,
+                       and the grid barriers cost more than the launches they
+                       replace                                           (0)    */
 } stokes_params;
 
 /* How each Vanka patch solve A_i^-1 r_i is applied (Section 4, Section 6.2). */
@@ -320,6 +331,19 @@ stokes_status stokes_device_status(stokes_hierarchy* h);
  *    creation frees what it holds and returns STOKES_ERR_OOM.  0 removes it. */
 stokes_status stokes_test_set_wait_limit(stokes_hierarchy* h, int polls);
 void stokes_test_set_alloc_limit(long long bytes);
+/*  - stokes_test_set_grid_barrier: polls of each grid barrier of the persistent
+ *    coarse-level launch before it gives up (negative: the default, about a
+ *    quarter of a second), and a CTA that withholds its arrival at the first
+ *    barrier (negative: none).  The other CTAs' waits then expire: they set
+ *    the hierarchy's error flag and the kernel returns; the next synchronising
+ *    call reports STOKES_ERR_TIMEOUT and resets the barrier. */
+stokes_status stokes_test_set_grid_barrier(stokes_hierarchy* h, int polls, int withhold_cta);
+
+/* The persistent coarse-level launch of a hierarchy (stokes_params.tail_n):
+ * its top level (-1: none; the levels 0..top run in one launch), the number of
+ * steps of one cycle there (sweeps, residuals, transfers, coarse solve; each
+ * ends at a grid barrier) and the CTAs of the cooperative launch. */
+stokes_status stokes_tail_info(const stokes_hierarchy* h, int* top_level, int* steps, int* ctas);
 
 /* Largest grid accepted by stokes_residual_norm_noalloc. */
 #define STOKES_NOALLOC_MAX_N 8192

@@ -116,6 +116,13 @@ void free_all(stokes_hierarchy* h) {
   h->ticket = nullptr;
   cudaFree(h->aux);
   h->aux = nullptr;
+  cudaFree(h->tail_ops);
+  cudaFree(h->tail_levels);
+  cudaFree(h->tail_bar);
+  h->tail_ops = nullptr;
+  h->tail_levels = nullptr;
+  h->tail_bar = nullptr;
+  h->tail_top = -1;
   if (h->ring_stream) {
     cudaStreamSynchronize(h->ring_stream);
     cudaStreamDestroy(h->ring_stream);
@@ -277,11 +284,103 @@ const char* level_range_name(const sv::Level& L, int l) {
 template <typename R>
 void vcycle_level(stokes_hierarchy* h, int l, const R* b, R* out);
 
+// The persistent coarse-level launch (FP32 cycles only): levels 0..tail_top in one
+// cooperative kernel running the steps recorded by tail_build.
+bool run_tail(stokes_hierarchy* h, int l, const double*, double*) { (void)h; (void)l; return false; }
+bool run_tail(stokes_hierarchy* h, int l, const float* b, float* out) {
+  if (l != h->tail_top || b != h->lv[l].bf || out != h->lv[l].ef) return false;
+  nvtxRangePushA("mg levels 0..tail (persistent launch)");
+  if (h->prm.tail_n > 0) {
+    sv::launch_tail(h->tail_ops, h->tail_nops, h->tail_levels, h->coarse_G, h->N0, h->fdf, h->prm.omega,
+                    h->tail_bar, h->dev_err, h->tail_spin_limit, h->tail_skip_arrival, h->tail_grid, h->stream);
+  } else {   // test mode: the same kernel and steps, one launch per step (no grid barrier)
+    for (int k = 0; k < h->tail_nops; ++k)
+      sv::launch_tail(h->tail_ops + k, 1, h->tail_levels, h->coarse_G, h->N0, h->fdf, h->prm.omega, h->tail_bar,
+                      h->dev_err, h->tail_spin_limit, -1, h->tail_grid, h->stream);
+  }
+  nvtxRangePop();
+  return true;
+}
+
 template <typename R>
 void vcycle(stokes_hierarchy* h, int l, const R* b, R* out) {
+  if (run_tail(h, l, b, out)) return;
   nvtxRangePushA(level_range_name(h->lv[l], l));
   vcycle_level<R>(h, l, b, out);
   nvtxRangePop();
+}
+
+// The steps of vcycle_level<float> on level l and below, in launch order, with the
+// same buffers (Algorithm 1; the coarse solve through the bordered inverse).
+void tail_build(stokes_hierarchy* h, int l, const float* b, float* out, std::vector<sv::TailOp>& ops) {
+  sv::Level& L = h->lv[l];
+  if (l == 0) {
+    ops.push_back({sv::TAIL_COARSE, 0, b, nullptr, out});
+    return;
+  }
+  float* X0 = L.xf0;
+  float* X1 = L.xf1;
+  float* cur = nullptr;
+  for (int it = 0; it < h->prm.nu1; ++it) {
+    float* dst = (cur == X0) ? X1 : X0;
+    ops.push_back({sv::TAIL_SWEEP, l, cur, b, dst});
+    cur = dst;
+  }
+  if (cur == nullptr) {
+    ops.push_back({sv::TAIL_ZERO, l, nullptr, nullptr, X0});
+    cur = X0;
+  }
+  sv::Level& C = h->lv[l - 1];
+  const int passes = (l - 1 == 0) ? 1 : h->prm.cycle;
+  for (int g = 0; g < passes; ++g) {
+    ops.push_back({sv::TAIL_RESID, l, cur, b, L.rf});
+    ops.push_back({sv::TAIL_RESTRICT, l, L.rf, nullptr, C.bf});
+    tail_build(h, l - 1, C.bf, C.ef, ops);
+    ops.push_back({sv::TAIL_PROLONG, l, C.ef, nullptr, cur});
+  }
+  for (int it = 0; it < h->prm.nu2; ++it) {
+    float* dst = (it == h->prm.nu2 - 1) ? out : ((cur == X0) ? X1 : X0);
+    ops.push_back({sv::TAIL_SWEEP, l, cur, b, dst});
+    cur = dst;
+  }
+  if (h->prm.nu2 == 0) ops.push_back({sv::TAIL_COPY, l, cur, nullptr, out});
+}
+
+// Levels n <= tail_n below the finest one, for an FP32 Vanka cycle: the tail's
+// step list, level table and barrier state on the device.
+cudaError_t tail_setup(stokes_hierarchy* h) {
+  const int top = static_cast<int>(h->lv.size()) - 2;
+  const int tail_n = h->prm.tail_n < 0 ? -h->prm.tail_n : h->prm.tail_n;
+  if (tail_n == 0 || h->prm.prec == STOKES_FP64 || h->prm.smoother != STOKES_SMOOTHER_SHARED ||
+      h->prm.precond != 0 || top < 1)
+    return cudaSuccess;
+  int t = -1;
+  for (int l = 1; l <= top; ++l)
+    if (h->lv[l].d.n <= tail_n) t = l;
+  if (t < 1 || t > 7) return cudaSuccess;
+  int max_ctas = 0;
+  cudaError_t e = sv::tail_prepare(&max_ctas);
+  if (e != cudaSuccess) return e;
+  std::vector<sv::TailOp> ops;
+  tail_build(h, t, h->lv[t].bf, h->lv[t].ef, ops);
+  std::vector<sv::TailLevel> lv(t + 1);
+  for (int l = 0; l <= t; ++l) lv[l] = {h->lv[l].d, h->lv[l].cdf};
+  const int np = h->lv[t].d.np, tiles = ((np + 7) / 8) * ((np + 7) / 8);
+  h->tail_grid = max_ctas < tiles ? max_ctas : tiles;
+  if (h->tail_grid < 1) return cudaSuccess;
+  if ((e = dalloc(&h->tail_ops, ops.size())) != cudaSuccess) return e;
+  if ((e = dalloc(&h->tail_levels, lv.size())) != cudaSuccess) return e;
+  if ((e = dalloc(&h->tail_bar, 2)) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(h->tail_ops, ops.data(), ops.size() * sizeof(sv::TailOp), cudaMemcpyHostToDevice)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpy(h->tail_levels, lv.data(), lv.size() * sizeof(sv::TailLevel), cudaMemcpyHostToDevice)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemset(h->tail_bar, 0, 2 * sizeof(unsigned))) != cudaSuccess) return e;
+  h->tail_nops = static_cast<int>(ops.size());
+  h->tail_top = t;
+  return cudaSuccess;
 }
 
 template <typename R>
@@ -434,9 +533,11 @@ stokes_status read_scalar(stokes_hierarchy* h, const double* dev, double* out) {
   int flag = 0;
   std::memcpy(&flag, h->host_scalars + 1, sizeof(int));
   if (flag != 0) {
-    // reported once: the flag is cleared so that the hierarchy stays usable
+    // reported once: the flag (and the grid-barrier state) is cleared so that the
+    // hierarchy stays usable
     cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream);
-    return fail(STOKES_ERR_TIMEOUT, "a bounded device wait expired in the tensor-core sweep");
+    if (h->tail_bar) cudaMemsetAsync(h->tail_bar, 0, 2 * sizeof(unsigned), h->stream);
+    return fail(STOKES_ERR_TIMEOUT, "a bounded device wait expired (tensor-core sweep or grid barrier)");
   }
   return STOKES_OK;
 }
@@ -667,6 +768,7 @@ cudaError_t choose_tiles(stokes_hierarchy* h) {
     }
     L.vk_cfg = L.vk_cfg_f = (L.d.n < 64) ? 0 : 1;
     if (&L == &h->lv.front()) continue;   // the coarsest level is solved exactly: no sweeps
+    if (static_cast<int>(&L - &h->lv.front()) <= h->tail_top) continue;   // swept by the persistent launch
     // only the precision the V-cycle runs in is tuned (the FP64 sweep of a
     // mixed hierarchy serves stokes_vanka_sweep alone and keeps 16x8)
     cudaError_t e = cudaSuccess;
@@ -707,6 +809,7 @@ void stokes_default_params(stokes_params* p) {
   p->bt_nu = 3;
   p->bt_omega_u = 1.0;
   p->bt_omega_p = 0.6;
+  p->tail_n = 0;
 }
 
 const char* stokes_last_error(void) { return g_err.c_str(); }
@@ -894,6 +997,11 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
     delete h;
     return cuda_fail(e, "Krylov workspace allocation");
   }
+  if ((e = tail_setup(h)) != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return cuda_fail(e, "persistent coarse-level set-up");
+  }
   if ((e = choose_tiles(h)) != cudaSuccess) {
     free_all(h);
     delete h;
@@ -1037,7 +1145,8 @@ stokes_status stokes_device_status(stokes_hierarchy* h) {
   std::memcpy(&flag, h->host_scalars + 1, sizeof(int));
   if (flag != 0) {
     SV_TRY(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream), "clear error flag");
-    return fail(STOKES_ERR_TIMEOUT, "a bounded device wait expired in the tensor-core sweep");
+    if (h->tail_bar) SV_TRY(cudaMemsetAsync(h->tail_bar, 0, 2 * sizeof(unsigned), h->stream), "reset grid barrier");
+    return fail(STOKES_ERR_TIMEOUT, "a bounded device wait expired (tensor-core sweep or grid barrier)");
   }
   return STOKES_OK;
 }
@@ -1049,6 +1158,21 @@ stokes_status stokes_test_set_wait_limit(stokes_hierarchy* h, int polls) {
 }
 
 void stokes_test_set_alloc_limit(long long bytes) { g_alloc_cap.store(bytes > 0 ? bytes : 0); }
+
+stokes_status stokes_test_set_grid_barrier(stokes_hierarchy* h, int polls, int withhold_cta) {
+  if (!h) return fail(STOKES_ERR_ARG, "null hierarchy");
+  h->tail_spin_limit = (polls < 0 || polls > sv::TAIL_SPIN_LIMIT) ? sv::TAIL_SPIN_LIMIT : polls;
+  h->tail_skip_arrival = withhold_cta >= 0 ? withhold_cta : -1;
+  return STOKES_OK;
+}
+
+stokes_status stokes_tail_info(const stokes_hierarchy* h, int* top_level, int* steps, int* ctas) {
+  if (!h) return fail(STOKES_ERR_ARG, "null hierarchy");
+  if (top_level) *top_level = h->tail_top;
+  if (steps) *steps = h->tail_nops;
+  if (ctas) *ctas = h->tail_grid;
+  return STOKES_OK;
+}
 
 stokes_status stokes_restrict(stokes_hierarchy* h, int level, const double* r_fine, double* r_coarse) {
   stokes_status st = check_level(h, level, 1);

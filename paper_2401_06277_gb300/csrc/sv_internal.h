@@ -88,6 +88,8 @@ using FastDiag = FastDiagT<double>;
 
 // Braess-Sarazin / Schur-Uzawa parameters (Sections 3.1, 3.3; see stokes_params).
 constexpr int TC_WAIT_LIMIT = 1 << 22;   // polls of an mbarrier before a tensor-core sweep's wait gives up
+constexpr int TAIL_SPIN_LIMIT = 1 << 22;   // polls (about 64 ns apart) of a grid barrier before it gives up
+
 
 struct BSParams {
   double t = 1.0, omega = 1.0, jacobi_weight = 1.0;
@@ -138,6 +140,32 @@ template <>
 __host__ __device__ inline double level_zsinv<double>(const LevelDev& L) { return L.zsinv; }
 template <>
 __host__ __device__ inline float level_zsinv<float>(const LevelDev& L) { return L.zsinvf; }
+
+// Persistent coarse-level kernel (sv_vanka.cu): the part of a V- or W-cycle
+// (Algorithm 1) on the levels n <= stokes_params.tail_n of an FP32 preconditioner
+// runs as one cooperative launch executing a list of steps separated by grid
+// barriers.  The list is built on the host by walking the same recursion as the
+// launch path, so both apply the same operations to the same buffers.
+enum TailKind : int {
+  TAIL_SWEEP = 0,     // c = sweep(level, x = a (null: zero guess), b)       (Algorithm 3)
+  TAIL_ZERO = 1,      // c = 0 on level
+  TAIL_RESID = 2,     // c = b - A a on level
+  TAIL_RESTRICT = 3,  // c (level - 1) = P^T a (level)
+  TAIL_PROLONG = 4,   // c (level) += P a (level - 1)
+  TAIL_COARSE = 5,    // c = A_0^-1 a on level 0 (bordered inverse, FP64 arithmetic)
+  TAIL_COPY = 6       // c = a on level
+};
+struct TailOp {
+  int kind, level;
+  const float* a;
+  const float* b;
+  float* c;
+};
+struct TailLevel {
+  LevelDev d;
+  const float* cd;    // FP32 class data of the level
+};
+constexpr int TAIL_NT = 128;   // threads per CTA (the 8 x 8 SIMT sweep tile)
 
 struct Level {
   LevelDev d;
@@ -198,6 +226,15 @@ struct stokes_hierarchy {
   double* host_scalars = nullptr;  // pinned host mirror of a few scalars
   int* dev_err = nullptr;          // set by kernels whose bounded waits expired
   int tc_wait_limit = sv::TC_WAIT_LIMIT;   // first bounded wait of the tensor-core sweep (test hook)
+  // persistent coarse-level kernel (mixed forms): levels 0..tail_top in one launch
+  int tail_top = -1;
+  sv::TailOp* tail_ops = nullptr;      // device: the steps of one cycle below and at tail_top
+  int tail_nops = 0;
+  sv::TailLevel* tail_levels = nullptr;   // device: levels 0..tail_top
+  unsigned* tail_bar = nullptr;        // device: grid-barrier count and generation
+  int tail_grid = 0;                   // CTAs of the cooperative launch
+  int tail_spin_limit = sv::TAIL_SPIN_LIMIT;
+  int tail_skip_arrival = -1;          // test hook: this CTA withholds its first barrier arrival
   // BF16 form: the SIMT ring of boundary tiles runs on ring_stream while the
   // tensor-core kernel sweeps the interior tiles on stream (fork / join events)
   cudaStream_t ring_stream = nullptr;
@@ -269,6 +306,13 @@ inline bool vanka_cfg_split(int cfg) { return cfg == VANKA_CFG_SPLIT || cfg == V
 template <typename R>
 void launch_vanka(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
                   double omega, int cfg, cudaStream_t s, int skip_lo = 1, int skip_hi = 0);
+
+// Persistent coarse-level kernel (sv_vanka.cu): one cooperative launch of `grid`
+// CTAs runs the nops steps; err is set to 1 if a grid barrier gave up.
+cudaError_t tail_prepare(int* max_ctas);
+void launch_tail(const TailOp* ops, int nops, const TailLevel* levels, const double* G, int N0,
+                 const FastDiagT<float>& fd, double omega, unsigned* bar, int* err, int spin_limit,
+                 int skip_arrival, int grid, cudaStream_t s);
 
 // Tensor-core sweep (sv_vanka_tc.cu, FP32 vectors, BF16 tcgen05 patch GEMM):
 // sweeps the 14 x 14 tiles [lo, hi]^2 whose patches are all of the interior

@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include "sv_internal.h"
+#include "sv_level_ops.cuh"
 #include "sv_stencil.cuh"
 #include "sv_vanka_common.cuh"
 
@@ -214,7 +215,7 @@ __device__ __forceinline__ void fd_solve_edge(const T* __restrict__ sx, const T*
 // address are formed once, and with compile-time extents every load is issued
 // before the stores.
 template <typename R, int ROWS, int WIDTH, int NW, typename OK>
-__device__ __forceinline__ void load_window(R* __restrict__ dst, const R* __restrict__ src, long long ld, int I0,
+__device__ __forceinline__ void load_window(R* __restrict__ dst, const R* src, long long ld, int I0,
                                             int J0, int warp, int lane, OK ok) {
   constexpr int RPW = (ROWS + NW - 1) / NW, CPL = (WIDTH + 31) / 32;
   R v[RPW][CPL];
@@ -238,36 +239,16 @@ __device__ __forceinline__ void load_window(R* __restrict__ dst, const R* __rest
   }
 }
 
+// One fused sweep of tile (bx, by) by the calling CTA (NT threads); smem_raw holds
+// (VT<TX, TY>::TOTAL + EDGE_TAB) elements.  Shared by the stand-alone kernel
+// below and the persistent coarse-level kernel, which loops over tiles.  x, b and
+// xo carry no __restrict__ (see sv_level_ops.cuh): in the persistent kernel they
+// are written by other steps of the same launch.
 template <typename R, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ cd,
-                                              const FastDiagT<R> fdg, const FastDiagT<float2> fdp,
-                                              const R* __restrict__ x,
-                                              const R* __restrict__ b, R* __restrict__ xo, R omega,
-                                              int skip_lo, int skip_hi) {
-  pdl_begin();
+__device__ __forceinline__ void vanka_tile(const LevelDev& L, const R* __restrict__ cd, const FastDiagT<R>& fdg,
+                                           const FastDiagT<float2>& fdp, const R* x, const R* b, R* xo, R omega,
+                                           int bx, int by, unsigned char* smem_raw) {
   using T = VT<TX, TY>;
-  // With a non-empty [skip_lo, skip_hi] the tensor-core kernel sweeps the tiles
-  // in that square and this launch enumerates the ring of tiles around it
-  // (1-D grid: rows below, the left/right parts of the middle rows, rows above).
-  int bx = blockIdx.x, by = blockIdx.y;
-  if (skip_hi >= skip_lo) {
-    const int gx = (L.np + TX - 1) / TX;
-    const int w = skip_hi - skip_lo + 1, mid_row = gx - w;
-    const int idx = blockIdx.x, n_bottom = skip_lo * gx, n_mid = w * mid_row;
-    if (idx < n_bottom) {
-      by = idx / gx;
-      bx = idx - by * gx;
-    } else if (idx < n_bottom + n_mid) {
-      const int k = idx - n_bottom, row = k / mid_row, c = k - row * mid_row;
-      by = skip_lo + row;
-      bx = c < skip_lo ? c : c + w;
-    } else {
-      const int k = idx - n_bottom - n_mid;
-      by = skip_hi + 1 + k / gx;
-      bx = k - (k / gx) * gx;
-    }
-  }
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sx = reinterpret_cast<R*>(smem_raw);
   R* sp = sx + T::SX;
   R* sr = sp + T::SP;
@@ -349,12 +330,18 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
   __syncthreads();
 
   // 3. exact patch solves, one thread per patch (Schur-factored class inverse)
-  for (int t = tid; t < T::NPATCH; t += NT) {
+  for (int t0 = 0; t0 < T::NPATCH; t0 += NT) {
+    const int t = t0 + tid;
     const int qj = t / T::QW, qi = t - qj * T::QW;
     const int pi = i0 - 1 + qi, pj = j0 - 1 + qj;
-    if (pi < 0 || pj < 0 || pi > n || pj > n) continue;
-    const int ax = axis_class(pi, n), ay = axis_class(pj, n);
+    const bool valid = t < T::NPATCH && pi >= 0 && pj >= 0 && pi <= n && pj <= n;
+    const int ax = valid ? axis_class(pi, n) : 2, ay = valid ? axis_class(pj, n) : 2;
     const int cls = 5 * ay + ax;
+    // the interior path for a warp whose patches are all interior: a vote of all 32
+    // lanes (lanes without a patch count as interior), so the choice depends on the
+    // tile alone, not on how the compiler converged the loop
+    const bool warp_interior = __all_sync(0xffffffffu, cls == INTERIOR_CLASS);
+    if (!valid) continue;
     const R* C = cd + cls * CD_STRIDE;
     R ru[50];
 #pragma unroll
@@ -364,7 +351,6 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
 #pragma unroll
         for (int wi = 0; wi < 5; ++wi)
           ru[c * 25 + wj * 5 + wi] = sr[c * T::RW * T::RH + (2 * qj + wj) * T::RW + 2 * qi + wi];
-    const bool warp_interior = !__any_sync(__activemask(), cls != INTERIOR_CLASS);
     const R dp = schur_dp<R>(warp_interior, L, C, ru, srp[t]);
     R* D = sd + t * 51;
     // K^-1 r_u by fast diagonalisation (exact up to rounding): warps whose
@@ -498,6 +484,38 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
   }
 }
 
+template <typename R, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ cd,
+                                              const FastDiagT<R> fdg, const FastDiagT<float2> fdp,
+                                              const R* __restrict__ x,
+                                              const R* __restrict__ b, R* __restrict__ xo, R omega,
+                                              int skip_lo, int skip_hi) {
+  pdl_begin();
+  // With a non-empty [skip_lo, skip_hi] the tensor-core kernel sweeps the tiles
+  // in that square and this launch enumerates the ring of tiles around it
+  // (1-D grid: rows below, the left/right parts of the middle rows, rows above).
+  int bx = blockIdx.x, by = blockIdx.y;
+  if (skip_hi >= skip_lo) {
+    const int gx = (L.np + TX - 1) / TX;
+    const int w = skip_hi - skip_lo + 1, mid_row = gx - w;
+    const int idx = blockIdx.x, n_bottom = skip_lo * gx, n_mid = w * mid_row;
+    if (idx < n_bottom) {
+      by = idx / gx;
+      bx = idx - by * gx;
+    } else if (idx < n_bottom + n_mid) {
+      const int k = idx - n_bottom, row = k / mid_row, c = k - row * mid_row;
+      by = skip_lo + row;
+      bx = c < skip_lo ? c : c + w;
+    } else {
+      const int k = idx - n_bottom - n_mid;
+      by = skip_hi + 1 + k / gx;
+      bx = k - (k / gx) * gx;
+    }
+  }
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  vanka_tile<R, TX, TY, NT>(L, cd, fdg, fdp, x, b, xo, omega, bx, by, smem_raw);
+}
+
 // ---------------------------------------------------------------------------
 // Split sweep: a CTA solves only the TX x TY patches of the vertices it owns
 // (no halo patches; the residual is needed on a one-vertex halo only) and
@@ -602,12 +620,15 @@ __global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __r
   }
   __syncthreads();
 
-  for (int t = tid; t < T::NPATCH; t += NT) {
+  for (int t0 = 0; t0 < T::NPATCH; t0 += NT) {
+    const int t = t0 + tid;
     const int qj = t / TX, qi = t - qj * TX;
     const int pi = i0 + qi, pj = j0 + qj;
-    if (pi > n || pj > n) continue;
-    const int ax = axis_class(pi, n), ay = axis_class(pj, n);
+    const bool valid = t < T::NPATCH && pi <= n && pj <= n;
+    const int ax = valid ? axis_class(pi, n) : 2, ay = valid ? axis_class(pj, n) : 2;
     const int cls = 5 * ay + ax;
+    const bool warp_interior = __all_sync(0xffffffffu, cls == INTERIOR_CLASS);   // as in vanka_tile
+    if (!valid) continue;
     const R* C = cd + cls * CD_STRIDE;
     R ru[50];
 #pragma unroll
@@ -617,7 +638,6 @@ __global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __r
 #pragma unroll
         for (int wi = 0; wi < 5; ++wi)
           ru[c * 25 + wj * 5 + wi] = sr[c * T::RW * T::RH + (2 * qj + wj) * T::RW + 2 * qi + wi];
-    const bool warp_interior = !__any_sync(__activemask(), cls != INTERIOR_CLASS);
     const R dp = schur_dp<R>(warp_interior, L, C, ru, srp[t]);
     const int p = pj * np + pi;
     R* D = delta + p;
@@ -678,6 +698,134 @@ void launch_t(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x
                                                                                     omega, skip_lo, skip_hi);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent coarse-level kernel.  The coarse levels of a V-cycle are small: a
+// level of n <= 128 has at most 289 sweep tiles, and launched kernel by kernel
+// every step costs its launch and drain latency rather than its work (about 65 us
+// per level in the FP32 forms).  Here one cooperative launch runs all steps of
+// the cycle below and at the tail's top level -- sweeps, residuals, transfers and
+// the coarse solve, each with the same device code as the stand-alone kernels --
+// separated by grid barriers.  Work items of a step (sweep tiles, vertices,
+// coarse elements, matrix rows) are spread over the CTAs.
+// ---------------------------------------------------------------------------
+struct TailArgs {
+  const TailOp* ops;
+  int nops;
+  const TailLevel* levels;
+  const double* G;
+  int N0;
+  FastDiagT<float> fdg;
+  FastDiagT<float2> fdp;
+  float omega;
+  unsigned* bar;     // [0] arrivals, [1] generation
+  int* err;
+  int spin_limit;
+  int skip_arrival;  // test hook: CTA that withholds its first arrival (-1: none)
+};
+
+// Grid-wide barrier of a cooperative launch: arrivals counted with an acquire-
+// release atomic, the last arrival resets the count and advances the generation
+// with a release, the others poll it with acquire loads (bounded: after
+// spin_limit polls the CTA sets *err and the kernel returns).  With the CTA
+// barriers around it this orders every CTA's writes of a step before any read of
+// the next step.
+__device__ bool grid_barrier(const TailArgs& A, bool withhold) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned* cnt = A.bar;
+    unsigned* gen = A.bar + 1;
+    unsigned g;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(gen) : "memory");
+    if (withhold) {
+      ok = 0;
+    } else {
+      unsigned old;
+      asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(cnt), "r"(1u) : "memory");
+      if (old == gridDim.x - 1) {
+        asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(cnt), "r"(0u) : "memory");
+        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(gen), "r"(1u) : "memory");
+        ok = 1;
+      } else {
+        int it = 0;
+        unsigned cur = g;
+        while (it < A.spin_limit) {
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(gen) : "memory");
+          if (cur != g) break;
+          __nanosleep(64);
+          ++it;
+        }
+        ok = (cur != g) ? 1 : 0;
+        if (!ok) atomicExch(A.err, 1);
+      }
+    }
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(TAIL_NT) k_tail(TailArgs A) {
+  pdl_begin();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const long long gtid = static_cast<long long>(cta) * TAIL_NT + tid, gstride = static_cast<long long>(G) * TAIL_NT;
+  for (int o = 0; o < A.nops; ++o) {
+    const TailOp op = A.ops[o];
+    const TailLevel T = A.levels[op.level];
+    const LevelDev& L = T.d;
+    switch (op.kind) {
+      case TAIL_SWEEP: {
+        const int gx = (L.np + 7) / 8, nt = gx * ((L.np + 7) / 8);
+        for (int t = cta; t < nt; t += G) {
+          const int by = t / gx, bx = t - by * gx;
+          vanka_tile<float, 8, 8, TAIL_NT>(L, T.cd, A.fdg, A.fdp, op.a, op.b, op.c, A.omega, bx, by, smem_raw);
+          __syncthreads();
+        }
+        break;
+      }
+      case TAIL_ZERO:
+        for (long long i = gtid; i < L.N; i += gstride) op.c[i] = 0.0f;
+        break;
+      case TAIL_COPY:
+        for (long long i = gtid; i < L.N; i += gstride) op.c[i] = op.a[i];
+        break;
+      case TAIL_RESID: {
+        const long long nvx = static_cast<long long>(L.np) * L.np;
+        for (long long i = gtid; i < nvx; i += gstride) {
+          const int bb = static_cast<int>(i / L.np), a = static_cast<int>(i - static_cast<long long>(bb) * L.np);
+          ops::apply_vertex<float>(L, op.a, op.b, op.c, 1, a, bb);
+        }
+        break;
+      }
+      case TAIL_RESTRICT:
+      case TAIL_PROLONG: {
+        const LevelDev C = A.levels[op.level - 1].d;
+        const long long ne = static_cast<long long>(C.n + 1) * (C.n + 1);
+        for (long long i = gtid; i < ne; i += gstride) {
+          const int ey = static_cast<int>(i / (C.n + 1)), ex = static_cast<int>(i - static_cast<long long>(ey) * (C.n + 1));
+          if (op.kind == TAIL_RESTRICT)
+            ops::restrict_elem<float>(L, C, op.a, op.c, ex, ey);
+          else
+            ops::prolong_elem<float>(L, C, op.a, op.c, ex, ey);
+        }
+        break;
+      }
+      case TAIL_COARSE: {
+        const long long w0 = gtid >> 5, ws = gstride >> 5;
+        const int lane = tid & 31;
+        for (long long row = w0; row < A.N0; row += ws) {
+          const double v = ops::coarse_row<float>(A.G, A.N0, op.a, static_cast<int>(row), lane);
+          if (lane == 0) op.c[row] = static_cast<float>(v);
+        }
+        break;
+      }
+      default:
+        break;
+    }
+    if (o + 1 < A.nops && !grid_barrier(A, o == 0 && cta == A.skip_arrival)) return;
+  }
+}
+
 template <typename R, int TX, int TY, int NT>
 cudaError_t prepare_t() {
   return cudaFuncSetAttribute(k_vanka<R, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -702,6 +850,53 @@ cudaError_t set_interior_unit_z(const double* z50) {
   cudaError_t e = cudaMemcpyToSymbol(c_zu, z50, 50 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_zu_f, zf, 50 * sizeof(float));
   return e;
+}
+
+constexpr size_t TAIL_SMEM = (VT<8, 8>::TOTAL + EDGE_TAB) * sizeof(float);
+
+cudaError_t tail_prepare(int* max_ctas) {
+  cudaError_t e = cudaFuncSetAttribute(k_tail, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(TAIL_SMEM));
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tail, TAIL_NT, TAIL_SMEM)) != cudaSuccess)
+    return e;
+  *max_ctas = per_sm * sms;
+  return cudaSuccess;
+}
+
+void launch_tail(const TailOp* ops, int nops, const TailLevel* levels, const double* G, int N0,
+                 const FastDiagT<float>& fd, double omega, unsigned* bar, int* err, int spin_limit,
+                 int skip_arrival, int grid, cudaStream_t s) {
+  count_launches(1);
+  TailArgs A;
+  A.ops = ops;
+  A.nops = nops;
+  A.levels = levels;
+  A.G = G;
+  A.N0 = N0;
+  A.fdg = fd;
+  for (int k = 0; k < 9; ++k) A.fdp.se[k] = make_float2(fd.se[k], fd.se[k]);
+  for (int k = 0; k < 4; ++k) A.fdp.so[k] = make_float2(fd.so[k], fd.so[k]);
+  for (int k = 0; k < 25; ++k) A.fdp.dinv[k] = make_float2(fd.dinv[k], fd.dinv[k]);
+  A.omega = static_cast<float>(omega);
+  A.bar = bar;
+  A.err = err;
+  A.spin_limit = spin_limit;
+  A.skip_arrival = skip_arrival;
+  // the grid barrier needs every CTA resident at once: a cooperative launch
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(TAIL_NT);
+  cfg.dynamicSmemBytes = TAIL_SMEM;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_tail, A);
 }
 
 cudaError_t vanka_prepare() {

@@ -54,7 +54,8 @@ class stokes_params(ctypes.Structure):
                 ("smoother", ctypes.c_int), ("bs_t", ctypes.c_double), ("bs_omega", ctypes.c_double),
                 ("bs_jacobi_weight", ctypes.c_double), ("bs_jacobi_iters", ctypes.c_int),
                 ("cycle", ctypes.c_int), ("precond", ctypes.c_int), ("bt_cycles", ctypes.c_int),
-                ("bt_nu", ctypes.c_int), ("bt_omega_u", ctypes.c_double), ("bt_omega_p", ctypes.c_double)]
+                ("bt_nu", ctypes.c_int), ("bt_omega_u", ctypes.c_double), ("bt_omega_p", ctypes.c_double),
+                ("tail_n", ctypes.c_int)]
 
 
 _lib = None
@@ -89,6 +90,8 @@ def _load():
         "stokes_device_status": (I, [P]),
         "stokes_test_set_wait_limit": (I, [P, I]),
         "stokes_test_set_alloc_limit": (None, [ctypes.c_longlong]),
+        "stokes_test_set_grid_barrier": (I, [P, I, I]),
+        "stokes_tail_info": (I, [P, IP, IP, IP]),
         "stokes_restrict": (I, [P, I, VP, VP]),
         "stokes_prolong_add": (I, [P, I, VP, VP]),
         "stokes_coarse_solve": (I, [P, VP, VP]),
@@ -123,7 +126,8 @@ def exported_symbols() -> list[str]:
             "stokes_level_info", "stokes_level_n", "stokes_level_tile", "stokes_assemble_rhs",
             "stokes_apply_operator",
             "stokes_residual", "stokes_vanka_sweep", "stokes_relaxation_sweep", "stokes_device_status",
-            "stokes_test_set_wait_limit", "stokes_test_set_alloc_limit", "stokes_restrict", "stokes_prolong_add",
+            "stokes_test_set_wait_limit", "stokes_test_set_alloc_limit", "stokes_test_set_grid_barrier",
+            "stokes_tail_info", "stokes_restrict", "stokes_prolong_add",
             "stokes_coarse_solve", "stokes_initial_guess", "stokes_vcycle_apply", "stokes_fgmres_solve",
             "stokes_solve_adjoint", "stokes_rhs_transpose", "stokes_batched_solve",
             "stokes_measure_fp64_peak", "stokes_stats_enable_timing", "stokes_stats_reset", "stokes_stats_read",
@@ -235,6 +239,16 @@ def stokes_test_set_wait_limit(h, polls: int) -> None:
 
 def stokes_test_set_alloc_limit(nbytes: int) -> None:
     _load().stokes_test_set_alloc_limit(int(nbytes))
+
+
+def stokes_test_set_grid_barrier(h, polls: int, withhold_cta: int = -1) -> None:
+    _check(_load().stokes_test_set_grid_barrier(h, int(polls), int(withhold_cta)))
+
+
+def stokes_tail_info(h) -> tuple[int, int, int]:
+    t, s, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_load().stokes_tail_info(h, ctypes.byref(t), ctypes.byref(s), ctypes.byref(c)))
+    return t.value, s.value, c.value
 
 
 def stokes_restrict(h, level: int, r_fine, r_coarse) -> None:
@@ -456,6 +470,7 @@ class Hierarchy:
     bt_nu: int = 3
     bt_omega_u: float = 1.0
     bt_omega_p: float = 0.6
+    tail_n: int = 0
 
     def __post_init__(self):
         p = default_params()
@@ -468,6 +483,7 @@ class Hierarchy:
         p.cycle = self.cycle
         p.precond, p.bt_cycles, p.bt_nu = self.precond, self.bt_cycles, self.bt_nu
         p.bt_omega_u, p.bt_omega_p = self.bt_omega_u, self.bt_omega_p
+        p.tail_n = self.tail_n
         self.handle = stokes_hierarchy_create(self.n, self.viscosity, p)
         self.levels, _ = stokes_level_info(self.handle)
         self.N = vec_len(self.n)

@@ -22,13 +22,15 @@ def pkg():
     return p
 
 
-@pytest.mark.parametrize("prec,smoother", [(0, 0), (1, 0), (2, 0), (1, 2), (0, 1)])
+@pytest.mark.parametrize("prec,smoother,tail_n", [(0, 0, 0), (1, 0, 0), (2, 0, 0), (1, 2, 0), (0, 1, 0),
+                                                  (1, 0, 128), (2, 0, 128)])
 @pytest.mark.parametrize("n", [16, 64])
-def test_graph_replay_equals_eager_vcycle(pkg, n, prec, smoother):
+def test_graph_replay_equals_eager_vcycle(pkg, n, prec, smoother, tail_n):
+    """tail_n = 128: the coarse levels as the persistent cooperative launch, captured too."""
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
-        H = pkg.Hierarchy(n, prec=prec, smoother=smoother)
+        H = pkg.Hierarchy(n, prec=prec, smoother=smoother, tail_n=tail_n)
         b = torch.from_numpy(si.random_vector(n, 31)).cuda()
         z_eager = torch.empty_like(b)
         z_graph = torch.full_like(b, float("nan"))

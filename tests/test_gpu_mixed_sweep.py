@@ -111,9 +111,10 @@ def test_bf16_form_launches_the_tensor_core_kernel(pkg):
     """The library's counters: one relaxation sweep on the 128^2 level with tile 3 is the
     tensor-core kernel plus its SIMT ring (2 launches) and three FP64/FP32 conversions; a
     V(2,2) cycle launches the tensor-core kernel 4 times on each level with at least two
-    interior tiles per axis (128 and 64: 8 launches)."""
+    interior tiles per axis (128 and 64: 8 launches); with the persistent coarse-level
+    launch for n <= 64 (tail_n = 64, the SIMT tile there) only on 128: 4."""
     from paper_2401_06277_gb300 import stokes
-    H = pkg.Hierarchy(128, prec=stokes.STOKES_MIXED_BF16, tile=3)
+    H = pkg.Hierarchy(128, prec=stokes.STOKES_MIXED_BF16, tile=3, tail_n=64)
     lv, x, b = inputs(128, 5, False)
     xd, bd = dev(x), dev(b)
     out = torch.empty_like(bd)
@@ -123,6 +124,13 @@ def test_bf16_form_launches_the_tensor_core_kernel(pkg):
     s1 = stokes.stokes_stats_read(H.handle)
     assert s1["tc_launches"] - s0["tc_launches"] == 1
     assert s1["kernel_launches"] - s0["kernel_launches"] == 5
+    stokes.stokes_vcycle_apply(H.handle, bd, out)
+    s2 = stokes.stokes_stats_read(H.handle)
+    assert s2["tc_launches"] - s1["tc_launches"] == 4
+    H.close()
+    H = pkg.Hierarchy(128, prec=stokes.STOKES_MIXED_BF16, tile=3, tail_n=0)
+    torch.cuda.synchronize()
+    s1 = stokes.stokes_stats_read(H.handle)
     stokes.stokes_vcycle_apply(H.handle, bd, out)
     s2 = stokes.stokes_stats_read(H.handle)
     assert s2["tc_launches"] - s1["tc_launches"] == 8
