@@ -358,9 +358,9 @@ stokes_status stokes_tail_info(const stokes_hierarchy* h, int* top_level, int* s
  * the norm when the stream reaches this work; stream is a cudaStream_t.
  * Scratch: a fixed array of 3 * STOKES_NOALLOC_MAX_N + 2 doubles (196.6 KB)
  * that every GPU using this library keeps until the process exits.  The
- * first call on a device looks up that array's device address
- * (cudaGetSymbolAddress), so make one call per device before any stream
- * capture.  Calls share the array: two calls whose kernels overlap on the
+ * first call on a device (and the first after a cudaDeviceReset, which makes a
+ * new context) looks up that array's device address (cudaGetSymbolAddress),
+ * so make one call per device before any stream capture.  Calls share the array: two calls whose kernels overlap on the
  * GPU (different streams or host threads) race.  Each call overwrites every
  * slot it later reads, so nothing is carried over from the previous call.
  * Returns STOKES_ERR_ARG for n out of range or null pointers. */

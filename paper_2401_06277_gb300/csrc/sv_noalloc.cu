@@ -30,7 +30,12 @@ constexpr int NOALLOC_SLOTS = (2 * STOKES_NOALLOC_MAX_N + 1) + (STOKES_NOALLOC_M
 __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SLOTS];
 
 constexpr int MAX_DEVICES = 64;
-std::atomic<double*> g_scratch_addr[MAX_DEVICES];
+// per device: the scratch address and the ID of the context it was looked up in
+struct ScratchEntry {
+  unsigned long long ctx_id;
+  double* addr;
+};
+ScratchEntry g_scratch[MAX_DEVICES];
 std::mutex g_scratch_mutex;
 
 __device__ __forceinline__ bool na_free(int I, int J, int nq) {
@@ -135,26 +140,53 @@ __global__ void k_resnorm_final(const double* __restrict__ scratch, int rows, do
   if (threadIdx.x == 0) *norm = sqrt(t);
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device (cudaGetSymbolAddress; host code cannot use the symbol itself).
+// ID of the current context (cuCtxGetId, through the runtime's driver entry
+// points: unique for the life of the process, so a context created after a
+// cudaDeviceReset never matches an entry of the one it replaced); 0 if unknown.
+unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  if (!get_current || !get_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || ctx == nullptr || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch array in the current context of the current
+// device (cudaGetSymbolAddress; host code cannot use the symbol itself), looked
+// up once per device and context: a device reset (new context) looks it up again.
 cudaError_t scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-  double* p = g_scratch_addr[dev].load(std::memory_order_acquire);
-  if (p == nullptr) {
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    p = g_scratch_addr[dev].load(std::memory_order_relaxed);
-    if (p == nullptr) {
-      void* a = nullptr;
-      e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
-      if (e != cudaSuccess) return e;
-      p = static_cast<double*>(a);
-      g_scratch_addr[dev].store(p, std::memory_order_release);
-    }
+  // 0 before the device's context exists (the lookup below creates it): looked up again
+  const unsigned long long id = current_context_id();
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  ScratchEntry& ent = g_scratch[dev];
+  if (ent.addr == nullptr || id == 0 || ent.ctx_id != id) {
+    void* a = nullptr;
+    e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    ent.addr = static_cast<double*>(a);
+    ent.ctx_id = id;
   }
-  *out = p;
+  *out = ent.addr;
   return cudaSuccess;
 }
 

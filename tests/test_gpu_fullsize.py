@@ -154,7 +154,8 @@ def test_fullsize_manufactured_solve(big):
     b = big.assemble_rhs(f, ud)
     x, it, rr = big.solve(b)
     assert rr <= 1e-8 and it <= 12
-    # the true residual through an independent path: the allocation-free residual norm
+    # the true residual through a second kernel (the allocation-free residual norm; it
+    # shares the operator kernel's stencil coefficient tables, not its tiling or code)
     from paper_2401_06277_gb300 import stokes
     x0 = torch.empty_like(b)
     stokes.stokes_initial_guess(big.handle, b, x0)

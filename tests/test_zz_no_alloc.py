@@ -75,3 +75,54 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(stokes):
     assert st == stokes.STOKES_ERR_ARG
     assert b"8192" in lib.stokes_last_error()
     assert lib.stokes_residual_norm_noalloc(0, 1.0, p, p, p, None) == stokes.STOKES_ERR_ARG
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_noalloc_residual_norm_on_the_smallest_grids(stokes, n):
+    """n = 1..3, below any hierarchy (n >= 4): nearly every row is near the boundary, where
+    the Dirichlet masks decide the stencil.  The norm equals ||b - A x|| with the oracle's
+    assembled, Dirichlet-eliminated operator (Section 2.2)."""
+    from oracle import stokes_oracle as O
+    A = O.stokes_operator(O.Mesh(n), 1.3)[0]
+    b, x = si.random_vector(n, 40 + n), si.random_vector(n, 50 + n)
+    ref = float(np.linalg.norm(b - A @ x))
+    lib = stokes._load()
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    bd, xd = torch.from_numpy(b).cuda(), torch.from_numpy(x).cuda()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = lib.stokes_residual_norm_noalloc(n, 1.3, ctypes.c_void_p(bd.data_ptr()), ctypes.c_void_p(xd.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr()), stream)
+    assert st == stokes.STOKES_OK, lib.stokes_last_error()
+    got = float(out.item())
+    assert abs(got - ref) <= RTOL * ref, (got, ref)
+
+
+def test_noalloc_residual_norm_inside_a_captured_graph(stokes):
+    """The call a capturing caller makes: after one call outside capture (which looks up
+    the scratch address), a second call recorded into a CUDA graph and replayed gives the
+    norm of stokes_residual's residual for the inputs the graph reads at replay."""
+    n = 16
+    h = stokes.Hierarchy(n, viscosity=1.3)
+    b = torch.from_numpy(si.random_vector(n, 60)).cuda()
+    x = torch.from_numpy(si.random_vector(n, 61)).cuda()
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stokes.stokes_residual_norm_noalloc(n, 1.3, b, x, out)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            stokes.stokes_residual_norm_noalloc(n, 1.3, b, x, out, stream=s)
+    for seed in (62, 63):   # new inputs in place, then replay
+        b.copy_(torch.from_numpy(si.random_vector(n, seed)))
+        out.zero_()
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        r = torch.empty_like(b)
+        stokes.stokes_residual(h.handle, h.levels - 1, b, x, r)
+        ref = float(torch.linalg.vector_norm(r))
+        assert abs(float(out.item()) - ref) <= RTOL * ref
+    del g
+    h.close()
