@@ -199,16 +199,20 @@ void sweep_f64(stokes_hierarchy* h, sv::Level& L, const double* x, const double*
     sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, L.vk_cfg, h->stream);
 }
 
-// BF16-form sweep of a level with tensor-core tiles: the interior tiles on the
-// tensor cores (stream s), the ring of boundary tiles on the SIMT kernel
-// (ring_stream), concurrently -- both read x and b and write disjoint owned
-// dofs of xo.  Fork and join are event waits, valid eagerly and under capture.
+// Mixed-form sweep of a level with strip tiles: the interior tiles on the strip
+// kernel (stream s) -- the tensor-core GEMM in the BF16 form, the FP32 fast-
+// diagonalisation solve in the FP32 form -- and the ring of boundary tiles on the
+// SIMT kernel (ring_stream), concurrently: both read x and b and write disjoint
+// owned dofs of xo.  Fork and join are event waits, valid eagerly and under capture.
 void tc_sweep(stokes_hierarchy* h, sv::Level& L, const float* x, const float* b, float* xo, cudaStream_t s) {
   cudaEventRecord(h->ring_fork, s);
   cudaStreamWaitEvent(h->ring_stream, h->ring_fork, 0);
   sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, sv::VANKA_CFG_14, h->ring_stream, L.tc_lo,
                           L.tc_hi);
-  sv::launch_vanka_tc(L.d, L.tcB, x, b, xo, h->prm.omega, L.tc_lo, L.tc_hi, h->dev_err, s, h->tc_wait_limit);
+  if (h->prm.prec == STOKES_MIXED_BF16)
+    sv::launch_vanka_tc(L.d, L.tcB, x, b, xo, h->prm.omega, L.tc_lo, L.tc_hi, h->dev_err, s, h->tc_wait_limit);
+  else
+    sv::launch_vanka_strip_f32(L.d, h->fdf, x, b, xo, h->prm.omega, L.tc_lo, L.tc_hi, s);
   cudaEventRecord(h->ring_join, h->ring_stream);
   cudaStreamWaitEvent(s, h->ring_join, 0);
 }
@@ -229,7 +233,7 @@ void timed_sweep<float>(stokes_hierarchy* h, bool finest, sv::Level& L, const fl
   if (ev) cudaEventRecord(ev[0], h->stream);
   if (h->prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN || h->prm.smoother == STOKES_SMOOTHER_SCHUR_UZAWA) {
     sv::launch_bs_sweep<float>(L.d, h->bs, static_cast<float*>(h->bs_buf), L.rf, x, b, xo, h->stream);
-  } else if (L.tcB != nullptr && L.tc_hi >= L.tc_lo && L.tc_on) {
+  } else if (L.strip && L.tc_on) {
     tc_sweep(h, L, x, b, xo, h->stream);
   } else if (sv::vanka_cfg_split(L.vk_cfg_f)) {
     sv::launch_vanka_split<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, h->deltaf,
@@ -708,14 +712,14 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
     return e;
   }
   float best = 1e30f;
-  // candidates: the fused tile shapes; in FP64 also the split sweep; in the BF16
-  // form (tensor-core image present) also the tensor-core sweep with its ring
-  const bool tc = (sizeof(R) == 4) && L.tcB != nullptr && L.tc_hi >= L.tc_lo;
-  constexpr int CAND_TC = sv::VANKA_CFG_4 + 1;   // the tensor-core sweep (BF16 form), tuning index only
+  // candidates: the fused tile shapes; in FP64 also the split sweep; in the mixed
+  // forms, on levels with interior strips, also the strip sweep with its ring
+  const bool tc = (sizeof(R) == 4) && L.strip;
+  constexpr int CAND_TC = sv::VANKA_CFG_4 + 1;   // the strip sweep (mixed forms), tuning index only
   const int ncand = tc ? CAND_TC + 1 : sv::VANKA_CFG_4 + 1;
   int best_c = 0;
   for (int c = 0; c < ncand; ++c) {
-    if (tc && c == sv::VANKA_CFG_14) continue;   // where the tensor-core tile fits, 14x14 means tensor cores
+    if (tc && c == sv::VANKA_CFG_14) continue;   // where the strip tiles fit, 14x14 means the strip sweep
     auto run = [&]() {
       if constexpr (sizeof(R) == 8) {
         if (sv::vanka_cfg_split(c))
@@ -746,7 +750,7 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
       best_c = c;
     }
   }
-  if (tc) {   // tensor cores, or the fastest SIMT configuration
+  if (tc) {   // the strip sweep, or the fastest SIMT configuration
     L.tc_on = (best_c == CAND_TC);
     *cfg = L.tc_on ? sv::VANKA_CFG_14 : best_c;
   } else {
@@ -773,7 +777,7 @@ cudaError_t choose_tiles(stokes_hierarchy* h) {
     // mixed hierarchy serves stokes_vanka_sweep alone and keeps 16x8)
     cudaError_t e = cudaSuccess;
     if (h->prm.prec == STOKES_FP64) e = tune_level<double>(h, L, &L.vk_cfg);
-    else e = tune_level<float>(h, L, &L.vk_cfg_f);   // BF16: tensor cores vs SIMT shapes
+    else e = tune_level<float>(h, L, &L.vk_cfg_f);   // strip sweep vs SIMT shapes
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -877,11 +881,15 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   if (e == cudaSuccess) {
     static std::once_flag z_once;
     static cudaError_t z_err = cudaSuccess;
-    std::call_once(z_once, [] { z_err = sv::set_interior_unit_z(unit_schur().z); });
+    std::call_once(z_once, [] {
+      z_err = sv::set_interior_unit_z(unit_schur().z);
+      if (z_err == cudaSuccess) z_err = sv::set_strip_unit_z(unit_schur().z);
+    });
     e = z_err;
   }
-  if (e == cudaSuccess && prm.prec == STOKES_MIXED_BF16) e = sv::vanka_tc_prepare();
-  if (e == cudaSuccess && prm.prec == STOKES_MIXED_BF16) {
+  const bool mixed = prm.prec == STOKES_MIXED_BF16 || prm.prec == STOKES_MIXED_FP32;
+  if (e == cudaSuccess && mixed) e = sv::vanka_tc_prepare();
+  if (e == cudaSuccess && mixed) {
     e = cudaStreamCreateWithFlags(&h->ring_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ring_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ring_join, cudaEventDisableTiming);
@@ -910,9 +918,10 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
     }
     sv::build_class_data(nl, viscosity, L.cd_host, &L.full_inv_host);
     e = cudaMemcpy(L.cd, L.cd_host.data(), L.cd_host.size() * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && prm.prec == STOKES_MIXED_BF16) {
+    if (e == cudaSuccess && mixed) {
       sv::tc_interior_range(nl, &L.tc_lo, &L.tc_hi);
-      if (L.tc_hi >= L.tc_lo) {
+      L.strip = L.tc_hi >= L.tc_lo;
+      if (L.strip && prm.prec == STOKES_MIXED_BF16) {
         std::vector<unsigned short> img(64 * 64);
         sv::tc_pack_inverse(L.full_inv_host.data() + static_cast<size_t>(sv::INTERIOR_CLASS) * 51 * 51, img.data());
         if ((e = dalloc_bytes(&L.tcB, img.size() * sizeof(unsigned short))) == cudaSuccess)

@@ -1,0 +1,84 @@
+// sv_fastdiag.cuh -- the interior patch solve of the Vanka sweeps by fast
+// diagonalisation (Section 6.3: every interior patch has the same matrix, and its
+// velocity block is a Kronecker sum, K = (nu/90)(k (x) m + m (x) k), so
+// K^-1 = S (x) S diag(1/(l_a + l_b)) (S (x) S)^T with the generalised eigenvectors
+// of (k, m)), shared by the SIMT sweep (sv_vanka.cu) and the FP32 strip sweep
+// (sv_vanka_tc.cu).
+#pragma once
+
+#include "sv_internal.h"
+
+namespace sv {
+namespace fdm {
+
+// Packed FP32 arithmetic on (u_x, u_y) pairs (sm_100 and later): both velocity
+// components of a patch go through the same fast-diagonalisation transforms,
+// so the FP32 sweep runs them as one pass of FFMA2 / FADD2 / FMUL2, each lane
+// rounded exactly as the scalar operation (a - b as b * -1 + a).
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
+using ::fma;   // keep the scalar overloads visible beside the pair one
+__device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Forward transform of one 5-vector into the generalised eigenbasis S^T v
+// (three symmetric, two antisymmetric eigenvectors, each scaled to 1 on the
+// pair {0, 4}, so the first term needs no multiply: 4 add/sub + 8 FMA).
+template <typename T>
+__device__ __forceinline__ void fd_fwd(const FastDiagT<T>& f, T v0, T v1, T v2, T v3, T v4, T* c) {
+  const T e0 = v0 + v4, e1 = v1 + v3, o0 = v0 - v4, o1 = v1 - v3;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) c[k] = fma(f.se[3 + k], e1, fma(f.se[6 + k], v2, e0));
+#pragma unroll
+  for (int k = 0; k < 2; ++k) c[3 + k] = fma(f.so[2 + k], o1, o0);
+}
+
+// Inverse transform S c of five eigen-coefficients (rows of the pair {0, 4}
+// are all ones: 7 add/sub + 8 FMA/MUL).
+template <typename T>
+__device__ __forceinline__ void fd_inv(const FastDiagT<T>& f, const T* c, T* v) {
+  T E[3], Od[2];
+  E[0] = (c[0] + c[1]) + c[2];
+#pragma unroll
+  for (int m = 1; m < 3; ++m) E[m] = fma(f.se[m * 3], c[0], fma(f.se[m * 3 + 1], c[1], f.se[m * 3 + 2] * c[2]));
+  Od[0] = c[3] + c[4];
+  Od[1] = fma(f.so[2], c[3], f.so[3] * c[4]);
+  v[0] = E[0] + Od[0];
+  v[4] = E[0] - Od[0];
+  v[1] = E[1] + Od[1];
+  v[3] = E[1] - Od[1];
+  v[2] = E[2];
+}
+
+// y = K^-1 r on an interior patch window (5 x 5, row-major [wj][wi]) by fast
+// diagonalisation: transform both axes, divide by l_a + l_b, transform back.
+template <typename T>
+__device__ __forceinline__ void fd_solve(const FastDiagT<T>& f, const T* r, T* y) {
+  T Tm[25], U[25];
+#pragma unroll
+  for (int wj = 0; wj < 5; ++wj)
+    fd_fwd(f, r[wj * 5], r[wj * 5 + 1], r[wj * 5 + 2], r[wj * 5 + 3], r[wj * 5 + 4], Tm + wj * 5);
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    T c[5];
+    fd_fwd(f, Tm[k], Tm[5 + k], Tm[10 + k], Tm[15 + k], Tm[20 + k], c);
+#pragma unroll
+    for (int k2 = 0; k2 < 5; ++k2) U[k2 * 5 + k] = c[k2] * f.dinv[k2 * 5 + k];
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    T c[5], v[5];
+#pragma unroll
+    for (int k2 = 0; k2 < 5; ++k2) c[k2] = U[k2 * 5 + k];
+    fd_inv(f, c, v);
+#pragma unroll
+    for (int wj = 0; wj < 5; ++wj) Tm[wj * 5 + k] = v[wj];
+  }
+#pragma unroll
+  for (int wj = 0; wj < 5; ++wj) fd_inv(f, Tm + wj * 5, y + wj * 5);
+}
+
+}  // namespace fdm
+}  // namespace sv

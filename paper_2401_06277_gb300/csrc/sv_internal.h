@@ -186,8 +186,9 @@ struct Level {
   int vk_cfg_f = 0;       // tile shape of the FP32 sweep on this level
   // tensor-core sweep (prec == STOKES_MIXED_BF16): interior tile range, BF16 inverse image
   int tc_lo = 1, tc_hi = 0;
+  bool strip = false;     // the interior tiles [tc_lo, tc_hi]^2 have a strip sweep (both mixed forms)
   bool tc_on = true;      // the autotuner may prefer the SIMT sweep on small levels
-  void* tcB = nullptr;
+  void* tcB = nullptr;    // BF16 form: the interior inverse for the tensor cores
   // simple Vanka (smoother == STOKES_SMOOTHER_PER_PATCH): per-patch inverses, entry-major
   double* pinv = nullptr;
   std::vector<double> cd_host;
@@ -327,6 +328,13 @@ void tc_interior_range(int n, int* lo, int* hi);
 void launch_vanka_tc(const LevelDev& L, const void* Bcanon, const float* x, const float* b, float* xo,
                      double omega, int lo, int hi, int* err, cudaStream_t s, int first_wait_limit = TC_WAIT_LIMIT);
 cudaError_t vanka_tc_prepare();
+// The FP32 strip sweep of the same interior tiles (mixed FP32 form): the strip walk
+// of launch_vanka_tc with every patch solved exactly in FP32 by fast
+// diagonalisation (fd: the interior factors) instead of the BF16 GEMM.
+void launch_vanka_strip_f32(const LevelDev& L, const FastDiagT<float>& fd, const float* x, const float* b,
+                            float* xo, double omega, int lo, int hi, cudaStream_t s);
+// uploads z_u (50 doubles, as for set_interior_unit_z) for the FP32 strip sweep
+cudaError_t set_strip_unit_z(const double* z50);
 // 64 x 64 BF16 core-matrix image (uint16 bits) of a 51 x 51 row-major inverse
 void tc_pack_inverse(const double* inv51, unsigned short* out4096);
 const char* vanka_cfg_name(int cfg);

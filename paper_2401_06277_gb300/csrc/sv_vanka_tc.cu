@@ -50,6 +50,7 @@
 #include <cstdint>
 #include <cstring>
 
+#include "sv_fastdiag.cuh"
 #include "sv_internal.h"
 #include "sv_stencil.cuh"
 #include "sv_vanka_common.cuh"
@@ -79,20 +80,25 @@ constexpr int PRR = 6, PPW = 36;                            // p: 6 vertex rows 
 constexpr int SRR = 6;                                      // partial sums: 6 patch rows
 static_assert(XN / 2 <= XHO && (2 * XHO) % 32 == 16, "x ring layout");
 
-constexpr int OFF_A = 0;                                    // 128 x 64 BF16 = 16 KB
-constexpr int OFF_B = OFF_A + 128 * 64 * 2;                 // 64 x 64 BF16 = 8 KB
-constexpr int OFF_X = OFF_B + 64 * 64 * 2;
-constexpr int OFF_R = OFF_X + XR * XPP * 8;
-constexpr int OFF_RPR = OFF_R + RR * RPP * 8;
-constexpr int OFF_P = OFF_RPR + CRR * NCC * 4;
-constexpr int OFF_PS = OFF_P + PRR * PPW * 4;               // [row][wj][lane] float4
-constexpr int OFF_PSP = OFF_PS + SRR * 5 * 32 * 16;         // [row][lane] pressure corrections
-constexpr int OFF_BAR = OFF_PSP + SRR * 32 * 4;             // bulk-copy and MMA mbarriers
-constexpr int OFF_TMEM = OFF_BAR + 16;
-constexpr int OFF_FLAG = OFF_TMEM + 4;
-constexpr int SMEM_BYTES = OFF_FLAG + 12;
-static_assert(OFF_X % 16 == 0 && OFF_PS % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
-static_assert(4 * (SMEM_BYTES + 1024) <= 228 * 1024, "four CTAs per SM");
+// Shared-memory layout (bytes).  The FP32 strip sweep (TC = false) has no GEMM
+// operands, so its rings start at 0.
+template <bool TC>
+struct SL {
+  static constexpr int A = 0;                               // 128 x 64 BF16 = 16 KB (TC)
+  static constexpr int B = A + 128 * 64 * 2;                // 64 x 64 BF16 = 8 KB (TC)
+  static constexpr int X = TC ? B + 64 * 64 * 2 : 0;
+  static constexpr int R = X + XR * XPP * 8;
+  static constexpr int RPR = R + RR * RPP * 8;
+  static constexpr int P = RPR + CRR * NCC * 4;
+  static constexpr int PS = P + PRR * PPW * 4;               // [row][wj][lane] float4
+  static constexpr int PSP = PS + SRR * 5 * 32 * 16;         // [row][lane] pressure corrections
+  static constexpr int BAR = PSP + SRR * 32 * 4;             // bulk-copy and MMA mbarriers
+  static constexpr int TMEM = BAR + 16;
+  static constexpr int FLAG = TMEM + 4;
+  static constexpr int BYTES = FLAG + 12;
+  static_assert(X % 16 == 0 && PS % 16 == 0 && BAR % 8 == 0, "alignment");
+  static_assert(4 * (BYTES + 1024) <= 228 * 1024, "four CTAs per SM");
+};
 
 constexpr uint32_t TMEM_COLS = 128;   // two 64-column accumulators (4 CTAs per SM: all 512 columns)
 constexpr int WAIT_LIMIT = TC_WAIT_LIMIT;
@@ -172,22 +178,32 @@ __device__ __forceinline__ bool free_node(int I, int J, int nq) {
   return I > 0 && J > 0 && I < nq - 1 && J < nq - 1;
 }
 
-__global__ void __launch_bounds__(NT, 4) k_vanka_tc(LevelDev L, const uint4* __restrict__ Bg,
-                                                    const float* __restrict__ x,
-                                                    const float* __restrict__ b, float* __restrict__ xo,
-                                                    float omega, int lo, int hi, int seg_tiles,
-                                                    int* __restrict__ err, int first_wait_limit) {
+// z_u of the interior patches (the Schur vector K^-1 b^T at unit viscosity and
+// spacing, u_x window then u_y window) for the FP32 strip sweep; a level scales it
+// by zs.  Compile-time slot indices make it a constant-bank operand.
+__constant__ float c_zu_strip[50];
+
+// TC: the BF16 tensor-core sweep; !TC: the FP32 strip sweep, each thread solving
+// its interior patch by fast diagonalisation (fdp: the (v, v) pairs of the FP32
+// factors; z_u from constant memory) in the same strip walk.
+template <bool TC>
+__global__ void __launch_bounds__(NT, 4) k_vanka_strip(LevelDev L, const uint4* __restrict__ Bg,
+                                                       const FastDiagT<float2> fdp, const float* __restrict__ x,
+                                                       const float* __restrict__ b, float* __restrict__ xo,
+                                                       float omega, int lo, int hi, int seg_tiles,
+                                                       int* __restrict__ err, int first_wait_limit) {
   pdl_begin();
+  using Y = SL<TC>;
   extern __shared__ __align__(1024) unsigned char sm[];
-  float2* sx = reinterpret_cast<float2*>(sm + OFF_X);
-  float2* sr = reinterpret_cast<float2*>(sm + OFF_R);
-  float* srp = reinterpret_cast<float*>(sm + OFF_RPR);
-  float* sp = reinterpret_cast<float*>(sm + OFF_P);
-  float4* sps = reinterpret_cast<float4*>(sm + OFF_PS);
-  float* spp = reinterpret_cast<float*>(sm + OFF_PSP);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + OFF_TMEM);
-  volatile int* s_fail = reinterpret_cast<volatile int*>(sm + OFF_FLAG);
+  float2* sx = reinterpret_cast<float2*>(sm + Y::X);
+  float2* sr = reinterpret_cast<float2*>(sm + Y::R);
+  float* srp = reinterpret_cast<float*>(sm + Y::RPR);
+  float* sp = reinterpret_cast<float*>(sm + Y::P);
+  float4* sps = reinterpret_cast<float4*>(sm + Y::PS);
+  float* spp = reinterpret_cast<float*>(sm + Y::PSP);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + Y::BAR);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + Y::TMEM);
+  volatile int* s_fail = reinterpret_cast<volatile int*>(sm + Y::FLAG);
   const uint32_t bar_b = su32(bars), bar_mma = su32(bars + 1);
   const int nq = L.nq, np = L.np;
   const long long nv = L.nv;
@@ -203,21 +219,24 @@ __global__ void __launch_bounds__(NT, 4) k_vanka_tc(LevelDev L, const uint4* __r
 
   // ---- set-up: barriers, tensor memory, bulk copy of the BF16 inverse, zero pad rows ----
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_b), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_mma), "r"(1));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if constexpr (TC) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_b), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_mma), "r"(1));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     *s_fail = 0;
   }
   __syncwarp();
-  if (r == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
-                 "r"(TMEM_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  // A: lanes 30, 31 of every 32-row group are padding patches (zero rows); the K
-  // chunk 7 (slots 56..63) of every row is zero
-  {
-    unsigned char* arow = sm + OFF_A + (tid >> 3) * 1024 + (tid & 7) * 16;
+  uint32_t tmem = 0;
+  if constexpr (TC) {
+    if (r == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                   "r"(TMEM_COLS));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // A: lanes 30, 31 of every 32-row group are padding patches (zero rows); the K
+    // chunk 7 (slots 56..63) of every row is zero
+    unsigned char* arow = sm + Y::A + (tid >> 3) * 1024 + (tid & 7) * 16;
     const uint4 z = make_uint4(0u, 0u, 0u, 0u);
     if (l >= NPC) {
 #pragma unroll
@@ -229,15 +248,17 @@ __global__ void __launch_bounds__(NT, 4) k_vanka_tc(LevelDev L, const uint4* __r
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tslot;
-  if (tid == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_b), "r"(64 * 64 * 2)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            su32(sm + OFF_B)),
-        "l"(Bg), "r"(64 * 64 * 2), "r"(bar_b)
-        : "memory");
+  if constexpr (TC) {
+    tmem = *tslot;
+    if (tid == 0) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_b), "r"(64 * 64 * 2)
+                   : "memory");
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              su32(sm + Y::B)),
+          "l"(Bg), "r"(64 * 64 * 2), "r"(bar_b)
+          : "memory");
+    }
   }
 
   // ---- loaders (warp r takes rows r, r + 4, ...) ----
@@ -321,12 +342,15 @@ __global__ void __launch_bounds__(NT, 4) k_vanka_tc(LevelDev L, const uint4* __r
   for (int k = 0; k < 9; ++k) xold[k] = 0.0f;
   uint32_t mma_phase = 0;
 
-  for (int t = 0; t <= T + 2; ++t) {
+  // the update trails the residual by 3 steps with the GEMM (its corrections are read
+  // a step after their MMA), by 2 with the FP32 solve
+  constexpr int LAG = TC ? 12 : 8;
+  for (int t = 0; t <= T + (TC ? 2 : 1); ++t) {
     // ================= phase A: residual of cell rows t, update, prefetch =================
     const bool pf = (t + 1 <= T);
     // the update of this step (vertex row vb) and, loaded a step ahead, the next
     // step's x_old (9 values per vertex; in L2: its rows were loaded into the window)
-    const int vb = j0 + 4 * t - 12 + r;
+    const int vb = j0 + 4 * t - LAG + r;
     const bool upd = vb >= j0 && vb < j0 + S && l >= 1 && l <= SW;
     const int vi = i0 + l - 1;
     const long long ke = static_cast<long long>(2 * vb) * nq + 2 * vi;   // node (2 vi, 2 vb)
@@ -480,77 +504,29 @@ __global__ void __launch_bounds__(NT, 4) k_vanka_tc(LevelDev L, const uint4* __r
     // the MMA of step t - 1 must be complete before its operand is overwritten and
     // its accumulator read (issued a whole phase A earlier); the inverse's bulk copy
     // before the first MMA
-    if (tid == 0) {
-      bool ok = true;
-      if (t == 0) ok = mbar_wait(bar_b, 0, first_wait_limit);
-      if (ok && t >= 1 && t - 1 <= T) {
-        ok = mbar_wait(bar_mma, mma_phase);
-        mma_phase ^= 1u;
+    if constexpr (TC) {
+      if (tid == 0) {
+        bool ok = true;
+        if (t == 0) ok = mbar_wait(bar_b, 0, first_wait_limit);
+        if (ok && t >= 1 && t - 1 <= T) {
+          ok = mbar_wait(bar_mma, mma_phase);
+          mma_phase ^= 1u;
+        }
+        if (!ok) *s_fail = t == 0 ? 1 : 2;
       }
-      if (!ok) *s_fail = t == 0 ? 1 : 2;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (*s_fail) break;
 
-    // ================= phase B: gather the patch rows of group t =================
-    if (t <= T && l < NPC) {
-      // patch (pi, pj) = (i0 - 1 + l, j0 + 4 t - 3 + r); window node (2 pi - 2 + wi, 2 pj - 2 + wj)
-      // sits at residual column 2 l + wi (even: pair l + wi/2, odd: RHO + l + (wi-1)/2)
-      const int pj = j0 + 4 * t - 3 + r;
-      uint32_t w[26];
-#pragma unroll
-      for (int wj = 0; wj < 5; ++wj) {
-        const float2* rrow = sr + ((2 * pj - 2 + wj) % RR) * RPP + l;
-#pragma unroll
-        for (int wi = 0; wi < 5; ++wi) {
-          const float2 v = rrow[(wi & 1) * RHO + (wi >> 1)];
-          w[wj * 5 + wi] = pack_bf16x2(v.x, v.y);
-        }
-      }
-      w[25] = pack_bf16x2(srp[(pj & (CRR - 1)) * NCC + l + 1], 0.0f);
-      unsigned char* arow = sm + OFF_A + (tid >> 3) * 1024 + (tid & 7) * 16;
-#pragma unroll
-      for (int kg = 0; kg < 7; ++kg) {
-        const uint32_t a0 = 4 * kg < 26 ? w[4 * kg] : 0u;
-        const uint32_t a1 = 4 * kg + 1 < 26 ? w[4 * kg + 1] : 0u;
-        const uint32_t a2 = 4 * kg + 2 < 26 ? w[4 * kg + 2] : 0u;
-        const uint32_t a3 = 4 * kg + 3 < 26 ? w[4 * kg + 3] : 0u;
-        *reinterpret_cast<uint4*>(arow + kg * 128) = make_uint4(a0, a1, a2, a3);
-      }
-    }
-    // make the generic-proxy writes of R visible to the tensor cores
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-    // ================= phase C: MMA of group t; corrections of group t - 1 =================
-    if (tid == 0 && t <= T) {
-      const uint32_t a0 = su32(sm + OFF_A), b0 = su32(sm + OFF_B), acc = tmem + 64 * (t & 1);
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const uint64_t da = umma_desc(a0 + s * 256);
-        const uint64_t db = umma_desc(b0 + s * 256);
-        const uint32_t accum = s > 0 ? 1u : 0u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
-            "l"(da), "l"(db), "r"(IDESC), "r"(accum));
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_mma)
-                   : "memory");
-    }
-    __syncwarp();
-    if (t >= 1 && t - 1 <= T) {
-      // patch row pj = j0 + 4 (t - 1) - 3 + r, lane l = patch pi = i0 - 1 + l; the node
-      // columns 2 pi - 1 (odd) and 2 pi (even) of window row wj take
-      //   odd:  D[pi - 1](wi = 3) + D[pi](wi = 1)
-      //   even: D[pi - 1](wi = 4) + D[pi](wi = 2) + D[pi + 1](wi = 0)
-      const int pj = j0 + 4 * (t - 1) - 3 + r;
-      float d[52];
-      tmem_ld52(tmem + (static_cast<uint32_t>(32 * r) << 16) + 64 * ((t - 1) & 1), d);
+    // corrections of patch row pj to per-node partial sums (phase C with the GEMM, in
+    // phase B with the FP32 solve, whose corrections are per thread, not in tensor memory).
+    // patch row pj, lane l = patch pi = i0 - 1 + l; the node columns 2 pi - 1 (odd) and
+    // 2 pi (even) of window row wj take
+    //   odd:  D[pi - 1](wi = 3) + D[pi](wi = 1)
+    //   even: D[pi - 1](wi = 4) + D[pi](wi = 2) + D[pi + 1](wi = 0)
+    auto store_partials = [&](int pj, const float* d) {
       float4* dst = sps + (pj % SRR) * 160 + l;
 #pragma unroll
       for (int wj = 0; wj < 5; ++wj) {
@@ -564,6 +540,104 @@ __global__ void __launch_bounds__(NT, 4) k_vanka_tc(LevelDev L, const uint4* __r
         dst[wj * 32] = make_float4(odd.x, odd.y, even.x, even.y);
       }
       spp[(pj % SRR) * 32 + l] = d[50];
+    };
+    // ================= phase B: the patch rows of group t =================
+    // patch (pi, pj) = (i0 - 1 + l, j0 + 4 t - 3 + r); window node (2 pi - 2 + wi, 2 pj - 2 + wj)
+    // sits at residual column 2 l + wi (even: pair l + wi/2, odd: RHO + l + (wi-1)/2)
+    if constexpr (TC) {
+      if (t <= T && l < NPC) {
+        const int pj = j0 + 4 * t - 3 + r;
+        uint32_t w[26];
+#pragma unroll
+        for (int wj = 0; wj < 5; ++wj) {
+          const float2* rrow = sr + ((2 * pj - 2 + wj) % RR) * RPP + l;
+#pragma unroll
+          for (int wi = 0; wi < 5; ++wi) {
+            const float2 v = rrow[(wi & 1) * RHO + (wi >> 1)];
+            w[wj * 5 + wi] = pack_bf16x2(v.x, v.y);
+          }
+        }
+        w[25] = pack_bf16x2(srp[(pj & (CRR - 1)) * NCC + l + 1], 0.0f);
+        unsigned char* arow = sm + Y::A + (tid >> 3) * 1024 + (tid & 7) * 16;
+#pragma unroll
+        for (int kg = 0; kg < 7; ++kg) {
+          const uint32_t a0 = 4 * kg < 26 ? w[4 * kg] : 0u;
+          const uint32_t a1 = 4 * kg + 1 < 26 ? w[4 * kg + 1] : 0u;
+          const uint32_t a2 = 4 * kg + 2 < 26 ? w[4 * kg + 2] : 0u;
+          const uint32_t a3 = 4 * kg + 3 < 26 ? w[4 * kg + 3] : 0u;
+          *reinterpret_cast<uint4*>(arow + kg * 128) = make_uint4(a0, a1, a2, a3);
+        }
+      }
+      // make the generic-proxy writes of R visible to the tensor cores
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    } else if (t <= T) {
+      // every lane takes part in the shuffles of the partial sums; lanes 30, 31 add zeros
+      float d[52];
+#pragma unroll
+      for (int k = 0; k < 52; ++k) d[k] = 0.0f;
+      const int pj = j0 + 4 * t - 3 + r;
+      if (l < NPC) {
+        // the exact interior patch solve (Section 6.3) in FP32, both velocity components
+        // packed: dp = (z . r_u - r_p) / s with z = zs z_u, then K^-1 (r_u - b^T dp) by
+        // fast diagonalisation; corrections in the kernel's slot order
+        float2 r2[25];
+#pragma unroll
+        for (int wj = 0; wj < 5; ++wj) {
+          const float2* rrow = sr + ((2 * pj - 2 + wj) % RR) * RPP + l;
+#pragma unroll
+          for (int wi = 0; wi < 5; ++wi) r2[wj * 5 + wi] = rrow[(wi & 1) * RHO + (wi >> 1)];
+        }
+        const float rp = srp[(pj & (CRR - 1)) * NCC + l + 1];
+        float zr = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 25; ++k) zr = fmaf(c_zu_strip[k], r2[k].x, zr);
+#pragma unroll
+        for (int k = 0; k < 25; ++k) zr = fmaf(c_zu_strip[25 + k], r2[k].y, zr);
+        const float dp = (L.zsf * zr - rp) * L.zsinvf;
+        const float q = cb * dp;
+#pragma unroll
+        for (int w = 0; w < 25; ++w) {
+          const int dI = w % 5 - 2, dJ = w / 5 - 2;
+          const float bx = static_cast<float>(crow(dI) * nrow(dJ)), by = static_cast<float>(nrow(dI) * crow(dJ));
+          if (bx != 0.0f || by != 0.0f) r2[w] = __ffma2_rn(make_float2(-bx, -by), make_float2(q, q), r2[w]);
+        }
+        float2 y2[25];
+        fdm::fd_solve<float2>(fdp, r2, y2);
+#pragma unroll
+        for (int w = 0; w < 25; ++w) {
+          d[2 * w] = y2[w].x;
+          d[2 * w + 1] = y2[w].y;
+        }
+        d[50] = dp;
+      }
+      store_partials(pj, d);
+    }
+    if constexpr (TC) {
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // the MMA of group t, then the corrections of group t - 1 from the other buffer
+      if (tid == 0 && t <= T) {
+        const uint32_t a0 = su32(sm + Y::A), b0 = su32(sm + Y::B), acc = tmem + 64 * (t & 1);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const uint64_t da = umma_desc(a0 + s * 256);
+          const uint64_t db = umma_desc(b0 + s * 256);
+          const uint32_t accum = s > 0 ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
+              "l"(da), "l"(db), "r"(IDESC), "r"(accum));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_mma)
+                     : "memory");
+      }
+      __syncwarp();
+      if (t >= 1 && t - 1 <= T) {
+        float d[52];
+        tmem_ld52(tmem + (static_cast<uint32_t>(32 * r) << 16) + 64 * ((t - 1) & 1), d);
+        store_partials(j0 + 4 * (t - 1) - 3 + r, d);
+      }
     }
     if (pf) {
       if (has_x) {
@@ -592,18 +666,20 @@ __global__ void __launch_bounds__(NT, 4) k_vanka_tc(LevelDev L, const uint4* __r
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   }
 
-  const int fail = *s_fail;
-  if (fail && tid == 0) {
-    atomicExch(err, 1);
-    // the bulk copy, and an MMA issued before the failed wait, may still be in flight
-    mbar_wait(bar_b, 0);
-    if (fail == 2) mbar_wait(bar_mma, mma_phase ^ 1u);
+  if constexpr (TC) {
+    const int fail = *s_fail;
+    if (fail && tid == 0) {
+      atomicExch(err, 1);
+      // the bulk copy, and an MMA issued before the failed wait, may still be in flight
+      mbar_wait(bar_b, 0);
+      if (fail == 2) mbar_wait(bar_mma, mma_phase ^ 1u);
+    }
+    // teardown: free tensor memory
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (r == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
   }
-  // teardown: free tensor memory
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (r == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
 }  // namespace
@@ -621,8 +697,29 @@ void tc_interior_range(int n, int* lo, int* hi) {
 }
 
 cudaError_t vanka_tc_prepare() {
-  return cudaFuncSetAttribute(k_vanka_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  cudaError_t e = cudaFuncSetAttribute(k_vanka_strip<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SL<true>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_vanka_strip<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SL<false>::BYTES);
+  return e;
 }
+
+cudaError_t set_strip_unit_z(const double* z50) {
+  float zf[50];
+  for (int k = 0; k < 50; ++k) zf[k] = static_cast<float>(z50[k]);
+  return cudaMemcpyToSymbol(c_zu_strip, zf, 50 * sizeof(float));
+}
+
+namespace {
+// segments of 4 tiles (fewer prologue steps) when that still gives the GPU several
+// waves of CTAs, else of 2 tiles
+dim3 strip_grid(int cnt, int* seg) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  *seg = ((cnt / 2) * ((cnt + SEG_MAX - 1) / SEG_MAX) >= 16 * sms) ? SEG_MAX : 2;
+  return dim3(cnt / 2, (cnt + *seg - 1) / *seg);
+}
+}  // namespace
 
 void launch_vanka_tc(const LevelDev& L, const void* Bcanon, const float* x, const float* b, float* xo,
                      double omega, int lo, int hi, int* err, cudaStream_t s, int first_wait_limit) {
@@ -630,15 +727,25 @@ void launch_vanka_tc(const LevelDev& L, const void* Bcanon, const float* x, cons
   if (cnt < 2 || (cnt & 1)) return;
   count_launches(1);
   g_tc_launches.fetch_add(1, std::memory_order_relaxed);
-  // segments of 4 tiles (fewer prologue steps) when that still gives the GPU
-  // several waves of CTAs, else of 2 tiles
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int seg = ((cnt / 2) * ((cnt + SEG_MAX - 1) / SEG_MAX) >= 16 * sms) ? SEG_MAX : 2;
-  const dim3 grid(cnt / 2, (cnt + seg - 1) / seg);
-  launch_pdl(k_vanka_tc, grid, dim3(NT), SMEM_BYTES, s, L, static_cast<const uint4*>(Bcanon), x, b, xo,
-             static_cast<float>(omega), lo, hi, seg, err, first_wait_limit);
+  int seg = 2;
+  const dim3 grid = strip_grid(cnt, &seg);
+  launch_pdl(k_vanka_strip<true>, grid, dim3(NT), SL<true>::BYTES, s, L, static_cast<const uint4*>(Bcanon),
+             FastDiagT<float2>{}, x, b, xo, static_cast<float>(omega), lo, hi, seg, err, first_wait_limit);
+}
+
+void launch_vanka_strip_f32(const LevelDev& L, const FastDiagT<float>& fd, const float* x, const float* b,
+                            float* xo, double omega, int lo, int hi, cudaStream_t s) {
+  const int cnt = hi - lo + 1;
+  if (cnt < 2 || (cnt & 1)) return;
+  count_launches(1);
+  FastDiagT<float2> fp{};   // (v, v) pairs: both velocity components in one packed pass
+  for (int k = 0; k < 9; ++k) fp.se[k] = make_float2(fd.se[k], fd.se[k]);
+  for (int k = 0; k < 4; ++k) fp.so[k] = make_float2(fd.so[k], fd.so[k]);
+  for (int k = 0; k < 25; ++k) fp.dinv[k] = make_float2(fd.dinv[k], fd.dinv[k]);
+  int seg = 2;
+  const dim3 grid = strip_grid(cnt, &seg);
+  launch_pdl(k_vanka_strip<false>, grid, dim3(NT), SL<false>::BYTES, s, L, static_cast<const uint4*>(nullptr), fp,
+             x, b, xo, static_cast<float>(omega), lo, hi, seg, static_cast<int*>(nullptr), 0);
 }
 
 // slot of the dense 51 x 51 inverse (u_x window 0..24, u_y window 25..49, p 50)

@@ -1,8 +1,9 @@
 """Mixed-precision sweeps dof by dof against the FP64 oracle, and the failure paths.
 
 stokes_relaxation_sweep runs one sweep of the V-cycle's smoother in the
-hierarchy's arithmetic: FP32 (mixed form) or FP32 with the interior patch
-solves as BF16 tensor-core GEMMs (BF16 form).  Each output dof is compared with
+hierarchy's arithmetic: FP32 (mixed form; with tile 3 the interior tiles on the
+FP32 strip kernel) or FP32 with the interior patch solves as BF16 tensor-core
+GEMMs (BF16 form).  Each output dof is compared with
 the oracle's FP64 sweep (Algorithm 3) against the a-priori rounding bound of
 oracle/rounding.py, computed from the oracle's own patch inverses and residual:
 BF16 terms on the dofs that tensor-core tiles own, FP32 terms everywhere.
@@ -104,6 +105,47 @@ def test_fp32_sweep_dof_by_dof(pkg, n, tile):
         ref = O.vanka_sweep(lv, np.zeros_like(b) if x is None else x, b, OMEGA)
         q = ratio(got, ref, RB.sweep_error_bound(lv, x, b, OMEGA))
         assert q <= 1.0, (zero_guess, q)
+    H.close()
+
+
+@pytest.mark.parametrize("zero_guess", [False, True])
+@pytest.mark.parametrize("n", [64, 128, 256])
+def test_fp32_strip_sweep_dof_by_dof(pkg, n, zero_guess):
+    """Tile 3 in the mixed FP32 form: the interior 14 x 14 tiles on the strip kernel, each
+    patch solved in FP32 by fast diagonalisation, the ring on the SIMT kernel.  Every dof,
+    those of the strips included, within the FP32 bound."""
+    from paper_2401_06277_gb300 import stokes
+    H = pkg.Hierarchy(n, prec=stokes.STOKES_MIXED_FP32, tile=3)
+    lv, x, b = inputs(n, 130 + n, zero_guess)
+    got = gpu_relax(H, x, b)
+    ref = O.vanka_sweep(lv, np.zeros_like(b) if x is None else x, b, OMEGA)
+    assert RB.tensor_core_dofs(n).any()
+    q = ratio(got, ref, RB.sweep_error_bound(lv, x, b, OMEGA))
+    assert q <= 1.0, q
+    H.close()
+
+
+def test_fp32_strip_sweep_on_a_coarser_level_and_its_launches(pkg):
+    """Level n = 128 of a 256 hierarchy within the FP32 bound; a sweep with strips is two
+    kernels (strip and ring) and three FP64/FP32 conversions, one without (the SIMT 8 x 8
+    tile, tile 0) is one kernel and the conversions."""
+    from paper_2401_06277_gb300 import stokes
+    H = pkg.Hierarchy(256, prec=stokes.STOKES_MIXED_FP32, tile=3)
+    lv, x, b = inputs(128, 79, False)
+    got = gpu_relax(H, x, b, lvl=H.levels - 2)
+    ref = O.vanka_sweep(lv, x, b, OMEGA)
+    assert ratio(got, ref, RB.sweep_error_bound(lv, x, b, OMEGA)) <= 1.0
+    xd, bd = dev(x), dev(b)
+    out = torch.empty_like(bd)
+    for tile, launches in ((3, 5), (0, 4)):
+        Ht = pkg.Hierarchy(128, prec=stokes.STOKES_MIXED_FP32, tile=tile)
+        torch.cuda.synchronize()
+        s0 = stokes.stokes_stats_read(Ht.handle)
+        stokes.stokes_relaxation_sweep(Ht.handle, Ht.levels - 1, xd, bd, out)
+        s1 = stokes.stokes_stats_read(Ht.handle)
+        assert s1["kernel_launches"] - s0["kernel_launches"] == launches, tile
+        assert s1["tc_launches"] == s0["tc_launches"]   # no tensor-core kernel in the FP32 form
+        Ht.close()
     H.close()
 
 
