@@ -464,8 +464,13 @@ def _time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother, h
         by = (3.0 - ZERO_GUESS_SHARE) * 4.0 * N
         peak = peaks.get("hbm_gbs", 6780.0)
         achieved = by / (sweep_ms * 1e-3) / 1e9
-        kname = ("k_vanka_tc interior tiles + k_vanka<float,14,14> ring (finest level)" if prec_name == "bf16"
-                 else "k_vanka<float> (finest level)")
+        if tile == "14x14":
+            kname = ("k_vanka_strip<true> (BF16 tcgen05 patch GEMMs) on the interior strips + k_vanka<float,14,14> "
+                     "ring (finest level)" if prec_name == "bf16" else
+                     "k_vanka_strip<false> (FP32 fast-diagonalisation solves) on the interior strips + "
+                     "k_vanka<float,14,14> ring (finest level)")
+        else:
+            kname = "k_vanka<float> (finest level)"
         roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                     "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)",

@@ -65,7 +65,7 @@ constexpr int XN = 2 * SW + 12;     // x window nodes per row (68)
 constexpr int NPW = SW + 6;         // p window vertices per row (34)
 constexpr int GR = 4;               // vertex rows per step
 constexpr int NT = 128;             // threads
-constexpr int SEG_MAX = 4;          // segment length in 14-vertex tiles: 4 (56 rows) or 2 (28)
+constexpr int CTAS_PER_SM = 4;      // resident CTAs per SM (registers; tensor memory in the GEMM form)
 static_assert(NCC == 32 && NPC <= 32 && GR * 32 == NT, "warp r <-> row r, lane <-> column");
 
 // Rings (row index taken modulo the ring size; each holds exactly the rows that are
@@ -190,7 +190,7 @@ template <bool TC>
 __global__ void __launch_bounds__(NT, 4) k_vanka_strip(LevelDev L, const uint4* __restrict__ Bg,
                                                        const FastDiagT<float2> fdp, const float* __restrict__ x,
                                                        const float* __restrict__ b, float* __restrict__ xo,
-                                                       float omega, int lo, int hi, int seg_tiles,
+                                                       float omega, int lo, int hi, int seg_rows,
                                                        int* __restrict__ err, int first_wait_limit) {
   pdl_begin();
   using Y = SL<TC>;
@@ -209,9 +209,8 @@ __global__ void __launch_bounds__(NT, 4) k_vanka_strip(LevelDev L, const uint4* 
   const long long nv = L.nv;
   const int tid = threadIdx.x, r = tid >> 5, l = tid & 31;
   const int i0 = TC_TILE * (lo + 2 * static_cast<int>(blockIdx.x));
-  const int seg0 = lo + seg_tiles * static_cast<int>(blockIdx.y);
-  const int j0 = TC_TILE * seg0;
-  const int S = TC_TILE * min(seg_tiles, hi + 1 - seg0);   // owned rows, a multiple of 28
+  const int j0 = TC_TILE * lo + seg_rows * static_cast<int>(blockIdx.y);
+  const int S = min(seg_rows, TC_TILE * (hi + 1) - j0);   // owned rows, a multiple of 4
   const int T = S / GR;                                     // steps with cells / patches
   const int XI0 = 2 * i0 - 6;                               // x window origin (Q2 column)
   const bool has_x = x != nullptr;
@@ -710,14 +709,37 @@ cudaError_t set_strip_unit_z(const double* z50) {
 }
 
 namespace {
-// segments of 4 tiles (fewer prologue steps) when that still gives the GPU several
-// waves of CTAs, else of 2 tiles
-dim3 strip_grid(int cnt, int* seg) {
+// Segments of a strip: a whole number of 4-row steps each.  A segment of s steps
+// runs s + 3 loop iterations (the first computes residual rows below it, the last
+// ones finish its updates), and the CTAs run in waves of CTAS_PER_SM per SM, so
+// the time is about waves x (s + 3) step times: the count of segments per strip
+// minimises that (ties: fewer CTAs).  At 2048^2 (72 strips of 504 steps, 152 SMs)
+// that is 8 segments of 63 steps, 576 CTAs: one wave.
+int strip_segment_steps(int strips, int steps, int sms) {
+  const int slots = CTAS_PER_SM * sms;
+  long long best = -1;
+  int best_s = steps;
+  for (int nseg = 1; nseg <= steps; ++nseg) {
+    const int s = (steps + nseg - 1) / nseg;
+    const int used = (steps + s - 1) / s;   // segments actually launched
+    const long long waves = (static_cast<long long>(strips) * used + slots - 1) / slots;
+    const long long cost = waves * (s + 3);
+    if (best < 0 || cost < best) {
+      best = cost;
+      best_s = s;
+    }
+  }
+  return best_s;
+}
+
+dim3 strip_grid(int cnt, int* seg_rows) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  *seg = ((cnt / 2) * ((cnt + SEG_MAX - 1) / SEG_MAX) >= 16 * sms) ? SEG_MAX : 2;
-  return dim3(cnt / 2, (cnt + *seg - 1) / *seg);
+  const int steps = TC_TILE * cnt / GR;   // cnt is even: 28-row pairs of tiles
+  const int s = strip_segment_steps(cnt / 2, steps, sms);
+  *seg_rows = GR * s;
+  return dim3(cnt / 2, (steps + s - 1) / s);
 }
 }  // namespace
 
@@ -727,7 +749,7 @@ void launch_vanka_tc(const LevelDev& L, const void* Bcanon, const float* x, cons
   if (cnt < 2 || (cnt & 1)) return;
   count_launches(1);
   g_tc_launches.fetch_add(1, std::memory_order_relaxed);
-  int seg = 2;
+  int seg = GR;
   const dim3 grid = strip_grid(cnt, &seg);
   launch_pdl(k_vanka_strip<true>, grid, dim3(NT), SL<true>::BYTES, s, L, static_cast<const uint4*>(Bcanon),
              FastDiagT<float2>{}, x, b, xo, static_cast<float>(omega), lo, hi, seg, err, first_wait_limit);
@@ -742,7 +764,7 @@ void launch_vanka_strip_f32(const LevelDev& L, const FastDiagT<float>& fd, const
   for (int k = 0; k < 9; ++k) fp.se[k] = make_float2(fd.se[k], fd.se[k]);
   for (int k = 0; k < 4; ++k) fp.so[k] = make_float2(fd.so[k], fd.so[k]);
   for (int k = 0; k < 25; ++k) fp.dinv[k] = make_float2(fd.dinv[k], fd.dinv[k]);
-  int seg = 2;
+  int seg = GR;
   const dim3 grid = strip_grid(cnt, &seg);
   launch_pdl(k_vanka_strip<false>, grid, dim3(NT), SL<false>::BYTES, s, L, static_cast<const uint4*>(nullptr), fp,
              x, b, xo, static_cast<float>(omega), lo, hi, seg, static_cast<int*>(nullptr), 0);
