@@ -255,12 +255,12 @@ TRAFFIC_1024 = {
     "fp64": {"bytes": 155278848 + 378243840 + 506067200 + 66107392, "tile": "split16x16x2",
              "source": "profiles/k_vanka_own_f64_n1024.md (k_vanka_own<double,16,16,256,2> + k_patch_update; "
                        "writes still in L2 at kernel end are not counted)"},
-    "mixed": {"bytes": 75656704 + 13535744, "tile": "14x14",
-              "source": "profiles/k_vanka_f32_n1024.md (k_vanka<float,14,14,256>, the tile the tuner picks; "
-                        "writes still in L2 at kernel end are not counted)"},
-    "bf16": {"bytes": 74801408 + 11694592, "tile": "14x14",
-             "source": "profiles/k_vanka_tc_n1024.md (k_vanka_tc interior tiles; the ring launch is not "
-                       "included; writes still in L2 at kernel end are not counted)"},
+    "mixed": {"bytes": 76410112 + 7026944, "tile": "14x14",
+              "source": "profiles/k_vanka_strip_f32_n1024.md (k_vanka_strip<false> interior strips; the ring "
+                        "launch is not included; writes still in L2 at kernel end are not counted)"},
+    "bf16": {"bytes": 77008640 + 5505280, "tile": "14x14",
+             "source": "profiles/k_vanka_strip_bf16_n1024.md (k_vanka_strip<true> interior strips; the ring "
+                       "launch is not included; writes still in L2 at kernel end are not counted)"},
 }
 
 

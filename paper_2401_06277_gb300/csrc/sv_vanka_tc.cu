@@ -65,39 +65,49 @@ constexpr int XN = 2 * SW + 12;     // x window nodes per row (68)
 constexpr int NPW = SW + 6;         // p window vertices per row (34)
 constexpr int GR = 4;               // vertex rows per step
 constexpr int NT = 128;             // threads
-constexpr int CTAS_PER_SM = 4;      // resident CTAs per SM (registers; tensor memory in the GEMM form)
+// resident CTAs per SM: 4 in the GEMM form (tensor memory, shared memory), 5 in the
+// FP32 form (registers)
+__host__ __device__ constexpr int ctas_per_sm(bool tc) { return tc ? 4 : 5; }
 static_assert(NCC == 32 && NPC <= 32 && GR * 32 == NT, "warp r <-> row r, lane <-> column");
 
 // Rings (row index taken modulo the ring size; each holds exactly the rows that are
 // alive across a phase boundary).  x: node rows, (u_x, u_y) pairs, column-parity
 // split (even nodes at pair c/2, odd nodes at XHO + c/2): the stencil loads of a
 // warp read 32 consecutive pairs; the prefetch stores of a half-warp (8 even, 8
-// odd nodes) hit disjoint banks since XHO = 40 = 8 (mod 16).
-constexpr int XR = 12, XHO = 40, XPP = XHO + XN / 2;        // 12 node rows of 74 pairs
+// odd nodes) hit disjoint banks since XHO = 40 = 8 (mod 16).  The GEMM form stores
+// the next step's x and p rows after phase B, over rows read in phase A (12 and 6
+// rows); the FP32 form stores them at the end of phase A, beside the rows still
+// being read (20 and 10 rows), so that no prefetched value is held in registers
+// across its patch solves.
+__host__ __device__ constexpr int xr_rows(bool tc) { return tc ? 12 : 20; }
+__host__ __device__ constexpr int prr_rows(bool tc) { return tc ? 6 : 10; }
+constexpr int XHO = 40, XPP = XHO + XN / 2;                 // node rows of 74 pairs
 constexpr int RR = 12, RHO = 32, RPP = 64;                  // residual: 12 node rows of 64 pairs
 constexpr int CRR = 8;                                      // cell rows (pressure residual)
-constexpr int PRR = 6, PPW = 36;                            // p: 6 vertex rows of 34 (+2)
+constexpr int PPW = 36;                                     // p: vertex rows of 34 (+2)
 constexpr int SRR = 6;                                      // partial sums: 6 patch rows
 static_assert(XN / 2 <= XHO && (2 * XHO) % 32 == 16, "x ring layout");
 
 // Shared-memory layout (bytes).  The FP32 strip sweep (TC = false) has no GEMM
-// operands, so its rings start at 0.
+// operands, so its rings start at 0; it keeps the next step's b of each thread's
+// cell in BS ([value][thread], 9 values) instead of registers.
 template <bool TC>
 struct SL {
   static constexpr int A = 0;                               // 128 x 64 BF16 = 16 KB (TC)
   static constexpr int B = A + 128 * 64 * 2;                // 64 x 64 BF16 = 8 KB (TC)
   static constexpr int X = TC ? B + 64 * 64 * 2 : 0;
-  static constexpr int R = X + XR * XPP * 8;
+  static constexpr int R = X + xr_rows(TC) * XPP * 8;
   static constexpr int RPR = R + RR * RPP * 8;
   static constexpr int P = RPR + CRR * NCC * 4;
-  static constexpr int PS = P + PRR * PPW * 4;               // [row][wj][lane] float4
+  static constexpr int PS = P + prr_rows(TC) * PPW * 4;      // [row][wj][lane] float4
   static constexpr int PSP = PS + SRR * 5 * 32 * 16;         // [row][lane] pressure corrections
-  static constexpr int BAR = PSP + SRR * 32 * 4;             // bulk-copy and MMA mbarriers
+  static constexpr int BS = PSP + SRR * 32 * 4;
+  static constexpr int BAR = BS + (TC ? 0 : 9 * NT * 4);     // bulk-copy and MMA mbarriers
   static constexpr int TMEM = BAR + 16;
   static constexpr int FLAG = TMEM + 4;
   static constexpr int BYTES = FLAG + 12;
   static_assert(X % 16 == 0 && PS % 16 == 0 && BAR % 8 == 0, "alignment");
-  static_assert(4 * (BYTES + 1024) <= 228 * 1024, "four CTAs per SM");
+  static_assert(ctas_per_sm(TC) * (BYTES + 1024) <= 228 * 1024, "resident CTAs per SM");
 };
 
 constexpr uint32_t TMEM_COLS = 128;   // two 64-column accumulators (4 CTAs per SM: all 512 columns)
@@ -174,10 +184,6 @@ __device__ __forceinline__ float ldg_early(const float* p) {
   return v;
 }
 
-__device__ __forceinline__ bool free_node(int I, int J, int nq) {
-  return I > 0 && J > 0 && I < nq - 1 && J < nq - 1;
-}
-
 // z_u of the interior patches (the Schur vector K^-1 b^T at unit viscosity and
 // spacing, u_x window then u_y window) for the FP32 strip sweep; a level scales it
 // by zs.  Compile-time slot indices make it a constant-bank operand.
@@ -187,13 +193,14 @@ __constant__ float c_zu_strip[50];
 // its interior patch by fast diagonalisation (fdp: the (v, v) pairs of the FP32
 // factors; z_u from constant memory) in the same strip walk.
 template <bool TC>
-__global__ void __launch_bounds__(NT, 4) k_vanka_strip(LevelDev L, const uint4* __restrict__ Bg,
+__global__ void __launch_bounds__(NT, ctas_per_sm(TC)) k_vanka_strip(LevelDev L, const uint4* __restrict__ Bg,
                                                        const FastDiagT<float2> fdp, const float* __restrict__ x,
                                                        const float* __restrict__ b, float* __restrict__ xo,
                                                        float omega, int lo, int hi, int seg_rows,
                                                        int* __restrict__ err, int first_wait_limit) {
   pdl_begin();
   using Y = SL<TC>;
+  constexpr int XR = xr_rows(TC), PRR = prr_rows(TC);
   extern __shared__ __align__(1024) unsigned char sm[];
   float2* sx = reinterpret_cast<float2*>(sm + Y::X);
   float2* sr = reinterpret_cast<float2*>(sm + Y::R);
@@ -201,6 +208,7 @@ __global__ void __launch_bounds__(NT, 4) k_vanka_strip(LevelDev L, const uint4* 
   float* sp = reinterpret_cast<float*>(sm + Y::P);
   float4* sps = reinterpret_cast<float4*>(sm + Y::PS);
   float* spp = reinterpret_cast<float*>(sm + Y::PSP);
+  float* sbs = reinterpret_cast<float*>(sm + Y::BS);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + Y::BAR);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + Y::TMEM);
   volatile int* s_fail = reinterpret_cast<volatile int*>(sm + Y::FLAG);
@@ -307,6 +315,27 @@ __global__ void __launch_bounds__(NT, 4) k_vanka_strip(LevelDev L, const uint4* 
     o.p = ldg_early(b + 2 * nv + static_cast<long long>(cy) * np + cx);
     return o;
   };
+  // FP32 form: the next step's b of this thread's cell, kept in shared memory
+  auto b_stash = [&](const BCell& v) {
+#pragma unroll
+    for (int PJ = 0; PJ < 2; ++PJ)
+#pragma unroll
+      for (int PI = 0; PI < 2; ++PI) {
+        sbs[(4 * PJ + 2 * PI) * NT + tid] = v.v[PJ][PI].x;
+        sbs[(4 * PJ + 2 * PI + 1) * NT + tid] = v.v[PJ][PI].y;
+      }
+    sbs[8 * NT + tid] = v.p;
+  };
+  auto b_unstash = [&]() -> BCell {
+    BCell o;
+#pragma unroll
+    for (int PJ = 0; PJ < 2; ++PJ)
+#pragma unroll
+      for (int PI = 0; PI < 2; ++PI)
+        o.v[PJ][PI] = make_float2(sbs[(4 * PJ + 2 * PI) * NT + tid], sbs[(4 * PJ + 2 * PI + 1) * NT + tid]);
+    o.p = sbs[8 * NT + tid];
+    return o;
+  };
 
   // prologue: x rows 2 j0 - 6 .. 2 j0 + 5, p rows j0 - 3 .. j0 + 2, b of step 0
   if (has_x) {
@@ -328,15 +357,23 @@ __global__ void __launch_bounds__(NT, 4) k_vanka_strip(LevelDev L, const uint4* 
     }
   }
   // b of this step's cells (bc) and of the next step's (bn), loaded two steps ahead
-  BCell bc = b_load(j0 - 2 + r);
-  BCell bn = b_load(j0 + 2 + r);
+  // (GEMM form); the FP32 form stashes step 0's and loads one step ahead
+  BCell bc, bn;
+  if constexpr (TC) {
+    bc = b_load(j0 - 2 + r);
+    bn = b_load(j0 + 2 + r);
+  } else {
+    b_stash(b_load(j0 - 2 + r));
+  }
   __syncthreads();
 
   // prefetch registers (step t + 1): x rows 2 j0 + 8 t + 6 + {r, r + 4} x 2 column-pair
   // chunks, p row j0 + 4 t + 3 + r x 2 chunks
   XPair xpf[2][2];
   float ppf[2];
-  float xold[9];   // x at the dofs of this step's update (loaded a step earlier; 0 for a zero guess)
+  // x at the dofs of this step's update (0 for a zero guess): loaded a step earlier in
+  // the GEMM form, at the top of phase A in the FP32 form
+  float xold[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) xold[k] = 0.0f;
   uint32_t mma_phase = 0;
@@ -347,35 +384,41 @@ __global__ void __launch_bounds__(NT, 4) k_vanka_strip(LevelDev L, const uint4* 
   for (int t = 0; t <= T + (TC ? 2 : 1); ++t) {
     // ================= phase A: residual of cell rows t, update, prefetch =================
     const bool pf = (t + 1 <= T);
-    // the update of this step (vertex row vb) and, loaded a step ahead, the next
-    // step's x_old (9 values per vertex; in L2: its rows were loaded into the window)
+    // the update of this step (vertex row vb) and its x_old (9 values per vertex; in
+    // L2: its rows were loaded into the window)
     const int vb = j0 + 4 * t - LAG + r;
     const bool upd = vb >= j0 && vb < j0 + S && l >= 1 && l <= SW;
     const int vi = i0 + l - 1;
     const long long ke = static_cast<long long>(2 * vb) * nq + 2 * vi;   // node (2 vi, 2 vb)
     const long long ko = ke - nq;                                         // node (2 vi, 2 vb - 1)
     const long long kp = 2 * nv + static_cast<long long>(vb) * np + vi;
-    float xold_n[9];
-    {
-      const int vbn = vb + GR;
-      if (has_x && vbn >= j0 && vbn < j0 + S && l >= 1 && l <= SW) {
-        const long long ken = ke + 2LL * GR * nq, kon = ken - nq, kpn = kp + static_cast<long long>(GR) * np;
-        xold_n[0] = ldg_early(x + ken);
-        xold_n[1] = ldg_early(x + nv + ken);
-        xold_n[2] = ldg_early(x + ken - 1);
-        xold_n[3] = ldg_early(x + nv + ken - 1);
-        xold_n[4] = ldg_early(x + kon);
-        xold_n[5] = ldg_early(x + nv + kon);
-        xold_n[6] = ldg_early(x + kon - 1);
-        xold_n[7] = ldg_early(x + nv + kon - 1);
-        xold_n[8] = ldg_early(x + kpn);
+    auto load_xold = [&](int dv, float* o) {   // vertex row vb + dv
+      const int vr = vb + dv;
+      if (has_x && vr >= j0 && vr < j0 + S && l >= 1 && l <= SW) {
+        const long long kk = ke + 2LL * dv * nq, kq = kk - nq, kpp = kp + static_cast<long long>(dv) * np;
+        o[0] = ldg_early(x + kk);
+        o[1] = ldg_early(x + nv + kk);
+        o[2] = ldg_early(x + kk - 1);
+        o[3] = ldg_early(x + nv + kk - 1);
+        o[4] = ldg_early(x + kq);
+        o[5] = ldg_early(x + nv + kq);
+        o[6] = ldg_early(x + kq - 1);
+        o[7] = ldg_early(x + nv + kq - 1);
+        o[8] = ldg_early(x + kpp);
       } else {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) xold_n[k] = 0.0f;
+        for (int k = 0; k < 9; ++k) o[k] = 0.0f;
       }
+    };
+    float xold_n[TC ? 9 : 1];
+    BCell bn2;   // b two steps ahead (GEMM form), one step ahead (FP32 form)
+    if constexpr (TC) {
+      load_xold(GR, xold_n);
+      if (t + 2 <= T) bn2 = b_load(j0 + 4 * t + 6 + r);
+    } else {
+      load_xold(0, xold);
+      if (t + 1 <= T) bn2 = b_load(j0 + 4 * t + 2 + r);
     }
-    BCell bn2;
-    if (t + 2 <= T) bn2 = b_load(j0 + 4 * t + 6 + r);
     if (pf) {
       if (has_x) {
 #pragma unroll
@@ -397,6 +440,7 @@ __global__ void __launch_bounds__(NT, 4) k_vanka_strip(LevelDev L, const uint4* 
     if (t <= T) {
       // cell (cx, cy) = (i0 - 2 + l, j0 - 2 + 4 t + r): Q2 nodes (2 cx + PI, 2 cy + PJ)
       const int cy = j0 - 2 + 4 * t + r;
+      if constexpr (!TC) bc = b_unstash();
       float2 res[2][2];
 #pragma unroll
       for (int PJ = 0; PJ < 2; ++PJ)
@@ -499,6 +543,30 @@ __global__ void __launch_bounds__(NT, 4) k_vanka_strip(LevelDev L, const uint4* 
       xo[ko - 1] = fmaf(w4, s_oo.x, xold[6]);
       xo[nv + ko - 1] = fmaf(w4, s_oo.y, xold[7]);
       xo[kp] = fmaf(omega, dp, xold[8]);
+    }
+    // the next step's x and p rows into their rings, b into its stash
+    auto store_prefetch = [&]() {
+      if (pf && has_x) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int J = 2 * j0 + 8 * t + 6 + r + 4 * h;
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const int q = l + 32 * k;
+            if (q < XN / 2) x_pair_store(J, q, xpf[h][k]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int c = l + 32 * k;
+          if (c < NPW) sp[((j0 + 4 * t + 3 + r) % PRR) * PPW + c] = ppf[k];
+        }
+      }
+    };
+    if constexpr (!TC) {
+      // FP32 form: rows no warp reads in this step (the rings hold both)
+      store_prefetch();
+      if (pf) b_stash(bn2);
     }
     // the MMA of step t - 1 must be complete before its operand is overwritten and
     // its accumulator read (issued a whole phase A earlier); the inverse's bulk copy
@@ -638,28 +706,16 @@ __global__ void __launch_bounds__(NT, 4) k_vanka_strip(LevelDev L, const uint4* 
         store_partials(j0 + 4 * (t - 1) - 3 + r, d);
       }
     }
-    if (pf) {
-      if (has_x) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int J = 2 * j0 + 8 * t + 6 + r + 4 * h;
-#pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            const int q = l + 32 * k;
-            if (q < XN / 2) x_pair_store(J, q, xpf[h][k]);
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int c = l + 32 * k;
-          if (c < NPW) sp[((j0 + 4 * t + 3 + r) % PRR) * PPW + c] = ppf[k];
-        }
+    if constexpr (TC) {
+      // GEMM form: over the rows phase A read
+      store_prefetch();
+      if (pf) {
+        bc = bn;
+        bn = bn2;
       }
-      bc = bn;
-      bn = bn2;
-    }
 #pragma unroll
-    for (int k = 0; k < 9; ++k) xold[k] = xold_n[k];
+      for (int k = 0; k < 9; ++k) xold[k] = xold_n[k];
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -711,12 +767,12 @@ cudaError_t set_strip_unit_z(const double* z50) {
 namespace {
 // Segments of a strip: a whole number of 4-row steps each.  A segment of s steps
 // runs s + 3 loop iterations (the first computes residual rows below it, the last
-// ones finish its updates), and the CTAs run in waves of CTAS_PER_SM per SM, so
+// ones finish its updates), and the CTAs run in waves of ctas_per_sm per SM, so
 // the time is about waves x (s + 3) step times: the count of segments per strip
 // minimises that (ties: fewer CTAs).  At 2048^2 (72 strips of 504 steps, 152 SMs)
-// that is 8 segments of 63 steps, 576 CTAs: one wave.
-int strip_segment_steps(int strips, int steps, int sms) {
-  const int slots = CTAS_PER_SM * sms;
+// that is 8 segments of 63 steps, 576 CTAs, in the GEMM form (4 per SM) and 10
+// segments of 51 steps, 720 CTAs, in the FP32 form (5 per SM): one wave.
+int strip_segment_steps(int strips, int steps, int slots) {
   long long best = -1;
   int best_s = steps;
   for (int nseg = 1; nseg <= steps; ++nseg) {
@@ -732,12 +788,12 @@ int strip_segment_steps(int strips, int steps, int sms) {
   return best_s;
 }
 
-dim3 strip_grid(int cnt, int* seg_rows) {
+dim3 strip_grid(int cnt, int* seg_rows, bool tc) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int steps = TC_TILE * cnt / GR;   // cnt is even: 28-row pairs of tiles
-  const int s = strip_segment_steps(cnt / 2, steps, sms);
+  const int s = strip_segment_steps(cnt / 2, steps, ctas_per_sm(tc) * sms);
   *seg_rows = GR * s;
   return dim3(cnt / 2, (steps + s - 1) / s);
 }
@@ -750,7 +806,7 @@ void launch_vanka_tc(const LevelDev& L, const void* Bcanon, const float* x, cons
   count_launches(1);
   g_tc_launches.fetch_add(1, std::memory_order_relaxed);
   int seg = GR;
-  const dim3 grid = strip_grid(cnt, &seg);
+  const dim3 grid = strip_grid(cnt, &seg, true);
   launch_pdl(k_vanka_strip<true>, grid, dim3(NT), SL<true>::BYTES, s, L, static_cast<const uint4*>(Bcanon),
              FastDiagT<float2>{}, x, b, xo, static_cast<float>(omega), lo, hi, seg, err, first_wait_limit);
 }
@@ -765,7 +821,7 @@ void launch_vanka_strip_f32(const LevelDev& L, const FastDiagT<float>& fd, const
   for (int k = 0; k < 4; ++k) fp.so[k] = make_float2(fd.so[k], fd.so[k]);
   for (int k = 0; k < 25; ++k) fp.dinv[k] = make_float2(fd.dinv[k], fd.dinv[k]);
   int seg = GR;
-  const dim3 grid = strip_grid(cnt, &seg);
+  const dim3 grid = strip_grid(cnt, &seg, false);
   launch_pdl(k_vanka_strip<false>, grid, dim3(NT), SL<false>::BYTES, s, L, static_cast<const uint4*>(nullptr), fp,
              x, b, xo, static_cast<float>(omega), lo, hi, seg, static_cast<int*>(nullptr), 0);
 }
