@@ -78,8 +78,10 @@ typedef struct {
   stokes_precision prec;  /*                                          (FP64) */
   int tile;         /* Vanka sweep configuration: -1 = chosen per level by
                        timing at creation; fused tiles of 0 = 8x8, 1 = 16x8,
-                       2 = 16x16, 3 = 14x14 vertices (BF16 form: 3 = the
-                       tensor-core sweep where it fits); 4 = split sweep
+                       2 = 16x16, 3 = 14x14 vertices (mixed forms: 3 = the
+                       strip sweep of the interior tiles where they fit --
+                       BF16 tensor-core patch GEMMs, or FP32 patch solves --
+                       with a 14x14 SIMT ring); 4 = split sweep
                        (16x16 own-patch solves writing the corrections, then a
                        separate update), 5 = the same compiled for two CTAs
                        per SM, 6 = fused 4x4 tiles (small levels: more
@@ -150,9 +152,9 @@ void stokes_default_params(stokes_params* p);
  * (Section 6.3) and the coarse-grid inverse.  n must be coarse_n * 2^k with
  * coarse_n >= 4.  viscosity > 0.  params may be NULL (defaults).  stream is a
  * cudaStream_t (NULL = legacy default stream).  The Krylov workspace
- * (2 restart + 1 vectors of N(n) doubles) is allocated here.  A BF16
- * hierarchy also owns a second (non-blocking) stream and two events: each
- * sweep forks the SIMT ring of boundary tiles onto that stream and joins it
+ * (2 restart + 1 vectors of N(n) doubles) is allocated here.  A mixed-
+ * precision hierarchy also owns a second (non-blocking) stream and two events:
+ * a strip sweep forks the SIMT ring of boundary tiles onto that stream and joins it
  * back, so every call stays ordered on `stream` (also under stream capture);
  * stokes_hierarchy_destroy synchronises and releases them. */
 stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_params* params,
@@ -162,10 +164,11 @@ stokes_status stokes_hierarchy_destroy(stokes_hierarchy* h);
 /* Number of levels L and the grid size n_l of level l (0 = coarsest). */
 stokes_status stokes_level_info(const stokes_hierarchy* h, int* num_levels, int* n_finest);
 stokes_status stokes_level_n(const stokes_hierarchy* h, int level, int* n_level);
-/* Sweep configuration used on a level (see stokes_params.tile).  In the BF16
- * form, 3 on a level where the tensor-core tile fits means the tensor-core
- * sweep (interior tiles) with its 14x14 SIMT ring; the autotuner may choose a
- * SIMT shape (0..2, 6, or the split sweep 4, 5) there instead. */
+/* Sweep configuration used on a level (see stokes_params.tile).  In the mixed
+ * forms, 3 on a level where the interior strips fit means the strip sweep
+ * (tensor-core GEMMs in the BF16 form, FP32 patch solves in the FP32 form) with
+ * its 14x14 SIMT ring; the autotuner may choose a SIMT shape (0..2, 6) there
+ * instead. */
 stokes_status stokes_level_tile(const stokes_hierarchy* h, int level, int* tile);
 
 /* Right-hand side of the eliminated system (Section 2.2 with the boundary data
@@ -195,9 +198,10 @@ stokes_status stokes_vanka_sweep(stokes_hierarchy* h, int level, const double* x
  * arithmetic the hierarchy's V-cycle uses (Algorithm 3 for Vanka; Algorithms 2
  * and 4 for the Braess-Sarazin and Schur-Uzawa smoothers): FP64 hierarchies as
  * stokes_vanka_sweep; STOKES_MIXED_FP32 rounds x and b to FP32, sweeps in FP32
- * and widens x_out; STOKES_MIXED_BF16 does the same with the interior patch
- * solves as BF16 tensor-core GEMMs on the tiles where they fit (the tile
- * configuration of the level, stokes_level_tile).  This is the sweep the
+ * (on the interior strips where the level's configuration is 3) and widens
+ * x_out; STOKES_MIXED_BF16 does the same with the interior patch solves as BF16
+ * tensor-core GEMMs on the strips (the tile configuration of the level,
+ * stokes_level_tile).  This is the sweep the
  * V-cycle applies, exposed so that it can be compared dof by dof with an FP64
  * sweep.  x == NULL means x = 0; x_out must not alias x or b.  Uses the
  * level's FP32 work vectors, so it must not overlap a V-cycle of the same
