@@ -25,9 +25,10 @@ __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __f
 
 // Forward transform of one 5-vector into the generalised eigenbasis S^T v
 // (three symmetric, two antisymmetric eigenvectors, each scaled to 1 on the
-// pair {0, 4}, so the first term needs no multiply: 4 add/sub + 8 FMA).
+// pair {0, 4}, so the first term needs no multiply: 4 add/sub + 8 FMA).  Also
+// compiled for the host (T = double), which transforms constant windows with it.
 template <typename T>
-__device__ __forceinline__ void fd_fwd(const FastDiagT<T>& f, T v0, T v1, T v2, T v3, T v4, T* c) {
+__host__ __device__ __forceinline__ void fd_fwd(const FastDiagT<T>& f, T v0, T v1, T v2, T v3, T v4, T* c) {
   const T e0 = v0 + v4, e1 = v1 + v3, o0 = v0 - v4, o1 = v1 - v3;
 #pragma unroll
   for (int k = 0; k < 3; ++k) c[k] = fma(f.se[3 + k], e1, fma(f.se[6 + k], v2, e0));
@@ -54,12 +55,19 @@ __device__ __forceinline__ void fd_inv(const FastDiagT<T>& f, const T* c, T* v) 
 
 // y = K^-1 r on an interior patch window (5 x 5, row-major [wj][wi]) by fast
 // diagonalisation: transform both axes, divide by l_a + l_b, transform back.
+// fd_rows is the first pass (along each window row), fd_finish the rest, which
+// takes the row-transformed window Tm (overwritten) -- a sweep whose patches share
+// their row transforms calls it alone.
 template <typename T>
-__device__ __forceinline__ void fd_solve(const FastDiagT<T>& f, const T* r, T* y) {
-  T Tm[25], U[25];
+__device__ __forceinline__ void fd_rows(const FastDiagT<T>& f, const T* r, T* Tm) {
 #pragma unroll
   for (int wj = 0; wj < 5; ++wj)
     fd_fwd(f, r[wj * 5], r[wj * 5 + 1], r[wj * 5 + 2], r[wj * 5 + 3], r[wj * 5 + 4], Tm + wj * 5);
+}
+
+template <typename T>
+__device__ __forceinline__ void fd_finish(const FastDiagT<T>& f, T* Tm, T* y) {
+  T U[25];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     T c[5];
@@ -78,6 +86,13 @@ __device__ __forceinline__ void fd_solve(const FastDiagT<T>& f, const T* r, T* y
   }
 #pragma unroll
   for (int wj = 0; wj < 5; ++wj) fd_inv(f, Tm + wj * 5, y + wj * 5);
+}
+
+template <typename T>
+__device__ __forceinline__ void fd_solve(const FastDiagT<T>& f, const T* r, T* y) {
+  T Tm[25];
+  fd_rows(f, r, Tm);
+  fd_finish(f, Tm, y);
 }
 
 }  // namespace fdm

@@ -45,6 +45,7 @@ namespace {
 using fdm::fd_fwd;
 using fdm::fd_inv;
 using fdm::fd_solve;
+using fdm::fd_finish;
 using fdm::operator+;
 using fdm::operator-;
 using fdm::operator*;
@@ -465,6 +466,16 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
 // smoother) forms x + W sum of the corrections.  Against the fused kernel this
 // trades 1.27x halo patch solves and 1.56x halo residuals for one write and one
 // read of delta: the better trade where the FP64 pipe, not HBM, is the bound.
+//
+// In a tile whose patches are all interior, the first pass of the fast
+// diagonalisation (the transform along each window row) is shared: patches
+// (qi, qj) and (qi, qj + 1) overlap in 3 node rows, so the transform of node row
+// J over the window columns of patch column qi serves 2 or 3 patches.  It is
+// computed once per (component, row, patch column) into shared memory, and each
+// patch applies its Schur coupling to it by linearity:
+//   T_rows(r_u - b^T q) = T_rows(r_u) - q T_rows(b^T),
+// with T_rows(b^T) a constant table (BRows) whose zero entries are known at
+// compile time (b^T rows are antisymmetric in x for u_x, symmetric for u_y).
 // ---------------------------------------------------------------------------
 template <int TX, int TY>
 struct VO {
@@ -474,21 +485,60 @@ struct VO {
   static constexpr int RW = 2 * CW, RH = 2 * CH;           // residual, Q2 nodes
   static constexpr int NPATCH = TX * TY;                   // own patches, origin i0
   static constexpr int SX = 2 * XW * XH, SP = PW * PH, SR = 2 * RW * RH, SRP = NPATCH;
-  static constexpr int TOTAL = SX + SP + SR + SRP;
+  static constexpr int TR = 2 * TY + 3;                    // node rows the patch windows use
+  static constexpr int ST = 2 * TR * 5 * TX;               // shared row transforms [c][J][mode][qi]
+  // layout: residual, pressure residual, then x, p and the edge tables, which the
+  // row transforms of an interior tile overwrite once the residual is formed
+  static constexpr int TAIL = (SX + SP + EDGE_TAB > ST) ? SX + SP + EDGE_TAB : ST;
+  static constexpr int SMEM = SR + SRP + TAIL;             // elements
 };
+
+// T_rows(b^T) of an interior patch: the row transforms of its coupling windows
+// (u_x window at 0, u_y window at 25; [wj * 5 + mode]), in the patch's units
+// (q = cb dp multiplies them)
+template <typename R>
+struct BRows {
+  R t[50];
+};
+
+// compile-time zero pattern of BRows: u_x rows wj = 1..3 are antisymmetric (crow in
+// x): only the antisymmetric modes 3, 4; u_y rows wj != 2 are symmetric (nrow in x):
+// only the symmetric modes 0..2
+__host__ __device__ constexpr bool brows_nonzero(int c, int wj, int k) {
+  return c == 0 ? (nrow(wj - 2) != 0.0 && k >= 3) : (crow(wj - 2) != 0.0 && k < 3);
+}
+
+template <typename R>
+BRows<R> coupling_row_transforms(const FastDiagT<R>& f) {
+  FastDiagT<double> fd{};
+  for (int k = 0; k < 9; ++k) fd.se[k] = static_cast<double>(f.se[k]);
+  for (int k = 0; k < 4; ++k) fd.so[k] = static_cast<double>(f.so[k]);
+  BRows<R> o{};
+  for (int c = 0; c < 2; ++c)
+    for (int wj = 0; wj < 5; ++wj) {
+      double v[5], cc[5];
+      for (int wi = 0; wi < 5; ++wi)
+        v[wi] = c == 0 ? crow(wi - 2) * nrow(wj - 2) : nrow(wi - 2) * crow(wj - 2);
+      fd_fwd<double>(fd, v[0], v[1], v[2], v[3], v[4], cc);
+      for (int k = 0; k < 5; ++k) o.t[c * 25 + wj * 5 + k] = brows_nonzero(c, wj, k) ? static_cast<R>(cc[k]) : R(0);
+    }
+  return o;
+}
 
 template <typename R, int TX, int TY, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __restrict__ cd,
-                                                  const FastDiagT<R> fdg, const R* __restrict__ x,
-                                                  const R* __restrict__ b, R* __restrict__ delta, int P) {
+                                                  const FastDiagT<R> fdg, const BRows<R> xb,
+                                                  const R* __restrict__ x, const R* __restrict__ b,
+                                                  R* __restrict__ delta, int P) {
   pdl_begin();
   using T = VO<TX, TY>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sx = reinterpret_cast<R*>(smem_raw);
-  R* sp = sx + T::SX;
-  R* sr = sp + T::SP;
+  R* sr = reinterpret_cast<R*>(smem_raw);
   R* srp = sr + T::SR;
-  R* se = srp + T::SRP;
+  R* sx = srp + T::SRP;
+  R* sp = sx + T::SX;
+  R* se = sp + T::SP;
+  R* sT = sx;   // interior tiles: the shared row transforms, once x and p are dead
   const int n = L.n, nq = L.nq, np = L.np;
   const long long nv = L.nv;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
@@ -561,6 +611,23 @@ __global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __r
   }
   __syncthreads();
 
+  // interior tile: the row transforms of every (component, node row, patch column),
+  // over x and p, which no thread reads any more
+  const bool shared_rows = !edge_tile;
+  if (shared_rows) {
+    for (int t = tid; t < T::ST / 5; t += NT) {
+      const int qi = t % TX, rest = t / TX;
+      const int J = rest % T::TR, c = rest / T::TR;
+      const R* src = sr + c * T::RW * T::RH + J * T::RW + 2 * qi;
+      R cc[5];
+      fd_fwd<R>(fdg, src[0], src[1], src[2], src[3], src[4], cc);
+      R* dst = sT + (c * T::TR + J) * 5 * TX + qi;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) dst[k * TX] = cc[k];
+    }
+    __syncthreads();
+  }
+
   for (int t0 = 0; t0 < T::NPATCH; t0 += NT) {
     const int t = t0 + tid;
     const int qj = t / TX, qi = t - qj * TX;
@@ -582,20 +649,21 @@ __global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __r
     const R dp = schur_dp<R>(warp_interior, L, C, ru, srp[t]);
     const int p = pj * np + pi;
     R* D = delta + p;
-    if (warp_interior) {
+    if (warp_interior && shared_rows) {
+      // K^-1 (r_u - b^T q) from the shared row transforms of r_u
       const R q = cb * dp;
 #pragma unroll
-      for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int w = 0; w < 25; ++w) {
-          const int dI = w % 5 - 2, dJ = w / 5 - 2;
-          const R bw = R(c == 0 ? crow(dI) * nrow(dJ) : nrow(dI) * crow(dJ));
-          if (bw != R(0)) ru[c * 25 + w] = fma(-bw, q, ru[c * 25 + w]);
-        }
-#pragma unroll
       for (int c = 0; c < 2; ++c) {
-        R y[25];
-        fd_solve<R>(fdg, ru + c * 25, y);
+        R Tm[25], y[25];
+        const R* src = sT + (c * T::TR + 2 * qj) * 5 * TX + qi;
+#pragma unroll
+        for (int wj = 0; wj < 5; ++wj)
+#pragma unroll
+          for (int k = 0; k < 5; ++k) {
+            const R v = src[(wj * 5 + k) * TX];
+            Tm[wj * 5 + k] = brows_nonzero(c, wj, k) ? fma(-q, xb.t[c * 25 + wj * 5 + k], v) : v;
+          }
+        fd_finish<R>(fdg, Tm, y);
 #pragma unroll
         for (int o = 0; o < 25; ++o) D[static_cast<long long>(c * 25 + o) * P] = y[o];
       }
@@ -841,7 +909,7 @@ void launch_tail(const TailOp* ops, int nops, const TailLevel* levels, const dou
 }
 
 cudaError_t vanka_prepare() {
-  const int smem_own = static_cast<int>((VO<16, 16>::TOTAL + EDGE_TAB) * sizeof(double));
+  const int smem_own = static_cast<int>(VO<16, 16>::SMEM * sizeof(double));
   cudaError_t e = cudaFuncSetAttribute(k_vanka_own<double, 16, 16, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        smem_own);
   if (e == cudaSuccess)
@@ -878,11 +946,12 @@ void launch_vanka_split(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, 
   count_launches(1);
   const int P = patch_stride(L);
   dim3 grid((L.np + 15) / 16, (L.np + 15) / 16);
-  constexpr size_t smem = (VO<16, 16>::TOTAL + EDGE_TAB) * sizeof(R);
+  constexpr size_t smem = VO<16, 16>::SMEM * sizeof(R);
+  const BRows<R> xb = coupling_row_transforms<R>(fd);
   if (two_per_sm)
-    launch_pdl(k_vanka_own<R, 16, 16, 256, 2>, dim3(grid), dim3(256), smem, s, L, cd, fd, x, b, delta, P);
+    launch_pdl(k_vanka_own<R, 16, 16, 256, 2>, dim3(grid), dim3(256), smem, s, L, cd, fd, xb, x, b, delta, P);
   else
-    launch_pdl(k_vanka_own<R, 16, 16, 256, 1>, dim3(grid), dim3(256), smem, s, L, cd, fd, x, b, delta, P);
+    launch_pdl(k_vanka_own<R, 16, 16, 256, 1>, dim3(grid), dim3(256), smem, s, L, cd, fd, xb, x, b, delta, P);
   launch_patch_update<R>(L, P, delta, x, xo, omega, s);
 }
 template void launch_vanka_split<double>(const LevelDev&, const double*, const FastDiag&, const double*,

@@ -120,6 +120,38 @@ def test_fullsize_vanka_sweep(big):
     assert outside_norm(out, NS, NBIG, OFF) == 0.0
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+def test_fullsize_mixed_sweep_within_rounding_bound(prec):
+    """One sweep of the mixed FP32 (prec 1) and BF16 (prec 2) forms on the finest 2048^2
+    level, in the bench's configuration: the autotuned strip sweep on the interior, where
+    the window sits (vertex offset 1400, inside the strips' tiles 1..144).  Every dof of the
+    window is within the rounding bound of oracle/rounding.py, evaluated on the 32^2 problem
+    for the scaled inputs and mapped back by D^-1 (the scaling is by powers of two, so the
+    rounding errors scale with it exactly, barring underflow); outside the window the output
+    is zero.  In the BF16 form the error exceeds the FP32-only bound somewhere in the window:
+    the tensor cores produced it."""
+    import paper_2401_06277_gb300 as pkg
+    from oracle import rounding as RB
+    from paper_2401_06277_gb300 import stokes
+    H = pkg.Hierarchy(NBIG, rtol=1e-8, restart=30, prec=prec)
+    assert stokes.stokes_level_tile(H.handle, H.levels - 1) == 3, "the tuner did not pick the strip sweep"
+    lv = O.build_level(NS, 1.0)
+    xs, bs = pattern(NS, 6 + prec), pattern(NS, 8 + prec)
+    xsc, bsc = pscale(xs, NS, S), pscale(bs, NS, 1 / S)
+    ref = pscale(O.vanka_sweep(lv, xsc, bsc, 0.7), NS, 1 / S)
+    out = cpu(H.relax(gpu(embed(xs, NS, NBIG, OFF)), gpu(embed(bs, NS, NBIG, OFF))))
+    H.close()
+    allbf = np.ones_like(bs, dtype=bool) if prec == 2 else None
+    bound = pscale(RB.sweep_error_bound(lv, xsc, bsc, 0.7, bf16_dofs=allbf), NS, 1 / S)
+    got = window(out, NS, NBIG, OFF)
+    q = np.max(np.abs(got - ref) / np.maximum(bound, 1e-300))
+    assert q <= 1.0, q
+    assert outside_norm(out, NS, NBIG, OFF) == 0.0
+    if prec == 2:
+        fp32 = pscale(RB.sweep_error_bound(lv, xsc, bsc, 0.7), NS, 1 / S)
+        assert np.max(np.abs(got - ref) / np.maximum(fp32, 1e-300)) > 1.0
+
+
 def test_fullsize_transfers(big):
     """Restriction and prolongation between the two finest levels (2048 -> 1024)."""
     from paper_2401_06277_gb300 import stokes

@@ -22,15 +22,17 @@ def pkg():
     return p
 
 
-@pytest.mark.parametrize("prec,smoother,tail_n", [(0, 0, 0), (1, 0, 0), (2, 0, 0), (1, 2, 0), (0, 1, 0),
-                                                  (1, 0, 128), (2, 0, 128)])
-@pytest.mark.parametrize("n", [16, 64])
-def test_graph_replay_equals_eager_vcycle(pkg, n, prec, smoother, tail_n):
-    """tail_n = 128: the coarse levels as the persistent cooperative launch, captured too."""
+@pytest.mark.parametrize("prec,smoother,tail_n,tile", [(0, 0, 0, -1), (1, 0, 0, -1), (2, 0, 0, -1), (1, 2, 0, -1),
+                                                       (0, 1, 0, -1), (1, 0, 128, -1), (2, 0, 128, -1),
+                                                       (1, 0, 0, 3), (2, 0, 0, 3)])
+@pytest.mark.parametrize("n", [16, 64, 128])
+def test_graph_replay_equals_eager_vcycle(pkg, n, prec, smoother, tail_n, tile):
+    """tail_n = 128: the coarse levels as the persistent cooperative launch, captured too;
+    tile = 3 in the mixed forms: the strip sweeps (with their ring fork) wherever they fit."""
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
-        H = pkg.Hierarchy(n, prec=prec, smoother=smoother, tail_n=tail_n)
+        H = pkg.Hierarchy(n, prec=prec, smoother=smoother, tail_n=tail_n, tile=tile)
         b = torch.from_numpy(si.random_vector(n, 31)).cuda()
         z_eager = torch.empty_like(b)
         z_graph = torch.full_like(b, float("nan"))
