@@ -873,9 +873,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   h->stream = static_cast<cudaStream_t>(stream);
   h->m = prm.restart;
   h->fd = sv::interior_fast_diag(viscosity);
-  for (int k = 0; k < 9; ++k) h->fdf.se[k] = static_cast<float>(h->fd.se[k]);
-  for (int k = 0; k < 4; ++k) h->fdf.so[k] = static_cast<float>(h->fd.so[k]);
-  for (int k = 0; k < 25; ++k) h->fdf.dinv[k] = static_cast<float>(h->fd.dinv[k]);
+  h->fdf = sv::fd_cast<float>(h->fd, [](double v) { return static_cast<float>(v); });
   cudaError_t e = sv::vanka_prepare();
   if (e == cudaSuccess) e = sv::simple_prepare();
   if (e == cudaSuccess) {

@@ -78,13 +78,32 @@ __host__ __device__ constexpr int axis_free_mask(int a) {
 // se[m*3+k]: symmetric eigenvector k at reduced index m (entries 0/4, 1/3, 2);
 // so[m*2+k]: antisymmetric eigenvector k at reduced index m (entries 0/-4, 1/-3);
 // dinv[a*5+b] = (90/nu) / (l_a + l_b), eigenvalues ordered sym 0..2, anti 0..1.
+// The solve's column pass (forward transform along y, division by l_a + l_b, inverse
+// transform along y, for window column b) is one operator per column that keeps the
+// parity split: gs[b*9 + m*3 + j] maps the symmetric inputs (v0 + v4, v1 + v3, v2)
+// to the symmetric outputs m, ga[b*4 + m*2 + j] the antisymmetric (v0 - v4, v1 - v3):
+//   gs = sum over sym modes a of se[m][a] dinv[a][b] se[j][a], ga likewise with so.
 template <typename T>
 struct FastDiagT {
   T se[9];
   T so[4];
   T dinv[25];
+  T gs[45];
+  T ga[20];
 };
 using FastDiag = FastDiagT<double>;
+
+// A table in another arithmetic type, entry by entry (conv: S -> D).
+template <typename D, typename S, typename F>
+inline FastDiagT<D> fd_cast(const FastDiagT<S>& s, F conv) {
+  FastDiagT<D> d;
+  for (int k = 0; k < 9; ++k) d.se[k] = conv(s.se[k]);
+  for (int k = 0; k < 4; ++k) d.so[k] = conv(s.so[k]);
+  for (int k = 0; k < 25; ++k) d.dinv[k] = conv(s.dinv[k]);
+  for (int k = 0; k < 45; ++k) d.gs[k] = conv(s.gs[k]);
+  for (int k = 0; k < 20; ++k) d.ga[k] = conv(s.ga[k]);
+  return d;
+}
 
 // Braess-Sarazin / Schur-Uzawa parameters (Sections 3.1, 3.3; see stokes_params).
 constexpr int TC_WAIT_LIMIT = 1 << 22;   // polls of an mbarrier before a tensor-core sweep's wait gives up

@@ -301,6 +301,21 @@ FastDiag interior_fast_diag(double nu) {
   double lam[5] = {ls[0], ls[1], ls[2], lo[0], lo[1]};
   for (int a = 0; a < 5; ++a)
     for (int b = 0; b < 5; ++b) f.dinv[a * 5 + b] = (90.0 / nu) * (g[a] * g[a]) * (g[b] * g[b]) / (lam[a] + lam[b]);
+  // the fused column operators (see FastDiagT)
+  for (int b = 0; b < 5; ++b) {
+    for (int m = 0; m < 3; ++m)
+      for (int j = 0; j < 3; ++j) {
+        double s = 0.0;
+        for (int a = 0; a < 3; ++a) s += f.se[m * 3 + a] * f.dinv[a * 5 + b] * f.se[j * 3 + a];
+        f.gs[b * 9 + m * 3 + j] = s;
+      }
+    for (int m = 0; m < 2; ++m)
+      for (int j = 0; j < 2; ++j) {
+        double s = 0.0;
+        for (int a = 0; a < 2; ++a) s += f.so[m * 2 + a] * f.dinv[(3 + a) * 5 + b] * f.so[j * 2 + a];
+        f.ga[b * 4 + m * 2 + j] = s;
+      }
+  }
   return f;
 }
 

@@ -33,6 +33,9 @@
 // the FP64 pipe is the bound.
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <utility>
+
 #include "sv_fastdiag.cuh"
 #include "sv_internal.h"
 #include "sv_level_ops.cuh"
@@ -493,20 +496,30 @@ struct VO {
   static constexpr int SMEM = SR + SRP + TAIL;             // elements
 };
 
-// T_rows(b^T) of an interior patch: the row transforms of its coupling windows
-// (u_x window at 0, u_y window at 25; [wj * 5 + mode]), in the patch's units
-// (q = cb dp multiplies them)
+// Constant tables of an interior patch in the row-transformed basis (u_x window
+// at 0, u_y window at 25; [wj * 5 + mode]):
+//   t:  T_rows(b^T), the row transforms of its coupling windows, in the patch's
+//       units (q = cb dp multiplies them);
+//   zh: the unit Schur vector z_u seen through the row transform, zh = M^-T z_u
+//       per row (M the 5 x 5 forward transform), so that z_u . r_u = zh . T_rows(r_u):
+//       the Schur step reads the shared row transforms instead of r_u and z.
 template <typename R>
 struct BRows {
   R t[50];
+  R zh[50];
 };
 
-// compile-time zero pattern of BRows: u_x rows wj = 1..3 are antisymmetric (crow in
-// x): only the antisymmetric modes 3, 4; u_y rows wj != 2 are symmetric (nrow in x):
-// only the symmetric modes 0..2
+// Compile-time zero patterns.  b^T: u_x rows wj = 1..3 are antisymmetric in x
+// (crow), so only the antisymmetric modes 3, 4 survive the row transform; u_y rows
+// wj != 2 are symmetric in x (nrow): only the symmetric modes 0..2.  z_u = K^-1 b^T
+// inherits the parities (K commutes with the reflection x -> -x): zh keeps modes 3, 4
+// of u_x and 0..2 of u_y in every row.
 __host__ __device__ constexpr bool brows_nonzero(int c, int wj, int k) {
   return c == 0 ? (nrow(wj - 2) != 0.0 && k >= 3) : (crow(wj - 2) != 0.0 && k < 3);
 }
+__host__ __device__ constexpr bool zh_nonzero(int c, int k) { return c == 0 ? k >= 3 : k < 3; }
+
+double g_zu_host[50];   // z_u as uploaded by set_interior_unit_z
 
 template <typename R>
 BRows<R> coupling_row_transforms(const FastDiagT<R>& f) {
@@ -521,6 +534,36 @@ BRows<R> coupling_row_transforms(const FastDiagT<R>& f) {
         v[wi] = c == 0 ? crow(wi - 2) * nrow(wj - 2) : nrow(wi - 2) * crow(wj - 2);
       fd_fwd<double>(fd, v[0], v[1], v[2], v[3], v[4], cc);
       for (int k = 0; k < 5; ++k) o.t[c * 25 + wj * 5 + k] = brows_nonzero(c, wj, k) ? static_cast<R>(cc[k]) : R(0);
+    }
+  // M (row k = the transform's weights of v_0..v_4), then M^T zh_row = z_row by
+  // Gaussian elimination with partial pivoting, row by row of each window
+  double M[5][5];
+  for (int k = 0; k < 5; ++k) {
+    double e[5] = {0, 0, 0, 0, 0}, cc[5];
+    e[k] = 1.0;
+    fd_fwd<double>(fd, e[0], e[1], e[2], e[3], e[4], cc);   // column k of M
+    for (int i = 0; i < 5; ++i) M[i][k] = cc[i];
+  }
+  for (int c = 0; c < 2; ++c)
+    for (int wj = 0; wj < 5; ++wj) {
+      double a[5][6];
+      for (int i = 0; i < 5; ++i) {
+        for (int j = 0; j < 5; ++j) a[i][j] = M[j][i];   // M^T
+        a[i][5] = g_zu_host[c * 25 + wj * 5 + i];
+      }
+      for (int col = 0; col < 5; ++col) {
+        int piv = col;
+        for (int i = col + 1; i < 5; ++i)
+          if (std::fabs(a[i][col]) > std::fabs(a[piv][col])) piv = i;
+        for (int j = 0; j < 6; ++j) std::swap(a[col][j], a[piv][j]);
+        for (int i = 0; i < 5; ++i) {
+          if (i == col) continue;
+          const double m = a[i][col] / a[col][col];
+          for (int j = col; j < 6; ++j) a[i][j] -= m * a[col][j];
+        }
+      }
+      for (int k = 0; k < 5; ++k)
+        o.zh[c * 25 + wj * 5 + k] = zh_nonzero(c, k) ? static_cast<R>(a[k][5] / a[k][k]) : R(0);
     }
   return o;
 }
@@ -638,18 +681,23 @@ __global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __r
     const bool warp_interior = __all_sync(0xffffffffu, cls == INTERIOR_CLASS);   // as in vanka_tile
     if (!valid) continue;
     const R* C = cd + cls * CD_STRIDE;
-    R ru[50];
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-      for (int wj = 0; wj < 5; ++wj)
-#pragma unroll
-        for (int wi = 0; wi < 5; ++wi)
-          ru[c * 25 + wj * 5 + wi] = sr[c * T::RW * T::RH + (2 * qj + wj) * T::RW + 2 * qi + wi];
-    const R dp = schur_dp<R>(warp_interior, L, C, ru, srp[t]);
     const int p = pj * np + pi;
     R* D = delta + p;
+    R dp;
     if (warp_interior && shared_rows) {
+      // Schur step from the shared row transforms: z . r_u = zs (zh . T_rows(r_u)),
+      // the two components summed separately
+      R zr[2] = {R(0), R(0)};
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const R* src = sT + (c * T::TR + 2 * qj) * 5 * TX + qi;
+#pragma unroll
+        for (int wj = 0; wj < 5; ++wj)
+#pragma unroll
+          for (int k = 0; k < 5; ++k)
+            if (zh_nonzero(c, k)) zr[c] = fma(xb.zh[c * 25 + wj * 5 + k], src[(wj * 5 + k) * TX], zr[c]);
+      }
+      dp = (level_zs<R>(L) * (zr[0] + zr[1]) - srp[t]) * level_zsinv<R>(L);
       // K^-1 (r_u - b^T q) from the shared row transforms of r_u
       const R q = cb * dp;
 #pragma unroll
@@ -668,6 +716,15 @@ __global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __r
         for (int o = 0; o < 25; ++o) D[static_cast<long long>(c * 25 + o) * P] = y[o];
       }
     } else {
+      R ru[50];
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int wj = 0; wj < 5; ++wj)
+#pragma unroll
+          for (int wi = 0; wi < 5; ++wi)
+            ru[c * 25 + wj * 5 + wi] = sr[c * T::RW * T::RH + (2 * qj + wj) * T::RW + 2 * qi + wi];
+      dp = schur_dp<R>(warp_interior, L, C, ru, srp[t]);
       const int fx = axis_free_mask(ax), fy = axis_free_mask(ay);
       int fmask = 0;
 #pragma unroll
@@ -697,12 +754,8 @@ void launch_t(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x
     grid = dim3(gx * gy - w * w, 1);
   }
   FastDiagT<float2> fp{};   // (v, v) pairs of the FP32 table for the packed interior solves
-  if constexpr (sizeof(R) == 4) {
-    for (int k = 0; k < 9; ++k) fp.se[k] = make_float2(static_cast<float>(fd.se[k]), static_cast<float>(fd.se[k]));
-    for (int k = 0; k < 4; ++k) fp.so[k] = make_float2(static_cast<float>(fd.so[k]), static_cast<float>(fd.so[k]));
-    for (int k = 0; k < 25; ++k)
-      fp.dinv[k] = make_float2(static_cast<float>(fd.dinv[k]), static_cast<float>(fd.dinv[k]));
-  }
+  if constexpr (sizeof(R) == 4)
+    fp = fd_cast<float2>(fd, [](R v) { return make_float2(static_cast<float>(v), static_cast<float>(v)); });
   launch_pdl(k_vanka<R, TX, TY, NT>, dim3(grid), dim3(NT), (VT<TX, TY>::TOTAL + EDGE_TAB) * sizeof(R), s, L, cd, fd, fp, x, b, xo,
                                                                                     omega, skip_lo, skip_hi);
 }
@@ -854,6 +907,7 @@ cudaError_t prepare_all() {
 }  // namespace
 
 cudaError_t set_interior_unit_z(const double* z50) {
+  for (int k = 0; k < 50; ++k) g_zu_host[k] = z50[k];
   float zf[50];
   for (int k = 0; k < 50; ++k) zf[k] = static_cast<float>(z50[k]);
   cudaError_t e = cudaMemcpyToSymbol(c_zu, z50, 50 * sizeof(double));
@@ -886,9 +940,7 @@ void launch_tail(const TailOp* ops, int nops, const TailLevel* levels, const dou
   A.G = G;
   A.N0 = N0;
   A.fdg = fd;
-  for (int k = 0; k < 9; ++k) A.fdp.se[k] = make_float2(fd.se[k], fd.se[k]);
-  for (int k = 0; k < 4; ++k) A.fdp.so[k] = make_float2(fd.so[k], fd.so[k]);
-  for (int k = 0; k < 25; ++k) A.fdp.dinv[k] = make_float2(fd.dinv[k], fd.dinv[k]);
+  A.fdp = fd_cast<float2>(fd, [](float v) { return make_float2(v, v); });
   A.omega = static_cast<float>(omega);
   A.bar = bar;
   A.err = err;

@@ -816,10 +816,8 @@ void launch_vanka_strip_f32(const LevelDev& L, const FastDiagT<float>& fd, const
   const int cnt = hi - lo + 1;
   if (cnt < 2 || (cnt & 1)) return;
   count_launches(1);
-  FastDiagT<float2> fp{};   // (v, v) pairs: both velocity components in one packed pass
-  for (int k = 0; k < 9; ++k) fp.se[k] = make_float2(fd.se[k], fd.se[k]);
-  for (int k = 0; k < 4; ++k) fp.so[k] = make_float2(fd.so[k], fd.so[k]);
-  for (int k = 0; k < 25; ++k) fp.dinv[k] = make_float2(fd.dinv[k], fd.dinv[k]);
+  // (v, v) pairs: both velocity components in one packed pass
+  const FastDiagT<float2> fp = fd_cast<float2>(fd, [](float v) { return make_float2(v, v); });
   int seg = GR;
   const dim3 grid = strip_grid(cnt, &seg, false);
   launch_pdl(k_vanka_strip<false>, grid, dim3(NT), SL<false>::BYTES, s, L, static_cast<const uint4*>(nullptr), fp,
