@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -935,9 +936,9 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
     }
     // patch corrections of the per-patch-inverse and the split sweeps (finest-level size)
     if (e == cudaSuccess && prm.prec == STOKES_FP64 && k + 1 == sizes.size())
-      e = dalloc(&h->delta, sv::patch_delta_doubles(L.d));
+      e = dalloc(&h->delta, std::max(sv::patch_delta_doubles(L.d), sv::split_delta_doubles(L.d)));
     if (e == cudaSuccess && prm.prec != STOKES_FP64 && k + 1 == sizes.size())
-      e = dalloc(&h->deltaf, sv::patch_delta_doubles(L.d));
+      e = dalloc(&h->deltaf, std::max(sv::patch_delta_doubles(L.d), sv::split_delta_doubles(L.d)));
     if (e == cudaSuccess && (prm.smoother == STOKES_SMOOTHER_BRAESS_SARAZIN ||
                              prm.smoother == STOKES_SMOOTHER_SCHUR_UZAWA) && k + 1 == sizes.size()) {
       const size_t el = sv::bs_scratch_elems(L.d) * (prm.prec == STOKES_FP64 ? sizeof(double) : sizeof(float));

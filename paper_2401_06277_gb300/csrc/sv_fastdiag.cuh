@@ -65,12 +65,12 @@ __device__ __forceinline__ void fd_rows(const FastDiagT<T>& f, const T* r, T* Tm
     fd_fwd(f, r[wj * 5], r[wj * 5 + 1], r[wj * 5 + 2], r[wj * 5 + 3], r[wj * 5 + 4], Tm + wj * 5);
 }
 
-// The column pass -- forward transform along y, division by l_a + l_b, inverse
-// transform along y -- is one operator per window column that keeps the parity
-// split (f.gs, f.ga): 4 add/sub, a 3 x 3 and a 2 x 2 product, 4 add/sub (21
-// operations instead of 12 + 5 + 15).
+// The column pass (fd_cols) -- forward transform along y, division by l_a + l_b,
+// inverse transform along y -- is one operator per window column that keeps the
+// parity split (f.gs, f.ga): 4 add/sub, a 3 x 3 and a 2 x 2 product, 4 add/sub (21
+// operations instead of 12 + 5 + 15).  Tm holds row coefficients before and after.
 template <typename T>
-__device__ __forceinline__ void fd_finish(const FastDiagT<T>& f, T* Tm, T* y) {
+__device__ __forceinline__ void fd_cols(const FastDiagT<T>& f, T* Tm) {
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     const T v0 = Tm[k], v1 = Tm[5 + k], v2 = Tm[10 + k], v3 = Tm[15 + k], v4 = Tm[20 + k];
@@ -87,6 +87,12 @@ __device__ __forceinline__ void fd_finish(const FastDiagT<T>& f, T* Tm, T* y) {
     Tm[15 + k] = E[1] - O1;
     Tm[10 + k] = E[2];
   }
+}
+
+// fd_cols, then the inverse transform along each window row
+template <typename T>
+__device__ __forceinline__ void fd_finish(const FastDiagT<T>& f, T* Tm, T* y) {
+  fd_cols(f, Tm);
 #pragma unroll
   for (int wj = 0; wj < 5; ++wj) fd_inv(f, Tm + wj * 5, y + wj * 5);
 }

@@ -388,6 +388,9 @@ bool bt_coarse_inverses(int n, double nu, std::vector<double>& GL, std::vector<d
 int patch_stride(const LevelDev& L);                 // patch count rounded up to 32
 size_t patch_inverse_doubles(const LevelDev& L);     // 51 * 51 * stride
 size_t patch_delta_doubles(const LevelDev& L);       // 51 * stride
+// scratch of the split sweep (launch_vanka_split): per-patch corrections of its edge
+// tiles, the column sums of every tile and the pressure corrections
+size_t split_delta_doubles(const LevelDev& L);
 cudaError_t simple_prepare();
 void launch_patch_inverse(const LevelDev& L, double* inv, cudaStream_t s);
 // xo = x + sum_i V_i^T W_i A_i^-1 V_i (b - A x) with the stored inverses; x may

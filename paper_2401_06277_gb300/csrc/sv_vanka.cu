@@ -49,6 +49,7 @@ using fdm::fd_fwd;
 using fdm::fd_inv;
 using fdm::fd_solve;
 using fdm::fd_finish;
+using fdm::fd_cols;
 using fdm::operator+;
 using fdm::operator-;
 using fdm::operator*;
@@ -493,8 +494,33 @@ struct VO {
   // layout: residual, pressure residual, then x, p and the edge tables, which the
   // row transforms of an interior tile overwrite once the residual is formed
   static constexpr int TAIL = (SX + SP + EDGE_TAB > ST) ? SX + SP + EDGE_TAB : ST;
-  static constexpr int SMEM = SR + SRP + TAIL;             // elements
+  static constexpr int SA = TR * 5 * TX;                   // summed row coefficients [J][mode][qi]
+  static constexpr int SMEM = SR + SRP + TAIL + SA;        // elements
 };
+
+// Output of the split sweep: per (component, tile row ty, node row lr of the tile's
+// windows, window column w, patch column pi) the sum of the corrections of the
+// tile's patches in patch column pi at node (2 pi - 2 + w, 32 ty - 2 + lr); the
+// update adds the 2 or 3 patch columns and the 1 or 2 tile rows around a node.
+// delta holds, in this order: 51 x P per-patch corrections (scratch of the edge
+// tiles), the column sums [c][ty][lr][w][pi] with pi pitch ncol, then the
+// pressure corrections [vertex].
+struct SplitOut {
+  int P;      // per-patch stride of the scratch
+  int ncol;   // patch-column pitch of the column sums (tiles x TX)
+  int nty;    // tile rows
+  long long col_off, dp_off;
+};
+inline SplitOut split_out(const LevelDev& L) {
+  SplitOut o;
+  o.P = patch_stride(L);
+  o.ncol = ((L.np + 15) / 16) * 16;
+  o.nty = (L.np + 15) / 16;
+  o.col_off = 51LL * o.P;
+  o.dp_off = o.col_off + 2LL * o.nty * VO<16, 16>::TR * 5 * o.ncol;
+  return o;
+}
+
 
 // Constant tables of an interior patch in the row-transformed basis (u_x window
 // at 0, u_y window at 25; [wj * 5 + mode]):
@@ -572,7 +598,7 @@ template <typename R, int TX, int TY, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __restrict__ cd,
                                                   const FastDiagT<R> fdg, const BRows<R> xb,
                                                   const R* __restrict__ x, const R* __restrict__ b,
-                                                  R* __restrict__ delta, int P) {
+                                                  R* delta, const SplitOut so) {
   pdl_begin();
   using T = VO<TX, TY>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -582,12 +608,21 @@ __global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __r
   R* sp = sx + T::SX;
   R* se = sp + T::SP;
   R* sT = sx;   // interior tiles: the shared row transforms, once x and p are dead
+  R* sA = se + (T::TAIL - T::SX - T::SP);   // summed row coefficients of one component
   const int n = L.n, nq = L.nq, np = L.np;
   const long long nv = L.nv;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int tid = threadIdx.x;
   const int XI0 = 2 * i0 - 4, XJ0 = 2 * j0 - 4;
   const int RI0 = 2 * i0 - 2, RJ0 = 2 * j0 - 2;
+  const int P = so.P;
+  R* colsum = delta + so.col_off;
+  R* dpo = delta + so.dp_off;
+  // column sum (c, lr, w) of patch column i0 + qi
+  auto col_at = [&](int c, int lr, int w, int qi) -> R& {
+    return colsum[((static_cast<long long>(c) * so.nty + blockIdx.y) * T::TR + lr) * 5 * so.ncol +
+                  static_cast<long long>(w) * so.ncol + i0 + qi];
+  };
 
   const bool edge_tile = (i0 <= 1) || (j0 <= 1) || (i0 + TX - 1 >= n - 1) || (j0 + TY - 1 >= n - 1);
   if (edge_tile)
@@ -671,51 +706,99 @@ __global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __r
     __syncthreads();
   }
 
-  for (int t0 = 0; t0 < T::NPATCH; t0 += NT) {
-    const int t = t0 + tid;
+  static_assert(T::NPATCH == NT, "one patch per thread");
+  if (shared_rows) {
+    // every patch of the tile is interior and valid: thread t owns patch (qi, qj)
+    const int qj = tid / TX, qi = tid - qj * TX;
+    const int pi = i0 + qi, pj = j0 + qj;
+    // Schur step from the shared row transforms: z . r_u = zs (zh . T_rows(r_u)),
+    // the two components summed separately
+    R zr[2] = {R(0), R(0)};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const R* src = sT + (c * T::TR + 2 * qj) * 5 * TX + qi;
+#pragma unroll
+      for (int wj = 0; wj < 5; ++wj)
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+          if (zh_nonzero(c, k)) zr[c] = fma(xb.zh[c * 25 + wj * 5 + k], src[(wj * 5 + k) * TX], zr[c]);
+    }
+    const R dp = (level_zs<R>(L) * (zr[0] + zr[1]) - srp[tid]) * level_zsinv<R>(L);
+    dpo[static_cast<long long>(pj) * np + pi] = dp;
+    const R q = cb * dp;
+    // first patch row (in the order of the phases below) whose window holds tile row lr
+    auto first_phase = [&](int lr) {
+      const int lo = max(0, (lr - 3) / 2), hi = min(TY - 1, lr / 2);
+      int f = 3;
+      for (int qq = lo; qq <= hi; ++qq) f = min(f, qq % 3);
+      return f;
+    };
+#pragma unroll 1
+    for (int c = 0; c < 2; ++c) {
+      // K^-1 (r_u - b^T q) up to its last pass: row transforms minus the coupling,
+      // then the column pass
+      R Tm[25];
+      const R* src = sT + (c * T::TR + 2 * qj) * 5 * TX + qi;
+#pragma unroll
+      for (int wj = 0; wj < 5; ++wj)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+          const R v = src[(wj * 5 + k) * TX];
+          Tm[wj * 5 + k] = brows_nonzero(c, wj, k) ? fma(-q, xb.t[c * 25 + wj * 5 + k], v) : v;
+        }
+      fd_cols<R>(fdg, Tm);
+      // sum the row coefficients of the patches sharing a node row: patch rows qj of
+      // one residue mod 3 have disjoint windows, so three phases add without races,
+      // in a fixed order; the first contributor of a row stores
+#pragma unroll 1
+      for (int ph = 0; ph < 3; ++ph) {
+        if (qj % 3 == ph) {
+#pragma unroll
+          for (int wj = 0; wj < 5; ++wj) {
+            const int lr = 2 * qj + wj;
+            R* dst = sA + lr * 5 * TX + qi;
+            if (first_phase(lr) == ph) {
+#pragma unroll
+              for (int k = 0; k < 5; ++k) dst[k * TX] = Tm[wj * 5 + k];
+            } else {
+#pragma unroll
+              for (int k = 0; k < 5; ++k) dst[k * TX] += Tm[wj * 5 + k];
+            }
+          }
+        }
+        __syncthreads();
+      }
+      // the last pass once per (node row, patch column): the inverse row transform of
+      // the summed coefficients is the sum of the patches' corrections there
+      for (int it = tid; it < T::TR * TX; it += NT) {
+        const int lr = it / TX, q2 = it - lr * TX;
+        R cc[5], v[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) cc[k] = sA[(lr * 5 + k) * TX + q2];
+        fd_inv<R>(fdg, cc, v);
+        if (i0 + q2 <= n) {
+#pragma unroll
+          for (int w = 0; w < 5; ++w) col_at(c, lr, w, q2) = v[w];
+        }
+      }
+      __syncthreads();
+    }
+    return;
+  }
+
+  // edge tile: per-patch corrections into the scratch, then their column sums
+  {
+    const int t = tid;
     const int qj = t / TX, qi = t - qj * TX;
     const int pi = i0 + qi, pj = j0 + qj;
-    const bool valid = t < T::NPATCH && pi <= n && pj <= n;
+    const bool valid = pi <= n && pj <= n;
     const int ax = valid ? axis_class(pi, n) : 2, ay = valid ? axis_class(pj, n) : 2;
     const int cls = 5 * ay + ax;
     const bool warp_interior = __all_sync(0xffffffffu, cls == INTERIOR_CLASS);   // as in vanka_tile
-    if (!valid) continue;
-    const R* C = cd + cls * CD_STRIDE;
-    const int p = pj * np + pi;
-    R* D = delta + p;
-    R dp;
-    if (warp_interior && shared_rows) {
-      // Schur step from the shared row transforms: z . r_u = zs (zh . T_rows(r_u)),
-      // the two components summed separately
-      R zr[2] = {R(0), R(0)};
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const R* src = sT + (c * T::TR + 2 * qj) * 5 * TX + qi;
-#pragma unroll
-        for (int wj = 0; wj < 5; ++wj)
-#pragma unroll
-          for (int k = 0; k < 5; ++k)
-            if (zh_nonzero(c, k)) zr[c] = fma(xb.zh[c * 25 + wj * 5 + k], src[(wj * 5 + k) * TX], zr[c]);
-      }
-      dp = (level_zs<R>(L) * (zr[0] + zr[1]) - srp[t]) * level_zsinv<R>(L);
-      // K^-1 (r_u - b^T q) from the shared row transforms of r_u
-      const R q = cb * dp;
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        R Tm[25], y[25];
-        const R* src = sT + (c * T::TR + 2 * qj) * 5 * TX + qi;
-#pragma unroll
-        for (int wj = 0; wj < 5; ++wj)
-#pragma unroll
-          for (int k = 0; k < 5; ++k) {
-            const R v = src[(wj * 5 + k) * TX];
-            Tm[wj * 5 + k] = brows_nonzero(c, wj, k) ? fma(-q, xb.t[c * 25 + wj * 5 + k], v) : v;
-          }
-        fd_finish<R>(fdg, Tm, y);
-#pragma unroll
-        for (int o = 0; o < 25; ++o) D[static_cast<long long>(c * 25 + o) * P] = y[o];
-      }
-    } else {
+    if (valid) {
+      const R* C = cd + cls * CD_STRIDE;
+      const int p = pj * np + pi;
+      R* D = delta + p;
       R ru[50];
 #pragma unroll
       for (int c = 0; c < 2; ++c)
@@ -724,7 +807,7 @@ __global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __r
 #pragma unroll
           for (int wi = 0; wi < 5; ++wi)
             ru[c * 25 + wj * 5 + wi] = sr[c * T::RW * T::RH + (2 * qj + wj) * T::RW + 2 * qi + wi];
-      dp = schur_dp<R>(warp_interior, L, C, ru, srp[t]);
+      const R dp = schur_dp<R>(warp_interior, L, C, ru, srp[t]);
       const int fx = axis_free_mask(ax), fy = axis_free_mask(ay);
       int fmask = 0;
 #pragma unroll
@@ -739,9 +822,70 @@ __global__ void __launch_bounds__(NT, MINB) k_vanka_own(LevelDev L, const R* __r
         for (int o = 0; o < 25; ++o)
           y[static_cast<long long>(o) * P] = fma(-__ldg(C + CD_Z + c * 25 + o), dp, y[static_cast<long long>(o) * P]);
       }
+      dpo[p] = dp;
     }
-    D[static_cast<long long>(50) * P] = dp;
   }
+  __syncthreads();   // the tile's corrections in the scratch are visible to the whole CTA
+  for (int it = tid; it < 2 * T::TR * TX; it += NT) {
+    const int qi = it % TX, rest = it / TX;
+    const int lr = rest % T::TR, c = rest / T::TR;
+    const int pi = i0 + qi;
+    if (pi > n) continue;
+    const int lo = max(0, (lr - 3) / 2), hi = min(min(TY - 1, lr / 2), n - j0);
+#pragma unroll
+    for (int w = 0; w < 5; ++w) {
+      R acc = R(0);
+      for (int qq = lo; qq <= hi; ++qq)   // patch rows in ascending order
+        acc += __ldcg(delta + static_cast<long long>(c * 25 + (lr - 2 * qq) * 5 + w) * P +
+                      static_cast<long long>(j0 + qq) * np + pi);
+      col_at(c, lr, w, qi) = acc;
+    }
+  }
+}
+
+// x_out = x + (omega / m_j) (sum of the corrections at dof j) from the split
+// sweep's column sums: for a Q2 node the 2 or 3 patch columns and the 1 or 2 tile
+// rows whose windows hold it, summed in ascending order; the pressure from the
+// dof's own patch.  One thread per vertex (a, b): its four Q2 nodes and p(a, b).
+template <typename T, int PI, int PJ>
+__device__ __forceinline__ void colsum_node(const LevelDev& L, const SplitOut& so, const T* __restrict__ cs,
+                                            const T* __restrict__ x, T* __restrict__ xo, T omega, int a, int b) {
+  using V = VO<16, 16>;
+  const int I = 2 * a + PI, J = 2 * b + PJ, nq = L.nq, n = L.n;
+  if (I >= nq || J >= nq) return;
+  const int pil = max(0, a - (PI ? 0 : 1)), pih = min(n, a + 1);
+  const int pjl = max(0, b - (PJ ? 0 : 1)), pjh = min(n, b + 1);
+  const T w = omega * vk::inv_mult<T>((pih - pil + 1) * (pjh - pjl + 1));
+  const int tyh = min(so.nty - 1, (J + 2) / 32);   // tile rows hold node rows 32 ty - 2 .. 32 ty + 32
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    T acc = T(0);
+    for (int ty = max(0, tyh - 1); ty <= tyh; ++ty) {
+      const int lr = J - 32 * ty + 2;
+      if (lr < 0 || lr >= V::TR) continue;
+      const T* row = cs + ((static_cast<long long>(c) * so.nty + ty) * V::TR + lr) * 5 * so.ncol;
+      for (int pi = pil; pi <= pih; ++pi) acc += row[static_cast<long long>(I - 2 * pi + 2) * so.ncol + pi];
+    }
+    const long long k = c * L.nv + static_cast<long long>(J) * nq + I;
+    xo[k] = fma(w, acc, x != nullptr ? x[k] : T(0));
+  }
+}
+
+template <typename T>
+__global__ void k_colsum_update(LevelDev L, const SplitOut so, const T* __restrict__ delta, const T* __restrict__ x,
+                                T* __restrict__ xo, T omega) {
+  pdl_begin();
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = blockIdx.y * blockDim.y + threadIdx.y;
+  if (a > L.n || b > L.n) return;
+  const T* cs = delta + so.col_off;
+  colsum_node<T, 0, 0>(L, so, cs, x, xo, omega, a, b);
+  colsum_node<T, 1, 0>(L, so, cs, x, xo, omega, a, b);
+  colsum_node<T, 0, 1>(L, so, cs, x, xo, omega, a, b);
+  colsum_node<T, 1, 1>(L, so, cs, x, xo, omega, a, b);
+  const int p = b * L.np + a;
+  const long long k = 2 * L.nv + p;
+  xo[k] = fma(omega, delta[so.dp_off + p], x != nullptr ? x[k] : T(0));
 }
 
 template <typename R, int TX, int TY, int NT>
@@ -996,16 +1140,23 @@ template <typename R>
 void launch_vanka_split(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
                         double omega, R* delta, int two_per_sm, cudaStream_t s) {
   count_launches(1);
-  const int P = patch_stride(L);
+  const SplitOut so = split_out(L);
   dim3 grid((L.np + 15) / 16, (L.np + 15) / 16);
   constexpr size_t smem = VO<16, 16>::SMEM * sizeof(R);
   const BRows<R> xb = coupling_row_transforms<R>(fd);
   if (two_per_sm)
-    launch_pdl(k_vanka_own<R, 16, 16, 256, 2>, dim3(grid), dim3(256), smem, s, L, cd, fd, xb, x, b, delta, P);
+    launch_pdl(k_vanka_own<R, 16, 16, 256, 2>, dim3(grid), dim3(256), smem, s, L, cd, fd, xb, x, b, delta, so);
   else
-    launch_pdl(k_vanka_own<R, 16, 16, 256, 1>, dim3(grid), dim3(256), smem, s, L, cd, fd, xb, x, b, delta, P);
-  launch_patch_update<R>(L, P, delta, x, xo, omega, s);
+    launch_pdl(k_vanka_own<R, 16, 16, 256, 1>, dim3(grid), dim3(256), smem, s, L, cd, fd, xb, x, b, delta, so);
+  count_launches(1);
+  launch_pdl(k_colsum_update<R>, dim3((L.np + 31) / 32, (L.np + 7) / 8), dim3(32, 8), 0, s, L, so,
+             static_cast<const R*>(delta), x, xo, static_cast<R>(omega));
 }
+size_t split_delta_doubles(const LevelDev& L) {
+  const SplitOut so = split_out(L);
+  return static_cast<size_t>(so.dp_off) + static_cast<size_t>(L.np) * L.np;
+}
+
 template void launch_vanka_split<double>(const LevelDev&, const double*, const FastDiag&, const double*,
                                          const double*, double*, double, double*, int, cudaStream_t);
 template void launch_vanka_split<float>(const LevelDev&, const float*, const FastDiagT<float>&, const float*,
