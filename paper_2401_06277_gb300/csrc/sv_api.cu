@@ -195,7 +195,7 @@ void sweep_f64(stokes_hierarchy* h, sv::Level& L, const double* x, const double*
     sv::launch_simple_sweep(L.d, L.pinv, h->delta, L.r, x, b, xo, h->prm.omega, h->stream);
   else if (sv::vanka_cfg_split(L.vk_cfg))
     sv::launch_vanka_split<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, h->delta, L.vk_cfg == sv::VANKA_CFG_SPLIT2,
-                           h->stream);
+                           h->stream, L.r);
   else
     sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, L.vk_cfg, h->stream);
 }
@@ -238,7 +238,7 @@ void timed_sweep<float>(stokes_hierarchy* h, bool finest, sv::Level& L, const fl
     tc_sweep(h, L, x, b, xo, h->stream);
   } else if (sv::vanka_cfg_split(L.vk_cfg_f)) {
     sv::launch_vanka_split<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, h->deltaf,
-                                  L.vk_cfg_f == sv::VANKA_CFG_SPLIT2, h->stream);
+                                  L.vk_cfg_f == sv::VANKA_CFG_SPLIT2, h->stream, nullptr);
   } else {
     sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, L.vk_cfg_f, h->stream);
   }
@@ -725,7 +725,7 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
       if constexpr (sizeof(R) == 8) {
         if (sv::vanka_cfg_split(c))
           sv::launch_vanka_split<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, h->delta,
-                                         c == sv::VANKA_CFG_SPLIT2, s);
+                                         c == sv::VANKA_CFG_SPLIT2, s, L.r);
         else
           sv::launch_vanka<double>(L.d, L.cd, h->fd, x, b, xo, h->prm.omega, c, s);
       } else {
@@ -733,7 +733,7 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
           tc_sweep(h, L, x, b, xo, s);
         } else if (sv::vanka_cfg_split(c)) {
           sv::launch_vanka_split<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, h->deltaf,
-                                        c == sv::VANKA_CFG_SPLIT2, s);
+                                        c == sv::VANKA_CFG_SPLIT2, s, nullptr);
         } else {
           sv::launch_vanka<float>(L.d, L.cdf, h->fdf, x, b, xo, h->prm.omega, c, s);
         }

@@ -399,11 +399,13 @@ void launch_patch_inverse(const LevelDev& L, double* inv, cudaStream_t s);
 // x_out = x + sum over patches of (omega / m_j) delta (entry-major corrections, stride P)
 template <typename T>
 void launch_patch_update(const LevelDev& L, int P, const T* delta, const T* x, T* xo, double omega, cudaStream_t s);
-// FP64 sweep in two kernels: own-patch solves (16 x 16 tiles, no halo patches)
-// writing delta (patch_delta_doubles), then launch_patch_update
+// Split sweep: own-patch solves (16 x 16 tiles, no halo patches) writing column
+// sums of the corrections into delta (split_delta_doubles), then the update.
+// rscratch (may be null): a level vector that receives r = b - A x first, so the
+// residual is formed once per cell instead of on the tiles' halo.
 template <typename R>
 void launch_vanka_split(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
-                        double omega, R* delta, int two_per_sm, cudaStream_t s);
+                        double omega, R* delta, int two_per_sm, cudaStream_t s, R* rscratch);
 void launch_simple_sweep(const LevelDev& L, const double* inv, double* delta, double* rscratch, const double* x,
                          const double* b, double* xo, double omega, cudaStream_t s);
 

@@ -1138,16 +1138,26 @@ void launch_vanka(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const 
 
 template <typename R>
 void launch_vanka_split(const LevelDev& L, const R* cd, const FastDiagT<R>& fd, const R* x, const R* b, R* xo,
-                        double omega, R* delta, int two_per_sm, cudaStream_t s) {
+                        double omega, R* delta, int two_per_sm, cudaStream_t s, R* rscratch) {
+  // with a scratch vector the residual is formed once per cell by the operator kernel
+  // (instead of on the tiles' one-vertex halo), and the own-patch kernel takes it as
+  // the right-hand side of a zero guess
+  const R* xs = x;
+  const R* bs = b;
+  if (rscratch != nullptr && x != nullptr) {
+    launch_apply<R>(L, x, b, rscratch, 1, s);
+    xs = nullptr;
+    bs = rscratch;
+  }
   count_launches(1);
   const SplitOut so = split_out(L);
   dim3 grid((L.np + 15) / 16, (L.np + 15) / 16);
   constexpr size_t smem = VO<16, 16>::SMEM * sizeof(R);
   const BRows<R> xb = coupling_row_transforms<R>(fd);
   if (two_per_sm)
-    launch_pdl(k_vanka_own<R, 16, 16, 256, 2>, dim3(grid), dim3(256), smem, s, L, cd, fd, xb, x, b, delta, so);
+    launch_pdl(k_vanka_own<R, 16, 16, 256, 2>, dim3(grid), dim3(256), smem, s, L, cd, fd, xb, xs, bs, delta, so);
   else
-    launch_pdl(k_vanka_own<R, 16, 16, 256, 1>, dim3(grid), dim3(256), smem, s, L, cd, fd, xb, x, b, delta, so);
+    launch_pdl(k_vanka_own<R, 16, 16, 256, 1>, dim3(grid), dim3(256), smem, s, L, cd, fd, xb, xs, bs, delta, so);
   count_launches(1);
   launch_pdl(k_colsum_update<R>, dim3((L.np + 31) / 32, (L.np + 7) / 8), dim3(32, 8), 0, s, L, so,
              static_cast<const R*>(delta), x, xo, static_cast<R>(omega));
@@ -1158,9 +1168,9 @@ size_t split_delta_doubles(const LevelDev& L) {
 }
 
 template void launch_vanka_split<double>(const LevelDev&, const double*, const FastDiag&, const double*,
-                                         const double*, double*, double, double*, int, cudaStream_t);
+                                         const double*, double*, double, double*, int, cudaStream_t, double*);
 template void launch_vanka_split<float>(const LevelDev&, const float*, const FastDiagT<float>&, const float*,
-                                        const float*, float*, double, float*, int, cudaStream_t);
+                                        const float*, float*, double, float*, int, cudaStream_t, float*);
 
 template void launch_vanka<double>(const LevelDev&, const double*, const FastDiagT<double>&, const double*,
                                    const double*, double*, double, int, cudaStream_t, int, int);
