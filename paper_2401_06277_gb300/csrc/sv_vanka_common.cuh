@@ -125,7 +125,8 @@ __device__ __forceinline__ void res_cell(T* r0, const T* x0, const T* pc, int I0
               if (w != T(0)) g = fma(w, P[dj + 1][di + 1], g);
             }
           }
-          r0[c * V::RW * V::RH + PJ * V::RW + PI] -= cl * sl + cb * g;
+          T& rr = r0[c * V::RW * V::RH + PJ * V::RW + PI];
+          rr = fma(-cl, sl, fma(-cb, g, rr));   // r - (cl sl + cb g) as two multiply-adds
         }
       }
     }

@@ -504,8 +504,9 @@ __global__ void __launch_bounds__(NT, ctas_per_sm(TC)) k_vanka_strip(LevelDev L,
                 if (w0 != 0.0f || w1 != 0.0f) g = __ffma2_rn(make_float2(w0, w1), make_float2(pv, pv), g);
               }
             }
-            const float2 ax = __ffma2_rn(make_float2(cl, cl), slap[PJ][PI], __fmul2_rn(make_float2(cb, cb), g));
-            res[PJ][PI] = __fadd2_rn(res[PJ][PI], make_float2(-ax.x, -ax.y));
+            // r - (cl slap + cb g) as two packed multiply-adds
+            res[PJ][PI] = __ffma2_rn(make_float2(-cl, -cl), slap[PJ][PI],
+                                     __ffma2_rn(make_float2(-cb, -cb), g, res[PJ][PI]));
           }
         }
         rp -= cb * (sdiv.x + sdiv.y);
