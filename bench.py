@@ -252,8 +252,9 @@ def job_throughput(ws, units_local: float, ms_local: float) -> tuple[float, floa
 # kernel at 1024 x 1024 (ncu --set full, summaries in profiles/); at other sizes the
 # bench scales them by the number of dofs (the traffic of a sweep is proportional)
 TRAFFIC_1024 = {
-    "fp64": {"bytes": 160869120 + 175796480 + 269554944 + 56444416, "tile": "split16x16x2",
-             "source": "profiles/k_vanka_own_f64_n1024.md (k_vanka_own<double,16,16,256,2> + k_colsum_update; "
+    "fp64": {"bytes": 151235072 + 45359872 + 84654592 + 172603904 + 269547776 + 56439552, "tile": "split16x16x2",
+             "source": "profiles/k_vanka_own_f64_n1024.md (k_apply<double> residual + k_vanka_own<double,16,16,256,2> "
+                       "+ k_colsum_update, a sweep from a non-zero iterate; "
                        "writes still in L2 at kernel end are not counted)"},
     "mixed": {"bytes": 76410112 + 7026944, "tile": "14x14",
               "source": "profiles/k_vanka_strip_f32_n1024.md (k_vanka_strip<false> interior strips; the ring "
@@ -448,7 +449,8 @@ def _time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother, h
         fl = sweep_flops(n) - ZERO_GUESS_SHARE * 361.0 * (n + 1) ** 2
         peak = FP64_PEAK["peak"]
         achieved = fl / (sweep_ms * 1e-3) / 1e9
-        kname = ("k_vanka_own<double,16,16> + k_colsum_update (split sweep, finest level)" if tile.startswith("split")
+        kname = ("k_apply<double> + k_vanka_own<double,16,16> + k_colsum_update (split sweep, finest level)"
+                 if tile.startswith("split")
                  else "k_vanka<double> (finest level)")
         roofline = {"bound": "alu", "kernel": kname, "achieved": round(achieved, 2),
                     "peak": round(peak, 1), "unit": "GFLOP/s", "frac": round(achieved / peak, 4),
@@ -458,9 +460,9 @@ def _time_form(args, prec_name, ws, rank, f_host, ud_host, with_e2e, smoother, h
                     "nominal_gflops": round(SM_COUNT * 4 * sm_max * 1e6 / 1e9, 1),
                     "algorithmic_flops_per_launch": fl,
                     "executed_flops_note": "the kernels execute fewer FP64 flops than the algorithmic count (about "
-                                           "1150 against 1681 per vertex at 1024^2, ncu: shared row transforms, the fused "
-                                           "column pass and the shared last pass of the fast diagonalisation); "
-                                           "profiles/k_vanka_own_f64_n1024.md",
+                                           "1071 against 1681 per vertex at 1024^2, ncu: shared row transforms, the fused "
+                                           "column pass and the shared last pass of the fast diagonalisation, the "
+                                           "residual once per cell); profiles/k_vanka_own_f64_n1024.md",
                     "algorithmic_bytes_per_launch": sweep_bytes(n) * (3.0 - ZERO_GUESS_SHARE) / 3.0,
                     "hbm_gbs_achieved": round(sweep_bytes(n) * (3.0 - ZERO_GUESS_SHARE) / 3.0 / (sweep_ms * 1e-3) / 1e9, 1)}
     else:
