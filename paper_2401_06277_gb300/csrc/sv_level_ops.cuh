@@ -69,9 +69,9 @@ __device__ __forceinline__ void apply_vertex_m(const LevelDev& L, const T* x,
         const int I = I0 + PI, J = J0 + PJ;
         if (MASK && (I >= nq || J >= nq)) continue;
         const long long k = c * nv + static_cast<long long>(J) * nq + I;
+        T v;
         if (MASK && !is_free(I, J, nq)) {
-          const T v = xc[static_cast<long long>(J) * nq + I];   // Dirichlet row: identity
-          y[k] = residual ? b[k] - v : v;
+          v = xc[static_cast<long long>(J) * nq + I];   // Dirichlet row: identity
         } else {
           T sl = T(0), g = T(0);
 #pragma unroll
@@ -89,9 +89,9 @@ __device__ __forceinline__ void apply_vertex_m(const LevelDev& L, const T* x,
                                    : ncol(2 + PI, 1 + di) * ccol(2 + PJ, 1 + dj));
               if (w != T(0)) g = fma(w, P[dj + 1][di + 1], g);
             }
-          // b - (cl sl + cb g) as two multiply-adds
-          y[k] = residual ? fma(-cl, sl, fma(-cb, g, b[k])) : fma(cl, sl, cb * g);
+          v = cl * sl + cb * g;
         }
+        y[k] = residual ? b[k] - v : v;
       }
     }
     // pressure row of (a, bb): taps at Q2 nodes (2a + dI, 2bb + dJ)
@@ -103,8 +103,9 @@ __device__ __forceinline__ void apply_vertex_m(const LevelDev& L, const T* x,
         if (w != T(0)) bu = fma(w, X[dJ + 2][dI + 2], bu);
       }
   }
+  const T ap = cb * bu;
   const long long k = 2 * nv + static_cast<long long>(bb) * np + a;
-  y[k] = residual ? fma(-cb, bu, b[k]) : cb * bu;
+  y[k] = residual ? b[k] - ap : ap;
 }
 
 // y = A x or b - A x at vertex (a, bb): the masked variant within two of the boundary
