@@ -62,7 +62,7 @@ __device__ __forceinline__ T btp(const T* pc) {
 // G: window geometry (XW, XH, PW, RW, RH), e.g. VT<TX, TY>
 template <typename T, int PI, int PJ, typename G>
 __device__ __forceinline__ void res_node(T* sr, const T* x0, const T* pc, int I, int J,
-                                         const LevelDev& L, const T* __restrict__ x, T cl, T cb) {
+                                         const LevelDev& L, const T* x, T cl, T cb) {
   using V = G;
   const int nq = L.nq;
   if (I < 0 || J < 0 || I >= nq || J >= nq) return;  // outside: r stays 0
@@ -77,6 +77,10 @@ __device__ __forceinline__ void res_node(T* sr, const T* x0, const T* pc, int I,
   sr[V::RW * V::RH] -= cl * lap<T, PI, PJ, V::XW>(x1) + cb * btp<T, PI, PJ, 1, V::PW>(pc);
 }
 
+// The global x of res_node / res_cell (read on Dirichlet rows) carries no
+// __restrict__: in the persistent coarse-level kernel one step writes it and a later
+// one reads it, so those loads must not take the read-only (non-coherent) path.
+//
 // Residual of the 2x2 cell of Q2 nodes (I0..I0+1) x (J0..J0+1) (I0, J0 even),
 // both components.  When all four nodes are free, the 6x6 x neighbourhood of
 // each component and the 3x3 pressures are loaded into registers once and the
@@ -85,7 +89,7 @@ __device__ __forceinline__ void res_node(T* sr, const T* x0, const T* pc, int I,
 // component 0, pc at the pressure of vertex (I0/2, J0/2).
 template <typename T, typename G>
 __device__ __forceinline__ void res_cell(T* r0, const T* x0, const T* pc, int I0, int J0, const LevelDev& L,
-                                         const T* __restrict__ x, T cl, T cb) {
+                                         const T* x, T cl, T cb) {
   using V = G;
   const int nq = L.nq;
   if (I0 >= 1 && J0 >= 1 && I0 + 1 <= nq - 2 && J0 + 1 <= nq - 2) {
