@@ -47,10 +47,12 @@ def vcycle(H, b):
 def test_persistent_launch_equals_one_launch_per_step(pkg, n, cycle):
     """Mixed FP32 form: the persistent launch (levels 4..n/2 at n = 64, 4..128 at 256)
     equals the same steps launched one by one, bit for bit, for the V- and the W-cycle,
-    on two right-hand sides in a row."""
+    on two right-hand sides in a row.  The sweep configuration is pinned (8 x 8 SIMT
+    tile) so the levels above the persistent launch run the same kernels in both
+    hierarchies; tuned independently, they could pick differently rounding sweeps."""
     from paper_2401_06277_gb300 import stokes
-    Ha = pkg.Hierarchy(n, prec=stokes.STOKES_MIXED_FP32, tail_n=-128, cycle=cycle)
-    Hb = pkg.Hierarchy(n, prec=stokes.STOKES_MIXED_FP32, tail_n=128, cycle=cycle)
+    Ha = pkg.Hierarchy(n, prec=stokes.STOKES_MIXED_FP32, tile=0, tail_n=-128, cycle=cycle)
+    Hb = pkg.Hierarchy(n, prec=stokes.STOKES_MIXED_FP32, tile=0, tail_n=128, cycle=cycle)
     top, steps, ctas = stokes.stokes_tail_info(Hb.handle)
     assert top == Hb.levels - 2 and steps > 0 and ctas > 0
     assert stokes.stokes_tail_info(Ha.handle)[:2] == (top, steps)
