@@ -252,14 +252,14 @@ def job_throughput(ws, units_local: float, ms_local: float) -> tuple[float, floa
 # kernel at 1024 x 1024 (ncu --set full, summaries in profiles/); at other sizes the
 # bench scales them by the number of dofs (the traffic of a sweep is proportional)
 TRAFFIC_1024 = {
-    "fp64": {"bytes": 151235072 + 45359872 + 84654592 + 172603904 + 269547776 + 56439552, "tile": "split16x16x2",
+    "fp64": {"bytes": 151244032 + 45977088 + 84809216 + 172724736 + 269548032 + 56484864, "tile": "split16x16x2",
              "source": "profiles/k_vanka_own_f64_n1024.md (k_apply<double> residual + k_vanka_own<double,16,16,256,2> "
                        "+ k_colsum_update, a sweep from a non-zero iterate; "
                        "writes still in L2 at kernel end are not counted)"},
-    "mixed": {"bytes": 76410112 + 7026944, "tile": "14x14",
+    "mixed": {"bytes": 77614592 + 7096320, "tile": "14x14",
               "source": "profiles/k_vanka_strip_f32_n1024.md (k_vanka_strip<false> interior strips; the ring "
                         "launch is not included; writes still in L2 at kernel end are not counted)"},
-    "bf16": {"bytes": 77008640 + 5505280, "tile": "14x14",
+    "bf16": {"bytes": 76957440 + 6176256, "tile": "14x14",
              "source": "profiles/k_vanka_strip_bf16_n1024.md (k_vanka_strip<true> interior strips; the ring "
                        "launch is not included; writes still in L2 at kernel end are not counted)"},
 }
