@@ -82,8 +82,9 @@ typedef struct {
                        strip sweep of the interior tiles where they fit --
                        BF16 tensor-core patch GEMMs, or FP32 patch solves --
                        with a 14x14 SIMT ring); 4 = split sweep
-                       (16x16 own-patch solves writing the corrections, then a
-                       separate update), 5 = the same compiled for two CTAs
+                       (16x16 own-patch solves writing sums of their
+                       corrections, then a separate update), 5 = the same
+                       compiled for two CTAs
                        per SM, 6 = fused 4x4 tiles (small levels: more
                        CTAs)                                           (-1) */
   int smoother;     /* stokes_smoother below                             (0)  */

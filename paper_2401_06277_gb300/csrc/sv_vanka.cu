@@ -28,9 +28,9 @@
 // patch solves of u_x and u_y run as one packed pass (FFMA2 on component
 // pairs) and the interior Schur vector is read from constant memory.
 //
-// The split sweep below (k_vanka_own + k_patch_update) solves only a tile's
-// own patches and passes the corrections through HBM: the better trade where
-// the FP64 pipe is the bound.
+// The split sweep below (the operator kernel's residual, k_vanka_own, then
+// k_colsum_update) solves only a tile's own patches and passes sums of their
+// corrections through HBM: the better trade where the FP64 pipe is the bound.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -463,13 +463,14 @@ __global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Split sweep: a CTA solves only the TX x TY patches of the vertices it owns
-// (no halo patches; the residual is needed on a one-vertex halo only) and
-// writes their 51 corrections to a global, entry-major delta (slot * P +
-// patch); a second kernel (k_patch_update, shared with the per-patch-inverse
-// smoother) forms x + W sum of the corrections.  Against the fused kernel this
-// trades 1.27x halo patch solves and 1.56x halo residuals for one write and one
-// read of delta: the better trade where the FP64 pipe, not HBM, is the bound.
+// Split sweep: a CTA solves only the TX x TY patches of the vertices it owns (no
+// halo patches) from the residual on a one-vertex halo -- formed by the operator
+// kernel beforehand when the caller passes a scratch vector, else in the tile --
+// and writes, per patch column, the sums of its patches' corrections (SplitOut);
+// k_colsum_update then forms x + W sum of the corrections.  Against the fused
+// kernel this trades 1.27x halo patch solves and 1.56x halo residuals for one
+// write and one read of the sums: the better trade where the FP64 pipe, not HBM,
+// is the bound.
 //
 // In a tile whose patches are all interior, the first pass of the fast
 // diagonalisation (the transform along each window row) is shared: patches
