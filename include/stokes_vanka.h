@@ -119,6 +119,16 @@ typedef struct {
                        a tile's patch solves, which the launch does not remove,
                        and the grid barriers cost more than the launches they
                        replace                                           (0)    */
+  int orth;         /* Gram-Schmidt of the Arnoldi step (Section 6.8): 1 =
+                       classical, two passes over the basis per iteration with
+                       the second only where the first removed more than half
+                       of ||w||^2 (DGKS test, taken on the device); 2 = modified,
+                       one pass per basis vector in the textbook order; 0 = by
+                       size: modified on grids of at least 2^20 dofs, where a
+                       pass streams HBM faster than the FP64 units do the
+                       classical passes' four FMAs per element and vector, and
+                       classical below, where the modified form's one launch
+                       per basis vector costs more than its arithmetic   (0)    */
 } stokes_params;
 
 /* How each Vanka patch solve A_i^-1 r_i is applied (Section 4, Section 6.2). */

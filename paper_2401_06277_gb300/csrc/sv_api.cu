@@ -597,11 +597,13 @@ void fg_start_cycle(stokes_hierarchy* h, double beta) {
   sv::launch_fill(sb.g, beta, 1, h->stream);
 }
 
-// iteration j: Z_j = MG(V_j), w = A Z_j, classical Gram-Schmidt against V_0..V_j
+// iteration j: Z_j = MG(V_j), w = A Z_j, Gram-Schmidt against V_0..V_j,
+// V_{j+1} = w / ||w||, Givens rotation j; sc[2] = |g_{j+1}| (the residual
+// estimate).  Gram-Schmidt is modified (one pass per basis vector) or classical
 // (a second pass when the first removed more than half of ||w||^2: the DGKS
-// test, taken on the device), V_{j+1} = w / ||w||, Givens rotation j;
-// sc[2] = |g_{j+1}| (the residual estimate).  Scalars: sc[0..1] = ||w||^2,
-// ||w||; sc[3..4] = ||A Z_j||^2 and its root; sc[5] = 1 if the second pass runs.
+// test, taken on the device), by stokes_params.orth.  Scalars: sc[0..1] =
+// ||w||^2, ||w||; sc[3..4] = ||A Z_j||^2 and its root; sc[5] = 1 if the
+// classical second pass runs.
 void fg_iteration(stokes_hierarchy* h, int j) {
   cudaStream_t s = h->stream;
   sv::Level& F = h->lv.back();
@@ -616,7 +618,20 @@ void fg_iteration(stokes_hierarchy* h, int j) {
   sv::launch_apply<double>(F.d, zj, nullptr, w, 0, s);
   double* P = h->partials;
   const int np = h->npart;
-  // pass 1: h = V^T w and ||w||^2; w -= V h with the new ||w||^2 and the DGKS
+  if (h->prm.orth == 2 || (h->prm.orth == 0 && N >= (1LL << 20))) {
+    // modified Gram-Schmidt: h_0 = <V_0, w> with ||w||^2 (sc[3..4]); then
+    // w -= h_{i-1} V_{i-1} and h_i = <V_i, w> for i = 1..j; last, w -= h_j V_j
+    // and the new ||w||^2 (sc[0..1])
+    sv::launch_mgs_step(w, nullptr, V, nullptr, N, P, np, h->ticket, sb.hcol, sb.sc + 3, s);
+    for (int i = 1; i <= j; ++i)
+      sv::launch_mgs_step(w, V + (i - 1) * ld, V + i * ld, sb.hcol + (i - 1), N, P, np, h->ticket, sb.hcol + i,
+                          nullptr, s);
+    sv::launch_mgs_step(w, V + j * ld, nullptr, sb.hcol + j, N, P, np, h->ticket, nullptr, sb.sc, s);
+    sv::launch_scale(w, w, sb.sc + 1, 0.0, N, s);
+    sv::launch_givens(sb.H, m + 1, sb.cs, sb.sn, sb.g, sb.hcol, sb.sc + 1, j, sb.sc + 2, s);
+    return;
+  }
+  // classical: pass 1: h = V^T w and ||w||^2; w -= V h with the new ||w||^2 and the DGKS
   // flag, fused (up to 16 basis vectors) with pass 2's dots h2 = V^T w
   sv::launch_orth_dots(V, ld, j + 1, w, N, P, np, h->ticket, sb.hcol, sb.sc + 3, nullptr, s);
   if (!sv::launch_orth_update_dots(w, V, ld, j + 1, sb.hcol, N, P, np, h->ticket, sb.h2, sb.sc, sb.sc + 3,
@@ -739,13 +754,22 @@ cudaError_t tune_level(stokes_hierarchy* h, sv::Level& L, int* cfg) {
         }
       }
     };
+    // one untimed run, then the best of three timed trials: a trial is a few sweeps
+    // on large levels and more on small ones, where one sweep lasts microseconds and
+    // a single trial is at the mercy of launch jitter
     run();
-    cudaEventRecord(e0, s);
-    for (int r = 0; r < 3; ++r) run();
-    cudaEventRecord(e1, s);
-    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    const int reps = L.d.N > (1 << 22) ? 3 : 10;
+    float ms = 1e30f;
+    for (int trial = 0; trial < 3 && e == cudaSuccess; ++trial) {
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps; ++r) run();
+      cudaEventRecord(e1, s);
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, e0, e1);
+      ms = std::min(ms, t / reps);
+    }
+    if (e != cudaSuccess) break;
     if (ms < best) {
       best = ms;
       best_c = c;
@@ -815,6 +839,7 @@ void stokes_default_params(stokes_params* p) {
   p->bt_omega_u = 1.0;
   p->bt_omega_p = 0.6;
   p->tail_n = 0;
+  p->orth = 0;
 }
 
 const char* stokes_last_error(void) { return g_err.c_str(); }
@@ -837,6 +862,7 @@ stokes_status stokes_hierarchy_create(int n, double viscosity, const stokes_para
   if (prm.tile < -1 || prm.tile > sv::VANKA_CFG_4) return fail(STOKES_ERR_ARG, "tile must be -1..6");
 
   if (prm.cycle < 1 || prm.cycle > 2) return fail(STOKES_ERR_ARG, "cycle must be 1 (V) or 2 (W)");
+  if (prm.orth < 0 || prm.orth > 2) return fail(STOKES_ERR_ARG, "orth must be 0 (by size), 1 or 2");
   if (prm.precond < 0 || prm.precond > 1) return fail(STOKES_ERR_ARG, "precond must be 0 or 1");
   if (prm.precond == 1 && (prm.prec != STOKES_FP64 || prm.bt_cycles < 1 || prm.bt_nu < 0 ||
                            !(prm.bt_omega_u > 0.0) || !(prm.bt_omega_p > 0.0)))

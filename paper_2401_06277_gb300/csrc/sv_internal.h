@@ -430,6 +430,13 @@ void launch_orth_update(double* w, const double* V, long long ld, int nk, const 
 bool launch_orth_update_dots(double* w, const double* V, long long ld, int nk, const double* coef, long long N,
                              double* partials, int npart, unsigned* ticket, double* dots, double* norm2,
                              const double* dgks_ref, double* flag, cudaStream_t s);
+// One step of modified Gram-Schmidt (see k_mgs_step): w -= coef[0] Va unless Va
+// is null; dots[0] = <Vb, w> unless Vb is null; when Va or Vb is null also
+// norm2[0] = <w, w>, norm2[1] = its root (first step: of w as given; last step:
+// of the updated w).  Va and Vb are not both null.  partials and ticket as for
+// launch_orth_dots.
+void launch_mgs_step(double* w, const double* Va, const double* Vb, const double* coef, long long N,
+                     double* partials, int npart, unsigned* ticket, double* dots, double* norm2, cudaStream_t s);
 // w += sign * sum_k coef[k] V_k
 void launch_multiaxpy(double* w, const double* V, long long ld, int nk, const double* coef,
                       double sign, long long N, cudaStream_t s);

@@ -261,6 +261,62 @@ __global__ void __launch_bounds__(DOT_NT) k_orth_update_dots(double* __restrict_
   }
 }
 
+// One step of modified Gram-Schmidt, in the order of the textbook loop: if UPD,
+// w -= coef[0] Va (coef[0] the dot the previous step produced); then, if DOT,
+// dots[0] = <Vb, w>, and, if NORM, norm2[0] = <w, w> and norm2[1] = its square
+// root, both of the updated w.  Every element costs at most two FP64 FMAs against
+// three vectors read and one written, so a step streams HBM: on a GPU whose FP64
+// rate is 1/64 of its FP32 rate this is cheaper per basis vector than classical
+// Gram-Schmidt with a second pass, which spends four FMAs per element and vector.
+template <bool UPD, bool DOT, bool NORM>
+__global__ void __launch_bounds__(DOT_NT) k_mgs_step(double* __restrict__ w, const double* __restrict__ Va,
+                                                     const double* __restrict__ Vb,
+                                                     const double* __restrict__ coef, long long N,
+                                                     double* __restrict__ partials, int npart, unsigned* ticket,
+                                                     double* __restrict__ dots, double* __restrict__ norm2) {
+  pdl_begin();
+  constexpr int NO = (DOT ? 1 : 0) + (NORM ? 1 : 0);
+  static_assert(NO > 0, "a step produces a dot or a norm");
+  constexpr int U = 4;
+  const double c = UPD ? coef[0] : 0.0;
+  double acc[NO];
+#pragma unroll
+  for (int k = 0; k < NO; ++k) acc[k] = 0.0;
+  auto step = [&](long long i, double x, double va, double vb) {
+    if (UPD) {
+      x = fma(-c, va, x);
+      w[i] = x;
+    }
+    if (DOT) acc[0] = fma(vb, x, acc[0]);
+    if (NORM) acc[NO - 1] = fma(x, x, acc[NO - 1]);
+  };
+  const long long stride = static_cast<long long>(gridDim.x) * DOT_NT;
+  long long i = blockIdx.x * static_cast<long long>(DOT_NT) + threadIdx.x;
+  for (; i + (U - 1) * stride < N; i += U * stride) {
+    double x[U], va[U], vb[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      x[u] = w[i + u * stride];
+      va[u] = UPD ? Va[i + u * stride] : 0.0;
+      vb[u] = DOT ? Vb[i + u * stride] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) step(i + u * stride, x[u], va[u], vb[u]);
+  }
+  for (; i < N; i += stride) step(i, w[i], UPD ? Va[i] : 0.0, DOT ? Vb[i] : 0.0);
+  if (!block_partials<NO>(acc, partials, npart, ticket)) return;
+  double tot[NO];
+  total_partials<NO>(partials, npart, tot);
+  if (threadIdx.x == 0) {
+    if (DOT) dots[0] = tot[0];
+    if (NORM) {
+      norm2[0] = tot[NO - 1];
+      norm2[1] = sqrt(tot[NO - 1]);
+    }
+    *ticket = 0u;
+  }
+}
+
 // out[k] (+)= sum_b partials[k * npart + b]; one CTA per k
 __global__ void k_reduce(const double* __restrict__ partials, int npart, double* __restrict__ out,
                          int accumulate) {
@@ -511,6 +567,18 @@ bool launch_orth_update_dots(double* w, const double* V, long long ld, int nk, c
 }
 
 #undef SV_ORTH_CASES
+
+void launch_mgs_step(double* w, const double* Va, const double* Vb, const double* coef, long long N,
+                     double* partials, int npart, unsigned* ticket, double* dots, double* norm2, cudaStream_t s) {
+  count_launches(1);
+  const dim3 g(npart), b(DOT_NT);
+  if (Va == nullptr)   // the first step: <V_0, w> and ||w||^2
+    launch_pdl(k_mgs_step<false, true, true>, g, b, 0, s, w, Va, Vb, coef, N, partials, npart, ticket, dots, norm2);
+  else if (Vb == nullptr)   // the last step: w -= h_j V_j and the new ||w||^2
+    launch_pdl(k_mgs_step<true, false, true>, g, b, 0, s, w, Va, Vb, coef, N, partials, npart, ticket, dots, norm2);
+  else
+    launch_pdl(k_mgs_step<true, true, false>, g, b, 0, s, w, Va, Vb, coef, N, partials, npart, ticket, dots, norm2);
+}
 
 void launch_multiaxpy(double* w, const double* V, long long ld, int nk, const double* coef,
                       double sign, long long N, cudaStream_t s) {

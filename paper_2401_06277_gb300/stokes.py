@@ -55,7 +55,7 @@ class stokes_params(ctypes.Structure):
                 ("bs_jacobi_weight", ctypes.c_double), ("bs_jacobi_iters", ctypes.c_int),
                 ("cycle", ctypes.c_int), ("precond", ctypes.c_int), ("bt_cycles", ctypes.c_int),
                 ("bt_nu", ctypes.c_int), ("bt_omega_u", ctypes.c_double), ("bt_omega_p", ctypes.c_double),
-                ("tail_n", ctypes.c_int)]
+                ("tail_n", ctypes.c_int), ("orth", ctypes.c_int)]
 
 
 _lib = None
@@ -471,6 +471,7 @@ class Hierarchy:
     bt_omega_u: float = 1.0
     bt_omega_p: float = 0.6
     tail_n: int = 0
+    orth: int = 0
 
     def __post_init__(self):
         p = default_params()
@@ -484,6 +485,7 @@ class Hierarchy:
         p.precond, p.bt_cycles, p.bt_nu = self.precond, self.bt_cycles, self.bt_nu
         p.bt_omega_u, p.bt_omega_p = self.bt_omega_u, self.bt_omega_p
         p.tail_n = self.tail_n
+        p.orth = self.orth
         self.handle = stokes_hierarchy_create(self.n, self.viscosity, p)
         self.levels, _ = stokes_level_info(self.handle)
         self.N = vec_len(self.n)

@@ -78,3 +78,34 @@ def test_product_code_never_imports_the_oracle():
         for f in files:
             if f.endswith(".py"):
                 assert not pat.search(open(os.path.join(dirpath, f)).read()), f
+
+
+def _header_struct_fields(name):
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src)
+    assert m, name
+    # enum-typed fields (stokes_precision) are ints
+    fields = re.findall(r"^\s*(int|double|long long|stokes_[a-z]+)\s+([a-z0-9_]+)\s*;", m.group(1), flags=re.M)
+    return [("int" if t.startswith("stokes_") else t, f) for t, f in fields]
+
+
+@pytest.mark.parametrize("name", ["stokes_params", "stokes_stats"])
+def test_binding_structs_match_the_header(name):
+    """The ctypes mirrors of the header's structs have the same fields, in the same order, of the same types."""
+    import ctypes as C
+    from paper_2401_06277_gb300 import stokes
+    ctype = {"int": C.c_int, "double": C.c_double, "long long": C.c_longlong}
+    want = [(f, C.sizeof(ctype[t]), t == "double") for t, f in _header_struct_fields(name)]
+    got = [(f, C.sizeof(t), t is C.c_double) for f, t in getattr(stokes, name)._fields_]
+    assert got == want
+
+
+def test_orth_parameter_default_and_range(lib_path):
+    from paper_2401_06277_gb300 import stokes
+    p = stokes.default_params()
+    assert p.orth == 0
+    lib = stokes._load()
+    out = ctypes.c_void_p()
+    p.orth = 3
+    assert lib.stokes_hierarchy_create(16, 1.0, ctypes.byref(p), None, ctypes.byref(out)) == stokes.STOKES_ERR_ARG
+    assert b"orth" in lib.stokes_last_error()

@@ -191,9 +191,12 @@ def test_vcycle_sweep_counts(pkg, nu1, nu2):
     assert rel(host(H.vcycle(dev(r))), O.vcycle(Ho, r)) <= 1e-12
 
 
+@pytest.mark.parametrize("orth", [0, 2])
 @pytest.mark.parametrize("n", [8, 16, 32, 64])
-def test_fgmres_solution(pkg, n):
-    H = gpu_h(pkg, n)
+def test_fgmres_solution(pkg, n, orth):
+    """orth 0 on these grids is classical Gram-Schmidt (DGKS); orth 2 forces the
+    modified form that grids of 2^20 dofs and more take by default."""
+    H = gpu_h(pkg, n, orth=orth)
     Ho = oracle_h(n)
     lv = Ho.levels[-1]
     f = si.manufactured_force(n) if n == 32 else si.random_force(n, 100 + n)
@@ -211,9 +214,10 @@ def test_fgmres_solution(pkg, n):
     assert np.linalg.norm(b - lv.A @ host(x)) / r0 <= 1.01e-8
 
 
-def test_fgmres_against_direct_solve(pkg):
+@pytest.mark.parametrize("orth", [1, 2])
+def test_fgmres_against_direct_solve(pkg, orth):
     n = 16
-    H = gpu_h(pkg, n, rtol=1e-13)
+    H = gpu_h(pkg, n, rtol=1e-13, orth=orth)
     lv = oracle_h(n).levels[-1]
     b = O.assemble_rhs(lv, si.random_force(n, 7), si.manufactured_velocity(n))
     x, it, rr = H.solve(dev(b))
@@ -222,12 +226,13 @@ def test_fgmres_against_direct_solve(pkg):
     assert np.linalg.norm(xg - xd) / np.linalg.norm(xd) <= 1e-10
 
 
-def test_fgmres_small_restart_and_maxit(pkg):
+@pytest.mark.parametrize("orth", [1, 2])
+def test_fgmres_small_restart_and_maxit(pkg, orth):
     from paper_2401_06277_gb300 import stokes
     n = 16
     lv = oracle_h(n).levels[-1]
     b = O.assemble_rhs(lv, si.manufactured_force(n), si.manufactured_velocity(n))
-    H3 = gpu_h(pkg, n, restart=3)
+    H3 = gpu_h(pkg, n, restart=3, orth=orth)
     x, it, rr = H3.solve(dev(b))
     ref = O.solve(O.build_hierarchy(n), b, restart=3)
     assert it == ref.iters and rr <= 1e-8
@@ -318,12 +323,12 @@ def test_mixed_vcycle_close_to_fp64(pkg, n, tile):
     assert err <= 1e-4, err
 
 
-@pytest.mark.parametrize("tile", [-1, 5])
+@pytest.mark.parametrize("tile,orth", [(-1, 0), (5, 0), (-1, 2)])
 @pytest.mark.parametrize("n", [16, 64])
-def test_mixed_fgmres_solution(pkg, n, tile):
+def test_mixed_fgmres_solution(pkg, n, tile, orth):
     """FGMRES (FP64) with the FP32 preconditioner reaches the same 1e-8 residual; the
     solution is within 1e-7 of the FP64 oracle's solution at the same tolerance."""
-    H = mixed_h(pkg, n, tile=tile)
+    H = mixed_h(pkg, n, tile=tile, orth=orth)
     Ho = oracle_h(n)
     lv = Ho.levels[-1]
     b = O.assemble_rhs(lv, si.random_force(n, 31), si.manufactured_velocity(n))
@@ -362,13 +367,13 @@ def test_bf16_vcycle_close_to_fp64(pkg, n, tile):
     assert err <= 1e-2, err
 
 
-@pytest.mark.parametrize("tile", [3, -1])
+@pytest.mark.parametrize("tile,orth", [(3, 0), (-1, 0), (3, 2)])
 @pytest.mark.parametrize("n", [64, 128])
-def test_bf16_fgmres_solution(pkg, n, tile):
+def test_bf16_fgmres_solution(pkg, n, tile, orth):
     """FGMRES (FP64) with the BF16 tensor-core preconditioner: same 1e-8 residual,
     solution within 1e-7 of the FP64 oracle's at the same tolerance."""
     from paper_2401_06277_gb300 import stokes
-    H = gpu_h(pkg, n, prec=stokes.STOKES_MIXED_BF16, tile=tile)
+    H = gpu_h(pkg, n, prec=stokes.STOKES_MIXED_BF16, tile=tile, orth=orth)
     Ho = oracle_h(n)
     lv = Ho.levels[-1]
     b = O.assemble_rhs(lv, si.random_force(n, 41), si.manufactured_velocity(n))
@@ -511,13 +516,15 @@ def test_batch_uneven_sizes_match_single_solves(pkg, prec):
     B.close()
 
 
-def test_batch_many_rhs_one_grid(pkg):
+@pytest.mark.parametrize("orth", [0, 2])
+def test_batch_many_rhs_one_grid(pkg, orth):
     """Eight right-hand sides on one grid (FP32 preconditioner): every solve reaches 1e-8
-    and matches the oracle's solution within 1e-7."""
+    and matches the oracle's solution within 1e-7, with either Gram-Schmidt captured in
+    the batch's per-iteration graphs."""
     from paper_2401_06277_gb300 import stokes
     n = 32
     ns = [n] * 8
-    B = pkg.Batch(ns, prec=stokes.STOKES_MIXED_FP32, restart=12)
+    B = pkg.Batch(ns, prec=stokes.STOKES_MIXED_FP32, restart=12, orth=orth)
     Ho = oracle_h(n)
     lv = Ho.levels[-1]
     rhs, bo = [], []
