@@ -1,11 +1,12 @@
 // sv_krylov.cu -- FP64 kernels of FGMRES (Section 6.8): the Arnoldi step's
-// classical Gram-Schmidt as two fused passes (all dots plus ||w||^2 in one
-// read of V and w; the update w -= V h plus the new ||w||^2 in another), with
-// a second pass only when the first lost more than half of ||w||^2 (the DGKS
-// test, decided on the device); scaling, Givens rotations and the small
-// triangular solve.  Every reduction is two-stage (warp shuffles, then the
-// last block to finish sums the per-block partials in block order), so each
-// result is deterministic.
+// Gram-Schmidt, either modified (one launch per basis vector: the previous
+// vector's update fused with the next one's dot) or classical as two fused
+// passes (all dots plus ||w||^2 in one read of V and w; the update w -= V h
+// plus the new ||w||^2 in another), with a second pass only when the first lost
+// more than half of ||w||^2 (the DGKS test, decided on the device); scaling,
+// Givens rotations and the small triangular solve.  Every reduction is
+// two-stage (warp shuffles, then the last block to finish sums the per-block
+// partials in block order), so each result is deterministic.
 #include <cuda_runtime.h>
 
 #include <cmath>

@@ -155,6 +155,68 @@ __device__ __forceinline__ void fd_solve_edge(const T* __restrict__ sx, const T*
   }
 }
 
+// FP32: fd_solve_edge for both velocity components at once.  The two components
+// of a patch see the same scalar block K, so the per-axis factors are shared and
+// each step is one packed multiply-add on the (u_x, u_y) pair, term by term the
+// scalar pass: the values are those of two fd_solve_edge calls, in half the
+// dependent steps.  r0, r1: the components' residual windows; y0, y1: their 25
+// outputs (shared memory, also the scratch between the passes).
+__device__ __forceinline__ void fd_solve_edge2(const float* __restrict__ sx, const float* __restrict__ sy,
+                                               const float* __restrict__ dv, int fmask, const float* r0,
+                                               const float* r1, int rs, float* y0, float* y1) {
+  const auto pair = [](float s) { return make_float2(s, s); };
+#pragma unroll 1
+  for (int wj = 0; wj < 5; ++wj) {
+    float2 v[5];
+#pragma unroll
+    for (int wi = 0; wi < 5; ++wi) v[wi] = make_float2(r0[wj * rs + wi], r1[wj * rs + wi]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      float2 a = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int wi = 0; wi < 5; ++wi) a = __ffma2_rn(v[wi], pair(sx[wi * 5 + k]), a);
+      y0[wj * 5 + k] = a.x;
+      y1[wj * 5 + k] = a.y;
+    }
+  }
+#pragma unroll 1
+  for (int k = 0; k < 5; ++k) {
+    float2 v[5], u[5];
+#pragma unroll
+    for (int wj = 0; wj < 5; ++wj) v[wj] = make_float2(y0[wj * 5 + k], y1[wj * 5 + k]);
+#pragma unroll
+    for (int k2 = 0; k2 < 5; ++k2) {
+      float2 a = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int wj = 0; wj < 5; ++wj) a = __ffma2_rn(pair(sy[wj * 5 + k2]), v[wj], a);
+      u[k2] = __fmul2_rn(a, pair(dv[k2 * 5 + k]));
+    }
+#pragma unroll
+    for (int wj = 0; wj < 5; ++wj) {
+      float2 a = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int k2 = 0; k2 < 5; ++k2) a = __ffma2_rn(pair(sy[wj * 5 + k2]), u[k2], a);
+      y0[wj * 5 + k] = a.x;
+      y1[wj * 5 + k] = a.y;
+    }
+  }
+#pragma unroll 1
+  for (int wj = 0; wj < 5; ++wj) {
+    float2 v[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] = make_float2(y0[wj * 5 + k], y1[wj * 5 + k]);
+#pragma unroll
+    for (int wi = 0; wi < 5; ++wi) {
+      float2 a = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int k = 0; k < 5; ++k) a = __ffma2_rn(pair(sx[wi * 5 + k]), v[k], a);
+      const bool keep = (fmask >> (wj * 5 + wi)) & 1;
+      y0[wj * 5 + wi] = keep ? a.x : r0[wj * rs + wi];
+      y1[wj * 5 + wi] = keep ? a.y : r1[wj * rs + wi];
+    }
+  }
+}
+
 // Load a ROWS x WIDTH window (row-major, pitch WIDTH) of src (row stride ld):
 // element (jj, ii) is src[(J0 + jj) ld + I0 + ii] where ok(I, J), else 0.  Warp w
 // takes rows w, w + NW, ...; lane k columns k, k + 32: the row's validity and
@@ -340,13 +402,21 @@ __device__ __forceinline__ void vanka_tile(const LevelDev& L, const R* __restric
 #pragma unroll
       for (int wj = 0; wj < 5; ++wj)
         if ((fy >> wj) & 1) fmask |= fx << (5 * wj);
-#pragma unroll 1
-      for (int c = 0; c < 2; ++c) {
-        R* y = D + c * 25;
-        fd_solve_edge<R>(se + EDGE_S + ax * 25, se + EDGE_S + ay * 25, se + EDGE_DINV + cls * 25, fmask,
-                         sr + c * T::RW * T::RH + (2 * qj) * T::RW + 2 * qi, T::RW, y);
+      if constexpr (sizeof(R) == 4) {   // FP32: both components in one packed pass
+        const R* r0 = sr + (2 * qj) * T::RW + 2 * qi;
+        fd_solve_edge2(se + EDGE_S + ax * 25, se + EDGE_S + ay * 25, se + EDGE_DINV + cls * 25, fmask, r0,
+                       r0 + T::RW * T::RH, T::RW, D, D + 25);
 #pragma unroll 5
-        for (int o = 0; o < 25; ++o) y[o] = fma(-__ldg(C + CD_Z + c * 25 + o), dp, y[o]);
+        for (int o = 0; o < 50; ++o) D[o] = fma(-__ldg(C + CD_Z + o), dp, D[o]);
+      } else {
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+          R* y = D + c * 25;
+          fd_solve_edge<R>(se + EDGE_S + ax * 25, se + EDGE_S + ay * 25, se + EDGE_DINV + cls * 25, fmask,
+                           sr + c * T::RW * T::RH + (2 * qj) * T::RW + 2 * qi, T::RW, y);
+#pragma unroll 5
+          for (int o = 0; o < 25; ++o) y[o] = fma(-__ldg(C + CD_Z + c * 25 + o), dp, y[o]);
+        }
       }
     }
     D[50] = dp;
@@ -431,7 +501,7 @@ __device__ __forceinline__ void vanka_tile(const LevelDev& L, const R* __restric
 }
 
 template <typename R, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) k_vanka(LevelDev L, const R* __restrict__ cd,
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 && NT == 256) ? 3 : 1) k_vanka(LevelDev L, const R* __restrict__ cd,
                                               const FastDiagT<R> fdg, const FastDiagT<float2> fdp,
                                               const R* __restrict__ x,
                                               const R* __restrict__ b, R* __restrict__ xo, R omega,
