@@ -571,6 +571,7 @@ bool launch_orth_update_dots(double* w, const double* V, long long ld, int nk, c
 
 void launch_mgs_step(double* w, const double* Va, const double* Vb, const double* coef, long long N,
                      double* partials, int npart, unsigned* ticket, double* dots, double* norm2, cudaStream_t s) {
+  if (Va == nullptr && Vb == nullptr) return;   // a step reads at least one basis vector
   count_launches(1);
   const dim3 g(npart), b(DOT_NT);
   if (Va == nullptr)   // the first step: <V_0, w> and ||w||^2
